@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 lattice FMM on the uniform 2^20-source / 2^20-target workload.
+
+One step = the whole hot path for one problem: lfmm_plan_create (root box, leaf
+level, leaf buckets, cached model-box operators) + lfmm_eval (P2M, M2M, M2L+L2L,
+P2P+L2P, binary64 final sum), i.e. (N_src + N_tgt) points solved.  value is
+Mpoints/s over the timed steps with inputs resident in device memory; e2e is the
+same through the C ABI with pinned host buffers (copies inside the timed region).
+L2 (129 MB) is flushed between timed steps by writing a 256 MB buffer.
+
+--impl reference times the CPU oracle (brute force, all host cores) on a bounded
+sample of the same workload and reports the same metric, extrapolated.
+Multi-GPU (torchrun): independent replicas, one problem per GPU, no collective in
+the data path; value = points of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s at rel err≤1e-6 (mixed vs plain FP64 on GPU); serve p50/p99 ms"
+WORKLOAD = "uniform_1m: 2^20 distinct sources + 2^20 distinct targets uniform in [0,4096)^2, seed 1"
+L2_FLUSH_BYTES = 256 << 20
+SM_COUNT = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["lfmm", "reference"], default="lfmm")
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, oracle checks, cpu baseline")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic work
+def near_pairs(src, tgt, info) -> int:
+    """Source-target pairs in the same or adjacent leaves (eq. 2.2) of the plan's tree."""
+    x0, y0, s, L = info["x0"], info["y0"], info["leaf_side"], info["L"]
+    n = 1 << L
+    def counts(p):
+        bx = (p[:, 0].astype(np.int64) - x0) // s
+        by = (p[:, 1].astype(np.int64) - y0) // s
+        c = np.zeros((n + 2, n + 2), dtype=np.int64)
+        np.add.at(c, (by + 1, bx + 1), 1)
+        return c
+    cs, ct = counts(src), counts(tgt)
+    nb = sum(np.roll(np.roll(cs, dy, 0), dx, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    return int((nb * ct).sum())
+
+
+def m2l_flops(info, P) -> int:
+    """Useful flops of M2L (+ fused L2L): 2 P^2 per (target box, interaction-list box) pair over
+    levels 2..L (Def. 6.1 lists, truncated at the root boundary), plus 2 P^2 per box for L2L."""
+    total = 0
+    for lvl in range(2, info["L"] + 1):
+        n = 1 << lvl
+        x = np.arange(n)
+        # per axis: number of valid source coordinates for each offset o in [-3, 3]
+        valid = {o: ((x + o >= 0) & (x + o < n)) for o in range(-3, 4)}
+        pairs = 0
+        for px in (0, 1):
+            for py in (0, 1):
+                mx = (x % 2) == px
+                for oy in range(-2 - py, 4 - py):
+                    for ox in range(-2 - px, 4 - px):
+                        if abs(ox) <= 1 and abs(oy) <= 1:
+                            continue
+                        cx = int((valid[ox] & mx).sum())
+                        cy = int((valid[oy] & ((x % 2) == py)).sum())
+                        pairs += cx * cy
+        total += 2 * P * P * pairs
+        if lvl >= 3:
+            total += 2 * P * P * n * n
+    return total
+
+
+# ---------------------------------------------------------------- reference arm (oracle)
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1105_3505_gb300 import workloads
+    oracle.build.build_oracle()
+    prob = workloads.uniform_1m()
+    ns, nt = prob.src.shape[0], prob.tgt.shape[0]
+    rng = np.random.default_rng(2024)
+    sample = 256
+    for _ in range(args.warmup):
+        oracle.lattice_sum(prob.src, prob.f, prob.tgt[rng.choice(nt, 16, replace=False)])
+    times = []
+    for _ in range(args.steps):
+        idx = rng.choice(nt, sample, replace=False)
+        t0 = time.perf_counter()
+        oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    pairs_per_s = sample * ns / t
+    full_s = ns * nt / pairs_per_s
+    value = (ns + nt) / full_s / 1e6
+    out = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "step": f"oracle brute force on {sample} sampled targets x all sources, "
+                                                    "extrapolated to the full solve"},
+           "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"{sample} of {nt} targets x {ns} sources per step"},
+           "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(prob, budget_s=12.0):
+    import oracle
+    ns, nt = prob.src.shape[0], prob.tgt.shape[0]
+    rng = np.random.default_rng(77)
+    t0 = time.perf_counter()
+    oracle.lattice_sum(prob.src, prob.f, prob.tgt[rng.choice(nt, 32, replace=False)])
+    per_tgt = (time.perf_counter() - t0) / 32
+    m = int(min(nt, max(64, budget_s / max(per_tgt, 1e-9))))
+    idx = rng.choice(nt, m, replace=False)
+    t0 = time.perf_counter()
+    oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+    dt = time.perf_counter() - t0
+    pairs_per_s = m * ns / dt
+    full_s = ns * nt / pairs_per_s
+    return {"value": (ns + nt) / full_s / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{m} of {nt} targets x all {ns} sources ({dt:.1f} s), "
+                                        f"extrapolated to the full {ns}x{nt} solve",
+            "pairs_per_s": pairs_per_s}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_1105_3505_gb300", "csrc", e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return e["bytes_per_launch"] if h == e.get("source_sha256_16") else None
+
+
+# ---------------------------------------------------------------- main arm
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1105_3505_gb300 import build as lbuild
+    if rank == 0:
+        lbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1105_3505_gb300 import lfmm, workloads
+    lfmm.load()
+
+    prob = workloads.uniform_1m()
+    ns, nt = prob.src.shape[0], prob.tgt.shape[0]
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    s_d = torch.from_numpy(prob.src).to(dev)
+    t_d = torch.from_numpy(prob.tgt).to(dev)
+    f_d = torch.from_numpy(prob.f).to(dev)
+    u_d = torch.empty(nt, dtype=torch.float64, device=dev)
+    s_h = torch.from_numpy(prob.src).pin_memory()
+    t_h = torch.from_numpy(prob.tgt).pin_memory()
+    f_h = torch.from_numpy(prob.f).pin_memory()
+    u_h = torch.empty(nt, dtype=torch.float64).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    opts = lfmm.make_opts(lfmm.LFMM_MIXED, args.p, 64, 32, 64)
+
+    def step(src, tgt, f, u, o):
+        h = lfmm.lfmm_plan_create(src, ns, tgt, nt, o, stream)
+        lfmm.lfmm_eval(h, f, u, stream)
+        return h
+
+    def timed(src, tgt, f, u, o, steps, warmup, sync_ranks=True):
+        for _ in range(warmup):
+            lfmm.lfmm_plan_destroy(step(src, tgt, f, u, o))
+        torch.cuda.synchronize()
+        if world > 1 and sync_ranks:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        launches0 = lfmm.lfmm_launch_count()
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h = step(src, tgt, f, u, o)
+            b.record(stream)
+            lfmm.lfmm_plan_destroy(h)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        launches = lfmm.lfmm_launch_count() - launches0
+        if world > 1 and sync_ranks:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        return ms, launches
+
+    # device-resident inputs (the value)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    ms, launches = timed(s_d, t_d, f_d, u_d, opts, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    # e2e through host buffers
+    ms_e2e, _ = timed(s_h, t_h, f_h, u_h, opts, args.steps, max(1, args.warmup // 2))
+    if world > 1:
+        t = torch.tensor([ms, ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    value = world * (ns + nt) / (ms * 1e-3) / 1e6
+    value_e2e = world * (ns + nt) / (ms_e2e * 1e-3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # per-phase device time (CUDA events recorded by the library on `stream`)
+    lfmm.lfmm_profile_enable(True)
+    lfmm.lfmm_profile_read(reset=True)
+    n_prof = max(3, min(args.steps, 10))
+    for _ in range(n_prof):
+        flush.fill_(1)
+        lfmm.lfmm_plan_destroy(step(s_d, t_d, f_d, u_d, opts))
+    phases = lfmm.lfmm_profile_read(reset=True)
+    lfmm.lfmm_profile_enable(False)
+    phase_ms = {k: v[0] / n_prof for k, v in phases.items()}
+
+    h = step(s_d, t_d, f_d, u_d, opts)
+    info = lfmm.lfmm_plan_get_info(h)
+    torch.cuda.synchronize()
+    lfmm.lfmm_plan_destroy(h)
+    u_mixed = u_d.cpu().numpy()
+    peaks, peak_src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+
+    # roofline of the dominant kernel
+    pairs = near_pairs(prob.src, prob.tgt, info)
+    P = 4 * (args.p - 1)
+    flops_m2l = m2l_flops(info, P)
+    dom = max(("p2p", "m2l", "tree", "p2m", "m2m"), key=lambda k: phase_ms.get(k, 0.0))
+    if dom == "p2p":
+        # one 4-byte table load + one FMA per pair; binding pipe = shared-memory loads,
+        # 32 lanes per clock per SM
+        achieved = pairs / (phase_ms["p2p"] * 1e-3) / 1e12
+        peak = SM_COUNT * 32 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "p2p_l2p_kernel<float,32>", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Tpairs/s", "frac": achieved / peak, "traffic": traffic_for("p2p_l2p"),
+                "peak_basis": f"152 SMs x 32 shared-memory load lanes/clk x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
+                "units_per_launch": pairs}
+    elif dom == "m2l":
+        achieved = flops_m2l / (phase_ms["m2l"] * 1e-3) / 1e12
+        peak = SM_COUNT * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "m2l_kernel<float,32>", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l"),
+                "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_src})",
+                "units_per_launch": flops_m2l}
+    else:
+        # tree build: algorithmic minimum of read coordinates + write bucketed (loc, perm)
+        bytes_tree = (ns + nt) * (8 + 8 + 8)
+        achieved = bytes_tree / (phase_ms[dom] * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "units_per_launch": bytes_tree}
+
+    out = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "p": args.p, "P": info["P"], "leaf_size": 64, "leaf_side": info["leaf_side"],
+                      "levels": info["L"], "precision": "mixed (fp32 near/far, fp64 final sum)",
+                      "step": "lfmm_plan_create + lfmm_eval", "l2": "flushed between timed steps (256 MB write)",
+                      "parallelism": f"replicas x{world}"},
+           "e2e": {"value": value_e2e, "unit": "Mpoints/s", "ms_per_step": ms_e2e,
+                   "h2d_bytes_per_step": int(s_h.numel() * 4 + t_h.numel() * 4 + f_h.numel() * 8),
+                   "d2h_bytes_per_step": int(u_h.numel() * 8)},
+           "gpu_launches": int(launches),
+           "roofline": roof,
+           "phases_ms": phase_ms,
+           "clocks": clocks}
+
+    if not args.no_extras:
+        import oracle
+        idx = np.random.default_rng(123).choice(nt, 128, replace=False)
+        ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+        scale = np.abs(ref).max()
+        out["rel_err"] = float(np.abs(u_mixed[idx] - ref).max() / scale)
+        # the plain all-binary64 path at p = 16 on the same workload
+        o64 = lfmm.make_opts(lfmm.LFMM_FP64, 16, 64, 32, 64)
+        ms64, _ = timed(s_d, t_d, f_d, u_d, o64, max(2, args.steps // 5), 1, sync_ranks=False)
+        u64 = u_d.cpu().numpy()
+        out["fp64_plain_p16"] = {"value": (ns + nt) / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
+                                 "rel_err": float(np.abs(u64[idx] - ref).max() / scale)}
+        out["cpu_baseline"] = cpu_baseline(prob)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

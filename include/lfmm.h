@@ -1,0 +1,179 @@
+/* lfmm.h - C ABI of the GB300 lattice fast multipole method library (liblfmm.so).
+ *
+ * The library evaluates the lattice sum
+ *
+ *     u(m) = sum_n phi(m - n) f(n),     m, n in Z^2                (eq. 1.7 / eq. 2.1)
+ *
+ * for finitely many source points n (charges f) and target points m, where phi
+ * is the fundamental solution of the 5-point discrete Laplacian A (eq. 1.2),
+ * normalised by the Fourier integral eq. 1.8 so that phi(0) = 0 and
+ * A phi = delta_0.  The evaluation is the lattice FMM of Sec. 8: a uniform
+ * quadtree (Sec. 6), skeleton-based outgoing/incoming expansions (Sec. 4-5),
+ * the translation operators T_ofs, T_ofo, T_ifo, T_ifi, T_tfi (Sec. 7), and a
+ * direct near field from a tabulated phi (Sec. 2, Sec. 3).
+ *
+ * Conventions
+ *  - Every entry point returns an int status (LFMM_OK = 0 on success); nothing
+ *    throws across this boundary and nothing exits the process.
+ *    lfmm_last_error() gives a human-readable detail for the calling thread.
+ *  - Coordinates are int32 pairs interleaved (x0, y0, x1, y1, ...).
+ *  - Any array argument may live in host memory (pageable or pinned) or in
+ *    device memory of the current CUDA device; the library detects which with
+ *    cudaPointerGetAttributes and copies host data through its own buffers.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it; when an output is a host pointer the call returns after
+ *    the result has been copied back, otherwise it returns asynchronously.
+ *  - The caller keeps ownership of all arrays it passes.  A plan owns copies of
+ *    the (sorted) coordinates, the tree, and its workspaces; the per-level
+ *    operators and the phi table live in a process-wide cache shared by plans.
+ *  - A plan may be used from one thread at a time; concurrent lfmm_eval calls
+ *    on one plan race on its workspaces.
+ */
+#ifndef LFMM_H
+#define LFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define LFMM_OK 0
+#define LFMM_EINVAL 1        /* invalid argument (NULL, n < 0, extent > 2^30, bad opts) */
+#define LFMM_ENOMEM 2        /* device or host allocation failed; nothing leaked       */
+#define LFMM_ECUDA 3         /* a CUDA runtime call failed (detail in lfmm_last_error)  */
+#define LFMM_ETIMEOUT 4      /* a bounded device-side wait gave up                      */
+#define LFMM_EUNSUPPORTED 5  /* valid request this build does not handle                */
+#define LFMM_EINTERNAL 6     /* internal consistency check failed                       */
+
+/* ---- precision paths ------------------------------------------------------------- */
+/* LFMM_FP64: every step in binary64 (the plain path, relative error <= 1e-10 at p >= 16).
+ * LFMM_MIXED: near field, expansions and translations in binary32, charges rounded
+ *   to binary32, the per-target sum of near and far parts in binary64 (<= 1e-6). */
+#define LFMM_FP64 0
+#define LFMM_MIXED 1
+
+typedef struct lfmm_plan lfmm_plan;
+
+typedef struct lfmm_opts {
+    int32_t precision;        /* LFMM_FP64 or LFMM_MIXED                                      */
+    int32_t p;                /* expansion order, 2 <= p <= 17; skeleton size P = 4(p-1)        */
+                              /* (Table 4.1: P ~ 27 gives 1e-8, P ~ 49 gives 1e-13)           */
+    int32_t leaf_size;        /* N_leaf of Sec. 6: the leaf level is the coarsest level whose  */
+                              /* boxes hold at most N_leaf sources and at most N_leaf targets  */
+    int32_t max_leaf_side;    /* largest leaf side in lattice cells, a power of 2 in [1, 32]   */
+    int32_t proxies_per_edge; /* proxy points per edge of the proxy ring of Sec. 5 (>= 8);     */
+                              /* the remark of Sec. 5 finds 40 enough for 1e-10               */
+    int32_t reserved[3];      /* must be zero                                                 */
+} lfmm_opts;
+
+/* Fill opts with the defaults: LFMM_MIXED, p = 8, leaf_size = 64, max_leaf_side = 32,
+ * proxies_per_edge = 64. */
+void lfmm_opts_default(lfmm_opts* opts);
+
+/* Build a plan for fixed source and target locations (Sec. 8.1 precomputation):
+ * root box, uniform quadtree with leaf level chosen by N_leaf (Sec. 6), points
+ * bucketed by leaf in Morton order, and the per-level skeletons and translation
+ * operators of the model boxes (Sec. 8.1 steps 3-4, Remark 8.2), which are cached
+ * process-wide by (leaf side, P, proxies per edge, precision).
+ *   plan     out: the new plan, or NULL on failure
+ *   src_xy   2*n_src int32 (host or device); n_src >= 1
+ *   tgt_xy   2*n_tgt int32 (host or device); n_tgt >= 1
+ *   opts     NULL for the defaults
+ *   stream   cudaStream_t for all device work
+ * The points must span at most 2^30 lattice cells per axis (LFMM_EINVAL).
+ * Duplicate points are allowed (the sum is linear).  Synchronises `stream` twice
+ * (the root box and the leaf level are read back to size the workspaces). */
+int lfmm_plan_create(lfmm_plan** plan, const int32_t* src_xy, int64_t n_src,
+                     const int32_t* tgt_xy, int64_t n_tgt, const lfmm_opts* opts, void* stream);
+
+/* Apply the plan (Sec. 8.2): u[i] = sum_j phi(tgt_i - src_j) f[j] for all targets,
+ * in the caller's target order.  f: n_src doubles, u: n_tgt doubles (host or device).
+ * A coincident source contributes phi(0) = 0.  If sum(f) != 0 the result keeps the
+ * normalisation phi(0) = 0 of eq. 1.8. */
+int lfmm_eval(lfmm_plan* plan, const double* f, double* u, void* stream);
+
+/* As lfmm_eval but returns the two parts separately: u_near (same and adjacent
+ * leaves, eq. 2.2) and u_far (everything else, eq. 2.4, through the expansions). */
+int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_far, void* stream);
+
+/* Release a plan (NULL is a no-op).  Waits for the plan's outstanding work. */
+int lfmm_plan_destroy(lfmm_plan* plan);
+
+typedef struct lfmm_plan_info {
+    int64_t n_src, n_tgt;
+    int64_t x0, y0;           /* lower-left corner of the root box                       */
+    int32_t K;                /* root side 2^K                                          */
+    int32_t L;                /* leaf level; 4^L leaves of side 2^(K-L)                  */
+    int32_t leaf_side;
+    int32_t P;                /* skeleton size of the leaf model box                     */
+    int32_t P_pad;            /* padded expansion length in device arrays (32 or 64)     */
+    int32_t precision;
+    int32_t max_leaf_src;     /* largest number of sources in one leaf                   */
+    int32_t max_leaf_tgt;
+    int64_t device_bytes;     /* device memory owned by the plan (not the shared cache)  */
+} lfmm_plan_info;
+
+int lfmm_plan_get_info(const lfmm_plan* plan, lfmm_plan_info* info);
+
+const char* lfmm_status_string(int status);
+/* Detail of the last failure on the calling thread ("" if none). */
+const char* lfmm_last_error(void);
+
+/* ---- tracing ---------------------------------------------------------------------- */
+/* Phases timed by the profiler with CUDA events recorded on the stream each phase is
+ * enqueued on (plan create: TREE, OPERATORS; eval: the sweeps of Sec. 8.2). */
+#define LFMM_PHASE_TREE 0       /* root box, leaf level, leaf buckets (Sec. 6)          */
+#define LFMM_PHASE_OPERATORS 1  /* model-box operator cache lookup / upload (Sec. 8.1)  */
+#define LFMM_PHASE_P2M 2        /* step 1: T_ofs                                        */
+#define LFMM_PHASE_M2M 3        /* step 2: T_ofo                                        */
+#define LFMM_PHASE_M2L 4        /* steps 3-4: T_ifo and T_ifi                           */
+#define LFMM_PHASE_P2P 5        /* step 5: near field, T_tfi, binary64 final sum        */
+#define LFMM_PHASE_COPY 6       /* host<->device copies of coordinates, f and u         */
+#define LFMM_NUM_PHASES 7
+
+/* Turn per-phase timing on (1) or off (0).  While on, every create/eval synchronises its
+ * stream once at the end to read the events.  Process-wide. */
+int lfmm_profile_enable(int enable);
+/* ms[i], launches[i] (either may be NULL; LFMM_NUM_PHASES entries) accumulated since the
+ * last reset; reset != 0 clears them after reading. */
+int lfmm_profile_read(double* ms, int64_t* launches, int reset);
+/* Total kernels this library has launched in the process (always counted). */
+int64_t lfmm_launch_count(void);
+
+/* ---- host-side views of the precomputation (no GPU needed) ------------------------- */
+
+/* The library's phi on the packed octant 0 <= lo <= hi <= R, entry hi*(hi+1)/2 + lo,
+ * computed by the one-dimensional integral of Remark 3.1 (t1 integrated in closed
+ * form, composite Gauss-Legendre in t2).  1 <= R <= 256; out holds (R+1)(R+2)/2 doubles. */
+int lfmm_phi_table(int32_t R, double* out);
+
+/* phi at n integer offsets d = (dx0, dy0, dx1, dy1, ...): the table above for
+ * |d|_inf <= 128, the asymptotic expansion eq. 3.1 beyond. */
+int lfmm_phi(const int64_t* d, int64_t n, double* out);
+
+/* Skeleton of the model box `level_above_leaf` levels above a leaf of side
+ * leaf_side (box side leaf_side * 2^level_above_leaf, lower-left corner at 0):
+ * xy receives up to 2*64 int32, *count the skeleton size (Sec. 5, Sec. 8.1 step 3). */
+int lfmm_model_skeleton(int32_t leaf_side, int32_t p, int32_t proxies_per_edge,
+                        int32_t level_above_leaf, int32_t* xy, int32_t* count);
+
+/* Leaf outgoing-from-sources operator for the dense leaf box (Remark 8.2):
+ * out receives count x leaf_side^2 doubles, row-major, column j the lattice point
+ * (j % leaf_side, j / leaf_side).  T_tfi is its transpose (Sec. 7). */
+int lfmm_model_tofs(int32_t leaf_side, int32_t p, int32_t proxies_per_edge, double* out);
+
+/* Parent-from-children interpolation S of Sec. 7 at `level_above_leaf` >= 1:
+ * out receives count_parent x (4 * count_child) doubles, row-major; column block i
+ * (children in Morton order (0,0),(1,0),(0,1),(1,1)) is T_ofo for child i, and its
+ * transpose is T_ifi. */
+int lfmm_model_s(int32_t leaf_side, int32_t p, int32_t proxies_per_edge,
+                 int32_t level_above_leaf, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFMM_H */

@@ -1,0 +1,531 @@
+// C ABI of liblfmm.so: plans, evaluation, diagnostics (declared in include/lfmm.h).
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+
+#include "lfmm_internal.h"
+
+namespace lfmm {
+
+namespace {
+thread_local std::string t_last_error;
+}
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+    t_last_error = msg;
+    return status;
+}
+
+const char* last_error_cstr() { return t_last_error.c_str(); }
+
+}  // namespace lfmm
+
+using namespace lfmm;
+
+struct lfmm_plan {
+    int device = 0;
+    int num_sms = 0;
+    lfmm_opts opts{};
+    int64_t ns = 0, nt = 0;
+    int64_t x0 = 0, y0 = 0;
+    int K = 0, L = 0, side = 1;
+    int P = 0, NP = 32;
+    int max_src = 0, max_tgt = 0;
+    const DeviceOps* ops = nullptr;
+    cudaStream_t last_stream = nullptr;
+    // device buffers (plan-owned, stream-ordered pool allocations)
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int32_t *src_begin = nullptr, *tgt_begin = nullptr;
+    int32_t *src_loc = nullptr, *src_perm = nullptr, *tgt_loc = nullptr, *tgt_perm = nullptr;
+    void* f_sorted = nullptr;
+    void* qhat = nullptr;
+    void* uhat = nullptr;
+    std::vector<int64_t> lvl_off;  // offset (boxes) of level l inside qhat / uhat
+    double* f_stage = nullptr;     // device copy of a host f
+    double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
+};
+
+namespace {
+
+constexpr int kMaxLevel = 13;  // 4^13 leaves at most on the uniform tree
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void setup_pool(int dev) {
+    static std::once_flag once;
+    std::call_once(once, [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    });
+}
+
+int palloc(lfmm_plan* p, void** out, size_t bytes, cudaStream_t s) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(out, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return fail(LFMM_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                     " bytes failed: " + cudaGetErrorString(e));
+    }
+    p->allocs.push_back(*out);
+    p->bytes += (int64_t)bytes;
+    return LFMM_OK;
+}
+
+struct Temp {  // stream-ordered temporary freed on scope exit
+    void* ptr = nullptr;
+    cudaStream_t s = nullptr;
+    ~Temp() {
+        if (ptr) cudaFreeAsync(ptr, s);
+    }
+};
+
+int talloc(Temp& t, size_t bytes, cudaStream_t s) {
+    t.s = s;
+    cudaError_t e = cudaMallocAsync(&t.ptr, bytes ? bytes : 16, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        t.ptr = nullptr;
+        return fail(LFMM_ENOMEM, std::string("temporary allocation failed: ") + cudaGetErrorString(e));
+    }
+    return LFMM_OK;
+}
+
+void free_plan_buffers(lfmm_plan* p) {
+    for (void* a : p->allocs) cudaFreeAsync(a, p->last_stream);
+    p->allocs.clear();
+}
+
+int validate_opts(const lfmm_opts& o) {
+    if (o.precision != LFMM_FP64 && o.precision != LFMM_MIXED)
+        return fail(LFMM_EINVAL, "opts.precision must be LFMM_FP64 or LFMM_MIXED");
+    if (o.p < 2 || o.p > 17) return fail(LFMM_EINVAL, "opts.p must be in [2, 17]");
+    if (o.leaf_size < 1) return fail(LFMM_EINVAL, "opts.leaf_size must be >= 1");
+    if (o.max_leaf_side < 1 || o.max_leaf_side > kMaxLeafSide ||
+        (o.max_leaf_side & (o.max_leaf_side - 1)))
+        return fail(LFMM_EINVAL, "opts.max_leaf_side must be a power of 2 in [1, 32]");
+    if (o.proxies_per_edge < 8 || o.proxies_per_edge > 1024)
+        return fail(LFMM_EINVAL, "opts.proxies_per_edge must be in [8, 1024]");
+    for (int r : o.reserved)
+        if (r != 0) return fail(LFMM_EINVAL, "opts.reserved must be zero");
+    return LFMM_OK;
+}
+
+int ilog2_ceil(int64_t v) {
+    int k = 0;
+    while (((int64_t)1 << k) < v) ++k;
+    return k;
+}
+
+// Coordinates usable by the kernels: 8-byte aligned device memory.
+int device_coords(lfmm_plan* p, const int32_t* xy, int64_t n, const int32_t** out, cudaStream_t s) {
+    const bool dev = is_device_ptr(xy);
+    if (dev && ((uintptr_t)xy % 8) == 0) {
+        *out = xy;
+        return LFMM_OK;
+    }
+    void* buf;
+    int st = palloc(p, &buf, (size_t)n * 8, s);
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(buf, xy, (size_t)n * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("coordinate copy: ") + cudaGetErrorString(e));
+    *out = (const int32_t*)buf;
+    return LFMM_OK;
+}
+
+int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaStream_t s) {
+    int st;
+    LFMM_CUDA_TRY(cudaGetDevice(&p->device));
+    LFMM_CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    setup_pool(p->device);
+    const int32_t *src, *tgt;
+    {
+        PhaseTimer pt(LFMM_PHASE_COPY, s);
+        if ((st = device_coords(p, src_xy, p->ns, &src, s))) return st;
+        if ((st = device_coords(p, tgt_xy, p->nt, &tgt, s))) return st;
+    }
+    std::unique_ptr<PhaseTimer> tree_timer(new PhaseTimer(LFMM_PHASE_TREE, s));
+
+    // ---- root box (Sec. 6): lower-left corner of all points, side 2^K
+    Temp t4;
+    if ((st = talloc(t4, 8 * sizeof(int), s))) return st;
+    int* d4 = (int*)t4.ptr;
+    LFMM_CUDA_TRY(launch_set4(d4, INT_MAX, INT_MAX, INT_MIN, INT_MIN, s));
+    LFMM_CUDA_TRY(launch_bbox(src, p->ns, tgt, p->nt, d4, s));
+    tree_timer->add_launches(2);
+    int h4[4];
+    LFMM_CUDA_TRY(cudaMemcpyAsync(h4, d4, sizeof(h4), cudaMemcpyDeviceToHost, s));
+    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    p->x0 = h4[0];
+    p->y0 = h4[1];
+    const int64_t ext = std::max((int64_t)h4[2] - h4[0], (int64_t)h4[3] - h4[1]) + 1;
+    if (ext > ((int64_t)1 << 30)) return fail(LFMM_EINVAL, "points span more than 2^30 lattice cells");
+    p->K = ilog2_ceil(ext);
+
+    // ---- leaf level: coarsest level with <= N_leaf sources and targets per box,
+    // leaf side <= max_leaf_side.  Levels below the pigeonhole bound cannot qualify.
+    const int nleaf = p->opts.leaf_size;
+    const int L_side = std::max(0, p->K - ilog2_ceil(p->opts.max_leaf_side));
+    const int64_t nmax = std::max(p->ns, p->nt);
+    int L_pig = 0;
+    while (((int64_t)nleaf << (2 * L_pig)) < nmax) ++L_pig;
+    int L_try = std::max(L_side, L_pig);
+    if (L_try > p->K) L_try = p->K;
+    int Lf = std::min(p->K, L_try + 1);
+    Temp cnt;
+    int32_t *cs = nullptr, *ct = nullptr;  // counts at the chosen level
+    int chosen = -1;
+    for (;;) {
+        if (Lf > kMaxLevel)
+            return fail(LFMM_EUNSUPPORTED, "uniform tree would need more than 4^13 leaves");
+        const int64_t nf = (int64_t)1 << (2 * Lf);
+        const int64_t nc = Lf >= 1 ? nf / 4 : 0;
+        Temp c2;
+        if ((st = talloc(c2, (size_t)(2 * nf + 2 * nc) * sizeof(int32_t), s))) return st;
+        int32_t* fs = (int32_t*)c2.ptr;
+        int32_t* ft = fs + nf;
+        int32_t* ccs = ft + nf;
+        int32_t* cct = ccs + nc;
+        LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
+        LFMM_CUDA_TRY(launch_histogram(src, p->ns, tgt, p->nt, p->x0, p->y0, p->K - Lf, fs, ft, s));
+        tree_timer->add_launches(1);
+        int m4[4] = {(int)std::min<int64_t>(p->ns, INT_MAX), (int)std::min<int64_t>(p->nt, INT_MAX), 0, 0};
+        if (Lf >= 1) {
+            LFMM_CUDA_TRY(launch_set4(d4 + 4, 0, 0, 0, 0, s));
+            LFMM_CUDA_TRY(launch_coarsen(fs, ft, nc, ccs, cct, d4 + 4, s));
+            tree_timer->add_launches(2);
+            LFMM_CUDA_TRY(cudaMemcpyAsync(m4, d4 + 4, sizeof(m4), cudaMemcpyDeviceToHost, s));
+            LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        if (Lf - 1 >= L_try && std::max(m4[2], m4[3]) <= nleaf) {
+            chosen = Lf - 1;
+            p->max_src = m4[2];
+            p->max_tgt = m4[3];
+            cs = ccs;
+            ct = cct;
+        } else if (std::max(m4[0], m4[1]) <= nleaf || Lf == p->K) {
+            chosen = Lf;
+            p->max_src = m4[0];
+            p->max_tgt = m4[1];
+            cs = fs;
+            ct = ft;
+        }
+        if (chosen >= 0) {
+            cnt.ptr = c2.ptr;  // keep the counts alive
+            cnt.s = s;
+            c2.ptr = nullptr;
+            break;
+        }
+        Lf = std::min(p->K, Lf + 2);
+    }
+    p->L = chosen;
+    p->side = 1 << (p->K - p->L);
+    const int64_t n_leaves = (int64_t)1 << (2 * p->L);
+
+    // ---- buckets
+    void* buf;
+    if ((st = palloc(p, &buf, (size_t)2 * (n_leaves + 1) * sizeof(int32_t), s))) return st;
+    p->src_begin = (int32_t*)buf;
+    p->tgt_begin = p->src_begin + (n_leaves + 1);
+    Temp part;
+    if ((st = talloc(part, scan_partials_size(n_leaves) * sizeof(int32_t), s))) return st;
+    LFMM_CUDA_TRY(launch_scan2(cs, p->src_begin, ct, p->tgt_begin, n_leaves, (int32_t*)part.ptr, s));
+    tree_timer->add_launches(3);
+    if ((st = palloc(p, &buf, (size_t)2 * (p->ns + p->nt) * sizeof(int32_t), s))) return st;
+    p->src_loc = (int32_t*)buf;
+    p->src_perm = p->src_loc + p->ns;
+    p->tgt_loc = p->src_perm + p->ns;
+    p->tgt_perm = p->tgt_loc + p->nt;
+    Temp cur;
+    if ((st = talloc(cur, (size_t)2 * n_leaves * sizeof(int32_t), s))) return st;
+    LFMM_CUDA_TRY(cudaMemsetAsync(cur.ptr, 0, (size_t)2 * n_leaves * sizeof(int32_t), s));
+    LFMM_CUDA_TRY(launch_scatter(src, p->ns, p->x0, p->y0, p->K - p->L, p->side, p->src_begin,
+                                 (int32_t*)cur.ptr, p->src_loc, p->src_perm, s));
+    LFMM_CUDA_TRY(launch_scatter(tgt, p->nt, p->x0, p->y0, p->K - p->L, p->side, p->tgt_begin,
+                                 (int32_t*)cur.ptr + n_leaves, p->tgt_loc, p->tgt_perm, s));
+    tree_timer->add_launches(2);
+    tree_timer.reset();
+    PhaseTimer op_timer(LFMM_PHASE_OPERATORS, s);
+
+    // ---- operators of the model boxes (cached across plans)
+    p->P = 4 * (p->opts.p - 1);
+    p->NP = p->P <= 32 ? 32 : 64;
+    const int n_levels = std::max(1, p->L - 1);
+    std::string err;
+    ModelOps* mo = get_model_ops(p->side, p->P, p->opts.proxies_per_edge, n_levels, &err);
+    if (!mo) return fail(LFMM_EINTERNAL, err);
+    p->ops = get_device_ops(mo, p->opts.precision, p->NP, n_levels, s, &err);
+    if (!p->ops) return fail(LFMM_ECUDA, err);
+
+    // ---- workspaces: sorted charges, expansions of levels min(2,L)..L
+    const size_t esz = p->opts.precision == LFMM_MIXED ? sizeof(float) : sizeof(double);
+    if ((st = palloc(p, &p->f_sorted, (size_t)p->ns * esz, s))) return st;
+    p->lvl_off.assign(p->L + 2, 0);
+    int64_t boxes = 0;
+    for (int l = std::min(2, p->L); l <= p->L; ++l) {
+        p->lvl_off[l] = boxes;
+        boxes += (int64_t)1 << (2 * l);
+    }
+    if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
+    if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
+    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    return LFMM_OK;
+}
+
+template <typename T>
+int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
+    TreeView t;
+    t.L = p->L;
+    t.side = p->side;
+    t.n_leaves = (int64_t)1 << (2 * p->L);
+    t.src_begin = p->src_begin;
+    t.tgt_begin = p->tgt_begin;
+    t.src_loc = p->src_loc;
+    t.src_perm = p->src_perm;
+    t.tgt_loc = p->tgt_loc;
+    t.tgt_perm = p->tgt_perm;
+    const DeviceOps& ops = *p->ops;
+    const int NP = p->NP;
+    T* q = (T*)p->qhat;
+    T* uh = (T*)p->uhat;
+    auto Q = [&](int l) { return q + (size_t)p->lvl_off[l] * NP; };
+    auto U = [&](int l) { return uh + (size_t)p->lvl_off[l] * NP; };
+    const int L = p->L;
+    {
+        PhaseTimer pt(LFMM_PHASE_P2M, s);
+        LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, Q(L), s));
+        pt.add_launches(1);
+    }
+    {
+        PhaseTimer pt(LFMM_PHASE_M2M, s);
+        for (int l = L - 1; l >= 2; --l) {
+            LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, Q(l + 1), Q(l), (int64_t)1 << (2 * l), s));
+            pt.add_launches(1);
+        }
+    }
+    {
+        PhaseTimer pt(LFMM_PHASE_M2L, s);
+        for (int l = 2; l <= L; ++l) {
+            LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Q(l), l >= 3 ? U(l - 1) : nullptr, U(l), s));
+            pt.add_launches(1);
+        }
+    }
+    {
+        PhaseTimer pt(LFMM_PHASE_P2P, s);
+        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, L >= 2 ? U(L) : nullptr, u, un,
+                                        uf, p->num_sms, s));
+        pt.add_launches(1);
+    }
+    return LFMM_OK;
+}
+
+int eval_common(lfmm_plan* p, const double* f, double* u, double* un, double* uf, void* stream) {
+    if (!p || !f) return fail(LFMM_EINVAL, "NULL plan or f");
+    if (!u && !un && !uf) return fail(LFMM_EINVAL, "no output");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    const double* fd = f;
+    if (!is_device_ptr(f)) {
+        if (!p->f_stage) {
+            void* b;
+            int st = palloc(p, &b, (size_t)p->ns * sizeof(double), s);
+            if (st) return st;
+            p->f_stage = (double*)b;
+        }
+        PhaseTimer pt(LFMM_PHASE_COPY, s);
+        LFMM_CUDA_TRY(cudaMemcpyAsync(p->f_stage, f, (size_t)p->ns * sizeof(double), cudaMemcpyHostToDevice, s));
+        fd = p->f_stage;
+    }
+    double* outs[3] = {u, un, uf};
+    double* douts[3] = {u, un, uf};
+    bool host_out[3] = {false, false, false};
+    for (int i = 0; i < 3; ++i) {
+        if (!outs[i] || is_device_ptr(outs[i])) continue;
+        if (!p->u_stage) {
+            void* b;
+            int st = palloc(p, &b, (size_t)3 * p->nt * sizeof(double), s);
+            if (st) return st;
+            p->u_stage = (double*)b;
+        }
+        douts[i] = p->u_stage + (size_t)i * p->nt;
+        host_out[i] = true;
+    }
+    int st = p->opts.precision == LFMM_MIXED ? eval_impl<float>(p, fd, douts[0], douts[1], douts[2], s)
+                                             : eval_impl<double>(p, fd, douts[0], douts[1], douts[2], s);
+    if (st) return st;
+    bool any_host = false;
+    {
+        PhaseTimer pt(LFMM_PHASE_COPY, s);
+        for (int i = 0; i < 3; ++i)
+            if (host_out[i]) {
+                LFMM_CUDA_TRY(cudaMemcpyAsync(outs[i], douts[i], (size_t)p->nt * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s));
+                any_host = true;
+            }
+    }
+    if (any_host) LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (profiling_enabled()) profile_flush();
+    return LFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lfmm_opts_default(lfmm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = LFMM_MIXED;
+    o->p = 8;
+    o->leaf_size = 64;
+    o->max_leaf_side = 32;
+    o->proxies_per_edge = 64;
+}
+
+int lfmm_plan_create(lfmm_plan** plan, const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy,
+                     int64_t n_tgt, const lfmm_opts* opts, void* stream) {
+    if (!plan) return fail(LFMM_EINVAL, "NULL plan out-pointer");
+    *plan = nullptr;
+    if (!src_xy || !tgt_xy) return fail(LFMM_EINVAL, "NULL coordinates");
+    if (n_src < 1 || n_tgt < 1 || n_src > INT32_MAX / 2 || n_tgt > INT32_MAX / 2)
+        return fail(LFMM_EINVAL, "n_src and n_tgt must be in [1, 2^30)");
+    lfmm_opts o;
+    if (opts) o = *opts;
+    else lfmm_opts_default(&o);
+    int st = validate_opts(o);
+    if (st) return st;
+    lfmm_plan* p = new (std::nothrow) lfmm_plan();
+    if (!p) return fail(LFMM_ENOMEM, "host allocation failed");
+    p->opts = o;
+    p->ns = n_src;
+    p->nt = n_tgt;
+    p->last_stream = (cudaStream_t)stream;
+    st = plan_build(p, src_xy, tgt_xy, (cudaStream_t)stream);
+    if (st) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaGetLastError();
+        free_plan_buffers(p);
+        delete p;
+        return st;
+    }
+    set_error("");
+    if (profiling_enabled()) profile_flush();
+    *plan = p;
+    return LFMM_OK;
+}
+
+int lfmm_eval(lfmm_plan* plan, const double* f, double* u, void* stream) {
+    return eval_common(plan, f, u, nullptr, nullptr, stream);
+}
+
+int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_far, void* stream) {
+    if (!u_near || !u_far) return fail(LFMM_EINVAL, "NULL output");
+    return eval_common(plan, f, nullptr, u_near, u_far, stream);
+}
+
+int lfmm_plan_destroy(lfmm_plan* plan) {
+    if (!plan) return LFMM_OK;
+    free_plan_buffers(plan);
+    cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    delete plan;
+    if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("plan destroy: ") + cudaGetErrorString(e));
+    return LFMM_OK;
+}
+
+int lfmm_plan_get_info(const lfmm_plan* p, lfmm_plan_info* info) {
+    if (!p || !info) return fail(LFMM_EINVAL, "NULL argument");
+    info->n_src = p->ns;
+    info->n_tgt = p->nt;
+    info->x0 = p->x0;
+    info->y0 = p->y0;
+    info->K = p->K;
+    info->L = p->L;
+    info->leaf_side = p->side;
+    info->P = p->ops ? p->P : 0;
+    info->P_pad = p->NP;
+    info->precision = p->opts.precision;
+    info->max_leaf_src = p->max_src;
+    info->max_leaf_tgt = p->max_tgt;
+    info->device_bytes = p->bytes;
+    return LFMM_OK;
+}
+
+const char* lfmm_status_string(int status) {
+    switch (status) {
+        case LFMM_OK: return "ok";
+        case LFMM_EINVAL: return "invalid argument";
+        case LFMM_ENOMEM: return "out of memory";
+        case LFMM_ECUDA: return "CUDA error";
+        case LFMM_ETIMEOUT: return "device wait timed out";
+        case LFMM_EUNSUPPORTED: return "unsupported";
+        case LFMM_EINTERNAL: return "internal error";
+        default: return "unknown status";
+    }
+}
+
+const char* lfmm_last_error(void) { return lfmm::last_error_cstr(); }
+
+int lfmm_phi_table(int32_t R, double* out) {
+    if (!out || R < 1 || R > 256) return fail(LFMM_EINVAL, "R must be in [1, 256]");
+    std::vector<double> t = R <= kPhiHostRadius ? phi_host_table() : compute_phi_octant(R);
+    std::memcpy(out, t.data(), sizeof(double) * (size_t)(R + 1) * (R + 2) / 2);
+    return LFMM_OK;
+}
+
+int lfmm_phi(const int64_t* d, int64_t n, double* out) {
+    if (!d || !out || n < 0) return fail(LFMM_EINVAL, "bad arguments");
+    for (int64_t i = 0; i < n; ++i) out[i] = phi_host(d[2 * i], d[2 * i + 1]);
+    return LFMM_OK;
+}
+
+int lfmm_model_skeleton(int32_t leaf_side, int32_t p, int32_t ppe, int32_t level, int32_t* xy, int32_t* count) {
+    if (!xy || !count || p < 2 || p > 17 || level < 0) return fail(LFMM_EINVAL, "bad arguments");
+    std::string err;
+    ModelOps* mo = get_model_ops(leaf_side, 4 * (p - 1), ppe, level + 1, &err);
+    if (!mo) return fail(LFMM_EINVAL, err);
+    std::lock_guard<std::mutex> g(mo->mu);
+    const LevelOps& lv = mo->levels[level];
+    *count = lv.P;
+    for (int i = 0; i < 2 * lv.P; ++i) xy[i] = lv.skel[i];
+    return LFMM_OK;
+}
+
+int lfmm_model_tofs(int32_t leaf_side, int32_t p, int32_t ppe, double* out) {
+    if (!out || p < 2 || p > 17) return fail(LFMM_EINVAL, "bad arguments");
+    std::string err;
+    ModelOps* mo = get_model_ops(leaf_side, 4 * (p - 1), ppe, 1, &err);
+    if (!mo) return fail(LFMM_EINVAL, err);
+    std::lock_guard<std::mutex> g(mo->mu);
+    std::memcpy(out, mo->tofs.data(), mo->tofs.size() * sizeof(double));
+    return LFMM_OK;
+}
+
+int lfmm_model_s(int32_t leaf_side, int32_t p, int32_t ppe, int32_t level, double* out) {
+    if (!out || p < 2 || p > 17 || level < 1) return fail(LFMM_EINVAL, "bad arguments");
+    std::string err;
+    ModelOps* mo = get_model_ops(leaf_side, 4 * (p - 1), ppe, level + 1, &err);
+    if (!mo) return fail(LFMM_EINVAL, err);
+    std::lock_guard<std::mutex> g(mo->mu);
+    const LevelOps& lv = mo->levels[level];
+    std::memcpy(out, lv.S.data(), lv.S.size() * sizeof(double));
+    return LFMM_OK;
+}
+
+}  // extern "C"

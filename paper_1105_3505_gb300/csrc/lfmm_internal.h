@@ -1,0 +1,181 @@
+// Internal declarations shared by the translation units of liblfmm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <array>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lfmm.h"
+
+namespace lfmm {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+
+#define LFMM_CUDA_TRY(expr)                                                            \
+    do {                                                                               \
+        cudaError_t _e = (expr);                                                       \
+        if (_e != cudaSuccess)                                                         \
+            return ::lfmm::fail(LFMM_ECUDA, std::string(#expr) + ": " +                 \
+                                                cudaGetErrorString(_e));               \
+    } while (0)
+
+// ---------------------------------------------------------------- constants
+constexpr int kPhiHostRadius = 128;   // host phi table radius; eq. 3.1 beyond
+constexpr int kMaxLeafSide = 32;      // largest supported leaf side (P2P table in shared memory)
+constexpr int kMaxP = 64;             // largest skeleton size
+constexpr int kNumOffsets = 40;       // offsets (ox,oy) in [-3,3]^2 with max(|ox|,|oy|) >= 2
+
+// The 40 interaction offsets, in row-major order over oy then ox, skipping the 3x3 core.
+struct OffsetTable {
+    int ox[kNumOffsets], oy[kNumOffsets];
+    int index[49];  // (oy+3)*7 + (ox+3) -> position in the list, -1 for the 3x3 core
+    OffsetTable();
+};
+const OffsetTable& offsets();
+
+// ---------------------------------------------------------------- Morton codes
+__host__ __device__ inline uint32_t spread_bits16(uint32_t v) {
+    v &= 0x0000ffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ inline uint32_t compact_bits16(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0f0f0f0fu;
+    v = (v | (v >> 4)) & 0x00ff00ffu;
+    v = (v | (v >> 8)) & 0x0000ffffu;
+    return v;
+}
+// Box (bx, by) at a level <= 15 -> Morton index; children of b are 4b + (cx + 2cy).
+__host__ __device__ inline uint32_t morton2(uint32_t bx, uint32_t by) {
+    return spread_bits16(bx) | (spread_bits16(by) << 1);
+}
+__host__ __device__ inline void unmorton2(uint32_t m, uint32_t& bx, uint32_t& by) {
+    bx = compact_bits16(m);
+    by = compact_bits16(m >> 1);
+}
+
+// ---------------------------------------------------------------- phi (host)
+// Library phi on the packed octant |m|_inf <= R by Remark 3.1 quadrature.
+std::vector<double> compute_phi_octant(int R);
+const std::vector<double>& phi_host_table();  // R = kPhiHostRadius, computed once
+double phi_asym_host(double m1, double m2);  // eq. 3.1 without the remainder
+double phi_host(int64_t dx, int64_t dy);     // table or eq. 3.1
+
+// ---------------------------------------------------------------- model-box operators
+struct LevelOps {
+    int side = 0;               // box side at this level
+    int P = 0;                  // skeleton size
+    std::vector<int> skel;      // 2*P coordinates relative to the box corner
+    std::vector<double> S;      // P x (4*P_child), row-major (levels above the leaf)
+};
+
+struct DeviceOps;  // per precision device copies
+
+struct ModelOps {
+    int leaf_side = 0, P_target = 0, ppe = 0;
+    std::vector<double> tofs;     // P0 x leaf_side^2, row-major
+    std::vector<LevelOps> levels; // 0 = leaf, k = k levels above
+    std::mutex mu;                // guards growth and device uploads
+    std::unique_ptr<DeviceOps> dev[2][2];  // [precision][NP==64]
+};
+
+// Returns the cached operators for (leaf_side, P, ppe) with at least n_levels levels.
+ModelOps* get_model_ops(int leaf_side, int P, int ppe, int n_levels, std::string* err);
+
+// phi(skel_p - skel_q - o*side) for offset o, P x P row-major.
+void tifo_matrix(const LevelOps& lv, int o, std::vector<double>& out);
+
+// ---------------------------------------------------------------- device operators
+// Layout per level k (levels above the leaf), element type T, padded length NP:
+//   m2m  [4NP][NP]   m2m[c*NP+q][p] = S_k[p][c*P_{k-1}+q]     (q-hat_parent = sum)
+//   l2l  [4][NP][NP] l2l[c][q][p]   = S_k[q][c*P_{k-1}+p]     (u-hat_child += ...)
+//   tifo [40][NP][NP] tifo[o][q][p] = phi(skel_p - skel_q - o*side)
+// Leaf: tofsT [s^2][NP] tofsT[J][p] = T_ofs[p][J];  P2P table [(2H+1)][W].
+struct DeviceOps {
+    int NP = 0, precision = 0, n_levels = 0, leaf_side = 0;
+    int tab_H = 0, tab_W = 0;             // P2P table half width and row width
+    void* base = nullptr;                 // one allocation
+    size_t bytes = 0;
+    void* tofsT = nullptr;
+    void* p2p_table = nullptr;
+    std::vector<void*> m2m, l2l, tifo;    // per level k
+    std::vector<void*> retired;           // earlier, smaller uploads (kept alive)
+};
+
+const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_levels,
+                                cudaStream_t stream, std::string* err);
+
+// ---------------------------------------------------------------- tracing
+// Counts every kernel launch; when profiling is on, brackets phases with CUDA events.
+void count_launches(int n);
+class PhaseTimer {
+   public:
+    PhaseTimer(int phase, cudaStream_t s);
+    ~PhaseTimer();
+    void add_launches(int n) { launches_ += n; count_launches(n); }
+
+   private:
+    int phase_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    int launches_ = 0;
+};
+// Reads and accumulates the events recorded since the last flush (synchronises).
+void profile_flush();
+bool profiling_enabled();
+
+// ---------------------------------------------------------------- kernels (launchers)
+struct TreeView {
+    int L = 0;                 // leaf level
+    int side = 0;              // leaf side
+    int64_t n_leaves = 0;      // 4^L
+    const int32_t* src_begin = nullptr;  // n_leaves + 1
+    const int32_t* tgt_begin = nullptr;
+    const int32_t* src_loc = nullptr;    // (lx | ly << 16) within the leaf
+    const int32_t* src_perm = nullptr;   // caller index of each sorted source
+    const int32_t* tgt_loc = nullptr;
+    const int32_t* tgt_perm = nullptr;
+};
+
+cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);
+cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
+                        cudaStream_t s);
+cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
+                             int64_t x0, int64_t y0, int shift, int32_t* cnt_src,
+                             int32_t* cnt_tgt, cudaStream_t s);
+cudaError_t launch_coarsen(const int32_t* fs, const int32_t* ft, int64_t n_coarse, int32_t* cs,
+                           int32_t* ct, int* max4, cudaStream_t s);
+cudaError_t launch_scan2(const int32_t* in_a, int32_t* out_a, const int32_t* in_b,
+                         int32_t* out_b, int64_t n, int32_t* partials, cudaStream_t s);
+size_t scan_partials_size(int64_t n);
+cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int shift,
+                           int leaf_side, const int32_t* begin, int32_t* cursor, int32_t* loc,
+                           int32_t* perm, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
+                       T* qhat_leaf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_m2m(const DeviceOps& ops, int k, const T* q_child, T* q_parent,
+                       int64_t n_parent, cudaStream_t s);
+template <typename T>
+cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
+                       const T* u_parent, T* u_level, cudaStream_t s);
+template <typename T>
+cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
+                           const T* uhat_leaf, double* u, double* u_near, double* u_far,
+                           int num_sms, cudaStream_t s);
+
+}  // namespace lfmm

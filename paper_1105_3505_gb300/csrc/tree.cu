@@ -1,0 +1,264 @@
+// Uniform quadtree build on the GPU (Sec. 6): root box, leaf level, points bucketed
+// by leaf in Morton order.
+//
+// The leaf level L is the coarsest level at which no box holds more than N_leaf
+// sources or N_leaf targets.  Counting runs on one fine level (one atomic per point
+// into a per-box counter, Morton-indexed so coarser boxes are contiguous ranges) and
+// one coarsening pass; an exclusive scan turns leaf counts into bucket offsets, and a
+// scatter places every point in its leaf bucket (order inside a bucket is the
+// arrival order of the atomics; nothing downstream depends on it beyond rounding).
+#include "lfmm_internal.h"
+
+namespace lfmm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int warp_min(int v) {
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// out4 = {min x, min y, max x, max y} over both point sets; out4 preset by the host.
+__global__ void bbox_kernel(const int2* __restrict__ a, int64_t na, const int2* __restrict__ b,
+                            int64_t nb, int* __restrict__ out4) {
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
+    const int64_t n = na + nb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = i < na ? a[i] : b[i - na];
+        mnx = min(mnx, p.x);
+        mny = min(mny, p.y);
+        mxx = max(mxx, p.x);
+        mxy = max(mxy, p.y);
+    }
+    mnx = warp_min(mnx);
+    mny = warp_min(mny);
+    mxx = warp_max(mxx);
+    mxy = warp_max(mxy);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out4 + 0, mnx);
+        atomicMin(out4 + 1, mny);
+        atomicMax(out4 + 2, mxx);
+        atomicMax(out4 + 3, mxy);
+    }
+}
+
+__device__ __forceinline__ uint32_t box_of(int2 p, int64_t x0, int64_t y0, int shift) {
+    const uint32_t bx = (uint32_t)(((int64_t)p.x - x0) >> shift);
+    const uint32_t by = (uint32_t)(((int64_t)p.y - y0) >> shift);
+    return morton2(bx, by);
+}
+
+__global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
+                                 const int2* __restrict__ tgt, int64_t nt, int64_t x0,
+                                 int64_t y0, int shift, int32_t* __restrict__ cs,
+                                 int32_t* __restrict__ ct) {
+    const int64_t n = ns + nt;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < ns) atomicAdd(cs + box_of(src[i], x0, y0, shift), 1);
+        else atomicAdd(ct + box_of(tgt[i - ns], x0, y0, shift), 1);
+    }
+}
+
+// coarse[b] = sum of fine[4b..4b+3]; max4 = {max fine src, max fine tgt, max coarse src,
+// max coarse tgt}.
+__global__ void coarsen_kernel(const int4* __restrict__ fs, const int4* __restrict__ ft,
+                               int64_t n_coarse, int32_t* __restrict__ cs,
+                               int32_t* __restrict__ ct, int* __restrict__ max4) {
+    int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_coarse;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int4 s = fs[b], t = ft[b];
+        const int ss = s.x + s.y + s.z + s.w, tt = t.x + t.y + t.z + t.w;
+        cs[b] = ss;
+        ct[b] = tt;
+        m0 = max(m0, max(max(s.x, s.y), max(s.z, s.w)));
+        m1 = max(m1, max(max(t.x, t.y), max(t.z, t.w)));
+        m2 = max(m2, ss);
+        m3 = max(m3, tt);
+    }
+    m0 = warp_max(m0);
+    m1 = warp_max(m1);
+    m2 = warp_max(m2);
+    m3 = warp_max(m3);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(max4 + 0, m0);
+        atomicMax(max4 + 1, m1);
+        atomicMax(max4 + 2, m2);
+        atomicMax(max4 + 3, m3);
+    }
+}
+
+// ---- exclusive scan of two int32 arrays of length n into out[0..n] (out[n] = total)
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+    // sh: kThreads/32 ints
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < kThreads / 32 ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kThreads / 32) sh[lane] = w;
+    }
+    __syncthreads();
+    const int warp_off = wid ? sh[wid - 1] : 0;
+    total = sh[kThreads / 32 - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+__global__ void scan_tile_sums(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                               int64_t n, int32_t* __restrict__ partials) {
+    __shared__ int sh[kThreads / 32];
+    const int32_t* in = blockIdx.y ? b : a;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    int total;
+    block_exclusive_scan(s, sh, total);
+    if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = total;
+}
+
+__global__ void scan_partials(int32_t* __restrict__ partials, int n_tiles) {
+    __shared__ int sh[kThreads / 32];
+    int32_t* p = partials + (int64_t)blockIdx.x * n_tiles;
+    int carry = 0;
+    for (int base = 0; base < n_tiles; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < n_tiles ? p[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, sh, total);
+        if (i < n_tiles) p[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void scan_tiles(const int32_t* __restrict__ a, int32_t* __restrict__ oa,
+                           const int32_t* __restrict__ b, int32_t* __restrict__ ob, int64_t n,
+                           const int32_t* __restrict__ partials) {
+    __shared__ int sh[kThreads / 32];
+    const int32_t* in = blockIdx.y ? b : a;
+    int32_t* out = blockIdx.y ? ob : oa;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_exclusive_scan(s, sh, total) + partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x];
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+        if (i == n - 1) out[n] = run;
+    }
+}
+
+__global__ void scatter_kernel(const int2* __restrict__ xy, int64_t n, int64_t x0, int64_t y0,
+                               int shift, int leaf_side, const int32_t* __restrict__ begin,
+                               int32_t* __restrict__ cursor, int32_t* __restrict__ loc,
+                               int32_t* __restrict__ perm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = xy[i];
+        const int64_t rx = (int64_t)p.x - x0, ry = (int64_t)p.y - y0;
+        const uint32_t leaf = morton2((uint32_t)(rx >> shift), (uint32_t)(ry >> shift));
+        const int slot = begin[leaf] + atomicAdd(cursor + leaf, 1);
+        const int lx = (int)(rx & (leaf_side - 1)), ly = (int)(ry & (leaf_side - 1));
+        loc[slot] = lx | (ly << 16);
+        perm[slot] = (int32_t)i;
+    }
+}
+
+__global__ void set4_kernel(int* p, int a, int b, int c, int d) {
+    p[0] = a;
+    p[1] = b;
+    p[2] = c;
+    p[3] = d;
+}
+
+int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s) {
+    set4_kernel<<<1, 1, 0, s>>>(p, a, b, c, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
+                        cudaStream_t s) {
+    bbox_kernel<<<grid_for(na + nb, kThreads), kThreads, 0, s>>>((const int2*)a, na,
+                                                                (const int2*)b, nb, out4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
+                             int64_t x0, int64_t y0, int shift, int32_t* cs, int32_t* ct,
+                             cudaStream_t s) {
+    histogram_kernel<<<grid_for(ns + nt, kThreads), kThreads, 0, s>>>(
+        (const int2*)src, ns, (const int2*)tgt, nt, x0, y0, shift, cs, ct);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen(const int32_t* fs, const int32_t* ft, int64_t n_coarse, int32_t* cs,
+                           int32_t* ct, int* max4, cudaStream_t s) {
+    coarsen_kernel<<<grid_for(n_coarse, kThreads), kThreads, 0, s>>>(
+        (const int4*)fs, (const int4*)ft, n_coarse, cs, ct, max4);
+    return cudaGetLastError();
+}
+
+size_t scan_partials_size(int64_t n) {
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(2 * (tiles < 1 ? 1 : tiles));
+}
+
+cudaError_t launch_scan2(const int32_t* a, int32_t* oa, const int32_t* b, int32_t* ob, int64_t n,
+                         int32_t* partials, cudaStream_t s) {
+    int tiles = (int)((n + kScanTile - 1) / kScanTile);
+    if (tiles < 1) tiles = 1;
+    dim3 g(tiles, 2);
+    scan_tile_sums<<<g, kThreads, 0, s>>>(a, b, n, partials);
+    scan_partials<<<2, kThreads, 0, s>>>(partials, tiles);
+    scan_tiles<<<g, kThreads, 0, s>>>(a, oa, b, ob, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int shift,
+                           int leaf_side, const int32_t* begin, int32_t* cursor, int32_t* loc,
+                           int32_t* perm, cudaStream_t s) {
+    scatter_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>((const int2*)xy, n, x0, y0, shift,
+                                                             leaf_side, begin, cursor, loc, perm);
+    return cudaGetLastError();
+}
+
+}  // namespace lfmm

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of liblfmm.so (C ABI in include/lfmm.h).
+
+Argument marshalling only: every step of the method runs inside the library.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); pointers are
+passed straight through and the library copies host data itself.  The library
+must have been built (``paper_1105_3505_gb300.build.build()``); loading fails
+loudly otherwise - there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL = range(7)
+LFMM_FP64, LFMM_MIXED = 0, 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lfmm.h")
+
+
+class LfmmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail or 'status ' + str(status)} (status {status})")
+        self.status = status
+
+
+class lfmm_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("max_leaf_side", ctypes.c_int32), ("proxies_per_edge", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class lfmm_plan_info(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("n_tgt", ctypes.c_int64), ("x0", ctypes.c_int64),
+                ("y0", ctypes.c_int64), ("K", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("leaf_side", ctypes.c_int32), ("P", ctypes.c_int32), ("P_pad", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_leaf_src", ctypes.c_int32),
+                ("max_leaf_tgt", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblfmm.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise OSError(f"liblfmm.so not found at {path}; build it with paper_1105_3505_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    sig = {
+        "lfmm_opts_default": (None, [ctypes.POINTER(lfmm_opts)]),
+        "lfmm_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, i64, vp, i64, ctypes.POINTER(lfmm_opts), vp]),
+        "lfmm_eval": (ctypes.c_int, [vp, vp, vp, vp]),
+        "lfmm_eval_parts": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "lfmm_plan_destroy": (ctypes.c_int, [vp]),
+        "lfmm_plan_get_info": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_plan_info)]),
+        "lfmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "lfmm_last_error": (ctypes.c_char_p, []),
+        "lfmm_phi_table": (ctypes.c_int, [i32, dp]),
+        "lfmm_phi": (ctypes.c_int, [vp, i64, dp]),
+        "lfmm_model_skeleton": (ctypes.c_int, [i32, i32, i32, i32, vp, ctypes.POINTER(i32)]),
+        "lfmm_model_tofs": (ctypes.c_int, [i32, i32, i32, dp]),
+        "lfmm_model_s": (ctypes.c_int, [i32, i32, i32, i32, dp]),
+        "lfmm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+        "lfmm_profile_read": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "lfmm_launch_count": (ctypes.c_int64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != LFMM_OK:
+        lib = load()
+        raise LfmmError(status, where, lib.lfmm_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Raw address of a numpy array or torch tensor (must be contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def lfmm_opts_default() -> lfmm_opts:
+    o = lfmm_opts()
+    load().lfmm_opts_default(ctypes.byref(o))
+    return o
+
+
+def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
+              proxies_per_edge: int = 64) -> lfmm_opts:
+    o = lfmm_opts_default()
+    o.precision, o.p, o.leaf_size = precision, p, leaf_size
+    o.max_leaf_side, o.proxies_per_edge = max_leaf_side, proxies_per_edge
+    return o
+
+
+def lfmm_plan_create(src_xy, n_src: int, tgt_xy, n_tgt: int, opts: lfmm_opts | None, stream=None) -> int:
+    h = ctypes.c_void_p()
+    st = load().lfmm_plan_create(ctypes.byref(h), _ptr(src_xy), int(n_src), _ptr(tgt_xy), int(n_tgt),
+                                 ctypes.byref(opts) if opts is not None else None, _stream_handle(stream))
+    _check(st, "lfmm_plan_create")
+    return h.value
+
+
+def lfmm_eval(plan: int, f, u, stream=None) -> None:
+    _check(load().lfmm_eval(plan, _ptr(f), _ptr(u), _stream_handle(stream)), "lfmm_eval")
+
+
+def lfmm_eval_parts(plan: int, f, u_near, u_far, stream=None) -> None:
+    _check(load().lfmm_eval_parts(plan, _ptr(f), _ptr(u_near), _ptr(u_far), _stream_handle(stream)),
+           "lfmm_eval_parts")
+
+
+def lfmm_plan_destroy(plan: int) -> None:
+    _check(load().lfmm_plan_destroy(plan), "lfmm_plan_destroy")
+
+
+def lfmm_plan_get_info(plan: int) -> dict:
+    info = lfmm_plan_info()
+    _check(load().lfmm_plan_get_info(plan, ctypes.byref(info)), "lfmm_plan_get_info")
+    return {name: getattr(info, name) for name, _ in lfmm_plan_info._fields_}
+
+
+def lfmm_status_string(status: int) -> str:
+    return load().lfmm_status_string(int(status)).decode()
+
+
+def lfmm_last_error() -> str:
+    return load().lfmm_last_error().decode()
+
+
+def lfmm_phi_table(R: int) -> np.ndarray:
+    out = np.empty((R + 1) * (R + 2) // 2, dtype=np.float64)
+    _check(load().lfmm_phi_table(int(R), out.ctypes.data), "lfmm_phi_table")
+    return out
+
+
+def lfmm_phi(d) -> np.ndarray:
+    d = np.ascontiguousarray(np.asarray(d, dtype=np.int64).reshape(-1, 2))
+    out = np.empty(d.shape[0], dtype=np.float64)
+    _check(load().lfmm_phi(d.ctypes.data, d.shape[0], out.ctypes.data), "lfmm_phi")
+    return out
+
+
+def lfmm_model_skeleton(leaf_side: int, p: int, proxies_per_edge: int, level_above_leaf: int) -> np.ndarray:
+    xy = np.zeros(2 * 64, dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(load().lfmm_model_skeleton(leaf_side, p, proxies_per_edge, level_above_leaf, xy.ctypes.data,
+                                      ctypes.byref(n)), "lfmm_model_skeleton")
+    return xy[: 2 * n.value].reshape(-1, 2).copy()
+
+
+def lfmm_model_tofs(leaf_side: int, p: int, proxies_per_edge: int) -> np.ndarray:
+    P0 = lfmm_model_skeleton(leaf_side, p, proxies_per_edge, 0).shape[0]
+    out = np.empty((P0, leaf_side * leaf_side), dtype=np.float64)
+    _check(load().lfmm_model_tofs(leaf_side, p, proxies_per_edge, out.ctypes.data), "lfmm_model_tofs")
+    return out
+
+
+def lfmm_model_s(leaf_side: int, p: int, proxies_per_edge: int, level_above_leaf: int) -> np.ndarray:
+    Pp = lfmm_model_skeleton(leaf_side, p, proxies_per_edge, level_above_leaf).shape[0]
+    Pc = lfmm_model_skeleton(leaf_side, p, proxies_per_edge, level_above_leaf - 1).shape[0]
+    out = np.empty((Pp, 4 * Pc), dtype=np.float64)
+    _check(load().lfmm_model_s(leaf_side, p, proxies_per_edge, level_above_leaf, out.ctypes.data), "lfmm_model_s")
+    return out
+
+
+PHASES = ("tree", "operators", "p2m", "m2m", "m2l", "p2p", "copy")
+
+
+def lfmm_profile_enable(enable: bool) -> None:
+    _check(load().lfmm_profile_enable(1 if enable else 0), "lfmm_profile_enable")
+
+
+def lfmm_profile_read(reset: bool = False) -> dict:
+    """{phase: (milliseconds, kernel launches)} accumulated by the library's phase timers."""
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    n = np.zeros(len(PHASES), dtype=np.int64)
+    _check(load().lfmm_profile_read(ms.ctypes.data, n.ctypes.data, 1 if reset else 0), "lfmm_profile_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PHASES)}
+
+
+def lfmm_launch_count() -> int:
+    return int(load().lfmm_launch_count())
+
+
+class Plan:
+    """Convenience owner of an lfmm plan: ``Plan(src, tgt, ...).eval(f) -> u``.
+
+    src, tgt: (n, 2) int32 numpy arrays or torch tensors (host or CUDA).
+    eval(f): f float64 of length n_src (host or CUDA); returns u in the same kind of
+    memory as f (numpy for numpy input, torch CUDA tensor for CUDA input)."""
+
+    def __init__(self, src, tgt, precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64,
+                 max_leaf_side: int = 32, proxies_per_edge: int = 64, stream=None):
+        self.n_src, self.n_tgt = int(src.shape[0]), int(tgt.shape[0])
+        self.stream = stream
+        self.handle = lfmm_plan_create(src, self.n_src, tgt, self.n_tgt,
+                                       make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge), stream)
+
+    def info(self) -> dict:
+        return lfmm_plan_get_info(self.handle)
+
+    def eval(self, f, out=None):
+        if out is None:
+            if isinstance(f, np.ndarray):
+                out = np.empty(self.n_tgt, dtype=np.float64)
+            else:
+                import torch
+                out = torch.empty(self.n_tgt, dtype=torch.float64, device=f.device)
+        lfmm_eval(self.handle, f, out, self.stream)
+        return out
+
+    def eval_parts(self, f):
+        if isinstance(f, np.ndarray):
+            un, uf = np.empty(self.n_tgt), np.empty(self.n_tgt)
+        else:
+            import torch
+            un = torch.empty(self.n_tgt, dtype=torch.float64, device=f.device)
+            uf = torch.empty_like(un)
+        lfmm_eval_parts(self.handle, f, un, uf, self.stream)
+        return un, uf
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lfmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,208 @@
+"""Parity of the CUDA lattice FMM (through the C ABI) with the CPU oracle.
+
+Metric: rel_err = max_i |u_i - u_i^oracle| / max_i |u_i^oracle| (max norm; pointwise
+relative error is undefined where u ~ 0).  Bars: 1e-10 for the all-binary64 path at
+p = 16 (the paper runs at 1e-10, Sec. 9), 1e-6 for the mixed path at p = 8.
+Integer outputs of the tree step (root box, leaf level) must equal the oracle's
+exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1105_3505_gb300 import build, workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lfmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_1105_3505_gb300 import lfmm as m
+    m.load()
+    torch.cuda.init()
+    return m
+
+
+def rel_err(u, ref):
+    return float(np.abs(np.asarray(u) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def run(lfmm, src, tgt, f, precision, p, **kw):
+    with lfmm.Plan(src, tgt, precision=precision, p=p, **kw) as pl:
+        u = pl.eval(f)
+        info = pl.info()
+    return u, info
+
+
+def test_uniform_4k_fp64_full_oracle(lfmm):
+    prob = workloads.uniform_4k()
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    u, info = run(lfmm, prob.src, prob.tgt, prob.f, lfmm.LFMM_FP64, 16)
+    tree = oracle.uniform_tree(prob.src, prob.tgt, 64, 32)
+    assert (info["x0"], info["y0"], info["K"], info["L"], info["leaf_side"]) == \
+        (tree["x0"], tree["y0"], tree["K"], tree["L"], tree["side"])
+    assert rel_err(u, ref) <= FP64_TOL
+
+
+def test_uniform_4k_mixed_full_oracle(lfmm):
+    prob = workloads.uniform_4k()
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    u, _ = run(lfmm, prob.src, prob.tgt, prob.f, lfmm.LFMM_MIXED, 8)
+    assert rel_err(u, ref) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,p,tol_near,tol_far", [("fp64", 16, 1e-13, 1e-10), ("mixed", 8, 1e-6, 1e-6)])
+def test_near_and_far_parts(lfmm, precision, p, tol_near, tol_far):
+    """Near field = same/adjacent leaves (eq. 2.2) under the oracle's own tree; far = rest."""
+    prob = workloads.uniform_box(3000, 2500, 300, seed=21)
+    prec = lfmm.LFMM_FP64 if precision == "fp64" else lfmm.LFMM_MIXED
+    tree = oracle.uniform_tree(prob.src, prob.tgt, 64, 32)
+    with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p) as pl:
+        un, uf = pl.eval_parts(prob.f)
+        u = pl.eval(prob.f)
+        info = pl.info()
+    assert (info["L"], info["leaf_side"]) == (tree["L"], tree["side"])
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    near = oracle.near_sum(prob.src, prob.f, prob.tgt, tree["x0"], tree["y0"], tree["side"])
+    assert np.abs(un - near).max() <= tol_near * np.abs(near).max()
+    assert np.abs(uf - (ref - near)).max() <= tol_far * np.abs(ref).max()
+    assert np.abs(u - (un + uf)).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _case(name):
+    rng = np.random.default_rng(abs(hash(name)) % (2 ** 32))
+    if name == "one_point":
+        s = np.array([[3, 4]], dtype=np.int32)
+        return s, s.copy(), np.array([1.5])
+    if name == "one_source_many_targets":
+        s = np.array([[0, 0]], dtype=np.int32)
+        t = workloads.distinct_in_box(rng, 50, 21, -10, -10)
+        return s, t, np.array([2.0])
+    if name == "line_of_three":
+        s = np.array([[0, 0], [1, 0], [2, 0]], dtype=np.int32)
+        return s, s.copy(), np.array([1.0, -2.0, 1.0])
+    if name == "tiny_random":
+        s = workloads.distinct_in_box(rng, 200, 40)
+        t = workloads.distinct_in_box(rng, 77, 40)
+        return s, t, rng.standard_normal(200)
+    if name == "negative_coords":
+        s = workloads.distinct_in_box(rng, 5000, 3000, -1000, -1700)
+        t = workloads.distinct_in_box(rng, 3000, 3000, -1000, -1700)
+        return s, t, workloads.zero_sum(rng.standard_normal(5000))
+    if name == "large_offset":
+        off = (1 << 30) - 5000
+        s = workloads.distinct_in_box(rng, 2000, 1024, off, -off)
+        t = workloads.distinct_in_box(rng, 1500, 1024, off, -off)
+        return s, t, workloads.zero_sum(rng.standard_normal(2000))
+    if name == "coincident_sources":
+        s = np.full((100, 2), 5, dtype=np.int32)
+        t = workloads.distinct_in_box(rng, 60, 64)
+        return s, t, rng.standard_normal(100)
+    if name == "disjoint_far_targets":
+        s = workloads.distinct_in_box(rng, 3000, 256)
+        t = workloads.distinct_in_box(rng, 500, 64, 5000, 7000)
+        return s, t, workloads.zero_sum(rng.standard_normal(3000))
+    if name == "dense_block":
+        s = np.array([(x, y) for y in range(64) for x in range(64)], dtype=np.int32)
+        return s, s.copy(), workloads.zero_sum(rng.standard_normal(4096))
+    if name == "ragged_counts":
+        # clusters of very different density in one uniform tree
+        a = workloads.distinct_in_box(rng, 1500, 50, 0, 0)
+        b = workloads.distinct_in_box(rng, 700, 600, 0, 0)
+        s = np.unique(np.concatenate([a, b]), axis=0).astype(np.int32)
+        t = workloads.distinct_in_box(rng, 1000, 600)
+        return s, t, workloads.zero_sum(rng.standard_normal(s.shape[0]))
+    raise KeyError(name)
+
+
+CASES = ["one_point", "one_source_many_targets", "line_of_three", "tiny_random", "negative_coords",
+         "large_offset", "coincident_sources", "disjoint_far_targets", "dense_block", "ragged_counts"]
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_cases(lfmm, name, precision):
+    s, t, f = _case(name)
+    ref = oracle.lattice_sum(s, f, t)
+    if precision == "fp64":
+        u, info = run(lfmm, s, t, f, lfmm.LFMM_FP64, 16)
+        tol = FP64_TOL
+    else:
+        u, info = run(lfmm, s, t, f, lfmm.LFMM_MIXED, 8)
+        tol = MIXED_TOL
+    tree = oracle.uniform_tree(s, t, 64, 32)
+    assert (info["K"], info["L"], info["leaf_side"]) == (tree["K"], tree["L"], tree["side"])
+    if np.abs(ref).max() == 0.0:
+        assert np.abs(u).max() == 0.0
+    else:
+        assert rel_err(u, ref) <= tol, (name, rel_err(u, ref))
+
+
+@pytest.mark.parametrize("leaf_size,max_side", [(4, 32), (16, 8), (200, 32), (64, 1)])
+def test_tree_shapes(lfmm, leaf_size, max_side):
+    prob = workloads.uniform_box(2500, 2000, 200, seed=leaf_size + max_side)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    u, info = run(lfmm, prob.src, prob.tgt, prob.f, lfmm.LFMM_FP64, 16, leaf_size=leaf_size,
+                  max_leaf_side=max_side)
+    tree = oracle.uniform_tree(prob.src, prob.tgt, leaf_size, max_side)
+    assert (info["L"], info["leaf_side"]) == (tree["L"], tree["side"])
+    assert rel_err(u, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("p,tol", [(2, 2e-2), (5, 1e-4), (8, 1e-7), (12, 1e-10)])
+def test_accuracy_improves_with_p(lfmm, p, tol):
+    prob = workloads.uniform_box(4000, 4000, 512, seed=5)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    u, _ = run(lfmm, prob.src, prob.tgt, prob.f, lfmm.LFMM_FP64, p)
+    assert rel_err(u, ref) <= tol
+
+
+def test_device_and_host_pointers_agree(lfmm):
+    prob = workloads.uniform_box(20000, 10000, 1000, seed=8)
+    dev = torch.device("cuda:0")
+    s_d = torch.from_numpy(prob.src).to(dev)
+    t_d = torch.from_numpy(prob.tgt).to(dev)
+    f_d = torch.from_numpy(prob.f).to(dev)
+    for prec, p in [(lfmm.LFMM_FP64, 16), (lfmm.LFMM_MIXED, 8)]:
+        with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p) as pl:
+            u_h = pl.eval(prob.f)
+            u_h2 = pl.eval(prob.f)
+        with lfmm.Plan(s_d, t_d, precision=prec, p=p) as pl:
+            u_d = pl.eval(f_d)
+            torch.cuda.synchronize()
+        assert np.array_equal(u_h, u_h2)  # same plan, same order: bitwise reproducible
+        scale = np.abs(u_h).max()
+        assert np.abs(u_d.cpu().numpy() - u_h).max() <= (1e-12 if prec == lfmm.LFMM_FP64 else 1e-6) * scale
+
+
+@pytest.fixture(scope="module")
+def uniform_1m():
+    return workloads.uniform_1m()
+
+
+@pytest.mark.parametrize("precision,p,tol", [("mixed", 8, MIXED_TOL), ("fp64", 16, FP64_TOL)])
+def test_uniform_1m_sampled(lfmm, uniform_1m, precision, p, tol):
+    """Full-size uniform workload (2^20 sources, 2^20 targets), in the launch configuration
+    the benchmark times; 256 seeded targets checked against the oracle one by one."""
+    prob = uniform_1m
+    prec = lfmm.LFMM_FP64 if precision == "fp64" else lfmm.LFMM_MIXED
+    dev = torch.device("cuda:0")
+    s_d = torch.from_numpy(prob.src).to(dev)
+    t_d = torch.from_numpy(prob.tgt).to(dev)
+    f_d = torch.from_numpy(prob.f).to(dev)
+    with lfmm.Plan(s_d, t_d, precision=prec, p=p) as pl:
+        u = pl.eval(f_d).cpu().numpy()
+        info = pl.info()
+    assert np.isfinite(u).all()
+    assert (info["K"], info["L"], info["leaf_side"]) == (12, 8, 16)
+    idx = np.random.default_rng(123).choice(prob.tgt.shape[0], 256, replace=False)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+    assert rel_err(u[idx], ref) <= tol
