@@ -44,6 +44,8 @@ struct lfmm_plan {
     void* f_sorted = nullptr;
     void* qhat = nullptr;
     void* uhat = nullptr;
+    void* Qbox = nullptr;          // per-box total charge (8 B per box)
+    void* Cbox = nullptr;          // per-box incoming constant (8 B per box)
     std::vector<int64_t> lvl_off;  // offset (boxes) of level l inside qhat / uhat
     double* f_stage = nullptr;     // device copy of a host f
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
@@ -246,7 +248,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     p->tgt_begin = p->src_begin + (n_leaves + 1);
     Temp part;
     if ((st = talloc(part, scan_partials_size(n_leaves) * sizeof(int32_t), s))) return st;
-    LFMM_CUDA_TRY(launch_scan2(cs, p->src_begin, ct, p->tgt_begin, n_leaves, (int32_t*)part.ptr, s));
+    LFMM_CUDA_TRY(launch_scan2(cs, p->src_begin, ct, p->tgt_begin, p->L, (int32_t*)part.ptr, s));
     tree_timer->add_launches(3);
     if ((st = palloc(p, &buf, (size_t)2 * (p->ns + p->nt) * sizeof(int32_t), s))) return st;
     p->src_loc = (int32_t*)buf;
@@ -256,9 +258,9 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     Temp cur;
     if ((st = talloc(cur, (size_t)2 * n_leaves * sizeof(int32_t), s))) return st;
     LFMM_CUDA_TRY(cudaMemsetAsync(cur.ptr, 0, (size_t)2 * n_leaves * sizeof(int32_t), s));
-    LFMM_CUDA_TRY(launch_scatter(src, p->ns, p->x0, p->y0, p->K - p->L, p->side, p->src_begin,
+    LFMM_CUDA_TRY(launch_scatter(src, p->ns, p->x0, p->y0, p->K - p->L, p->side, p->L, p->src_begin,
                                  (int32_t*)cur.ptr, p->src_loc, p->src_perm, s));
-    LFMM_CUDA_TRY(launch_scatter(tgt, p->nt, p->x0, p->y0, p->K - p->L, p->side, p->tgt_begin,
+    LFMM_CUDA_TRY(launch_scatter(tgt, p->nt, p->x0, p->y0, p->K - p->L, p->side, p->L, p->tgt_begin,
                                  (int32_t*)cur.ptr + n_leaves, p->tgt_loc, p->tgt_perm, s));
     tree_timer->add_launches(2);
     tree_timer.reset();
@@ -285,6 +287,8 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     }
     if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
+    if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
+    if ((st = palloc(p, &p->Cbox, (size_t)boxes * 8, s))) return st;
     LFMM_CUDA_TRY(cudaStreamSynchronize(s));
     return LFMM_OK;
 }
@@ -305,32 +309,35 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     const int NP = p->NP;
     T* q = (T*)p->qhat;
     T* uh = (T*)p->uhat;
-    auto Q = [&](int l) { return q + (size_t)p->lvl_off[l] * NP; };
-    auto U = [&](int l) { return uh + (size_t)p->lvl_off[l] * NP; };
+    auto Qx = [&](int l) { return q + (size_t)p->lvl_off[l] * NP; };
+    auto Ux = [&](int l) { return uh + (size_t)p->lvl_off[l] * NP; };
+    auto Qm = [&](int l) { return (void*)((char*)p->Qbox + (size_t)p->lvl_off[l] * 8); };
+    auto Cm = [&](int l) { return (void*)((char*)p->Cbox + (size_t)p->lvl_off[l] * 8); };
     const int L = p->L;
     {
         PhaseTimer pt(LFMM_PHASE_P2M, s);
-        LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, Q(L), s));
+        LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, Qx(L), Qm(L), s));
         pt.add_launches(1);
     }
     {
         PhaseTimer pt(LFMM_PHASE_M2M, s);
         for (int l = L - 1; l >= 2; --l) {
-            LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, Q(l + 1), Q(l), (int64_t)1 << (2 * l), s));
+            LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, l, Qx(l + 1), Qm(l + 1), Qx(l), Qm(l), s));
             pt.add_launches(1);
         }
     }
     {
         PhaseTimer pt(LFMM_PHASE_M2L, s);
         for (int l = 2; l <= L; ++l) {
-            LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Q(l), l >= 3 ? U(l - 1) : nullptr, U(l), s));
+            LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
+                                        l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), s));
             pt.add_launches(1);
         }
     }
     {
         PhaseTimer pt(LFMM_PHASE_P2P, s);
-        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, L >= 2 ? U(L) : nullptr, u, un,
-                                        uf, p->num_sms, s));
+        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, L >= 2 ? Ux(L) : nullptr,
+                                        L >= 2 ? Cm(L) : nullptr, u, un, uf, p->num_sms, s));
         pt.add_launches(1);
     }
     return LFMM_OK;

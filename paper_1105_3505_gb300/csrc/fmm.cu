@@ -9,10 +9,17 @@
 //
 // Element type T is float (mixed path) or double (plain path); NP is the padded
 // expansion length (32 or 64).  Expansions of level l are stored Morton-ordered,
-// [4^l][NP].  phi near the origin comes from a shared-memory table, so every
-// near-field pair costs one table load and one FMA (Sec. 2: "a table look-up").
-#include <cstdio>
-
+// [4^l][NP]; points are bucketed by leaf in row-major leaf order, so the sources of
+// a leaf's 3x3 neighbourhood are three contiguous ranges.
+//
+// Monopole channel.  phi has a large constant part (about -1.4 to -1.9 at the box
+// distances here) and the charges sum to zero, so the far field is a cancelling sum
+// of large terms.  The M2L operators are stored deflated, T_ifo - c_o 1 1^T with
+// c_o = phi(o*side); every box also carries its total charge Q (exact sum of f) and
+// the incoming constant C = C_parent + sum_list c_o Q_sigma in compensated arithmetic
+// (double-float pairs on the mixed path).  Interpolation reproduces constants
+// (T_ofs^T 1 = 1 and T_ifi 1 = 1 to the expansion accuracy), so C bypasses L2L/L2P
+// and joins the binary64 final sum.
 #include "lfmm_internal.h"
 
 namespace lfmm {
@@ -21,27 +28,71 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// ------------------------------------------------------------------------- compensated scalars
+// Error-free transformations (Knuth two-sum, FMA two-product) on float pairs.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bp = s - a;
+    const float ap = s - bp;
+    return {s, (a - ap) + (b - bp)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    DF t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+template <typename T>
+struct Mono;
+template <>
+struct Mono<float> {
+    using V = DF;
+    __device__ static V zero() { return {0.f, 0.f}; }
+    __device__ static V from_double(double x) {
+        const float h = (float)x;
+        return {h, (float)(x - (double)h)};
+    }
+    __device__ static V make(float hi, float lo) { return {hi, lo}; }
+    __device__ static V add(V a, V b) { return df_add(a, b); }
+    __device__ static V mul(V a, V b) { return df_mul(a, b); }
+    __device__ static double to_double(V a) { return (double)a.hi + (double)a.lo; }
+};
+template <>
+struct Mono<double> {
+    using V = double;
+    __device__ static V zero() { return 0.0; }
+    __device__ static V from_double(double x) { return x; }
+    __device__ static V make(double hi, double lo) { return hi + lo; }
+    __device__ static V add(V a, V b) { return a + b; }
+    __device__ static V mul(V a, V b) { return a * b; }
+    __device__ static double to_double(V a) { return a; }
+};
+
 template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) {
     return __shfl_sync(kFull, v, src);
 }
-
-// v[i] summed over the warp lands in lane i (31 shuffles for 32 values).
-template <typename T>
-__device__ __forceinline__ T reduce_scatter32(T (&v)[32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const bool upper = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < off; ++i) {
-            const T send = upper ? v[i] : v[i + off];
-            const T keep = upper ? v[i + off] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, off);
-        }
-    }
-    return v[0];
+__device__ __forceinline__ DF shfl_xor_v(DF v, int m) {
+    return {__shfl_xor_sync(kFull, v.hi, m), __shfl_xor_sync(kFull, v.lo, m)};
 }
+__device__ __forceinline__ double shfl_xor_v(double v, int m) { return __shfl_xor_sync(kFull, v, m); }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -57,24 +108,41 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Position of offset (ox, oy) in the list of 40: row-major over [-3,3]^2 minus the core.
+__device__ __forceinline__ int offset_index(int ox, int oy) {
+    const int raw = (oy + 3) * 7 + (ox + 3);
+    int inner_before;
+    if (oy < -1) inner_before = 0;
+    else if (oy > 1) inner_before = 9;
+    else inner_before = 3 * (oy + 1) + (ox > 1 ? 3 : 0);
+    return raw - inner_before;
+}
+
 // ------------------------------------------------------------------------- P2M
+// One warp per leaf (row-major leaf index).  Writes the sorted charges in T, the
+// outgoing expansion and the leaf's total charge (Morton index).
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) p2m_kernel(int64_t n_leaves, const int32_t* __restrict__ begin,
+__global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restrict__ begin,
                                                   const int32_t* __restrict__ loc,
                                                   const int32_t* __restrict__ perm,
                                                   const double* __restrict__ f,
                                                   T* __restrict__ f_sorted,
                                                   const T* __restrict__ tofsT, int side,
-                                                  T* __restrict__ qhat) {
+                                                  T* __restrict__ qhat,
+                                                  typename Mono<T>::V* __restrict__ Q) {
+    using M = Mono<T>;
     constexpr int PL = NP / 32;
     const int lane = threadIdx.x & 31;
+    const int64_t n_leaves = (int64_t)1 << (2 * L);
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves;
          leaf += nw) {
         const int b = begin[leaf], e = begin[leaf + 1];
+        const uint32_t mort = morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L));
         T acc[PL];
 #pragma unroll
         for (int i = 0; i < PL; ++i) acc[i] = T(0);
+        typename M::V qsum = M::zero();
         for (int j0 = b; j0 < e; j0 += 32) {
             const int j = j0 + lane;
             T fj = T(0);
@@ -82,8 +150,10 @@ __global__ void __launch_bounds__(256) p2m_kernel(int64_t n_leaves, const int32_
             if (j < e) {
                 const int l = loc[j];
                 J = (l & 0xffff) + side * (l >> 16);
-                fj = (T)f[perm[j]];
+                const double fd = f[perm[j]];
+                fj = (T)fd;
                 f_sorted[j] = fj;
+                qsum = M::add(qsum, M::from_double(fd));
             }
             const int cnt = min(32, e - j0);
             for (int k = 0; k < cnt; ++k) {
@@ -94,129 +164,118 @@ __global__ void __launch_bounds__(256) p2m_kernel(int64_t n_leaves, const int32_
             }
         }
 #pragma unroll
-        for (int i = 0; i < PL; ++i) qhat[(size_t)leaf * NP + lane + 32 * i] = acc[i];
+        for (int i = 0; i < PL; ++i) qhat[(size_t)mort * NP + lane + 32 * i] = acc[i];
+        // warp sum of the compensated partial charges
+#pragma unroll
+        for (int off = 16; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
+        if (lane == 0) Q[mort] = qsum;
     }
 }
 
-// ------------------------------------------------------------------------- M2M
+// ------------------------------------------------------------------------- M2M / M2L
+// One block: BB target rows, all NP outputs, a K loop of NP-wide steps.  Per step the
+// gathered source rows (A, [BB][AS]) and the operator block (B, [NP][NP], k-major) are
+// staged with cp.async, double buffered; each lane owns MB rows x MP outputs.
+//   M2M: rows = parents b of level l (row-major over the parent grid); steps c = 0..3
+//        take child 4b+c with operator block c of S.  Also Q_b = sum of children's Q.
+//   M2L: rows = boxes of parity class (px, py) = blockIdx.y; steps = the class's 27
+//        interaction offsets (Def. 6.1) with deflated T_ifo, then (level >= 3) the
+//        parent's incoming expansion with T_ifi block (px + 2py).  Also the incoming
+//        constant C (see the monopole channel above).
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) m2m_kernel(int64_t n_parent, const T* __restrict__ qc,
-                                                  const T* __restrict__ m2m, T* __restrict__ qp) {
-    constexpr int CL = 4 * NP / 32, PL = NP / 32;
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t par = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; par < n_parent;
-         par += nw) {
-        T x[CL];
-#pragma unroll
-        for (int c = 0; c < CL; ++c) x[c] = qc[(size_t)par * 4 * NP + lane + 32 * c];
-        T acc[PL];
-#pragma unroll
-        for (int i = 0; i < PL; ++i) acc[i] = T(0);
-#pragma unroll
-        for (int c = 0; c < CL; ++c) {
-#pragma unroll 8
-            for (int l = 0; l < 32; ++l) {
-                const T v = shfl(x[c], l);
-                const T* row = m2m + (size_t)(32 * c + l) * NP;
-#pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(__ldg(row + lane + 32 * i), v, acc[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PL; ++i) qp[(size_t)par * NP + lane + 32 * i] = acc[i];
-    }
-}
-
-// ------------------------------------------------------------------------- M2L (+L2L)
-// One block: BB target boxes of one parity class c = (px, py) (boxes (2i+px, 2j+py)),
-// all NP outputs.  K loop: the class's 27 interaction offsets (Def. 6.1), then the
-// parent's incoming expansion through T_ifi (level >= 3).  Per step the gathered
-// source rows (A, [BB][AS]) and the operator (B, [NP][NP], k-major) are staged in
-// shared memory with cp.async, double buffered.  Lane tile: MB boxes x MP outputs.
-template <typename T, int NP>
-struct M2LCfg {
+struct TrCfg {
     static constexpr int MB = 4, MP = 8;
-    static constexpr int NPG = NP / MP;           // lanes along outputs
-    static constexpr int NBG = 32 / NPG;          // lanes along boxes
-    static constexpr int WB = MB * NBG;           // boxes per warp
+    static constexpr int NPG = NP / MP;
+    static constexpr int NBG = 32 / NPG;
+    static constexpr int WB = MB * NBG;
     static constexpr int WARPS = 4;
-    static constexpr int BB = WB * WARPS;         // boxes per block
-    static constexpr int AS = NP + 16 / (int)sizeof(T);  // A row stride (elements)
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int BB = WB * WARPS;
+    static constexpr int AS = NP + 16 / (int)sizeof(T);
     static constexpr int A_ELEMS = BB * AS;
     static constexpr int B_ELEMS = NP * NP;
     static constexpr int STAGE = A_ELEMS + B_ELEMS;
     static constexpr size_t SMEM = 2 * (size_t)STAGE * sizeof(T);
 };
 
-template <typename T, int NP>
-__global__ void __launch_bounds__(128) m2l_kernel(int level, const T* __restrict__ q,
-                                                  const T* __restrict__ u_par,
-                                                  const T* __restrict__ tifo,
-                                                  const T* __restrict__ l2l,
-                                                  T* __restrict__ u) {
-    using C = M2LCfg<T, NP>;
+constexpr int kModeM2M = 0, kModeM2L = 1;
+
+template <typename T, int NP, int MODE>
+__global__ void __launch_bounds__(128) translate_kernel(int level, const T* __restrict__ q,
+                                                        const T* __restrict__ u_par,
+                                                        const T* __restrict__ ops,
+                                                        const T* __restrict__ l2l,
+                                                        const T* __restrict__ mono,
+                                                        const typename Mono<T>::V* __restrict__ Qin,
+                                                        const typename Mono<T>::V* __restrict__ Cpar,
+                                                        T* __restrict__ out,
+                                                        typename Mono<T>::V* __restrict__ Qout,
+                                                        typename Mono<T>::V* __restrict__ Cout) {
+    using C = TrCfg<T, NP>;
+    using M = Mono<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_off[27][3];
     T* smem = reinterpret_cast<T*>(smem_raw);
-    const int cls = blockIdx.y;
+    const int cls = MODE == kModeM2L ? (int)blockIdx.y : 0;
     const int px = cls & 1, py = cls >> 1;
-    const int np_side = 1 << (level - 1);          // parents per axis
-    const int64_t n_par = (int64_t)np_side * np_side;
+    // M2M: grid of parents at `level` (2^level per axis); M2L: parents at level-1
+    const int lg = MODE == kModeM2L ? level - 1 : level;
+    const int np_side = 1 << lg;
+    const int64_t n_rows = (int64_t)1 << (2 * lg);
     const int64_t tile0 = (int64_t)blockIdx.x * C::BB;
     const int side = 1 << level;
-    const bool has_l2l = (u_par != nullptr);
+    const bool has_l2l = MODE == kModeM2L && u_par != nullptr;
+    const int n_steps = MODE == kModeM2M ? 4 : 27 + (has_l2l ? 1 : 0);
 
-    // the class's offsets: ox in [-2-px, 3-px], oy in [-2-py, 3-py], not in [-1,1]^2
-    const int n_steps = 27 + (has_l2l ? 1 : 0);
+    if (MODE == kModeM2L && threadIdx.x == 0) {
+        int n = 0;
+        for (int d = 0; d < 36; ++d) {
+            const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            s_off[n][0] = dx;
+            s_off[n][1] = dy;
+            s_off[n][2] = offset_index(dx, dy);
+            ++n;
+        }
+    }
+    __syncthreads();
+
+    auto row_ij = [&](int64_t r, int& i, int& j) {
+        i = (int)(r & (np_side - 1));
+        j = (int)(r >> lg);
+    };
 
     auto stage = [&](int step, int buf) {
         T* As = smem + (size_t)buf * C::STAGE;
         T* Bs = As + C::A_ELEMS;
         const T* op;
         int ox = 0, oy = 0;
-        bool l2l_step = step >= 27;
-        if (!l2l_step) {
-            int cnt = 0, o_idx = 0;
-            // enumerate the 6x6 block minus the 3x3 core, row-major
-            for (int d = 0; d < 36; ++d) {
-                const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
-                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-                if (cnt == step) {
-                    ox = dx;
-                    oy = dy;
-                    break;
-                }
-                ++cnt;
-            }
-            // index among the 40 offsets: row-major over [-3,3]^2 minus the core
-            {
-                int idx = 0;
-                for (int yy = -3; yy <= 3; ++yy)
-                    for (int xx = -3; xx <= 3; ++xx) {
-                        if (xx >= -1 && xx <= 1 && yy >= -1 && yy <= 1) continue;
-                        if (xx == ox && yy == oy) o_idx = idx;
-                        ++idx;
-                    }
-            }
-            op = tifo + (size_t)o_idx * NP * NP;
+        if (MODE == kModeM2M) {
+            op = ops + (size_t)step * NP * NP;
+        } else if (step < 27) {
+            ox = s_off[step][0];
+            oy = s_off[step][1];
+            op = ops + (size_t)s_off[step][2] * NP * NP;
         } else {
             op = l2l + (size_t)cls * NP * NP;
         }
-        // B: NP*NP elements, contiguous
         constexpr int B_CHUNKS = C::B_ELEMS * (int)sizeof(T) / 16;
-        for (int c = threadIdx.x; c < B_CHUNKS; c += blockDim.x)
+        for (int c = threadIdx.x; c < B_CHUNKS; c += C::THREADS)
             cp_async16(reinterpret_cast<char*>(Bs) + 16 * c,
                        reinterpret_cast<const char*>(op) + 16 * c, 16);
-        // A: BB rows of NP elements, gathered
-        constexpr int ROW_CHUNKS = NP * (int)sizeof(T) / 16;
-        for (int c = threadIdx.x; c < C::BB * ROW_CHUNKS; c += blockDim.x) {
-            const int r = c / ROW_CHUNKS, ch = c % ROW_CHUNKS;
-            const int64_t pi = tile0 + r;
+        constexpr int RC = NP * (int)sizeof(T) / 16;
+        for (int c = threadIdx.x; c < C::BB * RC; c += C::THREADS) {
+            const int r = c / RC, ch = c % RC;
+            const int64_t pr = tile0 + r;
             const T* src = q;
             int bytes = 0;
-            if (pi < n_par) {
-                const int i = (int)(pi % np_side), j = (int)(pi / np_side);
-                if (!l2l_step) {
+            if (pr < n_rows) {
+                int i, j;
+                row_ij(pr, i, j);
+                if (MODE == kModeM2M) {
+                    src = q + ((size_t)morton2(i, j) * 4 + step) * NP;
+                    bytes = 16;
+                } else if (step < 27) {
                     const int sx = 2 * i + px + ox, sy = 2 * j + py + oy;
                     if (sx >= 0 && sx < side && sy >= 0 && sy < side) {
                         src = q + (size_t)morton2(sx, sy) * NP;
@@ -232,6 +291,35 @@ __global__ void __launch_bounds__(128) m2l_kernel(int level, const T* __restrict
         }
     };
 
+    stage(0, 0);
+    cp_async_commit();
+
+    // scalar channel, one thread per row, overlapped with the first copies
+    if (threadIdx.x < C::BB) {
+        const int64_t pr = tile0 + threadIdx.x;
+        if (pr < n_rows) {
+            int i, j;
+            row_ij(pr, i, j);
+            if (MODE == kModeM2M) {
+                const uint32_t b = morton2(i, j);
+                typename M::V s = Qin[4 * b];
+#pragma unroll
+                for (int c = 1; c < 4; ++c) s = M::add(s, Qin[4 * b + c]);
+                Qout[b] = s;
+            } else {
+                typename M::V s = has_l2l ? Cpar[morton2(i, j)] : M::zero();
+                for (int st = 0; st < 27; ++st) {
+                    const int sx = 2 * i + px + s_off[st][0], sy = 2 * j + py + s_off[st][1];
+                    if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
+                    const int o = s_off[st][2];
+                    const typename M::V co = M::make(mono[o], mono[kNumOffsets + o]);
+                    s = M::add(s, M::mul(co, Qin[morton2(sx, sy)]));
+                }
+                Cout[morton2(2 * i + px, 2 * j + py)] = s;
+            }
+        }
+    }
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bg = lane % C::NBG, pg = lane / C::NBG;
     const int wbox = warp * C::WB;
@@ -241,8 +329,6 @@ __global__ void __launch_bounds__(128) m2l_kernel(int level, const T* __restrict
 #pragma unroll
         for (int j = 0; j < C::MP; ++j) acc[i][j] = T(0);
 
-    stage(0, 0);
-    cp_async_commit();
     for (int step = 0; step < n_steps; ++step) {
         if (step + 1 < n_steps) {
             stage(step + 1, (step + 1) & 1);
@@ -270,153 +356,162 @@ __global__ void __launch_bounds__(128) m2l_kernel(int level, const T* __restrict
     }
 #pragma unroll
     for (int i = 0; i < C::MB; ++i) {
-        const int64_t pi = tile0 + wbox + bg + C::NBG * i;
-        if (pi >= n_par) continue;
-        const int ii = (int)(pi % np_side), jj = (int)(pi / np_side);
-        T* dst = u + (size_t)morton2(2 * ii + px, 2 * jj + py) * NP + pg * C::MP;
+        const int64_t pr = tile0 + wbox + bg + C::NBG * i;
+        if (pr >= n_rows) continue;
+        int ii, jj;
+        row_ij(pr, ii, jj);
+        const uint32_t dst_box = MODE == kModeM2M ? morton2(ii, jj) : morton2(2 * ii + px, 2 * jj + py);
+        T* dst = out + (size_t)dst_box * NP + pg * C::MP;
 #pragma unroll
         for (int j = 0; j < C::MP; ++j) dst[j] = acc[i][j];
     }
 }
 
 // ------------------------------------------------------------------------- P2P + L2P
-// One warp per target leaf.  The sources of the leaf and its (up to) 8 neighbours are
-// staged in shared memory as (table offset, charge); lanes take sources, loop over up
-// to 32 targets held as table offsets, and a reduce-scatter leaves target t's sum in
-// lane t.  The table holds phi(dx, dy) for |dx|, |dy| <= 2s-1 at row width W, so
+// One warp per target leaf (row-major).  The sources of the leaf's 3x3 neighbourhood
+// (three contiguous ranges) are staged in shared memory as (table offset, charge).
+// For a batch of nt <= 32 targets the lanes are split into G = 32/nt groups: lane l
+// takes target l % nt and every G-th source of its group, so each near-field pair is
+// one table load and one FMA; the G partial sums are combined with shuffles.  The
+// table holds phi(dx, dy) for |dx|, |dy| <= 2s-1 with row width W, so
 // idx(target) - idx(source) addresses phi(target - source) directly.
 constexpr int kP2PWarps = 8;
 constexpr int kP2PCap = 9 * 64;  // staged sources per warp per chunk
 
+template <typename T>
+struct SrcEntry;
+template <>
+struct alignas(8) SrcEntry<float> {
+    int off;
+    float f;
+};
+template <>
+struct alignas(16) SrcEntry<double> {
+    int off, pad;
+    double f;
+};
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
-    int L, int side, int64_t n_leaves, const int32_t* __restrict__ sbeg,
-    const int32_t* __restrict__ sloc, const int32_t* __restrict__ tbeg,
-    const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
-    const T* __restrict__ f_sorted, const T* __restrict__ table, int tab_H, int tab_W,
-    const T* __restrict__ uhat, const T* __restrict__ tofsT, double* __restrict__ u,
-    double* __restrict__ u_near, double* __restrict__ u_far) {
+    int L, int side, const int32_t* __restrict__ sbeg, const int32_t* __restrict__ sloc,
+    const int32_t* __restrict__ tbeg, const int32_t* __restrict__ tloc,
+    const int32_t* __restrict__ tperm, const T* __restrict__ f_sorted, const T* __restrict__ table,
+    int tab_H, int tab_W, const T* __restrict__ uhat, const typename Mono<T>::V* __restrict__ Cleaf,
+    const T* __restrict__ tofsT, double* __restrict__ u, double* __restrict__ u_near,
+    double* __restrict__ u_far) {
+    using M = Mono<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tab_n = (2 * tab_H + 1) * tab_W;
     T* tab = reinterpret_cast<T*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int* s_off = reinterpret_cast<int*>(tab + tab_n) + warp * kP2PCap;
-    T* s_f = reinterpret_cast<T*>(reinterpret_cast<int*>(tab + tab_n) + kP2PWarps * kP2PCap) +
-             warp * kP2PCap;
+    SrcEntry<T>* s_src = reinterpret_cast<SrcEntry<T>*>(tab + tab_n) + warp * kP2PCap;
+    T* s_uhat = reinterpret_cast<T*>(reinterpret_cast<SrcEntry<T>*>(tab + tab_n) + kP2PWarps * kP2PCap) +
+                warp * NP;
     for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
     __syncthreads();
-    const char* tab_c = reinterpret_cast<const char*>(tab) +
-                        (size_t)(tab_H + tab_H * tab_W) * sizeof(T);  // centre
-    const int nside = 1 << L;
+    const T* tab_c = tab + (tab_H + tab_H * tab_W);  // centre: phi(0, 0)
+    const int n = 1 << L;
+    const int64_t n_leaves = (int64_t)n * n;
     const int64_t nwarps = (int64_t)gridDim.x * kP2PWarps;
-    constexpr int PL = NP / 32;
 
     for (int64_t leaf = (int64_t)blockIdx.x * kP2PWarps + warp; leaf < n_leaves; leaf += nwarps) {
         const int tb = tbeg[leaf], te = tbeg[leaf + 1];
         if (tb == te) continue;
-        uint32_t bx, by;
-        unmorton2((uint32_t)leaf, bx, by);
-        // neighbour ranges
-        int rb[9], rc[9], rbase[9];
+        const int bx = (int)(leaf & (n - 1)), by = (int)(leaf >> L);
+        const int c0 = max(bx - 1, 0), c1 = min(bx + 1, n - 1);
+        // three row ranges [rb, re) with column boundaries
+        int rb[3], rm1[3], rm2[3], re[3], rdy[3];
         int ns = 0;
 #pragma unroll
-        for (int d = 0; d < 9; ++d) {
-            const int dx = d % 3 - 1, dy = d / 3 - 1;
-            const int nx = (int)bx + dx, ny = (int)by + dy;
-            rb[d] = 0;
-            rc[d] = 0;
-            rbase[d] = dx * side + tab_W * (dy * side);
-            if (nx >= 0 && nx < nside && ny >= 0 && ny < nside) {
-                const uint32_t m = morton2(nx, ny);
-                rb[d] = sbeg[m];
-                rc[d] = sbeg[m + 1] - rb[d];
+        for (int r = 0; r < 3; ++r) {
+            const int yy = by + r - 1;
+            rdy[r] = r - 1;
+            if (yy < 0 || yy >= n) {
+                rb[r] = rm1[r] = rm2[r] = re[r] = 0;
+                continue;
             }
-            ns += rc[d];
+            const int base = yy * n;
+            rb[r] = sbeg[base + c0];
+            rm1[r] = sbeg[base + c0 + 1];
+            rm2[r] = c1 - c0 >= 2 ? sbeg[base + c0 + 2] : sbeg[base + c1 + 1];
+            re[r] = sbeg[base + c1 + 1];
+            ns += re[r] - rb[r];
         }
-        T uh[PL];
-#pragma unroll
-        for (int i = 0; i < PL; ++i) uh[i] = uhat ? uhat[(size_t)leaf * NP + lane + 32 * i] : T(0);
+        if (uhat) {
+            const uint32_t mort = morton2(bx, by);
+            for (int i = lane; i < NP; i += 32) s_uhat[i] = uhat[(size_t)mort * NP + i];
+        }
+        __syncwarp();
         const int n_chunks = (ns + kP2PCap - 1) / kP2PCap;
-
-        auto fill = [&](int c0) {
-            const int cn = min(kP2PCap, ns - c0);
-            for (int v = lane; v < cn; v += 32) {
-                int g = c0 + v, d = 0;
-                while (g >= rc[d]) {
-                    g -= rc[d];
-                    ++d;
+        auto fill = [&](int v0) {
+            const int cn = min(kP2PCap, ns - v0);
+            int skip = v0;
+            int w = 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int len = re[r] - rb[r];
+                int a = min(skip, len);
+                skip -= a;
+                const int take = min(len - a, cn - w);
+                const int ybase = tab_W * (rdy[r] * side);
+                for (int v = lane; v < take; v += 32) {
+                    const int j = rb[r] + a + v;
+                    const int col = c0 + (j >= rm1[r]) + (j >= rm2[r]);
+                    const int l = sloc[j];
+                    SrcEntry<T> e;
+                    e.off = (col - bx) * side + (l & 0xffff) + ybase + tab_W * (l >> 16);
+                    e.f = f_sorted[j];
+                    s_src[w + v] = e;
                 }
-                const int j = rb[d] + g;
-                const int l = sloc[j];
-                s_off[v] = rbase[d] + (l & 0xffff) + tab_W * (l >> 16);
-                s_f[v] = f_sorted[j];
+                w += take;
             }
             __syncwarp();
             return cn;
         };
-
         int cn = n_chunks == 1 ? fill(0) : 0;
+        const typename M::V cl = Cleaf ? Cleaf[morton2(bx, by)] : M::zero();
         for (int t0 = tb; t0 < te; t0 += 32) {
             const int nt = min(32, te - t0);
-            int my_toff = 0, my_J = 0;
-            if (lane < nt) {
-                const int l = tloc[t0 + lane];
-                const int tx = l & 0xffff, ty = l >> 16;
-                my_toff = tx + tab_W * ty;
-                my_J = tx + side * ty;
-            }
-            int toff[32];
-#pragma unroll
-            for (int t = 0; t < 32; ++t) toff[t] = shfl(my_toff, t) * (int)sizeof(T);
-            T acc[32];
-#pragma unroll
-            for (int t = 0; t < 32; ++t) acc[t] = T(0);
+            const int G = 32 / nt;
+            const int t = lane % nt, g = lane / nt;
+            const bool active = g < G;
+            const int tl = tloc[t0 + t];
+            const int tx = tl & 0xffff, ty = tl >> 16;
+            const T* tp = tab_c + (tx + tab_W * ty);
+            T acc = T(0);
             for (int ch = 0; ch < n_chunks; ++ch) {
                 if (n_chunks > 1) {
                     __syncwarp();
                     cn = fill(ch * kP2PCap);
                 }
-                for (int r = 0; r < cn; r += 32) {
-                    const int v = r + lane;
-                    const int so = v < cn ? s_off[v] : s_off[0];
-                    const T fj = v < cn ? s_f[v] : T(0);
-                    const char* tb_c = tab_c - (ptrdiff_t)so * (ptrdiff_t)sizeof(T);
-#pragma unroll
-                    for (int tc = 0; tc < 4; ++tc) {
-                        if (tc * 8 < nt) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q)
-                                acc[tc * 8 + q] =
-                                    fma(*reinterpret_cast<const T*>(tb_c + toff[tc * 8 + q]), fj,
-                                        acc[tc * 8 + q]);
-                        }
+                if (active) {
+                    int j = g;
+                    for (; j + G < cn; j += 2 * G) {
+                        const SrcEntry<T> e0 = s_src[j], e1 = s_src[j + G];
+                        acc = fma(tp[-e0.off], e0.f, acc);
+                        acc = fma(tp[-e1.off], e1.f, acc);
+                    }
+                    if (j < cn) {
+                        const SrcEntry<T> e0 = s_src[j];
+                        acc = fma(tp[-e0.off], e0.f, acc);
                     }
                 }
             }
-            const T near = reduce_scatter32(acc);
-            // L2P: u_far(t) = sum_p T_ofs[p][J_t] u_hat[p]
-            T far = T(0);
-            if (uhat) {
-#pragma unroll
-                for (int t = 0; t < 32; ++t) acc[t] = T(0);
-#pragma unroll
-                for (int tc = 0; tc < 4; ++tc) {
-                    if (tc * 8 < nt) {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const T* row = tofsT + (size_t)shfl(my_J, tc * 8 + q) * NP;
-                            T s = T(0);
-#pragma unroll
-                            for (int i = 0; i < PL; ++i) s = fma(__ldg(row + lane + 32 * i), uh[i], s);
-                            acc[tc * 8 + q] = s;
-                        }
-                    }
-                }
-                far = reduce_scatter32(acc);
+            // combine the G groups into lane t
+            for (int k = 1; k < G; ++k) {
+                const T v = shfl(acc, t + k * nt);
+                if (g == 0) acc += v;
             }
             if (lane < nt) {
+                T far = T(0);
+                if (uhat) {
+                    const T* row = tofsT + (size_t)(tx + side * ty) * NP;
+#pragma unroll 8
+                    for (int p = 0; p < NP; ++p) far = fma(__ldg(row + p), s_uhat[p], far);
+                }
                 const int dst = tperm[t0 + lane];
-                const double dn = (double)near, df = (double)far;
+                const double dn = (double)acc;
+                const double df = (double)far + M::to_double(cl);
                 if (u) u[dst] = dn + df;
                 if (u_near) u_near[dst] = dn;
                 if (u_far) u_far[dst] = df;
@@ -431,100 +526,113 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
 // ------------------------------------------------------------------------- launchers
 template <typename T>
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
-                       T* qhat_leaf, cudaStream_t s) {
+                       T* qhat_leaf, void* Q, cudaStream_t s) {
     const int threads = 256;
     int64_t blocks = (t.n_leaves * 32 + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
+    using V = typename Mono<T>::V;
     if (ops.NP == 32)
-        p2m_kernel<T, 32><<<(int)blocks, threads, 0, s>>>(t.n_leaves, t.src_begin, t.src_loc, t.src_perm, f,
-                                                          f_sorted, (const T*)ops.tofsT, t.side, qhat_leaf);
+        p2m_kernel<T, 32><<<(int)blocks, threads, 0, s>>>(t.L, t.src_begin, t.src_loc, t.src_perm, f, f_sorted,
+                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q);
     else
-        p2m_kernel<T, 64><<<(int)blocks, threads, 0, s>>>(t.n_leaves, t.src_begin, t.src_loc, t.src_perm, f,
-                                                          f_sorted, (const T*)ops.tofsT, t.side, qhat_leaf);
+        p2m_kernel<T, 64><<<(int)blocks, threads, 0, s>>>(t.L, t.src_begin, t.src_loc, t.src_perm, f, f_sorted,
+                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_m2m(const DeviceOps& ops, int k, const T* q_child, T* q_parent, int64_t n_parent,
-                       cudaStream_t s) {
-    const int threads = 256;
-    int64_t blocks = (n_parent * 32 + threads - 1) / threads;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    if (blocks < 1) blocks = 1;
-    if (ops.NP == 32)
-        m2m_kernel<T, 32><<<(int)blocks, threads, 0, s>>>(n_parent, q_child, (const T*)ops.m2m[k], q_parent);
-    else
-        m2m_kernel<T, 64><<<(int)blocks, threads, 0, s>>>(n_parent, q_child, (const T*)ops.m2m[k], q_parent);
-    return cudaGetLastError();
-}
-
-template <typename T, int NP>
-static cudaError_t launch_m2l_np(const DeviceOps& ops, int k, int level, const T* q, const T* u_par,
-                                 T* u, cudaStream_t s) {
-    using C = M2LCfg<T, NP>;
+template <typename T, int NP, int MODE>
+static cudaError_t launch_translate(int level, const T* q, const T* u_par, const T* op, const T* l2l,
+                                    const T* mono, const void* Qin, const void* Cpar, T* out, void* Qout,
+                                    void* Cout, cudaStream_t s) {
+    using C = TrCfg<T, NP>;
+    using V = typename Mono<T>::V;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(m2l_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(translate_kernel<T, NP, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t n_par = (int64_t)1 << (2 * (level - 1));
-    dim3 grid((unsigned)((n_par + C::BB - 1) / C::BB), 4);
-    m2l_kernel<T, NP><<<grid, 128, C::SMEM, s>>>(level, q, u_par, (const T*)ops.tifo[k],
-                                                 u_par ? (const T*)ops.l2l[k + 1] : nullptr, u);
+    const int lg = MODE == kModeM2L ? level - 1 : level;
+    const int64_t rows = (int64_t)1 << (2 * lg);
+    dim3 grid((unsigned)((rows + C::BB - 1) / C::BB), MODE == kModeM2L ? 4 : 1);
+    translate_kernel<T, NP, MODE><<<grid, C::THREADS, C::SMEM, s>>>(
+        level, q, u_par, op, l2l, mono, (const V*)Qin, (const V*)Cpar, out, (V*)Qout, (V*)Cout);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const T* u_parent,
-                       T* u_level, cudaStream_t s) {
-    if (ops.NP == 32) return launch_m2l_np<T, 32>(ops, k, level, q_level, u_parent, u_level, s);
-    return launch_m2l_np<T, 64>(ops, k, level, q_level, u_parent, u_level, s);
+cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
+                       T* q_parent, void* Q_parent, cudaStream_t s) {
+    if (ops.NP == 32)
+        return launch_translate<T, 32, kModeM2M>(level, q_child, nullptr, (const T*)ops.m2m[k], nullptr, nullptr,
+                                                 Q_child, nullptr, q_parent, Q_parent, nullptr, s);
+    return launch_translate<T, 64, kModeM2M>(level, q_child, nullptr, (const T*)ops.m2m[k], nullptr, nullptr,
+                                             Q_child, nullptr, q_parent, Q_parent, nullptr, s);
+}
+
+template <typename T>
+cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
+                       const T* u_parent, const void* C_parent, T* u_level, void* C_level, cudaStream_t s) {
+    const T* l2l = u_parent ? (const T*)ops.l2l[k + 1] : nullptr;
+    if (ops.NP == 32)
+        return launch_translate<T, 32, kModeM2L>(level, q_level, u_parent, (const T*)ops.tifo[k], l2l,
+                                                 (const T*)ops.mono[k], Q_level, C_parent, u_level, nullptr,
+                                                 C_level, s);
+    return launch_translate<T, 64, kModeM2L>(level, q_level, u_parent, (const T*)ops.tifo[k], l2l,
+                                             (const T*)ops.mono[k], Q_level, C_parent, u_level, nullptr, C_level,
+                                             s);
 }
 
 template <typename T, int NP>
-static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
-                                 const T* uhat, double* u, double* un, double* uf, int num_sms,
+static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const T* f_sorted, const T* uhat,
+                                 const void* Cleaf, double* u, double* un, double* uf, int num_sms,
                                  cudaStream_t s) {
     const size_t tab_bytes = (size_t)(2 * ops.tab_H + 1) * ops.tab_W * sizeof(T);
-    const size_t smem = ((tab_bytes + 15) & ~(size_t)15) +
-                        (size_t)kP2PWarps * kP2PCap * (sizeof(int) + sizeof(T));
+    const size_t smem = ((tab_bytes + 15) & ~(size_t)15) + (size_t)kP2PWarps * kP2PCap * sizeof(SrcEntry<T>) +
+                        (size_t)kP2PWarps * NP * sizeof(T);
     static size_t attr_bytes = 0;
+    static int per_sm_cached = 0;
+    static size_t per_sm_for = 0;
     if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(p2p_l2p_kernel<T, NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(p2p_l2p_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_l2p_kernel<T, NP>, kP2PWarps * 32, smem);
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm_for != smem) {
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_l2p_kernel<T, NP>, kP2PWarps * 32, smem);
+        per_sm_cached = per_sm < 1 ? 1 : per_sm;
+        per_sm_for = smem;
+    }
     int64_t blocks = (t.n_leaves + kP2PWarps - 1) / kP2PWarps;
-    const int64_t cap = (int64_t)num_sms * per_sm;
+    const int64_t cap = (int64_t)num_sms * per_sm_cached;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    using V = typename Mono<T>::V;
     p2p_l2p_kernel<T, NP><<<(int)blocks, kP2PWarps * 32, smem, s>>>(
-        t.L, t.side, t.n_leaves, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted,
-        (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, uhat, (const T*)ops.tofsT, u, un, uf);
+        t.L, t.side, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted, (const T*)ops.p2p_table,
+        ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const T*)ops.tofsT, u, un, uf);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted, const T* uhat,
-                           double* u, double* un, double* uf, int num_sms, cudaStream_t s) {
-    if (ops.NP == 32) return launch_p2p_np<T, 32>(t, ops, f_sorted, uhat, u, un, uf, num_sms, s);
-    return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, u, un, uf, num_sms, s);
+                           const void* Cleaf, double* u, double* un, double* uf, int num_sms, cudaStream_t s) {
+    if (ops.NP == 32) return launch_p2p_np<T, 32>(t, ops, f_sorted, uhat, Cleaf, u, un, uf, num_sms, s);
+    return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, Cleaf, u, un, uf, num_sms, s);
 }
 
-#define LFMM_INSTANTIATE(T)                                                                         \
-    template cudaError_t launch_p2m<T>(const TreeView&, const DeviceOps&, const double*, T*, T*,    \
-                                       cudaStream_t);                                               \
-    template cudaError_t launch_m2m<T>(const DeviceOps&, int, const T*, T*, int64_t, cudaStream_t); \
-    template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const T*, T*,          \
-                                       cudaStream_t);                                               \
-    template cudaError_t launch_p2p_l2p<T>(const TreeView&, const DeviceOps&, const T*, const T*,   \
+#define LFMM_INSTANTIATE(T)                                                                                   \
+    template cudaError_t launch_p2m<T>(const TreeView&, const DeviceOps&, const double*, T*, T*, void*,       \
+                                       cudaStream_t);                                                         \
+    template cudaError_t launch_m2m<T>(const DeviceOps&, int, int, const T*, const void*, T*, void*,         \
+                                       cudaStream_t);                                                         \
+    template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const void*, const T*,          \
+                                       const void*, T*, void*, cudaStream_t);                                 \
+    template cudaError_t launch_p2p_l2p<T>(const TreeView&, const DeviceOps&, const T*, const T*, const void*, \
                                            double*, double*, double*, int, cudaStream_t);
 
 LFMM_INSTANTIATE(float)

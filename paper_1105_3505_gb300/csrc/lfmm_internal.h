@@ -101,7 +101,8 @@ void tifo_matrix(const LevelOps& lv, int o, std::vector<double>& out);
 // Layout per level k (levels above the leaf), element type T, padded length NP:
 //   m2m  [4NP][NP]   m2m[c*NP+q][p] = S_k[p][c*P_{k-1}+q]     (q-hat_parent = sum)
 //   l2l  [4][NP][NP] l2l[c][q][p]   = S_k[q][c*P_{k-1}+p]     (u-hat_child += ...)
-//   tifo [40][NP][NP] tifo[o][q][p] = phi(skel_p - skel_q - o*side)
+//   tifo [40][NP][NP] tifo[o][q][p] = phi(skel_p - skel_q - o*side) - c_o
+//   mono [2][40]      c_o = phi(o*side) split as (hi, lo) of the element type
 // Leaf: tofsT [s^2][NP] tofsT[J][p] = T_ofs[p][J];  P2P table [(2H+1)][W].
 struct DeviceOps {
     int NP = 0, precision = 0, n_levels = 0, leaf_side = 0;
@@ -111,6 +112,7 @@ struct DeviceOps {
     void* tofsT = nullptr;
     void* p2p_table = nullptr;
     std::vector<void*> m2m, l2l, tifo;    // per level k
+    std::vector<void*> mono;              // per level k: deflation constants (hi[40], lo[40])
     std::vector<void*> retired;           // earlier, smaller uploads (kept alive)
 };
 
@@ -141,7 +143,7 @@ struct TreeView {
     int L = 0;                 // leaf level
     int side = 0;              // leaf side
     int64_t n_leaves = 0;      // 4^L
-    const int32_t* src_begin = nullptr;  // n_leaves + 1
+    const int32_t* src_begin = nullptr;  // n_leaves + 1, row-major leaf order
     const int32_t* tgt_begin = nullptr;
     const int32_t* src_loc = nullptr;    // (lx | ly << 16) within the leaf
     const int32_t* src_perm = nullptr;   // caller index of each sorted source
@@ -157,25 +159,31 @@ cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt,
                              int32_t* cnt_tgt, cudaStream_t s);
 cudaError_t launch_coarsen(const int32_t* fs, const int32_t* ft, int64_t n_coarse, int32_t* cs,
                            int32_t* ct, int* max4, cudaStream_t s);
+// Exclusive scan over the 4^L leaves in row-major order of two Morton-indexed count
+// arrays; out has 4^L + 1 entries.
 cudaError_t launch_scan2(const int32_t* in_a, int32_t* out_a, const int32_t* in_b,
-                         int32_t* out_b, int64_t n, int32_t* partials, cudaStream_t s);
+                         int32_t* out_b, int L, int32_t* partials, cudaStream_t s);
 size_t scan_partials_size(int64_t n);
+// Buckets points by leaf in row-major leaf order (leaf = by * 2^L + bx).
 cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int shift,
-                           int leaf_side, const int32_t* begin, int32_t* cursor, int32_t* loc,
+                           int leaf_side, int L, const int32_t* begin, int32_t* cursor, int32_t* loc,
                            int32_t* perm, cudaStream_t s);
 
+// Per-box scalars Q (total charge) and C (incoming constant) are 8 bytes per box:
+// a float (hi, lo) pair on the mixed path, a double on the binary64 path.
 template <typename T>
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
-                       T* qhat_leaf, cudaStream_t s);
+                       T* qhat_leaf, void* Q_leaf, cudaStream_t s);
 template <typename T>
-cudaError_t launch_m2m(const DeviceOps& ops, int k, const T* q_child, T* q_parent,
-                       int64_t n_parent, cudaStream_t s);
+cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
+                       T* q_parent, void* Q_parent, cudaStream_t s);
 template <typename T>
-cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
-                       const T* u_parent, T* u_level, cudaStream_t s);
+cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
+                       const T* u_parent, const void* C_parent, T* u_level, void* C_level,
+                       cudaStream_t s);
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
-                           const T* uhat_leaf, double* u, double* u_near, double* u_far,
-                           int num_sms, cudaStream_t s);
+                           const T* uhat_leaf, const void* C_leaf, double* u, double* u_near,
+                           double* u_far, int num_sms, cudaStream_t s);
 
 }  // namespace lfmm

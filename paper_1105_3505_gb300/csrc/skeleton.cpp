@@ -277,7 +277,7 @@ template <typename T>
 void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
                        std::vector<T>& img, size_t& off_tofs, size_t& off_tab,
                        std::vector<size_t>& off_m2m, std::vector<size_t>& off_l2l,
-                       std::vector<size_t>& off_tifo) {
+                       std::vector<size_t>& off_tifo, std::vector<size_t>& off_mono) {
     const int s = mo.leaf_side;
     auto align = [](size_t v) { return (v + 31) & ~(size_t)31; };  // 128/256-byte aligned blocks
     size_t n = 0;
@@ -288,7 +288,10 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
     off_m2m.assign(n_levels, 0);
     off_l2l.assign(n_levels, 0);
     off_tifo.assign(n_levels, 0);
+    off_mono.assign(n_levels, 0);
     for (int k = 0; k < n_levels; ++k) {
+        off_mono[k] = n;
+        n = align(n + (size_t)2 * kNumOffsets);
         if (k >= 1) {
             off_m2m[k] = n;
             n = align(n + (size_t)4 * NP * NP);
@@ -322,11 +325,20 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
                         img[off_l2l[k] + ((size_t)c * NP + p) * NP + q] = (T)v;   // [c][p_par][q_child]
                     }
         }
+        // Deflated M2L: T_ifo minus its centre-to-centre value c_o = phi(o * side).  The
+        // removed rank-one part c_o 1 1^T acts on a box's total charge Q; the kernels
+        // carry c_o * Q in a compensated scalar channel (values ~|Q| that cancel across
+        // boxes and levels), so rounding of the expansions only meets the small remainder.
+        const OffsetTable& ot = offsets();
         for (int o = 0; o < kNumOffsets; ++o) {
             tifo_matrix(lv, o, t);
+            const double c = phi_host((int64_t)ot.ox[o] * lv.side, (int64_t)ot.oy[o] * lv.side);
+            const T hi = (T)c;
+            img[off_mono[k] + o] = hi;
+            img[off_mono[k] + kNumOffsets + o] = (T)(c - (double)hi);
             for (int p = 0; p < lv.P; ++p)
                 for (int q = 0; q < lv.P; ++q)
-                    img[off_tifo[k] + ((size_t)o * NP + q) * NP + p] = (T)t[(size_t)p * lv.P + q];
+                    img[off_tifo[k] + ((size_t)o * NP + q) * NP + p] = (T)(t[(size_t)p * lv.P + q] - c);
         }
     }
 }
@@ -348,17 +360,17 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
     d->tab_H = 2 * mo->leaf_side - 1;
     d->tab_W = 4 * mo->leaf_side;
     size_t off_tofs, off_tab;
-    std::vector<size_t> om, ol, ot;
+    std::vector<size_t> om, ol, ot, omono;
     std::vector<char> bytes;
     size_t elem;
     if (precision == LFMM_MIXED) {
         std::vector<float> img;
-        fill_device_image<float>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot);
+        fill_device_image<float>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono);
         elem = sizeof(float);
         bytes.assign((const char*)img.data(), (const char*)img.data() + img.size() * elem);
     } else {
         std::vector<double> img;
-        fill_device_image<double>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot);
+        fill_device_image<double>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono);
         elem = sizeof(double);
         bytes.assign((const char*)img.data(), (const char*)img.data() + img.size() * elem);
     }
@@ -381,10 +393,12 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
     d->m2m.resize(nl);
     d->l2l.resize(nl);
     d->tifo.resize(nl);
+    d->mono.resize(nl);
     for (int k = 0; k < nl; ++k) {
         d->m2m[k] = k >= 1 ? b + om[k] * elem : nullptr;
         d->l2l[k] = k >= 1 ? b + ol[k] * elem : nullptr;
         d->tifo[k] = b + ot[k] * elem;
+        d->mono[k] = b + omono[k] * elem;
     }
     if (slot) d->retired.push_back(slot.release());  // plans built earlier may still use it
     slot = std::move(d);

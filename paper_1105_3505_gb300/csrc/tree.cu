@@ -125,15 +125,22 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) 
     return warp_off + x - v;
 }
 
+// Counts are stored Morton-indexed; the scan runs over leaves in row-major order
+// (index i = by * 2^L + bx), gathering count[morton(bx, by)].
+__device__ __forceinline__ int32_t count_rm(const int32_t* in, int64_t i, int L) {
+    const uint32_t bx = (uint32_t)(i & ((1 << L) - 1)), by = (uint32_t)(i >> L);
+    return in[morton2(bx, by)];
+}
+
 __global__ void scan_tile_sums(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
-                               int64_t n, int32_t* __restrict__ partials) {
+                               int64_t n, int L, int32_t* __restrict__ partials) {
     __shared__ int sh[kThreads / 32];
     const int32_t* in = blockIdx.y ? b : a;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int s = 0;
     for (int k = 0; k < kScanItems; ++k) {
         const int64_t i = base + (int64_t)k * kThreads + threadIdx.x;
-        if (i < n) s += in[i];
+        if (i < n) s += count_rm(in, i, L);
     }
     int total;
     block_exclusive_scan(s, sh, total);
@@ -155,7 +162,7 @@ __global__ void scan_partials(int32_t* __restrict__ partials, int n_tiles) {
 }
 
 __global__ void scan_tiles(const int32_t* __restrict__ a, int32_t* __restrict__ oa,
-                           const int32_t* __restrict__ b, int32_t* __restrict__ ob, int64_t n,
+                           const int32_t* __restrict__ b, int32_t* __restrict__ ob, int64_t n, int L,
                            const int32_t* __restrict__ partials) {
     __shared__ int sh[kThreads / 32];
     const int32_t* in = blockIdx.y ? b : a;
@@ -165,7 +172,7 @@ __global__ void scan_tiles(const int32_t* __restrict__ a, int32_t* __restrict__ 
     int s = 0;
     for (int k = 0; k < kScanItems; ++k) {
         const int64_t i = base + k;
-        v[k] = i < n ? in[i] : 0;
+        v[k] = i < n ? count_rm(in, i, L) : 0;
         s += v[k];
     }
     int total;
@@ -179,14 +186,15 @@ __global__ void scan_tiles(const int32_t* __restrict__ a, int32_t* __restrict__ 
 }
 
 __global__ void scatter_kernel(const int2* __restrict__ xy, int64_t n, int64_t x0, int64_t y0,
-                               int shift, int leaf_side, const int32_t* __restrict__ begin,
+                               int shift, int leaf_side, int n_side, const int32_t* __restrict__ begin,
                                int32_t* __restrict__ cursor, int32_t* __restrict__ loc,
                                int32_t* __restrict__ perm) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = xy[i];
         const int64_t rx = (int64_t)p.x - x0, ry = (int64_t)p.y - y0;
-        const uint32_t leaf = morton2((uint32_t)(rx >> shift), (uint32_t)(ry >> shift));
+        const uint32_t L = (uint32_t)__popc((unsigned)(n_side - 1));
+        const uint32_t leaf = ((uint32_t)(ry >> shift) << L) | (uint32_t)(rx >> shift);
         const int slot = begin[leaf] + atomicAdd(cursor + leaf, 1);
         const int lx = (int)(rx & (leaf_side - 1)), ly = (int)(ry & (leaf_side - 1));
         loc[slot] = lx | (ly << 16);
@@ -242,22 +250,23 @@ size_t scan_partials_size(int64_t n) {
     return (size_t)(2 * (tiles < 1 ? 1 : tiles));
 }
 
-cudaError_t launch_scan2(const int32_t* a, int32_t* oa, const int32_t* b, int32_t* ob, int64_t n,
+cudaError_t launch_scan2(const int32_t* a, int32_t* oa, const int32_t* b, int32_t* ob, int L,
                          int32_t* partials, cudaStream_t s) {
+    const int64_t n = (int64_t)1 << (2 * L);
     int tiles = (int)((n + kScanTile - 1) / kScanTile);
     if (tiles < 1) tiles = 1;
     dim3 g(tiles, 2);
-    scan_tile_sums<<<g, kThreads, 0, s>>>(a, b, n, partials);
+    scan_tile_sums<<<g, kThreads, 0, s>>>(a, b, n, L, partials);
     scan_partials<<<2, kThreads, 0, s>>>(partials, tiles);
-    scan_tiles<<<g, kThreads, 0, s>>>(a, oa, b, ob, n, partials);
+    scan_tiles<<<g, kThreads, 0, s>>>(a, oa, b, ob, n, L, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int shift,
-                           int leaf_side, const int32_t* begin, int32_t* cursor, int32_t* loc,
+                           int leaf_side, int L, const int32_t* begin, int32_t* cursor, int32_t* loc,
                            int32_t* perm, cudaStream_t s) {
     scatter_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>((const int2*)xy, n, x0, y0, shift,
-                                                             leaf_side, begin, cursor, loc, perm);
+                                                             leaf_side, 1 << L, begin, cursor, loc, perm);
     return cudaGetLastError();
 }
 
