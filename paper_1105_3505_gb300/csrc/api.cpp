@@ -337,7 +337,7 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     {
         PhaseTimer pt(LFMM_PHASE_P2P, s);
         LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, L >= 2 ? Ux(L) : nullptr,
-                                        L >= 2 ? Cm(L) : nullptr, u, un, uf, p->num_sms, s));
+                                        L >= 2 ? Cm(L) : nullptr, Qm(L), u, un, uf, p->num_sms, s));
         pt.add_launches(1);
     }
     return LFMM_OK;

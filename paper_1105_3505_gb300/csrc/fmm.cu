@@ -372,9 +372,12 @@ __global__ void __launch_bounds__(128) translate_kernel(int level, const T* __re
 // (three contiguous ranges) are staged in shared memory as (table offset, charge).
 // For a batch of nt <= 32 targets the lanes are split into G = 32/nt groups: lane l
 // takes target l % nt and every G-th source of its group, so each near-field pair is
-// one table load and one FMA; the G partial sums are combined with shuffles.  The
-// table holds phi(dx, dy) for |dx|, |dy| <= 2s-1 with row width W, so
-// idx(target) - idx(source) addresses phi(target - source) directly.
+// one table load and one multiply-add; the G partial sums are combined with shuffles.
+// The table holds phi(dx, dy) - phi0 for |dx|, |dy| <= 2s-1 with row width W, so
+// idx(target) - idx(source) addresses it directly; phi0 times the block's charge (sum
+// of the nine leaf charges Q) is added in the compensated channel.  On the mixed path
+// each lane sums its products with Kahan compensation: the near field of a target is
+// a sum of up to 9 N_leaf terms whose constant parts cancel.
 constexpr int kP2PWarps = 8;
 constexpr int kP2PCap = 9 * 64;  // staged sources per warp per chunk
 
@@ -397,8 +400,8 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
     const int32_t* __restrict__ tbeg, const int32_t* __restrict__ tloc,
     const int32_t* __restrict__ tperm, const T* __restrict__ f_sorted, const T* __restrict__ table,
     int tab_H, int tab_W, const T* __restrict__ uhat, const typename Mono<T>::V* __restrict__ Cleaf,
-    const T* __restrict__ tofsT, double* __restrict__ u, double* __restrict__ u_near,
-    double* __restrict__ u_far) {
+    const typename Mono<T>::V* __restrict__ Qleaf, const T* __restrict__ tofsT,
+    double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
     using M = Mono<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tab_n = (2 * tab_H + 1) * tab_W;
@@ -408,8 +411,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
     T* s_uhat = reinterpret_cast<T*>(reinterpret_cast<SrcEntry<T>*>(tab + tab_n) + kP2PWarps * kP2PCap) +
                 warp * NP;
     for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    const typename M::V phi0 = M::make(table[tab_n], table[tab_n + 1]);
     __syncthreads();
-    const T* tab_c = tab + (tab_H + tab_H * tab_W);  // centre: phi(0, 0)
+    const T* tab_c = tab + (tab_H + tab_H * tab_W);  // centre: phi(0, 0) - phi0
     const int n = 1 << L;
     const int64_t n_leaves = (int64_t)n * n;
     const int64_t nwarps = (int64_t)gridDim.x * kP2PWarps;
@@ -422,6 +426,16 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
         // three row ranges [rb, re) with column boundaries
         int rb[3], rm1[3], rm2[3], re[3], rdy[3];
         int ns = 0;
+        // charge of the 3x3 block (lanes 0..8 each read one leaf)
+        typename M::V qn = M::zero();
+        {
+            const int dx = lane % 3 - 1, dy = lane / 3 - 1;
+            const int nx = bx + dx, ny = by + dy;
+            if (lane < 9 && nx >= 0 && nx < n && ny >= 0 && ny < n) qn = Qleaf[morton2(nx, ny)];
+#pragma unroll
+            for (int off = 16; off; off >>= 1) qn = M::add(qn, shfl_xor_v(qn, off));
+        }
+        const double near_const = M::to_double(M::mul(phi0, qn));
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             const int yy = by + r - 1;
@@ -478,7 +492,17 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
             const int tl = tloc[t0 + t];
             const int tx = tl & 0xffff, ty = tl >> 16;
             const T* tp = tab_c + (tx + tab_W * ty);
-            T acc = T(0);
+            T acc = T(0), cmp = T(0);  // Kahan sum and its compensation (mixed path)
+            auto add = [&](T term) {
+                if constexpr (sizeof(T) == 4) {
+                    const T y = term - cmp;
+                    const T s2 = acc + y;
+                    cmp = (s2 - acc) - y;
+                    acc = s2;
+                } else {
+                    acc += term;
+                }
+            };
             for (int ch = 0; ch < n_chunks; ++ch) {
                 if (n_chunks > 1) {
                     __syncwarp();
@@ -488,20 +512,24 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
                     int j = g;
                     for (; j + G < cn; j += 2 * G) {
                         const SrcEntry<T> e0 = s_src[j], e1 = s_src[j + G];
-                        acc = fma(tp[-e0.off], e0.f, acc);
-                        acc = fma(tp[-e1.off], e1.f, acc);
+                        const T p0 = tp[-e0.off] * e0.f;
+                        const T p1 = tp[-e1.off] * e1.f;
+                        add(p0);
+                        add(p1);
                     }
                     if (j < cn) {
                         const SrcEntry<T> e0 = s_src[j];
-                        acc = fma(tp[-e0.off], e0.f, acc);
+                        add(tp[-e0.off] * e0.f);
                     }
                 }
             }
-            // combine the G groups into lane t
+            // combine the G groups into lane t (compensations folded in)
+            acc -= cmp;
             for (int k = 1; k < G; ++k) {
                 const T v = shfl(acc, t + k * nt);
-                if (g == 0) acc += v;
+                if (g == 0) add(v);
             }
+            acc -= cmp;
             if (lane < nt) {
                 T far = T(0);
                 if (uhat) {
@@ -510,7 +538,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
                     for (int p = 0; p < NP; ++p) far = fma(__ldg(row + p), s_uhat[p], far);
                 }
                 const int dst = tperm[t0 + lane];
-                const double dn = (double)acc;
+                const double dn = (double)acc + near_const;
                 const double df = (double)far + M::to_double(cl);
                 if (u) u[dst] = dn + df;
                 if (u_near) u_near[dst] = dn;
@@ -587,8 +615,8 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
 
 template <typename T, int NP>
 static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const T* f_sorted, const T* uhat,
-                                 const void* Cleaf, double* u, double* un, double* uf, int num_sms,
-                                 cudaStream_t s) {
+                                 const void* Cleaf, const void* Qleaf, double* u, double* un, double* uf,
+                                 int num_sms, cudaStream_t s) {
     const size_t tab_bytes = (size_t)(2 * ops.tab_H + 1) * ops.tab_W * sizeof(T);
     const size_t smem = ((tab_bytes + 15) & ~(size_t)15) + (size_t)kP2PWarps * kP2PCap * sizeof(SrcEntry<T>) +
                         (size_t)kP2PWarps * NP * sizeof(T);
@@ -614,15 +642,16 @@ static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const 
     using V = typename Mono<T>::V;
     p2p_l2p_kernel<T, NP><<<(int)blocks, kP2PWarps * 32, smem, s>>>(
         t.L, t.side, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted, (const T*)ops.p2p_table,
-        ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const T*)ops.tofsT, u, un, uf);
+        ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const V*)Qleaf, (const T*)ops.tofsT, u, un, uf);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted, const T* uhat,
-                           const void* Cleaf, double* u, double* un, double* uf, int num_sms, cudaStream_t s) {
-    if (ops.NP == 32) return launch_p2p_np<T, 32>(t, ops, f_sorted, uhat, Cleaf, u, un, uf, num_sms, s);
-    return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, Cleaf, u, un, uf, num_sms, s);
+                           const void* Cleaf, const void* Qleaf, double* u, double* un, double* uf, int num_sms,
+                           cudaStream_t s) {
+    if (ops.NP == 32) return launch_p2p_np<T, 32>(t, ops, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
+    return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
 }
 
 #define LFMM_INSTANTIATE(T)                                                                                   \
@@ -633,7 +662,7 @@ cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_s
     template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const void*, const T*,          \
                                        const void*, T*, void*, cudaStream_t);                                 \
     template cudaError_t launch_p2p_l2p<T>(const TreeView&, const DeviceOps&, const T*, const T*, const void*, \
-                                           double*, double*, double*, int, cudaStream_t);
+                                           const void*, double*, double*, double*, int, cudaStream_t);
 
 LFMM_INSTANTIATE(float)
 LFMM_INSTANTIATE(double)

@@ -103,7 +103,8 @@ void tifo_matrix(const LevelOps& lv, int o, std::vector<double>& out);
 //   l2l  [4][NP][NP] l2l[c][q][p]   = S_k[q][c*P_{k-1}+p]     (u-hat_child += ...)
 //   tifo [40][NP][NP] tifo[o][q][p] = phi(skel_p - skel_q - o*side) - c_o
 //   mono [2][40]      c_o = phi(o*side) split as (hi, lo) of the element type
-// Leaf: tofsT [s^2][NP] tofsT[J][p] = T_ofs[p][J];  P2P table [(2H+1)][W].
+// Leaf: tofsT [s^2][NP] tofsT[J][p] = T_ofs[p][J];
+//   P2P table [(2H+1)][W] of phi(dx,dy) - phi0, then phi0 = phi(s, 0) as (hi, lo).
 struct DeviceOps {
     int NP = 0, precision = 0, n_levels = 0, leaf_side = 0;
     int tab_H = 0, tab_W = 0;             // P2P table half width and row width
@@ -183,7 +184,7 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
                        cudaStream_t s);
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
-                           const T* uhat_leaf, const void* C_leaf, double* u, double* u_near,
-                           double* u_far, int num_sms, cudaStream_t s);
+                           const T* uhat_leaf, const void* C_leaf, const void* Q_leaf, double* u,
+                           double* u_near, double* u_far, int num_sms, cudaStream_t s);
 
 }  // namespace lfmm

@@ -284,7 +284,7 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
     off_tofs = n;
     n = align(n + (size_t)s * s * NP);
     off_tab = n;
-    n = align(n + (size_t)(2 * H + 1) * W);
+    n = align(n + (size_t)(2 * H + 1) * W + 2);
     off_m2m.assign(n_levels, 0);
     off_l2l.assign(n_levels, 0);
     off_tifo.assign(n_levels, 0);
@@ -307,10 +307,20 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
     for (int p = 0; p < leaf.P; ++p)
         for (int J = 0; J < s * s; ++J)
             img[off_tofs + (size_t)J * NP + p] = (T)mo.tofs[(size_t)p * s * s + J];
-    // P2P table: entry (dx, dy), |dx|,|dy| <= H, at (dy + H) * W + (dx + H)
+    // P2P table: entry (dx, dy), |dx|,|dy| <= H, at (dy + H) * W + (dx + H), deflated by
+    // phi0 = phi(s, 0) (about the middle of the near-field range); phi0 times the charge of
+    // the 3x3 leaf block is added back in the compensated channel.  phi0 as (hi, lo) after
+    // the table.
+    const double phi0 = phi_host(s, 0);
     for (int dy = -H; dy <= H; ++dy)
         for (int dx = -H; dx <= H; ++dx)
-            img[off_tab + (size_t)(dy + H) * W + (dx + H)] = (T)phi_host(dx, dy);
+            img[off_tab + (size_t)(dy + H) * W + (dx + H)] = (T)(phi_host(dx, dy) - phi0);
+    {
+        const size_t e = off_tab + (size_t)(2 * H + 1) * W;
+        const T hi = (T)phi0;
+        img[e] = hi;
+        img[e + 1] = (T)(phi0 - (double)hi);
+    }
     std::vector<double> t;
     for (int k = 0; k < n_levels; ++k) {
         const LevelOps& lv = mo.levels[k];
