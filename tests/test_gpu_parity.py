@@ -143,7 +143,9 @@ def test_edge_cases(lfmm, name, precision):
     tree = oracle.uniform_tree(s, t, 64, 32)
     assert (info["K"], info["L"], info["leaf_side"]) == (tree["K"], tree["L"], tree["side"])
     if np.abs(ref).max() == 0.0:
-        assert np.abs(u).max() == 0.0
+        # only coincident sources: phi(0) = 0 exactly; the mixed path's deflated table
+        # leaves a rounding residue of order eps * |f|
+        assert np.abs(u).max() <= (0.0 if precision == "fp64" else 1e-12 * np.abs(f).sum())
     elif name == "disjoint_far_targets" and precision == "mixed":
         # Zero-sum charges seen from far away: |u| is ~1e-3 of the size of the terms that
         # cancel in it, so a max-norm relative bound measures the problem's conditioning,
