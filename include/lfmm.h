@@ -122,6 +122,31 @@ const char* lfmm_status_string(int status);
 /* Detail of the last failure on the calling thread ("" if none). */
 const char* lfmm_last_error(void);
 
+/* ---- plan shape without allocation -------------------------------------------------- */
+/* The paper has no counterpart: this is a service entry point for callers that cannot
+ * allocate device memory when they have to decide about a problem - an admission
+ * controller sizing a request before committing memory to it, host code running while
+ * a stream is being captured into a CUDA graph (where allocation calls are illegal), or
+ * a process whose device memory belongs to another allocator.
+ *
+ * Fills *info with what lfmm_plan_create would produce for these points and opts: root
+ * corner and K, leaf level L and leaf side, largest leaf occupancies, P and P_pad, and
+ * device_bytes = the device memory the plan would own when its coordinates are given
+ * in device memory.  Calls no cudaMalloc/cudaFree or any allocating routine.
+ *   src_xy, tgt_xy  8-byte aligned DEVICE memory (LFMM_EINVAL otherwise)
+ *   stream          the work runs on it; the call synchronises it (results go to the host)
+ * Limits: the leaf-count scratch is a static device array of LFMM_NOALLOC_SCRATCH_BYTES
+ * (every GPU that loads the library holds it until the process exits); trees that need
+ * counting below level 10 (more than 4^10 boxes per level) are rejected with
+ * LFMM_EINVAL and a message saying so.  The first call on a device resolves the
+ * array's device address (cudaGetSymbolAddress) and should be made before any stream
+ * capture.  Calls share the array: concurrent calls (other streams or threads) race
+ * and must be serialised by the caller. */
+#define LFMM_NOALLOC_SCRATCH_BYTES (4 * (2 * (1 << 20) + 2 * (1 << 18) + 64))
+int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy,
+                            int64_t n_tgt, const lfmm_opts* opts, lfmm_plan_info* info,
+                            void* stream);
+
 /* ---- tracing ---------------------------------------------------------------------- */
 /* Phases timed by the profiler with CUDA events recorded on the stream each phase is
  * enqueued on (plan create: TREE, OPERATORS; eval: the sweeps of Sec. 8.2). */

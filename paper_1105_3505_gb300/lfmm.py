@@ -71,6 +71,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "lfmm_profile_read": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "lfmm_launch_count": (ctypes.c_int64, []),
+        "lfmm_plan_shape_noalloc": (ctypes.c_int, [vp, i64, vp, i64, ctypes.POINTER(lfmm_opts),
+                                                   ctypes.POINTER(lfmm_plan_info), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -145,6 +147,18 @@ def lfmm_plan_destroy(plan: int) -> None:
 def lfmm_plan_get_info(plan: int) -> dict:
     info = lfmm_plan_info()
     _check(load().lfmm_plan_get_info(plan, ctypes.byref(info)), "lfmm_plan_get_info")
+    return {name: getattr(info, name) for name, _ in lfmm_plan_info._fields_}
+
+
+def lfmm_plan_shape_noalloc(src_xy, n_src: int, tgt_xy, n_tgt: int, opts: lfmm_opts | None,
+                            stream=None) -> dict:
+    """Tree shape and device footprint of a would-be plan, computed without allocating
+    (see include/lfmm.h); coordinates must be CUDA tensors."""
+    info = lfmm_plan_info()
+    _check(load().lfmm_plan_shape_noalloc(_ptr(src_xy), int(n_src), _ptr(tgt_xy), int(n_tgt),
+                                          ctypes.byref(opts) if opts is not None else None,
+                                          ctypes.byref(info), _stream_handle(stream)),
+           "lfmm_plan_shape_noalloc")
     return {name: getattr(info, name) for name, _ in lfmm_plan_info._fields_}
 
 
