@@ -305,6 +305,8 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     t.src_perm = p->src_perm;
     t.tgt_loc = p->tgt_loc;
     t.tgt_perm = p->tgt_perm;
+    t.max_leaf_src = p->max_src;
+    t.max_leaf_tgt = p->max_tgt;
     const DeviceOps& ops = *p->ops;
     const int NP = p->NP;
     T* q = (T*)p->qhat;

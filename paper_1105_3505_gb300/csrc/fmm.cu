@@ -367,6 +367,152 @@ __global__ void __launch_bounds__(128) translate_kernel(int level, const T* __re
     }
 }
 
+// ------------------------------------------------------------------------- small levels
+// Levels with few boxes are latency-bound in the tiled kernel (each block walks all
+// 28 K-steps).  Here one block takes one target box: warp w handles K-steps w, w+8,
+// ..., lanes own outputs p, the source row is broadcast by shuffles, the operator row
+// is read from L1/L2, and the warps' partial sums meet in shared memory.
+constexpr int kBoxWarps = 8;
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(kBoxWarps * 32) m2l_box_kernel(int level, const T* __restrict__ q,
+                                                                 const T* __restrict__ u_par,
+                                                                 const T* __restrict__ ops,
+                                                                 const T* __restrict__ l2l,
+                                                                 const T* __restrict__ mono,
+                                                                 const typename Mono<T>::V* __restrict__ Qin,
+                                                                 const typename Mono<T>::V* __restrict__ Cpar,
+                                                                 T* __restrict__ out,
+                                                                 typename Mono<T>::V* __restrict__ Cout) {
+    using M = Mono<T>;
+    using V = typename M::V;
+    constexpr int PL = NP / 32;
+    __shared__ T part[kBoxWarps][NP];
+    __shared__ int s_off[27][3];
+    const uint32_t box = blockIdx.x;
+    uint32_t x, y;
+    unmorton2(box, x, y);
+    const int px = x & 1, py = y & 1, cls = px + 2 * py;
+    const int side = 1 << level;
+    const bool has_l2l = u_par != nullptr;
+    const int n_steps = 27 + (has_l2l ? 1 : 0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        int nn = 0;
+        for (int d = 0; d < 36; ++d) {
+            const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            s_off[nn][0] = dx;
+            s_off[nn][1] = dy;
+            s_off[nn][2] = offset_index(dx, dy);
+            ++nn;
+        }
+    }
+    __syncthreads();
+    T acc[PL];
+#pragma unroll
+    for (int i = 0; i < PL; ++i) acc[i] = T(0);
+    for (int st = warp; st < n_steps; st += kBoxWarps) {
+        const T* src;
+        const T* op;
+        if (st < 27) {
+            const int sx = (int)x + s_off[st][0], sy = (int)y + s_off[st][1];
+            if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
+            src = q + (size_t)morton2(sx, sy) * NP;
+            op = ops + (size_t)s_off[st][2] * NP * NP;
+        } else {
+            src = u_par + (size_t)(box >> 2) * NP;
+            op = l2l + (size_t)cls * NP * NP;
+        }
+        T xv[PL];
+#pragma unroll
+        for (int i = 0; i < PL; ++i) xv[i] = src[lane + 32 * i];
+#pragma unroll
+        for (int c = 0; c < PL; ++c) {
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                const T v = shfl(xv[c], l);
+                const T* row = op + (size_t)(32 * c + l) * NP;
+#pragma unroll
+                for (int i = 0; i < PL; ++i) acc[i] = fma(__ldg(row + lane + 32 * i), v, acc[i]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PL; ++i) part[warp][lane + 32 * i] = acc[i];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < PL; ++i) {
+            T v = T(0);
+#pragma unroll
+            for (int w = 0; w < kBoxWarps; ++w) v += part[w][lane + 32 * i];
+            out[(size_t)box * NP + lane + 32 * i] = v;
+        }
+    } else if (warp == 1) {
+        // incoming constant: C_parent + sum over the list of c_o Q_sigma
+        V sacc = M::zero();
+        if (lane < 27) {
+            const int sx = (int)x + s_off[lane][0], sy = (int)y + s_off[lane][1];
+            if (sx >= 0 && sx < side && sy >= 0 && sy < side) {
+                const int o = s_off[lane][2];
+                sacc = M::mul(M::make(mono[o], mono[kNumOffsets + o]), Qin[morton2(sx, sy)]);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) sacc = M::add(sacc, shfl_xor_v(sacc, off));
+        if (lane == 0) Cout[box] = has_l2l ? M::add(Cpar[box >> 2], sacc) : sacc;
+    }
+}
+
+// M2M with one warp per parent: lanes own outputs, children's expansions broadcast by
+// shuffles, the operator [4NP][NP] staged in shared memory when it fits (else L1/L2).
+template <typename T, int NP, bool SMEM_OP>
+__global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __restrict__ qc,
+                                                       const T* __restrict__ m2m,
+                                                       const typename Mono<T>::V* __restrict__ Qin,
+                                                       T* __restrict__ qp,
+                                                       typename Mono<T>::V* __restrict__ Qout) {
+    using M = Mono<T>;
+    constexpr int CL = 4 * NP / 32, PL = NP / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sop = reinterpret_cast<T*>(smem_raw);
+    if (SMEM_OP) {
+        for (int i = threadIdx.x; i < 4 * NP * NP; i += blockDim.x) sop[i] = m2m[i];
+        __syncthreads();
+    }
+    const T* op = SMEM_OP ? sop : m2m;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_parent = (int64_t)1 << (2 * level);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t par = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; par < n_parent; par += nw) {
+        T xv[CL];
+#pragma unroll
+        for (int c = 0; c < CL; ++c) xv[c] = qc[(size_t)par * 4 * NP + lane + 32 * c];
+        T acc[PL];
+#pragma unroll
+        for (int i = 0; i < PL; ++i) acc[i] = T(0);
+#pragma unroll
+        for (int c = 0; c < CL; ++c) {
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                const T v = shfl(xv[c], l);
+                const T* row = op + (size_t)(32 * c + l) * NP;
+#pragma unroll
+                for (int i = 0; i < PL; ++i) acc[i] = fma(row[lane + 32 * i], v, acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < PL; ++i) qp[(size_t)par * NP + lane + 32 * i] = acc[i];
+        if (lane < 4) {
+            typename M::V qv = Qin[4 * par + lane];
+            qv = M::add(qv, shfl_xor_v(qv, 1));
+            qv = M::add(qv, shfl_xor_v(qv, 2));
+            if (lane == 0) Qout[par] = qv;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------- P2P + L2P
 // One warp per target leaf (row-major).  The sources of the leaf's 3x3 neighbourhood
 // (three contiguous ranges) are staged in shared memory as (table offset, charge).
@@ -395,7 +541,7 @@ struct alignas(16) SrcEntry<double> {
 };
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
+__global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(
     int L, int side, const int32_t* __restrict__ sbeg, const int32_t* __restrict__ sloc,
     const int32_t* __restrict__ tbeg, const int32_t* __restrict__ tloc,
     const int32_t* __restrict__ tperm, const T* __restrict__ f_sorted, const T* __restrict__ table,
@@ -549,6 +695,197 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_l2p_kernel(
     }
 }
 
+// Strip variant (the normal case).  A block takes a strip of SW consecutive leaves
+// of one leaf row.  Their 3x3 neighbourhoods lie in three contiguous source ranges
+// (rows by-1, by, by+1, columns bx0-1 .. bx0+SW), which are staged once with
+// coalesced loads; each staged source gets its table offset relative to the strip's
+// first leaf, so a target in leaf bx reads phi through a pointer shifted by
+// (bx - bx0) * s and the pair loop stays one load and one multiply-add per pair.
+// Targets, leaf charges, incoming expansions and constants of the strip are staged
+// alongside.  The host picks SW so the staged data fit (3 (SW+2) max_leaf_src <= CAPS).
+template <typename T>
+struct StripCfg {
+    static constexpr int WARPS = 8;
+    static constexpr int CAPS = sizeof(T) == 4 ? 4096 : 2048;  // staged sources
+    static constexpr int CAPT = 2048;                          // staged targets
+    static constexpr int MAXSW = 32;
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
+    int L, int side, int SW, const int32_t* __restrict__ sbeg, const int32_t* __restrict__ sloc,
+    const int32_t* __restrict__ tbeg, const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
+    const T* __restrict__ f_sorted, const T* __restrict__ table, int tab_H, int tab_W,
+    const T* __restrict__ uhat, const typename Mono<T>::V* __restrict__ Cleaf,
+    const typename Mono<T>::V* __restrict__ Qleaf, const T* __restrict__ tofsT, double* __restrict__ u,
+    double* __restrict__ u_near, double* __restrict__ u_far) {
+    using M = Mono<T>;
+    using V = typename M::V;
+    using Cfg = StripCfg<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tab_n = (2 * tab_H + 1) * tab_W;
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    SrcEntry<T>* s_src = reinterpret_cast<SrcEntry<T>*>(tab + tab_n);
+    T* s_uhat = reinterpret_cast<T*>(s_src + Cfg::CAPS);                 // [MAXSW][NP]
+    V* s_q = reinterpret_cast<V*>(s_uhat + Cfg::MAXSW * NP);             // [3][MAXSW+2]
+    V* s_c = s_q + 3 * (Cfg::MAXSW + 2);                                 // [MAXSW]
+    int* s_tloc = reinterpret_cast<int*>(s_c + Cfg::MAXSW);              // [CAPT]
+    int* s_tperm = s_tloc + Cfg::CAPT;                                   // [CAPT]
+    int* s_sb = s_tperm + Cfg::CAPT;                                     // [3][MAXSW+3]
+    int* s_tb = s_sb + 3 * (Cfg::MAXSW + 3);                             // [MAXSW+1]
+    __shared__ int s_rs[4], s_clo, s_chi;
+
+    for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
+    const T* tab_c = tab + (tab_H + tab_H * tab_W);
+    const int n = 1 << L;
+    const int n_seg = (n + SW - 1) / SW;
+    const int64_t n_strips = (int64_t)n * n_seg;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int64_t strip = blockIdx.x; strip < n_strips; strip += gridDim.x) {
+        const int by = (int)(strip / n_seg);
+        const int bx0 = (int)(strip % n_seg) * SW;
+        const int bx1 = min(bx0 + SW, n);  // exclusive
+        const int c_lo = max(bx0 - 1, 0), c_hi = min(bx1, n - 1);
+        const int ncol = c_hi - c_lo + 1;
+        __syncthreads();  // previous strip done with the staging buffers
+        // leaf boundaries of the three source rows and the target row, leaf data
+        for (int i = threadIdx.x; i < 3 * (ncol + 1); i += blockDim.x) {
+            const int r = i / (ncol + 1), c = i % (ncol + 1);
+            const int yy = by + r - 1;
+            s_sb[r * (Cfg::MAXSW + 3) + c] = (yy >= 0 && yy < n) ? sbeg[(int64_t)yy * n + c_lo + c] : 0;
+        }
+        for (int i = threadIdx.x; i <= bx1 - bx0; i += blockDim.x) s_tb[i] = tbeg[(int64_t)by * n + bx0 + i];
+        for (int i = threadIdx.x; i < 3 * ncol; i += blockDim.x) {
+            const int r = i / ncol, c = i % ncol;
+            const int yy = by + r - 1;
+            s_q[r * (Cfg::MAXSW + 2) + c] = (yy >= 0 && yy < n) ? Qleaf[morton2(c_lo + c, yy)] : M::zero();
+        }
+        for (int i = threadIdx.x; i < (bx1 - bx0) * NP; i += blockDim.x) {
+            const int c = i / NP, pp = i % NP;
+            s_uhat[i] = uhat ? uhat[(size_t)morton2(bx0 + c, by) * NP + pp] : T(0);
+        }
+        for (int i = threadIdx.x; i < bx1 - bx0; i += blockDim.x)
+            s_c[i] = Cleaf ? Cleaf[morton2(bx0 + i, by)] : M::zero();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int r = 0; r < 3; ++r) {
+                s_rs[r] = acc;
+                acc += s_sb[r * (Cfg::MAXSW + 3) + ncol] - s_sb[r * (Cfg::MAXSW + 3)];
+            }
+            s_rs[3] = acc;
+        }
+        __syncthreads();
+        const int ns_strip = s_rs[3];
+        // sources: coalesced copy + strip-relative table offset
+        for (int v = threadIdx.x; v < ns_strip; v += blockDim.x) {
+            const int r = (v >= s_rs[1]) + (v >= s_rs[2]);
+            const int* sb = s_sb + r * (Cfg::MAXSW + 3);
+            const int j = sb[0] + (v - s_rs[r]);
+            int lo = 0, hi = ncol;  // find leaf column c with sb[c] <= j < sb[c+1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sb[mid] <= j) lo = mid;
+                else hi = mid;
+            }
+            const int l = sloc[j];
+            SrcEntry<T> e;
+            e.off = (c_lo + lo - bx0) * side + (l & 0xffff) + tab_W * ((r - 1) * side + (l >> 16));
+            e.f = f_sorted[j];
+            s_src[v] = e;
+        }
+        const int tb0 = s_tb[0], nt_strip = s_tb[bx1 - bx0] - tb0;
+        for (int v = threadIdx.x; v < nt_strip; v += blockDim.x) {
+            s_tloc[v] = tloc[tb0 + v];
+            s_tperm[v] = tperm[tb0 + v];
+        }
+        __syncthreads();
+
+        for (int bx = bx0 + warp; bx < bx1; bx += Cfg::WARPS) {
+            const int li = bx - bx0;
+            const int tb = s_tb[li] - tb0, te = s_tb[li + 1] - tb0;
+            if (tb == te) continue;
+            // three staged source ranges (columns bx-1 .. bx+1 of each row)
+            const int ca = max(bx - 1, 0) - c_lo, cb = min(bx + 1, n - 1) - c_lo + 1;
+            int ra[3], rlen[3];
+            V qn = M::zero();
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int* sb = s_sb + r * (Cfg::MAXSW + 3);
+                ra[r] = s_rs[r] + (sb[ca] - sb[0]);
+                rlen[r] = sb[cb] - sb[ca];
+                for (int c = ca; c < cb; ++c) qn = M::add(qn, s_q[r * (Cfg::MAXSW + 2) + c]);
+            }
+            const double near_const = M::to_double(M::mul(phi0, qn));
+            const V cl = s_c[li];
+            const T* uh = s_uhat + li * NP;
+            const int shift = li * side;
+            for (int t0 = tb; t0 < te; t0 += 32) {
+                const int nt = min(32, te - t0);
+                const int G = 32 / nt;
+                const int t = lane % nt, g = lane / nt;
+                const bool active = g < G;
+                const int tl = s_tloc[t0 + t];
+                const int tx = tl & 0xffff, ty = tl >> 16;
+                const T* tp = tab_c + (tx + tab_W * ty + shift);
+                T acc = T(0), cmp = T(0);
+                auto add = [&](T term) {
+                    if constexpr (sizeof(T) == 4) {
+                        const T y = term - cmp;
+                        const T s2 = acc + y;
+                        cmp = (s2 - acc) - y;
+                        acc = s2;
+                    } else {
+                        acc += term;
+                    }
+                };
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        const SrcEntry<T>* src = s_src + ra[r];
+                        const int len = rlen[r];
+                        int j = g;
+                        for (; j + G < len; j += 2 * G) {
+                            const SrcEntry<T> e0 = src[j], e1 = src[j + G];
+                            const T p0 = tp[-e0.off] * e0.f;
+                            const T p1 = tp[-e1.off] * e1.f;
+                            add(p0);
+                            add(p1);
+                        }
+                        if (j < len) {
+                            const SrcEntry<T> e0 = src[j];
+                            add(tp[-e0.off] * e0.f);
+                        }
+                    }
+                }
+                acc -= cmp;
+                cmp = T(0);
+                for (int k = 1; k < G; ++k) {
+                    const T v = shfl(acc, t + k * nt);
+                    if (g == 0) add(v);
+                }
+                acc -= cmp;
+                if (lane < nt) {
+                    T far = T(0);
+                    if (uhat) {
+                        const T* row = tofsT + (size_t)(tx + side * ty) * NP;
+#pragma unroll 8
+                        for (int pp = 0; pp < NP; ++pp) far = fma(__ldg(row + pp), uh[pp], far);
+                    }
+                    const int dst = s_tperm[t0 + lane];
+                    const double dn = (double)acc + near_const;
+                    const double df = (double)far + M::to_double(cl);
+                    if (u) u[dst] = dn + df;
+                    if (u_near) u_near[dst] = dn;
+                    if (u_far) u_far[dst] = df;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------- launchers
@@ -590,19 +927,61 @@ static cudaError_t launch_translate(int level, const T* q, const T* u_par, const
     return cudaGetLastError();
 }
 
+template <typename T, int NP>
+static cudaError_t launch_m2m_warp(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
+                                   T* q_parent, void* Q_parent, cudaStream_t s) {
+    using V = typename Mono<T>::V;
+    const int64_t n_par = (int64_t)1 << (2 * level);
+    int64_t blocks = (n_par * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    constexpr size_t op_bytes = (size_t)4 * NP * NP * sizeof(T);
+    if constexpr (op_bytes <= 64 * 1024) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(m2m_warp_kernel<T, NP, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op_bytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        m2m_warp_kernel<T, NP, true><<<(int)blocks, 256, op_bytes, s>>>(level, q_child, (const T*)ops.m2m[k],
+                                                                         (const V*)Q_child, q_parent, (V*)Q_parent);
+    } else {
+        m2m_warp_kernel<T, NP, false><<<(int)blocks, 256, 0, s>>>(level, q_child, (const T*)ops.m2m[k],
+                                                                   (const V*)Q_child, q_parent, (V*)Q_parent);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
                        T* q_parent, void* Q_parent, cudaStream_t s) {
-    if (ops.NP == 32)
-        return launch_translate<T, 32, kModeM2M>(level, q_child, nullptr, (const T*)ops.m2m[k], nullptr, nullptr,
-                                                 Q_child, nullptr, q_parent, Q_parent, nullptr, s);
-    return launch_translate<T, 64, kModeM2M>(level, q_child, nullptr, (const T*)ops.m2m[k], nullptr, nullptr,
-                                             Q_child, nullptr, q_parent, Q_parent, nullptr, s);
+    if (ops.NP == 32) return launch_m2m_warp<T, 32>(ops, k, level, q_child, Q_child, q_parent, Q_parent, s);
+    return launch_m2m_warp<T, 64>(ops, k, level, q_child, Q_child, q_parent, Q_parent, s);
+}
+
+// Levels up to this size use the box-per-block M2L kernel, larger ones the tiled kernel.
+constexpr int kM2LBoxMaxLevel = 7;
+
+template <typename T, int NP>
+static cudaError_t launch_m2l_box(const DeviceOps& ops, int k, int level, const T* q, const void* Qin,
+                                  const T* u_par, const void* Cpar, T* out, void* Cout, cudaStream_t s) {
+    using V = typename Mono<T>::V;
+    const T* l2l = u_par ? (const T*)ops.l2l[k + 1] : nullptr;
+    const unsigned boxes = 1u << (2 * level);
+    m2l_box_kernel<T, NP><<<boxes, kBoxWarps * 32, 0, s>>>(level, q, u_par, (const T*)ops.tifo[k], l2l,
+                                                           (const T*)ops.mono[k], (const V*)Qin, (const V*)Cpar,
+                                                           out, (V*)Cout);
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
                        const T* u_parent, const void* C_parent, T* u_level, void* C_level, cudaStream_t s) {
+    if (level <= kM2LBoxMaxLevel) {
+        if (ops.NP == 32)
+            return launch_m2l_box<T, 32>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
+        return launch_m2l_box<T, 64>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
+    }
     const T* l2l = u_parent ? (const T*)ops.l2l[k + 1] : nullptr;
     if (ops.NP == 32)
         return launch_translate<T, 32, kModeM2L>(level, q_level, u_parent, (const T*)ops.tifo[k], l2l,
@@ -624,14 +1003,14 @@ static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const 
     static int per_sm_cached = 0;
     static size_t per_sm_for = 0;
     if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(p2p_l2p_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(p2p_leaf_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr_bytes = smem;
     }
     if (per_sm_for != smem) {
         int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_l2p_kernel<T, NP>, kP2PWarps * 32, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_leaf_kernel<T, NP>, kP2PWarps * 32, smem);
         per_sm_cached = per_sm < 1 ? 1 : per_sm;
         per_sm_for = smem;
     }
@@ -640,9 +1019,45 @@ static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const 
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     using V = typename Mono<T>::V;
-    p2p_l2p_kernel<T, NP><<<(int)blocks, kP2PWarps * 32, smem, s>>>(
+    p2p_leaf_kernel<T, NP><<<(int)blocks, kP2PWarps * 32, smem, s>>>(
         t.L, t.side, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted, (const T*)ops.p2p_table,
         ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const V*)Qleaf, (const T*)ops.tofsT, u, un, uf);
+    return cudaGetLastError();
+}
+
+template <typename T, int NP>
+static cudaError_t launch_p2p_strip(const TreeView& t, const DeviceOps& ops, int SW, const T* f_sorted,
+                                    const T* uhat, const void* Cleaf, const void* Qleaf, double* u, double* un,
+                                    double* uf, int num_sms, cudaStream_t s) {
+    using Cfg = StripCfg<T>;
+    using V = typename Mono<T>::V;
+    const size_t tab_bytes = (size_t)(2 * ops.tab_H + 1) * ops.tab_W * sizeof(T);
+    const size_t smem = tab_bytes + (size_t)Cfg::CAPS * sizeof(SrcEntry<T>) + (size_t)Cfg::MAXSW * NP * sizeof(T) +
+                        (size_t)(3 * (Cfg::MAXSW + 2) + Cfg::MAXSW) * sizeof(V) + (size_t)2 * Cfg::CAPT * sizeof(int) +
+                        (size_t)(3 * (Cfg::MAXSW + 3) + Cfg::MAXSW + 1) * sizeof(int);
+    static size_t attr_bytes = 0;
+    static int per_sm_cached = 0;
+    static size_t per_sm_for = 0;
+    if (smem > attr_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(p2p_strip_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_bytes = smem;
+    }
+    if (per_sm_for != smem) {
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_strip_kernel<T, NP>, Cfg::WARPS * 32, smem);
+        per_sm_cached = per_sm < 1 ? 1 : per_sm;
+        per_sm_for = smem;
+    }
+    const int n = 1 << t.L;
+    const int64_t strips = (int64_t)n * ((n + SW - 1) / SW);
+    int64_t blocks = std::min<int64_t>(strips, (int64_t)num_sms * per_sm_cached);
+    if (blocks < 1) blocks = 1;
+    p2p_strip_kernel<T, NP><<<(int)blocks, Cfg::WARPS * 32, smem, s>>>(
+        t.L, t.side, SW, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted,
+        (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const V*)Qleaf, (const T*)ops.tofsT,
+        u, un, uf);
     return cudaGetLastError();
 }
 
@@ -650,6 +1065,14 @@ template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted, const T* uhat,
                            const void* Cleaf, const void* Qleaf, double* u, double* un, double* uf, int num_sms,
                            cudaStream_t s) {
+    using Cfg = StripCfg<T>;
+    const int n = 1 << t.L;
+    const int ms = std::max(1, t.max_leaf_src), mt = std::max(1, t.max_leaf_tgt);
+    int SW = std::min({Cfg::MAXSW, Cfg::CAPS / (3 * ms) - 2, Cfg::CAPT / mt, n});
+    if (SW >= 1) {
+        if (ops.NP == 32) return launch_p2p_strip<T, 32>(t, ops, SW, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
+        return launch_p2p_strip<T, 64>(t, ops, SW, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
+    }
     if (ops.NP == 32) return launch_p2p_np<T, 32>(t, ops, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
     return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
 }

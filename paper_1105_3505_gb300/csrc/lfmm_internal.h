@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <array>
 #include <memory>
 #include <mutex>
@@ -150,6 +151,8 @@ struct TreeView {
     const int32_t* src_perm = nullptr;   // caller index of each sorted source
     const int32_t* tgt_loc = nullptr;
     const int32_t* tgt_perm = nullptr;
+    int max_leaf_src = 0;      // largest leaf occupancies (size the P2P staging)
+    int max_leaf_tgt = 0;
 };
 
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);

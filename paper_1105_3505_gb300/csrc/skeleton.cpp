@@ -368,7 +368,10 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
     d->n_levels = nl;
     d->leaf_side = mo->leaf_side;
     d->tab_H = 2 * mo->leaf_side - 1;
-    d->tab_W = 4 * mo->leaf_side;
+    // row width: at least 2H+1, and 16 mod 32 so that targets in the same column but in
+    // rows of different parity fall in different shared-memory banks
+    d->tab_W = 16;
+    while (d->tab_W < 2 * d->tab_H + 1) d->tab_W += 32;
     size_t off_tofs, off_tab;
     std::vector<size_t> om, ol, ot, omono;
     std::vector<char> bytes;

@@ -25,8 +25,10 @@ __device__ __forceinline__ int warp_max(int v) {
 }
 
 // out4 = {min x, min y, max x, max y} over both point sets; out4 preset by the host.
+// Warp and block reductions first: one set of atomics per block.
 __global__ void bbox_kernel(const int2* __restrict__ a, int64_t na, const int2* __restrict__ b,
                             int64_t nb, int* __restrict__ out4) {
+    __shared__ int sh[4][kThreads / 32];
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
     const int64_t n = na + nb;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -41,11 +43,26 @@ __global__ void bbox_kernel(const int2* __restrict__ a, int64_t na, const int2* 
     mny = warp_min(mny);
     mxx = warp_max(mxx);
     mxy = warp_max(mxy);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(out4 + 0, mnx);
-        atomicMin(out4 + 1, mny);
-        atomicMax(out4 + 2, mxx);
-        atomicMax(out4 + 3, mxy);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = mnx;
+        sh[1][wid] = mny;
+        sh[2][wid] = mxx;
+        sh[3][wid] = mxy;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const bool ok = lane < kThreads / 32;
+        mnx = warp_min(ok ? sh[0][lane] : INT_MAX);
+        mny = warp_min(ok ? sh[1][lane] : INT_MAX);
+        mxx = warp_max(ok ? sh[2][lane] : INT_MIN);
+        mxy = warp_max(ok ? sh[3][lane] : INT_MIN);
+        if (lane == 0) {
+            atomicMin(out4 + 0, mnx);
+            atomicMin(out4 + 1, mny);
+            atomicMax(out4 + 2, mxx);
+            atomicMax(out4 + 3, mxy);
+        }
     }
 }
 
@@ -225,7 +242,7 @@ cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s) {
 
 cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
                         cudaStream_t s) {
-    bbox_kernel<<<grid_for(na + nb, kThreads), kThreads, 0, s>>>((const int2*)a, na,
+    bbox_kernel<<<grid_for((na + nb + 7) / 8, kThreads, 152 * 8), kThreads, 0, s>>>((const int2*)a, na,
                                                                 (const int2*)b, nb, out4);
     return cudaGetLastError();
 }
