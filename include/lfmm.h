@@ -66,11 +66,13 @@ typedef struct lfmm_opts {
     int32_t max_leaf_side;    /* largest leaf side in lattice cells, a power of 2 in [1, 32]   */
     int32_t proxies_per_edge; /* proxy points per edge of the proxy ring of Sec. 5 (>= 8);     */
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
-    int32_t reserved[3];      /* must be zero                                                 */
+    int32_t tc_min_level;     /* mixed path, P <= 32: tree levels >= this run M2L on the      */
+                              /* tensor cores (0 = default 8; a value > 30 disables them)     */
+    int32_t reserved[2];      /* must be zero                                                 */
 } lfmm_opts;
 
 /* Fill opts with the defaults: LFMM_MIXED, p = 8, leaf_size = 64, max_leaf_side = 32,
- * proxies_per_edge = 64. */
+ * proxies_per_edge = 64, tc_min_level = 0. */
 void lfmm_opts_default(lfmm_opts* opts);
 
 /* Build a plan for fixed source and target locations (Sec. 8.1 precomputation):
@@ -101,6 +103,11 @@ int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_
 
 /* Release a plan (NULL is a no-op).  Waits for the plan's outstanding work. */
 int lfmm_plan_destroy(lfmm_plan* plan);
+
+/* Synchronise `stream` and report device-side failures of the plan's kernels since the
+ * last call: LFMM_ETIMEOUT if a bounded wait inside a kernel gave up (the affected
+ * results are not valid), else LFMM_OK.  Clears the status. */
+int lfmm_plan_status(lfmm_plan* plan, void* stream);
 
 typedef struct lfmm_plan_info {
     int64_t n_src, n_tgt;

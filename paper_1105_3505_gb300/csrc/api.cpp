@@ -47,6 +47,8 @@ struct lfmm_plan {
     void* Qbox = nullptr;          // per-box total charge (8 B per box)
     void* Cbox = nullptr;          // per-box incoming constant (8 B per box)
     std::vector<int64_t> lvl_off;  // offset (boxes) of level l inside qhat / uhat
+    int* status = nullptr;         // device status word written by kernels (LFMM_ETIMEOUT)
+    int tc_min_level = 8;
     double* f_stage = nullptr;     // device copy of a host f
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
 };
@@ -125,6 +127,7 @@ int validate_opts(const lfmm_opts& o) {
         return fail(LFMM_EINVAL, "opts.max_leaf_side must be a power of 2 in [1, 32]");
     if (o.proxies_per_edge < 8 || o.proxies_per_edge > 1024)
         return fail(LFMM_EINVAL, "opts.proxies_per_edge must be in [8, 1024]");
+    if (o.tc_min_level < 0) return fail(LFMM_EINVAL, "opts.tc_min_level must be >= 0");
     for (int r : o.reserved)
         if (r != 0) return fail(LFMM_EINVAL, "opts.reserved must be zero");
     return LFMM_OK;
@@ -289,6 +292,11 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
     if ((st = palloc(p, &p->Cbox, (size_t)boxes * 8, s))) return st;
+    void* stbuf;
+    if ((st = palloc(p, &stbuf, 16, s))) return st;
+    p->status = (int*)stbuf;
+    LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+    p->tc_min_level = p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level;
     LFMM_CUDA_TRY(cudaStreamSynchronize(s));
     return LFMM_OK;
 }
@@ -332,7 +340,8 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         PhaseTimer pt(LFMM_PHASE_M2L, s);
         for (int l = 2; l <= L; ++l) {
             LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
-                                        l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), s));
+                                        l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), p->tc_min_level,
+                                        p->status, s));
             pt.add_launches(1);
         }
     }
@@ -455,6 +464,19 @@ int lfmm_plan_destroy(lfmm_plan* plan) {
     cudaError_t e = cudaStreamSynchronize(plan->last_stream);
     delete plan;
     if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("plan destroy: ") + cudaGetErrorString(e));
+    return LFMM_OK;
+}
+
+int lfmm_plan_status(lfmm_plan* p, void* stream) {
+    if (!p) return fail(LFMM_EINVAL, "NULL plan");
+    int h = 0;
+    LFMM_CUDA_TRY(cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    LFMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h != LFMM_OK) {
+        LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), (cudaStream_t)stream));
+        LFMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        return fail(h, "a bounded device-side wait gave up; results of the affected evaluation are invalid");
+    }
     return LFMM_OK;
 }
 

@@ -369,30 +369,34 @@ __global__ void __launch_bounds__(128) translate_kernel(int level, const T* __re
 
 // ------------------------------------------------------------------------- small levels
 // Levels with few boxes are latency-bound in the tiled kernel (each block walks all
-// 28 K-steps).  Here one block takes one target box: warp w handles K-steps w, w+8,
-// ..., lanes own outputs p, the source row is broadcast by shuffles, the operator row
-// is read from L1/L2, and the warps' partial sums meet in shared memory.
-constexpr int kBoxWarps = 8;
+// 28 K-steps in sequence).  Here a block takes 32 target boxes of one parity class and
+// splits the K-steps over its 8 warps (warp w: steps w, w+8, ...).  Per step a warp
+// stages the 32 x 32 operator block in its own shared memory, each lane takes one box
+// (its source row in registers) and 32 outputs, so every operator value loaded is used
+// by 32 boxes; the 8 warps' partial sums are added in shared memory.
+constexpr int kSkWarps = 8;
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(kBoxWarps * 32) m2l_box_kernel(int level, const T* __restrict__ q,
-                                                                 const T* __restrict__ u_par,
-                                                                 const T* __restrict__ ops,
-                                                                 const T* __restrict__ l2l,
-                                                                 const T* __restrict__ mono,
-                                                                 const typename Mono<T>::V* __restrict__ Qin,
-                                                                 const typename Mono<T>::V* __restrict__ Cpar,
-                                                                 T* __restrict__ out,
-                                                                 typename Mono<T>::V* __restrict__ Cout) {
+__global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, const T* __restrict__ q,
+                                                                   const T* __restrict__ u_par,
+                                                                   const T* __restrict__ ops,
+                                                                   const T* __restrict__ l2l,
+                                                                   const T* __restrict__ mono,
+                                                                   const typename Mono<T>::V* __restrict__ Qin,
+                                                                   const typename Mono<T>::V* __restrict__ Cpar,
+                                                                   T* __restrict__ out,
+                                                                   typename Mono<T>::V* __restrict__ Cout) {
     using M = Mono<T>;
     using V = typename M::V;
-    constexpr int PL = NP / 32;
-    __shared__ T part[kBoxWarps][NP];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sop = reinterpret_cast<T*>(smem_raw);            // [warps][NP][32] operator slice
+    T* red = sop + kSkWarps * NP * 32;                  // [warps][32 boxes][33]
     __shared__ int s_off[27][3];
-    const uint32_t box = blockIdx.x;
-    uint32_t x, y;
-    unmorton2(box, x, y);
-    const int px = x & 1, py = y & 1, cls = px + 2 * py;
+    const int cls = blockIdx.y;
+    const int px = cls & 1, py = cls >> 1;
+    const int lg = level - 1;
+    const int np_side = 1 << lg;
+    const int64_t n_rows = (int64_t)1 << (2 * lg);
     const int side = 1 << level;
     const bool has_l2l = u_par != nullptr;
     const int n_steps = 27 + (has_l2l ? 1 : 0);
@@ -409,59 +413,70 @@ __global__ void __launch_bounds__(kBoxWarps * 32) m2l_box_kernel(int level, cons
         }
     }
     __syncthreads();
-    T acc[PL];
+    const int64_t row = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = row < n_rows;
+    const int ri = valid ? (int)(row & (np_side - 1)) : 0, rj = valid ? (int)(row >> lg) : 0;
+    T* my_op = sop + warp * NP * 32;
+    for (int half = 0; half < NP / 32; ++half) {  // 32 outputs per pass
+        T acc[32];
 #pragma unroll
-    for (int i = 0; i < PL; ++i) acc[i] = T(0);
-    for (int st = warp; st < n_steps; st += kBoxWarps) {
-        const T* src;
-        const T* op;
-        if (st < 27) {
-            const int sx = (int)x + s_off[st][0], sy = (int)y + s_off[st][1];
-            if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
-            src = q + (size_t)morton2(sx, sy) * NP;
-            op = ops + (size_t)s_off[st][2] * NP * NP;
-        } else {
-            src = u_par + (size_t)(box >> 2) * NP;
-            op = l2l + (size_t)cls * NP * NP;
-        }
-        T xv[PL];
+        for (int j = 0; j < 32; ++j) acc[j] = T(0);
+        for (int st = warp; st < n_steps; st += kSkWarps) {
+            const T* op;
+            const T* src = nullptr;
+            if (st < 27) {
+                op = ops + (size_t)s_off[st][2] * NP * NP;
+                const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
+                if (valid && sx >= 0 && sx < side && sy >= 0 && sy < side) src = q + (size_t)morton2(sx, sy) * NP;
+            } else {
+                op = l2l + (size_t)cls * NP * NP;
+                if (valid) src = u_par + (size_t)morton2(ri, rj) * NP;
+            }
+            // operator slice: my_op[k][j] = op[k][32*half + j]   (op is k-major [q][p])
+            __syncwarp();
+            for (int i = lane; i < NP * 32; i += 32) {
+                const int k = i >> 5, j = i & 31;
+                my_op[i] = op[(size_t)k * NP + 32 * half + j];
+            }
+            __syncwarp();
+            if (src) {
+#pragma unroll 4
+                for (int k = 0; k < NP; ++k) {
+                    const T a = src[k];
+                    const T* b = my_op + k * 32;
 #pragma unroll
-        for (int i = 0; i < PL; ++i) xv[i] = src[lane + 32 * i];
-#pragma unroll
-        for (int c = 0; c < PL; ++c) {
-#pragma unroll 8
-            for (int l = 0; l < 32; ++l) {
-                const T v = shfl(xv[c], l);
-                const T* row = op + (size_t)(32 * c + l) * NP;
-#pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(__ldg(row + lane + 32 * i), v, acc[i]);
+                    for (int j = 0; j < 32; ++j) acc[j] = fma(a, b[j], acc[j]);
+                }
             }
         }
-    }
+        // reduce the warps' partial sums
+        T* my_red = red + (size_t)warp * 32 * 33;
 #pragma unroll
-    for (int i = 0; i < PL; ++i) part[warp][lane + 32 * i] = acc[i];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int i = 0; i < PL; ++i) {
+        for (int j = 0; j < 32; ++j) my_red[lane * 33 + j] = acc[j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
+            const int b = i >> 5, j = i & 31;
             T v = T(0);
 #pragma unroll
-            for (int w = 0; w < kBoxWarps; ++w) v += part[w][lane + 32 * i];
-            out[(size_t)box * NP + lane + 32 * i] = v;
-        }
-    } else if (warp == 1) {
-        // incoming constant: C_parent + sum over the list of c_o Q_sigma
-        V sacc = M::zero();
-        if (lane < 27) {
-            const int sx = (int)x + s_off[lane][0], sy = (int)y + s_off[lane][1];
-            if (sx >= 0 && sx < side && sy >= 0 && sy < side) {
-                const int o = s_off[lane][2];
-                sacc = M::mul(M::make(mono[o], mono[kNumOffsets + o]), Qin[morton2(sx, sy)]);
+            for (int w = 0; w < kSkWarps; ++w) v += red[(size_t)w * 32 * 33 + b * 33 + j];
+            const int64_t r = (int64_t)blockIdx.x * 32 + b;
+            if (r < n_rows) {
+                const int ii = (int)(r & (np_side - 1)), jj = (int)(r >> lg);
+                out[(size_t)morton2(2 * ii + px, 2 * jj + py) * NP + 32 * half + j] = v;
             }
         }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) sacc = M::add(sacc, shfl_xor_v(sacc, off));
-        if (lane == 0) Cout[box] = has_l2l ? M::add(Cpar[box >> 2], sacc) : sacc;
+        __syncthreads();
+    }
+    // incoming constant (compensated), warp 0, one box per lane
+    if (warp == 0 && valid) {
+        V sacc = has_l2l ? Cpar[morton2(ri, rj)] : M::zero();
+        for (int st = 0; st < 27; ++st) {
+            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
+            if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
+            const int o = s_off[st][2];
+            sacc = M::add(sacc, M::mul(M::make(mono[o], mono[kNumOffsets + o]), Qin[morton2(sx, sy)]));
+        }
+        Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
     }
 }
 
@@ -504,12 +519,11 @@ __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __res
         }
 #pragma unroll
         for (int i = 0; i < PL; ++i) qp[(size_t)par * NP + lane + 32 * i] = acc[i];
-        if (lane < 4) {
-            typename M::V qv = Qin[4 * par + lane];
-            qv = M::add(qv, shfl_xor_v(qv, 1));
-            qv = M::add(qv, shfl_xor_v(qv, 2));
-            if (lane == 0) Qout[par] = qv;
-        }
+        // total charge of the parent: lanes 0..3 hold the children's, all lanes shuffle
+        typename M::V qv = lane < 4 ? Qin[4 * par + lane] : M::zero();
+        qv = M::add(qv, shfl_xor_v(qv, 1));
+        qv = M::add(qv, shfl_xor_v(qv, 2));
+        if (lane == 0) Qout[par] = qv;
     }
 }
 
@@ -932,8 +946,8 @@ static cudaError_t launch_m2m_warp(const DeviceOps& ops, int k, int level, const
                                    T* q_parent, void* Q_parent, cudaStream_t s) {
     using V = typename Mono<T>::V;
     const int64_t n_par = (int64_t)1 << (2 * level);
-    int64_t blocks = (n_par * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    int64_t blocks = (n_par + 7) / 8;  // 8 warps per block, grid-stride: one operator load per block
+    if (blocks > 152 * 2) blocks = 152 * 2;
     constexpr size_t op_bytes = (size_t)4 * NP * NP * sizeof(T);
     if constexpr (op_bytes <= 64 * 1024) {
         static bool attr = false;
@@ -959,28 +973,44 @@ cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child,
     return launch_m2m_warp<T, 64>(ops, k, level, q_child, Q_child, q_parent, Q_parent, s);
 }
 
-// Levels up to this size use the box-per-block M2L kernel, larger ones the tiled kernel.
-constexpr int kM2LBoxMaxLevel = 7;
-
 template <typename T, int NP>
-static cudaError_t launch_m2l_box(const DeviceOps& ops, int k, int level, const T* q, const void* Qin,
-                                  const T* u_par, const void* Cpar, T* out, void* Cout, cudaStream_t s) {
+static cudaError_t launch_m2l_splitk(const DeviceOps& ops, int k, int level, const T* q, const void* Qin,
+                                     const T* u_par, const void* Cpar, T* out, void* Cout, cudaStream_t s) {
     using V = typename Mono<T>::V;
     const T* l2l = u_par ? (const T*)ops.l2l[k + 1] : nullptr;
-    const unsigned boxes = 1u << (2 * level);
-    m2l_box_kernel<T, NP><<<boxes, kBoxWarps * 32, 0, s>>>(level, q, u_par, (const T*)ops.tifo[k], l2l,
-                                                           (const T*)ops.mono[k], (const V*)Qin, (const V*)Cpar,
-                                                           out, (V*)Cout);
+    const size_t smem = (size_t)kSkWarps * NP * 32 * sizeof(T) + (size_t)kSkWarps * 32 * 33 * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(m2l_splitk_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t rows = (int64_t)1 << (2 * (level - 1));
+    dim3 grid((unsigned)((rows + 31) / 32), 4);
+    m2l_splitk_kernel<T, NP><<<grid, kSkWarps * 32, smem, s>>>(level, q, u_par, (const T*)ops.tifo[k], l2l,
+                                                              (const T*)ops.mono[k], (const V*)Qin, (const V*)Cpar,
+                                                              out, (V*)Cout);
     return cudaGetLastError();
 }
 
+// Levels below this use the split-K kernel; larger ones the tensor-core kernel (mixed
+// path, P <= 32) or the tiled SIMT kernel.
+constexpr int kM2LSplitKMaxLevel = 7;
+
 template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
-                       const T* u_parent, const void* C_parent, T* u_level, void* C_level, cudaStream_t s) {
-    if (level <= kM2LBoxMaxLevel) {
+                       const T* u_parent, const void* C_parent, T* u_level, void* C_level, int tc_min_level,
+                       int* status, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (ops.NP == 32 && ops.tc.size() > (size_t)k && ops.tc[k] && level >= tc_min_level)
+            return launch_m2l_tc(ops, k, level, (const float*)q_level, Q_level, (const float*)u_parent, C_parent,
+                                 (float*)u_level, C_level, status, s);
+    }
+    if (level <= kM2LSplitKMaxLevel) {
         if (ops.NP == 32)
-            return launch_m2l_box<T, 32>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
-        return launch_m2l_box<T, 64>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
+            return launch_m2l_splitk<T, 32>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
+        return launch_m2l_splitk<T, 64>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
     }
     const T* l2l = u_parent ? (const T*)ops.l2l[k + 1] : nullptr;
     if (ops.NP == 32)
@@ -1083,7 +1113,7 @@ cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_s
     template cudaError_t launch_m2m<T>(const DeviceOps&, int, int, const T*, const void*, T*, void*,         \
                                        cudaStream_t);                                                         \
     template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const void*, const T*,          \
-                                       const void*, T*, void*, cudaStream_t);                                 \
+                                       const void*, T*, void*, int, int*, cudaStream_t);                      \
     template cudaError_t launch_p2p_l2p<T>(const TreeView&, const DeviceOps&, const T*, const T*, const void*, \
                                            const void*, double*, double*, double*, int, cudaStream_t);
 

@@ -115,6 +115,8 @@ struct DeviceOps {
     void* p2p_table = nullptr;
     std::vector<void*> m2m, l2l, tifo;    // per level k
     std::vector<void*> mono;              // per level k: deflation constants (hi[40], lo[40])
+    std::vector<void*> tc;                // per level k (mixed, NP = 32): tensor-core B tiles,
+                                          // [40 offsets + 4 L2L classes][hi, lo][32 x 32 fp32]
     std::vector<void*> retired;           // earlier, smaller uploads (kept alive)
 };
 
@@ -181,10 +183,15 @@ cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f,
 template <typename T>
 cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
                        T* q_parent, void* Q_parent, cudaStream_t s);
+// M2L + L2L of one level; mixed-path levels >= tc_min_level (P <= 32) run on the
+// tensor cores, which report a timed-out wait in *status.
 template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
                        const T* u_parent, const void* C_parent, T* u_level, void* C_level,
-                       cudaStream_t s);
+                       int tc_min_level, int* status, cudaStream_t s);
+cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level,
+                          const void* Q_level, const float* u_parent, const void* C_parent,
+                          float* u_level, void* C_level, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
                            const T* uhat_leaf, const void* C_leaf, const void* Q_leaf, double* u,

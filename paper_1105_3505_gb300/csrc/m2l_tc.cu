@@ -1,0 +1,378 @@
+// M2L (+ fused L2L) on the 5th-generation tensor cores, mixed path (Sec. 7, Sec. 8.2
+// steps 3-4): for the boxes tau of one parity class,
+//
+//   u_hat^tau = sum_{sigma in int(tau)} (T_ifo^o - c_o 1 1^T) q_hat^sigma + T_ifi^c u_hat^parent
+//
+// as an implicit GEMM per CTA: M = 128 target boxes (TMEM lanes), N = 32 outputs,
+// K = 27 x 32 gathered source expansions (+ 32 for the parent).  Operands are split
+// into TF32 hi + lo parts (round to nearest) and three products hi*hi + hi*lo + lo*hi
+// are accumulated in fp32 in TMEM (the lo*lo term is below 2^-22 relative).
+//
+//  - A (gathered expansions): each thread owns one box = one TMEM lane; it loads the
+//    source row for the current K-step, splits it and writes hi and lo with
+//    tcgen05.st into A columns of TMEM (the MMA reads A from tensor memory).
+//  - B (operators): pre-split, pre-swizzled 4 KB tiles in the device image, fetched
+//    with cp.async.bulk into shared memory, completion tracked by an mbarrier.
+//  - one elected thread issues 12 tcgen05.mma (K = 8 each) per K-step and commits
+//    them to a second mbarrier that frees the step's A/B buffers two steps later.
+//  - epilogue: tcgen05.ld of the 128 x 32 fp32 accumulator.
+// Every mbarrier wait is bounded (clock64 budget); on expiry the CTA records
+// LFMM_ETIMEOUT in the plan's status word, stops issuing work, waits (bounded) for
+// what it already issued, frees its TMEM and returns.
+#include "lfmm_internal.h"
+
+namespace lfmm {
+
+namespace {
+
+constexpr int kTcThreads = 128;          // 4 warps, one TMEM lane quarter each
+constexpr int kTcCols = 256;             // D [0,32), A stage s: hi [32+64s, 64+64s), lo [64+64s, 96+64s)
+constexpr long long kWaitBudget = 4000000000ll;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitBudget) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] x B[smem descriptor], kind::tf32, cta_group::1
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)0 << 16;                          // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: fp32 accumulate, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t tf32_rna_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ int offset_index_tc(int ox, int oy) {
+    const int raw = (oy + 3) * 7 + (ox + 3);
+    int inner_before;
+    if (oy < -1) inner_before = 0;
+    else if (oy > 1) inner_before = 9;
+    else inner_before = 3 * (oy + 1) + (ox > 1 ? 3 : 0);
+    return raw - inner_before;
+}
+
+struct DFv {
+    float hi, lo;
+};
+__device__ __forceinline__ DFv tsum(float a, float b) {
+    const float s = a + b, bp = s - a, ap = s - bp;
+    return {s, (a - ap) + (b - bp)};
+}
+__device__ __forceinline__ DFv qsum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ DFv dadd(DFv a, DFv b) {
+    DFv s = tsum(a.hi, b.hi), t = tsum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = qsum(s.hi, s.lo);
+    s.lo += t.lo;
+    return qsum(s.hi, s.lo);
+}
+__device__ __forceinline__ DFv dmul(DFv a, DFv b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return qsum(p, e);
+}
+
+__global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const float* __restrict__ q,
+                                                            const float* __restrict__ u_par,
+                                                            const float* __restrict__ tiles,
+                                                            const float* __restrict__ mono,
+                                                            const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar,
+                                                            float* __restrict__ out, DFv* __restrict__ Cout,
+                                                            int* __restrict__ status) {
+    constexpr int NP = 32;
+    __shared__ __align__(1024) float sB[2][2][1024];  // [stage][hi, lo][32 x 32 swizzled]
+    __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_off[27][3];
+    __shared__ int s_abort;
+
+    const int cls = blockIdx.y;
+    const int px = cls & 1, py = cls >> 1;
+    const int lg = level - 1;
+    const int np_side = 1 << lg;
+    const int64_t n_rows = (int64_t)1 << (2 * lg);
+    const int64_t row = (int64_t)blockIdx.x * kTcThreads + threadIdx.x;
+    const bool valid = row < n_rows;
+    const int side = 1 << level;
+    const bool has_l2l = u_par != nullptr;
+    const int n_steps = 27 + (has_l2l ? 1 : 0);
+    const int warp = threadIdx.x >> 5;
+    const int ri = valid ? (int)(row & (np_side - 1)) : 0;
+    const int rj = valid ? (int)(row >> lg) : 0;
+
+    // the swizzled B tiles need 1024-byte aligned shared memory; refuse to run otherwise
+    if (smem_u32(&sB[0][0][0]) & 1023u) {
+        if (threadIdx.x == 0) atomicExch(status, LFMM_EINTERNAL);
+        return;
+    }
+
+    if (threadIdx.x == 0) {
+        int nn = 0;
+        for (int d = 0; d < 36; ++d) {
+            const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            s_off[nn][0] = dx;
+            s_off[nn][1] = dy;
+            s_off[nn][2] = offset_index_tc(dx, dy);
+            ++nn;
+        }
+        mbar_init(&bar_b[0], 1);
+        mbar_init(&bar_b[1], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, kTcCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+
+    auto src_row = [&](int step) -> const float* {
+        if (!valid) return nullptr;
+        if (step < 27) {
+            const int sx = 2 * ri + px + s_off[step][0], sy = 2 * rj + py + s_off[step][1];
+            if (sx < 0 || sx >= side || sy < 0 || sy >= side) return nullptr;
+            return q + (size_t)morton2(sx, sy) * NP;
+        }
+        return u_par + (size_t)morton2(ri, rj) * NP;
+    };
+    auto load_row = [&](const float* r, float4 (&x)[8]) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            x[c] = r ? __ldg(reinterpret_cast<const float4*>(r) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+
+    constexpr uint32_t kIdesc = idesc_tf32(128, NP);
+    bool ok = true;
+    int issued_steps = 0, b_issued = 0;
+    float4 nxt[8];
+    load_row(src_row(0), nxt);
+    for (int step = 0; step < n_steps; ++step) {
+        const int buf = step & 1;
+        float4 cur[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
+        if (step + 1 < n_steps) load_row(src_row(step + 1), nxt);  // in flight during this step
+        if (step >= 2) {
+            if (!mbar_wait_bounded(&bar_mma[buf], ((step - 2) >> 1) & 1)) atomicExch(&s_abort, 1);
+            tc_fence_after();
+        }
+        __syncthreads();
+        if (s_abort) {
+            ok = false;
+            break;
+        }
+        // B tiles (hi, lo) for this step
+        if (threadIdx.x == 0) {
+            const float* src = step < 27 ? tiles + (size_t)s_off[step][2] * 2048
+                                         : tiles + (size_t)(kNumOffsets + cls) * 2048;
+            mbar_arrive_expect_tx(&bar_b[buf], 8192);
+            bulk_g2s(&sB[buf][0][0], src, 8192, &bar_b[buf]);
+            b_issued = step + 1;
+        }
+        // this thread's A row -> TMEM lane (hi, lo)
+        uint32_t hv[32], lv[32];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float xs[4] = {cur[c].x, cur[c].y, cur[c].z, cur[c].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t h = tf32_rna_bits(xs[e]);
+                hv[4 * c + e] = h;
+                lv[4 * c + e] = tf32_rna_bits(xs[e] - __uint_as_float(h));
+            }
+        }
+        const uint32_t a_hi = tmem + 32 + 64 * buf, a_lo = a_hi + 32;
+        tmem_st32(tmem + lane_base + 32 + 64 * buf, hv);
+        tmem_st32(tmem + lane_base + 64 + 64 * buf, lv);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            if (!mbar_wait_bounded(&bar_b[buf], (step >> 1) & 1)) {
+                atomicExch(&s_abort, 1);
+            } else {
+                const uint32_t b_hi = smem_u32(&sB[buf][0][0]), b_lo = smem_u32(&sB[buf][1][0]);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t dh = smem_desc_sw128(b_hi + 32 * kk), dl = smem_desc_sw128(b_lo + 32 * kk);
+                    mma_tf32_ts(tmem, a_hi + 8 * kk, dh, kIdesc, (step > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32_ts(tmem, a_hi + 8 * kk, dl, kIdesc, 1u);
+                    mma_tf32_ts(tmem, a_lo + 8 * kk, dh, kIdesc, 1u);
+                }
+                mma_commit(&bar_mma[buf]);
+            }
+        }
+        issued_steps = step + 1;
+    }
+
+    // scalar channel (compensated), one box per thread, while the last MMAs run
+    if (valid) {
+        DFv sacc = has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
+#pragma unroll 9
+        for (int st = 0; st < 27; ++st) {
+            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
+            if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
+            const int o = s_off[st][2];
+            sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, Qin[morton2(sx, sy)]));
+        }
+        Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
+    }
+
+    __syncthreads();
+    if (s_abort) ok = false;
+    // wait (bounded) for the last committed MMAs before reading or freeing TMEM; after an
+    // abort also for a bulk copy still in flight
+    if (issued_steps > 0) {
+        const int last = issued_steps - 1;
+        if (!mbar_wait_bounded(&bar_mma[last & 1], (last >> 1) & 1)) ok = false;
+        if (!ok && issued_steps > 1) mbar_wait_bounded(&bar_mma[(last - 1) & 1], ((last - 1) >> 1) & 1);
+    }
+    if (!ok && threadIdx.x == 0 && b_issued > 0)
+        mbar_wait_bounded(&bar_b[(b_issued - 1) & 1], ((b_issued - 1) >> 1) & 1);
+    tc_fence_after();
+    if (ok) {
+        uint32_t dv[32];
+        tmem_ld32(tmem + lane_base, dv);
+        tmem_wait_ld();
+        if (valid) {
+            float4* dst = reinterpret_cast<float4*>(out + (size_t)morton2(2 * ri + px, 2 * rj + py) * NP);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                dst[c] = make_float4(__uint_as_float(dv[4 * c]), __uint_as_float(dv[4 * c + 1]),
+                                     __uint_as_float(dv[4 * c + 2]), __uint_as_float(dv[4 * c + 3]));
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(status, LFMM_ETIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTcCols);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
+                          const float* u_parent, const void* C_parent, float* u_level, void* C_level, int* status,
+                          cudaStream_t s) {
+    const int64_t rows = (int64_t)1 << (2 * (level - 1));
+    dim3 grid((unsigned)((rows + kTcThreads - 1) / kTcThreads), 4);
+    m2l_tc_kernel<<<grid, kTcThreads, 0, s>>>(level, q_level, u_parent, (const float*)ops.tc[k],
+                                              (const float*)ops.mono[k], (const DFv*)Q_level,
+                                              (const DFv*)C_parent, u_level, (DFv*)C_level, status);
+    return cudaGetLastError();
+}
+
+}  // namespace lfmm

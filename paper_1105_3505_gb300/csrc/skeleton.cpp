@@ -26,6 +26,7 @@
 // more than Def. 6.1 allows).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <numeric>
 #include <tuple>
@@ -273,11 +274,38 @@ ModelOps* get_model_ops(int leaf_side, int P, int ppe, int n_levels, std::string
 
 namespace {
 
+// TF32 with round-to-nearest (ties away): keep 10 explicit mantissa bits.
+float tf32_rna(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// One tensor-core B tile: 32 rows (n = output p) x 32 K (q) fp32, K-major, laid out as the
+// 128-byte-swizzled shared-memory image (row n at 128 n bytes, 16-byte chunk c of the row
+// at chunk c ^ (n mod 8)); value(n, k) split into TF32 hi and lo tiles.
+template <typename F>
+void write_tc_tile(float* hi, float* lo, int rows, int cols, F value) {
+    for (int n = 0; n < 32; ++n)
+        for (int k = 0; k < 32; ++k) {
+            const float v = (n < rows && k < cols) ? (float)value(n, k) : 0.0f;
+            const float h = tf32_rna(v);
+            const float l = tf32_rna(v - h);
+            const size_t idx = (size_t)n * 32 + ((size_t)(((k >> 2) ^ (n & 7)) << 2)) + (k & 3);
+            hi[idx] = h;
+            lo[idx] = l;
+        }
+}
+
 template <typename T>
 void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
                        std::vector<T>& img, size_t& off_tofs, size_t& off_tab,
                        std::vector<size_t>& off_m2m, std::vector<size_t>& off_l2l,
-                       std::vector<size_t>& off_tifo, std::vector<size_t>& off_mono) {
+                       std::vector<size_t>& off_tifo, std::vector<size_t>& off_mono,
+                       std::vector<size_t>& off_tc) {
     const int s = mo.leaf_side;
     auto align = [](size_t v) { return (v + 31) & ~(size_t)31; };  // 128/256-byte aligned blocks
     size_t n = 0;
@@ -289,7 +317,14 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
     off_l2l.assign(n_levels, 0);
     off_tifo.assign(n_levels, 0);
     off_mono.assign(n_levels, 0);
+    off_tc.assign(n_levels, 0);
+    const bool tc = sizeof(T) == 4 && NP == 32;
     for (int k = 0; k < n_levels; ++k) {
+        if (tc) {
+            n = (n + 255) & ~(size_t)255;  // 1 KB aligned tiles
+            off_tc[k] = n;
+            n += (size_t)(kNumOffsets + 4) * 2 * 1024;
+        }
         off_mono[k] = n;
         n = align(n + (size_t)2 * kNumOffsets);
         if (k >= 1) {
@@ -349,6 +384,21 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
             for (int p = 0; p < lv.P; ++p)
                 for (int q = 0; q < lv.P; ++q)
                     img[off_tifo[k] + ((size_t)o * NP + q) * NP + p] = (T)(t[(size_t)p * lv.P + q] - c);
+            if (tc) {
+                float* base = reinterpret_cast<float*>(img.data() + off_tc[k]) + (size_t)o * 2048;
+                write_tc_tile(base, base + 1024, lv.P, lv.P,
+                              [&](int n_, int k_) { return t[(size_t)n_ * lv.P + k_] - c; });
+            }
+        }
+        // tensor-core L2L tiles for class c: B[n = child p][k = parent q] = S_{k+1}[q][c P_k + p]
+        if (tc && k + 1 < (int)mo.levels.size() && k + 1 < n_levels) {
+            const LevelOps& par = mo.levels[k + 1];
+            for (int c = 0; c < 4; ++c) {
+                float* base = reinterpret_cast<float*>(img.data() + off_tc[k]) + (size_t)(kNumOffsets + c) * 2048;
+                write_tc_tile(base, base + 1024, lv.P, par.P, [&](int n_, int k_) {
+                    return par.S[(size_t)k_ * (4 * lv.P) + c * lv.P + n_];
+                });
+            }
         }
     }
 }
@@ -373,17 +423,17 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
     d->tab_W = 16;
     while (d->tab_W < 2 * d->tab_H + 1) d->tab_W += 32;
     size_t off_tofs, off_tab;
-    std::vector<size_t> om, ol, ot, omono;
+    std::vector<size_t> om, ol, ot, omono, otc;
     std::vector<char> bytes;
     size_t elem;
     if (precision == LFMM_MIXED) {
         std::vector<float> img;
-        fill_device_image<float>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono);
+        fill_device_image<float>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono, otc);
         elem = sizeof(float);
         bytes.assign((const char*)img.data(), (const char*)img.data() + img.size() * elem);
     } else {
         std::vector<double> img;
-        fill_device_image<double>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono);
+        fill_device_image<double>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono, otc);
         elem = sizeof(double);
         bytes.assign((const char*)img.data(), (const char*)img.data() + img.size() * elem);
     }
@@ -407,7 +457,9 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
     d->l2l.resize(nl);
     d->tifo.resize(nl);
     d->mono.resize(nl);
+    d->tc.assign(nl, nullptr);
     for (int k = 0; k < nl; ++k) {
+        if (precision == LFMM_MIXED && NP == 32) d->tc[k] = b + otc[k] * elem;
         d->m2m[k] = k >= 1 ? b + om[k] * elem : nullptr;
         d->l2l[k] = k >= 1 ? b + ol[k] * elem : nullptr;
         d->tifo[k] = b + ot[k] * elem;

@@ -30,7 +30,7 @@ class LfmmError(RuntimeError):
 class lfmm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("max_leaf_side", ctypes.c_int32), ("proxies_per_edge", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("tc_min_level", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class lfmm_plan_info(ctypes.Structure):
@@ -60,6 +60,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_eval": (ctypes.c_int, [vp, vp, vp, vp]),
         "lfmm_eval_parts": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lfmm_plan_destroy": (ctypes.c_int, [vp]),
+        "lfmm_plan_status": (ctypes.c_int, [vp, vp]),
         "lfmm_plan_get_info": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_plan_info)]),
         "lfmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "lfmm_last_error": (ctypes.c_char_p, []),
@@ -116,10 +117,10 @@ def lfmm_opts_default() -> lfmm_opts:
 
 
 def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
-              proxies_per_edge: int = 64) -> lfmm_opts:
+              proxies_per_edge: int = 64, tc_min_level: int = 0) -> lfmm_opts:
     o = lfmm_opts_default()
     o.precision, o.p, o.leaf_size = precision, p, leaf_size
-    o.max_leaf_side, o.proxies_per_edge = max_leaf_side, proxies_per_edge
+    o.max_leaf_side, o.proxies_per_edge, o.tc_min_level = max_leaf_side, proxies_per_edge, tc_min_level
     return o
 
 
@@ -142,6 +143,11 @@ def lfmm_eval_parts(plan: int, f, u_near, u_far, stream=None) -> None:
 
 def lfmm_plan_destroy(plan: int) -> None:
     _check(load().lfmm_plan_destroy(plan), "lfmm_plan_destroy")
+
+
+def lfmm_plan_status(plan: int, stream=None) -> None:
+    """Raise LfmmError(LFMM_ETIMEOUT) if a bounded device-side wait of the plan gave up."""
+    _check(load().lfmm_plan_status(plan, _stream_handle(stream)), "lfmm_plan_status")
 
 
 def lfmm_plan_get_info(plan: int) -> dict:
@@ -233,11 +239,15 @@ class Plan:
     memory as f (numpy for numpy input, torch CUDA tensor for CUDA input)."""
 
     def __init__(self, src, tgt, precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64,
-                 max_leaf_side: int = 32, proxies_per_edge: int = 64, stream=None):
+                 max_leaf_side: int = 32, proxies_per_edge: int = 64, tc_min_level: int = 0, stream=None):
         self.n_src, self.n_tgt = int(src.shape[0]), int(tgt.shape[0])
         self.stream = stream
         self.handle = lfmm_plan_create(src, self.n_src, tgt, self.n_tgt,
-                                       make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge), stream)
+                                       make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge,
+                                                 tc_min_level), stream)
+
+    def status(self):
+        lfmm_plan_status(self.handle, self.stream)
 
     def info(self) -> dict:
         return lfmm_plan_get_info(self.handle)

@@ -37,7 +37,8 @@ def test_status_strings_and_defaults(lib):
     assert lfmm.lfmm_status_string(0) == "ok"
     assert lfmm.lfmm_status_string(lfmm.LFMM_EINVAL) == "invalid argument"
     o = lfmm.lfmm_opts_default()
-    assert (o.precision, o.p, o.leaf_size, o.max_leaf_side, o.proxies_per_edge) == (lfmm.LFMM_MIXED, 8, 64, 32, 64)
+    assert (o.precision, o.p, o.leaf_size, o.max_leaf_side, o.proxies_per_edge, o.tc_min_level) == \
+        (lfmm.LFMM_MIXED, 8, 64, 32, 64, 0)
     assert ctypes.sizeof(lfmm.lfmm_opts) == 32
 
 
