@@ -6,7 +6,11 @@
 // as an implicit GEMM per CTA: M = 128 target boxes (TMEM lanes), N = 32 outputs,
 // K = 27 x 32 gathered source expansions (+ 32 for the parent).  Operands are split
 // into TF32 hi + lo parts (round to nearest) and three products hi*hi + hi*lo + lo*hi
-// are accumulated in fp32 in TMEM (the lo*lo term is below 2^-22 relative).
+// are formed (the lo*lo term is below 2^-22 relative).  The tensor core's fp32
+// accumulation rounds toward zero, and that bias grows linearly with the number of
+// MMAs feeding one accumulator; so every K-step writes fresh TMEM accumulators (hi*hi
+// in one, the small hi*lo + lo*hi terms in another), which the threads read back two
+// steps later and add in registers with round-to-nearest fp32.
 //
 //  - A (gathered expansions): each thread owns one box = one TMEM lane; it loads the
 //    source row for the current K-step, splits it and writes hi and lo with
@@ -26,7 +30,9 @@ namespace lfmm {
 namespace {
 
 constexpr int kTcThreads = 128;          // 4 warps, one TMEM lane quarter each
-constexpr int kTcCols = 256;             // D [0,32), A stage s: hi [32+64s, 64+64s), lo [64+64s, 96+64s)
+// TMEM columns: D_big[b] [32b, 32b+32), D_small[b] [64+32b, 96+32b),
+// A stage b: hi [128+64b, 160+64b), lo [160+64b, 192+64b)
+constexpr int kTcCols = 256;
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -253,6 +259,18 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     constexpr uint32_t kIdesc = idesc_tf32(128, NP);
     bool ok = true;
     int issued_steps = 0, b_issued = 0;
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    // add the K-step partials held in TMEM buffer b to the register accumulator
+    auto flush = [&](int b) {
+        uint32_t big[32], small[32];
+        tmem_ld32(tmem + lane_base + 32 * b, big);
+        tmem_ld32(tmem + lane_base + 64 + 32 * b, small);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+    };
     float4 nxt[8];
     load_row(src_row(0), nxt);
     for (int step = 0; step < n_steps; ++step) {
@@ -270,6 +288,7 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
             ok = false;
             break;
         }
+        if (step >= 2) flush(buf);  // partials of step - 2, before this step overwrites them
         // B tiles (hi, lo) for this step
         if (threadIdx.x == 0) {
             const float* src = step < 27 ? tiles + (size_t)s_off[step][2] * 2048
@@ -290,9 +309,9 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
                 lv[4 * c + e] = tf32_rna_bits(xs[e] - __uint_as_float(h));
             }
         }
-        const uint32_t a_hi = tmem + 32 + 64 * buf, a_lo = a_hi + 32;
-        tmem_st32(tmem + lane_base + 32 + 64 * buf, hv);
-        tmem_st32(tmem + lane_base + 64 + 64 * buf, lv);
+        const uint32_t a_hi = tmem + 128 + 64 * buf, a_lo = a_hi + 32;
+        tmem_st32(tmem + lane_base + 128 + 64 * buf, hv);
+        tmem_st32(tmem + lane_base + 160 + 64 * buf, lv);
         tmem_wait_st();
         tc_fence_before();
         __syncthreads();
@@ -302,12 +321,13 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
                 atomicExch(&s_abort, 1);
             } else {
                 const uint32_t b_hi = smem_u32(&sB[buf][0][0]), b_lo = smem_u32(&sB[buf][1][0]);
+                const uint32_t d_big = tmem + 32 * buf, d_small = tmem + 64 + 32 * buf;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint64_t dh = smem_desc_sw128(b_hi + 32 * kk), dl = smem_desc_sw128(b_lo + 32 * kk);
-                    mma_tf32_ts(tmem, a_hi + 8 * kk, dh, kIdesc, (step > 0 || kk > 0) ? 1u : 0u);
-                    mma_tf32_ts(tmem, a_hi + 8 * kk, dl, kIdesc, 1u);
-                    mma_tf32_ts(tmem, a_lo + 8 * kk, dh, kIdesc, 1u);
+                    mma_tf32_ts(d_big, a_hi + 8 * kk, dh, kIdesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_ts(d_small, a_hi + 8 * kk, dl, kIdesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_ts(d_small, a_lo + 8 * kk, dh, kIdesc, 1u);
                 }
                 mma_commit(&bar_mma[buf]);
             }
@@ -330,26 +350,29 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
 
     __syncthreads();
     if (s_abort) ok = false;
-    // wait (bounded) for the last committed MMAs before reading or freeing TMEM; after an
-    // abort also for a bulk copy still in flight
-    if (issued_steps > 0) {
-        const int last = issued_steps - 1;
-        if (!mbar_wait_bounded(&bar_mma[last & 1], (last >> 1) & 1)) ok = false;
-        if (!ok && issued_steps > 1) mbar_wait_bounded(&bar_mma[(last - 1) & 1], ((last - 1) >> 1) & 1);
+    // the last two steps' partials (bounded waits); after an abort also wait for a bulk
+    // copy still in flight before the CTA exits
+    for (int st = ok ? std::max(0, issued_steps - 2) : issued_steps; st < issued_steps; ++st) {
+        if (!mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1)) atomicExch(&s_abort, 1);
+        __syncthreads();  // agree on the outcome before the warp-wide TMEM loads
+        if (s_abort) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        flush(st & 1);
     }
-    if (!ok && threadIdx.x == 0 && b_issued > 0)
-        mbar_wait_bounded(&bar_b[(b_issued - 1) & 1], ((b_issued - 1) >> 1) & 1);
-    tc_fence_after();
+    if (!ok) {
+        for (int st = std::max(0, issued_steps - 2); st < issued_steps; ++st)
+            mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
+        if (threadIdx.x == 0 && b_issued > 0)
+            mbar_wait_bounded(&bar_b[(b_issued - 1) & 1], ((b_issued - 1) >> 1) & 1);
+    }
     if (ok) {
-        uint32_t dv[32];
-        tmem_ld32(tmem + lane_base, dv);
-        tmem_wait_ld();
         if (valid) {
             float4* dst = reinterpret_cast<float4*>(out + (size_t)morton2(2 * ri + px, 2 * rj + py) * NP);
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                dst[c] = make_float4(__uint_as_float(dv[4 * c]), __uint_as_float(dv[4 * c + 1]),
-                                     __uint_as_float(dv[4 * c + 2]), __uint_as_float(dv[4 * c + 3]));
+            for (int c = 0; c < 8; ++c) dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
         }
     } else if (threadIdx.x == 0) {
         atomicExch(status, LFMM_ETIMEOUT);
