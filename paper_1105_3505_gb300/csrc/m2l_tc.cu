@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     if (s_abort) ok = false;
     // the last two steps' partials (bounded waits); after an abort also wait for a bulk
     // copy still in flight before the CTA exits
-    for (int st = ok ? std::max(0, issued_steps - 2) : issued_steps; st < issued_steps; ++st) {
+    for (int st = ok ? max(0, issued_steps - 2) : issued_steps; st < issued_steps; ++st) {
         if (!mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1)) atomicExch(&s_abort, 1);
         __syncthreads();  // agree on the outcome before the warp-wide TMEM loads
         if (s_abort) {
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
         flush(st & 1);
     }
     if (!ok) {
-        for (int st = std::max(0, issued_steps - 2); st < issued_steps; ++st)
+        for (int st = max(0, issued_steps - 2); st < issued_steps; ++st)
             mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
         if (threadIdx.x == 0 && b_issued > 0)
             mbar_wait_bounded(&bar_b[(b_issued - 1) & 1], ((b_issued - 1) >> 1) & 1);
