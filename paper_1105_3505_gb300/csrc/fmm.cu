@@ -94,6 +94,23 @@ __device__ __forceinline__ DF shfl_xor_v(DF v, int m) {
 }
 __device__ __forceinline__ double shfl_xor_v(double v, int m) { return __shfl_xor_sync(kFull, v, m); }
 
+// v[i] summed over the warp lands in lane i (31 shuffles for 32 values).
+template <typename T>
+__device__ __forceinline__ T reduce_scatter32(T (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const T send = upper ? v[i] : v[i + off];
+            const T keep = upper ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, off);
+        }
+    }
+    return v[0];
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
@@ -432,11 +449,22 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
                 op = l2l + (size_t)cls * NP * NP;
                 if (valid) src = u_par + (size_t)morton2(ri, rj) * NP;
             }
-            // operator slice: my_op[k][j] = op[k][32*half + j]   (op is k-major [q][p])
+            // operator slice: my_op[k][j] = op[k][32*half + j]   (op is k-major [q][p]);
+            // 16-byte loads, all issued before the stores
             __syncwarp();
-            for (int i = lane; i < NP * 32; i += 32) {
-                const int k = i >> 5, j = i & 31;
-                my_op[i] = op[(size_t)k * NP + 32 * half + j];
+            {
+                constexpr int V4 = (int)(16 / sizeof(T));        // elements per 16 bytes
+                constexpr int PER = NP * 32 / V4 / 32;           // 16-byte chunks per lane
+                uint4 buf[PER];
+#pragma unroll
+                for (int c = 0; c < PER; ++c) {
+                    const int i = (c * 32 + lane) * V4;
+                    const int k = i >> 5, j = i & 31;
+                    buf[c] = __ldg(reinterpret_cast<const uint4*>(op + (size_t)k * NP + 32 * half + j));
+                }
+#pragma unroll
+                for (int c = 0; c < PER; ++c)
+                    reinterpret_cast<uint4*>(my_op)[c * 32 + lane] = buf[c];
             }
             __syncwarp();
             if (src) {
@@ -881,13 +909,34 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
                     if (g == 0) add(v);
                 }
                 acc -= cmp;
-                if (lane < nt) {
-                    T far = T(0);
-                    if (uhat) {
-                        const T* row = tofsT + (size_t)(tx + side * ty) * NP;
-#pragma unroll 8
-                        for (int pp = 0; pp < NP; ++pp) far = fma(__ldg(row + pp), uh[pp], far);
+                // L2P: lanes own expansion entries p, one coalesced row of T_ofs^T per
+                // target, then a reduce-scatter leaves target t's value in lane t
+                T far = T(0);
+                if (uhat) {
+                    constexpr int PL = NP / 32;
+                    T uhl[PL];
+#pragma unroll
+                    for (int i = 0; i < PL; ++i) uhl[i] = uh[lane + 32 * i];
+                    const int myJ = tx + side * ty;
+                    T part[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) part[q] = T(0);
+#pragma unroll
+                    for (int tc = 0; tc < 4; ++tc) {
+                        if (tc * 8 < nt) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const T* row = tofsT + (size_t)shfl(myJ, tc * 8 + q) * NP;
+                                T v = T(0);
+#pragma unroll
+                                for (int i = 0; i < PL; ++i) v = fma(__ldg(row + lane + 32 * i), uhl[i], v);
+                                part[tc * 8 + q] = v;
+                            }
+                        }
                     }
+                    far = reduce_scatter32(part);
+                }
+                if (lane < nt) {
                     const int dst = s_tperm[t0 + lane];
                     const double dn = (double)acc + near_const;
                     const double df = (double)far + M::to_double(cl);

@@ -16,9 +16,11 @@
 //    source row for the current K-step, splits it and writes hi and lo with
 //    tcgen05.st into A columns of TMEM (the MMA reads A from tensor memory).
 //  - B (operators): pre-split, pre-swizzled 4 KB tiles in the device image, fetched
-//    with cp.async.bulk into shared memory, completion tracked by an mbarrier.
-//  - one elected thread issues 12 tcgen05.mma (K = 8 each) per K-step and commits
-//    them to a second mbarrier that frees the step's A/B buffers two steps later.
+//    with cp.async.bulk into a 3-deep ring in shared memory one step ahead, completion
+//    tracked by mbarriers.
+//  - every thread arrives on an "A ready" mbarrier after its TMEM stores; one elected
+//    thread waits on it, issues 12 tcgen05.mma (K = 8 each) per K-step and commits
+//    them to a third mbarrier that frees the step's A and D buffers two steps later.
 //  - epilogue: tcgen05.ld of the 128 x 32 fp32 accumulator.
 // Every mbarrier wait is bounded (clock64 budget); on expiry the CTA records
 // LFMM_ETIMEOUT in the plan's status word, stops issuing work, waits (bounded) for
@@ -43,6 +45,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -188,8 +193,8 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
                                                             float* __restrict__ out, DFv* __restrict__ Cout,
                                                             int* __restrict__ status) {
     constexpr int NP = 32;
-    __shared__ __align__(1024) float sB[2][2][1024];  // [stage][hi, lo][32 x 32 swizzled]
-    __shared__ __align__(8) uint64_t bar_b[2], bar_mma[2];
+    __shared__ __align__(1024) float sB[3][2][1024];  // [ring slot][hi, lo][32 x 32 swizzled]
+    __shared__ __align__(8) uint64_t bar_b[3], bar_a[2], bar_mma[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_off[27][3];
     __shared__ int s_abort;
@@ -224,8 +229,9 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
             s_off[nn][2] = offset_index_tc(dx, dy);
             ++nn;
         }
-        mbar_init(&bar_b[0], 1);
-        mbar_init(&bar_b[1], 1);
+        for (int i = 0; i < 3; ++i) mbar_init(&bar_b[i], 1);
+        mbar_init(&bar_a[0], kTcThreads);
+        mbar_init(&bar_a[1], kTcThreads);
         mbar_init(&bar_mma[0], 1);
         mbar_init(&bar_mma[1], 1);
         fence_barrier_init();
@@ -271,6 +277,15 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
     };
+    auto b_src = [&](int step) -> const float* {
+        return step < 27 ? tiles + (size_t)s_off[step][2] * 2048 : tiles + (size_t)(kNumOffsets + cls) * 2048;
+    };
+    volatile int* vabort = &s_abort;
+    if (threadIdx.x == 0) {  // B tiles of step 0
+        mbar_arrive_expect_tx(&bar_b[0], 8192);
+        bulk_g2s(&sB[0][0][0], b_src(0), 8192, &bar_b[0]);
+        b_issued = 1;
+    }
     float4 nxt[8];
     load_row(src_row(0), nxt);
     for (int step = 0; step < n_steps; ++step) {
@@ -280,22 +295,19 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
         for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
         if (step + 1 < n_steps) load_row(src_row(step + 1), nxt);  // in flight during this step
         if (step >= 2) {
-            if (!mbar_wait_bounded(&bar_mma[buf], ((step - 2) >> 1) & 1)) atomicExch(&s_abort, 1);
+            // A stage and D buffer of step - 2 become free; fold its partials in.  Every
+            // exit from this loop is warp-uniform (vote), so warp-collective TMEM loads
+            // never run with part of a warp missing.
+            bool w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[buf], ((step - 2) >> 1) & 1);
+            w_ok = __all_sync(0xffffffffu, w_ok);
+            if (!w_ok) {
+                atomicExch(&s_abort, 1);
+                break;
+            }
             tc_fence_after();
-        }
-        __syncthreads();
-        if (s_abort) {
-            ok = false;
+            flush(buf);
+        } else if (__any_sync(0xffffffffu, *vabort != 0)) {
             break;
-        }
-        if (step >= 2) flush(buf);  // partials of step - 2, before this step overwrites them
-        // B tiles (hi, lo) for this step
-        if (threadIdx.x == 0) {
-            const float* src = step < 27 ? tiles + (size_t)s_off[step][2] * 2048
-                                         : tiles + (size_t)(kNumOffsets + cls) * 2048;
-            mbar_arrive_expect_tx(&bar_b[buf], 8192);
-            bulk_g2s(&sB[buf][0][0], src, 8192, &bar_b[buf]);
-            b_issued = step + 1;
         }
         // this thread's A row -> TMEM lane (hi, lo)
         uint32_t hv[32], lv[32];
@@ -314,22 +326,32 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
         tmem_st32(tmem + lane_base + 160 + 64 * buf, lv);
         tmem_wait_st();
         tc_fence_before();
-        __syncthreads();
+        mbar_arrive(&bar_a[buf]);
         if (threadIdx.x == 0) {
+            const int slot = step % 3;
+            const bool good = *vabort == 0 && mbar_wait_bounded(&bar_a[buf], (step >> 1) & 1) &&
+                              mbar_wait_bounded(&bar_b[slot], (step / 3) & 1);
+            if (!good) atomicExch(&s_abort, 1);  // no MMAs for this step; all warps stop next step
+        }
+        if (threadIdx.x == 0 && *vabort == 0) {
+            const int slot = step % 3;
             tc_fence_after();
-            if (!mbar_wait_bounded(&bar_b[buf], (step >> 1) & 1)) {
-                atomicExch(&s_abort, 1);
-            } else {
-                const uint32_t b_hi = smem_u32(&sB[buf][0][0]), b_lo = smem_u32(&sB[buf][1][0]);
-                const uint32_t d_big = tmem + 32 * buf, d_small = tmem + 64 + 32 * buf;
+            const uint32_t b_hi = smem_u32(&sB[slot][0][0]), b_lo = smem_u32(&sB[slot][1][0]);
+            const uint32_t d_big = tmem + 32 * buf, d_small = tmem + 64 + 32 * buf;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t dh = smem_desc_sw128(b_hi + 32 * kk), dl = smem_desc_sw128(b_lo + 32 * kk);
-                    mma_tf32_ts(d_big, a_hi + 8 * kk, dh, kIdesc, kk > 0 ? 1u : 0u);
-                    mma_tf32_ts(d_small, a_hi + 8 * kk, dl, kIdesc, kk > 0 ? 1u : 0u);
-                    mma_tf32_ts(d_small, a_lo + 8 * kk, dh, kIdesc, 1u);
-                }
-                mma_commit(&bar_mma[buf]);
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t dh = smem_desc_sw128(b_hi + 32 * kk), dl = smem_desc_sw128(b_lo + 32 * kk);
+                mma_tf32_ts(d_big, a_hi + 8 * kk, dh, kIdesc, kk > 0 ? 1u : 0u);
+                mma_tf32_ts(d_small, a_hi + 8 * kk, dl, kIdesc, kk > 0 ? 1u : 0u);
+                mma_tf32_ts(d_small, a_lo + 8 * kk, dh, kIdesc, 1u);
+            }
+            mma_commit(&bar_mma[buf]);
+            // B tiles of the next step into the slot step - 2 used (its MMAs are done)
+            if (step + 1 < n_steps) {
+                const int ns = (step + 1) % 3;
+                mbar_arrive_expect_tx(&bar_b[ns], 8192);
+                bulk_g2s(&sB[ns][0][0], b_src(step + 1), 8192, &bar_b[ns]);
+                b_issued = step + 2;
             }
         }
         issued_steps = step + 1;
@@ -348,25 +370,30 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
         Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
     }
 
+    // the last two steps' partials (bounded, warp-uniform waits); after an abort, wait
+    // (bounded) for work already issued before the CTA exits
+    __syncthreads();
+    ok = s_abort == 0;
+    if (ok) {
+        for (int st = max(0, n_steps - 2); st < n_steps; ++st) {
+            bool w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
+            w_ok = __all_sync(0xffffffffu, w_ok);
+            if (!w_ok) {
+                atomicExch(&s_abort, 1);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            flush(st & 1);
+        }
+    }
     __syncthreads();
     if (s_abort) ok = false;
-    // the last two steps' partials (bounded waits); after an abort also wait for a bulk
-    // copy still in flight before the CTA exits
-    for (int st = ok ? max(0, issued_steps - 2) : issued_steps; st < issued_steps; ++st) {
-        if (!mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1)) atomicExch(&s_abort, 1);
-        __syncthreads();  // agree on the outcome before the warp-wide TMEM loads
-        if (s_abort) {
-            ok = false;
-            break;
-        }
-        tc_fence_after();
-        flush(st & 1);
-    }
     if (!ok) {
         for (int st = max(0, issued_steps - 2); st < issued_steps; ++st)
             mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
         if (threadIdx.x == 0 && b_issued > 0)
-            mbar_wait_bounded(&bar_b[(b_issued - 1) & 1], ((b_issued - 1) >> 1) & 1);
+            mbar_wait_bounded(&bar_b[(b_issued - 1) % 3], ((b_issued - 1) / 3) & 1);
     }
     if (ok) {
         if (valid) {

@@ -153,7 +153,7 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     for (int l = std::min(2, L); l <= L; ++l) boxes += (int64_t)1 << (2 * l);
     auto a = [](int64_t b) { return b == 0 ? (int64_t)16 : b; };
     const int64_t bytes = a(2 * (n_leaves + 1) * 4) + a(2 * (n_src + n_tgt) * 4) + a(n_src * esz) +
-                          2 * a(boxes * NP * esz) + 2 * a(boxes * 8);
+                          2 * a(boxes * NP * esz) + 2 * a(boxes * 8) + 16 /* status word */;
 
     std::memset(info, 0, sizeof(*info));
     info->n_src = n_src;
