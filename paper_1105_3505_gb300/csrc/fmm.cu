@@ -434,6 +434,9 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
     const bool valid = row < n_rows;
     const int ri = valid ? (int)(row & (np_side - 1)) : 0, rj = valid ? (int)(row >> lg) : 0;
     T* my_op = sop + warp * NP * 32;
+    // per-warp source rows, skewed so that column reads across rows hit distinct banks:
+    // element k of row r at r * NP + ((k + r) mod NP)
+    T* my_rows = red + (size_t)kSkWarps * 32 * 33 + (size_t)warp * 32 * NP;
     for (int half = 0; half < NP / 32; ++half) {  // 32 outputs per pass
         T acc[32];
 #pragma unroll
@@ -467,15 +470,40 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
                     reinterpret_cast<uint4*>(my_op)[c * 32 + lane] = buf[c];
             }
             __syncwarp();
+            // coalesced copy of the 32 source rows of this warp (lane l: 16-byte chunk
+            // l % CPR of rows l / CPR + (32 / CPR) i)
+            {
+                constexpr int V4 = (int)(16 / sizeof(T));
+                constexpr int CPR = NP / V4;          // 16-byte chunks per row
+                constexpr int RPI = 32 / CPR;         // rows per instruction
+                const int ch = lane % CPR;
+#pragma unroll
+                for (int i = 0; i < 32 / RPI; ++i) {
+                    const int r = lane / CPR + RPI * i;
+                    const T* rs = reinterpret_cast<const T*>(
+                        __shfl_sync(kFull, reinterpret_cast<unsigned long long>(src), r));
+                    uint4 v = make_uint4(0, 0, 0, 0);
+                    if (rs) v = __ldg(reinterpret_cast<const uint4*>(rs) + ch);
+                    const T* ve = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                    for (int e = 0; e < V4; ++e) {
+                        const int k = ch * V4 + e;
+                        my_rows[r * NP + ((k + r) & (NP - 1))] = ve[e];
+                    }
+                }
+                __syncwarp();
+            }
             if (src) {
+                const T* rowp = my_rows + lane * NP;
 #pragma unroll 4
                 for (int k = 0; k < NP; ++k) {
-                    const T a = src[k];
+                    const T a = rowp[(k + lane) & (NP - 1)];
                     const T* b = my_op + k * 32;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) acc[j] = fma(a, b[j], acc[j]);
                 }
             }
+            __syncwarp();
         }
         // reduce the warps' partial sums
         T* my_red = red + (size_t)warp * 32 * 33;
@@ -521,7 +549,9 @@ __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sop = reinterpret_cast<T*>(smem_raw);
     if (SMEM_OP) {
-        for (int i = threadIdx.x; i < 4 * NP * NP; i += blockDim.x) sop[i] = m2m[i];
+        constexpr int N4 = 4 * NP * NP * (int)sizeof(T) / 16;
+        for (int i = threadIdx.x; i < N4; i += blockDim.x)
+            reinterpret_cast<uint4*>(sop)[i] = __ldg(reinterpret_cast<const uint4*>(m2m) + i);
         __syncthreads();
     }
     const T* op = SMEM_OP ? sop : m2m;
@@ -1027,7 +1057,8 @@ static cudaError_t launch_m2l_splitk(const DeviceOps& ops, int k, int level, con
                                      const T* u_par, const void* Cpar, T* out, void* Cout, cudaStream_t s) {
     using V = typename Mono<T>::V;
     const T* l2l = u_par ? (const T*)ops.l2l[k + 1] : nullptr;
-    const size_t smem = (size_t)kSkWarps * NP * 32 * sizeof(T) + (size_t)kSkWarps * 32 * 33 * sizeof(T);
+    const size_t smem = (size_t)kSkWarps * NP * 32 * sizeof(T) + (size_t)kSkWarps * 32 * 33 * sizeof(T) +
+                        (size_t)kSkWarps * 32 * NP * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(m2l_splitk_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,

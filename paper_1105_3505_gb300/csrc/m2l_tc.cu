@@ -193,7 +193,12 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
                                                             float* __restrict__ out, DFv* __restrict__ Cout,
                                                             int* __restrict__ status) {
     constexpr int NP = 32;
-    __shared__ __align__(1024) float sB[3][2][1024];  // [ring slot][hi, lo][32 x 32 swizzled]
+    // dynamic shared memory: B ring [3][hi, lo][32 x 32 swizzled] (1024-byte aligned),
+    // then the gathered fp32 A rows [2][128 x 32] (16-byte chunks XOR-swizzled)
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    float (*sB)[2][1024] = reinterpret_cast<float (*)[2][1024]>(
+        tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u));
+    float (*sA)[kTcThreads * 32] = reinterpret_cast<float (*)[kTcThreads * 32]>(&sB[3][0][0]);
     __shared__ __align__(8) uint64_t bar_b[3], bar_a[2], bar_mma[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_off[27][3];
@@ -247,19 +252,31 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     const uint32_t tmem = s_tmem;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 
-    auto src_row = [&](int step) -> const float* {
-        if (!valid) return nullptr;
-        if (step < 27) {
-            const int sx = 2 * ri + px + s_off[step][0], sy = 2 * rj + py + s_off[step][1];
-            if (sx < 0 || sx >= side || sy < 0 || sy >= side) return nullptr;
-            return q + (size_t)morton2(sx, sy) * NP;
-        }
-        return u_par + (size_t)morton2(ri, rj) * NP;
-    };
-    auto load_row = [&](const float* r, float4 (&x)[8]) {
+    // coalesced gather of the step's 128 source rows into sA[b]: thread t copies 16-byte
+    // chunk (t % 8) of rows t/8 + 16 j; chunk c of row r lands at chunk c ^ (r % 8)
+    auto gather = [&](int step, int b) {
+        const int ch = threadIdx.x & 7;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            x[c] = r ? __ldg(reinterpret_cast<const float4*>(r) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < 8; ++j) {
+            const int r = (threadIdx.x >> 3) + 16 * j;
+            const int64_t rr = (int64_t)blockIdx.x * kTcThreads + r;
+            const float* srow = nullptr;
+            if (rr < n_rows) {
+                const int ii = (int)(rr & (np_side - 1)), jj = (int)(rr >> lg);
+                if (step < 27) {
+                    const int sx = 2 * ii + px + s_off[step][0], sy = 2 * jj + py + s_off[step][1];
+                    if (sx >= 0 && sx < side && sy >= 0 && sy < side) srow = q + (size_t)morton2(sx, sy) * NP;
+                } else {
+                    srow = u_par + (size_t)morton2(ii, jj) * NP;
+                }
+            }
+            const uint32_t dst = smem_u32(&sA[b][r * 32 + ((ch ^ (r & 7)) << 2)]);
+            const void* src = srow ? (const void*)(srow + 4 * ch) : (const void*)q;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                         "r"(srow ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
     constexpr uint32_t kIdesc = idesc_tf32(128, NP);
@@ -286,14 +303,21 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
         bulk_g2s(&sB[0][0][0], b_src(0), 8192, &bar_b[0]);
         b_issued = 1;
     }
-    float4 nxt[8];
-    load_row(src_row(0), nxt);
+    gather(0, 0);
     for (int step = 0; step < n_steps; ++step) {
         const int buf = step & 1;
+        // this step's rows have landed (own copies), and every thread is done with the
+        // buffer the next gather overwrites (it held step - 1)
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
+        if (step + 1 < n_steps) gather(step + 1, buf ^ 1);
         float4 cur[8];
+        {
+            const float* myrow = &sA[buf][threadIdx.x * 32];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) cur[c] = nxt[c];
-        if (step + 1 < n_steps) load_row(src_row(step + 1), nxt);  // in flight during this step
+            for (int c = 0; c < 8; ++c)
+                cur[c] = *reinterpret_cast<const float4*>(myrow + ((c ^ (threadIdx.x & 7)) << 2));
+        }
         if (step >= 2) {
             // A stage and D buffer of step - 2 become free; fold its partials in.  Every
             // exit from this loop is warp-uniform (vote), so warp-collective TMEM loads
@@ -372,6 +396,7 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
 
     // the last two steps' partials (bounded, warp-uniform waits); after an abort, wait
     // (bounded) for work already issued before the CTA exits
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     ok = s_abort == 0;
     if (ok) {
@@ -417,9 +442,16 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
 cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                           const float* u_parent, const void* C_parent, float* u_level, void* C_level, int* status,
                           cudaStream_t s) {
+    constexpr size_t smem = 1024 + sizeof(float) * (3 * 2 * 1024 + 2 * kTcThreads * 32);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     const int64_t rows = (int64_t)1 << (2 * (level - 1));
     dim3 grid((unsigned)((rows + kTcThreads - 1) / kTcThreads), 4);
-    m2l_tc_kernel<<<grid, kTcThreads, 0, s>>>(level, q_level, u_parent, (const float*)ops.tc[k],
+    m2l_tc_kernel<<<grid, kTcThreads, smem, s>>>(level, q_level, u_parent, (const float*)ops.tc[k],
                                               (const float*)ops.mono[k], (const DFv*)Q_level,
                                               (const DFv*)C_parent, u_level, (DFv*)C_level, status);
     return cudaGetLastError();
