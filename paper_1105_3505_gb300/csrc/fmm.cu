@@ -387,14 +387,23 @@ __global__ void __launch_bounds__(128) translate_kernel(int level, const T* __re
 // ------------------------------------------------------------------------- small levels
 // Levels with few boxes are latency-bound in the tiled kernel (each block walks all
 // 28 K-steps in sequence).  Here a block takes 32 target boxes of one parity class and
-// splits the K-steps over its 8 warps (warp w: steps w, w+8, ...).  Per step a warp
-// stages the 32 x 32 operator block in its own shared memory, each lane takes one box
-// (its source row in registers) and 32 outputs, so every operator value loaded is used
-// by 32 boxes; the 8 warps' partial sums are added in shared memory.
-constexpr int kSkWarps = 8;
+// splits the K-steps over its W warps (warp w: steps w, w+W, ...).  Per step a warp
+// stages the NP x 32 operator block and the 32 source rows in its own shared memory,
+// each lane takes one box and 32 outputs, so every operator value loaded is used by 32
+// boxes; the W warps' partial sums are added in shared memory.
+// Shared memory per warp: the operator slice (NP x 32) and the 32 source rows, the
+// rows padded by 32 elements; the padded row area doubles as the warp's 32 x 33 block of
+// partial sums once its K-steps are done.  Binary64 with 64 coefficients uses 6 warps
+// so that the block fits in 227 KB.
+template <typename T, int NP>
+struct SkCfg {
+    static constexpr int WARPS = (sizeof(T) == 8 && NP == 64) ? 6 : 8;
+    static constexpr int ROWS = 32 * NP + 32;  // per-warp row area (>= 32 * 33)
+    static constexpr size_t SMEM = (size_t)WARPS * (NP * 32 + ROWS) * sizeof(T);
+};
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, const T* __restrict__ q,
+__global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(int level, const T* __restrict__ q,
                                                                    const T* __restrict__ u_par,
                                                                    const T* __restrict__ ops,
                                                                    const T* __restrict__ l2l,
@@ -406,8 +415,10 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
     using M = Mono<T>;
     using V = typename M::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int kSkWarps = SkCfg<T, NP>::WARPS;
+    constexpr int kRows = SkCfg<T, NP>::ROWS;
     T* sop = reinterpret_cast<T*>(smem_raw);            // [warps][NP][32] operator slice
-    T* red = sop + kSkWarps * NP * 32;                  // [warps][32 boxes][33]
+    T* red = sop + kSkWarps * NP * 32;                  // [warps][kRows]: rows, then 32 x 33 sums
     __shared__ int s_off[27][3];
     const int cls = blockIdx.y;
     const int px = cls & 1, py = cls >> 1;
@@ -436,7 +447,7 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
     T* my_op = sop + warp * NP * 32;
     // per-warp source rows, skewed so that column reads across rows hit distinct banks:
     // element k of row r at r * NP + ((k + r) mod NP)
-    T* my_rows = red + (size_t)kSkWarps * 32 * 33 + (size_t)warp * 32 * NP;
+    T* my_rows = red + (size_t)warp * kRows;
     for (int half = 0; half < NP / 32; ++half) {  // 32 outputs per pass
         T acc[32];
 #pragma unroll
@@ -506,7 +517,7 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
             __syncwarp();
         }
         // reduce the warps' partial sums
-        T* my_red = red + (size_t)warp * 32 * 33;
+        T* my_red = my_rows;  // this warp is done with its rows
 #pragma unroll
         for (int j = 0; j < 32; ++j) my_red[lane * 33 + j] = acc[j];
         __syncthreads();
@@ -514,7 +525,7 @@ __global__ void __launch_bounds__(kSkWarps * 32) m2l_splitk_kernel(int level, co
             const int b = i >> 5, j = i & 31;
             T v = T(0);
 #pragma unroll
-            for (int w = 0; w < kSkWarps; ++w) v += red[(size_t)w * 32 * 33 + b * 33 + j];
+            for (int w = 0; w < kSkWarps; ++w) v += red[(size_t)w * kRows + b * 33 + j];
             const int64_t r = (int64_t)blockIdx.x * 32 + b;
             if (r < n_rows) {
                 const int ii = (int)(r & (np_side - 1)), jj = (int)(r >> lg);
@@ -1009,7 +1020,7 @@ static cudaError_t launch_translate(int level, const T* q, const T* u_par, const
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(translate_kernel<T, NP, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return clear_and_return(e);
         attr_set = true;
     }
     const int lg = MODE == kModeM2L ? level - 1 : level;
@@ -1033,7 +1044,7 @@ static cudaError_t launch_m2m_warp(const DeviceOps& ops, int k, int level, const
         if (!attr) {
             cudaError_t e = cudaFuncSetAttribute(m2m_warp_kernel<T, NP, true>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op_bytes);
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) return clear_and_return(e);
             attr = true;
         }
         m2m_warp_kernel<T, NP, true><<<(int)blocks, 256, op_bytes, s>>>(level, q_child, (const T*)ops.m2m[k],
@@ -1057,18 +1068,18 @@ static cudaError_t launch_m2l_splitk(const DeviceOps& ops, int k, int level, con
                                      const T* u_par, const void* Cpar, T* out, void* Cout, cudaStream_t s) {
     using V = typename Mono<T>::V;
     const T* l2l = u_par ? (const T*)ops.l2l[k + 1] : nullptr;
-    const size_t smem = (size_t)kSkWarps * NP * 32 * sizeof(T) + (size_t)kSkWarps * 32 * 33 * sizeof(T) +
-                        (size_t)kSkWarps * 32 * NP * sizeof(T);
+    constexpr size_t smem = SkCfg<T, NP>::SMEM;
+    static_assert(smem <= 227 * 1024, "split-K M2L block exceeds the shared memory of one SM");
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(m2l_splitk_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return clear_and_return(e);
         attr = true;
     }
     const int64_t rows = (int64_t)1 << (2 * (level - 1));
     dim3 grid((unsigned)((rows + 31) / 32), 4);
-    m2l_splitk_kernel<T, NP><<<grid, kSkWarps * 32, smem, s>>>(level, q, u_par, (const T*)ops.tifo[k], l2l,
+    m2l_splitk_kernel<T, NP><<<grid, SkCfg<T, NP>::WARPS * 32, smem, s>>>(level, q, u_par, (const T*)ops.tifo[k], l2l,
                                                               (const T*)ops.mono[k], (const V*)Qin, (const V*)Cpar,
                                                               out, (V*)Cout);
     return cudaGetLastError();
@@ -1115,7 +1126,7 @@ static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const 
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(p2p_leaf_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return clear_and_return(e);
         attr_bytes = smem;
     }
     if (per_sm_for != smem) {
@@ -1151,7 +1162,7 @@ static cudaError_t launch_p2p_strip(const TreeView& t, const DeviceOps& ops, int
     if (smem > attr_bytes) {
         cudaError_t e = cudaFuncSetAttribute(p2p_strip_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return clear_and_return(e);
         attr_bytes = smem;
     }
     if (per_sm_for != smem) {

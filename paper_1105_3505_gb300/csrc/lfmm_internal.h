@@ -27,6 +27,14 @@ int fail(int status, const std::string& msg);
                                                 cudaGetErrorString(_e));               \
     } while (0)
 
+// A failed runtime call that is not a launch (an attribute set, say) also leaves its
+// code as the thread's last error, which the next launch check would report again:
+// read it off before handing the code back.
+inline cudaError_t clear_and_return(cudaError_t e) {
+    (void)cudaGetLastError();
+    return e;
+}
+
 // ---------------------------------------------------------------- constants
 constexpr int kPhiHostRadius = 128;   // host phi table radius; eq. 3.1 beyond
 constexpr int kMaxLeafSide = 32;      // largest supported leaf side (P2P table in shared memory)

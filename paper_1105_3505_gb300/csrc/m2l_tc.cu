@@ -446,7 +446,7 @@ cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return clear_and_return(e);
         attr = true;
     }
     const int64_t rows = (int64_t)1 << (2 * (level - 1));
