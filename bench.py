@@ -35,6 +35,8 @@ METRIC = "Mpoints/s at rel err≤1e-6 (mixed vs plain FP64 on GPU); serve p50/p9
 WORKLOAD = "uniform_1m: 2^20 distinct sources + 2^20 distinct targets uniform in [0,4096)^2, seed 1"
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
+TC_MIN_LEVEL = 8            # library default: levels >= 8 of the fp32 path on the tensor cores
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 : bf16 tensor throughput
 
 
 def parse_args():
@@ -120,11 +122,11 @@ def near_pairs(src, tgt, info) -> int:
     return int((nb * ct).sum())
 
 
-def m2l_flops(info, P) -> int:
+def m2l_flops(info, P, levels=None) -> int:
     """Useful flops of M2L (+ fused L2L): 2 P^2 per (target box, interaction-list box) pair over
     levels 2..L (Def. 6.1 lists, truncated at the root boundary), plus 2 P^2 per box for L2L."""
     total = 0
-    for lvl in range(2, info["L"] + 1):
+    for lvl in (levels if levels is not None else range(2, info["L"] + 1)):
         n = 1 << lvl
         x = np.arange(n)
         # per axis: number of valid source coordinates for each offset o in [-3, 3]
@@ -302,7 +304,8 @@ def main():
             dist.destroy_process_group()
         return
 
-    # per-phase device time (CUDA events recorded by the library on `stream`)
+    # per-phase device time: CUDA events the library records on `stream` around each
+    # phase, over a second pass of the same timed loop (L2 flushed before every step)
     lfmm.lfmm_profile_enable(True)
     lfmm.lfmm_profile_read(reset=True)
     n_prof = max(3, min(args.steps, 10))
@@ -312,6 +315,7 @@ def main():
     phases = lfmm.lfmm_profile_read(reset=True)
     lfmm.lfmm_profile_enable(False)
     phase_ms = {k: v[0] / n_prof for k, v in phases.items()}
+    phase_launch_ms = {k: v[0] / v[1] for k, v in phases.items() if v[1] > 0}
 
     h = step(s_d, t_d, f_d, u_d, opts)
     info = lfmm.lfmm_plan_get_info(h)
@@ -321,34 +325,40 @@ def main():
     peaks, peak_src = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
 
-    # roofline of the dominant kernel
-    pairs = near_pairs(prob.src, prob.tgt, info)
+    # roofline of the dominant kernel: the longest single kernel launch of the step
     P = 4 * (args.p - 1)
-    flops_m2l = m2l_flops(info, P)
-    dom = max(("p2p", "m2l", "tree", "p2m", "m2m"), key=lambda k: phase_ms.get(k, 0.0))
+    tc_levels = [lvl for lvl in range(2, info["L"] + 1) if lvl >= TC_MIN_LEVEL]
+    cands = {k: phase_launch_ms[k] for k in ("p2p", "m2l_tc", "p2m") if k in phase_launch_ms}
+    dom = max(cands, key=cands.get)
+    t_launch = cands[dom] * 1e-3
     if dom == "p2p":
-        # one 4-byte table load + one FMA per pair; binding pipe = shared-memory loads,
-        # 32 lanes per clock per SM
-        achieved = pairs / (phase_ms["p2p"] * 1e-3) / 1e12
-        peak = SM_COUNT * 32 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "p2p_l2p_kernel<float,32>", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tpairs/s", "frac": achieved / peak, "traffic": traffic_for("p2p_l2p"),
-                "peak_basis": f"152 SMs x 32 shared-memory load lanes/clk x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})",
-                "units_per_launch": pairs}
-    elif dom == "m2l":
-        achieved = flops_m2l / (phase_ms["m2l"] * 1e-3) / 1e12
-        peak = SM_COUNT * 128 * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"kernel": "m2l_kernel<float,32>", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l"),
-                "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_src})",
-                "units_per_launch": flops_m2l}
+        # one 4-byte table load + one multiply-add per pair: the binding pipe is the
+        # shared-memory load path, 32 lanes per clock per SM
+        pairs = near_pairs(prob.src, prob.tgt, info)
+        achieved = pairs / t_launch / 1e9
+        peak = SM_COUNT * 32 * sm_mhz * 1e6 / 1e9
+        roof = {"kernel": "p2p_strip_kernel<float,32>", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Gpairs/s", "frac": achieved / peak, "traffic": traffic_for("p2p_strip_kernel"),
+                "peak_basis": f"shared-memory loads: 152 SMs x 32 lanes/clk x {sm_mhz:.0f} MHz ({peak_src})",
+                "units_per_launch": pairs, "ms_per_launch": cands[dom]}
+    elif dom == "m2l_tc":
+        flops = m2l_flops(info, P, tc_levels) // max(1, len(tc_levels))
+        achieved = flops / t_launch / 1e12
+        peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
+        roof = {"kernel": "m2l_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l_tc_kernel"),
+                "peak_basis": f"tf32 dense = measured bf16 burst {peaks['bf16_tflops']} x {TF32_PER_BF16:.3f} "
+                              f"(nominal 1.1 / 2.25 PFLOP/s) ({peak_src}); useful flops only, the 3xTF32 split "
+                              f"issues 3 MMAs per useful product",
+                "units_per_launch": flops, "ms_per_launch": cands[dom]}
     else:
-        # tree build: algorithmic minimum of read coordinates + write bucketed (loc, perm)
-        bytes_tree = (ns + nt) * (8 + 8 + 8)
-        achieved = bytes_tree / (phase_ms[dom] * 1e-3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "units_per_launch": bytes_tree}
+        flops = 2 * P * ns
+        achieved = flops / t_launch / 1e12
+        peak = SM_COUNT * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": "p2m_kernel<float,32>", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("p2m_kernel"),
+                "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz ({peak_src})",
+                "units_per_launch": flops, "ms_per_launch": cands[dom]}
 
     out = {"metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -161,10 +161,11 @@ int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, const int32_t*
 #define LFMM_PHASE_OPERATORS 1  /* model-box operator cache lookup / upload (Sec. 8.1)  */
 #define LFMM_PHASE_P2M 2        /* step 1: T_ofs                                        */
 #define LFMM_PHASE_M2M 3        /* step 2: T_ofo                                        */
-#define LFMM_PHASE_M2L 4        /* steps 3-4: T_ifo and T_ifi                           */
+#define LFMM_PHASE_M2L 4        /* steps 3-4: T_ifo and T_ifi (SIMT kernels)            */
 #define LFMM_PHASE_P2P 5        /* step 5: near field, T_tfi, binary64 final sum        */
 #define LFMM_PHASE_COPY 6       /* host<->device copies of coordinates, f and u         */
-#define LFMM_NUM_PHASES 7
+#define LFMM_PHASE_M2L_TC 7     /* steps 3-4 on the tensor cores (fp32 levels, P <= 32) */
+#define LFMM_NUM_PHASES 8
 
 /* Turn per-phase timing on (1) or off (0).  While on, every create/eval synchronises its
  * stream once at the end to read the events.  Process-wide. */

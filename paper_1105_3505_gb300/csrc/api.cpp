@@ -336,14 +336,12 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
             pt.add_launches(1);
         }
     }
-    {
-        PhaseTimer pt(LFMM_PHASE_M2L, s);
-        for (int l = 2; l <= L; ++l) {
-            LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
-                                        l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), p->tc_min_level,
-                                        p->status, s));
-            pt.add_launches(1);
-        }
+    for (int l = 2; l <= L; ++l) {
+        const bool tc = m2l_uses_tc(ops, L - l, l, p->tc_min_level, sizeof(T) == 4);
+        PhaseTimer pt(tc ? LFMM_PHASE_M2L_TC : LFMM_PHASE_M2L, s);
+        LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
+                                    l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), p->tc_min_level, p->status, s));
+        pt.add_launches(1);
     }
     {
         PhaseTimer pt(LFMM_PHASE_P2P, s);

@@ -325,12 +325,20 @@ __global__ void __launch_bounds__(128) translate_kernel(int level, const T* __re
                 Qout[b] = s;
             } else {
                 typename M::V s = has_l2l ? Cpar[morton2(i, j)] : M::zero();
-                for (int st = 0; st < 27; ++st) {
-                    const int sx = 2 * i + px + s_off[st][0], sy = 2 * j + py + s_off[st][1];
-                    if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
-                    const int o = s_off[st][2];
-                    const typename M::V co = M::make(mono[o], mono[kNumOffsets + o]);
-                    s = M::add(s, M::mul(co, Qin[morton2(sx, sy)]));
+                // nine loads in flight at a time
+                for (int c0 = 0; c0 < 27; c0 += 9) {
+                    typename M::V qv[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const int sx = 2 * i + px + s_off[c0 + k][0], sy = 2 * j + py + s_off[c0 + k][1];
+                        const bool in = sx >= 0 && sx < side && sy >= 0 && sy < side;
+                        qv[k] = in ? Qin[morton2(sx, sy)] : M::zero();
+                    }
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const int o = s_off[c0 + k][2];
+                        s = M::add(s, M::mul(M::make(mono[o], mono[kNumOffsets + o]), qv[k]));
+                    }
                 }
                 Cout[morton2(2 * i + px, 2 * j + py)] = s;
             }
@@ -448,6 +456,10 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
     // per-warp source rows, skewed so that column reads across rows hit distinct banks:
     // element k of row r at r * NP + ((k + r) mod NP)
     T* my_rows = red + (size_t)warp * kRows;
+    // incoming constant: each warp adds c_o Q(source) of its own K-steps (compensated),
+    // the partials are combined after the loop
+    __shared__ V s_cpart[kSkWarps][32];
+    V cacc = M::zero();
     for (int half = 0; half < NP / 32; ++half) {  // 32 outputs per pass
         T acc[32];
 #pragma unroll
@@ -456,9 +468,14 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
             const T* op;
             const T* src = nullptr;
             if (st < 27) {
-                op = ops + (size_t)s_off[st][2] * NP * NP;
+                const int o = s_off[st][2];
+                op = ops + (size_t)o * NP * NP;
                 const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
-                if (valid && sx >= 0 && sx < side && sy >= 0 && sy < side) src = q + (size_t)morton2(sx, sy) * NP;
+                if (valid && sx >= 0 && sx < side && sy >= 0 && sy < side) {
+                    const uint32_t sb = morton2(sx, sy);
+                    src = q + (size_t)sb * NP;
+                    if (half == 0) cacc = M::add(cacc, M::mul(M::make(mono[o], mono[kNumOffsets + o]), Qin[sb]));
+                }
             } else {
                 op = l2l + (size_t)cls * NP * NP;
                 if (valid) src = u_par + (size_t)morton2(ri, rj) * NP;
@@ -520,6 +537,7 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
         T* my_red = my_rows;  // this warp is done with its rows
 #pragma unroll
         for (int j = 0; j < 32; ++j) my_red[lane * 33 + j] = acc[j];
+        if (half == 0) s_cpart[warp][lane] = cacc;
         __syncthreads();
         for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
             const int b = i >> 5, j = i & 31;
@@ -534,15 +552,11 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
         }
         __syncthreads();
     }
-    // incoming constant (compensated), warp 0, one box per lane
+    // incoming constant: parent's constant plus the warps' partials, one box per lane
     if (warp == 0 && valid) {
         V sacc = has_l2l ? Cpar[morton2(ri, rj)] : M::zero();
-        for (int st = 0; st < 27; ++st) {
-            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
-            if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
-            const int o = s_off[st][2];
-            sacc = M::add(sacc, M::mul(M::make(mono[o], mono[kNumOffsets + o]), Qin[morton2(sx, sy)]));
-        }
+#pragma unroll
+        for (int w = 0; w < kSkWarps; ++w) sacc = M::add(sacc, s_cpart[w][lane]);
         Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
     }
 }
@@ -573,21 +587,29 @@ __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __res
         T xv[CL];
 #pragma unroll
         for (int c = 0; c < CL; ++c) xv[c] = qc[(size_t)par * 4 * NP + lane + 32 * c];
-        T acc[PL];
+        // one accumulator chain per 32-wide input chunk, added at the end
+        T acc[CL][PL];
 #pragma unroll
-        for (int i = 0; i < PL; ++i) acc[i] = T(0);
+        for (int c = 0; c < CL; ++c)
 #pragma unroll
-        for (int c = 0; c < CL; ++c) {
-#pragma unroll 8
-            for (int l = 0; l < 32; ++l) {
+            for (int i = 0; i < PL; ++i) acc[c][i] = T(0);
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+#pragma unroll
+            for (int c = 0; c < CL; ++c) {
                 const T v = shfl(xv[c], l);
                 const T* row = op + (size_t)(32 * c + l) * NP;
 #pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(row[lane + 32 * i], v, acc[i]);
+                for (int i = 0; i < PL; ++i) acc[c][i] = fma(row[lane + 32 * i], v, acc[c][i]);
             }
         }
 #pragma unroll
-        for (int i = 0; i < PL; ++i) qp[(size_t)par * NP + lane + 32 * i] = acc[i];
+        for (int i = 0; i < PL; ++i) {
+            T a = acc[0][i];
+#pragma unroll
+            for (int c = 1; c < CL; ++c) a += acc[c][i];
+            qp[(size_t)par * NP + lane + 32 * i] = a;
+        }
         // total charge of the parent: lanes 0..3 hold the children's, all lanes shuffle
         typename M::V qv = lane < 4 ? Qin[4 * par + lane] : M::zero();
         qv = M::add(qv, shfl_xor_v(qv, 1));
@@ -816,7 +838,9 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
     int* s_tperm = s_tloc + Cfg::CAPT;                                   // [CAPT]
     int* s_sb = s_tperm + Cfg::CAPT;                                     // [3][MAXSW+3]
     int* s_tb = s_sb + 3 * (Cfg::MAXSW + 3);                             // [MAXSW+1]
-    __shared__ int s_rs[4], s_clo, s_chi;
+    __shared__ int s_rs[4];
+    __shared__ int s_ra[Cfg::MAXSW][3], s_rl[Cfg::MAXSW][3];  // per-leaf source ranges
+    __shared__ double s_nc[Cfg::MAXSW];                       // per-leaf phi0 * Q_near
 
     for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
     const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
@@ -852,6 +876,22 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
         for (int i = threadIdx.x; i < bx1 - bx0; i += blockDim.x)
             s_c[i] = Cleaf ? Cleaf[morton2(bx0 + i, by)] : M::zero();
         __syncthreads();
+        // per-leaf source ranges (three staged rows) and near-field constant phi0 * Q_near
+        for (int li = threadIdx.x; li < bx1 - bx0; li += blockDim.x) {
+            const int bx = bx0 + li;
+            const int ca = max(bx - 1, 0) - c_lo, cb = min(bx + 1, n - 1) - c_lo + 1;
+            int rs = 0;
+            V qn = M::zero();
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int* sb = s_sb + r * (Cfg::MAXSW + 3);
+                s_ra[li][r] = rs + (sb[ca] - sb[0]);
+                s_rl[li][r] = sb[cb] - sb[ca];
+                rs += sb[ncol] - sb[0];
+                for (int c = ca; c < cb; ++c) qn = M::add(qn, s_q[r * (Cfg::MAXSW + 2) + c]);
+            }
+            s_nc[li] = M::to_double(M::mul(phi0, qn));
+        }
         if (threadIdx.x == 0) {
             int acc = 0;
             for (int r = 0; r < 3; ++r) {
@@ -879,112 +919,96 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
             e.f = f_sorted[j];
             s_src[v] = e;
         }
+        // targets, with their leaf's index in the strip packed into bits 8..15 of the
+        // local position (x and y are below 32)
         const int tb0 = s_tb[0], nt_strip = s_tb[bx1 - bx0] - tb0;
         for (int v = threadIdx.x; v < nt_strip; v += blockDim.x) {
-            s_tloc[v] = tloc[tb0 + v];
+            int lo = 0, hi = bx1 - bx0;  // leaf li with s_tb[li] <= tb0 + v < s_tb[li + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_tb[mid] - tb0 <= v) lo = mid;
+                else hi = mid;
+            }
+            s_tloc[v] = tloc[tb0 + v] | (lo << 8);
             s_tperm[v] = tperm[tb0 + v];
         }
         __syncthreads();
 
-        for (int bx = bx0 + warp; bx < bx1; bx += Cfg::WARPS) {
-            const int li = bx - bx0;
-            const int tb = s_tb[li] - tb0, te = s_tb[li + 1] - tb0;
-            if (tb == te) continue;
-            // three staged source ranges (columns bx-1 .. bx+1 of each row)
-            const int ca = max(bx - 1, 0) - c_lo, cb = min(bx + 1, n - 1) - c_lo + 1;
-            int ra[3], rlen[3];
-            V qn = M::zero();
+        // pairs: a warp takes 32 consecutive targets of the strip (one per lane, from up
+        // to three leaves); each lane walks its leaf's three source ranges.  Products are
+        // summed by plain multiply-adds in blocks of four, and the block sums are added
+        // with compensation (fp32) so the long sums keep fp32-level relative accuracy.
+        const int n_chunks = (nt_strip + 31) >> 5;
+        for (int chunk = warp; chunk < n_chunks; chunk += Cfg::WARPS) {
+            const int v = chunk * 32 + lane;
+            const bool active = v < nt_strip;
+            const int n_act = min(32, nt_strip - chunk * 32);
+            const int tl = s_tloc[active ? v : chunk * 32];
+            const int li = (tl >> 8) & 0xff, tx = tl & 0xff, ty = tl >> 16;
+            const T* tp = tab_c + (tx + tab_W * ty + li * side);
+            T acc = T(0), cmp = T(0);
+            auto add = [&](T term) {
+                if constexpr (sizeof(T) == 4) {
+                    const T y = term - cmp;
+                    const T s2 = acc + y;
+                    cmp = (s2 - acc) - y;
+                    acc = s2;
+                } else {
+                    acc += term;
+                }
+            };
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const int* sb = s_sb + r * (Cfg::MAXSW + 3);
-                ra[r] = s_rs[r] + (sb[ca] - sb[0]);
-                rlen[r] = sb[cb] - sb[ca];
-                for (int c = ca; c < cb; ++c) qn = M::add(qn, s_q[r * (Cfg::MAXSW + 2) + c]);
+                const SrcEntry<T>* src = s_src + s_ra[li][r];
+                const int len = active ? s_rl[li][r] : 0;
+                int j = 0;
+                for (; j + 4 <= len; j += 4) {
+                    const SrcEntry<T> e0 = src[j], e1 = src[j + 1], e2 = src[j + 2], e3 = src[j + 3];
+                    T b = tp[-e0.off] * e0.f;
+                    b = fma(tp[-e1.off], e1.f, b);
+                    b = fma(tp[-e2.off], e2.f, b);
+                    b = fma(tp[-e3.off], e3.f, b);
+                    add(b);
+                }
+                if (j < len) {
+                    T b = T(0);
+                    for (; j < len; ++j) {
+                        const SrcEntry<T> e = src[j];
+                        b = fma(tp[-e.off], e.f, b);
+                    }
+                    add(b);
+                }
             }
-            const double near_const = M::to_double(M::mul(phi0, qn));
-            const V cl = s_c[li];
-            const T* uh = s_uhat + li * NP;
-            const int shift = li * side;
-            for (int t0 = tb; t0 < te; t0 += 32) {
-                const int nt = min(32, te - t0);
-                const int G = 32 / nt;
-                const int t = lane % nt, g = lane / nt;
-                const bool active = g < G;
-                const int tl = s_tloc[t0 + t];
-                const int tx = tl & 0xffff, ty = tl >> 16;
-                const T* tp = tab_c + (tx + tab_W * ty + shift);
-                T acc = T(0), cmp = T(0);
-                auto add = [&](T term) {
-                    if constexpr (sizeof(T) == 4) {
-                        const T y = term - cmp;
-                        const T s2 = acc + y;
-                        cmp = (s2 - acc) - y;
-                        acc = s2;
-                    } else {
-                        acc += term;
+            acc -= cmp;
+            // L2P: lanes own expansion entries p; one coalesced row of T_ofs^T per target
+            // against its leaf's incoming expansion, then a reduce-scatter leaves target
+            // q's value in lane q
+            T far = T(0);
+            if (uhat) {
+                constexpr int PL = NP / 32;
+                const int myJ = tx + side * ty;
+                T part[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int Jq = shfl(myJ, q), lq = shfl(li, q);
+                    T w = T(0);
+                    if (q < n_act) {
+                        const T* row = tofsT + (size_t)Jq * NP;
+                        const T* uq = s_uhat + lq * NP;
+#pragma unroll
+                        for (int i = 0; i < PL; ++i) w = fma(__ldg(row + lane + 32 * i), uq[lane + 32 * i], w);
                     }
-                };
-                if (active) {
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const SrcEntry<T>* src = s_src + ra[r];
-                        const int len = rlen[r];
-                        int j = g;
-                        for (; j + G < len; j += 2 * G) {
-                            const SrcEntry<T> e0 = src[j], e1 = src[j + G];
-                            const T p0 = tp[-e0.off] * e0.f;
-                            const T p1 = tp[-e1.off] * e1.f;
-                            add(p0);
-                            add(p1);
-                        }
-                        if (j < len) {
-                            const SrcEntry<T> e0 = src[j];
-                            add(tp[-e0.off] * e0.f);
-                        }
-                    }
+                    part[q] = w;
                 }
-                acc -= cmp;
-                cmp = T(0);
-                for (int k = 1; k < G; ++k) {
-                    const T v = shfl(acc, t + k * nt);
-                    if (g == 0) add(v);
-                }
-                acc -= cmp;
-                // L2P: lanes own expansion entries p, one coalesced row of T_ofs^T per
-                // target, then a reduce-scatter leaves target t's value in lane t
-                T far = T(0);
-                if (uhat) {
-                    constexpr int PL = NP / 32;
-                    T uhl[PL];
-#pragma unroll
-                    for (int i = 0; i < PL; ++i) uhl[i] = uh[lane + 32 * i];
-                    const int myJ = tx + side * ty;
-                    T part[32];
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) part[q] = T(0);
-#pragma unroll
-                    for (int tc = 0; tc < 4; ++tc) {
-                        if (tc * 8 < nt) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const T* row = tofsT + (size_t)shfl(myJ, tc * 8 + q) * NP;
-                                T v = T(0);
-#pragma unroll
-                                for (int i = 0; i < PL; ++i) v = fma(__ldg(row + lane + 32 * i), uhl[i], v);
-                                part[tc * 8 + q] = v;
-                            }
-                        }
-                    }
-                    far = reduce_scatter32(part);
-                }
-                if (lane < nt) {
-                    const int dst = s_tperm[t0 + lane];
-                    const double dn = (double)acc + near_const;
-                    const double df = (double)far + M::to_double(cl);
-                    if (u) u[dst] = dn + df;
-                    if (u_near) u_near[dst] = dn;
-                    if (u_far) u_far[dst] = df;
-                }
+                far = reduce_scatter32(part);
+            }
+            if (active) {
+                const int dst = s_tperm[v];
+                const double dn = (double)acc + s_nc[li];
+                const double df = (double)far + M::to_double(s_c[li]);
+                if (u) u[dst] = dn + df;
+                if (u_near) u_near[dst] = dn;
+                if (u_far) u_far[dst] = df;
             }
         }
     }
@@ -1036,8 +1060,8 @@ static cudaError_t launch_m2m_warp(const DeviceOps& ops, int k, int level, const
                                    T* q_parent, void* Q_parent, cudaStream_t s) {
     using V = typename Mono<T>::V;
     const int64_t n_par = (int64_t)1 << (2 * level);
-    int64_t blocks = (n_par + 7) / 8;  // 8 warps per block, grid-stride: one operator load per block
-    if (blocks > 152 * 2) blocks = 152 * 2;
+    int64_t blocks = (n_par + 7) / 8;  // 8 warps per block, grid-stride over parents
+    if (blocks > 152 * 8) blocks = 152 * 8;
     constexpr size_t op_bytes = (size_t)4 * NP * NP * sizeof(T);
     if constexpr (op_bytes <= 64 * 1024) {
         static bool attr = false;
@@ -1094,7 +1118,7 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
                        const T* u_parent, const void* C_parent, T* u_level, void* C_level, int tc_min_level,
                        int* status, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
-        if (ops.NP == 32 && ops.tc.size() > (size_t)k && ops.tc[k] && level >= tc_min_level)
+        if (m2l_uses_tc(ops, k, level, tc_min_level, true))
             return launch_m2l_tc(ops, k, level, (const float*)q_level, Q_level, (const float*)u_parent, C_parent,
                                  (float*)u_level, C_level, status, s);
     }

@@ -384,12 +384,20 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     // scalar channel (compensated), one box per thread, while the last MMAs run
     if (valid) {
         DFv sacc = has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
-#pragma unroll 9
-        for (int st = 0; st < 27; ++st) {
-            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
-            if (sx < 0 || sx >= side || sy < 0 || sy >= side) continue;
-            const int o = s_off[st][2];
-            sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, Qin[morton2(sx, sy)]));
+        // nine loads in flight at a time
+        for (int c0 = 0; c0 < 27; c0 += 9) {
+            DFv qv[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int sx = 2 * ri + px + s_off[c0 + k][0], sy = 2 * rj + py + s_off[c0 + k][1];
+                const bool in = sx >= 0 && sx < side && sy >= 0 && sy < side;
+                qv[k] = in ? Qin[morton2(sx, sy)] : DFv{0.f, 0.f};
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int o = s_off[c0 + k][2];
+                sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+            }
         }
         Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
     }
