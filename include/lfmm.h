@@ -68,11 +68,21 @@ typedef struct lfmm_opts {
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
     int32_t tc_min_level;     /* mixed path, P <= 32: tree levels >= this run M2L on the      */
                               /* tensor cores (0 = default 8; a value > 30 disables them)     */
-    int32_t reserved[2];      /* must be zero                                                 */
+    int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
+    int32_t reserved;         /* must be zero                                                 */
 } lfmm_opts;
 
+/* Tree storage.  UNIFORM: every box of every level is stored (Sec. 6), the layout for
+ * points that fill their root box.  PRUNED: the same levels and boxes, but only boxes
+ * with a source or target below them are kept, each with explicit parent, children and
+ * interaction list; the layout for clustered points, whose leaf level is set by the
+ * densest cluster.  AUTO picks PRUNED when there are fewer points than leaves. */
+#define LFMM_TREE_AUTO 0
+#define LFMM_TREE_UNIFORM 1
+#define LFMM_TREE_PRUNED 2
+
 /* Fill opts with the defaults: LFMM_MIXED, p = 8, leaf_size = 64, max_leaf_side = 32,
- * proxies_per_edge = 64, tc_min_level = 0. */
+ * proxies_per_edge = 64, tc_min_level = 0, tree = LFMM_TREE_AUTO. */
 void lfmm_opts_default(lfmm_opts* opts);
 
 /* Build a plan for fixed source and target locations (Sec. 8.1 precomputation):
@@ -90,6 +100,21 @@ void lfmm_opts_default(lfmm_opts* opts);
  * (the root box and the leaf level are read back to size the workspaces). */
 int lfmm_plan_create(lfmm_plan** plan, const int32_t* src_xy, int64_t n_src,
                      const int32_t* tgt_xy, int64_t n_tgt, const lfmm_opts* opts, void* stream);
+
+/* A forest: n_problems independent problems in one plan, evaluated together.  Problem
+ * i owns sources src_xy[2 src_offsets[i] .. 2 src_offsets[i+1]) and targets likewise;
+ * every problem needs at least one source and one target.  All problems share the leaf
+ * side (the largest power of two <= opts.max_leaf_side at which no leaf of any problem
+ * holds more than opts.leaf_size sources or targets), hence the model-box operators of
+ * every level; each has its own root box and leaf level.  Boxes are stored pruned (see
+ * LFMM_TREE_PRUNED) and every sweep covers all problems in one launch per level.
+ *   src_offsets, tgt_offsets  n_problems + 1 int64 in HOST memory, offsets[0] = 0,
+ *                             non-decreasing, offsets[n_problems] = the point count
+ * lfmm_eval on the plan takes f for all sources and writes u for all targets, both in
+ * the concatenated order.  Synchronises `stream` (several times). */
+int lfmm_forest_create(lfmm_plan** plan, const int32_t* src_xy, const int64_t* src_offsets,
+                       const int32_t* tgt_xy, const int64_t* tgt_offsets, int64_t n_problems,
+                       const lfmm_opts* opts, void* stream);
 
 /* Apply the plan (Sec. 8.2): u[i] = sum_j phi(tgt_i - src_j) f[j] for all targets,
  * in the caller's target order.  f: n_src doubles, u: n_tgt doubles (host or device).
@@ -121,6 +146,9 @@ typedef struct lfmm_plan_info {
     int32_t max_leaf_src;     /* largest number of sources in one leaf                   */
     int32_t max_leaf_tgt;
     int64_t device_bytes;     /* device memory owned by the plan (not the shared cache)  */
+    int32_t tree;             /* LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED (forests: PRUNED) */
+    int32_t n_problems;       /* 1, or the number of problems of a forest                */
+    int64_t n_boxes;          /* boxes holding expansions (levels >= 2; pruned: leaves)  */
 } lfmm_plan_info;
 
 int lfmm_plan_get_info(const lfmm_plan* plan, lfmm_plan_info* info);

@@ -51,11 +51,13 @@ struct lfmm_plan {
     int tc_min_level = 8;
     double* f_stage = nullptr;     // device copy of a host f
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
+    std::unique_ptr<Forest> forest;  // pruned tree or forest (null: uniform tree)
+    int64_t n_boxes = 0;
 };
 
 namespace {
 
-constexpr int kMaxLevel = 13;  // 4^13 leaves at most on the uniform tree
+constexpr int kMaxLevel = 14;  // deepest leaf level searched (pruned storage beyond 4^13 leaves)
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
@@ -96,6 +98,10 @@ int palloc(lfmm_plan* p, void** out, size_t bytes, cudaStream_t s) {
 struct Temp {  // stream-ordered temporary freed on scope exit
     void* ptr = nullptr;
     cudaStream_t s = nullptr;
+    void reset_now() {
+        if (ptr) cudaFreeAsync(ptr, s);
+        ptr = nullptr;
+    }
     ~Temp() {
         if (ptr) cudaFreeAsync(ptr, s);
     }
@@ -115,6 +121,7 @@ int talloc(Temp& t, size_t bytes, cudaStream_t s) {
 void free_plan_buffers(lfmm_plan* p) {
     for (void* a : p->allocs) cudaFreeAsync(a, p->last_stream);
     p->allocs.clear();
+    if (p->forest) p->forest->release(p->last_stream);
 }
 
 int validate_opts(const lfmm_opts& o) {
@@ -128,8 +135,9 @@ int validate_opts(const lfmm_opts& o) {
     if (o.proxies_per_edge < 8 || o.proxies_per_edge > 1024)
         return fail(LFMM_EINVAL, "opts.proxies_per_edge must be in [8, 1024]");
     if (o.tc_min_level < 0) return fail(LFMM_EINVAL, "opts.tc_min_level must be >= 0");
-    for (int r : o.reserved)
-        if (r != 0) return fail(LFMM_EINVAL, "opts.reserved must be zero");
+    if (o.tree != LFMM_TREE_AUTO && o.tree != LFMM_TREE_UNIFORM && o.tree != LFMM_TREE_PRUNED)
+        return fail(LFMM_EINVAL, "opts.tree must be LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED");
+    if (o.reserved != 0) return fail(LFMM_EINVAL, "opts.reserved must be zero");
     return LFMM_OK;
 }
 
@@ -152,6 +160,49 @@ int device_coords(lfmm_plan* p, const int32_t* xy, int64_t n, const int32_t** ou
     cudaError_t e = cudaMemcpyAsync(buf, xy, (size_t)n * 8, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("coordinate copy: ") + cudaGetErrorString(e));
     *out = (const int32_t*)buf;
+    return LFMM_OK;
+}
+
+// Operators and workspaces of a pruned tree or forest (tree already in p->forest).
+int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
+    int st;
+    Forest& F = *p->forest;
+    p->side = F.side;
+    p->max_src = F.max_src;
+    p->max_tgt = F.max_tgt;
+    p->K = 0;
+    p->L = 0;
+    for (int i = 0; i < F.np; ++i) {
+        p->K = std::max(p->K, (int)F.K[i]);
+        p->L = std::max(p->L, (int)F.L[i]);
+    }
+    if (F.np == 1) {
+        p->x0 = F.x0[0];
+        p->y0 = F.y0[0];
+    }
+    p->P = 4 * (p->opts.p - 1);
+    p->NP = p->P <= 32 ? 32 : 64;
+    const int n_levels = std::max(1, F.kmax + 1);
+    std::string err;
+    ModelOps* mo = get_model_ops(F.side, p->P, p->opts.proxies_per_edge, n_levels, &err);
+    if (!mo) return fail(LFMM_EINTERNAL, err);
+    p->ops = get_device_ops(mo, p->opts.precision, p->NP, n_levels, s, &err);
+    if (!p->ops) return fail(LFMM_ECUDA, err);
+    const size_t esz = p->opts.precision == LFMM_MIXED ? sizeof(float) : sizeof(double);
+    if ((st = palloc(p, &p->f_sorted, (size_t)p->ns * esz, s))) return st;
+    const int64_t boxes = std::max<int64_t>(F.total_boxes, 1);
+    p->n_boxes = F.total_boxes;
+    if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
+    if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
+    if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
+    if ((st = palloc(p, &p->Cbox, (size_t)boxes * 8, s))) return st;
+    void* stbuf;
+    if ((st = palloc(p, &stbuf, 16, s))) return st;
+    p->status = (int*)stbuf;
+    LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+    p->tc_min_level = p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level;
+    p->bytes += F.bytes;
+    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
     return LFMM_OK;
 }
 
@@ -199,7 +250,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     int chosen = -1;
     for (;;) {
         if (Lf > kMaxLevel)
-            return fail(LFMM_EUNSUPPORTED, "uniform tree would need more than 4^13 leaves");
+            return fail(LFMM_EUNSUPPORTED, "tree would need more than 4^14 leaves");
         const int64_t nf = (int64_t)1 << (2 * Lf);
         const int64_t nc = Lf >= 1 ? nf / 4 : 0;
         Temp c2;
@@ -238,11 +289,27 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
             c2.ptr = nullptr;
             break;
         }
-        Lf = std::min(p->K, Lf + 2);
+        const int next = std::min({p->K, Lf + 2, kMaxLevel});
+        Lf = next > Lf ? next : kMaxLevel + 1;
     }
     p->L = chosen;
     p->side = 1 << (p->K - p->L);
     const int64_t n_leaves = (int64_t)1 << (2 * p->L);
+
+    // ---- pruned storage: fewer points than leaves (or asked for)
+    const bool pruned = p->opts.tree == LFMM_TREE_PRUNED ||
+                        (p->opts.tree == LFMM_TREE_AUTO && p->ns + p->nt < n_leaves);
+    if (pruned) {
+        cnt.reset_now();
+        tree_timer.reset();
+        PhaseTimer pt(LFMM_PHASE_TREE, s);
+        p->forest.reset(new (std::nothrow) Forest());
+        if (!p->forest) return fail(LFMM_ENOMEM, "host allocation failed");
+        const int64_t so[2] = {0, p->ns}, to[2] = {0, p->nt};
+        if ((st = forest_build(*p->forest, src, so, p->ns, tgt, to, p->nt, 1, p->opts.leaf_size, p->side, s, &pt)))
+            return st;
+        return forest_workspaces(p, s);
+    }
 
     // ---- buckets
     void* buf;
@@ -288,6 +355,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         p->lvl_off[l] = boxes;
         boxes += (int64_t)1 << (2 * l);
     }
+    p->n_boxes = boxes;
     if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
@@ -303,6 +371,9 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
 
 template <typename T>
 int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
+    if (p->forest)
+        return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
+                              u, un, uf, p->tc_min_level, p->status, p->num_sms, s);
     TreeView t;
     t.L = p->L;
     t.side = p->side;
@@ -493,6 +564,67 @@ int lfmm_plan_get_info(const lfmm_plan* p, lfmm_plan_info* info) {
     info->max_leaf_src = p->max_src;
     info->max_leaf_tgt = p->max_tgt;
     info->device_bytes = p->bytes;
+    info->tree = p->forest ? LFMM_TREE_PRUNED : LFMM_TREE_UNIFORM;
+    info->n_problems = p->forest ? p->forest->np : 1;
+    info->n_boxes = p->n_boxes;
+    return LFMM_OK;
+}
+
+int lfmm_forest_create(lfmm_plan** plan, const int32_t* src_xy, const int64_t* src_offsets, const int32_t* tgt_xy,
+                       const int64_t* tgt_offsets, int64_t n_problems, const lfmm_opts* opts, void* stream) {
+    if (!plan) return fail(LFMM_EINVAL, "NULL plan out-pointer");
+    *plan = nullptr;
+    if (!src_xy || !tgt_xy || !src_offsets || !tgt_offsets) return fail(LFMM_EINVAL, "NULL argument");
+    if (n_problems < 1 || n_problems > (1 << 24)) return fail(LFMM_EINVAL, "n_problems must be in [1, 2^24]");
+    if (src_offsets[0] != 0 || tgt_offsets[0] != 0) return fail(LFMM_EINVAL, "offsets must start at 0");
+    for (int64_t i = 0; i < n_problems; ++i)
+        if (src_offsets[i + 1] <= src_offsets[i] || tgt_offsets[i + 1] <= tgt_offsets[i])
+            return fail(LFMM_EINVAL, "every problem needs at least one source and one target (problem " +
+                                         std::to_string(i) + ")");
+    const int64_t ns = src_offsets[n_problems], nt = tgt_offsets[n_problems];
+    if (ns > INT32_MAX / 2 || nt > INT32_MAX / 2) return fail(LFMM_EINVAL, "more than 2^30 points");
+    lfmm_opts o;
+    if (opts) o = *opts;
+    else lfmm_opts_default(&o);
+    int st = validate_opts(o);
+    if (st) return st;
+    lfmm_plan* p = new (std::nothrow) lfmm_plan();
+    if (!p) return fail(LFMM_ENOMEM, "host allocation failed");
+    p->opts = o;
+    p->ns = ns;
+    p->nt = nt;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    auto build = [&]() -> int {
+        LFMM_CUDA_TRY(cudaGetDevice(&p->device));
+        LFMM_CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+        setup_pool(p->device);
+        const int32_t *src, *tgt;
+        int r;
+        {
+            PhaseTimer pt(LFMM_PHASE_COPY, s);
+            if ((r = device_coords(p, src_xy, ns, &src, s))) return r;
+            if ((r = device_coords(p, tgt_xy, nt, &tgt, s))) return r;
+        }
+        PhaseTimer pt(LFMM_PHASE_TREE, s);
+        p->forest.reset(new (std::nothrow) Forest());
+        if (!p->forest) return fail(LFMM_ENOMEM, "host allocation failed");
+        if ((r = forest_build(*p->forest, src, src_offsets, ns, tgt, tgt_offsets, nt, (int)n_problems, o.leaf_size,
+                              o.max_leaf_side, s, &pt)))
+            return r;
+        return forest_workspaces(p, s);
+    };
+    st = build();
+    if (st) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        free_plan_buffers(p);
+        delete p;
+        return st;
+    }
+    set_error("");
+    if (profiling_enabled()) profile_flush();
+    *plan = p;
     return LFMM_OK;
 }
 

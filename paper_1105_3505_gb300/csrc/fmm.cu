@@ -20,120 +20,12 @@
 // (double-float pairs on the mixed path).  Interpolation reproduces constants
 // (T_ofs^T 1 = 1 and T_ifi 1 = 1 to the expansion accuracy), so C bypasses L2L/L2P
 // and joins the binary64 final sum.
+#include "device_common.h"
 #include "lfmm_internal.h"
 
 namespace lfmm {
 
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// ------------------------------------------------------------------------- compensated scalars
-// Error-free transformations (Knuth two-sum, FMA two-product) on float pairs.
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = a + b;
-    const float bp = s - a;
-    const float ap = s - bp;
-    return {s, (a - ap) + (b - bp)};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    DF s = two_sum(a.hi, b.hi);
-    DF t = two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
-    return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-    return fast_two_sum(p, e);
-}
-
-template <typename T>
-struct Mono;
-template <>
-struct Mono<float> {
-    using V = DF;
-    __device__ static V zero() { return {0.f, 0.f}; }
-    __device__ static V from_double(double x) {
-        const float h = (float)x;
-        return {h, (float)(x - (double)h)};
-    }
-    __device__ static V make(float hi, float lo) { return {hi, lo}; }
-    __device__ static V add(V a, V b) { return df_add(a, b); }
-    __device__ static V mul(V a, V b) { return df_mul(a, b); }
-    __device__ static double to_double(V a) { return (double)a.hi + (double)a.lo; }
-};
-template <>
-struct Mono<double> {
-    using V = double;
-    __device__ static V zero() { return 0.0; }
-    __device__ static V from_double(double x) { return x; }
-    __device__ static V make(double hi, double lo) { return hi + lo; }
-    __device__ static V add(V a, V b) { return a + b; }
-    __device__ static V mul(V a, V b) { return a * b; }
-    __device__ static double to_double(V a) { return a; }
-};
-
-template <typename T>
-__device__ __forceinline__ T shfl(T v, int src) {
-    return __shfl_sync(kFull, v, src);
-}
-__device__ __forceinline__ DF shfl_xor_v(DF v, int m) {
-    return {__shfl_xor_sync(kFull, v.hi, m), __shfl_xor_sync(kFull, v.lo, m)};
-}
-__device__ __forceinline__ double shfl_xor_v(double v, int m) { return __shfl_xor_sync(kFull, v, m); }
-
-// v[i] summed over the warp lands in lane i (31 shuffles for 32 values).
-template <typename T>
-__device__ __forceinline__ T reduce_scatter32(T (&v)[32]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const bool upper = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < off; ++i) {
-            const T send = upper ? v[i] : v[i + off];
-            const T keep = upper ? v[i + off] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, off);
-        }
-    }
-    return v[0];
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Position of offset (ox, oy) in the list of 40: row-major over [-3,3]^2 minus the core.
-__device__ __forceinline__ int offset_index(int ox, int oy) {
-    const int raw = (oy + 3) * 7 + (ox + 3);
-    int inner_before;
-    if (oy < -1) inner_before = 0;
-    else if (oy > 1) inner_before = 9;
-    else inner_before = 3 * (oy + 1) + (ox > 1 ? 3 : 0);
-    return raw - inner_before;
-}
 
 // ------------------------------------------------------------------------- P2M
 // One warp per leaf (row-major leaf index).  Writes the sorted charges in T, the
@@ -631,19 +523,6 @@ __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __res
 // a sum of up to 9 N_leaf terms whose constant parts cancel.
 constexpr int kP2PWarps = 8;
 constexpr int kP2PCap = 9 * 64;  // staged sources per warp per chunk
-
-template <typename T>
-struct SrcEntry;
-template <>
-struct alignas(8) SrcEntry<float> {
-    int off;
-    float f;
-};
-template <>
-struct alignas(16) SrcEntry<double> {
-    int off, pad;
-    double f;
-};
 
 template <typename T, int NP>
 __global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(

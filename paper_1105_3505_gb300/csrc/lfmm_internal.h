@@ -165,6 +165,77 @@ struct TreeView {
     int max_leaf_tgt = 0;
 };
 
+// ---------------------------------------------------------------- pruned trees / forests
+// Stream-ordered temporary, freed on scope exit.
+struct DevTemp {
+    void* ptr = nullptr;
+    cudaStream_t s = nullptr;
+    void reset(cudaStream_t st) {
+        if (ptr) cudaFreeAsync(ptr, s);
+        ptr = nullptr;
+        s = st;
+    }
+    ~DevTemp() {
+        if (ptr) cudaFreeAsync(ptr, s);
+    }
+};
+
+// Boxes k levels above the leaves over all problems of a forest.  The dense map lists
+// every cell of the level in parity-plane order (class c = (x & 1) + 2 (y & 1), then
+// problem, then the (x >> 1, y >> 1) grid row by row); compact ids number the
+// non-empty boxes in that order, so each parity class is one contiguous range.
+struct ForestLevel {
+    int64_t S = 0;             // map entries per class segment
+    int64_t* off = nullptr;    // [np] start of each problem inside a class segment (device)
+    int64_t* size = nullptr;   // [np] entries of each problem per class (0: not at this level)
+    int32_t* map = nullptr;    // [4 S] compact id or -1 (device)
+    int64_t nb = 0;            // compact boxes
+    int64_t cls[5] = {0};      // class ranges of the compact ids (host)
+    int64_t* d_cls = nullptr;  // same on the device
+    int64_t box_off = 0;       // offset of this level in the expansion arrays (boxes)
+    int32_t* bp = nullptr;     // [nb] problem of each box
+    int32_t* bxy = nullptr;    // [nb] x | y << 16 at the box's level
+    int32_t* par = nullptr;    // [nb] parent's compact id at k + 1, or -1
+    int32_t* il = nullptr;     // [nb][27] interaction list (slot order of the box's class)
+    int32_t* ch = nullptr;     // [nb][4] children's compact ids at k - 1 (k >= 1), -1 if empty
+};
+
+struct Forest {
+    int np = 0;
+    int64_t ns = 0, nt = 0;
+    int ls = 0, side = 1;                   // common leaf side 2^ls
+    std::vector<int32_t> x0, y0, K, L;      // per problem: root corner, root 2^K, leaf level
+    std::vector<int64_t> leaf_off;          // [np + 1] first absolute leaf of each problem
+    int64_t NL = 0;                         // leaves over all problems (dense per problem)
+    int kmax = -1;                          // deepest k with expansions (levels >= 2)
+    int max_src = 0, max_tgt = 0;           // largest leaf occupancies
+    int SW = 1;                             // leaves per near-field strip
+    int64_t total_boxes = 0;                // expansion rows over all levels
+    std::vector<ForestLevel> levels;        // k = 0 .. max(kmax, 0)
+    // device
+    int32_t *spid = nullptr, *tpid = nullptr;
+    int32_t *geo_x0 = nullptr, *geo_y0 = nullptr, *d_L = nullptr;
+    int64_t* d_leaf_off = nullptr;
+    int32_t *sbeg = nullptr, *tbeg = nullptr;   // [NL + 1] absolute bucket starts
+    int32_t *sloc = nullptr, *sperm = nullptr, *tloc = nullptr, *tperm = nullptr;
+    int4* strips = nullptr;                     // (problem, leaf row, first column, 0)
+    int32_t* n_strips_d = nullptr;
+    std::vector<void*> owned;
+    int64_t bytes = 0;
+    void release(cudaStream_t s);
+};
+
+// Builds the tree of every problem (offsets: n_problems + 1 entries, host memory).
+// Leaf side: the largest power of two <= max_leaf_side at which no leaf holds more than
+// leaf_size sources or targets.  Synchronises the stream.
+int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
+                 const int64_t* toff_h, int64_t nt, int np, int leaf_size, int max_leaf_side, cudaStream_t s,
+                 PhaseTimer* timer);
+template <typename T>
+int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
+                void* Cbox, double* u, double* un, double* uf, int tc_min_level, int* status, int num_sms,
+                cudaStream_t s);
+
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);
 cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
                         cudaStream_t s);

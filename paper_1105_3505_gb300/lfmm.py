@@ -17,6 +17,7 @@ from .build import LIB
 
 LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL = range(7)
 LFMM_FP64, LFMM_MIXED = 0, 1
+LFMM_TREE_AUTO, LFMM_TREE_UNIFORM, LFMM_TREE_PRUNED = 0, 1, 2
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lfmm.h")
 
@@ -30,7 +31,7 @@ class LfmmError(RuntimeError):
 class lfmm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("max_leaf_side", ctypes.c_int32), ("proxies_per_edge", ctypes.c_int32),
-                ("tc_min_level", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("tc_min_level", ctypes.c_int32), ("tree", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lfmm_plan_info(ctypes.Structure):
@@ -38,7 +39,8 @@ class lfmm_plan_info(ctypes.Structure):
                 ("y0", ctypes.c_int64), ("K", ctypes.c_int32), ("L", ctypes.c_int32),
                 ("leaf_side", ctypes.c_int32), ("P", ctypes.c_int32), ("P_pad", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_leaf_src", ctypes.c_int32),
-                ("max_leaf_tgt", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("max_leaf_tgt", ctypes.c_int32), ("device_bytes", ctypes.c_int64), ("tree", ctypes.c_int32),
+                ("n_problems", ctypes.c_int32), ("n_boxes", ctypes.c_int64)]
 
 
 _lib = None
@@ -57,6 +59,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     sig = {
         "lfmm_opts_default": (None, [ctypes.POINTER(lfmm_opts)]),
         "lfmm_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, i64, vp, i64, ctypes.POINTER(lfmm_opts), vp]),
+        "lfmm_forest_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, vp, vp, vp, i64, ctypes.POINTER(lfmm_opts),
+                                              vp]),
         "lfmm_eval": (ctypes.c_int, [vp, vp, vp, vp]),
         "lfmm_eval_parts": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lfmm_plan_destroy": (ctypes.c_int, [vp]),
@@ -117,10 +121,11 @@ def lfmm_opts_default() -> lfmm_opts:
 
 
 def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
-              proxies_per_edge: int = 64, tc_min_level: int = 0) -> lfmm_opts:
+              proxies_per_edge: int = 64, tc_min_level: int = 0, tree: int = LFMM_TREE_AUTO) -> lfmm_opts:
     o = lfmm_opts_default()
     o.precision, o.p, o.leaf_size = precision, p, leaf_size
     o.max_leaf_side, o.proxies_per_edge, o.tc_min_level = max_leaf_side, proxies_per_edge, tc_min_level
+    o.tree = tree
     return o
 
 
@@ -129,6 +134,20 @@ def lfmm_plan_create(src_xy, n_src: int, tgt_xy, n_tgt: int, opts: lfmm_opts | N
     st = load().lfmm_plan_create(ctypes.byref(h), _ptr(src_xy), int(n_src), _ptr(tgt_xy), int(n_tgt),
                                  ctypes.byref(opts) if opts is not None else None, _stream_handle(stream))
     _check(st, "lfmm_plan_create")
+    return h.value
+
+
+def lfmm_forest_create(src_xy, src_offsets, tgt_xy, tgt_offsets, opts: lfmm_opts | None, stream=None) -> int:
+    """src_offsets, tgt_offsets: n_problems + 1 int64 offsets (host numpy)."""
+    so = np.ascontiguousarray(np.asarray(src_offsets, dtype=np.int64))
+    to = np.ascontiguousarray(np.asarray(tgt_offsets, dtype=np.int64))
+    if so.shape != to.shape or so.ndim != 1 or so.shape[0] < 2:
+        raise ValueError("offsets must be two 1-D arrays of n_problems + 1 entries")
+    h = ctypes.c_void_p()
+    st = load().lfmm_forest_create(ctypes.byref(h), _ptr(src_xy), so.ctypes.data, _ptr(tgt_xy), to.ctypes.data,
+                                   so.shape[0] - 1, ctypes.byref(opts) if opts is not None else None,
+                                   _stream_handle(stream))
+    _check(st, "lfmm_forest_create")
     return h.value
 
 
@@ -239,12 +258,13 @@ class Plan:
     memory as f (numpy for numpy input, torch CUDA tensor for CUDA input)."""
 
     def __init__(self, src, tgt, precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64,
-                 max_leaf_side: int = 32, proxies_per_edge: int = 64, tc_min_level: int = 0, stream=None):
+                 max_leaf_side: int = 32, proxies_per_edge: int = 64, tc_min_level: int = 0,
+                 tree: int = LFMM_TREE_AUTO, stream=None):
         self.n_src, self.n_tgt = int(src.shape[0]), int(tgt.shape[0])
         self.stream = stream
         self.handle = lfmm_plan_create(src, self.n_src, tgt, self.n_tgt,
                                        make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge,
-                                                 tc_min_level), stream)
+                                                 tc_min_level, tree), stream)
 
     def status(self):
         lfmm_plan_status(self.handle, self.stream)
@@ -288,3 +308,20 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Forest(Plan):
+    """Many independent problems in one plan: ``Forest(src, src_offsets, tgt, tgt_offsets)``.
+
+    src, tgt: concatenated (n, 2) int32 points of all problems; problem i owns rows
+    src_offsets[i]:src_offsets[i+1] (and likewise for targets).  eval(f) takes f of all
+    sources and returns u of all targets, concatenated in the same order."""
+
+    def __init__(self, src, src_offsets, tgt, tgt_offsets, precision: int = LFMM_MIXED, p: int = 8,
+                 leaf_size: int = 64, max_leaf_side: int = 32, proxies_per_edge: int = 64, tc_min_level: int = 0,
+                 stream=None):
+        self.n_src, self.n_tgt = int(src.shape[0]), int(tgt.shape[0])
+        self.stream = stream
+        self.handle = lfmm_forest_create(src, src_offsets, tgt, tgt_offsets,
+                                         make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge,
+                                                   tc_min_level), stream)

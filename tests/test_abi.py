@@ -4,6 +4,8 @@ CPU only: nothing here launches a kernel."""
 import ctypes
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_1105_3505_gb300 import build, lfmm
@@ -51,3 +53,21 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.lfmm_plan_destroy(None) == lfmm.LFMM_OK
     with pytest.raises(lfmm.LfmmError):
         lfmm.lfmm_phi_table(0)
+
+
+def test_forest_offsets_validated_without_gpu(lib):
+    h = ctypes.c_void_p(123)
+    pts = np.zeros((4, 2), dtype=np.int32)
+    so = np.array([0, 2, 2, 4], dtype=np.int64)  # problem 1 has no sources
+    to = np.array([0, 1, 2, 4], dtype=np.int64)
+    st = lib.lfmm_forest_create(ctypes.byref(h), pts.ctypes.data, so.ctypes.data, pts.ctypes.data,
+                                to.ctypes.data, 3, None, None)
+    assert st == lfmm.LFMM_EINVAL and h.value is None
+    assert "problem 1" in lfmm.lfmm_last_error()
+    so = np.array([1, 2, 4], dtype=np.int64)  # does not start at 0
+    st = lib.lfmm_forest_create(ctypes.byref(h), pts.ctypes.data, so.ctypes.data, pts.ctypes.data,
+                                to.ctypes.data, 2, None, None)
+    assert st == lfmm.LFMM_EINVAL
+    o = lfmm.make_opts(tree=7)
+    st = lib.lfmm_plan_create(ctypes.byref(h), pts.ctypes.data, 4, pts.ctypes.data, 4, ctypes.byref(o), None)
+    assert st == lfmm.LFMM_EINVAL and "opts.tree" in lfmm.lfmm_last_error()

@@ -1,0 +1,193 @@
+"""Pruned trees and forests through the C ABI, against the CPU oracle.
+
+Pruned storage keeps only boxes with points below them (clustered inputs); a forest
+evaluates many independent problems in one plan.  Both must reach the same bars as
+the uniform tree: rel_err <= 1e-10 for binary64 at p = 16, <= 1e-6 mixed at p = 8.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1105_3505_gb300 import build, workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lfmm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_1105_3505_gb300 import lfmm as m
+    m.load()
+    torch.cuda.init()
+    return m
+
+
+def rel_err(u, ref):
+    return float(np.abs(np.asarray(u) - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def prec_of(lfmm, name):
+    return (lfmm.LFMM_FP64, 16, FP64_TOL) if name == "fp64" else (lfmm.LFMM_MIXED, 8, MIXED_TOL)
+
+
+def small_clustered(seed=7):
+    """Four Gaussian clusters and a line in a 4096^2 box: most leaves of the uniform
+    tree are empty."""
+    return workloads.clustered_4m(seed=seed, n_total=24000, n_clusters=4, sigma=40.0, n_segments=2,
+                                  seg_len=600.0, frac_lines=0.02, domain=4096)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pruned_clustered_full_oracle(lfmm, precision):
+    prob = small_clustered()
+    prec, p, tol = prec_of(lfmm, precision)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p) as pl:
+        u = pl.eval(prob.f)
+        info = pl.info()
+    assert info["tree"] == lfmm.LFMM_TREE_PRUNED  # chosen automatically
+    tree = oracle.uniform_tree(prob.src, prob.tgt, 64, 32)
+    assert (info["x0"], info["y0"], info["K"], info["L"], info["leaf_side"]) == \
+        (tree["x0"], tree["y0"], tree["K"], tree["L"], tree["side"])
+    assert rel_err(u, ref) <= tol, rel_err(u, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pruned_equals_uniform(lfmm, precision):
+    """Same boxes, operators and summation structure: the two storages agree to rounding."""
+    prob = workloads.uniform_box(6000, 4000, 700, seed=31)
+    prec, p, _ = prec_of(lfmm, precision)
+    with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p, tree=lfmm.LFMM_TREE_UNIFORM) as a:
+        ua = a.eval(prob.f)
+        ia = a.info()
+    with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p, tree=lfmm.LFMM_TREE_PRUNED) as b:
+        ub = b.eval(prob.f)
+        ib = b.info()
+        un, uf = b.eval_parts(prob.f)
+    assert ia["tree"] == lfmm.LFMM_TREE_UNIFORM and ib["tree"] == lfmm.LFMM_TREE_PRUNED
+    assert (ia["K"], ia["L"], ia["leaf_side"]) == (ib["K"], ib["L"], ib["leaf_side"])
+    scale = np.abs(ua).max()
+    assert np.abs(ua - ub).max() <= (1e-12 if precision == "fp64" else 1e-6) * scale
+    assert np.abs(ub - (un + uf)).max() <= 1e-12 * scale
+
+
+def forest_case(seed, n_problems, n_min=64, n_max=3000, targets_equal=True):
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=n_problems))).astype(int)
+    probs = []
+    for i, n in enumerate(sizes):
+        r = np.random.default_rng([seed, i])
+        side = int(np.ceil(4 * np.sqrt(n)))
+        x0, y0 = r.integers(-100000, 100000, size=2)
+        src = workloads.distinct_in_box(r, int(n), side, int(x0), int(y0))
+        if targets_equal:
+            tgt = src.copy()
+        else:
+            nt = max(1, int(n) // 3)
+            tgt = workloads.distinct_in_box(r, nt, side, int(x0), int(y0))
+        f = workloads.zero_sum(r.standard_normal(int(n)))
+        probs.append((src, tgt, f))
+    return probs
+
+
+def concat(probs):
+    src = np.ascontiguousarray(np.concatenate([p[0] for p in probs]).astype(np.int32))
+    tgt = np.ascontiguousarray(np.concatenate([p[1] for p in probs]).astype(np.int32))
+    f = np.concatenate([p[2] for p in probs])
+    so = np.concatenate([[0], np.cumsum([p[0].shape[0] for p in probs])]).astype(np.int64)
+    to = np.concatenate([[0], np.cumsum([p[1].shape[0] for p in probs])]).astype(np.int64)
+    return src, so, tgt, to, f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("targets_equal", [True, False])
+def test_forest_full_oracle(lfmm, precision, targets_equal):
+    probs = forest_case(zlib.crc32(f"forest{targets_equal}".encode()), 40, targets_equal=targets_equal)
+    src, so, tgt, to, f = concat(probs)
+    prec, p, tol = prec_of(lfmm, precision)
+    with lfmm.Forest(src, so, tgt, to, precision=prec, p=p) as fo:
+        u = fo.eval(f)
+        info = fo.info()
+    assert info["n_problems"] == 40 and info["tree"] == lfmm.LFMM_TREE_PRUNED
+    for i, (s, t, fi) in enumerate(probs):
+        ref = oracle.lattice_sum(s, fi, t)
+        ui = u[to[i]:to[i + 1]]
+        assert rel_err(ui, ref) <= tol, (i, s.shape[0], rel_err(ui, ref))
+
+
+def test_forest_edge_problems(lfmm):
+    """One-point problems, a single leaf, coincident sources, a problem far from the
+    others, and targets outside the sources' box - all in one forest."""
+    rng = np.random.default_rng(5)
+    probs = []
+    probs.append((np.array([[3, 4]], np.int32), np.array([[3, 4]], np.int32), np.array([1.5])))
+    probs.append((np.array([[0, 0]], np.int32), workloads.distinct_in_box(rng, 30, 20, -10, -10), np.array([2.0])))
+    s = workloads.distinct_in_box(rng, 50, 10, 1000, 1000)
+    probs.append((s, s.copy(), workloads.zero_sum(rng.standard_normal(50))))
+    probs.append((np.full((40, 2), 7, np.int32), workloads.distinct_in_box(rng, 25, 64), rng.standard_normal(40)))
+    off = (1 << 30) - 3000
+    s = workloads.distinct_in_box(rng, 1500, 400, off, -off)
+    probs.append((s, workloads.distinct_in_box(rng, 700, 400, off, -off), workloads.zero_sum(rng.standard_normal(1500))))
+    s = workloads.distinct_in_box(rng, 800, 300)
+    probs.append((s, workloads.distinct_in_box(rng, 200, 100, 2000, 2500), workloads.zero_sum(rng.standard_normal(800))))
+    src, so, tgt, to, f = concat(probs)
+    for precision in ("fp64", "mixed"):
+        prec, p, tol = prec_of(lfmm, precision)
+        with lfmm.Forest(src, so, tgt, to, precision=prec, p=p) as fo:
+            u = fo.eval(f)
+        for i, (s, t, fi) in enumerate(probs):
+            ref = oracle.lattice_sum(s, fi, t)
+            ui = u[to[i]:to[i + 1]]
+            if np.abs(ref).max() == 0.0:
+                # phi(0) = 0: the mixed path's table is deflated by phi0 = phi(s, 0), which
+                # fp32 rounds at the forest's leaf side; the residue is O(eps32 |phi0| |f|)
+                assert np.abs(ui).max() <= (0.0 if precision == "fp64" else 1e-6 * np.abs(fi).sum())
+            elif i == 5 and precision == "mixed":
+                # targets far from zero-sum sources: bound against the natural scale
+                d = (t[:, None, :].astype(np.int64) - s[None, :, :]).reshape(-1, 2)
+                ph = oracle.phi(d).reshape(t.shape[0], s.shape[0])
+                scale = (np.abs(fi)[None, :] * np.abs(ph - ph[:, :1])).sum(axis=1).max()
+                assert np.abs(ui - ref).max() <= MIXED_TOL * scale
+            else:
+                assert rel_err(ui, ref) <= tol, (precision, i, rel_err(ui, ref))
+
+
+def test_forest_4096_sampled(lfmm):
+    """The full batched workload: 4,096 problems, N_src log-uniform in [512, 8192] in a
+    box of side 4 sqrt(N), targets = sources; 24 problems checked in full."""
+    probs = workloads.forest_4096()
+    src, so, tgt, to, f = concat([(p.src, p.tgt, p.f) for p in probs])
+    dev = torch.device("cuda:0")
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (src, tgt, f))
+    with lfmm.Forest(s_d, so, t_d, to, precision=lfmm.LFMM_MIXED, p=8) as fo:
+        u = fo.eval(f_d).cpu().numpy()
+        info = fo.info()
+    assert info["n_problems"] == 4096 and np.isfinite(u).all()
+    for i in np.random.default_rng(11).choice(4096, 24, replace=False):
+        pr = probs[i]
+        ref = oracle.lattice_sum(pr.src, pr.f, pr.tgt)
+        assert rel_err(u[to[i]:to[i + 1]], ref) <= MIXED_TOL, i
+
+
+def test_clustered_4m_sampled(lfmm):
+    """The full clustered workload (4,194,304 points, 64 clusters + 16 segments) on the
+    pruned tree; 256 seeded targets checked against the oracle."""
+    prob = workloads.clustered_4m()
+    dev = torch.device("cuda:0")
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (prob.src, prob.tgt, prob.f))
+    with lfmm.Plan(s_d, t_d, precision=lfmm.LFMM_MIXED, p=8) as pl:
+        u = pl.eval(f_d).cpu().numpy()
+        info = pl.info()
+    assert info["tree"] == lfmm.LFMM_TREE_PRUNED and np.isfinite(u).all()
+    idx = np.random.default_rng(321).choice(prob.tgt.shape[0], 256, replace=False)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+    assert rel_err(u[idx], ref) <= MIXED_TOL
