@@ -46,7 +46,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lfmm", "reference"], default="lfmm")
     ap.add_argument("--p", type=int, default=8)
-    ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, oracle checks, cpu baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, oracle checks, cpu baseline, serving")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests of the serving stream replayed at its arrival times (0: skip)")
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -215,6 +218,77 @@ def traffic_for(kernel: str):
     src = os.path.join(ROOT, "paper_1105_3505_gb300", "csrc", e["source"])
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return e["bytes_per_launch"] if h == e.get("source_sha256_16") else None
+
+
+# ---------------------------------------------------------------- serving leg
+def _serve_gen(task):
+    seed, n, i = task
+    from paper_1105_3505_gb300 import workloads
+    return workloads.serve_request(workloads.serve_schedule(seed=seed, n_requests=n), i)
+
+
+def serve_leg(lfmm, n_requests: int, slots: int, check: int = 24):
+    """Replays the first n_requests of the serving stream (Poisson arrivals at 2,000
+    req/s, N_src log-uniform in [1e3, 1e6], uniform or four clusters, N_tgt = N_src/4,
+    tolerance 1e-6 or 1e-10) against an lfmm server: each request is submitted at its
+    arrival time; latency = submit -> result in host memory."""
+    import multiprocessing as mp
+    import threading
+    import oracle
+    from paper_1105_3505_gb300 import workloads
+    seed = 4
+    t_gen = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        reqs = pool.map(_serve_gen, [(seed, n_requests, i) for i in range(n_requests)], chunksize=4)
+        warm = pool.map(_serve_gen, [(seed + 101, 24, i) for i in range(24)], chunksize=2)
+    t_gen = time.perf_counter() - t_gen
+    with lfmm.Server(n_slots=slots) as sv:
+        # warm start: model-box operators of both precisions at the leaf sides that occur
+        for r in warm:
+            sv.wait(sv.submit(r.problem.src, r.problem.tgt, r.problem.f, r.tol))
+        tickets, submit_t = [], []
+        results = [None] * n_requests
+        done_t = [0.0] * n_requests
+
+        def waiter():
+            for i in range(n_requests):
+                while i >= len(tickets):
+                    time.sleep(0.0002)
+                results[i] = sv.wait(tickets[i])
+                done_t[i] = time.perf_counter()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for r in reqs:
+            delay = t0 + r.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            submit_t.append(time.perf_counter())
+            tickets.append(sv.submit(r.problem.src, r.problem.tgt, r.problem.f, r.tol))
+        th.join()
+    lat = np.array([st["total_ms"] for _, st in results])
+    qms = np.array([st["queue_ms"] for _, st in results])
+    pts = sum(r.problem.n_points for r in reqs)
+    span = max(done_t) - t0
+    errs = []
+    for i in np.random.default_rng(7).choice(n_requests, min(check, n_requests), replace=False):
+        r = reqs[i]
+        idx = np.random.default_rng(int(i)).choice(r.problem.tgt.shape[0], min(64, r.problem.tgt.shape[0]),
+                                                   replace=False)
+        ref = oracle.lattice_sum(r.problem.src, r.problem.f, r.problem.tgt[idx])
+        errs.append((r.tol, float(np.abs(results[i][0][idx] - ref).max() / np.abs(ref).max())))
+    return {"requests": n_requests, "rate_req_per_s": 2000.0, "slots": slots,
+            "arrival_span_s": float(reqs[-1].arrival_s), "completion_span_s": span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_mixed": float(np.percentile([l for l, r in zip(lat, reqs) if r.tol >= 1e-6], 50)),
+            "p50_ms_fp64": float(np.percentile([l for l, r in zip(lat, reqs) if r.tol < 1e-6], 50)),
+            "queue_p50_ms": float(np.percentile(qms, 50)), "queue_p99_ms": float(np.percentile(qms, 99)),
+            "Mpoints_per_s": pts / span / 1e6, "points": int(pts),
+            "checked": len(errs), "max_rel_err_1e-6_requests": max([e for t, e in errs if t >= 1e-6], default=None),
+            "max_rel_err_1e-10_requests": max([e for t, e in errs if t < 1e-6], default=None),
+            "generation_s": t_gen,
+            "note": "first n requests of the 20,000-request stream (seed 4), submitted at their arrival times"}
 
 
 # ---------------------------------------------------------------- main arm
@@ -388,6 +462,8 @@ def main():
         out["fp64_plain_p16"] = {"value": (ns + nt) / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
                                  "rel_err": float(np.abs(u64[idx] - ref).max() / scale)}
         out["cpu_baseline"] = cpu_baseline(prob)
+        if args.serve_requests > 0:
+            out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()

@@ -76,7 +76,7 @@ typedef struct lfmm_opts {
  * points that fill their root box.  PRUNED: the same levels and boxes, but only boxes
  * with a source or target below them are kept, each with explicit parent, children and
  * interaction list; the layout for clustered points, whose leaf level is set by the
- * densest cluster.  AUTO picks PRUNED when there are fewer points than leaves. */
+ * densest cluster.  AUTO picks PRUNED when more than half of the leaves are empty. */
 #define LFMM_TREE_AUTO 0
 #define LFMM_TREE_UNIFORM 1
 #define LFMM_TREE_PRUNED 2
@@ -157,6 +157,51 @@ const char* lfmm_status_string(int status);
 /* Detail of the last failure on the calling thread ("" if none). */
 const char* lfmm_last_error(void);
 
+/* ---- serving ----------------------------------------------------------------------- */
+/* A request loop for solves that arrive over time (different point sets and counts).
+ * The server runs n_slots requests at once, each on its own worker thread and CUDA
+ * stream; requests wait in arrival order and the oldest is admitted as soon as a slot
+ * is free and its estimated device footprint fits beside the running ones, within
+ * hbm_budget_bytes and the device's free memory (memory the stream-ordered pool holds
+ * unused counts as free).  Binary64 requests may hold at most n_slots - max(1,
+ * n_slots/4) slots; while they fill those, later mixed requests may pass them.  An admitted request builds its plan, evaluates and frees
+ * the plan on its stream, overlapping on the device with the others.  The model-box
+ * operators and phi tables stay resident (process-wide cache).  A request's result is
+ * independent of the requests that run beside it. */
+typedef struct lfmm_server lfmm_server;
+
+typedef struct lfmm_request {
+    const int32_t* src_xy;    /* 2*n_src int32, host or device; owned by the caller until  */
+    int64_t n_src;            /* lfmm_server_wait returns                                  */
+    const int32_t* tgt_xy;
+    int64_t n_tgt;
+    const double* f;          /* n_src, host or device                                     */
+    double* u;                /* n_tgt result, host or device                              */
+    double tol;               /* requested relative error: >= 1e-6 runs the mixed path at  */
+                              /* p = 8, smaller values the binary64 path at p = 16 with    */
+                              /* leaves of up to 128 points                                */
+} lfmm_request;
+
+typedef struct lfmm_request_stats {
+    int32_t status;           /* the request's own status                                   */
+    int32_t precision;        /* LFMM_MIXED or LFMM_FP64                                    */
+    double queue_ms;          /* submit -> admission                                        */
+    double run_ms;            /* admission -> result in u                                   */
+    double total_ms;          /* submit -> result in u (latency)                            */
+    int64_t device_bytes;     /* device memory of the request's plan                        */
+} lfmm_request_stats;
+
+/* n_slots in [1, 64]; hbm_budget_bytes = 0 for 80 % of the device memory available at
+ * creation.  Uses the current device. */
+int lfmm_server_create(lfmm_server** server, int32_t n_slots, int64_t hbm_budget_bytes);
+/* Queue a request (returns at once); *ticket identifies it for lfmm_server_wait. */
+int lfmm_server_submit(lfmm_server* server, const lfmm_request* req, int64_t* ticket);
+/* Block until the request is done; fills *stats (may be NULL) and returns its status.
+ * Each ticket can be waited for once. */
+int lfmm_server_wait(lfmm_server* server, int64_t ticket, lfmm_request_stats* stats);
+/* Finish the queued requests, stop the workers and free the server (NULL: no-op). */
+int lfmm_server_destroy(lfmm_server* server);
+
 /* ---- plan shape without allocation -------------------------------------------------- */
 /* The paper has no counterpart: this is a service entry point for callers that cannot
  * allocate device memory when they have to decide about a problem - an admission
@@ -167,7 +212,9 @@ const char* lfmm_last_error(void);
  * Fills *info with what lfmm_plan_create would produce for these points and opts: root
  * corner and K, leaf level L and leaf side, largest leaf occupancies, P and P_pad, and
  * device_bytes = the device memory the plan would own when its coordinates are given
- * in device memory.  Calls no cudaMalloc/cudaFree or any allocating routine.
+ * in device memory, and the storage the plan would pick (info->tree).  For pruned
+ * storage, device_bytes and n_boxes are those of the uniform layout (upper bounds).
+ * Calls no cudaMalloc/cudaFree or any allocating routine.
  *   src_xy, tgt_xy  8-byte aligned DEVICE memory (LFMM_EINVAL otherwise)
  *   stream          the work runs on it; the call synchronises it (results go to the host)
  * Limits: the leaf-count scratch is a static device array of LFMM_NOALLOC_SCRATCH_BYTES

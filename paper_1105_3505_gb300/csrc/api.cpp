@@ -221,7 +221,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
 
     // ---- root box (Sec. 6): lower-left corner of all points, side 2^K
     Temp t4;
-    if ((st = talloc(t4, 8 * sizeof(int), s))) return st;
+    if ((st = talloc(t4, 10 * sizeof(int), s))) return st;
     int* d4 = (int*)t4.ptr;
     LFMM_CUDA_TRY(launch_set4(d4, INT_MAX, INT_MAX, INT_MIN, INT_MIN, s));
     LFMM_CUDA_TRY(launch_bbox(src, p->ns, tgt, p->nt, d4, s));
@@ -248,6 +248,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     Temp cnt;
     int32_t *cs = nullptr, *ct = nullptr;  // counts at the chosen level
     int chosen = -1;
+    int64_t nonempty = 1;  // leaves holding a source or a target at the chosen level
     for (;;) {
         if (Lf > kMaxLevel)
             return fail(LFMM_EUNSUPPORTED, "tree would need more than 4^14 leaves");
@@ -262,11 +263,12 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
         LFMM_CUDA_TRY(launch_histogram(src, p->ns, tgt, p->nt, p->x0, p->y0, p->K - Lf, fs, ft, s));
         tree_timer->add_launches(1);
-        int m4[4] = {(int)std::min<int64_t>(p->ns, INT_MAX), (int)std::min<int64_t>(p->nt, INT_MAX), 0, 0};
+        // [max fine src, max fine tgt, max coarse src, max coarse tgt, non-empty fine, non-empty coarse]
+        int m4[6] = {(int)std::min<int64_t>(p->ns, INT_MAX), (int)std::min<int64_t>(p->nt, INT_MAX), 0, 0, 1, 1};
         if (Lf >= 1) {
-            LFMM_CUDA_TRY(launch_set4(d4 + 4, 0, 0, 0, 0, s));
+            LFMM_CUDA_TRY(cudaMemsetAsync(d4 + 4, 0, 6 * sizeof(int), s));
             LFMM_CUDA_TRY(launch_coarsen(fs, ft, nc, ccs, cct, d4 + 4, s));
-            tree_timer->add_launches(2);
+            tree_timer->add_launches(1);
             LFMM_CUDA_TRY(cudaMemcpyAsync(m4, d4 + 4, sizeof(m4), cudaMemcpyDeviceToHost, s));
             LFMM_CUDA_TRY(cudaStreamSynchronize(s));
         }
@@ -274,12 +276,14 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
             chosen = Lf - 1;
             p->max_src = m4[2];
             p->max_tgt = m4[3];
+            nonempty = m4[5];
             cs = ccs;
             ct = cct;
         } else if (std::max(m4[0], m4[1]) <= nleaf || Lf == p->K) {
             chosen = Lf;
             p->max_src = m4[0];
             p->max_tgt = m4[1];
+            nonempty = m4[4];
             cs = fs;
             ct = ft;
         }
@@ -296,9 +300,9 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     p->side = 1 << (p->K - p->L);
     const int64_t n_leaves = (int64_t)1 << (2 * p->L);
 
-    // ---- pruned storage: fewer points than leaves (or asked for)
+    // ---- pruned storage: most leaves empty (or asked for)
     const bool pruned = p->opts.tree == LFMM_TREE_PRUNED ||
-                        (p->opts.tree == LFMM_TREE_AUTO && p->ns + p->nt < n_leaves);
+                        (p->opts.tree == LFMM_TREE_AUTO && 2 * nonempty < n_leaves);
     if (pruned) {
         cnt.reset_now();
         tree_timer.reset();

@@ -919,12 +919,9 @@ static cudaError_t launch_translate(int level, const T* q, const T* u_par, const
                                     void* Cout, cudaStream_t s) {
     using C = TrCfg<T, NP>;
     using V = typename Mono<T>::V;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(translate_kernel<T, NP, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return clear_and_return(e);
-        attr_set = true;
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)translate_kernel<T, NP, MODE>, C::SMEM);
+        if (e != cudaSuccess) return e;
     }
     const int lg = MODE == kModeM2L ? level - 1 : level;
     const int64_t rows = (int64_t)1 << (2 * lg);
@@ -943,12 +940,9 @@ static cudaError_t launch_m2m_warp(const DeviceOps& ops, int k, int level, const
     if (blocks > 152 * 8) blocks = 152 * 8;
     constexpr size_t op_bytes = (size_t)4 * NP * NP * sizeof(T);
     if constexpr (op_bytes <= 64 * 1024) {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(m2m_warp_kernel<T, NP, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op_bytes);
-            if (e != cudaSuccess) return clear_and_return(e);
-            attr = true;
+        {
+            cudaError_t e = ensure_dynamic_smem((const void*)m2m_warp_kernel<T, NP, true>, op_bytes);
+            if (e != cudaSuccess) return e;
         }
         m2m_warp_kernel<T, NP, true><<<(int)blocks, 256, op_bytes, s>>>(level, q_child, (const T*)ops.m2m[k],
                                                                          (const V*)Q_child, q_parent, (V*)Q_parent);
@@ -973,12 +967,9 @@ static cudaError_t launch_m2l_splitk(const DeviceOps& ops, int k, int level, con
     const T* l2l = u_par ? (const T*)ops.l2l[k + 1] : nullptr;
     constexpr size_t smem = SkCfg<T, NP>::SMEM;
     static_assert(smem <= 227 * 1024, "split-K M2L block exceeds the shared memory of one SM");
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(m2l_splitk_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return clear_and_return(e);
-        attr = true;
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_splitk_kernel<T, NP>, smem);
+        if (e != cudaSuccess) return e;
     }
     const int64_t rows = (int64_t)1 << (2 * (level - 1));
     dim3 grid((unsigned)((rows + 31) / 32), 4);
@@ -1023,21 +1014,11 @@ static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const 
     const size_t tab_bytes = (size_t)(2 * ops.tab_H + 1) * ops.tab_W * sizeof(T);
     const size_t smem = ((tab_bytes + 15) & ~(size_t)15) + (size_t)kP2PWarps * kP2PCap * sizeof(SrcEntry<T>) +
                         (size_t)kP2PWarps * NP * sizeof(T);
-    static size_t attr_bytes = 0;
-    static int per_sm_cached = 0;
-    static size_t per_sm_for = 0;
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(p2p_leaf_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return clear_and_return(e);
-        attr_bytes = smem;
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)p2p_leaf_kernel<T, NP>, smem);
+        if (e != cudaSuccess) return e;
     }
-    if (per_sm_for != smem) {
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_leaf_kernel<T, NP>, kP2PWarps * 32, smem);
-        per_sm_cached = per_sm < 1 ? 1 : per_sm;
-        per_sm_for = smem;
-    }
+    const int per_sm_cached = blocks_per_sm((const void*)p2p_leaf_kernel<T, NP>, kP2PWarps * 32, smem);
     int64_t blocks = (t.n_leaves + kP2PWarps - 1) / kP2PWarps;
     const int64_t cap = (int64_t)num_sms * per_sm_cached;
     if (blocks > cap) blocks = cap;
@@ -1059,21 +1040,11 @@ static cudaError_t launch_p2p_strip(const TreeView& t, const DeviceOps& ops, int
     const size_t smem = tab_bytes + (size_t)Cfg::CAPS * sizeof(SrcEntry<T>) + (size_t)Cfg::MAXSW * NP * sizeof(T) +
                         (size_t)(3 * (Cfg::MAXSW + 2) + Cfg::MAXSW) * sizeof(V) + (size_t)2 * Cfg::CAPT * sizeof(int) +
                         (size_t)(3 * (Cfg::MAXSW + 3) + Cfg::MAXSW + 1) * sizeof(int);
-    static size_t attr_bytes = 0;
-    static int per_sm_cached = 0;
-    static size_t per_sm_for = 0;
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(p2p_strip_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return clear_and_return(e);
-        attr_bytes = smem;
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)p2p_strip_kernel<T, NP>, smem);
+        if (e != cudaSuccess) return e;
     }
-    if (per_sm_for != smem) {
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_strip_kernel<T, NP>, Cfg::WARPS * 32, smem);
-        per_sm_cached = per_sm < 1 ? 1 : per_sm;
-        per_sm_for = smem;
-    }
+    const int per_sm_cached = blocks_per_sm((const void*)p2p_strip_kernel<T, NP>, Cfg::WARPS * 32, smem);
     const int n = 1 << t.L;
     const int64_t strips = (int64_t)n * ((n + SW - 1) / SW);
     int64_t blocks = std::min<int64_t>(strips, (int64_t)num_sms * per_sm_cached);

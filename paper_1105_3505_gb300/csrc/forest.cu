@@ -1251,12 +1251,9 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             auto go = [&](auto np_tag) -> cudaError_t {
                 constexpr int NPc = decltype(np_tag)::value;
                 constexpr size_t smem = LCfg<T, NPc>::SMEM;
-                static bool attr = false;
-                if (!attr) {
-                    cudaError_t e = cudaFuncSetAttribute(m2l_list_kernel<T, NPc>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                    if (e != cudaSuccess) return clear_and_return(e);
-                    attr = true;
+                {
+                    cudaError_t e = ensure_dynamic_smem((const void*)m2l_list_kernel<T, NPc>, smem);
+                    if (e != cudaSuccess) return e;
                 }
                 m2l_list_kernel<T, NPc><<<grid, LCfg<T, NPc>::WARPS * 32, smem, s>>>(
                     lv.d_cls, lv.il, l2l ? lv.par : nullptr, Qx(k), l2l ? Ux(k + 1) : nullptr,
@@ -1281,16 +1278,11 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         LeafMap lm{l0.map, l0.off, l0.S};
         auto go = [&](auto np_tag) -> cudaError_t {
             constexpr int NPc = decltype(np_tag)::value;
-            static size_t attr_bytes = 0;
-            if (smem > attr_bytes) {
-                cudaError_t e = cudaFuncSetAttribute(p2p_list_kernel<T, NPc>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return clear_and_return(e);
-                attr_bytes = smem;
+            {
+                cudaError_t e = ensure_dynamic_smem((const void*)p2p_list_kernel<T, NPc>, smem);
+                if (e != cudaSuccess) return e;
             }
-            int per_sm = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p2p_list_kernel<T, NPc>, Cfg::WARPS * 32, smem);
-            per_sm = std::max(1, per_sm);
+            const int per_sm = blocks_per_sm((const void*)p2p_list_kernel<T, NPc>, Cfg::WARPS * 32, smem);
             p2p_list_kernel<T, NPc><<<num_sms * per_sm, Cfg::WARPS * 32, smem, s>>>(
                 F.strips, F.n_strips_d, g, lm, F.side, F.SW, F.sbeg, F.sloc, F.tbeg, F.tloc, F.tperm, f_sorted,
                 (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, far ? Ux(0) : nullptr, far ? Cm(0) : nullptr, Qm(0),

@@ -35,6 +35,13 @@ inline cudaError_t clear_and_return(cudaError_t e) {
     return e;
 }
 
+// Raises the dynamic shared-memory limit of kernel `func` to at least `bytes`
+// (thread-safe; each kernel's limit only grows).
+cudaError_t ensure_dynamic_smem(const void* func, size_t bytes);
+// Resident blocks per SM of `func` at this block size and dynamic shared memory
+// (cached, thread-safe; at least 1).
+int blocks_per_sm(const void* func, int threads, size_t smem);
+
 // ---------------------------------------------------------------- constants
 constexpr int kPhiHostRadius = 128;   // host phi table radius; eq. 3.1 beyond
 constexpr int kMaxLeafSide = 32;      // largest supported leaf side (P2P table in shared memory)
@@ -242,6 +249,9 @@ cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t 
 cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
                              int64_t x0, int64_t y0, int shift, int32_t* cnt_src,
                              int32_t* cnt_tgt, cudaStream_t s);
+// Sums 2x2 blocks of two Morton count arrays; max4[0..3] receive (atomic max) the
+// largest fine source / target count and the largest coarse ones, max4[4..5] (atomic
+// add) the number of non-empty fine and coarse boxes.  max4 must be zeroed first.
 cudaError_t launch_coarsen(const int32_t* fs, const int32_t* ft, int64_t n_coarse, int32_t* cs,
                            int32_t* ct, int* max4, cudaStream_t s);
 // Exclusive scan over the 4^L leaves in row-major order of two Morton-indexed count

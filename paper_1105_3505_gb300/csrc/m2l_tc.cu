@@ -451,11 +451,9 @@ cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q
                           const float* u_parent, const void* C_parent, float* u_level, void* C_level, int* status,
                           cudaStream_t s) {
     constexpr size_t smem = 1024 + sizeof(float) * (3 * 2 * 1024 + 2 * kTcThreads * 32);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(m2l_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return clear_and_return(e);
-        attr = true;
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tc_kernel, smem);
+        if (e != cudaSuccess) return e;
     }
     const int64_t rows = (int64_t)1 << (2 * (level - 1));
     dim3 grid((unsigned)((rows + kTcThreads - 1) / kTcThreads), 4);

@@ -115,6 +115,7 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     int L_try = std::min(K, std::max(L_side, L_pig));
     int Lf = std::min(K, L_try + 1);
     int L = -1, msrc = 0, mtgt = 0;
+    int64_t nonempty = 1;
     for (;;) {
         if (Lf > kNoAllocMaxLevel)
             return fail(LFMM_EINVAL, "tree needs counting on level " + std::to_string(Lf) +
@@ -125,9 +126,9 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
         int32_t *fs = scratch, *ft = scratch + nf, *cs = ft + nf, *ct = cs + nc;
         LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
         LFMM_CUDA_TRY(launch_histogram(src_xy, n_src, tgt_xy, n_tgt, h4[0], h4[1], K - Lf, fs, ft, s));
-        int m4[4] = {(int)n_src, (int)n_tgt, 0, 0};
+        int m4[6] = {(int)n_src, (int)n_tgt, 0, 0, 1, 1};
         if (Lf >= 1) {
-            LFMM_CUDA_TRY(launch_set4(d4 + 4, 0, 0, 0, 0, s));
+            LFMM_CUDA_TRY(cudaMemsetAsync(d4 + 4, 0, 6 * sizeof(int), s));
             LFMM_CUDA_TRY(launch_coarsen(fs, ft, nc, cs, ct, d4 + 4, s));
             LFMM_CUDA_TRY(cudaMemcpyAsync(m4, d4 + 4, sizeof(m4), cudaMemcpyDeviceToHost, s));
             LFMM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -136,10 +137,12 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
             L = Lf - 1;
             msrc = m4[2];
             mtgt = m4[3];
+            nonempty = m4[5];
         } else if (std::max(m4[0], m4[1]) <= o.leaf_size || Lf == K) {
             L = Lf;
             msrc = m4[0];
             mtgt = m4[1];
+            nonempty = m4[4];
         }
         if (L >= 0) break;
         Lf = std::min(K, Lf + 2);
@@ -169,5 +172,10 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     info->max_leaf_src = msrc;
     info->max_leaf_tgt = mtgt;
     info->device_bytes = bytes;
+    info->tree = (o.tree == LFMM_TREE_PRUNED || (o.tree == LFMM_TREE_AUTO && 2 * nonempty < n_leaves))
+                     ? LFMM_TREE_PRUNED
+                     : LFMM_TREE_UNIFORM;
+    info->n_problems = 1;
+    info->n_boxes = boxes;
     return LFMM_OK;
 }

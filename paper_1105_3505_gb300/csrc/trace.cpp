@@ -1,6 +1,8 @@
 // Launch counting and per-phase CUDA-event timing (see lfmm_profile_* in include/lfmm.h).
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "lfmm_internal.h"
 
@@ -100,3 +102,38 @@ int lfmm_profile_read(double* ms, int64_t* launches, int reset) {
 int64_t lfmm_launch_count(void) { return lfmm::g_launches.load(); }
 
 }  // extern "C"
+
+namespace lfmm {
+
+namespace {
+std::mutex g_attr_mu;
+std::map<const void*, size_t> g_smem_limit;
+std::map<std::pair<const void*, std::pair<int, size_t>>, int> g_occ;
+}  // namespace
+
+cudaError_t ensure_dynamic_smem(const void* func, size_t bytes) {
+    std::lock_guard<std::mutex> g(g_attr_mu);
+    size_t& cur = g_smem_limit[func];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return clear_and_return(e);
+    cur = bytes;
+    return cudaSuccess;
+}
+
+int blocks_per_sm(const void* func, int threads, size_t smem) {
+    std::lock_guard<std::mutex> g(g_attr_mu);
+    auto key = std::make_pair(func, std::make_pair(threads, smem));
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+    int n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    n = n < 1 ? 1 : n;
+    g_occ[key] = n;
+    return n;
+}
+
+}  // namespace lfmm

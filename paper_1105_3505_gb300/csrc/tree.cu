@@ -89,7 +89,7 @@ __global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
 __global__ void coarsen_kernel(const int4* __restrict__ fs, const int4* __restrict__ ft,
                                int64_t n_coarse, int32_t* __restrict__ cs,
                                int32_t* __restrict__ ct, int* __restrict__ max4) {
-    int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int m0 = 0, m1 = 0, m2 = 0, m3 = 0, nf = 0, nc = 0;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_coarse;
          b += (int64_t)gridDim.x * blockDim.x) {
         const int4 s = fs[b], t = ft[b];
@@ -100,16 +100,24 @@ __global__ void coarsen_kernel(const int4* __restrict__ fs, const int4* __restri
         m1 = max(m1, max(max(t.x, t.y), max(t.z, t.w)));
         m2 = max(m2, ss);
         m3 = max(m3, tt);
+        nf += (s.x + t.x > 0) + (s.y + t.y > 0) + (s.z + t.z > 0) + (s.w + t.w > 0);
+        nc += ss + tt > 0;
     }
     m0 = warp_max(m0);
     m1 = warp_max(m1);
     m2 = warp_max(m2);
     m3 = warp_max(m3);
+    for (int o = 16; o; o >>= 1) {
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+    }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(max4 + 0, m0);
         atomicMax(max4 + 1, m1);
         atomicMax(max4 + 2, m2);
         atomicMax(max4 + 3, m3);
+        atomicAdd(max4 + 4, nf);
+        atomicAdd(max4 + 5, nc);
     }
 }
 

@@ -43,6 +43,16 @@ class lfmm_plan_info(ctypes.Structure):
                 ("n_problems", ctypes.c_int32), ("n_boxes", ctypes.c_int64)]
 
 
+class lfmm_request(ctypes.Structure):
+    _fields_ = [("src_xy", ctypes.c_void_p), ("n_src", ctypes.c_int64), ("tgt_xy", ctypes.c_void_p),
+                ("n_tgt", ctypes.c_int64), ("f", ctypes.c_void_p), ("u", ctypes.c_void_p), ("tol", ctypes.c_double)]
+
+
+class lfmm_request_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("precision", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -78,6 +88,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_launch_count": (ctypes.c_int64, []),
         "lfmm_plan_shape_noalloc": (ctypes.c_int, [vp, i64, vp, i64, ctypes.POINTER(lfmm_opts),
                                                    ctypes.POINTER(lfmm_plan_info), vp]),
+        "lfmm_server_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i64]),
+        "lfmm_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_request), ctypes.POINTER(i64)]),
+        "lfmm_server_wait": (ctypes.c_int, [vp, i64, ctypes.POINTER(lfmm_request_stats)]),
+        "lfmm_server_destroy": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -325,3 +339,57 @@ class Forest(Plan):
         self.handle = lfmm_forest_create(src, src_offsets, tgt, tgt_offsets,
                                          make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge,
                                                    tc_min_level), stream)
+
+
+class Server:
+    """Request loop with continuous admission (lfmm_server_* in include/lfmm.h).
+
+    submit(src, tgt, f, tol) queues a solve and returns a ticket; wait(ticket) blocks
+    until it is done and returns (u, stats).  The arrays passed to submit are kept
+    referenced here until the ticket has been waited for."""
+
+    def __init__(self, n_slots: int = 4, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().lfmm_server_create(ctypes.byref(h), int(n_slots), int(hbm_budget_bytes)),
+               "lfmm_server_create")
+        self.handle = h.value
+        self._live = {}
+
+    def submit(self, src, tgt, f, tol: float, out=None) -> int:
+        if out is None:
+            if isinstance(f, np.ndarray):
+                out = np.empty(int(tgt.shape[0]), dtype=np.float64)
+            else:
+                import torch
+                out = torch.empty(int(tgt.shape[0]), dtype=torch.float64, device=f.device)
+        req = lfmm_request(_ptr(src), int(src.shape[0]), _ptr(tgt), int(tgt.shape[0]), _ptr(f), _ptr(out),
+                           float(tol))
+        t = ctypes.c_int64()
+        _check(load().lfmm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)), "lfmm_server_submit")
+        self._live[t.value] = (src, tgt, f, out)
+        return t.value
+
+    def wait(self, ticket: int):
+        st = lfmm_request_stats()
+        status = load().lfmm_server_wait(self.handle, int(ticket), ctypes.byref(st))
+        _, _, _, out = self._live.pop(ticket)
+        _check(status, "lfmm_server_wait")
+        return out, {name: getattr(st, name) for name, _ in lfmm_request_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().lfmm_server_destroy(self.handle), "lfmm_server_destroy")
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -162,41 +162,57 @@ class Request:
     problem: Problem
 
 
-def serve_stream(seed: int = 4, n_requests: int = 20_000, rate_per_s: float = 2000.0,
-                 n_min: float = 1e3, n_max: float = 1e6):
-    """Yields Requests lazily (the whole stream does not fit in host memory at once)."""
+def serve_schedule(seed: int = 4, n_requests: int = 20_000, rate_per_s: float = 2000.0,
+                   n_min: float = 1e3, n_max: float = 1e6) -> dict:
+    """Arrival times (Poisson at rate_per_s), sizes (log-uniform N_src), point-set kinds
+    (0 uniform, 1 four clusters) and tolerances (1e-6 or 1e-10) of the serving stream."""
     top = np.random.default_rng(seed)
     gaps = top.exponential(1.0 / rate_per_s, size=n_requests)
-    arrivals = np.cumsum(gaps)
-    sizes = np.rint(np.exp(top.uniform(np.log(n_min), np.log(n_max), size=n_requests))).astype(np.int64)
-    kinds = top.integers(0, 2, size=n_requests)        # 0 uniform, 1 four clusters
-    tols = np.where(top.integers(0, 2, size=n_requests) == 0, 1e-6, 1e-10)
-    ss = np.random.SeedSequence(seed + 1_000_003).spawn(n_requests)
+    return {"seed": seed,
+            "arrival_s": np.cumsum(gaps),
+            "n_src": np.rint(np.exp(top.uniform(np.log(n_min), np.log(n_max), size=n_requests))).astype(np.int64),
+            "kind": top.integers(0, 2, size=n_requests),
+            "tol": np.where(top.integers(0, 2, size=n_requests) == 0, 1e-6, 1e-10)}
+
+
+def serve_request(schedule: dict, i: int) -> Request:
+    """Request i of a schedule; independent of the others (its own seed), so requests can
+    be generated in any order or in parallel."""
+    seed = schedule["seed"]
+    rng = np.random.default_rng(np.random.SeedSequence([seed + 1_000_003, i]))
+    n = int(schedule["n_src"][i])
+    side = int(math.ceil(4.0 * math.sqrt(n)))
+    if int(schedule["kind"][i]) == 0:
+        src = distinct_in_box(rng, n, side)
+    else:
+        seen: set = set()
+        centres = rng.uniform(0, side, size=(4, 2))
+        per = [n // 4 + (1 if j < n % 4 else 0) for j in range(4)]
+        parts = []
+        for c, k in zip(centres, per):
+            got = np.empty((0, 2), dtype=np.int32)
+            while got.shape[0] < k:
+                need = k - got.shape[0]
+                cand = np.rint(rng.normal(c, side / 16.0, size=(need + need // 8 + 16, 2))).astype(np.int32)
+                got = np.concatenate([got, _take_new(cand, seen, need)])
+            parts.append(got)
+        src = np.ascontiguousarray(np.concatenate(parts))
+    n_t = max(1, n // 4)
+    tgt = np.empty((n_t, 2), dtype=np.int32)
+    tgt[:, 0] = rng.integers(0, side, size=n_t)
+    tgt[:, 1] = rng.integers(0, side, size=n_t)
+    f = zero_sum(rng.standard_normal(n))
+    return Request(i, float(schedule["arrival_s"][i]), float(schedule["tol"][i]),
+                   Problem(f"req_{i}", src, tgt, f, False))
+
+
+def serve_stream(seed: int = 4, n_requests: int = 20_000, rate_per_s: float = 2000.0,
+                 n_min: float = 1e3, n_max: float = 1e6):
+    """Yields the Requests of the serving stream lazily (all of them do not fit in host
+    memory at once)."""
+    sch = serve_schedule(seed, n_requests, rate_per_s, n_min, n_max)
     for i in range(n_requests):
-        rng = np.random.default_rng(ss[i])
-        n = int(sizes[i])
-        side = int(math.ceil(4.0 * math.sqrt(n)))
-        if kinds[i] == 0:
-            src = distinct_in_box(rng, n, side)
-        else:
-            seen: set = set()
-            centres = rng.uniform(0, side, size=(4, 2))
-            per = [n // 4 + (1 if j < n % 4 else 0) for j in range(4)]
-            parts = []
-            for c, k in zip(centres, per):
-                got = np.empty((0, 2), dtype=np.int32)
-                while got.shape[0] < k:
-                    need = k - got.shape[0]
-                    cand = np.rint(rng.normal(c, side / 16.0, size=(need + need // 8 + 16, 2))).astype(np.int32)
-                    got = np.concatenate([got, _take_new(cand, seen, need)])
-                parts.append(got)
-            src = np.ascontiguousarray(np.concatenate(parts))
-        n_t = max(1, n // 4)
-        tgt = np.empty((n_t, 2), dtype=np.int32)
-        tgt[:, 0] = rng.integers(0, side, size=n_t)
-        tgt[:, 1] = rng.integers(0, side, size=n_t)
-        f = zero_sum(rng.standard_normal(n))
-        yield Request(i, float(arrivals[i]), float(tols[i]), Problem(f"req_{i}", src, tgt, f, False))
+        yield serve_request(sch, i)
 
 
 WORKLOADS = {

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 FIELDS = ["n_src", "n_tgt", "x0", "y0", "K", "L", "leaf_side", "P", "P_pad", "precision",
-          "max_leaf_src", "max_leaf_tgt", "device_bytes"]
+          "max_leaf_src", "max_leaf_tgt", "device_bytes", "tree", "n_problems", "n_boxes"]
 
 
 @pytest.fixture(scope="module")
