@@ -52,13 +52,17 @@ extern "C" {
 /* LFMM_FP64: every step in binary64 (the plain path, relative error <= 1e-10 at p >= 16).
  * LFMM_MIXED: near field, expansions and translations in binary32, charges rounded
  *   to binary32, the per-target sum of near and far parts in binary64 (<= 1e-6). */
-#define LFMM_FP64 0
-#define LFMM_MIXED 1
+#define LFMM_FP64 0   /* every step in binary64                                         */
+#define LFMM_MIXED 1  /* binary32 near and far field, compensated charge channel, TF32    */
+                      /* tensor-core M2L; binary64 final sum (relative error ~1e-7)       */
+#define LFMM_DF 2     /* binary64 inputs and outputs, every step in float-float pairs     */
+                      /* (~48 bits) on the FP32 pipes: binary64-level accuracy at a       */
+                      /* fraction of the binary64 pipe's cost                             */
 
 typedef struct lfmm_plan lfmm_plan;
 
 typedef struct lfmm_opts {
-    int32_t precision;        /* LFMM_FP64 or LFMM_MIXED                                      */
+    int32_t precision;        /* LFMM_FP64, LFMM_MIXED or LFMM_DF                             */
     int32_t p;                /* expansion order, 2 <= p <= 17; skeleton size P = 4(p-1)        */
                               /* (Table 4.1: P ~ 27 gives 1e-8, P ~ 49 gives 1e-13)           */
     int32_t leaf_size;        /* N_leaf of Sec. 6: the leaf level is the coarsest level whose  */
@@ -163,8 +167,9 @@ const char* lfmm_last_error(void);
  * stream; requests wait in arrival order and the oldest is admitted as soon as a slot
  * is free and its estimated device footprint fits beside the running ones, within
  * hbm_budget_bytes and the device's free memory (memory the stream-ordered pool holds
- * unused counts as free).  Binary64 requests may hold at most n_slots - max(1,
- * n_slots/4) slots; while they fill those, later mixed requests may pass them.  An admitted request builds its plan, evaluates and frees
+ * unused counts as free).  Requests at binary64-level tolerance may hold at most
+ * n_slots - max(1, n_slots/4) slots; while they fill those, later mixed requests may
+ * pass them.  An admitted request builds its plan, evaluates and frees
  * the plan on its stream, overlapping on the device with the others.  The model-box
  * operators and phi tables stay resident (process-wide cache).  A request's result is
  * independent of the requests that run beside it. */
@@ -178,13 +183,13 @@ typedef struct lfmm_request {
     const double* f;          /* n_src, host or device                                     */
     double* u;                /* n_tgt result, host or device                              */
     double tol;               /* requested relative error: >= 1e-6 runs the mixed path at  */
-                              /* p = 8, smaller values the binary64 path at p = 16 with    */
-                              /* leaves of up to 128 points                                */
+                              /* p = 8, smaller values the float-float path (LFMM_DF) at   */
+                              /* p = 16 with leaves of up to 128 points                    */
 } lfmm_request;
 
 typedef struct lfmm_request_stats {
     int32_t status;           /* the request's own status                                   */
-    int32_t precision;        /* LFMM_MIXED or LFMM_FP64                                    */
+    int32_t precision;        /* LFMM_MIXED or LFMM_DF                                      */
     double queue_ms;          /* submit -> admission                                        */
     double run_ms;            /* admission -> result in u                                   */
     double total_ms;          /* submit -> result in u (latency)                            */

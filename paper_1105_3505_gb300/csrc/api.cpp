@@ -125,8 +125,8 @@ void free_plan_buffers(lfmm_plan* p) {
 }
 
 int validate_opts(const lfmm_opts& o) {
-    if (o.precision != LFMM_FP64 && o.precision != LFMM_MIXED)
-        return fail(LFMM_EINVAL, "opts.precision must be LFMM_FP64 or LFMM_MIXED");
+    if (o.precision != LFMM_FP64 && o.precision != LFMM_MIXED && o.precision != LFMM_DF)
+        return fail(LFMM_EINVAL, "opts.precision must be LFMM_FP64, LFMM_MIXED or LFMM_DF");
     if (o.p < 2 || o.p > 17) return fail(LFMM_EINVAL, "opts.p must be in [2, 17]");
     if (o.leaf_size < 1) return fail(LFMM_EINVAL, "opts.leaf_size must be >= 1");
     if (o.max_leaf_side < 1 || o.max_leaf_side > kMaxLeafSide ||
@@ -459,6 +459,7 @@ int eval_common(lfmm_plan* p, const double* f, double* u, double* un, double* uf
         host_out[i] = true;
     }
     int st = p->opts.precision == LFMM_MIXED ? eval_impl<float>(p, fd, douts[0], douts[1], douts[2], s)
+             : p->opts.precision == LFMM_DF  ? eval_impl<DF>(p, fd, douts[0], douts[1], douts[2], s)
                                              : eval_impl<double>(p, fd, douts[0], douts[1], douts[2], s);
     if (st) return st;
     bool any_host = false;

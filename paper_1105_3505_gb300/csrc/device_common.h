@@ -7,17 +7,17 @@
 
 #include <cstdint>
 
+#include "lfmm_internal.h"
+
 namespace lfmm {
 namespace {
+
+using ::fma;  // the float / double overloads stay visible beside the DF one below
 
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------------- compensated scalars
 // Error-free transformations (Knuth two-sum, FMA two-product) on float pairs.
-struct DF {
-    float hi, lo;
-};
-
 __device__ __forceinline__ DF fast_two_sum(float a, float b) {
     const float s = a + b;
     return {s, b - (s - a)};
@@ -43,6 +43,38 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
     return fast_two_sum(p, e);
 }
 
+// ---- DF as a number (element type of the LFMM_DF path)
+__device__ __forceinline__ DF operator-(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF operator+(DF a, DF b) { return df_add(a, b); }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return df_add(a, -b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) { return df_mul(a, b); }
+__device__ __forceinline__ DF& operator+=(DF& a, DF b) { return a = df_add(a, b); }
+__device__ __forceinline__ DF& operator-=(DF& a, DF b) { return a = df_add(a, -b); }
+// a * b + c: the exact product (FMA two-product, 4 operations) added to c by two-sum
+// (6) with the low parts (2) and one renormalisation (3): 15 binary32 operations
+__device__ __forceinline__ DF fma(DF a, DF b, DF c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi;
+    const float bb = s - p;
+    const float err = (p - (s - bb)) + (c.hi - bb);
+    const float t = (err + c.lo) + e;
+    const float hi = s + t;
+    return DF{hi, t - (hi - s)};
+}
+
+// read-only loads of any element type
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) {
+    return __ldg(p);
+}
+__device__ __forceinline__ DF ldg(const DF* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return DF{v.x, v.y};
+}
+
 template <typename T>
 struct Mono;
 template <>
@@ -54,6 +86,16 @@ struct Mono<float> {
         return {h, (float)(x - (double)h)};
     }
     __device__ static V make(float hi, float lo) { return {hi, lo}; }
+    __device__ static V add(V a, V b) { return df_add(a, b); }
+    __device__ static V mul(V a, V b) { return df_mul(a, b); }
+    __device__ static double to_double(V a) { return (double)a.hi + (double)a.lo; }
+};
+template <>
+struct Mono<DF> {
+    using V = DF;
+    __device__ static V zero() { return {0.f, 0.f}; }
+    __device__ static V from_double(double x) { return DF(x); }
+    __device__ static V make(DF hi, DF lo) { return df_add(hi, lo); }
     __device__ static V add(V a, V b) { return df_add(a, b); }
     __device__ static V mul(V a, V b) { return df_mul(a, b); }
     __device__ static double to_double(V a) { return (double)a.hi + (double)a.lo; }
@@ -73,10 +115,14 @@ template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) {
     return __shfl_sync(kFull, v, src);
 }
+__device__ __forceinline__ DF shfl(DF v, int src) {
+    return DF{__shfl_sync(kFull, v.hi, src), __shfl_sync(kFull, v.lo, src)};
+}
 __device__ __forceinline__ DF shfl_xor_v(DF v, int m) {
     return {__shfl_xor_sync(kFull, v.hi, m), __shfl_xor_sync(kFull, v.lo, m)};
 }
 __device__ __forceinline__ double shfl_xor_v(double v, int m) { return __shfl_xor_sync(kFull, v, m); }
+__device__ __forceinline__ float shfl_xor_v(float v, int m) { return __shfl_xor_sync(kFull, v, m); }
 
 // v[i] summed over the warp lands in lane i (31 shuffles for 32 values).
 template <typename T>
@@ -89,7 +135,7 @@ __device__ __forceinline__ T reduce_scatter32(T (&v)[32]) {
         for (int i = 0; i < off; ++i) {
             const T send = upper ? v[i] : v[i + off];
             const T keep = upper ? v[i + off] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, off);
+            v[i] = keep + shfl_xor_v(send, off);
         }
     }
     return v[0];
@@ -130,6 +176,11 @@ template <>
 struct alignas(16) SrcEntry<double> {
     int off, pad;
     double f;
+};
+template <>
+struct alignas(16) SrcEntry<DF> {
+    int off, pad;
+    DF f;
 };
 
 // The 27 interaction-list slots of a box of parity class (px, py): offsets (dx, dy) of

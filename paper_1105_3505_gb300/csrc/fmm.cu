@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                 const T fk = shfl(fj, k);
                 const T* row = tofsT + (size_t)shfl(J, k) * NP;
 #pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(__ldg(row + lane + 32 * i), fk, acc[i]);
+                for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), fk, acc[i]);
             }
         }
 #pragma unroll
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(
                 if (uhat) {
                     const T* row = tofsT + (size_t)(tx + side * ty) * NP;
 #pragma unroll 8
-                    for (int p = 0; p < NP; ++p) far = fma(__ldg(row + p), s_uhat[p], far);
+                    for (int p = 0; p < NP; ++p) far = fma(ldg(row + p), s_uhat[p], far);
                 }
                 const int dst = tperm[t0 + lane];
                 const double dn = (double)acc + near_const;
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
                         const T* row = tofsT + (size_t)Jq * NP;
                         const T* uq = s_uhat + lq * NP;
 #pragma unroll
-                        for (int i = 0; i < PL; ++i) w = fma(__ldg(row + lane + 32 * i), uq[lane + 32 * i], w);
+                        for (int i = 0; i < PL; ++i) w = fma(ldg(row + lane + 32 * i), uq[lane + 32 * i], w);
                     }
                     part[q] = w;
                 }
@@ -1084,5 +1084,6 @@ cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_s
 
 LFMM_INSTANTIATE(float)
 LFMM_INSTANTIATE(double)
+LFMM_INSTANTIATE(DF)
 
 }  // namespace lfmm

@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t
                 const T fk = shfl(fj, kk);
                 const T* row = tofsT + (size_t)shfl(J, kk) * NP;
 #pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(__ldg(row + lane + 32 * i), fk, acc[i]);
+                for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), fk, acc[i]);
             }
         }
 #pragma unroll
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256) m2m_list_kernel(int64_t nb, const int32_t
                 const T v = shfl(xv[c], l);
                 const T* row = m2m + (size_t)(32 * c + l) * NP;
 #pragma unroll
-                for (int i = 0; i < PL; ++i) acc[c][i] = fma(__ldg(row + lane + 32 * i), v, acc[c][i]);
+                for (int i = 0; i < PL; ++i) acc[c][i] = fma(ldg(row + lane + 32 * i), v, acc[c][i]);
             }
         }
 #pragma unroll
@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
                         const T* row = tofsT + (size_t)Jq * NP;
                         const T* uq = s_uhat + lq * NP;
 #pragma unroll
-                        for (int i = 0; i < PL; ++i) w = fma(__ldg(row + lane + 32 * i), uq[lane + 32 * i], w);
+                        for (int i = 0; i < PL; ++i) w = fma(ldg(row + lane + 32 * i), uq[lane + 32 * i], w);
                     }
                     part[qq] = w;
                 }
@@ -1300,5 +1300,7 @@ template int forest_eval<float>(const Forest&, const DeviceOps&, const double*, 
                                 double*, double*, double*, int, int*, int, cudaStream_t);
 template int forest_eval<double>(const Forest&, const DeviceOps&, const double*, double*, double*, double*, void*,
                                  void*, double*, double*, double*, int, int*, int, cudaStream_t);
+template int forest_eval<DF>(const Forest&, const DeviceOps&, const double*, DF*, DF*, DF*, void*, void*, double*,
+                             double*, double*, int, int*, int, cudaStream_t);
 
 }  // namespace lfmm

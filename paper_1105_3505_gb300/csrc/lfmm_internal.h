@@ -15,6 +15,19 @@
 
 namespace lfmm {
 
+// ---------------------------------------------------------------- float-float numbers
+// hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits in two binary32 values.
+// Element type of the LFMM_DF path (and of the compensated total-charge / incoming-
+// constant channel of the mixed path); its arithmetic (device_common.h) runs on the
+// FP32 pipes.
+struct DF {
+    float hi, lo;
+    DF() = default;
+    __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit DF(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
@@ -104,7 +117,7 @@ struct ModelOps {
     std::vector<double> tofs;     // P0 x leaf_side^2, row-major
     std::vector<LevelOps> levels; // 0 = leaf, k = k levels above
     std::mutex mu;                // guards growth and device uploads
-    std::unique_ptr<DeviceOps> dev[2][2];  // [precision][NP==64]
+    std::unique_ptr<DeviceOps> dev[3][2];  // [precision][NP==64]
 };
 
 // Returns the cached operators for (leaf_side, P, ppe) with at least n_levels levels.

@@ -81,7 +81,8 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     lfmm_opts o;
     if (opts) o = *opts;
     else lfmm_opts_default(&o);
-    if (o.precision != LFMM_FP64 && o.precision != LFMM_MIXED) return fail(LFMM_EINVAL, "bad opts.precision");
+    if (o.precision != LFMM_FP64 && o.precision != LFMM_MIXED && o.precision != LFMM_DF)
+        return fail(LFMM_EINVAL, "bad opts.precision");
     if (o.p < 2 || o.p > 17 || o.leaf_size < 1 || o.max_leaf_side < 1 || o.max_leaf_side > kMaxLeafSide ||
         (o.max_leaf_side & (o.max_leaf_side - 1)))
         return fail(LFMM_EINVAL, "bad opts");

@@ -1,6 +1,6 @@
 // Request loop with continuous admission (lfmm_server_* in include/lfmm.h).
 //
-// A server owns n_slots worker threads, each with its own non-blocking CUDA stream.
+// A server owns n_slots worker threads, each with its own non-blocking CUDA streams.
 // Submitted requests wait in arrival order; a free worker admits the oldest one as
 // soon as its estimated device footprint fits the memory budget next to the requests
 // already running (and the device's free memory, counting what the stream-ordered
@@ -24,6 +24,10 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// leaf size of the float-float path in the server (its M2L costs ~15 binary32 operations
+// per multiply-add, so larger leaves that trade M2L boxes for near-field pairs pay off)
+constexpr int kServeLeafDF = 128;
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
@@ -112,11 +116,17 @@ struct lfmm_server {
 
     void worker_main() {
         cudaSetDevice(device);
-        cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            s = nullptr;
-        }
+        // two streams per worker: mixed-path requests (short, latency-bound) run at the
+        // highest priority so that their blocks are scheduled ahead of the long M2L
+        // kernels of binary64-level requests sharing the device
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) cudaGetLastError();
+        cudaStream_t sp[2] = {nullptr, nullptr};
+        for (int c = 0; c < 2; ++c)
+            if (cudaStreamCreateWithPriority(&sp[c], cudaStreamNonBlocking, c == 0 ? greatest : least) != cudaSuccess) {
+                cudaGetLastError();
+                sp[c] = nullptr;
+            }
         for (;;) {
             int64_t ticket;
             Job* job;
@@ -133,7 +143,7 @@ struct lfmm_server {
                 ++running;
                 ++running_cls[job->cls];
             }
-            int st = run(*job, s);
+            int st = run(*job, sp[job->cls]);
             {
                 std::lock_guard<std::mutex> lk(mu);
                 job->t_done = Clock::now();
@@ -150,10 +160,11 @@ struct lfmm_server {
             cv_done.notify_all();
             cv_work.notify_all();
         }
-        if (s) {
-            cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
-        }
+        for (cudaStream_t s : sp)
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
     }
 
     int run(Job& j, cudaStream_t s) {
@@ -208,16 +219,16 @@ int lfmm_server_submit(lfmm_server* sv, const lfmm_request* req, int64_t* ticket
     Job j;
     j.req = *req;
     lfmm_opts_default(&j.opts);
-    // tolerance -> path: the mixed path reaches ~2e-7; binary64 at p = 16 reaches ~1e-14,
-    // and is fastest with leaves of up to 128 points (fewer boxes for its expensive M2L)
+    // tolerance -> path: the mixed path reaches ~2e-7; the float-float path at p = 16
+    // reaches binary64-level accuracy (~1e-14) on the FP32 pipes
     if (req->tol >= 1e-6) {
         j.opts.precision = LFMM_MIXED;
         j.opts.p = 8;
         j.cls = 0;
     } else {
-        j.opts.precision = LFMM_FP64;
+        j.opts.precision = LFMM_DF;
         j.opts.p = 16;
-        j.opts.leaf_size = 128;
+        j.opts.leaf_size = kServeLeafDF;
         j.cls = 1;
     }
     j.est = estimate_bytes(*req, j.opts);

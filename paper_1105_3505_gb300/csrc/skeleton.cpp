@@ -409,7 +409,7 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
                                 cudaStream_t stream, std::string* err) {
     std::lock_guard<std::mutex> g(mo->mu);
     while ((int)mo->levels.size() < n_levels) build_level(*mo);
-    auto& slot = mo->dev[precision == LFMM_MIXED ? 1 : 0][NP == 64 ? 1 : 0];
+    auto& slot = mo->dev[precision == LFMM_MIXED ? 1 : (precision == LFMM_DF ? 2 : 0)][NP == 64 ? 1 : 0];
     if (slot && slot->n_levels >= n_levels) return slot.get();
     const int nl = std::max(n_levels, slot ? slot->n_levels : 0);
     std::unique_ptr<DeviceOps> d(new DeviceOps());
@@ -430,6 +430,11 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
         std::vector<float> img;
         fill_device_image<float>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono, otc);
         elem = sizeof(float);
+        bytes.assign((const char*)img.data(), (const char*)img.data() + img.size() * elem);
+    } else if (precision == LFMM_DF) {
+        std::vector<DF> img;
+        fill_device_image<DF>(*mo, NP, nl, d->tab_H, d->tab_W, img, off_tofs, off_tab, om, ol, ot, omono, otc);
+        elem = sizeof(DF);
         bytes.assign((const char*)img.data(), (const char*)img.data() + img.size() * elem);
     } else {
         std::vector<double> img;

@@ -16,7 +16,7 @@ import numpy as np
 from .build import LIB
 
 LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL = range(7)
-LFMM_FP64, LFMM_MIXED = 0, 1
+LFMM_FP64, LFMM_MIXED, LFMM_DF = 0, 1, 2
 LFMM_TREE_AUTO, LFMM_TREE_UNIFORM, LFMM_TREE_PRUNED = 0, 1, 2
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lfmm.h")

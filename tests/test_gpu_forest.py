@@ -36,7 +36,8 @@ def rel_err(u, ref):
 
 
 def prec_of(lfmm, name):
-    return (lfmm.LFMM_FP64, 16, FP64_TOL) if name == "fp64" else (lfmm.LFMM_MIXED, 8, MIXED_TOL)
+    return {"fp64": (lfmm.LFMM_FP64, 16, FP64_TOL), "df": (lfmm.LFMM_DF, 16, FP64_TOL),
+            "mixed": (lfmm.LFMM_MIXED, 8, MIXED_TOL)}[name]
 
 
 def small_clustered(seed=7):
@@ -46,7 +47,7 @@ def small_clustered(seed=7):
                                   seg_len=600.0, frac_lines=0.02, domain=4096)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df"])
 def test_pruned_clustered_full_oracle(lfmm, precision):
     prob = small_clustered()
     prec, p, tol = prec_of(lfmm, precision)
@@ -108,7 +109,7 @@ def concat(probs):
     return src, so, tgt, to, f
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df"])
 @pytest.mark.parametrize("targets_equal", [True, False])
 def test_forest_full_oracle(lfmm, precision, targets_equal):
     probs = forest_case(zlib.crc32(f"forest{targets_equal}".encode()), 40, targets_equal=targets_equal)

@@ -44,10 +44,12 @@ def run(lfmm, src, tgt, f, precision, p, **kw):
     return u, info
 
 
-def test_uniform_4k_fp64_full_oracle(lfmm):
+@pytest.mark.parametrize("precision", ["fp64", "df"])
+def test_uniform_4k_fp64_full_oracle(lfmm, precision):
+    """Binary64 (plain) and float-float paths at p = 16: both reach the binary64 bar."""
     prob = workloads.uniform_4k()
     ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
-    u, info = run(lfmm, prob.src, prob.tgt, prob.f, lfmm.LFMM_FP64, 16)
+    u, info = run(lfmm, prob.src, prob.tgt, prob.f, lfmm.LFMM_FP64 if precision == "fp64" else lfmm.LFMM_DF, 16)
     tree = oracle.uniform_tree(prob.src, prob.tgt, 64, 32)
     assert (info["x0"], info["y0"], info["K"], info["L"], info["leaf_side"]) == \
         (tree["x0"], tree["y0"], tree["K"], tree["L"], tree["side"])
@@ -61,11 +63,15 @@ def test_uniform_4k_mixed_full_oracle(lfmm):
     assert rel_err(u, ref) <= MIXED_TOL
 
 
-@pytest.mark.parametrize("precision,p,tol_near,tol_far", [("fp64", 16, 1e-13, 1e-10), ("mixed", 8, 1e-6, 1e-6)])
+PRECISIONS = {"fp64": "LFMM_FP64", "mixed": "LFMM_MIXED", "df": "LFMM_DF"}
+
+
+@pytest.mark.parametrize("precision,p,tol_near,tol_far", [("fp64", 16, 1e-13, 1e-10), ("mixed", 8, 1e-6, 1e-6),
+                                                          ("df", 16, 1e-13, 1e-10)])
 def test_near_and_far_parts(lfmm, precision, p, tol_near, tol_far):
     """Near field = same/adjacent leaves (eq. 2.2) under the oracle's own tree; far = rest."""
     prob = workloads.uniform_box(3000, 2500, 300, seed=21)
-    prec = lfmm.LFMM_FP64 if precision == "fp64" else lfmm.LFMM_MIXED
+    prec = getattr(lfmm, PRECISIONS[precision])
     tree = oracle.uniform_tree(prob.src, prob.tgt, 64, 32)
     with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p) as pl:
         un, uf = pl.eval_parts(prob.f)
@@ -130,12 +136,12 @@ CASES = ["one_point", "one_source_many_targets", "line_of_three", "tiny_random",
 
 
 @pytest.mark.parametrize("name", CASES)
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df"])
 def test_edge_cases(lfmm, name, precision):
     s, t, f = _case(name)
     ref = oracle.lattice_sum(s, f, t)
-    if precision == "fp64":
-        u, info = run(lfmm, s, t, f, lfmm.LFMM_FP64, 16)
+    if precision in ("fp64", "df"):
+        u, info = run(lfmm, s, t, f, getattr(lfmm, PRECISIONS[precision]), 16)
         tol = FP64_TOL
     else:
         u, info = run(lfmm, s, t, f, lfmm.LFMM_MIXED, 8)
@@ -145,7 +151,7 @@ def test_edge_cases(lfmm, name, precision):
     if np.abs(ref).max() == 0.0:
         # only coincident sources: phi(0) = 0 exactly; the mixed path's deflated table
         # leaves a rounding residue of order eps * |f|
-        assert np.abs(u).max() <= (0.0 if precision == "fp64" else 1e-12 * np.abs(f).sum())
+        assert np.abs(u).max() <= {"fp64": 0.0, "df": 1e-14, "mixed": 1e-12}[precision] * np.abs(f).sum()
     elif name == "disjoint_far_targets" and precision == "mixed":
         # Zero-sum charges seen from far away: |u| is ~1e-3 of the size of the terms that
         # cancel in it, so a max-norm relative bound measures the problem's conditioning,
@@ -202,12 +208,12 @@ def uniform_1m():
     return workloads.uniform_1m()
 
 
-@pytest.mark.parametrize("precision,p,tol", [("mixed", 8, MIXED_TOL), ("fp64", 16, FP64_TOL)])
+@pytest.mark.parametrize("precision,p,tol", [("mixed", 8, MIXED_TOL), ("fp64", 16, FP64_TOL), ("df", 16, FP64_TOL)])
 def test_uniform_1m_sampled(lfmm, uniform_1m, precision, p, tol):
     """Full-size uniform workload (2^20 sources, 2^20 targets), in the launch configuration
     the benchmark times; 256 seeded targets checked against the oracle one by one."""
     prob = uniform_1m
-    prec = lfmm.LFMM_FP64 if precision == "fp64" else lfmm.LFMM_MIXED
+    prec = getattr(lfmm, PRECISIONS[precision])
     dev = torch.device("cuda:0")
     s_d = torch.from_numpy(prob.src).to(dev)
     t_d = torch.from_numpy(prob.tgt).to(dev)

@@ -44,7 +44,7 @@ def test_same_alone_and_in_the_mix(lfmm, requests):
         mixed = [sv.wait(t) for t in tickets]
     for r, (ua, sa), (um, sm) in zip(requests, alone, mixed):
         assert sa["status"] == 0 and sm["status"] == 0
-        want = lfmm.LFMM_MIXED if r.tol >= 1e-6 else lfmm.LFMM_FP64
+        want = lfmm.LFMM_MIXED if r.tol >= 1e-6 else lfmm.LFMM_DF
         assert sa["precision"] == want and sm["precision"] == want
         assert 0.0 <= sm["queue_ms"] and 0.0 < sm["run_ms"] <= sm["total_ms"] + 1e-9
         scale = np.abs(ua).max()
