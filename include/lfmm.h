@@ -184,7 +184,7 @@ typedef struct lfmm_request {
     double* u;                /* n_tgt result, host or device                              */
     double tol;               /* requested relative error: >= 1e-6 runs the mixed path at  */
                               /* p = 8, smaller values the float-float path (LFMM_DF) at   */
-                              /* p = 16 with leaves of up to 128 points                    */
+                              /* p = 16 with leaves of up to 192 points                    */
 } lfmm_request;
 
 typedef struct lfmm_request_stats {

@@ -49,14 +49,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or the
+// hint (ns) runs out, instead of spinning through issue slots
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -203,6 +205,9 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     __shared__ uint32_t s_tmem;
     __shared__ int s_off[27][3];
     __shared__ int s_abort;
+    // per K-step and row: source box (Morton index of q_hat at this level, or of u_hat at
+    // the parent level for the L2L step), -1 where the neighbour lies outside
+    __shared__ int s_src[28][kTcThreads];
 
     const int cls = blockIdx.y;
     const int px = cls & 1, py = cls >> 1;
@@ -249,6 +254,17 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // this thread's row: its 27 interaction-list sources and its parent, once per tile
+    for (int st = 0; st < 27; ++st) {
+        int si = -1;
+        if (valid) {
+            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
+            if (sx >= 0 && sx < side && sy >= 0 && sy < side) si = (int)morton2(sx, sy);
+        }
+        s_src[st][threadIdx.x] = si;
+    }
+    s_src[27][threadIdx.x] = (valid && has_l2l) ? (int)morton2(ri, rj) : -1;
+    __syncthreads();
     const uint32_t tmem = s_tmem;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 
@@ -259,17 +275,8 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int r = (threadIdx.x >> 3) + 16 * j;
-            const int64_t rr = (int64_t)blockIdx.x * kTcThreads + r;
-            const float* srow = nullptr;
-            if (rr < n_rows) {
-                const int ii = (int)(rr & (np_side - 1)), jj = (int)(rr >> lg);
-                if (step < 27) {
-                    const int sx = 2 * ii + px + s_off[step][0], sy = 2 * jj + py + s_off[step][1];
-                    if (sx >= 0 && sx < side && sy >= 0 && sy < side) srow = q + (size_t)morton2(sx, sy) * NP;
-                } else {
-                    srow = u_par + (size_t)morton2(ii, jj) * NP;
-                }
-            }
+            const int si = s_src[step][r];
+            const float* srow = si < 0 ? nullptr : (step < 27 ? q : u_par) + (size_t)si * NP;
             const uint32_t dst = smem_u32(&sA[b][r * 32 + ((ch ^ (r & 7)) << 2)]);
             const void* src = srow ? (const void*)(srow + 4 * ch) : (const void*)q;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
@@ -389,9 +396,8 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
             DFv qv[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                const int sx = 2 * ri + px + s_off[c0 + k][0], sy = 2 * rj + py + s_off[c0 + k][1];
-                const bool in = sx >= 0 && sx < side && sy >= 0 && sy < side;
-                qv[k] = in ? Qin[morton2(sx, sy)] : DFv{0.f, 0.f};
+                const int si = s_src[c0 + k][threadIdx.x];
+                qv[k] = si >= 0 ? Qin[si] : DFv{0.f, 0.f};
             }
 #pragma unroll
             for (int k = 0; k < 9; ++k) {

@@ -27,7 +27,7 @@ using Clock = std::chrono::steady_clock;
 
 // leaf size of the float-float path in the server (its M2L costs ~15 binary32 operations
 // per multiply-add, so larger leaves that trade M2L boxes for near-field pairs pay off)
-constexpr int kServeLeafDF = 128;
+constexpr int kServeLeafDF = 192;
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();

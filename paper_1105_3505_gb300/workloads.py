@@ -165,14 +165,16 @@ class Request:
 def serve_schedule(seed: int = 4, n_requests: int = 20_000, rate_per_s: float = 2000.0,
                    n_min: float = 1e3, n_max: float = 1e6) -> dict:
     """Arrival times (Poisson at rate_per_s), sizes (log-uniform N_src), point-set kinds
-    (0 uniform, 1 four clusters) and tolerances (1e-6 or 1e-10) of the serving stream."""
-    top = np.random.default_rng(seed)
-    gaps = top.exponential(1.0 / rate_per_s, size=n_requests)
+    (0 uniform, 1 four clusters) and tolerances (1e-6 or 1e-10) of the serving stream.
+    Each array comes from its own generator, so the schedule of the first n requests
+    is a prefix of the schedule of any longer stream."""
+    g_arr, g_size, g_kind, g_tol = (np.random.default_rng(s) for s in np.random.SeedSequence(seed).spawn(4))
+    gaps = g_arr.exponential(1.0 / rate_per_s, size=n_requests)
     return {"seed": seed,
             "arrival_s": np.cumsum(gaps),
-            "n_src": np.rint(np.exp(top.uniform(np.log(n_min), np.log(n_max), size=n_requests))).astype(np.int64),
-            "kind": top.integers(0, 2, size=n_requests),
-            "tol": np.where(top.integers(0, 2, size=n_requests) == 0, 1e-6, 1e-10)}
+            "n_src": np.rint(np.exp(g_size.uniform(np.log(n_min), np.log(n_max), size=n_requests))).astype(np.int64),
+            "kind": g_kind.integers(0, 2, size=n_requests),
+            "tol": np.where(g_tol.integers(0, 2, size=n_requests) == 0, 1e-6, 1e-10)}
 
 
 def serve_request(schedule: dict, i: int) -> Request:
