@@ -134,7 +134,8 @@ int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_
 int lfmm_plan_destroy(lfmm_plan* plan);
 
 /* Synchronise `stream` and report device-side failures of the plan's kernels since the
- * last call: LFMM_ETIMEOUT if a bounded wait inside a kernel gave up (the affected
+ * last call: LFMM_ETIMEOUT if a bounded wait inside a kernel gave up (an mbarrier wait of
+ * the tensor-core M2L or a grid barrier of the fused coarse-level kernels; the affected
  * results are not valid), else LFMM_OK.  Clears the status. */
 int lfmm_plan_status(lfmm_plan* plan, void* stream);
 

@@ -199,10 +199,9 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     void* stbuf;
     if ((st = palloc(p, &stbuf, 16, s))) return st;
     p->status = (int*)stbuf;
-    LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+    LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
     p->tc_min_level = p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level;
     p->bytes += F.bytes;
-    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
     return LFMM_OK;
 }
 
@@ -247,6 +246,10 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     int Lf = std::min(p->K, L_try + 1);
     Temp cnt;
     int32_t *cs = nullptr, *ct = nullptr;  // counts at the chosen level
+    int32_t *fs_last = nullptr, *ft_last = nullptr;  // counts at the histogram level Lf_last
+    int Lf_last = 0;
+    Temp ranks;  // each point's arrival rank in its box of level Lf_last
+    if ((st = talloc(ranks, (size_t)(p->ns + p->nt) * sizeof(int32_t), s))) return st;
     int chosen = -1;
     int64_t nonempty = 1;  // leaves holding a source or a target at the chosen level
     for (;;) {
@@ -261,7 +264,8 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         int32_t* ccs = ft + nf;
         int32_t* cct = ccs + nc;
         LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
-        LFMM_CUDA_TRY(launch_histogram(src, p->ns, tgt, p->nt, p->x0, p->y0, p->K - Lf, fs, ft, s));
+        LFMM_CUDA_TRY(launch_histogram(src, p->ns, tgt, p->nt, p->x0, p->y0, p->K - Lf, fs, ft, s,
+                                       (int32_t*)ranks.ptr));
         tree_timer->add_launches(1);
         // [max fine src, max fine tgt, max coarse src, max coarse tgt, non-empty fine, non-empty coarse]
         int m4[6] = {(int)std::min<int64_t>(p->ns, INT_MAX), (int)std::min<int64_t>(p->nt, INT_MAX), 0, 0, 1, 1};
@@ -291,6 +295,9 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
             cnt.ptr = c2.ptr;  // keep the counts alive
             cnt.s = s;
             c2.ptr = nullptr;
+            fs_last = fs;
+            ft_last = ft;
+            Lf_last = Lf;
             break;
         }
         const int next = std::min({p->K, Lf + 2, kMaxLevel});
@@ -329,13 +336,11 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     p->src_perm = p->src_loc + p->ns;
     p->tgt_loc = p->src_perm + p->ns;
     p->tgt_perm = p->tgt_loc + p->nt;
-    Temp cur;
-    if ((st = talloc(cur, (size_t)2 * n_leaves * sizeof(int32_t), s))) return st;
-    LFMM_CUDA_TRY(cudaMemsetAsync(cur.ptr, 0, (size_t)2 * n_leaves * sizeof(int32_t), s));
-    LFMM_CUDA_TRY(launch_scatter(src, p->ns, p->x0, p->y0, p->K - p->L, p->side, p->L, p->src_begin,
-                                 (int32_t*)cur.ptr, p->src_loc, p->src_perm, s));
-    LFMM_CUDA_TRY(launch_scatter(tgt, p->nt, p->x0, p->y0, p->K - p->L, p->side, p->L, p->tgt_begin,
-                                 (int32_t*)cur.ptr + n_leaves, p->tgt_loc, p->tgt_perm, s));
+    // bucket by the histogram ranks (no second atomic pass)
+    LFMM_CUDA_TRY(launch_scatter_ranked(src, p->ns, p->x0, p->y0, p->K, p->L, Lf_last, p->src_begin, fs_last,
+                                        (const int32_t*)ranks.ptr, p->src_loc, p->src_perm, s));
+    LFMM_CUDA_TRY(launch_scatter_ranked(tgt, p->nt, p->x0, p->y0, p->K, p->L, Lf_last, p->tgt_begin, ft_last,
+                                        (const int32_t*)ranks.ptr + p->ns, p->tgt_loc, p->tgt_perm, s));
     tree_timer->add_launches(2);
     tree_timer.reset();
     PhaseTimer op_timer(LFMM_PHASE_OPERATORS, s);
@@ -367,9 +372,10 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     void* stbuf;
     if ((st = palloc(p, &stbuf, 16, s))) return st;
     p->status = (int*)stbuf;
-    LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+    LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
     p->tc_min_level = p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level;
-    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    // no final synchronisation: temporaries are freed in stream order, and the host
+    // buffers of copied coordinates were read before the root-box readback
     return LFMM_OK;
 }
 
@@ -404,14 +410,35 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, Qx(L), Qm(L), s));
         pt.add_launches(1);
     }
+    LevelBufs lb;
+    for (int l = std::min(2, L); l <= L && l < 16; ++l) {
+        lb.q[l] = Qx(l);
+        lb.u[l] = Ux(l);
+        lb.Q[l] = Qm(l);
+        lb.C[l] = Cm(l);
+    }
+    unsigned* gsync = (unsigned*)(p->status + 1);  // grid-barrier words beside the status word
     {
         PhaseTimer pt(LFMM_PHASE_M2M, s);
-        for (int l = L - 1; l >= 2; --l) {
-            LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, l, Qx(l + 1), Qm(l + 1), Qx(l), Qm(l), s));
+        if (L >= 3 && launch_m2m_fused<T>(ops, L, lb, gsync, p->status, p->num_sms, s) == cudaSuccess) {
             pt.add_launches(1);
+        } else {
+            for (int l = L - 1; l >= 2; --l) {
+                LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, l, Qx(l + 1), Qm(l + 1), Qx(l), Qm(l), s));
+                pt.add_launches(1);
+            }
         }
     }
-    for (int l = 2; l <= L; ++l) {
+    int l_first = 2;  // first level left for the per-level M2L launches
+    if (L >= 2) {
+        PhaseTimer pt(LFMM_PHASE_M2L, s);
+        int last = 1;
+        if (launch_m2l_fused<T>(ops, L, lb, p->tc_min_level, gsync, p->status, p->num_sms, &last, s) == cudaSuccess) {
+            pt.add_launches(1);
+            l_first = last + 1;
+        }
+    }
+    for (int l = l_first; l <= L; ++l) {
         const bool tc = m2l_uses_tc(ops, L - l, l, p->tc_min_level, sizeof(T) == 4);
         PhaseTimer pt(tc ? LFMM_PHASE_M2L_TC : LFMM_PHASE_M2L, s);
         LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
@@ -547,7 +574,8 @@ int lfmm_plan_status(lfmm_plan* p, void* stream) {
     LFMM_CUDA_TRY(cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     LFMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     if (h != LFMM_OK) {
-        LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, sizeof(int), (cudaStream_t)stream));
+        // status word and the grid-barrier words (a barrier that gave up may leave them set)
+        LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, (cudaStream_t)stream));
         LFMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
         return fail(h, "a bounded device-side wait gave up; results of the affected evaluation are invalid");
     }

@@ -75,6 +75,17 @@ __device__ __forceinline__ DF ldg(const DF* p) {
     return DF{v.x, v.y};
 }
 
+// loads that bypass L1 (cache at L2 only): for data another block of the same launch
+// wrote before a grid barrier, which a stale L1 line could otherwise hide
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+    return __ldcg(p);
+}
+__device__ __forceinline__ DF ldcg(const DF* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return DF{v.x, v.y};
+}
+
 template <typename T>
 struct Mono;
 template <>

@@ -20,6 +20,9 @@
 // (double-float pairs on the mixed path).  Interpolation reproduces constants
 // (T_ofs^T 1 = 1 and T_ifi 1 = 1 to the expansion accuracy), so C bypasses L2L/L2P
 // and joins the binary64 final sum.
+#include <cstring>
+#include <type_traits>
+
 #include "device_common.h"
 #include "lfmm_internal.h"
 
@@ -302,25 +305,24 @@ struct SkCfg {
     static constexpr size_t SMEM = (size_t)WARPS * (NP * 32 + ROWS) * sizeof(T);
 };
 
-template <typename T, int NP>
-__global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(int level, const T* __restrict__ q,
-                                                                   const T* __restrict__ u_par,
-                                                                   const T* __restrict__ ops,
-                                                                   const T* __restrict__ l2l,
-                                                                   const T* __restrict__ mono,
-                                                                   const typename Mono<T>::V* __restrict__ Qin,
-                                                                   const typename Mono<T>::V* __restrict__ Cpar,
-                                                                   T* __restrict__ out,
-                                                                   typename Mono<T>::V* __restrict__ Cout) {
+// One 32-box tile of parity class cls at `level` (shared by the per-level kernel and
+// the fused small-level kernel).  u_par == nullptr: no L2L step and C starts at 0.
+template <typename T, int NP, int W>
+__device__ __forceinline__ void m2l_splitk_tile(int level, int cls, int64_t tile, const T* __restrict__ q,
+                                                const T* __restrict__ u_par, const T* __restrict__ ops,
+                                                const T* __restrict__ l2l, const T* __restrict__ mono,
+                                                const typename Mono<T>::V* __restrict__ Qin,
+                                                const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out,
+                                                typename Mono<T>::V* __restrict__ Cout) {
     using M = Mono<T>;
     using V = typename M::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int kSkWarps = SkCfg<T, NP>::WARPS;
+    constexpr int kSkWarps = W;
     constexpr int kRows = SkCfg<T, NP>::ROWS;
     T* sop = reinterpret_cast<T*>(smem_raw);            // [warps][NP][32] operator slice
     T* red = sop + kSkWarps * NP * 32;                  // [warps][kRows]: rows, then 32 x 33 sums
     __shared__ int s_off[27][3];
-    const int cls = blockIdx.y;
+    __syncthreads();  // the previous tile of this block is done with the shared buffers
     const int px = cls & 1, py = cls >> 1;
     const int lg = level - 1;
     const int np_side = 1 << lg;
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
         }
     }
     __syncthreads();
-    const int64_t row = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t row = tile * 32 + lane;
     const bool valid = row < n_rows;
     const int ri = valid ? (int)(row & (np_side - 1)) : 0, rj = valid ? (int)(row >> lg) : 0;
     T* my_op = sop + warp * NP * 32;
@@ -418,9 +420,16 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
 #pragma unroll 4
                 for (int k = 0; k < NP; ++k) {
                     const T a = rowp[(k + lane) & (NP - 1)];
-                    const T* b = my_op + k * 32;
+                    // the 32 operator values of row k (broadcast) in 16-byte loads
+                    constexpr int E = (int)(16 / sizeof(T));
+                    const uint4* b16 = reinterpret_cast<const uint4*>(my_op + k * 32);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] = fma(a, b[j], acc[j]);
+                    for (int c = 0; c < 32 / E; ++c) {
+                        const uint4 raw = b16[c];
+                        const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+                        for (int t = 0; t < E; ++t) acc[c * E + t] = fma(a, e[t], acc[c * E + t]);
+                    }
                 }
             }
             __syncwarp();
@@ -436,7 +445,7 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
             T v = T(0);
 #pragma unroll
             for (int w = 0; w < kSkWarps; ++w) v += red[(size_t)w * kRows + b * 33 + j];
-            const int64_t r = (int64_t)blockIdx.x * 32 + b;
+            const int64_t r = tile * 32 + b;
             if (r < n_rows) {
                 const int ii = (int)(r & (np_side - 1)), jj = (int)(r >> lg);
                 out[(size_t)morton2(2 * ii + px, 2 * jj + py) * NP + 32 * half + j] = v;
@@ -453,32 +462,54 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
     }
 }
 
+template <typename T, int NP>
+__global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(int level, const T* __restrict__ q,
+                                                                   const T* __restrict__ u_par,
+                                                                   const T* __restrict__ ops,
+                                                                   const T* __restrict__ l2l,
+                                                                   const T* __restrict__ mono,
+                                                                   const typename Mono<T>::V* __restrict__ Qin,
+                                                                   const typename Mono<T>::V* __restrict__ Cpar,
+                                                                   T* __restrict__ out,
+                                                                   typename Mono<T>::V* __restrict__ Cout) {
+    m2l_splitk_tile<T, NP, SkCfg<T, NP>::WARPS>(level, blockIdx.y, blockIdx.x, q, u_par, ops, l2l, mono, Qin, Cpar,
+                                                 out, Cout);
+}
+
 // M2M with one warp per parent: lanes own outputs, children's expansions broadcast by
 // shuffles, the operator [4NP][NP] staged in shared memory when it fits (else L1/L2).
-template <typename T, int NP, bool SMEM_OP>
-__global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __restrict__ qc,
-                                                       const T* __restrict__ m2m,
-                                                       const typename Mono<T>::V* __restrict__ Qin,
-                                                       T* __restrict__ qp,
-                                                       typename Mono<T>::V* __restrict__ Qout) {
+// M2M of the parents [warp_id, n_parent) with stride n_warps: one warp per parent,
+// lanes own outputs, the children's expansions broadcast by shuffles; op is the
+// operator [4NP][NP] in shared memory (staged by the caller) or global memory.
+template <typename T, int NP>
+__device__ __forceinline__ void m2m_parents(int level, const T* __restrict__ qc, const T* __restrict__ op,
+                                            const typename Mono<T>::V* __restrict__ Qin, T* __restrict__ qp,
+                                            typename Mono<T>::V* __restrict__ Qout, int64_t warp_id,
+                                            int64_t n_warps) {
     using M = Mono<T>;
     constexpr int CL = 4 * NP / 32, PL = NP / 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sop = reinterpret_cast<T*>(smem_raw);
-    if (SMEM_OP) {
-        constexpr int N4 = 4 * NP * NP * (int)sizeof(T) / 16;
-        for (int i = threadIdx.x; i < N4; i += blockDim.x)
-            reinterpret_cast<uint4*>(sop)[i] = __ldg(reinterpret_cast<const uint4*>(m2m) + i);
-        __syncthreads();
-    }
-    const T* op = SMEM_OP ? sop : m2m;
     const int lane = threadIdx.x & 31;
     const int64_t n_parent = (int64_t)1 << (2 * level);
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t par = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; par < n_parent; par += nw) {
+    // software pipeline: the next parent's children and charges are loaded while this
+    // parent is computed
+    T nx[CL];
+    typename M::V nq = M::zero();
+    if (warp_id < n_parent) {
+#pragma unroll
+        for (int c = 0; c < CL; ++c) nx[c] = ldcg(qc + (size_t)warp_id * 4 * NP + lane + 32 * c);
+        if (lane < 4) nq = ldcg(Qin + 4 * warp_id + lane);
+    }
+    for (int64_t par = warp_id; par < n_parent; par += n_warps) {
         T xv[CL];
 #pragma unroll
-        for (int c = 0; c < CL; ++c) xv[c] = qc[(size_t)par * 4 * NP + lane + 32 * c];
+        for (int c = 0; c < CL; ++c) xv[c] = nx[c];
+        typename M::V qv = nq;
+        const int64_t nxt = par + n_warps;
+        if (nxt < n_parent) {
+#pragma unroll
+            for (int c = 0; c < CL; ++c) nx[c] = ldcg(qc + (size_t)nxt * 4 * NP + lane + 32 * c);
+            if (lane < 4) nq = ldcg(Qin + 4 * nxt + lane);
+        }
         // one accumulator chain per 32-wide input chunk, added at the end
         T acc[CL][PL];
 #pragma unroll
@@ -503,11 +534,28 @@ __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __res
             qp[(size_t)par * NP + lane + 32 * i] = a;
         }
         // total charge of the parent: lanes 0..3 hold the children's, all lanes shuffle
-        typename M::V qv = lane < 4 ? Qin[4 * par + lane] : M::zero();
         qv = M::add(qv, shfl_xor_v(qv, 1));
         qv = M::add(qv, shfl_xor_v(qv, 2));
         if (lane == 0) Qout[par] = qv;
     }
+}
+
+template <typename T, int NP, bool SMEM_OP>
+__global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __restrict__ qc,
+                                                       const T* __restrict__ m2m,
+                                                       const typename Mono<T>::V* __restrict__ Qin,
+                                                       T* __restrict__ qp,
+                                                       typename Mono<T>::V* __restrict__ Qout) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sop = reinterpret_cast<T*>(smem_raw);
+    if (SMEM_OP) {
+        constexpr int N4 = 4 * NP * NP * (int)sizeof(T) / 16;
+        for (int i = threadIdx.x; i < N4; i += blockDim.x)
+            reinterpret_cast<uint4*>(sop)[i] = __ldg(reinterpret_cast<const uint4*>(m2m) + i);
+        __syncthreads();
+    }
+    m2m_parents<T, NP>(level, qc, SMEM_OP ? sop : m2m, Qin, qp, Qout,
+                       ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 // ------------------------------------------------------------------------- P2P + L2P
@@ -893,6 +941,161 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
     }
 }
 
+// ------------------------------------------------------------------------- fused small levels
+// The coarse levels hold few boxes, so one launch per level is mostly launch and
+// latency.  Two cooperative kernels (all blocks co-resident) cover them instead:
+//   upward:   M2M of every level from L-1 up to 2, one grid barrier between levels;
+//   downward: the M2L part (27 K-steps, no parent term) of every small level at once,
+//             then the L2L chain u_hat_l += T_ifi u_hat_parent and C_l += C_parent from
+//             level 3 down to the last small level, one barrier per level.
+// The result equals the per-level sweeps (the parent term is added after instead of
+// beside the interaction-list terms).
+constexpr int kMaxLevels = 16;
+
+template <typename T>
+struct LevelPtrs {
+    using V = typename Mono<T>::V;
+    T* q[kMaxLevels];            // outgoing expansions of level l
+    T* u[kMaxLevels];            // incoming expansions of level l
+    V* Q[kMaxLevels];            // total charges
+    V* C[kMaxLevels];            // incoming constants
+    const T* tifo[kMaxLevels];   // deflated T_ifo of level l's boxes
+    const T* mono[kMaxLevels];   // deflation constants
+    const T* l2l[kMaxLevels];    // [4][NP][NP] from level l-1 to level l
+    const T* m2m[kMaxLevels];    // [4NP][NP] from level l+1 to level l
+    int64_t item_off[kMaxLevels + 1];  // downward: first M2L work item of level l0 + i
+};
+
+// Grid-wide barrier of a cooperative launch.  count and gen are plan-owned device words
+// (zero before the first use, and back to that state after every barrier).  The wait is
+// bounded (~1 s); on expiry the block records LFMM_ETIMEOUT and goes on (results
+// invalid, no hang).
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) + 1 == gridDim.x) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*vgen == g) {
+                if (++it > (1u << 24)) {
+                    atomicExch(status, LFMM_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <typename T, int NP, bool SMEM_OP>
+__global__ void __launch_bounds__(256) m2m_up_kernel(LevelPtrs<T> P, int l_top, int l_bot, unsigned* sync,
+                                                     int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sop = reinterpret_cast<T*>(smem_raw);
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int l = l_top; l >= l_bot; --l) {
+        const T* op = P.m2m[l];
+        if (SMEM_OP) {
+            constexpr int N4 = 4 * NP * NP * (int)sizeof(T) / 16;
+            __syncthreads();
+            for (int i = threadIdx.x; i < N4; i += blockDim.x)
+                reinterpret_cast<uint4*>(sop)[i] = __ldg(reinterpret_cast<const uint4*>(op) + i);
+            __syncthreads();
+            op = sop;
+        }
+        m2m_parents<T, NP>(l, P.q[l + 1], op, P.Q[l + 1], P.q[l], P.Q[l], wid, nw);
+        if (l > l_bot) grid_barrier(sync, sync + 1, status);
+    }
+}
+
+// The fused kernel's tiles have 27 K-steps (no parent term): 9 warps take 3 each (3 warps
+// x 9 for binary64-width elements with 64 coefficients, to fit shared memory).
+template <typename T, int NP>
+struct FusedCfg {
+    static constexpr int WARPS = (sizeof(T) == 8 && NP == 64) ? 3 : 9;
+    static constexpr size_t SMEM = (size_t)WARPS * (NP * 32 + SkCfg<T, NP>::ROWS) * sizeof(T);
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(LevelPtrs<T> P, int l0, int l1,
+                                                                                unsigned* sync, int* status) {
+    using M = Mono<T>;
+    constexpr int PL = NP / 32;
+    const int nl = l1 - l0 + 1;
+    const int64_t n_items = P.item_off[nl];
+    // M2L part of every level: work item = (level, class, 32-box tile)
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        int i = 0;
+        while (item >= P.item_off[i + 1]) ++i;
+        const int l = l0 + i;
+        const int64_t tiles = (((int64_t)1 << (2 * (l - 1))) + 31) / 32;
+        const int64_t local = item - P.item_off[i];
+        m2l_splitk_tile<T, NP, FusedCfg<T, NP>::WARPS>(l, (int)(local / tiles), local % tiles, P.q[l], nullptr,
+                                                       P.tifo[l], nullptr, P.mono[l], P.Q[l], nullptr, P.u[l],
+                                                       P.C[l]);
+    }
+    if (nl == 1) return;
+    grid_barrier(sync, sync + 1, status);
+    // L2L chain: one warp per child box, lanes own outputs, the parent's expansion
+    // broadcast by shuffles
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int l = l0 + 1; l <= l1; ++l) {
+        const int64_t nb = (int64_t)1 << (2 * l);
+        const T* up = P.u[l - 1];
+        // software pipeline over the boxes: the next box's rows load during this one
+        T npv[PL], nacc[PL];
+        if (wid < nb) {
+#pragma unroll
+            for (int i = 0; i < PL; ++i) {
+                npv[i] = ldcg(up + (size_t)(wid >> 2) * NP + lane + 32 * i);
+                nacc[i] = ldcg(P.u[l] + (size_t)wid * NP + lane + 32 * i);
+            }
+        }
+        for (int64_t b = wid; b < nb; b += nw) {
+            const int64_t par = b >> 2;
+            const int c = (int)(b & 3);  // Morton: child index = parity class (cx + 2 cy)
+            const T* op = P.l2l[l] + (size_t)c * NP * NP;
+            T pv[PL], acc[PL];
+#pragma unroll
+            for (int i = 0; i < PL; ++i) {
+                pv[i] = npv[i];
+                acc[i] = nacc[i];
+            }
+            if (b + nw < nb) {
+#pragma unroll
+                for (int i = 0; i < PL; ++i) {
+                    npv[i] = ldcg(up + (size_t)((b + nw) >> 2) * NP + lane + 32 * i);
+                    nacc[i] = ldcg(P.u[l] + (size_t)(b + nw) * NP + lane + 32 * i);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < PL; ++i)
+#pragma unroll 8
+                for (int kk = 0; kk < 32; ++kk) {
+                    const T v = shfl(pv[i], kk);
+                    const T* row = op + (size_t)(32 * i + kk) * NP;
+#pragma unroll
+                    for (int o = 0; o < PL; ++o) acc[o] = fma(ldg(row + lane + 32 * o), v, acc[o]);
+                }
+#pragma unroll
+            for (int i = 0; i < PL; ++i) P.u[l][(size_t)b * NP + lane + 32 * i] = acc[i];
+            if (lane == 0) P.C[l][b] = M::add(ldcg(P.C[l] + b), ldcg(P.C[l - 1] + par));
+        }
+        if (l < l1) grid_barrier(sync, sync + 1, status);
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------- launchers
@@ -1072,7 +1275,92 @@ cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_s
     return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
 }
 
+// ---- fused small levels (cooperative launches)
+template <typename T>
+static void fill_levels(LevelPtrs<T>& P, const DeviceOps& ops, int L, const LevelBufs& b) {
+    using V = typename Mono<T>::V;
+    std::memset(&P, 0, sizeof(P));
+    for (int l = 0; l <= L && l < kMaxLevels; ++l) {
+        P.q[l] = (T*)b.q[l];
+        P.u[l] = (T*)b.u[l];
+        P.Q[l] = (V*)b.Q[l];
+        P.C[l] = (V*)b.C[l];
+        const int k = L - l;
+        if (l >= 2 && k >= 0 && k < (int)ops.tifo.size()) {
+            P.tifo[l] = (const T*)ops.tifo[k];
+            P.mono[l] = (const T*)ops.mono[k];
+            if (k + 1 < (int)ops.l2l.size()) P.l2l[l] = (const T*)ops.l2l[k + 1];
+            if (k >= 1) P.m2m[l] = (const T*)ops.m2m[k];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, unsigned* sync, int* status,
+                             int num_sms, cudaStream_t s) {
+    if (L < 3 || L >= kMaxLevels) return cudaErrorNotSupported;
+    LevelPtrs<T> P;
+    fill_levels<T>(P, ops, L, b);
+    int l_top = L - 1, l_bot = 2;
+    auto go = [&](const void* fn, size_t smem) -> cudaError_t {
+        cudaError_t e = ensure_dynamic_smem(fn, smem);
+        if (e != cudaSuccess) return e;
+        // one block per SM: 8 warps per SM cover the largest level (one parent per warp
+        // and pass), and every extra block costs each grid barrier an arrival
+        const int grid = num_sms;
+        void* args[] = {&P, &l_top, &l_bot, &sync, &status};
+        e = cudaLaunchCooperativeKernel(fn, grid, 256, args, smem, s);
+        return e == cudaSuccess ? cudaSuccess : clear_and_return(e);
+    };
+    if (ops.NP == 32) {
+        constexpr size_t ob = (size_t)4 * 32 * 32 * sizeof(T);
+        if constexpr (ob <= 64 * 1024) return go((const void*)m2m_up_kernel<T, 32, true>, ob);
+        else return go((const void*)m2m_up_kernel<T, 32, false>, 0);
+    }
+    constexpr size_t ob = (size_t)4 * 64 * 64 * sizeof(T);
+    if constexpr (ob <= 64 * 1024) return go((const void*)m2m_up_kernel<T, 64, true>, ob);
+    else return go((const void*)m2m_up_kernel<T, 64, false>, 0);
+}
+
+template <typename T>
+cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, int tc_min_level, unsigned* sync,
+                             int* status, int num_sms, int* last_level, cudaStream_t s) {
+    *last_level = 1;
+    // small levels: 2 .. Ls, the levels the per-level path sends to the split-K kernel
+    int Ls = 1;
+    for (int l = 2; l <= std::min(L, kM2LSplitKMaxLevel); ++l) {
+        if (m2l_uses_tc(ops, L - l, l, tc_min_level, sizeof(T) == 4)) break;
+        Ls = l;
+    }
+    if (Ls < 2 || L >= kMaxLevels) return cudaErrorNotSupported;
+    LevelPtrs<T> P;
+    fill_levels<T>(P, ops, L, b);
+    int l0 = 2, l1 = Ls;
+    P.item_off[0] = 0;
+    for (int l = l0; l <= l1; ++l)
+        P.item_off[l - l0 + 1] = P.item_off[l - l0] + 4 * ((((int64_t)1 << (2 * (l - 1))) + 31) / 32);
+    auto go = [&](auto np_tag) -> cudaError_t {
+        constexpr int NPc = decltype(np_tag)::value;
+        const void* fn = (const void*)m2l_small_kernel<T, NPc>;
+        constexpr size_t smem = FusedCfg<T, NPc>::SMEM;
+        constexpr int threads = FusedCfg<T, NPc>::WARPS * 32;
+        cudaError_t e = ensure_dynamic_smem(fn, smem);
+        if (e != cudaSuccess) return e;
+        const int grid = num_sms * blocks_per_sm(fn, threads, smem);
+        void* args[] = {&P, &l0, &l1, &sync, &status};
+        e = cudaLaunchCooperativeKernel(fn, grid, threads, args, smem, s);
+        return e == cudaSuccess ? cudaSuccess : clear_and_return(e);
+    };
+    cudaError_t e = ops.NP == 32 ? go(std::integral_constant<int, 32>()) : go(std::integral_constant<int, 64>());
+    if (e == cudaSuccess) *last_level = Ls;
+    return e;
+}
+
 #define LFMM_INSTANTIATE(T)                                                                                   \
+    template cudaError_t launch_m2m_fused<T>(const DeviceOps&, int, const LevelBufs&, unsigned*, int*, int,      \
+                                             cudaStream_t);                                                  \
+    template cudaError_t launch_m2l_fused<T>(const DeviceOps&, int, const LevelBufs&, int, unsigned*, int*, int, \
+                                             int*, cudaStream_t);                                            \
     template cudaError_t launch_p2m<T>(const TreeView&, const DeviceOps&, const double*, T*, T*, void*,       \
                                        cudaStream_t);                                                         \
     template cudaError_t launch_m2m<T>(const DeviceOps&, int, int, const T*, const void*, T*, void*,         \

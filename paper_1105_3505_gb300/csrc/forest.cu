@@ -118,11 +118,12 @@ __device__ __forceinline__ int64_t leaf_of(const ProblemGeo& g, int p, int2 v, i
     return g.leaf_off[p] + (int64_t)by * n + bx;
 }
 
+// leaf counts; rank[i] = the point's arrival rank in its leaf (its slot offset later)
 __global__ void count_forest_kernel(const int2* __restrict__ xy, int64_t n, ProblemGeo g, int ls,
-                                    int32_t* __restrict__ cnt) {
+                                    int32_t* __restrict__ cnt, int32_t* __restrict__ rank) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lx, ly;
-        atomicAdd(cnt + leaf_of(g, g.pid[i], xy[i], ls, lx, ly), 1);
+        rank[i] = atomicAdd(cnt + leaf_of(g, g.pid[i], xy[i], ls, lx, ly), 1);
     }
 }
 
@@ -144,12 +145,12 @@ __global__ void max2_kernel(const int32_t* __restrict__ a, const int32_t* __rest
 }
 
 __global__ void scatter_forest_kernel(const int2* __restrict__ xy, int64_t n, ProblemGeo g, int ls,
-                                      const int32_t* __restrict__ begin, int32_t* __restrict__ cursor,
+                                      const int32_t* __restrict__ begin, const int32_t* __restrict__ rank,
                                       int32_t* __restrict__ loc, int32_t* __restrict__ perm) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lx, ly;
         const int64_t leaf = leaf_of(g, g.pid[i], xy[i], ls, lx, ly);
-        const int slot = begin[leaf] + atomicAdd(cursor + leaf, 1);
+        const int slot = begin[leaf] + rank[i];
         loc[slot] = lx | (ly << 16);
         perm[slot] = (int32_t)i;
     }
@@ -597,9 +598,16 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
 #pragma unroll 4
                 for (int k = 0; k < NP; ++k) {
                     const T a = rowp[(k + lane) & (NP - 1)];
-                    const T* b = my_op + k * 32;
+                    // the 32 operator values of row k (broadcast) in 16-byte loads
+                    constexpr int E = (int)(16 / sizeof(T));
+                    const uint4* b16 = reinterpret_cast<const uint4*>(my_op + k * 32);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] = fma(a, b[j], acc[j]);
+                    for (int c = 0; c < 32 / E; ++c) {
+                        const uint4 raw = b16[c];
+                        const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+                        for (int t = 0; t < E; ++t) acc[c * E + t] = fma(a, e[t], acc[c * E + t]);
+                    }
                 }
             }
             __syncwarp();
@@ -956,6 +964,11 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     if ((1 << ls) > max_leaf_side) --ls;
     ls = std::min(ls, Kmax);
     DevTemp counts;  // dense leaf counts of the accepted side
+    DevTemp ranks;   // each point's arrival rank in its leaf (sources, then targets)
+    LFMM_CUDA_TRY(cudaMallocAsync(&ranks.ptr, (size_t)(ns + nt) * sizeof(int32_t), s));
+    ranks.s = s;
+    int32_t* rank_s = (int32_t*)ranks.ptr;
+    int32_t* rank_t = rank_s + ns;
     std::vector<int64_t> leaf_off(np + 1);
     int maxs = 0, maxt = 0;
     for (;;) {
@@ -979,9 +992,9 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
         LFMM_CUDA_TRY(cudaMemcpyAsync(dL, F.L.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         LFMM_CUDA_TRY(cudaMemcpyAsync(dlo, leaf_off.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         ProblemGeo g{F.spid, dx0, dy0, dL, dlo};
-        count_forest_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>((const int2*)src, ns, g, ls, cs);
+        count_forest_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>((const int2*)src, ns, g, ls, cs, rank_s);
         g.pid = F.tpid;
-        count_forest_kernel<<<grid_for(nt, kThreads), kThreads, 0, s>>>((const int2*)tgt, nt, g, ls, ct);
+        count_forest_kernel<<<grid_for(nt, kThreads), kThreads, 0, s>>>((const int2*)tgt, nt, g, ls, ct, rank_t);
         max2_kernel<<<grid_for(NL, kThreads), kThreads, 0, s>>>(cs, ct, NL, mx);
         LFMM_CUDA_TRY(cudaGetLastError());
         timer->add_launches(3);
@@ -1015,10 +1028,9 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     F.tbeg = F.sbeg + (NL + 1);
     DevTemp tmp;
     const int64_t big = std::max<int64_t>(NL, 1);
-    LFMM_CUDA_TRY(cudaMallocAsync(&tmp.ptr, (size_t)(exscan_tmp_ints(big) + 2 * big) * sizeof(int32_t), s));
+    LFMM_CUDA_TRY(cudaMallocAsync(&tmp.ptr, (size_t)exscan_tmp_ints(big) * sizeof(int32_t), s));
     tmp.s = s;
     int32_t* sums = (int32_t*)tmp.ptr;
-    int32_t* cur = sums + exscan_tmp_ints(big);
     LFMM_CUDA_TRY(exscan(cs, F.sbeg, NL, sums, s));
     LFMM_CUDA_TRY(exscan(ct, F.tbeg, NL, sums, s));
     if ((st = A(&v, (size_t)2 * (ns + nt) * sizeof(int32_t)))) return st;
@@ -1026,13 +1038,12 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     F.sperm = F.sloc + ns;
     F.tloc = F.sperm + ns;
     F.tperm = F.tloc + nt;
-    LFMM_CUDA_TRY(cudaMemsetAsync(cur, 0, (size_t)2 * NL * sizeof(int32_t), s));
     g.pid = F.spid;
-    scatter_forest_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>((const int2*)src, ns, g, ls, F.sbeg, cur,
+    scatter_forest_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>((const int2*)src, ns, g, ls, F.sbeg, rank_s,
                                                                        F.sloc, F.sperm);
     g.pid = F.tpid;
-    scatter_forest_kernel<<<grid_for(nt, kThreads), kThreads, 0, s>>>((const int2*)tgt, nt, g, ls, F.tbeg,
-                                                                       cur + NL, F.tloc, F.tperm);
+    scatter_forest_kernel<<<grid_for(nt, kThreads), kThreads, 0, s>>>((const int2*)tgt, nt, g, ls, F.tbeg, rank_t,
+                                                                       F.tloc, F.tperm);
     LFMM_CUDA_TRY(cudaGetLastError());
     timer->add_launches(8);
 
@@ -1186,8 +1197,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     LFMM_CUDA_TRY(cudaMemcpyAsync(F.n_strips_d, sscan + ncand, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     LFMM_CUDA_TRY(cudaGetLastError());
     timer->add_launches(5);
-    LFMM_CUDA_TRY(cudaStreamSynchronize(s));  // temporaries are freed on return
-    return LFMM_OK;
+    return LFMM_OK;  // temporaries are freed in stream order
 }
 
 template <typename T>

@@ -259,9 +259,16 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);
 cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
                         cudaStream_t s);
+// Morton counts of sources and targets per box of the level K - shift; rank (optional,
+// ns + nt entries, sources first) receives each point's arrival rank in its box.
 cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
                              int64_t x0, int64_t y0, int shift, int32_t* cnt_src,
-                             int32_t* cnt_tgt, cudaStream_t s);
+                             int32_t* cnt_tgt, cudaStream_t s, int32_t* rank = nullptr);
+// Leaf buckets from histogram ranks taken at level Lf (L or L + 1; fine = that level's
+// Morton counts): no atomics.
+cudaError_t launch_scatter_ranked(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int K, int L, int Lf,
+                                  const int32_t* begin, const int32_t* fine, const int32_t* rank, int32_t* loc,
+                                  int32_t* perm, cudaStream_t s);
 // Sums 2x2 blocks of two Morton count arrays; max4[0..3] receive (atomic max) the
 // largest fine source / target count and the largest coarse ones, max4[4..5] (atomic
 // add) the number of non-empty fine and coarse boxes.  max4 must be zeroed first.
@@ -285,6 +292,25 @@ cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f,
 template <typename T>
 cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
                        T* q_parent, void* Q_parent, cudaStream_t s);
+// Device buffers of every level of a uniform tree (index = level; null where absent).
+struct LevelBufs {
+    void* q[16] = {nullptr};
+    void* u[16] = {nullptr};
+    void* Q[16] = {nullptr};
+    void* C[16] = {nullptr};
+};
+// M2M of levels L-1 .. 2 in one cooperative launch (grid barriers between levels).
+// sync: two zero device words (barrier state).  Returns an error (nothing launched)
+// when a cooperative launch is not possible; the caller then runs the per-level path.
+template <typename T>
+cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, unsigned* sync, int* status,
+                             int num_sms, cudaStream_t s);
+// M2L + L2L of the small levels 2 .. *last_level (those the per-level path runs on the
+// split-K kernel) in one cooperative launch; the caller continues at *last_level + 1.
+template <typename T>
+cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, int tc_min_level, unsigned* sync,
+                             int* status, int num_sms, int* last_level, cudaStream_t s);
+
 // Whether level `level` (k levels above the leaves) runs M2L + L2L on the tensor cores:
 // fp32 arithmetic, P <= 32, tiles present, level >= tc_min_level.
 inline bool m2l_uses_tc(const DeviceOps& ops, int k, int level, int tc_min_level, bool fp32) {

@@ -72,15 +72,43 @@ __device__ __forceinline__ uint32_t box_of(int2 p, int64_t x0, int64_t y0, int s
     return morton2(bx, by);
 }
 
+// Counts points per box; with `rank` set, also records each point's arrival rank in
+// its box (the value its atomic increment returned), which places it in its bucket
+// later without a second atomic pass.
 __global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
                                  const int2* __restrict__ tgt, int64_t nt, int64_t x0,
                                  int64_t y0, int shift, int32_t* __restrict__ cs,
-                                 int32_t* __restrict__ ct) {
+                                 int32_t* __restrict__ ct, int32_t* __restrict__ rank) {
     const int64_t n = ns + nt;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < ns) atomicAdd(cs + box_of(src[i], x0, y0, shift), 1);
-        else atomicAdd(ct + box_of(tgt[i - ns], x0, y0, shift), 1);
+        const int r = i < ns ? atomicAdd(cs + box_of(src[i], x0, y0, shift), 1)
+                             : atomicAdd(ct + box_of(tgt[i - ns], x0, y0, shift), 1);
+        if (rank) rank[i] = r;
+    }
+}
+
+// Buckets points by leaf (row-major leaf order at level L) from the ranks the histogram
+// recorded at level Lf (= L or L + 1, Morton counts `fine` of that level): a point's
+// slot is its leaf's start, plus the counts of its box's earlier siblings when Lf = L + 1,
+// plus its rank.
+__global__ void scatter_ranked_kernel(const int2* __restrict__ xy, int64_t n, int64_t x0, int64_t y0, int K, int L,
+                                      int Lf, const int32_t* __restrict__ begin, const int32_t* __restrict__ fine,
+                                      const int32_t* __restrict__ rank, int32_t* __restrict__ loc,
+                                      int32_t* __restrict__ perm) {
+    const int shift = K - L, lside = 1 << shift;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = xy[i];
+        const int64_t rx = (int64_t)p.x - x0, ry = (int64_t)p.y - y0;
+        const int64_t leaf = ((ry >> shift) << L) | (rx >> shift);
+        int slot = begin[leaf] + rank[i];
+        if (Lf == L + 1) {
+            const uint32_t mf = morton2((uint32_t)(rx >> (shift - 1)), (uint32_t)(ry >> (shift - 1)));
+            const uint32_t base = mf & ~3u;
+            for (uint32_t c = base; c < mf; ++c) slot += fine[c];
+        }
+        loc[slot] = (int)(rx & (lside - 1)) | ((int)(ry & (lside - 1)) << 16);
+        perm[slot] = (int32_t)i;
     }
 }
 
@@ -257,9 +285,17 @@ cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t 
 
 cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
                              int64_t x0, int64_t y0, int shift, int32_t* cs, int32_t* ct,
-                             cudaStream_t s) {
+                             cudaStream_t s, int32_t* rank) {
     histogram_kernel<<<grid_for(ns + nt, kThreads), kThreads, 0, s>>>(
-        (const int2*)src, ns, (const int2*)tgt, nt, x0, y0, shift, cs, ct);
+        (const int2*)src, ns, (const int2*)tgt, nt, x0, y0, shift, cs, ct, rank);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_ranked(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int K, int L, int Lf,
+                                  const int32_t* begin, const int32_t* fine, const int32_t* rank, int32_t* loc,
+                                  int32_t* perm, cudaStream_t s) {
+    scatter_ranked_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>((const int2*)xy, n, x0, y0, K, L, Lf, begin,
+                                                                     fine, rank, loc, perm);
     return cudaGetLastError();
 }
 
