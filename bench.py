@@ -316,6 +316,65 @@ def serve_leg(lfmm, n_requests: int, slots: int, check: int = 24):
                     "tol 1e-6 -> mixed path p = 8, tol 1e-10 -> float-float path p = 16 (leaf 192)"}
 
 
+# ---------------------------------------------------------------- batched forest leg
+def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
+    """The batched workload: 4,096 independent problems (N_src log-uniform in [512, 8192],
+    box side 4 sqrt(N), targets = sources) in one forest plan, mixed path p = 8; one step
+    = lfmm_forest_create + lfmm_eval with inputs resident in device memory, L2 flushed
+    before each step; 24 problems checked in full against the oracle."""
+    import torch
+    import oracle
+    from paper_1105_3505_gb300 import workloads
+    t_gen = time.perf_counter()
+    probs = workloads.forest_4096()
+    t_gen = time.perf_counter() - t_gen
+    src = np.ascontiguousarray(np.concatenate([p.src for p in probs]))
+    tgt = np.ascontiguousarray(np.concatenate([p.tgt for p in probs]))
+    f = np.concatenate([p.f for p in probs])
+    so = np.concatenate([[0], np.cumsum([p.src.shape[0] for p in probs])]).astype(np.int64)
+    to = np.concatenate([[0], np.cumsum([p.tgt.shape[0] for p in probs])]).astype(np.int64)
+    dev = torch.device("cuda:0")
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (src, tgt, f))
+    u_d = torch.empty(tgt.shape[0], dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    opts = lfmm.make_opts(lfmm.LFMM_MIXED, 8, 64, 32, 64)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        h = lfmm.lfmm_forest_create(s_d, so, t_d, to, opts, stream)
+        lfmm.lfmm_eval(h, f_d, u_d, stream)
+        return h
+
+    for _ in range(warmup):
+        lfmm.lfmm_plan_destroy(step())
+    torch.cuda.synchronize()
+    evs = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h = step()
+        b.record(stream)
+        lfmm.lfmm_plan_destroy(h)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    h = step()
+    info = lfmm.lfmm_plan_get_info(h)
+    torch.cuda.synchronize()
+    lfmm.lfmm_plan_destroy(h)
+    u = u_d.cpu().numpy()
+    err = 0.0
+    for i in np.random.default_rng(11).choice(len(probs), 24, replace=False):
+        ref = oracle.lattice_sum(probs[i].src, probs[i].f, probs[i].tgt)
+        err = max(err, float(np.abs(u[to[i]:to[i + 1]] - ref).max() / np.abs(ref).max()))
+    pts = int(src.shape[0] + tgt.shape[0])
+    return {"workload": "forest_4096: 4,096 problems, N log-uniform in [512, 8192], side 4 sqrt(N), targets = sources, seed 3",
+            "points": pts, "ms_per_step": ms, "Mpoints_per_s": pts / (ms * 1e-3) / 1e6,
+            "leaf_side": info["leaf_side"], "boxes": info["n_boxes"], "max_rel_err_24_problems": err,
+            "step": "lfmm_forest_create + lfmm_eval", "generation_s": t_gen}
+
+
 # ---------------------------------------------------------------- replicas
 def replica_throughput(ms_local, points_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` independent replicas: every rank solved
@@ -505,6 +564,7 @@ def main():
             out[key] = {"value": (ns + nt) / (ms2 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms2,
                         "rel_err": float(np.abs(u2[idx] - ref).max() / scale), "leaf_size": leaf}
         out["cpu_baseline"] = cpu_baseline(prob)
+        out["forest"] = forest_leg(lfmm)
         if args.serve_requests > 0:
             out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots)
     print(json.dumps(out), flush=True)

@@ -246,7 +246,9 @@ int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, const int32_t*
 #define LFMM_PHASE_P2P 5        /* step 5: near field, T_tfi, binary64 final sum        */
 #define LFMM_PHASE_COPY 6       /* host<->device copies of coordinates, f and u         */
 #define LFMM_PHASE_M2L_TC 7     /* steps 3-4 on the tensor cores (fp32 levels, P <= 32) */
-#define LFMM_NUM_PHASES 8
+#define LFMM_PHASE_L2P 8        /* step 5 far part and final sum, when the near field   */
+                                /* runs concurrently with the far-field sweeps          */
+#define LFMM_NUM_PHASES 9
 
 /* Turn per-phase timing on (1) or off (0).  While on, every create/eval synchronises its
  * stream once at the end to read the events.  Process-wide. */

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "lfmm_internal.h"
@@ -52,10 +53,58 @@ struct lfmm_plan {
     double* f_stage = nullptr;     // device copy of a host f
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
     std::unique_ptr<Forest> forest;  // pruned tree or forest (null: uniform tree)
+    void* tc_split = nullptr;        // TF32 hi/lo copies of q_hat and the parent u_hat for the tensor cores
+    double* un_tmp = nullptr;        // near field per target (caller order) from the concurrent near-field pass
+    double* uf_tmp = nullptr;        // far field per target (caller order), before the final sum
+    struct AuxStream* aux = nullptr;  // near-field pass runs here, beside the far-field sweeps
     int64_t n_boxes = 0;
 };
 
+// A second stream with its fork / join events, pooled process-wide (plans are often
+// short-lived; creating streams and events per plan would cost more than the overlap
+// gains on small problems).
+struct AuxStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int device = -1;
+};
+
 namespace {
+
+std::mutex g_aux_mu;
+std::vector<AuxStream*> g_aux_free;
+
+AuxStream* acquire_aux(int device) {
+    {
+        std::lock_guard<std::mutex> g(g_aux_mu);
+        for (size_t i = 0; i < g_aux_free.size(); ++i)
+            if (g_aux_free[i]->device == device) {
+                AuxStream* a = g_aux_free[i];
+                g_aux_free.erase(g_aux_free.begin() + i);
+                return a;
+            }
+    }
+    AuxStream* a = new (std::nothrow) AuxStream();
+    if (!a) return nullptr;
+    a->device = device;
+    if (cudaStreamCreateWithFlags(&a->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (a->s) cudaStreamDestroy(a->s);
+        if (a->fork) cudaEventDestroy(a->fork);
+        delete a;
+        return nullptr;
+    }
+    return a;
+}
+
+void release_aux(AuxStream* a) {
+    if (!a) return;
+    cudaStreamSynchronize(a->s);
+    std::lock_guard<std::mutex> g(g_aux_mu);
+    g_aux_free.push_back(a);
+}
 
 constexpr int kMaxLevel = 14;  // deepest leaf level searched (pruned storage beyond 4^13 leaves)
 
@@ -365,10 +414,21 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         boxes += (int64_t)1 << (2 * l);
     }
     p->n_boxes = boxes;
+    if (p->opts.precision == LFMM_MIXED && p->NP == 32 && p->L >= (p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level)) {
+        // largest tensor-core level: TF32 hi/lo of its q_hat and of its parent's u_hat
+        const size_t n = ((size_t)p->NP << (2 * p->L)) * 2 + ((size_t)p->NP << (2 * std::max(0, p->L - 1))) * 2;
+        if ((st = palloc(p, &p->tc_split, n * sizeof(float), s))) return st;
+    }
     if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
     if ((st = palloc(p, &p->Cbox, (size_t)boxes * 8, s))) return st;
+    if (p->L >= 2) {  // a far field: near and far parts go to these buffers, then one sum
+        void* b;
+        if ((st = palloc(p, &b, (size_t)2 * p->nt * sizeof(double), s))) return st;
+        p->un_tmp = (double*)b;
+        p->uf_tmp = p->un_tmp + p->nt;
+    }
     void* stbuf;
     if ((st = palloc(p, &stbuf, 16, s))) return st;
     p->status = (int*)stbuf;
@@ -410,6 +470,12 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, Qx(L), Qm(L), s));
         pt.add_launches(1);
     }
+    // The near field depends only on the sorted charges and the leaf charges (P2M): it
+    // runs on the plan's second stream beside the per-level M2L launches and the L2P
+    // (after the cooperative coarse-level kernels, which need the whole device), and
+    // one elementwise sum joins the two.
+    if (L >= 2 && p->un_tmp && !p->aux) p->aux = acquire_aux(p->device);
+    const bool concurrent = L >= 2 && p->un_tmp != nullptr && p->aux != nullptr;
     LevelBufs lb;
     for (int l = std::min(2, L); l <= L && l < 16; ++l) {
         lb.q[l] = Qx(l);
@@ -438,14 +504,49 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
             l_first = last + 1;
         }
     }
+    if (concurrent) {
+        LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
+        LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
+        PhaseTimer pt(LFMM_PHASE_P2P, p->aux->s);
+        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Qm(L), nullptr, p->un_tmp,
+                                        nullptr, p->num_sms, p->aux->s));
+        pt.add_launches(1);
+    }
     for (int l = l_first; l <= L; ++l) {
         const bool tc = m2l_uses_tc(ops, L - l, l, p->tc_min_level, sizeof(T) == 4);
         PhaseTimer pt(tc ? LFMM_PHASE_M2L_TC : LFMM_PHASE_M2L, s);
+        if constexpr (sizeof(T) == 4) {
+            if (tc) {
+                float* qhi = (float*)p->tc_split;
+                float* qlo = qhi + ((size_t)NP << (2 * l));
+                float* uhi = qlo + ((size_t)NP << (2 * l));
+                float* ulo = uhi + ((size_t)NP << (2 * (l - 1)));
+                LFMM_CUDA_TRY(launch_split_tf32((const float*)Qx(l), qhi, qlo, (int64_t)NP << (2 * l), s));
+                if (l >= 3)
+                    LFMM_CUDA_TRY(launch_split_tf32((const float*)Ux(l - 1), uhi, ulo, (int64_t)NP << (2 * (l - 1)), s));
+                LFMM_CUDA_TRY(launch_m2l_tc_ss(ops, L - l, l, qhi, qlo, Qm(l), l >= 3 ? uhi : nullptr,
+                                               l >= 3 ? ulo : nullptr, l >= 3 ? Cm(l - 1) : nullptr, (float*)Ux(l),
+                                               Cm(l), p->status, s));
+                pt.add_launches(l >= 3 ? 3 : 2);
+                continue;
+            }
+        }
         LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
                                     l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), p->tc_min_level, p->status, s));
         pt.add_launches(1);
     }
-    {
+    if (concurrent) {
+        {
+            PhaseTimer pt(LFMM_PHASE_L2P, s);
+            LFMM_CUDA_TRY(launch_l2p<T>(t, ops, Ux(L), Cm(L), p->uf_tmp, s));
+            pt.add_launches(1);
+        }
+        LFMM_CUDA_TRY(cudaEventRecord(p->aux->join, p->aux->s));
+        LFMM_CUDA_TRY(cudaStreamWaitEvent(s, p->aux->join, 0));
+        PhaseTimer pt(LFMM_PHASE_L2P, s);
+        LFMM_CUDA_TRY(launch_combine(p->nt, p->un_tmp, p->uf_tmp, u, un, uf, s));
+        pt.add_launches(1);
+    } else {
         PhaseTimer pt(LFMM_PHASE_P2P, s);
         LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, L >= 2 ? Ux(L) : nullptr,
                                         L >= 2 ? Cm(L) : nullptr, Qm(L), u, un, uf, p->num_sms, s));
@@ -563,6 +664,7 @@ int lfmm_plan_destroy(lfmm_plan* plan) {
     if (!plan) return LFMM_OK;
     free_plan_buffers(plan);
     cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    release_aux(plan->aux);
     delete plan;
     if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("plan destroy: ") + cudaGetErrorString(e));
     return LFMM_OK;

@@ -1096,6 +1096,65 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
     }
 }
 
+// ------------------------------------------------------------------------- L2P, final sum
+// Far field of every target when the near field runs as a separate pass: one warp per
+// leaf (row-major), lanes own expansion entries p; per target one coalesced row of
+// T_ofs^T against the leaf's incoming expansion, reduce-scattered so that lane q holds
+// target q's value; uf = far + C in binary64, caller order.
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) l2p_kernel(int L, int side, const int32_t* __restrict__ tbeg,
+                                                          const int32_t* __restrict__ tloc,
+                                                          const int32_t* __restrict__ tperm,
+                                                          const T* __restrict__ uhat,
+                                                          const typename Mono<T>::V* __restrict__ Cleaf,
+                                                          const T* __restrict__ tofsT, double* __restrict__ uf) {
+    using M = Mono<T>;
+    constexpr int PL = NP / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_leaves = (int64_t)1 << (2 * L);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves; leaf += nw) {
+        const int tb = tbeg[leaf], te = tbeg[leaf + 1];
+        if (tb == te) continue;
+        const uint32_t mort = morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L));
+        T uh[PL];
+#pragma unroll
+        for (int i = 0; i < PL; ++i) uh[i] = uhat[(size_t)mort * NP + lane + 32 * i];
+        const double cl = M::to_double(Cleaf[mort]);
+        for (int t0 = tb; t0 < te; t0 += 32) {
+            const int n = min(32, te - t0);
+            const int l = tloc[t0 + min(lane, n - 1)];
+            const int myJ = (l & 0xffff) + side * (l >> 16);
+            T part[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int Jq = shfl(myJ, q);
+                T w = T(0);
+                if (q < n) {
+                    const T* row = tofsT + (size_t)Jq * NP;
+#pragma unroll
+                    for (int i = 0; i < PL; ++i) w = fma(ldg(row + lane + 32 * i), uh[i], w);
+                }
+                part[q] = w;
+            }
+            const T far = reduce_scatter32(part);
+            if (lane < n) uf[tperm[t0 + lane]] = (double)far + cl;
+        }
+    }
+}
+
+
+// u = u_near + u_far (caller order), and the parts where requested
+__global__ void combine_kernel(int64_t n, const double* __restrict__ un, const double* __restrict__ uf,
+                               double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = un[i], b = uf[i];
+        if (u) u[i] = a + b;
+        if (u_near) u_near[i] = a;
+        if (u_far) u_far[i] = b;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------- launchers
@@ -1356,11 +1415,38 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
     return e;
 }
 
+template <typename T>
+cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_leaf, const void* Cleaf, double* uf,
+                       cudaStream_t s) {
+    using V = typename Mono<T>::V;
+    int64_t blocks = (t.n_leaves * 32 + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    if (ops.NP == 32)
+        l2p_kernel<T, 32><<<(int)blocks, 256, 0, s>>>(t.L, t.side, t.tgt_begin, t.tgt_loc, t.tgt_perm, uhat_leaf,
+                                                              (const V*)Cleaf, (const T*)ops.tofsT, uf);
+    else
+        l2p_kernel<T, 64><<<(int)blocks, 256, 0, s>>>(t.L, t.side, t.tgt_begin, t.tgt_loc, t.tgt_perm, uhat_leaf,
+                                                              (const V*)Cleaf, (const T*)ops.tofsT, uf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double* u, double* u_near, double* u_far,
+                           cudaStream_t s) {
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    combine_kernel<<<(int)blocks, 256, 0, s>>>(n, un, uf, u, u_near, u_far);
+    return cudaGetLastError();
+}
+
 #define LFMM_INSTANTIATE(T)                                                                                   \
     template cudaError_t launch_m2m_fused<T>(const DeviceOps&, int, const LevelBufs&, unsigned*, int*, int,      \
                                              cudaStream_t);                                                  \
     template cudaError_t launch_m2l_fused<T>(const DeviceOps&, int, const LevelBufs&, int, unsigned*, int*, int, \
                                              int*, cudaStream_t);                                            \
+    template cudaError_t launch_l2p<T>(const TreeView&, const DeviceOps&, const T*, const void*, double*,          \
+                                       cudaStream_t);                                                        \
     template cudaError_t launch_p2m<T>(const TreeView&, const DeviceOps&, const double*, T*, T*, void*,       \
                                        cudaStream_t);                                                         \
     template cudaError_t launch_m2m<T>(const DeviceOps&, int, int, const T*, const void*, T*, void*,         \

@@ -289,6 +289,13 @@ cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0,
 template <typename T>
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
                        T* qhat_leaf, void* Q_leaf, cudaStream_t s);
+// Far field of every target (L2P + incoming constant), binary64, caller order.
+template <typename T>
+cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_leaf, const void* Cleaf, double* uf,
+                       cudaStream_t s);
+// u = un + uf elementwise (and the parts, where requested; any output may be null).
+cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double* u, double* u_near, double* u_far,
+                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_m2m(const DeviceOps& ops, int k, int level, const T* q_child, const void* Q_child,
                        T* q_parent, void* Q_parent, cudaStream_t s);
@@ -322,6 +329,13 @@ template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
                        const T* u_parent, const void* C_parent, T* u_level, void* C_level,
                        int tc_min_level, int* status, cudaStream_t s);
+// Shared-memory form of the tensor-core M2L: the level's expansions and the parent
+// level's incoming expansions pre-split into TF32 hi / lo arrays (launch_split_tf32).
+cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float* qhi, const float* qlo,
+                             const void* Q_level, const float* uhi, const float* ulo, const void* C_parent,
+                             float* u_level, void* C_level, int* status, cudaStream_t s);
+// hi = TF32(x), lo = TF32(x - hi), n floats (a multiple of 4).
+cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s);
 cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level,
                           const void* Q_level, const float* u_parent, const void* C_parent,
                           float* u_level, void* C_level, int* status, cudaStream_t s);

@@ -126,6 +126,20 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// D[tmem] (+)= A[smem descriptor] x B[smem descriptor], kind::tf32, cta_group::1
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// makes this thread's completed cp.async writes to shared memory visible to the tensor core
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -451,6 +465,281 @@ __global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const flo
     }
 }
 
+
+// ---------------------------------------------------------------------------------
+// Second form: both operands from shared memory.  The expansions of the level (and the
+// parent level's incoming expansions) are split once into TF32 hi and lo arrays by
+// split_tf32_kernel; each K-step copies the 128 gathered source rows of hi and of lo
+// (cp.async, 16-byte chunks) straight into the 128-byte-swizzled K-major layout that a
+// shared-memory matrix descriptor describes, so the tensor core reads A like B and no
+// thread touches the values between the gather and the MMA.  TMEM holds only the two
+// accumulator pairs (128 columns).
+//   step s: fold in the partials of step s-1 (waiting for its MMAs, which also frees the
+//   A stage it read), start the gather of step s+1 into that stage, wait for the own
+//   copies of step s, make them visible to the tensor core, barrier; one thread issues
+//   the 12 MMAs of step s and the B copy of step s+2.
+constexpr int kTc2Cols = 128;  // D_big[b]: [32b, 32b+32), D_small[b]: [64+32b, 96+32b)
+
+__global__ void __launch_bounds__(kTcThreads) m2l_tc_ss_kernel(int level, const float* __restrict__ qhi,
+                                                               const float* __restrict__ qlo,
+                                                               const float* __restrict__ uhi,
+                                                               const float* __restrict__ ulo,
+                                                               const float* __restrict__ tiles,
+                                                               const float* __restrict__ mono,
+                                                               const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar,
+                                                               float* __restrict__ out, DFv* __restrict__ Cout,
+                                                               int* __restrict__ status) {
+    constexpr int NP = 32;
+    // dynamic shared memory (1024-byte aligned): B ring [3][hi, lo][32 x 32], then the A
+    // stages [2][hi, lo][128 x 32], all 128-byte swizzled
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    float (*sB)[2][1024] = reinterpret_cast<float (*)[2][1024]>(
+        tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u));
+    float (*sA)[2][kTcThreads * 32] = reinterpret_cast<float (*)[2][kTcThreads * 32]>(&sB[3][0][0]);
+    __shared__ __align__(8) uint64_t bar_b[3], bar_mma[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_off[27][3];
+    __shared__ int s_abort;
+    __shared__ int s_src[28][kTcThreads];
+
+    const int cls = blockIdx.y;
+    const int px = cls & 1, py = cls >> 1;
+    const int lg = level - 1;
+    const int np_side = 1 << lg;
+    const int64_t n_rows = (int64_t)1 << (2 * lg);
+    const int64_t row = (int64_t)blockIdx.x * kTcThreads + threadIdx.x;
+    const bool valid = row < n_rows;
+    const int side = 1 << level;
+    const bool has_l2l = uhi != nullptr;
+    const int n_steps = 27 + (has_l2l ? 1 : 0);
+    const int warp = threadIdx.x >> 5;
+    const int ri = valid ? (int)(row & (np_side - 1)) : 0;
+    const int rj = valid ? (int)(row >> lg) : 0;
+
+    if (smem_u32(&sB[0][0][0]) & 1023u) {
+        if (threadIdx.x == 0) atomicExch(status, LFMM_EINTERNAL);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        int nn = 0;
+        for (int d = 0; d < 36; ++d) {
+            const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            s_off[nn][0] = dx;
+            s_off[nn][1] = dy;
+            s_off[nn][2] = offset_index_tc(dx, dy);
+            ++nn;
+        }
+        for (int i = 0; i < 3; ++i) mbar_init(&bar_b[i], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, kTc2Cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    for (int st = 0; st < 27; ++st) {
+        int si = -1;
+        if (valid) {
+            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
+            if (sx >= 0 && sx < side && sy >= 0 && sy < side) si = (int)morton2(sx, sy);
+        }
+        s_src[st][threadIdx.x] = si;
+    }
+    s_src[27][threadIdx.x] = (valid && has_l2l) ? (int)morton2(ri, rj) : -1;
+    __syncthreads();
+    const uint32_t tmem = s_tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+
+    // gather of step `step` into A stage b: thread t copies 16-byte chunk t % 8 of rows
+    // t / 8 + 16 j of hi and of lo; chunk c of row r lands at chunk c ^ (r % 8)
+    auto gather = [&](int step, int b) {
+        const int ch = threadIdx.x & 7;
+        const float* hsrc = step < 27 ? qhi : uhi;
+        const float* lsrc = step < 27 ? qlo : ulo;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int r = (threadIdx.x >> 3) + 16 * j;
+            const int si = s_src[step][r];
+            const size_t off = si < 0 ? 0 : (size_t)si * NP + 4 * ch;
+            const int bytes = si < 0 ? 0 : 16;
+            const int pos = r * 32 + ((ch ^ (r & 7)) << 2);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(&sA[b][0][pos])),
+                         "l"(hsrc + off), "r"(bytes)
+                         : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(&sA[b][1][pos])),
+                         "l"(lsrc + off), "r"(bytes)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    auto b_src = [&](int step) -> const float* {
+        return step < 27 ? tiles + (size_t)s_off[step][2] * 2048 : tiles + (size_t)(kNumOffsets + cls) * 2048;
+    };
+
+    constexpr uint32_t kIdesc = idesc_tf32(128, NP);
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    auto flush = [&](int b) {
+        uint32_t big[32], small[32];
+        tmem_ld32(tmem + lane_base + 32 * b, big);
+        tmem_ld32(tmem + lane_base + 64 + 32 * b, small);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+    };
+    volatile int* vabort = &s_abort;
+    int issued_steps = 0, b_issued = 0;
+    if (threadIdx.x == 0) {  // B tiles of steps 0 and 1
+        for (int st = 0; st < 2 && st < n_steps; ++st) {
+            mbar_arrive_expect_tx(&bar_b[st], 8192);
+            bulk_g2s(&sB[st][0][0], b_src(st), 8192, &bar_b[st]);
+            b_issued = st + 1;
+        }
+    }
+    gather(0, 0);
+    // Aborts are block-uniform: a failed wait only records s_abort; every thread tests
+    // it right after the step's barrier, so all warps leave the loop at the same step
+    // and meet the same barriers afterwards.
+    for (int step = 0; step < n_steps; ++step) {
+        const int buf = step & 1;
+        bool w_ok = true;
+        if (step >= 1) {
+            // MMAs of step - 1 done: their partials in, their A stage free
+            w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[buf ^ 1], ((step - 1) >> 1) & 1);
+            w_ok = __all_sync(0xffffffffu, w_ok);
+            if (w_ok) {
+                tc_fence_after();
+                flush(buf ^ 1);
+            } else {
+                atomicExch(&s_abort, 1);
+            }
+        }
+        if (w_ok && step + 1 < n_steps) {
+            gather(step + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (*vabort != 0) break;
+        if (threadIdx.x == 0) {
+            const int slot = step % 3;
+            const bool good = mbar_wait_bounded(&bar_b[slot], (step / 3) & 1);
+            if (!good) {
+                atomicExch(&s_abort, 1);  // seen by all after the next barrier
+            } else {
+                tc_fence_after();
+                const uint32_t a_hi = smem_u32(&sA[buf][0][0]), a_lo = smem_u32(&sA[buf][1][0]);
+                const uint32_t b_hi = smem_u32(&sB[slot][0][0]), b_lo = smem_u32(&sB[slot][1][0]);
+                const uint32_t d_big = tmem + 32 * buf, d_small = tmem + 64 + 32 * buf;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ah = smem_desc_sw128(a_hi + 32 * kk), al = smem_desc_sw128(a_lo + 32 * kk);
+                    const uint64_t bh = smem_desc_sw128(b_hi + 32 * kk), bl = smem_desc_sw128(b_lo + 32 * kk);
+                    mma_tf32_ss(d_big, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, ah, bl, kIdesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, al, bh, kIdesc, 1u);
+                }
+                mma_commit(&bar_mma[buf]);
+                // B tiles of step + 2 into the slot step - 1 used (its MMAs are done)
+                if (step + 2 < n_steps) {
+                    const int ns = (step + 2) % 3;
+                    mbar_arrive_expect_tx(&bar_b[ns], 8192);
+                    bulk_g2s(&sB[ns][0][0], b_src(step + 2), 8192, &bar_b[ns]);
+                    b_issued = step + 3;
+                }
+            }
+        }
+        issued_steps = step + 1;
+    }
+
+    // incoming constant (compensated), one box per thread, while the last MMAs run
+    if (valid) {
+        DFv sacc = has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
+        for (int c0 = 0; c0 < 27; c0 += 9) {
+            DFv qv[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int si = s_src[c0 + k][threadIdx.x];
+                qv[k] = si >= 0 ? Qin[si] : DFv{0.f, 0.f};
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int o = s_off[c0 + k][2];
+                sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+            }
+        }
+        Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
+    }
+
+    // partials of the last step; after an abort, wait (bounded) for what was issued
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    bool ok = s_abort == 0;
+    if (ok && n_steps > 0) {
+        const int st = n_steps - 1;
+        bool w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
+        w_ok = __all_sync(0xffffffffu, w_ok);
+        if (!w_ok) {
+            atomicExch(&s_abort, 1);
+            ok = false;
+        } else {
+            tc_fence_after();
+            flush(st & 1);
+        }
+    }
+    __syncthreads();
+    if (s_abort) ok = false;
+    if (!ok) {
+        for (int st = max(0, issued_steps - 2); st < issued_steps; ++st)
+            mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
+        if (threadIdx.x == 0 && b_issued > 0)
+            for (int st = max(0, b_issued - 2); st < b_issued; ++st) mbar_wait_bounded(&bar_b[st % 3], (st / 3) & 1);
+    }
+    if (ok) {
+        if (valid) {
+            float4* dst = reinterpret_cast<float4*>(out + (size_t)morton2(2 * ri + px, 2 * rj + py) * NP);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(status, LFMM_ETIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTc2Cols);
+    }
+}
+
+// hi = TF32 round-to-nearest of x, lo = the same of the remainder (the A operand split
+// of the shared-memory form), elementwise over n floats (n a multiple of 4)
+__global__ void split_tf32_kernel(const float4* __restrict__ x, float4* __restrict__ hi, float4* __restrict__ lo,
+                                  int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x[i];
+        const float a[4] = {v.x, v.y, v.z, v.w};
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = __uint_as_float(tf32_rna_bits(a[e]));
+            l[e] = __uint_as_float(tf32_rna_bits(a[e] - h[e]));
+        }
+        hi[i] = make_float4(h[0], h[1], h[2], h[3]);
+        lo[i] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
@@ -466,6 +755,32 @@ cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q
     m2l_tc_kernel<<<grid, kTcThreads, smem, s>>>(level, q_level, u_parent, (const float*)ops.tc[k],
                                               (const float*)ops.mono[k], (const DFv*)Q_level,
                                               (const DFv*)C_parent, u_level, (DFv*)C_level, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s) {
+    const int64_t n4 = n / 4;
+    int64_t blocks = (n4 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    split_tf32_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(hi),
+                                                   reinterpret_cast<float4*>(lo), n4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float* qhi, const float* qlo,
+                             const void* Q_level, const float* uhi, const float* ulo, const void* C_parent,
+                             float* u_level, void* C_level, int* status, cudaStream_t s) {
+    constexpr size_t smem = 1024 + sizeof(float) * (3 * 2 * 1024 + 2 * 2 * kTcThreads * 32);
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tc_ss_kernel, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t rows = (int64_t)1 << (2 * (level - 1));
+    dim3 grid((unsigned)((rows + kTcThreads - 1) / kTcThreads), 4);
+    m2l_tc_ss_kernel<<<grid, kTcThreads, smem, s>>>(level, qhi, qlo, uhi, ulo, (const float*)ops.tc[k],
+                                                    (const float*)ops.mono[k], (const DFv*)Q_level,
+                                                    (const DFv*)C_parent, u_level, (DFv*)C_level, status);
     return cudaGetLastError();
 }
 

@@ -245,7 +245,7 @@ def lfmm_model_s(leaf_side: int, p: int, proxies_per_edge: int, level_above_leaf
     return out
 
 
-PHASES = ("tree", "operators", "p2m", "m2m", "m2l", "p2p", "copy", "m2l_tc")
+PHASES = ("tree", "operators", "p2m", "m2m", "m2l", "p2p", "copy", "m2l_tc", "l2p")
 
 
 def lfmm_profile_enable(enable: bool) -> None:
