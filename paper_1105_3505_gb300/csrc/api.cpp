@@ -42,6 +42,7 @@ struct lfmm_plan {
     int64_t bytes = 0;
     int32_t *src_begin = nullptr, *tgt_begin = nullptr;
     int32_t *src_loc = nullptr, *src_perm = nullptr, *tgt_loc = nullptr, *tgt_perm = nullptr;
+    int32_t* tgt_leaf = nullptr;   // Morton index of each sorted target's leaf
     void* f_sorted = nullptr;
     void* qhat = nullptr;
     void* uhat = nullptr;
@@ -380,16 +381,17 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     if ((st = talloc(part, scan_partials_size(n_leaves) * sizeof(int32_t), s))) return st;
     LFMM_CUDA_TRY(launch_scan2(cs, p->src_begin, ct, p->tgt_begin, p->L, (int32_t*)part.ptr, s));
     tree_timer->add_launches(3);
-    if ((st = palloc(p, &buf, (size_t)2 * (p->ns + p->nt) * sizeof(int32_t), s))) return st;
+    if ((st = palloc(p, &buf, (size_t)(2 * (p->ns + p->nt) + p->nt) * sizeof(int32_t), s))) return st;
     p->src_loc = (int32_t*)buf;
     p->src_perm = p->src_loc + p->ns;
     p->tgt_loc = p->src_perm + p->ns;
     p->tgt_perm = p->tgt_loc + p->nt;
+    p->tgt_leaf = p->tgt_perm + p->nt;
     // bucket by the histogram ranks (no second atomic pass)
     LFMM_CUDA_TRY(launch_scatter_ranked(src, p->ns, p->x0, p->y0, p->K, p->L, Lf_last, p->src_begin, fs_last,
                                         (const int32_t*)ranks.ptr, p->src_loc, p->src_perm, s));
     LFMM_CUDA_TRY(launch_scatter_ranked(tgt, p->nt, p->x0, p->y0, p->K, p->L, Lf_last, p->tgt_begin, ft_last,
-                                        (const int32_t*)ranks.ptr + p->ns, p->tgt_loc, p->tgt_perm, s));
+                                        (const int32_t*)ranks.ptr + p->ns, p->tgt_loc, p->tgt_perm, s, p->tgt_leaf));
     tree_timer->add_launches(2);
     tree_timer.reset();
     PhaseTimer op_timer(LFMM_PHASE_OPERATORS, s);
@@ -454,6 +456,8 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     t.src_perm = p->src_perm;
     t.tgt_loc = p->tgt_loc;
     t.tgt_perm = p->tgt_perm;
+    t.tgt_leaf = p->tgt_leaf;
+    t.n_tgt = p->nt;
     t.max_leaf_src = p->max_src;
     t.max_leaf_tgt = p->max_tgt;
     const DeviceOps& ops = *p->ops;

@@ -1097,52 +1097,44 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
 }
 
 // ------------------------------------------------------------------------- L2P, final sum
-// Far field of every target when the near field runs as a separate pass: one warp per
-// leaf (row-major), lanes own expansion entries p; per target one coalesced row of
-// T_ofs^T against the leaf's incoming expansion, reduce-scattered so that lane q holds
-// target q's value; uf = far + C in binary64, caller order.
-template <typename T, int NP>
-__global__ void __launch_bounds__(256) l2p_kernel(int L, int side, const int32_t* __restrict__ tbeg,
-                                                          const int32_t* __restrict__ tloc,
-                                                          const int32_t* __restrict__ tperm,
-                                                          const T* __restrict__ uhat,
-                                                          const typename Mono<T>::V* __restrict__ Cleaf,
-                                                          const T* __restrict__ tofsT, double* __restrict__ uf) {
+// Far field of every target when the near field runs as a separate pass: one thread per
+// sorted target, uf[caller index] = T_ofs(:, J)^T u_hat_leaf + C_leaf in binary64.
+// T_ofs^T ([s^2][NP]) is staged in shared memory with row stride NP + 1, so the 32
+// targets of a warp, at random local positions, read element p of their rows from 32
+// different banks; the leaf's expansion row is shared by its ~N_leaf consecutive targets.
+template <typename T, int NP, bool SMEM>
+__global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const int32_t* __restrict__ tleaf,
+                                                  const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
+                                                  const T* __restrict__ uhat,
+                                                  const typename Mono<T>::V* __restrict__ Cleaf,
+                                                  const T* __restrict__ tofsT, double* __restrict__ uf) {
     using M = Mono<T>;
-    constexpr int PL = NP / 32;
-    const int lane = threadIdx.x & 31;
-    const int64_t n_leaves = (int64_t)1 << (2 * L);
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves; leaf += nw) {
-        const int tb = tbeg[leaf], te = tbeg[leaf + 1];
-        if (tb == te) continue;
-        const uint32_t mort = morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L));
-        T uh[PL];
+    constexpr int E = (int)(16 / sizeof(T));
+    constexpr int RS = NP + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* st = reinterpret_cast<T*>(smem_raw);
+    if (SMEM) {
+        const int rows = side * side;
+        for (int i = threadIdx.x; i < rows * NP; i += blockDim.x) st[(i / NP) * RS + (i % NP)] = tofsT[i];
+        __syncthreads();
+    }
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        const int leaf = tleaf[t];
+        const int l = tloc[t];
+        const int J = (l & 0xffff) + side * (l >> 16);
+        const T* row = SMEM ? st + J * RS : tofsT + (size_t)J * NP;  // (table too large: L1 / L2)
+        const uint4* uh = reinterpret_cast<const uint4*>(uhat + (size_t)leaf * NP);
+        T far = T(0);
 #pragma unroll
-        for (int i = 0; i < PL; ++i) uh[i] = uhat[(size_t)mort * NP + lane + 32 * i];
-        const double cl = M::to_double(Cleaf[mort]);
-        for (int t0 = tb; t0 < te; t0 += 32) {
-            const int n = min(32, te - t0);
-            const int l = tloc[t0 + min(lane, n - 1)];
-            const int myJ = (l & 0xffff) + side * (l >> 16);
-            T part[32];
+        for (int c = 0; c < NP / E; ++c) {
+            const uint4 ur = __ldg(uh + c);
+            const T* v = reinterpret_cast<const T*>(&ur);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int Jq = shfl(myJ, q);
-                T w = T(0);
-                if (q < n) {
-                    const T* row = tofsT + (size_t)Jq * NP;
-#pragma unroll
-                    for (int i = 0; i < PL; ++i) w = fma(ldg(row + lane + 32 * i), uh[i], w);
-                }
-                part[q] = w;
-            }
-            const T far = reduce_scatter32(part);
-            if (lane < n) uf[tperm[t0 + lane]] = (double)far + cl;
+            for (int e = 0; e < E; ++e) far = fma(row[c * E + e], v[e], far);
         }
+        uf[tperm[t]] = (double)far + M::to_double(Cleaf[leaf]);
     }
 }
-
 
 // u = u_near + u_far (caller order), and the parts where requested
 __global__ void combine_kernel(int64_t n, const double* __restrict__ un, const double* __restrict__ uf,
@@ -1419,16 +1411,31 @@ template <typename T>
 cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_leaf, const void* Cleaf, double* uf,
                        cudaStream_t s) {
     using V = typename Mono<T>::V;
-    int64_t blocks = (t.n_leaves * 32 + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    if (blocks < 1) blocks = 1;
-    if (ops.NP == 32)
-        l2p_kernel<T, 32><<<(int)blocks, 256, 0, s>>>(t.L, t.side, t.tgt_begin, t.tgt_loc, t.tgt_perm, uhat_leaf,
-                                                              (const V*)Cleaf, (const T*)ops.tofsT, uf);
-    else
-        l2p_kernel<T, 64><<<(int)blocks, 256, 0, s>>>(t.L, t.side, t.tgt_begin, t.tgt_loc, t.tgt_perm, uhat_leaf,
-                                                              (const V*)Cleaf, (const T*)ops.tofsT, uf);
-    return cudaGetLastError();
+    if (!t.tgt_leaf) return cudaErrorInvalidValue;
+    const size_t table = (size_t)t.side * t.side * (ops.NP + 1) * sizeof(T);
+    const bool in_smem = table <= 96 * 1024;
+    const size_t smem = in_smem ? table : 0;
+    auto go = [&](auto np_tag, auto smem_tag) -> cudaError_t {
+        constexpr int NPc = decltype(np_tag)::value;
+        constexpr bool SM = decltype(smem_tag)::value;
+        const void* fn = (const void*)l2p_kernel<T, NPc, SM>;
+        cudaError_t e = ensure_dynamic_smem(fn, smem);
+        if (e != cudaSuccess) return e;
+        // persistent: each block stages the table once
+        int64_t blocks = (t.n_tgt + 255) / 256;
+        const int64_t cap = (int64_t)152 * blocks_per_sm(fn, 256, smem);
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        l2p_kernel<T, NPc, SM><<<(int)blocks, 256, smem, s>>>(t.n_tgt, t.side, t.tgt_leaf, t.tgt_loc, t.tgt_perm,
+                                                              uhat_leaf, (const V*)Cleaf, (const T*)ops.tofsT, uf);
+        return cudaGetLastError();
+    };
+    using I32 = std::integral_constant<int, 32>;
+    using I64 = std::integral_constant<int, 64>;
+    using BT = std::true_type;
+    using BF = std::false_type;
+    if (ops.NP == 32) return in_smem ? go(I32(), BT()) : go(I32(), BF());
+    return in_smem ? go(I64(), BT()) : go(I64(), BF());
 }
 
 cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double* u, double* u_near, double* u_far,

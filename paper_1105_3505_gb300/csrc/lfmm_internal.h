@@ -181,6 +181,8 @@ struct TreeView {
     const int32_t* src_perm = nullptr;   // caller index of each sorted source
     const int32_t* tgt_loc = nullptr;
     const int32_t* tgt_perm = nullptr;
+    const int32_t* tgt_leaf = nullptr;   // Morton index of each sorted target's leaf
+    int64_t n_tgt = 0;         // targets
     int max_leaf_src = 0;      // largest leaf occupancies (size the P2P staging)
     int max_leaf_tgt = 0;
 };
@@ -268,7 +270,7 @@ cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt,
 // Morton counts): no atomics.
 cudaError_t launch_scatter_ranked(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int K, int L, int Lf,
                                   const int32_t* begin, const int32_t* fine, const int32_t* rank, int32_t* loc,
-                                  int32_t* perm, cudaStream_t s);
+                                  int32_t* perm, cudaStream_t s, int32_t* leaf_of_slot = nullptr);
 // Sums 2x2 blocks of two Morton count arrays; max4[0..3] receive (atomic max) the
 // largest fine source / target count and the largest coarse ones, max4[4..5] (atomic
 // add) the number of non-empty fine and coarse boxes.  max4 must be zeroed first.

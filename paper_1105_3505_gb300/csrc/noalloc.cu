@@ -161,7 +161,8 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
                               ? a(((int64_t)NP << (2 * L)) * 2 * 4 + ((int64_t)NP << (2 * std::max(0, L - 1))) * 2 * 4)
                               : 0;  // TF32 hi/lo copies for the tensor-core M2L
     const int64_t un_tmp = L >= 2 ? a(2 * n_tgt * 8) : 0;  // near and far parts before the final sum
-    const int64_t bytes = a(2 * (n_leaves + 1) * 4) + a(2 * (n_src + n_tgt) * 4) + a(n_src * esz) + split + un_tmp +
+    const int64_t bytes = a(2 * (n_leaves + 1) * 4) + a((2 * (n_src + n_tgt) + n_tgt) * 4) + a(n_src * esz) + split +
+                          un_tmp +
                           2 * a(boxes * NP * esz) + 2 * a(boxes * 8) + 16 /* status word */;
 
     std::memset(info, 0, sizeof(*info));

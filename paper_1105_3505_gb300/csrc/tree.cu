@@ -95,7 +95,7 @@ __global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
 __global__ void scatter_ranked_kernel(const int2* __restrict__ xy, int64_t n, int64_t x0, int64_t y0, int K, int L,
                                       int Lf, const int32_t* __restrict__ begin, const int32_t* __restrict__ fine,
                                       const int32_t* __restrict__ rank, int32_t* __restrict__ loc,
-                                      int32_t* __restrict__ perm) {
+                                      int32_t* __restrict__ perm, int32_t* __restrict__ leaf_of_slot) {
     const int shift = K - L, lside = 1 << shift;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = xy[i];
@@ -109,6 +109,7 @@ __global__ void scatter_ranked_kernel(const int2* __restrict__ xy, int64_t n, in
         }
         loc[slot] = (int)(rx & (lside - 1)) | ((int)(ry & (lside - 1)) << 16);
         perm[slot] = (int32_t)i;
+        if (leaf_of_slot) leaf_of_slot[slot] = (int32_t)morton2((uint32_t)(rx >> shift), (uint32_t)(ry >> shift));
     }
 }
 
@@ -293,9 +294,9 @@ cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt,
 
 cudaError_t launch_scatter_ranked(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int K, int L, int Lf,
                                   const int32_t* begin, const int32_t* fine, const int32_t* rank, int32_t* loc,
-                                  int32_t* perm, cudaStream_t s) {
+                                  int32_t* perm, cudaStream_t s, int32_t* leaf_of_slot) {
     scatter_ranked_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>((const int2*)xy, n, x0, y0, K, L, Lf, begin,
-                                                                     fine, rank, loc, perm);
+                                                                     fine, rank, loc, perm, leaf_of_slot);
     return cudaGetLastError();
 }
 
