@@ -536,7 +536,7 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
             }
         }
         LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
-                                    l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), p->tc_min_level, p->status, s));
+                                    l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), s));
         pt.add_launches(1);
     }
     if (concurrent) {

@@ -1233,19 +1233,13 @@ static cudaError_t launch_m2l_splitk(const DeviceOps& ops, int k, int level, con
     return cudaGetLastError();
 }
 
-// Levels below this use the split-K kernel; larger ones the tensor-core kernel (mixed
-// path, P <= 32) or the tiled SIMT kernel.
+// Levels below this use the split-K kernel, larger ones the tiled SIMT kernel (the
+// tensor-core levels of the mixed path are launched by the caller).
 constexpr int kM2LSplitKMaxLevel = 7;
 
 template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
-                       const T* u_parent, const void* C_parent, T* u_level, void* C_level, int tc_min_level,
-                       int* status, cudaStream_t s) {
-    if constexpr (sizeof(T) == 4) {
-        if (m2l_uses_tc(ops, k, level, tc_min_level, true))
-            return launch_m2l_tc(ops, k, level, (const float*)q_level, Q_level, (const float*)u_parent, C_parent,
-                                 (float*)u_level, C_level, status, s);
-    }
+                       const T* u_parent, const void* C_parent, T* u_level, void* C_level, cudaStream_t s) {
     if (level <= kM2LSplitKMaxLevel) {
         if (ops.NP == 32)
             return launch_m2l_splitk<T, 32>(ops, k, level, q_level, Q_level, u_parent, C_parent, u_level, C_level, s);
@@ -1459,7 +1453,7 @@ cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double
     template cudaError_t launch_m2m<T>(const DeviceOps&, int, int, const T*, const void*, T*, void*,         \
                                        cudaStream_t);                                                         \
     template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const void*, const T*,          \
-                                       const void*, T*, void*, int, int*, cudaStream_t);                      \
+                                       const void*, T*, void*, cudaStream_t);                                \
     template cudaError_t launch_p2p_l2p<T>(const TreeView&, const DeviceOps&, const T*, const T*, const void*, \
                                            const void*, double*, double*, double*, int, cudaStream_t);
 

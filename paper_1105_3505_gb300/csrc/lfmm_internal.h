@@ -329,8 +329,7 @@ inline bool m2l_uses_tc(const DeviceOps& ops, int k, int level, int tc_min_level
 // tensor cores, which report a timed-out wait in *status.
 template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
-                       const T* u_parent, const void* C_parent, T* u_level, void* C_level,
-                       int tc_min_level, int* status, cudaStream_t s);
+                       const T* u_parent, const void* C_parent, T* u_level, void* C_level, cudaStream_t s);
 // Shared-memory form of the tensor-core M2L: the level's expansions and the parent
 // level's incoming expansions pre-split into TF32 hi / lo arrays (launch_split_tf32).
 cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float* qhi, const float* qlo,
@@ -338,9 +337,6 @@ cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float
                              float* u_level, void* C_level, int* status, cudaStream_t s);
 // hi = TF32(x), lo = TF32(x - hi), n floats (a multiple of 4).
 cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s);
-cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level,
-                          const void* Q_level, const float* u_parent, const void* C_parent,
-                          float* u_level, void* C_level, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
                            const T* uhat_leaf, const void* C_leaf, const void* Q_leaf, double* u,

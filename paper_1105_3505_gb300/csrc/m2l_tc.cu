@@ -9,22 +9,27 @@
 // are formed (the lo*lo term is below 2^-22 relative).  The tensor core's fp32
 // accumulation rounds toward zero, and that bias grows linearly with the number of
 // MMAs feeding one accumulator; so every K-step writes fresh TMEM accumulators (hi*hi
-// in one, the small hi*lo + lo*hi terms in another), which the threads read back two
-// steps later and add in registers with round-to-nearest fp32.
+// in one, the small hi*lo + lo*hi terms in another), which the threads read back one
+// step later and add in registers with round-to-nearest fp32.
 //
-//  - A (gathered expansions): each thread owns one box = one TMEM lane; it loads the
-//    source row for the current K-step, splits it and writes hi and lo with
-//    tcgen05.st into A columns of TMEM (the MMA reads A from tensor memory).
+//  - A (gathered expansions): the level's expansions, and the parent level's incoming
+//    expansions, are split once into TF32 hi and lo arrays (split_tf32_kernel).  Each
+//    K-step copies the 128 gathered source rows of hi and of lo with cp.async (16-byte
+//    chunks) straight into the 128-byte-swizzled K-major layout that a shared-memory
+//    matrix descriptor describes, so the tensor core reads A like B and no thread
+//    touches the values between the gather and the MMA.
 //  - B (operators): pre-split, pre-swizzled 4 KB tiles in the device image, fetched
-//    with cp.async.bulk into a 3-deep ring in shared memory one step ahead, completion
+//    with cp.async.bulk into a 3-deep ring in shared memory two steps ahead, completion
 //    tracked by mbarriers.
-//  - every thread arrives on an "A ready" mbarrier after its TMEM stores; one elected
-//    thread waits on it, issues 12 tcgen05.mma (K = 8 each) per K-step and commits
-//    them to a third mbarrier that frees the step's A and D buffers two steps later.
-//  - epilogue: tcgen05.ld of the 128 x 32 fp32 accumulator.
-// Every mbarrier wait is bounded (clock64 budget); on expiry the CTA records
-// LFMM_ETIMEOUT in the plan's status word, stops issuing work, waits (bounded) for
-// what it already issued, frees its TMEM and returns.
+//  - TMEM holds only the two accumulator pairs (128 columns).
+//  - step s: fold in the partials of step s-1 (waiting for its MMAs, which also frees
+//    the A stage they read), start the gather of step s+1 into that stage, wait for the
+//    own copies of step s, make them visible to the tensor core, barrier; one elected
+//    thread issues the 12 MMAs (K = 8 each) of step s and the B copy of step s+2.
+// Every mbarrier wait is bounded (clock64 budget, suspend-time hint); on expiry the CTA
+// records LFMM_ETIMEOUT in the plan's status word, all its threads stop issuing work
+// together (the abort flag is block-uniform), wait (bounded) for what was issued, free
+// the TMEM and return.
 #include "lfmm_internal.h"
 
 namespace lfmm {
@@ -32,9 +37,6 @@ namespace lfmm {
 namespace {
 
 constexpr int kTcThreads = 128;          // 4 warps, one TMEM lane quarter each
-// TMEM columns: D_big[b] [32b, 32b+32), D_small[b] [64+32b, 96+32b),
-// A stage b: hi [128+64b, 160+64b), lo [160+64b, 192+64b)
-constexpr int kTcCols = 256;
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,17 +93,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// 32 consecutive fp32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-        : "memory");
-}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -113,19 +104,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "r"(taddr)
         : "memory");
 }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// D[tmem] (+)= A[tmem] x B[smem descriptor], kind::tf32, cta_group::1
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                            uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 // D[tmem] (+)= A[smem descriptor] x B[smem descriptor], kind::tf32, cta_group::1
 __device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                             uint32_t accumulate) {
@@ -201,283 +181,6 @@ __device__ __forceinline__ DFv dmul(DFv a, DFv b) {
     return qsum(p, e);
 }
 
-__global__ void __launch_bounds__(kTcThreads) m2l_tc_kernel(int level, const float* __restrict__ q,
-                                                            const float* __restrict__ u_par,
-                                                            const float* __restrict__ tiles,
-                                                            const float* __restrict__ mono,
-                                                            const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar,
-                                                            float* __restrict__ out, DFv* __restrict__ Cout,
-                                                            int* __restrict__ status) {
-    constexpr int NP = 32;
-    // dynamic shared memory: B ring [3][hi, lo][32 x 32 swizzled] (1024-byte aligned),
-    // then the gathered fp32 A rows [2][128 x 32] (16-byte chunks XOR-swizzled)
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    float (*sB)[2][1024] = reinterpret_cast<float (*)[2][1024]>(
-        tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u));
-    float (*sA)[kTcThreads * 32] = reinterpret_cast<float (*)[kTcThreads * 32]>(&sB[3][0][0]);
-    __shared__ __align__(8) uint64_t bar_b[3], bar_a[2], bar_mma[2];
-    __shared__ uint32_t s_tmem;
-    __shared__ int s_off[27][3];
-    __shared__ int s_abort;
-    // per K-step and row: source box (Morton index of q_hat at this level, or of u_hat at
-    // the parent level for the L2L step), -1 where the neighbour lies outside
-    __shared__ int s_src[28][kTcThreads];
-
-    const int cls = blockIdx.y;
-    const int px = cls & 1, py = cls >> 1;
-    const int lg = level - 1;
-    const int np_side = 1 << lg;
-    const int64_t n_rows = (int64_t)1 << (2 * lg);
-    const int64_t row = (int64_t)blockIdx.x * kTcThreads + threadIdx.x;
-    const bool valid = row < n_rows;
-    const int side = 1 << level;
-    const bool has_l2l = u_par != nullptr;
-    const int n_steps = 27 + (has_l2l ? 1 : 0);
-    const int warp = threadIdx.x >> 5;
-    const int ri = valid ? (int)(row & (np_side - 1)) : 0;
-    const int rj = valid ? (int)(row >> lg) : 0;
-
-    // the swizzled B tiles need 1024-byte aligned shared memory; refuse to run otherwise
-    if (smem_u32(&sB[0][0][0]) & 1023u) {
-        if (threadIdx.x == 0) atomicExch(status, LFMM_EINTERNAL);
-        return;
-    }
-
-    if (threadIdx.x == 0) {
-        int nn = 0;
-        for (int d = 0; d < 36; ++d) {
-            const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
-            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-            s_off[nn][0] = dx;
-            s_off[nn][1] = dy;
-            s_off[nn][2] = offset_index_tc(dx, dy);
-            ++nn;
-        }
-        for (int i = 0; i < 3; ++i) mbar_init(&bar_b[i], 1);
-        mbar_init(&bar_a[0], kTcThreads);
-        mbar_init(&bar_a[1], kTcThreads);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
-        fence_barrier_init();
-        s_abort = 0;
-    }
-    if (warp == 0) {
-        tmem_alloc(&s_tmem, kTcCols);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // this thread's row: its 27 interaction-list sources and its parent, once per tile
-    for (int st = 0; st < 27; ++st) {
-        int si = -1;
-        if (valid) {
-            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
-            if (sx >= 0 && sx < side && sy >= 0 && sy < side) si = (int)morton2(sx, sy);
-        }
-        s_src[st][threadIdx.x] = si;
-    }
-    s_src[27][threadIdx.x] = (valid && has_l2l) ? (int)morton2(ri, rj) : -1;
-    __syncthreads();
-    const uint32_t tmem = s_tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-
-    // coalesced gather of the step's 128 source rows into sA[b]: thread t copies 16-byte
-    // chunk (t % 8) of rows t/8 + 16 j; chunk c of row r lands at chunk c ^ (r % 8)
-    auto gather = [&](int step, int b) {
-        const int ch = threadIdx.x & 7;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = (threadIdx.x >> 3) + 16 * j;
-            const int si = s_src[step][r];
-            const float* srow = si < 0 ? nullptr : (step < 27 ? q : u_par) + (size_t)si * NP;
-            const uint32_t dst = smem_u32(&sA[b][r * 32 + ((ch ^ (r & 7)) << 2)]);
-            const void* src = srow ? (const void*)(srow + 4 * ch) : (const void*)q;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-                         "r"(srow ? 16 : 0)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-
-    constexpr uint32_t kIdesc = idesc_tf32(128, NP);
-    bool ok = true;
-    int issued_steps = 0, b_issued = 0;
-    float acc[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    // add the K-step partials held in TMEM buffer b to the register accumulator
-    auto flush = [&](int b) {
-        uint32_t big[32], small[32];
-        tmem_ld32(tmem + lane_base + 32 * b, big);
-        tmem_ld32(tmem + lane_base + 64 + 32 * b, small);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
-    };
-    auto b_src = [&](int step) -> const float* {
-        return step < 27 ? tiles + (size_t)s_off[step][2] * 2048 : tiles + (size_t)(kNumOffsets + cls) * 2048;
-    };
-    volatile int* vabort = &s_abort;
-    if (threadIdx.x == 0) {  // B tiles of step 0
-        mbar_arrive_expect_tx(&bar_b[0], 8192);
-        bulk_g2s(&sB[0][0][0], b_src(0), 8192, &bar_b[0]);
-        b_issued = 1;
-    }
-    gather(0, 0);
-    for (int step = 0; step < n_steps; ++step) {
-        const int buf = step & 1;
-        // this step's rows have landed (own copies), and every thread is done with the
-        // buffer the next gather overwrites (it held step - 1)
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncthreads();
-        if (step + 1 < n_steps) gather(step + 1, buf ^ 1);
-        float4 cur[8];
-        {
-            const float* myrow = &sA[buf][threadIdx.x * 32];
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-                cur[c] = *reinterpret_cast<const float4*>(myrow + ((c ^ (threadIdx.x & 7)) << 2));
-        }
-        if (step >= 2) {
-            // A stage and D buffer of step - 2 become free; fold its partials in.  Every
-            // exit from this loop is warp-uniform (vote), so warp-collective TMEM loads
-            // never run with part of a warp missing.
-            bool w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[buf], ((step - 2) >> 1) & 1);
-            w_ok = __all_sync(0xffffffffu, w_ok);
-            if (!w_ok) {
-                atomicExch(&s_abort, 1);
-                break;
-            }
-            tc_fence_after();
-            flush(buf);
-        } else if (__any_sync(0xffffffffu, *vabort != 0)) {
-            break;
-        }
-        // this thread's A row -> TMEM lane (hi, lo)
-        uint32_t hv[32], lv[32];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float xs[4] = {cur[c].x, cur[c].y, cur[c].z, cur[c].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint32_t h = tf32_rna_bits(xs[e]);
-                hv[4 * c + e] = h;
-                lv[4 * c + e] = tf32_rna_bits(xs[e] - __uint_as_float(h));
-            }
-        }
-        const uint32_t a_hi = tmem + 128 + 64 * buf, a_lo = a_hi + 32;
-        tmem_st32(tmem + lane_base + 128 + 64 * buf, hv);
-        tmem_st32(tmem + lane_base + 160 + 64 * buf, lv);
-        tmem_wait_st();
-        tc_fence_before();
-        mbar_arrive(&bar_a[buf]);
-        if (threadIdx.x == 0) {
-            const int slot = step % 3;
-            const bool good = *vabort == 0 && mbar_wait_bounded(&bar_a[buf], (step >> 1) & 1) &&
-                              mbar_wait_bounded(&bar_b[slot], (step / 3) & 1);
-            if (!good) atomicExch(&s_abort, 1);  // no MMAs for this step; all warps stop next step
-        }
-        if (threadIdx.x == 0 && *vabort == 0) {
-            const int slot = step % 3;
-            tc_fence_after();
-            const uint32_t b_hi = smem_u32(&sB[slot][0][0]), b_lo = smem_u32(&sB[slot][1][0]);
-            const uint32_t d_big = tmem + 32 * buf, d_small = tmem + 64 + 32 * buf;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t dh = smem_desc_sw128(b_hi + 32 * kk), dl = smem_desc_sw128(b_lo + 32 * kk);
-                mma_tf32_ts(d_big, a_hi + 8 * kk, dh, kIdesc, kk > 0 ? 1u : 0u);
-                mma_tf32_ts(d_small, a_hi + 8 * kk, dl, kIdesc, kk > 0 ? 1u : 0u);
-                mma_tf32_ts(d_small, a_lo + 8 * kk, dh, kIdesc, 1u);
-            }
-            mma_commit(&bar_mma[buf]);
-            // B tiles of the next step into the slot step - 2 used (its MMAs are done)
-            if (step + 1 < n_steps) {
-                const int ns = (step + 1) % 3;
-                mbar_arrive_expect_tx(&bar_b[ns], 8192);
-                bulk_g2s(&sB[ns][0][0], b_src(step + 1), 8192, &bar_b[ns]);
-                b_issued = step + 2;
-            }
-        }
-        issued_steps = step + 1;
-    }
-
-    // scalar channel (compensated), one box per thread, while the last MMAs run
-    if (valid) {
-        DFv sacc = has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
-        // nine loads in flight at a time
-        for (int c0 = 0; c0 < 27; c0 += 9) {
-            DFv qv[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int si = s_src[c0 + k][threadIdx.x];
-                qv[k] = si >= 0 ? Qin[si] : DFv{0.f, 0.f};
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int o = s_off[c0 + k][2];
-                sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
-            }
-        }
-        Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
-    }
-
-    // the last two steps' partials (bounded, warp-uniform waits); after an abort, wait
-    // (bounded) for work already issued before the CTA exits
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    ok = s_abort == 0;
-    if (ok) {
-        for (int st = max(0, n_steps - 2); st < n_steps; ++st) {
-            bool w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
-            w_ok = __all_sync(0xffffffffu, w_ok);
-            if (!w_ok) {
-                atomicExch(&s_abort, 1);
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            flush(st & 1);
-        }
-    }
-    __syncthreads();
-    if (s_abort) ok = false;
-    if (!ok) {
-        for (int st = max(0, issued_steps - 2); st < issued_steps; ++st)
-            mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
-        if (threadIdx.x == 0 && b_issued > 0)
-            mbar_wait_bounded(&bar_b[(b_issued - 1) % 3], ((b_issued - 1) / 3) & 1);
-    }
-    if (ok) {
-        if (valid) {
-            float4* dst = reinterpret_cast<float4*>(out + (size_t)morton2(2 * ri + px, 2 * rj + py) * NP);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-        }
-    } else if (threadIdx.x == 0) {
-        atomicExch(status, LFMM_ETIMEOUT);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kTcCols);
-    }
-}
-
-
-// ---------------------------------------------------------------------------------
-// Second form: both operands from shared memory.  The expansions of the level (and the
-// parent level's incoming expansions) are split once into TF32 hi and lo arrays by
-// split_tf32_kernel; each K-step copies the 128 gathered source rows of hi and of lo
-// (cp.async, 16-byte chunks) straight into the 128-byte-swizzled K-major layout that a
-// shared-memory matrix descriptor describes, so the tensor core reads A like B and no
-// thread touches the values between the gather and the MMA.  TMEM holds only the two
-// accumulator pairs (128 columns).
-//   step s: fold in the partials of step s-1 (waiting for its MMAs, which also frees the
-//   A stage it read), start the gather of step s+1 into that stage, wait for the own
-//   copies of step s, make them visible to the tensor core, barrier; one thread issues
-//   the 12 MMAs of step s and the B copy of step s+2.
 constexpr int kTc2Cols = 128;  // D_big[b]: [32b, 32b+32), D_small[b]: [64+32b, 96+32b)
 
 __global__ void __launch_bounds__(kTcThreads) m2l_tc_ss_kernel(int level, const float* __restrict__ qhi,
@@ -741,22 +444,6 @@ __global__ void split_tf32_kernel(const float4* __restrict__ x, float4* __restri
 }
 
 }  // namespace
-
-cudaError_t launch_m2l_tc(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
-                          const float* u_parent, const void* C_parent, float* u_level, void* C_level, int* status,
-                          cudaStream_t s) {
-    constexpr size_t smem = 1024 + sizeof(float) * (3 * 2 * 1024 + 2 * kTcThreads * 32);
-    {
-        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tc_kernel, smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int64_t rows = (int64_t)1 << (2 * (level - 1));
-    dim3 grid((unsigned)((rows + kTcThreads - 1) / kTcThreads), 4);
-    m2l_tc_kernel<<<grid, kTcThreads, smem, s>>>(level, q_level, u_parent, (const float*)ops.tc[k],
-                                              (const float*)ops.mono[k], (const DFv*)Q_level,
-                                              (const DFv*)C_parent, u_level, (DFv*)C_level, status);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s) {
     const int64_t n4 = n / 4;
