@@ -375,6 +375,50 @@ def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
             "step": "lfmm_forest_create + lfmm_eval", "generation_s": t_gen}
 
 
+def eval_leg(lfmm, steps: int = 20, warmup: int = 3):
+    """Evaluation alone (plan built once, outside the timed region), eager launches vs
+    the plan's recorded CUDA graph (LFMM_FLAG_GRAPH), on uniform_1m (mixed, p = 8) and
+    uniform_4k (binary64, p = 16); L2 flushed before every timed evaluation."""
+    import torch
+    from paper_1105_3505_gb300 import workloads
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, prob, prec, p in (("uniform_1m_mixed_p8", workloads.uniform_1m(), lfmm.LFMM_MIXED, 8),
+                                ("uniform_4k_fp64_p16", workloads.uniform_4k(), lfmm.LFMM_FP64, 16)):
+        s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (prob.src, prob.tgt, prob.f))
+        u_d = torch.empty(prob.tgt.shape[0], dtype=torch.float64, device=dev)
+        pts = prob.src.shape[0] + prob.tgt.shape[0]
+        row = {}
+        ref = None
+        for mode in ("eager", "graph"):
+            o = lfmm.make_opts(prec, p, 64, 32, 64, graph=(mode == "graph"))
+            h = lfmm.lfmm_plan_create(s_d, prob.src.shape[0], t_d, prob.tgt.shape[0], o, stream)
+            for _ in range(warmup):
+                lfmm.lfmm_eval(h, f_d, u_d, stream)
+            torch.cuda.synchronize()
+            evs = []
+            for k in range(steps):
+                flush.fill_(k & 0xFF)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lfmm.lfmm_eval(h, f_d, u_d, stream)
+                b.record(stream)
+                evs.append((a, b))
+            torch.cuda.synchronize()
+            lfmm.lfmm_plan_destroy(h)
+            ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+            u = u_d.cpu().numpy()
+            if ref is None:
+                ref = u
+            row[mode] = {"ms": ms, "Mpoints_per_s": pts / (ms * 1e-3) / 1e6}
+        # two plans of the same points may order a leaf's points differently
+        row["max_rel_diff"] = float(np.abs(ref - u).max() / np.abs(ref).max())
+        res[name] = row
+    return res
+
+
 # ---------------------------------------------------------------- replicas
 def replica_throughput(ms_local, points_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` independent replicas: every rank solved
@@ -514,8 +558,8 @@ def main():
         flops = m2l_flops(info, P, tc_levels) // max(1, len(tc_levels))
         achieved = flops / t_launch / 1e12
         peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
-        roof = {"kernel": "m2l_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l_tc_kernel"),
+        roof = {"kernel": "m2l_tc_ss_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l_tc_ss_kernel"),
                 "peak_basis": f"tf32 dense = measured bf16 burst {peaks['bf16_tflops']} x {TF32_PER_BF16:.3f} "
                               f"(nominal 1.1 / 2.25 PFLOP/s) ({peak_src}); useful flops only, the 3xTF32 split "
                               f"issues 3 MMAs per useful product",
@@ -565,6 +609,7 @@ def main():
                         "rel_err": float(np.abs(u2[idx] - ref).max() / scale), "leaf_size": leaf}
         out["cpu_baseline"] = cpu_baseline(prob)
         out["forest"] = forest_leg(lfmm)
+        out["eval_only"] = eval_leg(lfmm)
         if args.serve_requests > 0:
             out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots)
     print(json.dumps(out), flush=True)

@@ -73,8 +73,18 @@ typedef struct lfmm_opts {
     int32_t tc_min_level;     /* mixed path, P <= 32: tree levels >= this run M2L on the      */
                               /* tensor cores (0 = default 8; a value > 30 disables them)     */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
-    int32_t reserved;         /* must be zero                                                 */
+    int32_t flags;            /* bitwise OR of LFMM_FLAG_* (0: none)                           */
 } lfmm_opts;
+
+/* Evaluate through a CUDA graph: the first lfmm_eval / lfmm_eval_parts of a plan records
+ * its kernel launches (stream capture on a plan-owned stream, nothing runs) into a graph,
+ * which that call and every later one with the same device argument pointers launch on
+ * the caller's stream in one call; new pointers re-record it (the executable graph is
+ * updated in place when possible).  Host f / u are staged through plan-owned device
+ * buffers, so they reuse the graph too.  Results are bit-identical to the eager
+ * launches.  While phase profiling is on (lfmm_profile_enable) evaluation is eager, so
+ * that each phase can be timed. */
+#define LFMM_FLAG_GRAPH 1
 
 /* Tree storage.  UNIFORM: every box of every level is stored (Sec. 6), the layout for
  * points that fill their root box.  PRUNED: the same levels and boxes, but only boxes
@@ -86,7 +96,7 @@ typedef struct lfmm_opts {
 #define LFMM_TREE_PRUNED 2
 
 /* Fill opts with the defaults: LFMM_MIXED, p = 8, leaf_size = 64, max_leaf_side = 32,
- * proxies_per_edge = 64, tc_min_level = 0, tree = LFMM_TREE_AUTO. */
+ * proxies_per_edge = 64, tc_min_level = 0, tree = LFMM_TREE_AUTO, flags = 0. */
 void lfmm_opts_default(lfmm_opts* opts);
 
 /* Build a plan for fixed source and target locations (Sec. 8.1 precomputation):
@@ -207,6 +217,50 @@ int lfmm_server_submit(lfmm_server* server, const lfmm_request* req, int64_t* ti
 int lfmm_server_wait(lfmm_server* server, int64_t ticket, lfmm_request_stats* stats);
 /* Finish the queued requests, stop the workers and free the server (NULL: no-op). */
 int lfmm_server_destroy(lfmm_server* server);
+
+/* ---- autotuner ---------------------------------------------------------------------- */
+/* Picks the expansion order p, the leaf size N_leaf and the tensor-core levels for a
+ * point set (or a forest of point sets) and a required accuracy, by measurement on the
+ * device.  The paper fixes none of these (it reports the error for chosen P, Table 4.1,
+ * and times one leaf size, Sec. 9); the choice is the fastest configuration whose error
+ * meets the request:
+ *   1. precision: LFMM_MIXED when tol >= 1e-6, else LFMM_DF;
+ *   2. reference: the same points evaluated by LFMM_DF at p = 16 (rel. error ~1e-13)
+ *      for a fixed pseudo-random zero-sum charge vector;
+ *   3. p: the smallest candidate (MIXED: 4..9, DF: 10, 12, 14, 16, 17) whose max-norm
+ *      relative error against the reference is <= tol / 2 at leaf size 64;
+ *   4. N_leaf (MIXED: 32, 64, 128; DF: 64, 128, 192) and then, for MIXED, the first
+ *      tensor-core level (the leaf level, the one above it, or none): the smallest
+ *      median time of plan creation + evaluation over three timed steps; a candidate
+ *      whose error exceeds tol / 2 is skipped;
+ * Results are cached process-wide by (precision, decade of tol, ceil(log2) of the
+ * source and target counts, ceil(log2) of the problem count, tree storage); a cached
+ * entry is returned without measuring (result->from_cache = 1).
+ *   src_offsets, tgt_offsets  NULL with n_problems = 1 for one problem, else as for
+ *                             lfmm_forest_create (host memory)
+ *   tol                       required max-norm relative error, in [1e-13, 1e-2]
+ *   base                      NULL for the defaults; its max_leaf_side, proxies_per_edge
+ *                             and tree are kept, its flags copied to the result
+ *   result                    out: the chosen options and their measurements
+ * Runs on `stream` and synchronises it; the plans it builds are destroyed before it
+ * returns. */
+typedef struct lfmm_tune_result {
+    lfmm_opts opts;           /* the chosen options                                        */
+    double rel_err;           /* their error against the reference evaluation             */
+    double ms;                /* their median plan create + eval time (ms)                 */
+    int32_t candidates;       /* configurations measured (0 when from the cache)           */
+    int32_t from_cache;
+} lfmm_tune_result;
+
+int lfmm_autotune(const int32_t* src_xy, int64_t n_src, const int64_t* src_offsets,
+                  const int32_t* tgt_xy, int64_t n_tgt, const int64_t* tgt_offsets, int64_t n_problems,
+                  double tol, const lfmm_opts* base, lfmm_tune_result* result, void* stream);
+/* Forget every cached tuning result. */
+int lfmm_tune_cache_clear(void);
+/* Write the cache to `path` (one text line per entry) / merge entries from such a file
+ * (LFMM_EINVAL on a malformed line; entries before it are kept). */
+int lfmm_tune_cache_save(const char* path);
+int lfmm_tune_cache_load(const char* path);
 
 /* ---- plan shape without allocation -------------------------------------------------- */
 /* The paper has no counterpart: this is a service entry point for callers that cannot

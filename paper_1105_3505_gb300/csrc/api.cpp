@@ -59,6 +59,11 @@ struct lfmm_plan {
     double* uf_tmp = nullptr;        // far field per target (caller order), before the final sum
     struct AuxStream* aux = nullptr;  // near-field pass runs here, beside the far-field sweeps
     int64_t n_boxes = 0;
+    // LFMM_FLAG_GRAPH: the recorded evaluation and the device pointers it was recorded for
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    const double* graph_f = nullptr;
+    double* graph_out[3] = {nullptr, nullptr, nullptr};
 };
 
 // A second stream with its fork / join events, pooled process-wide (plans are often
@@ -187,7 +192,7 @@ int validate_opts(const lfmm_opts& o) {
     if (o.tc_min_level < 0) return fail(LFMM_EINVAL, "opts.tc_min_level must be >= 0");
     if (o.tree != LFMM_TREE_AUTO && o.tree != LFMM_TREE_UNIFORM && o.tree != LFMM_TREE_PRUNED)
         return fail(LFMM_EINVAL, "opts.tree must be LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED");
-    if (o.reserved != 0) return fail(LFMM_EINVAL, "opts.reserved must be zero");
+    if (o.flags & ~LFMM_FLAG_GRAPH) return fail(LFMM_EINVAL, "opts.flags has unknown bits");
     return LFMM_OK;
 }
 
@@ -521,16 +526,9 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         PhaseTimer pt(tc ? LFMM_PHASE_M2L_TC : LFMM_PHASE_M2L, s);
         if constexpr (sizeof(T) == 4) {
             if (tc) {
-                float* qhi = (float*)p->tc_split;
-                float* qlo = qhi + ((size_t)NP << (2 * l));
-                float* uhi = qlo + ((size_t)NP << (2 * l));
-                float* ulo = uhi + ((size_t)NP << (2 * (l - 1)));
-                LFMM_CUDA_TRY(launch_split_tf32((const float*)Qx(l), qhi, qlo, (int64_t)NP << (2 * l), s));
-                if (l >= 3)
-                    LFMM_CUDA_TRY(launch_split_tf32((const float*)Ux(l - 1), uhi, ulo, (int64_t)NP << (2 * (l - 1)), s));
-                LFMM_CUDA_TRY(launch_m2l_tc_ss(ops, L - l, l, qhi, qlo, Qm(l), l >= 3 ? uhi : nullptr,
-                                               l >= 3 ? ulo : nullptr, l >= 3 ? Cm(l - 1) : nullptr, (float*)Ux(l),
-                                               Cm(l), p->status, s));
+                LFMM_CUDA_TRY(launch_m2l_tma(ops, L - l, l, (const float*)Qx(l), Qm(l),
+                                             l >= 3 ? (const float*)Ux(l - 1) : nullptr, l >= 3 ? Cm(l - 1) : nullptr,
+                                             (float*)Ux(l), Cm(l), (float*)p->tc_split, p->status, p->num_sms, s));
                 pt.add_launches(l >= 3 ? 3 : 2);
                 continue;
             }
@@ -556,6 +554,56 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
                                         L >= 2 ? Cm(L) : nullptr, Qm(L), u, un, uf, p->num_sms, s));
         pt.add_launches(1);
     }
+    return LFMM_OK;
+}
+
+int eval_dispatch(lfmm_plan* p, const double* f, double* const out[3], cudaStream_t s) {
+    return p->opts.precision == LFMM_MIXED ? eval_impl<float>(p, f, out[0], out[1], out[2], s)
+           : p->opts.precision == LFMM_DF  ? eval_impl<DF>(p, f, out[0], out[1], out[2], s)
+                                           : eval_impl<double>(p, f, out[0], out[1], out[2], s);
+}
+
+// Graph form of one evaluation.  The launch sequence depends only on the plan and the
+// argument pointers, so a graph recorded once replays it exactly.  Recording happens on
+// a plan-owned stream (the caller's may be the legacy default stream, which cannot be
+// captured); the executable graph is launched on the caller's stream, after whatever
+// the caller queued there.
+int eval_graph(lfmm_plan* p, const double* f, double* const out[3], cudaStream_t s) {
+    const bool same = p->graph && p->graph_f == f && p->graph_out[0] == out[0] && p->graph_out[1] == out[1] &&
+                      p->graph_out[2] == out[2];
+    if (!same) {
+        if (!p->cap_stream) LFMM_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        LFMM_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int st = eval_dispatch(p, f, out, p->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (st || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st ? st : fail(LFMM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        if (p->graph) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(p->graph, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(p->graph);
+                p->graph = nullptr;
+            }
+        }
+        if (!p->graph) {
+            const cudaError_t ei = cudaGraphInstantiate(&p->graph, g, 0);
+            if (ei != cudaSuccess) {
+                cudaGraphDestroy(g);
+                p->graph = nullptr;
+                cudaGetLastError();
+                return fail(LFMM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+            }
+        }
+        cudaGraphDestroy(g);
+        p->graph_f = f;
+        for (int i = 0; i < 3; ++i) p->graph_out[i] = out[i];
+    }
+    LFMM_CUDA_TRY(cudaGraphLaunch(p->graph, s));
     return LFMM_OK;
 }
 
@@ -590,9 +638,8 @@ int eval_common(lfmm_plan* p, const double* f, double* u, double* un, double* uf
         douts[i] = p->u_stage + (size_t)i * p->nt;
         host_out[i] = true;
     }
-    int st = p->opts.precision == LFMM_MIXED ? eval_impl<float>(p, fd, douts[0], douts[1], douts[2], s)
-             : p->opts.precision == LFMM_DF  ? eval_impl<DF>(p, fd, douts[0], douts[1], douts[2], s)
-                                             : eval_impl<double>(p, fd, douts[0], douts[1], douts[2], s);
+    const int st = (p->opts.flags & LFMM_FLAG_GRAPH) && !profiling_enabled() ? eval_graph(p, fd, douts, s)
+                                                                               : eval_dispatch(p, fd, douts, s);
     if (st) return st;
     bool any_host = false;
     {
@@ -668,6 +715,8 @@ int lfmm_plan_destroy(lfmm_plan* plan) {
     if (!plan) return LFMM_OK;
     free_plan_buffers(plan);
     cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    if (plan->graph) cudaGraphExecDestroy(plan->graph);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     release_aux(plan->aux);
     delete plan;
     if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("plan destroy: ") + cudaGetErrorString(e));

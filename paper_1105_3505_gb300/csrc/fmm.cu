@@ -1340,6 +1340,24 @@ static void fill_levels(LevelPtrs<T>& P, const DeviceOps& ops, int L, const Leve
     }
 }
 
+// Cooperative launch (all blocks co-resident, as the grid barrier needs) through the
+// extensible launch API, whose cooperative attribute is also valid for kernels captured
+// into a CUDA graph.
+static cudaError_t launch_cooperative(const void* fn, int grid, int threads, size_t smem, void** args,
+                                      cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 template <typename T>
 cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, unsigned* sync, int* status,
                              int num_sms, cudaStream_t s) {
@@ -1354,7 +1372,7 @@ cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, un
         // and pass), and every extra block costs each grid barrier an arrival
         const int grid = num_sms;
         void* args[] = {&P, &l_top, &l_bot, &sync, &status};
-        e = cudaLaunchCooperativeKernel(fn, grid, 256, args, smem, s);
+        e = launch_cooperative(fn, grid, 256, smem, args, s);
         return e == cudaSuccess ? cudaSuccess : clear_and_return(e);
     };
     if (ops.NP == 32) {
@@ -1393,7 +1411,7 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
         if (e != cudaSuccess) return e;
         const int grid = num_sms * blocks_per_sm(fn, threads, smem);
         void* args[] = {&P, &l0, &l1, &sync, &status};
-        e = cudaLaunchCooperativeKernel(fn, grid, threads, args, smem, s);
+        e = launch_cooperative(fn, grid, threads, smem, args, s);
         return e == cudaSuccess ? cudaSuccess : clear_and_return(e);
     };
     cudaError_t e = ops.NP == 32 ? go(std::integral_constant<int, 32>()) : go(std::integral_constant<int, 64>());

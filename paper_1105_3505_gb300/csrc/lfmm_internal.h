@@ -335,6 +335,13 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
 cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float* qhi, const float* qlo,
                              const void* Q_level, const float* uhi, const float* ulo, const void* C_parent,
                              float* u_level, void* C_level, int* status, cudaStream_t s);
+// TMA form of the tensor-core M2L + L2L of one level (Morton-ordered q_hat / u_hat in
+// and out): splits the level's expansions and the parent's into TF32 hi / lo layouts in
+// `split` (8 np^2 + 2 np^2 rows of 32 floats, np = 2^(level-1)), then one persistent
+// launch; a timed-out wait is reported in *status.
+cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
+                           const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
+                           int* status, int num_sms, cudaStream_t s);
 // hi = TF32(x), lo = TF32(x - hi), n floats (a multiple of 4).
 cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s);
 template <typename T>

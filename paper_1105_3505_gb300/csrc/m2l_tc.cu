@@ -30,6 +30,9 @@
 // records LFMM_ETIMEOUT in the plan's status word, all its threads stop issuing work
 // together (the abort flag is block-uniform), wait (bounded) for what was issued, free
 // the TMEM and return.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lfmm_internal.h"
 
 namespace lfmm {
@@ -73,6 +76,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_u32(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
@@ -443,6 +451,342 @@ __global__ void split_tf32_kernel(const float4* __restrict__ x, float4* __restri
     }
 }
 
+// ---------------------------------------------------------------------------------
+// TMA form.  The level's expansions are split into TF32 hi / lo once and stored by
+// parity plane, Q5[hl][py'][px'][y'][x'][32] with box (x, y) = (2x' + px', 2y' + py'):
+// for a target tile of one parity class, the sources at one interaction offset are then
+// a rectangle of one plane, so a single tiled TMA load (5-D tensor map, 128-byte
+// swizzle, zero fill outside the level) writes the A operand of a K-step directly in
+// the layout the tensor core reads.  The parent level's incoming expansions are stored
+// row-major (4-D map) and their window is the tile itself.
+//
+// Persistent CTAs (one per SM) walk the tiles with a continuous pipeline:
+//   warp 4 (one thread): producer - for every K-step of every tile, wait until the
+//     stage is free, then two TMA loads (A hi, A lo) and one bulk copy (B hi + lo)
+//     completing on the stage's "full" mbarrier;
+//   warp 5 (one thread): MMA issuer - wait "full", wait until the accumulator buffer
+//     is folded, issue the 12 MMAs of the step, commit to the stage's "empty" barrier
+//     (frees the shared memory) and to the buffer's "acc_full" barrier;
+//   warps 0-3: one target box per thread (TMEM lane) - fold every step's fresh
+//     accumulators into round-to-nearest fp32 registers, arrive on "acc_empty"; at a
+//     tile's last step write the row of u_hat; at its first, the compensated constant.
+// Every wait is bounded; on expiry the CTA records LFMM_ETIMEOUT, every role stops at
+// its next iteration, and the teardown waits (bounded) for the copies and MMAs issued.
+constexpr int kTmaStages = 4;
+constexpr int kTmaAcc = 4;
+constexpr int kTmaThreads = 192;
+constexpr int kTmaCols = 256;  // D_big[b]: [32b, 32b+32), D_small[b]: [128+32b, 160+32b)
+constexpr uint32_t kTmaABytes = 128 * 32 * 4;
+constexpr uint32_t kTmaStageBytes = 2 * kTmaABytes + 8192;
+
+struct TmaGeo {
+    int level;            // tree level of the targets
+    int lg;               // log2 of np, the side of a parity class (2^(level-1))
+    int TX, TY;           // target tile: TX x TY boxes of one class, TX * TY <= 128
+    int tiles_x;          // tiles per class row
+    int tiles_per_class;
+    int n_tiles;          // 4 classes x tiles_per_class
+    int has_l2l;
+};
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
+    const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_u, const TmaGeo g,
+    const float* __restrict__ tiles, const float* __restrict__ mono, const DFv* __restrict__ Qin,
+    const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout, int* __restrict__ status) {
+    constexpr int NP = 32;
+    extern __shared__ __align__(1024) unsigned char tma_smem[];
+    // stage i: A hi, A lo (128 rows x 128 B each, 128-byte swizzled), B hi + lo (8 KB)
+    const uint32_t base = smem_u32(tma_smem) + ((1024u - (smem_u32(tma_smem) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages], acc_full[kTmaAcc], acc_empty[kTmaAcc];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_off[4][27][3];
+    __shared__ int s_abort;
+    __shared__ long long s_issued[2];  // K-steps issued by the producer and by the MMA thread
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_steps = 27 + g.has_l2l;
+    const int np = 1 << g.lg, side = 2 << g.lg;
+    const int rows = g.TX * g.TY;
+    const uint32_t tx_bytes = 2u * (uint32_t)rows * 128u + 8192u;
+    const int my_tiles = blockIdx.x < (unsigned)g.n_tiles ? (g.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const long long total = (long long)my_tiles * n_steps;
+    volatile int* vabort = &s_abort;
+
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 4; ++c) {
+            const int px = c & 1, py = c >> 1;
+            int nn = 0;
+            for (int d = 0; d < 36; ++d) {
+                const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+                s_off[c][nn][0] = dx;
+                s_off[c][nn][1] = dy;
+                s_off[c][nn][2] = offset_index_tc(dx, dy);
+                ++nn;
+            }
+        }
+        for (int i = 0; i < kTmaStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < kTmaAcc; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        fence_barrier_init();
+        s_abort = 0;
+        s_issued[0] = s_issued[1] = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, kTmaCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    auto abort_now = [&]() {
+        atomicExch(&s_abort, 1);
+        atomicExch(status, LFMM_ETIMEOUT);
+    };
+    // tile t: class t & 3 (classes interleave for balance), then row-major tiles
+    auto tile_of = [&](long long gs, int& cls, int& ri0, int& rj0) {
+        const int t = (int)blockIdx.x + (int)(gs / n_steps) * (int)gridDim.x;
+        cls = t & 3;
+        const int k = t >> 2;
+        ri0 = (k % g.tiles_x) * g.TX;
+        rj0 = (k / g.tiles_x) * g.TY;
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {
+            for (long long gs = 0; gs < total; ++gs) {
+                if (*vabort) break;
+                const int slot = (int)(gs % kTmaStages);
+                const long long use = gs / kTmaStages;
+                if (use > 0 && !mbar_wait_bounded(&empty[slot], (uint32_t)((use - 1) & 1))) {
+                    abort_now();
+                    break;
+                }
+                int cls, ri0, rj0;
+                tile_of(gs, cls, ri0, rj0);
+                const int st = (int)(gs % n_steps);
+                const uint32_t sa = base + (uint32_t)slot * kTmaStageBytes;
+                mbar_arrive_expect_tx(&full[slot], tx_bytes);
+                if (st < 27) {
+                    const int sx = (cls & 1) + s_off[cls][st][0], sy = (cls >> 1) + s_off[cls][st][1];
+                    const int plane = (sx & 1) + 2 * (sy & 1);
+                    tma_load_5d(sa, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 0, &full[slot]);
+                    tma_load_5d(sa + kTmaABytes, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 1, &full[slot]);
+                    bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)s_off[cls][st][2] * 2048, 8192, &full[slot]);
+                } else {
+                    tma_load_4d(sa, &tm_u, ri0, rj0, 0, &full[slot]);
+                    tma_load_4d(sa + kTmaABytes, &tm_u, ri0, rj0, 1, &full[slot]);
+                    bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)(kNumOffsets + cls) * 2048, 8192, &full[slot]);
+                }
+                s_issued[0] = gs + 1;
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t kIdesc = idesc_tf32(128, NP);
+            for (long long gs = 0; gs < total; ++gs) {
+                if (*vabort) break;
+                const int slot = (int)(gs % kTmaStages);
+                const int d = (int)(gs % kTmaAcc);
+                const long long du = gs / kTmaAcc;
+                if (!mbar_wait_bounded(&full[slot], (uint32_t)((gs / kTmaStages) & 1)) ||
+                    (du > 0 && !mbar_wait_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1)))) {
+                    abort_now();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_hi = base + (uint32_t)slot * kTmaStageBytes, a_lo = a_hi + kTmaABytes;
+                const uint32_t b_hi = a_hi + 2 * kTmaABytes, b_lo = b_hi + 4096;
+                const uint32_t d_big = tmem + 32 * d, d_small = tmem + 128 + 32 * d;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t ah = smem_desc_sw128(a_hi + 32 * kk), al = smem_desc_sw128(a_lo + 32 * kk);
+                    const uint64_t bh = smem_desc_sw128(b_hi + 32 * kk), bl = smem_desc_sw128(b_lo + 32 * kk);
+                    mma_tf32_ss(d_big, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, ah, bl, kIdesc, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, al, bh, kIdesc, 1u);
+                }
+                mma_commit(&empty[slot]);
+                mma_commit(&acc_full[d]);
+                s_issued[1] = gs + 1;
+            }
+        }
+    } else {
+        const int r = threadIdx.x;  // TMEM lane = tile row
+        const bool valid = r < rows;
+        const int xl = r % g.TX, yl = r / g.TX;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        int cls = 0, ri = 0, rj = 0;
+        for (long long gs = 0; gs < total; ++gs) {
+            const int st = (int)(gs % n_steps);
+            if (st == 0) {
+                int ri0, rj0;
+                tile_of(gs, cls, ri0, rj0);
+                ri = ri0 + xl;
+                rj = rj0 + yl;
+                // incoming constant (compensated) of this box, while the tile's MMAs run
+                if (valid) {
+                    const int px = cls & 1, py = cls >> 1;
+                    DFv sacc = g.has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
+                    for (int c0 = 0; c0 < 27; c0 += 9) {
+                        DFv qv[9];
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) {
+                            const int sx = 2 * ri + px + s_off[cls][c0 + k][0], sy = 2 * rj + py + s_off[cls][c0 + k][1];
+                            qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qin[morton2(sx, sy)]
+                                                                                     : DFv{0.f, 0.f};
+                        }
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) {
+                            const int o = s_off[cls][c0 + k][2];
+                            sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+                        }
+                    }
+                    Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
+                }
+            }
+            const int d = (int)(gs % kTmaAcc);
+            bool ok = *vabort == 0 && mbar_wait_bounded(&acc_full[d], (uint32_t)((gs / kTmaAcc) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) abort_now();
+                break;
+            }
+            tc_fence_after();
+            uint32_t big[32], small[32];
+            tmem_ld32(tmem + lane_base + 32 * d, big);
+            tmem_ld32(tmem + lane_base + 128 + 32 * d, small);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[d]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+            if (st == n_steps - 1) {
+                if (valid) {
+                    float4* dst = reinterpret_cast<float4*>(
+                        out + (size_t)morton2(2 * ri + (cls & 1), 2 * rj + (cls >> 1)) * NP);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+            }
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) {
+        // copies and MMAs issued before the abort land before the memory is released
+        const long long p = s_issued[0], m = s_issued[1];
+        for (long long gs = p > kTmaStages ? p - kTmaStages : 0; gs < p; ++gs)
+            mbar_wait_bounded(&full[gs % kTmaStages], (uint32_t)((gs / kTmaStages) & 1));
+        if (m > 0) mbar_wait_bounded(&acc_full[(m - 1) % kTmaAcc], (uint32_t)(((m - 1) / kTmaAcc) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmaCols);
+    }
+}
+
+// hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
+// tensor maps describe: planes = 1 -> [hl][plane][y'][x'][32] (targets' level),
+// planes = 0 -> [hl][y][x][32] (parent level, row-major).  One float4 per thread.
+__global__ void split_tf32_layout_kernel(const float4* __restrict__ x, float4* __restrict__ dst, int lg,
+                                         int planes) {
+    const int np = 1 << lg;
+    const int64_t nb = planes ? (int64_t)4 << (2 * lg) : (int64_t)1 << (2 * lg);  // boxes
+    const int64_t n4 = nb * 8;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i >> 3;
+        const int c = (int)(i & 7);
+        uint32_t bx, by;
+        if (planes) {
+            const int plane = (int)(b >> (2 * lg));
+            const int64_t rem = b & (((int64_t)1 << (2 * lg)) - 1);
+            bx = 2 * (uint32_t)(rem & (np - 1)) + (plane & 1);
+            by = 2 * (uint32_t)(rem >> lg) + (plane >> 1);
+        } else {
+            bx = (uint32_t)(b & (np - 1));
+            by = (uint32_t)(b >> lg);
+        }
+        const float4 v = x[(size_t)morton2(bx, by) * 8 + c];
+        const float a[4] = {v.x, v.y, v.z, v.w};
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = __uint_as_float(tf32_rna_bits(a[e]));
+            l[e] = __uint_as_float(tf32_rna_bits(a[e] - h[e]));
+        }
+        dst[i] = make_float4(h[0], h[1], h[2], h[3]);
+        dst[i + n4] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// fp32 tiled map over `rank` dims (dims[0] = 32 coefficients, innermost), box
+// {32, TX, TY, 1, ...}, 128-byte swizzle, zero fill outside
+bool encode_map(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, int TX, int TY) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t gd[5], gs[4];
+    cuuint32_t box[5], es[5];
+    uint64_t stride = 4;
+    for (int i = 0; i < rank; ++i) {
+        gd[i] = dims[i];
+        if (i > 0) gs[i - 1] = stride;
+        stride *= dims[i];
+        box[i] = i == 0 ? 32u : i == 1 ? (cuuint32_t)TX : i == 2 ? (cuuint32_t)TY : 1u;
+        es[i] = 1;
+    }
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(base), gd, gs, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s) {
@@ -452,6 +796,53 @@ cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, c
     if (blocks < 1) blocks = 1;
     split_tf32_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(hi),
                                                    reinterpret_cast<float4*>(lo), n4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
+                           const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
+                           int* status, int num_sms, cudaStream_t s) {
+    const int lg = level - 1;
+    const int np = 1 << lg;
+    const bool l2l = u_parent != nullptr;
+    float* qs = split;                                    // [2][4][np][np][32]
+    float* us = split + ((size_t)2 * 4 * np * np * 32);   // [2][np][np][32]
+    auto grid_for = [&](int64_t n4) {
+        int64_t b = (n4 + 255) / 256;
+        return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
+    };
+    split_tf32_layout_kernel<<<grid_for((int64_t)4 * np * np * 8), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs), lg, 1);
+    if (l2l)
+        split_tf32_layout_kernel<<<grid_for((int64_t)np * np * 8), 256, 0, s>>>(
+            reinterpret_cast<const float4*>(u_parent), reinterpret_cast<float4*>(us), lg, 0);
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    TmaGeo g;
+    g.level = level;
+    g.lg = lg;
+    g.TX = std::min(np, 128);
+    g.TY = std::min(128 / g.TX, np);
+    g.tiles_x = np / g.TX;
+    g.tiles_per_class = g.tiles_x * (np / g.TY);
+    g.n_tiles = 4 * g.tiles_per_class;
+    g.has_l2l = l2l ? 1 : 0;
+    CUtensorMap mq, mu;
+    const uint64_t dq[5] = {32, (uint64_t)np, (uint64_t)np, 4, 2};
+    const uint64_t du[4] = {32, (uint64_t)np, (uint64_t)np, 2};
+    if (!encode_map(&mq, qs, 5, dq, g.TX, g.TY)) return cudaErrorInvalidValue;
+    if (!encode_map(&mu, l2l ? us : qs, 4, du, g.TX, g.TY)) return cudaErrorInvalidValue;
+    constexpr size_t smem = 1024 + (size_t)kTmaStages * kTmaStageBytes;
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tma_kernel, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = std::min(g.n_tiles, num_sms);
+    m2l_tma_kernel<<<grid, kTmaThreads, smem, s>>>(mq, mu, g, (const float*)ops.tc[k], (const float*)ops.mono[k],
+                                                   (const DFv*)Q_level, (const DFv*)C_parent, u_level,
+                                                   (DFv*)C_level, status);
     return cudaGetLastError();
 }
 

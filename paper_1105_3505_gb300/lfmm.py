@@ -18,6 +18,7 @@ from .build import LIB
 LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL = range(7)
 LFMM_FP64, LFMM_MIXED, LFMM_DF = 0, 1, 2
 LFMM_TREE_AUTO, LFMM_TREE_UNIFORM, LFMM_TREE_PRUNED = 0, 1, 2
+LFMM_FLAG_GRAPH = 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lfmm.h")
 
@@ -31,7 +32,7 @@ class LfmmError(RuntimeError):
 class lfmm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("max_leaf_side", ctypes.c_int32), ("proxies_per_edge", ctypes.c_int32),
-                ("tc_min_level", ctypes.c_int32), ("tree", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tc_min_level", ctypes.c_int32), ("tree", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class lfmm_plan_info(ctypes.Structure):
@@ -51,6 +52,11 @@ class lfmm_request(ctypes.Structure):
 class lfmm_request_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("precision", ctypes.c_int32), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+class lfmm_tune_result(ctypes.Structure):
+    _fields_ = [("opts", lfmm_opts), ("rel_err", ctypes.c_double), ("ms", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("from_cache", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +98,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_request), ctypes.POINTER(i64)]),
         "lfmm_server_wait": (ctypes.c_int, [vp, i64, ctypes.POINTER(lfmm_request_stats)]),
         "lfmm_server_destroy": (ctypes.c_int, [vp]),
+        "lfmm_autotune": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, i64, ctypes.c_double, ctypes.POINTER(lfmm_opts),
+                                         ctypes.POINTER(lfmm_tune_result), vp]),
+        "lfmm_tune_cache_clear": (ctypes.c_int, []),
+        "lfmm_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+        "lfmm_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -135,11 +146,13 @@ def lfmm_opts_default() -> lfmm_opts:
 
 
 def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
-              proxies_per_edge: int = 64, tc_min_level: int = 0, tree: int = LFMM_TREE_AUTO) -> lfmm_opts:
+              proxies_per_edge: int = 64, tc_min_level: int = 0, tree: int = LFMM_TREE_AUTO,
+              graph: bool = False) -> lfmm_opts:
     o = lfmm_opts_default()
     o.precision, o.p, o.leaf_size = precision, p, leaf_size
     o.max_leaf_side, o.proxies_per_edge, o.tc_min_level = max_leaf_side, proxies_per_edge, tc_min_level
     o.tree = tree
+    o.flags = LFMM_FLAG_GRAPH if graph else 0
     return o
 
 
@@ -264,6 +277,39 @@ def lfmm_launch_count() -> int:
     return int(load().lfmm_launch_count())
 
 
+def autotune(src, tgt, tol: float, src_offsets=None, tgt_offsets=None, base: lfmm_opts | None = None,
+             stream=None) -> tuple[lfmm_opts, dict]:
+    """lfmm_autotune: (chosen opts, {rel_err, ms, candidates, from_cache}).  With offsets
+    (host int64 arrays, as for Forest) the points are a forest of problems."""
+    r = lfmm_tune_result()
+    so = to = None
+    n_prob = 1
+    if src_offsets is not None:
+        so = np.ascontiguousarray(src_offsets, dtype=np.int64)
+        to = np.ascontiguousarray(tgt_offsets, dtype=np.int64)
+        n_prob = so.shape[0] - 1
+    st = load().lfmm_autotune(_ptr(src), int(src.shape[0]), so.ctypes.data if so is not None else None, _ptr(tgt),
+                              int(tgt.shape[0]), to.ctypes.data if to is not None else None, n_prob, float(tol),
+                              ctypes.byref(base) if base is not None else None, ctypes.byref(r),
+                              _stream_handle(stream))
+    _check(st, "lfmm_autotune")
+    return r.opts, {"rel_err": r.rel_err, "ms": r.ms, "candidates": int(r.candidates),
+                    "from_cache": bool(r.from_cache), "p": int(r.opts.p), "leaf_size": int(r.opts.leaf_size),
+                    "tc_min_level": int(r.opts.tc_min_level), "precision": int(r.opts.precision)}
+
+
+def tune_cache_clear() -> None:
+    _check(load().lfmm_tune_cache_clear(), "lfmm_tune_cache_clear")
+
+
+def tune_cache_save(path: str) -> None:
+    _check(load().lfmm_tune_cache_save(path.encode()), "lfmm_tune_cache_save")
+
+
+def tune_cache_load(path: str) -> None:
+    _check(load().lfmm_tune_cache_load(path.encode()), "lfmm_tune_cache_load")
+
+
 class Plan:
     """Convenience owner of an lfmm plan: ``Plan(src, tgt, ...).eval(f) -> u``.
 
@@ -273,12 +319,12 @@ class Plan:
 
     def __init__(self, src, tgt, precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64,
                  max_leaf_side: int = 32, proxies_per_edge: int = 64, tc_min_level: int = 0,
-                 tree: int = LFMM_TREE_AUTO, stream=None):
+                 tree: int = LFMM_TREE_AUTO, graph: bool = False, stream=None, opts: lfmm_opts | None = None):
         self.n_src, self.n_tgt = int(src.shape[0]), int(tgt.shape[0])
         self.stream = stream
-        self.handle = lfmm_plan_create(src, self.n_src, tgt, self.n_tgt,
-                                       make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge,
-                                                 tc_min_level, tree), stream)
+        if opts is None:
+            opts = make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge, tc_min_level, tree, graph)
+        self.handle = lfmm_plan_create(src, self.n_src, tgt, self.n_tgt, opts, stream)
 
     def status(self):
         lfmm_plan_status(self.handle, self.stream)
@@ -333,12 +379,13 @@ class Forest(Plan):
 
     def __init__(self, src, src_offsets, tgt, tgt_offsets, precision: int = LFMM_MIXED, p: int = 8,
                  leaf_size: int = 64, max_leaf_side: int = 32, proxies_per_edge: int = 64, tc_min_level: int = 0,
-                 stream=None):
+                 graph: bool = False, stream=None, opts: lfmm_opts | None = None):
         self.n_src, self.n_tgt = int(src.shape[0]), int(tgt.shape[0])
         self.stream = stream
-        self.handle = lfmm_forest_create(src, src_offsets, tgt, tgt_offsets,
-                                         make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge,
-                                                   tc_min_level), stream)
+        if opts is None:
+            opts = make_opts(precision, p, leaf_size, max_leaf_side, proxies_per_edge, tc_min_level,
+                             LFMM_TREE_AUTO, graph)
+        self.handle = lfmm_forest_create(src, src_offsets, tgt, tgt_offsets, opts, stream)
 
 
 class Server:

@@ -71,3 +71,44 @@ def test_forest_offsets_validated_without_gpu(lib):
     o = lfmm.make_opts(tree=7)
     st = lib.lfmm_plan_create(ctypes.byref(h), pts.ctypes.data, 4, pts.ctypes.data, 4, ctypes.byref(o), None)
     assert st == lfmm.LFMM_EINVAL and "opts.tree" in lfmm.lfmm_last_error()
+
+
+def test_opts_flags_validated_without_gpu(lib):
+    h = ctypes.c_void_p(123)
+    pts = np.zeros((4, 2), dtype=np.int32)
+    o = lfmm.make_opts()
+    o.flags = 6  # unknown bits
+    st = lib.lfmm_plan_create(ctypes.byref(h), pts.ctypes.data, 4, pts.ctypes.data, 4, ctypes.byref(o), None)
+    assert st == lfmm.LFMM_EINVAL and "flags" in lfmm.lfmm_last_error()
+    assert lfmm.make_opts(graph=True).flags == lfmm.LFMM_FLAG_GRAPH
+
+
+def test_autotune_arguments_validated_without_gpu(lib):
+    pts = np.zeros((4, 2), dtype=np.int32)
+    r = lfmm.lfmm_tune_result()
+    for tol in (0.0, 1e-14, 0.5, float("nan")):
+        st = lib.lfmm_autotune(pts.ctypes.data, 4, None, pts.ctypes.data, 4, None, 1, tol, None, ctypes.byref(r), None)
+        assert st == lfmm.LFMM_EINVAL and "tol" in lfmm.lfmm_last_error()
+    so = np.array([0, 4], dtype=np.int64)
+    st = lib.lfmm_autotune(pts.ctypes.data, 4, so.ctypes.data, pts.ctypes.data, 4, None, 1, 1e-6, None,
+                           ctypes.byref(r), None)
+    assert st == lfmm.LFMM_EINVAL
+
+
+def test_tune_cache_roundtrip_without_gpu(lib, tmp_path):
+    lfmm.tune_cache_clear()
+    good = tmp_path / "tune.txt"
+    good.write_text("lfmm-tune-1 1 -6 20 20 0 0 7 64 7 2.500000e-07 4.100000e-01\n"
+                    "lfmm-tune-1 2 -10 17 15 0 0 14 128 0 3.000000e-12 2.000000e+00\n")
+    lfmm.tune_cache_load(str(good))
+    out = tmp_path / "out.txt"
+    lfmm.tune_cache_save(str(out))
+    lines = sorted(out.read_text().splitlines())
+    assert lines == sorted(good.read_text().splitlines())
+    bad = tmp_path / "bad.txt"
+    bad.write_text("lfmm-tune-1 1 -6 20 20 0 0 99 64 7 1e-7 1.0\n")  # p out of range
+    with pytest.raises(lfmm.LfmmError, match="line 1"):
+        lfmm.tune_cache_load(str(bad))
+    lfmm.tune_cache_clear()
+    lfmm.tune_cache_save(str(out))
+    assert out.read_text() == ""
