@@ -71,7 +71,7 @@ typedef struct lfmm_opts {
     int32_t proxies_per_edge; /* proxy points per edge of the proxy ring of Sec. 5 (>= 8);     */
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
     int32_t tc_min_level;     /* mixed path, P <= 32: tree levels >= this run M2L on the      */
-                              /* tensor cores (0 = default 8; a value > 30 disables them)     */
+                              /* tensor cores (0 = default 7; a value > 30 disables them)     */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
     int32_t flags;            /* bitwise OR of LFMM_FLAG_* (0: none)                           */
 } lfmm_opts;
@@ -85,6 +85,12 @@ typedef struct lfmm_opts {
  * launches.  While phase profiling is on (lfmm_profile_enable) evaluation is eager, so
  * that each phase can be timed. */
 #define LFMM_FLAG_GRAPH 1
+/* Run the whole evaluation on the caller's stream, one kernel after the other.  By
+ * default the near field (P2P) runs on a second stream beside the far-field sweeps and
+ * the two are joined by one elementwise sum; serial order gives each kernel the whole
+ * device, so per-phase timings (lfmm_profile_*) measure each kernel alone.  Results
+ * are bit-identical either way. */
+#define LFMM_FLAG_SERIAL 2
 
 /* Tree storage.  UNIFORM: every box of every level is stored (Sec. 6), the layout for
  * points that fill their root box.  PRUNED: the same levels and boxes, but only boxes
@@ -142,6 +148,11 @@ int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_
 
 /* Release a plan (NULL is a no-op).  Waits for the plan's outstanding work. */
 int lfmm_plan_destroy(lfmm_plan* plan);
+
+/* Replace the plan's LFMM_FLAG_* bits (graph replay, serial order) for later
+ * evaluations; clearing LFMM_FLAG_GRAPH releases the recorded graph.  Work already
+ * queued is not affected. */
+int lfmm_plan_set_flags(lfmm_plan* plan, int32_t flags);
 
 /* Synchronise `stream` and report device-side failures of the plan's kernels since the
  * last call: LFMM_ETIMEOUT if a bounded wait inside a kernel gave up (an mbarrier wait of

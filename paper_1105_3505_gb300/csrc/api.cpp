@@ -50,7 +50,7 @@ struct lfmm_plan {
     void* Cbox = nullptr;          // per-box incoming constant (8 B per box)
     std::vector<int64_t> lvl_off;  // offset (boxes) of level l inside qhat / uhat
     int* status = nullptr;         // device status word written by kernels (LFMM_ETIMEOUT)
-    int tc_min_level = 8;
+    int tc_min_level = kDefaultTcMinLevel;
     double* f_stage = nullptr;     // device copy of a host f
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
     std::unique_ptr<Forest> forest;  // pruned tree or forest (null: uniform tree)
@@ -192,7 +192,7 @@ int validate_opts(const lfmm_opts& o) {
     if (o.tc_min_level < 0) return fail(LFMM_EINVAL, "opts.tc_min_level must be >= 0");
     if (o.tree != LFMM_TREE_AUTO && o.tree != LFMM_TREE_UNIFORM && o.tree != LFMM_TREE_PRUNED)
         return fail(LFMM_EINVAL, "opts.tree must be LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED");
-    if (o.flags & ~LFMM_FLAG_GRAPH) return fail(LFMM_EINVAL, "opts.flags has unknown bits");
+    if (o.flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL)) return fail(LFMM_EINVAL, "opts.flags has unknown bits");
     return LFMM_OK;
 }
 
@@ -255,7 +255,7 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     if ((st = palloc(p, &stbuf, 16, s))) return st;
     p->status = (int*)stbuf;
     LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
-    p->tc_min_level = p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level;
+    p->tc_min_level = p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level;
     p->bytes += F.bytes;
     return LFMM_OK;
 }
@@ -421,7 +421,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         boxes += (int64_t)1 << (2 * l);
     }
     p->n_boxes = boxes;
-    if (p->opts.precision == LFMM_MIXED && p->NP == 32 && p->L >= (p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level)) {
+    if (p->opts.precision == LFMM_MIXED && p->NP == 32 && p->L >= (p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level)) {
         // largest tensor-core level: TF32 hi/lo of its q_hat and of its parent's u_hat
         const size_t n = ((size_t)p->NP << (2 * p->L)) * 2 + ((size_t)p->NP << (2 * std::max(0, p->L - 1))) * 2;
         if ((st = palloc(p, &p->tc_split, n * sizeof(float), s))) return st;
@@ -440,7 +440,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     if ((st = palloc(p, &stbuf, 16, s))) return st;
     p->status = (int*)stbuf;
     LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
-    p->tc_min_level = p->opts.tc_min_level == 0 ? 8 : p->opts.tc_min_level;
+    p->tc_min_level = p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level;
     // no final synchronisation: temporaries are freed in stream order, and the host
     // buffers of copied coordinates were read before the root-box readback
     return LFMM_OK;
@@ -483,8 +483,11 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     // runs on the plan's second stream beside the per-level M2L launches and the L2P
     // (after the cooperative coarse-level kernels, which need the whole device), and
     // one elementwise sum joins the two.
-    if (L >= 2 && p->un_tmp && !p->aux) p->aux = acquire_aux(p->device);
-    const bool concurrent = L >= 2 && p->un_tmp != nullptr && p->aux != nullptr;
+    // With LFMM_FLAG_SERIAL the same kernels run in the same order on `s` alone.
+    const bool split = L >= 2 && p->un_tmp != nullptr;
+    if (split && !(p->opts.flags & LFMM_FLAG_SERIAL) && !p->aux) p->aux = acquire_aux(p->device);
+    const bool concurrent = split && !(p->opts.flags & LFMM_FLAG_SERIAL) && p->aux != nullptr;
+    cudaStream_t near_s = concurrent ? p->aux->s : s;
     LevelBufs lb;
     for (int l = std::min(2, L); l <= L && l < 16; ++l) {
         lb.q[l] = Qx(l);
@@ -513,12 +516,14 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
             l_first = last + 1;
         }
     }
-    if (concurrent) {
-        LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
-        LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
-        PhaseTimer pt(LFMM_PHASE_P2P, p->aux->s);
+    if (split) {
+        if (concurrent) {
+            LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
+            LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
+        }
+        PhaseTimer pt(LFMM_PHASE_P2P, near_s);
         LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Qm(L), nullptr, p->un_tmp,
-                                        nullptr, p->num_sms, p->aux->s));
+                                        nullptr, p->num_sms, near_s));
         pt.add_launches(1);
     }
     for (int l = l_first; l <= L; ++l) {
@@ -537,14 +542,16 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
                                     l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), s));
         pt.add_launches(1);
     }
-    if (concurrent) {
+    if (split) {
         {
             PhaseTimer pt(LFMM_PHASE_L2P, s);
             LFMM_CUDA_TRY(launch_l2p<T>(t, ops, Ux(L), Cm(L), p->uf_tmp, s));
             pt.add_launches(1);
         }
-        LFMM_CUDA_TRY(cudaEventRecord(p->aux->join, p->aux->s));
-        LFMM_CUDA_TRY(cudaStreamWaitEvent(s, p->aux->join, 0));
+        if (concurrent) {
+            LFMM_CUDA_TRY(cudaEventRecord(p->aux->join, p->aux->s));
+            LFMM_CUDA_TRY(cudaStreamWaitEvent(s, p->aux->join, 0));
+        }
         PhaseTimer pt(LFMM_PHASE_L2P, s);
         LFMM_CUDA_TRY(launch_combine(p->nt, p->un_tmp, p->uf_tmp, u, un, uf, s));
         pt.add_launches(1);
@@ -720,6 +727,18 @@ int lfmm_plan_destroy(lfmm_plan* plan) {
     release_aux(plan->aux);
     delete plan;
     if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("plan destroy: ") + cudaGetErrorString(e));
+    return LFMM_OK;
+}
+
+int lfmm_plan_set_flags(lfmm_plan* p, int32_t flags) {
+    if (!p) return fail(LFMM_EINVAL, "NULL plan");
+    if (flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL)) return fail(LFMM_EINVAL, "flags has unknown bits");
+    if (flags != p->opts.flags && p->graph) {
+        // the recorded launch sequence depends on the flags
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    p->opts.flags = flags;
     return LFMM_OK;
 }
 

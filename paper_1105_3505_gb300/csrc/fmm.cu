@@ -31,8 +31,16 @@ namespace lfmm {
 namespace {
 
 // ------------------------------------------------------------------------- P2M
-// One warp per leaf (row-major leaf index).  Writes the sorted charges in T, the
+// Half a warp per leaf (row-major leaf index; a leaf holds ~16 sources at the usual
+// leaf sizes, so a whole warp would idle half its lanes and pay the per-leaf work
+// twice).  Lane h of a half owns expansion entries [h PL, h PL + PL); each source's
+// row of T_ofs^T is one vector load per lane.  Writes the sorted charges in T, the
 // outgoing expansion and the leaf's total charge (Morton index).
+template <typename T, int N>
+struct alignas(sizeof(T) * N > 16 ? 16 : sizeof(T) * N) VecT {
+    T v[N];
+};
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restrict__ begin,
                                                   const int32_t* __restrict__ loc,
@@ -43,23 +51,25 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                                                   T* __restrict__ qhat,
                                                   typename Mono<T>::V* __restrict__ Q) {
     using M = Mono<T>;
-    constexpr int PL = NP / 32;
-    const int lane = threadIdx.x & 31;
+    constexpr int G = 16, PL = NP / G;
+    using Row = VecT<T, PL>;
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & (G - 1);
     const int64_t n_leaves = (int64_t)1 << (2 * L);
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < n_leaves;
-         leaf += nw) {
-        const int b = begin[leaf], e = begin[leaf + 1];
-        const uint32_t mort = morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L));
+    for (int64_t pair = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; 2 * pair < n_leaves; pair += nw) {
+        const int64_t leaf = 2 * pair + half;
+        const bool lv = leaf < n_leaves;
+        const int b = lv ? begin[leaf] : 0, cnt = lv ? begin[leaf + 1] - b : 0;
+        const int cmax = max(cnt, __shfl_xor_sync(kFull, cnt, 16));
         T acc[PL];
 #pragma unroll
         for (int i = 0; i < PL; ++i) acc[i] = T(0);
         typename M::V qsum = M::zero();
-        for (int j0 = b; j0 < e; j0 += 32) {
-            const int j = j0 + lane;
+        for (int j0 = 0; j0 < cmax; j0 += G) {
             T fj = T(0);
             int J = 0;
-            if (j < e) {
+            if (j0 + hl < cnt) {
+                const int j = b + j0 + hl;
                 const int l = loc[j];
                 J = (l & 0xffff) + side * (l >> 16);
                 const double fd = f[perm[j]];
@@ -67,20 +77,27 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                 f_sorted[j] = fj;
                 qsum = M::add(qsum, M::from_double(fd));
             }
-            const int cnt = min(32, e - j0);
-            for (int k = 0; k < cnt; ++k) {
-                const T fk = shfl(fj, k);
-                const T* row = tofsT + (size_t)shfl(J, k) * NP;
+            const int cc = min(G, cmax - j0);
+            for (int k = 0; k < cc; ++k) {
+                // lanes of a half with fewer sources multiply row 0 by zero
+                const T fk = shfl(fj, (half << 4) + k);
+                const int Jk = __shfl_sync(kFull, J, (half << 4) + k);
+                const Row r = *reinterpret_cast<const Row*>(tofsT + (size_t)Jk * NP + hl * PL);
 #pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), fk, acc[i]);
+                for (int i = 0; i < PL; ++i) acc[i] = fma(r.v[i], fk, acc[i]);
             }
         }
+        if (lv) {
+            const uint32_t mort = morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L));
+            Row o;
 #pragma unroll
-        for (int i = 0; i < PL; ++i) qhat[(size_t)mort * NP + lane + 32 * i] = acc[i];
-        // warp sum of the compensated partial charges
+            for (int i = 0; i < PL; ++i) o.v[i] = acc[i];
+            *reinterpret_cast<Row*>(qhat + (size_t)mort * NP + hl * PL) = o;
+        }
+        // sum of the compensated partial charges over the half
 #pragma unroll
-        for (int off = 16; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
-        if (lane == 0) Q[mort] = qsum;
+        for (int off = 8; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
+        if (lv && hl == 0) Q[morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L))] = qsum;
     }
 }
 
@@ -1154,7 +1171,7 @@ template <typename T>
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
                        T* qhat_leaf, void* Q, cudaStream_t s) {
     const int threads = 256;
-    int64_t blocks = (t.n_leaves * 32 + threads - 1) / threads;
+    int64_t blocks = (t.n_leaves * 16 + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
     using V = typename Mono<T>::V;

@@ -320,6 +320,9 @@ template <typename T>
 cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, int tc_min_level, unsigned* sync,
                              int* status, int num_sms, int* last_level, cudaStream_t s);
 
+// First tree level whose M2L runs on the tensor cores when opts.tc_min_level is 0
+// (levels of 4^7 boxes and more; below that the fused SIMT kernel wins).
+constexpr int kDefaultTcMinLevel = 7;
 // Whether level `level` (k levels above the leaves) runs M2L + L2L on the tensor cores:
 // fp32 arithmetic, P <= 32, tiles present, level >= tc_min_level.
 inline bool m2l_uses_tc(const DeviceOps& ops, int k, int level, int tc_min_level, bool fp32) {

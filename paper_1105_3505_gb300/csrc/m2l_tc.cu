@@ -73,6 +73,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (clock64() - t0 > kWaitBudget) return false;
     return true;
 }
+// non-blocking probe of a phase; the TMA pipeline's role threads poll with it, since a
+// suspended try_wait can sleep past the phase change and every K-step waits three times
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_poll_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > kWaitBudget) return false;
+    return true;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
@@ -469,13 +489,15 @@ __global__ void split_tf32_kernel(const float4* __restrict__ x, float4* __restri
 //     (frees the shared memory) and to the buffer's "acc_full" barrier;
 //   warps 0-3: one target box per thread (TMEM lane) - fold every step's fresh
 //     accumulators into round-to-nearest fp32 registers, arrive on "acc_empty"; at a
-//     tile's last step write the row of u_hat; at its first, the compensated constant.
+//     tile's last step write the row of u_hat;
+//   warp 6: the compensated incoming constant of every box of the CTA's tiles (plain
+//     loads and float-pair arithmetic, independent of the pipeline).
 // Every wait is bounded; on expiry the CTA records LFMM_ETIMEOUT, every role stops at
 // its next iteration, and the teardown waits (bounded) for the copies and MMAs issued.
-constexpr int kTmaStages = 4;
+constexpr int kTmaStages = 5;
 constexpr int kTmaAcc = 4;
-constexpr int kTmaThreads = 192;
-constexpr int kTmaCols = 256;  // D_big[b]: [32b, 32b+32), D_small[b]: [128+32b, 160+32b)
+constexpr int kTmaThreads = 224;
+constexpr int kTmaCols = 256;  // buffer b: D_big at columns [64b, 64b+32), D_small at [64b+32, 64b+64)
 constexpr uint32_t kTmaABytes = 128 * 32 * 4;
 constexpr uint32_t kTmaStageBytes = 2 * kTmaABytes + 8192;
 
@@ -518,7 +540,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     __shared__ uint32_t s_tmem;
     __shared__ int s_off[4][27][3];
     __shared__ int s_abort;
-    __shared__ long long s_issued[2];  // K-steps issued by the producer and by the MMA thread
+    __shared__ int s_issued[2];  // K-steps issued by the producer and by the MMA thread
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_steps = 27 + g.has_l2l;
@@ -526,7 +548,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     const int rows = g.TX * g.TY;
     const uint32_t tx_bytes = 2u * (uint32_t)rows * 128u + 8192u;
     const int my_tiles = blockIdx.x < (unsigned)g.n_tiles ? (g.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const long long total = (long long)my_tiles * n_steps;
+    const int total = my_tiles * n_steps;  // K-steps of this CTA (< 2^31: n_tiles <= 4^14 / 128)
     volatile int* vabort = &s_abort;
 
     if (threadIdx.x == 0) {
@@ -566,28 +588,30 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         atomicExch(&s_abort, 1);
         atomicExch(status, LFMM_ETIMEOUT);
     };
-    // tile t: class t & 3 (classes interleave for balance), then row-major tiles
-    auto tile_of = [&](long long gs, int& cls, int& ri0, int& rj0) {
-        const int t = (int)blockIdx.x + (int)(gs / n_steps) * (int)gridDim.x;
+    // it-th tile of this CTA: t = blockIdx.x + it * gridDim.x; class t & 3 (classes
+    // interleave for balance), then row-major tiles of the class
+    auto tile_of = [&](int it, int& cls, int& ri0, int& rj0) {
+        const int t = (int)blockIdx.x + it * (int)gridDim.x;
         cls = t & 3;
         const int k = t >> 2;
         ri0 = (k % g.tiles_x) * g.TX;
         rj0 = (k / g.tiles_x) * g.TY;
     };
+    // The roles walk the same sequence of K-steps gs = it * n_steps + st with running
+    // counters: stage slot gs % kTmaStages and its use count, accumulator buffer
+    // gs % kTmaAcc and its use count.
 
     if (warp == 4) {
         if (lane == 0) {
-            for (long long gs = 0; gs < total; ++gs) {
+            int it = 0, st = 0, slot = 0, use = 0;
+            int cls = 0, ri0 = 0, rj0 = 0;
+            tile_of(0, cls, ri0, rj0);
+            for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
-                const int slot = (int)(gs % kTmaStages);
-                const long long use = gs / kTmaStages;
-                if (use > 0 && !mbar_wait_bounded(&empty[slot], (uint32_t)((use - 1) & 1))) {
+                if (use > 0 && !mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1))) {
                     abort_now();
                     break;
                 }
-                int cls, ri0, rj0;
-                tile_of(gs, cls, ri0, rj0);
-                const int st = (int)(gs % n_steps);
                 const uint32_t sa = base + (uint32_t)slot * kTmaStageBytes;
                 mbar_arrive_expect_tx(&full[slot], tx_bytes);
                 if (st < 27) {
@@ -602,36 +626,73 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                     bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)(kNumOffsets + cls) * 2048, 8192, &full[slot]);
                 }
                 s_issued[0] = gs + 1;
+                if (++slot == kTmaStages) {
+                    slot = 0;
+                    ++use;
+                }
+                if (++st == n_steps) {
+                    st = 0;
+                    if (++it < my_tiles) tile_of(it, cls, ri0, rj0);
+                }
             }
         }
     } else if (warp == 5) {
         if (lane == 0) {
-            constexpr uint32_t kIdesc = idesc_tf32(128, NP);
-            for (long long gs = 0; gs < total; ++gs) {
+            // per kk: D[0, 64) = A_hi x [B_hi | B_lo] (N = 64: the hi*hi and hi*lo terms
+            // side by side), then D[32, 64) += A_lo x B_hi (N = 32)
+            constexpr uint32_t kIdesc64 = idesc_tf32(128, 64), kIdesc32 = idesc_tf32(128, 32);
+            int slot = 0, use = 0, d = 0, du = 0;
+            for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
-                const int slot = (int)(gs % kTmaStages);
-                const int d = (int)(gs % kTmaAcc);
-                const long long du = gs / kTmaAcc;
-                if (!mbar_wait_bounded(&full[slot], (uint32_t)((gs / kTmaStages) & 1)) ||
-                    (du > 0 && !mbar_wait_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1)))) {
+                if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1)) ||
+                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1)))) {
                     abort_now();
                     break;
                 }
                 tc_fence_after();
                 const uint32_t a_hi = base + (uint32_t)slot * kTmaStageBytes, a_lo = a_hi + kTmaABytes;
-                const uint32_t b_hi = a_hi + 2 * kTmaABytes, b_lo = b_hi + 4096;
-                const uint32_t d_big = tmem + 32 * d, d_small = tmem + 128 + 32 * d;
+                const uint32_t b_hi = a_hi + 2 * kTmaABytes;
+                const uint32_t d_big = tmem + 64 * d, d_small = d_big + 32;
+                const uint64_t dah = smem_desc_sw128(a_hi), dal = smem_desc_sw128(a_lo), dbh = smem_desc_sw128(b_hi);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t ah = smem_desc_sw128(a_hi + 32 * kk), al = smem_desc_sw128(a_lo + 32 * kk);
-                    const uint64_t bh = smem_desc_sw128(b_hi + 32 * kk), bl = smem_desc_sw128(b_lo + 32 * kk);
-                    mma_tf32_ss(d_big, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, ah, bl, kIdesc, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, al, bh, kIdesc, 1u);
+                    // +32 bytes along K inside the swizzled rows = +2 in the descriptor's address field
+                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdesc64, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdesc32, 1u);
                 }
                 mma_commit(&empty[slot]);
                 mma_commit(&acc_full[d]);
                 s_issued[1] = gs + 1;
+                if (++slot == kTmaStages) {
+                    slot = 0;
+                    ++use;
+                }
+                if (++d == kTmaAcc) {
+                    d = 0;
+                    ++du;
+                }
+            }
+        }
+    } else if (warp == 6) {
+        for (int it = 0; it < my_tiles; ++it) {
+            int cls, ri0, rj0;
+            tile_of(it, cls, ri0, rj0);
+            const int px = cls & 1, py = cls >> 1;
+            for (int r = lane; r < rows; r += 32) {
+                const int ri = ri0 + r % g.TX, rj = rj0 + r / g.TX;
+                DFv sacc = g.has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
+                DFv qv[27];
+#pragma unroll
+                for (int k = 0; k < 27; ++k) {
+                    const int sx = 2 * ri + px + s_off[cls][k][0], sy = 2 * rj + py + s_off[cls][k][1];
+                    qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qin[morton2(sx, sy)] : DFv{0.f, 0.f};
+                }
+#pragma unroll
+                for (int k = 0; k < 27; ++k) {
+                    const int o = s_off[cls][k][2];
+                    sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+                }
+                Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
             }
         }
     } else {
@@ -642,37 +703,16 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         float acc[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        int it = 0, st = 0, d = 0, du = 0;
         int cls = 0, ri = 0, rj = 0;
-        for (long long gs = 0; gs < total; ++gs) {
-            const int st = (int)(gs % n_steps);
+        for (int gs = 0; gs < total; ++gs) {
             if (st == 0) {
                 int ri0, rj0;
-                tile_of(gs, cls, ri0, rj0);
+                tile_of(it, cls, ri0, rj0);
                 ri = ri0 + xl;
                 rj = rj0 + yl;
-                // incoming constant (compensated) of this box, while the tile's MMAs run
-                if (valid) {
-                    const int px = cls & 1, py = cls >> 1;
-                    DFv sacc = g.has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
-                    for (int c0 = 0; c0 < 27; c0 += 9) {
-                        DFv qv[9];
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) {
-                            const int sx = 2 * ri + px + s_off[cls][c0 + k][0], sy = 2 * rj + py + s_off[cls][c0 + k][1];
-                            qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qin[morton2(sx, sy)]
-                                                                                     : DFv{0.f, 0.f};
-                        }
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) {
-                            const int o = s_off[cls][c0 + k][2];
-                            sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
-                        }
-                    }
-                    Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
-                }
             }
-            const int d = (int)(gs % kTmaAcc);
-            bool ok = *vabort == 0 && mbar_wait_bounded(&acc_full[d], (uint32_t)((gs / kTmaAcc) & 1));
+            bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) abort_now();
@@ -680,8 +720,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
             }
             tc_fence_after();
             uint32_t big[32], small[32];
-            tmem_ld32(tmem + lane_base + 32 * d, big);
-            tmem_ld32(tmem + lane_base + 128 + 32 * d, small);
+            tmem_ld32(tmem + lane_base + 64 * d, big);
+            tmem_ld32(tmem + lane_base + 64 * d + 32, small);
             tmem_wait_ld();
             tc_fence_before();
             __syncwarp();
@@ -699,16 +739,24 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 #pragma unroll
                 for (int j = 0; j < 32; ++j) acc[j] = 0.f;
             }
+            if (++d == kTmaAcc) {
+                d = 0;
+                ++du;
+            }
+            if (++st == n_steps) {
+                st = 0;
+                ++it;
+            }
         }
     }
     __syncwarp();
     __syncthreads();
     if (s_abort && threadIdx.x == 0) {
         // copies and MMAs issued before the abort land before the memory is released
-        const long long p = s_issued[0], m = s_issued[1];
-        for (long long gs = p > kTmaStages ? p - kTmaStages : 0; gs < p; ++gs)
-            mbar_wait_bounded(&full[gs % kTmaStages], (uint32_t)((gs / kTmaStages) & 1));
-        if (m > 0) mbar_wait_bounded(&acc_full[(m - 1) % kTmaAcc], (uint32_t)(((m - 1) / kTmaAcc) & 1));
+        const int p = s_issued[0], m = s_issued[1];
+        for (int gs = p > kTmaStages ? p - kTmaStages : 0; gs < p; ++gs)
+            mbar_poll_bounded(&full[gs % kTmaStages], (uint32_t)((gs / kTmaStages) & 1));
+        if (m > 0) mbar_poll_bounded(&acc_full[(m - 1) % kTmaAcc], (uint32_t)(((m - 1) / kTmaAcc) & 1));
     }
     tc_fence_before();
     __syncthreads();

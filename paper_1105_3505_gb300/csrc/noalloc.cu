@@ -156,7 +156,7 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     int64_t boxes = 0;
     for (int l = std::min(2, L); l <= L; ++l) boxes += (int64_t)1 << (2 * l);
     auto a = [](int64_t b) { return b == 0 ? (int64_t)16 : b; };
-    const int tc_min = o.tc_min_level == 0 ? 8 : o.tc_min_level;
+    const int tc_min = o.tc_min_level == 0 ? kDefaultTcMinLevel : o.tc_min_level;
     const int64_t split = (o.precision == LFMM_MIXED && NP == 32 && L >= tc_min)
                               ? a(((int64_t)NP << (2 * L)) * 2 * 4 + ((int64_t)NP << (2 * std::max(0, L - 1))) * 2 * 4)
                               : 0;  // TF32 hi/lo copies for the tensor-core M2L

@@ -240,7 +240,7 @@ int lfmm_autotune(const int32_t* src_xy, int64_t n_src, const int64_t* src_offse
             lfmm_plan_destroy(plan);
         }
         for (int tc : {L, L - 1, 99}) {
-            if (tc < 2 || tc == (pick.tc_min_level == 0 ? 8 : pick.tc_min_level)) continue;
+            if (tc < 2 || tc == (pick.tc_min_level == 0 ? lfmm::kDefaultTcMinLevel : pick.tc_min_level)) continue;
             lfmm_opts c = pick;
             c.tc_min_level = tc;
             double ms = 0.0;

@@ -18,7 +18,7 @@ from .build import LIB
 LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL = range(7)
 LFMM_FP64, LFMM_MIXED, LFMM_DF = 0, 1, 2
 LFMM_TREE_AUTO, LFMM_TREE_UNIFORM, LFMM_TREE_PRUNED = 0, 1, 2
-LFMM_FLAG_GRAPH = 1
+LFMM_FLAG_GRAPH, LFMM_FLAG_SERIAL = 1, 2
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lfmm.h")
 
@@ -80,6 +80,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_eval": (ctypes.c_int, [vp, vp, vp, vp]),
         "lfmm_eval_parts": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lfmm_plan_destroy": (ctypes.c_int, [vp]),
+        "lfmm_plan_set_flags": (ctypes.c_int, [vp, i32]),
         "lfmm_plan_status": (ctypes.c_int, [vp, vp]),
         "lfmm_plan_get_info": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_plan_info)]),
         "lfmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -147,12 +148,12 @@ def lfmm_opts_default() -> lfmm_opts:
 
 def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
               proxies_per_edge: int = 64, tc_min_level: int = 0, tree: int = LFMM_TREE_AUTO,
-              graph: bool = False) -> lfmm_opts:
+              graph: bool = False, serial: bool = False) -> lfmm_opts:
     o = lfmm_opts_default()
     o.precision, o.p, o.leaf_size = precision, p, leaf_size
     o.max_leaf_side, o.proxies_per_edge, o.tc_min_level = max_leaf_side, proxies_per_edge, tc_min_level
     o.tree = tree
-    o.flags = LFMM_FLAG_GRAPH if graph else 0
+    o.flags = (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0)
     return o
 
 
@@ -328,6 +329,11 @@ class Plan:
 
     def status(self):
         lfmm_plan_status(self.handle, self.stream)
+
+    def set_flags(self, graph: bool = False, serial: bool = False):
+        """lfmm_plan_set_flags: graph replay and serial order for later evaluations."""
+        flags = (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0)
+        _check(load().lfmm_plan_set_flags(self.handle, flags), "lfmm_plan_set_flags")
 
     def info(self) -> dict:
         return lfmm_plan_get_info(self.handle)

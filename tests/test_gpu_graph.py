@@ -2,8 +2,7 @@
 
 The graph replays exactly the launches of the eager evaluation of the same plan, and
 no kernel of the evaluation uses atomics, so its results must be bit-identical to the
-eager ones (a graph plan evaluates eagerly while phase profiling is on, which gives the
-eager reference on the same plan): on the first call (record + launch), on replays with
+eager ones (lfmm_plan_set_flags switches one plan between the two): on the first call (record + launch), on replays with
 the same pointers, after new pointers force a re-record, for host-staged arrays, and
 for forests.  Two plans built from the same points may order the points of a leaf
 differently (the bucket ranks come from atomics), so across plans the results agree
@@ -36,13 +35,12 @@ def prec(lfmm, name):
 
 
 def eager(lfmm, plan, f, parts=False):
-    """The eager evaluation of a graph plan (phase profiling on)."""
-    lfmm.lfmm_profile_enable(True)
+    """The eager evaluation of a graph plan (graph flag cleared, then set again)."""
+    plan.set_flags(graph=False)
     try:
         return plan.eval_parts(f) if parts else plan.eval(f)
     finally:
-        lfmm.lfmm_profile_enable(False)
-        lfmm.lfmm_profile_read(reset=True)
+        plan.set_flags(graph=True)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64", "df"])
@@ -112,3 +110,18 @@ def test_graph_with_profiling_runs_eager(lfmm):
             lfmm.lfmm_profile_enable(False)
     assert np.array_equal(u0, u1)
     assert ph["p2p"][1] >= 1 and ph["p2m"][1] >= 1
+
+
+@pytest.mark.parametrize("precision", ["mixed", "df"])
+def test_serial_equals_overlapped(lfmm, precision):
+    """LFMM_FLAG_SERIAL runs the same kernels on one stream: bit-identical results."""
+    prob = workloads.uniform_box(40000, 30000, 800, seed=13)
+    pr, p = prec(lfmm, precision)
+    with lfmm.Plan(prob.src, prob.tgt, precision=pr, p=p) as pl:
+        u0 = pl.eval(prob.f)
+        pl.set_flags(serial=True)
+        u1 = pl.eval(prob.f)
+        pl.set_flags(serial=True, graph=True)
+        u2 = pl.eval(prob.f)
+        pl.status()
+    assert np.array_equal(u0, u1) and np.array_equal(u0, u2)
