@@ -1,8 +1,11 @@
 """The tensor-core M2L (tcgen05, 3xTF32 split, mixed path) against the oracle.
 
 tc_min_level = 2 puts every M2L level on the tensor-core kernel, so small problems
-exercise it; the default (level >= 8) is exercised by the full-size test in
-test_gpu_parity.py.  lfmm_plan_status must report no timed-out device wait."""
+exercise it; the default (level >= 7) is exercised by the full-size test in
+test_gpu_parity.py.  Levels whose parity class spans >= 128 boxes per row (level >= 8)
+use row tiles (one class row per tile); a sparse point set in a 4096^2 box with leaves
+capped at side 16 reaches level 8 with few points, so the oracle checks that shape in
+full.  lfmm_plan_status must report no timed-out device wait."""
 import numpy as np
 import pytest
 
@@ -47,3 +50,15 @@ def test_tensor_core_m2l_parity(lfmm, case):
     assert rel_err(u_simt, ref) <= 1e-6
     # the two M2L implementations differ only by rounding
     assert np.abs(u_tc - u_simt).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_tensor_core_row_windows_full_oracle(lfmm):
+    prob = workloads.uniform_box(30000, 20000, 4096, seed=46)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    with lfmm.Plan(prob.src, prob.tgt, precision=lfmm.LFMM_MIXED, p=8, max_leaf_side=16,
+                   tree=lfmm.LFMM_TREE_UNIFORM) as pl:
+        info = pl.info()
+        u = pl.eval(prob.f)
+        pl.status()
+    assert info["L"] == 8 and info["leaf_side"] == 16
+    assert rel_err(u, ref) <= 1e-6, rel_err(u, ref)
