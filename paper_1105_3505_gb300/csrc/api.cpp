@@ -256,6 +256,14 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     p->status = (int*)stbuf;
     LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
     p->tc_min_level = p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level;
+    if (p->opts.precision == LFMM_MIXED && p->NP == 32 && p->tc_min_level <= 30) {
+        // TF32 hi / lo of the largest tensor-core level's q_hat and of its parent's u_hat
+        int64_t rows = 0;
+        for (size_t k = 0; k < F.levels.size(); ++k)
+            if (F.levels[k].nb >= kForestTcMinBoxes)
+                rows = std::max(rows, F.levels[k].nb + (k + 1 < F.levels.size() ? F.levels[k + 1].nb : 0));
+        if (rows > 0 && (st = palloc(p, &p->tc_split, (size_t)2 * rows * 32 * sizeof(float), s))) return st;
+    }
     p->bytes += F.bytes;
     return LFMM_OK;
 }
@@ -450,7 +458,7 @@ template <typename T>
 int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
     if (p->forest)
         return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
-                              u, un, uf, p->tc_min_level, p->status, p->num_sms, s);
+                              u, un, uf, (float*)p->tc_split, p->status, p->num_sms, s);
     TreeView t;
     t.L = p->L;
     t.side = p->side;

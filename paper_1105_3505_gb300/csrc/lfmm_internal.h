@@ -253,9 +253,12 @@ struct Forest {
 int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
                  const int64_t* toff_h, int64_t nt, int np, int leaf_size, int max_leaf_side, cudaStream_t s,
                  PhaseTimer* timer);
+// Levels with at least this many boxes run the list form of the tensor-core M2L
+// (mixed path, P <= 32) when a split buffer is given.
+constexpr int64_t kForestTcMinBoxes = 1024;
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, int tc_min_level, int* status, int num_sms,
+                void* Cbox, double* u, double* un, double* uf, float* tc_split, int* status, int num_sms,
                 cudaStream_t s);
 
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);
@@ -345,6 +348,15 @@ cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
                            int* status, int num_sms, cudaStream_t s);
+// List form of the tensor-core M2L + L2L (pruned storage, forests): compact boxes of
+// one level grouped by class (cls_start, device, 5 entries; n_tiles = sum over classes
+// of ceil(count / 128)), 27 list entries and the parent per box; `split` holds
+// 2 (nb + nb_parent) rows of 32 floats.
+cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, int64_t n_tiles,
+                               const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
+                               const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
+                               float* u_level, void* C_level, float* split, int* status, int num_sms,
+                               cudaStream_t s);
 // hi = TF32(x), lo = TF32(x - hi), n floats (a multiple of 4).
 cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s);
 template <typename T>

@@ -766,6 +766,289 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------------
+// List form, for pruned storage and forests: the boxes of a level are compact and
+// grouped by parity class, and each box carries its 27 interaction-list entries (-1:
+// no box) and its parent.  Same persistent warp-specialised pipeline as the TMA form,
+// but the A operand is gathered: the producer warp copies the 128 source rows of a
+// K-step (hi and lo, split beforehand by split_tf32_kernel) with cp.async into the
+// 128-byte-swizzled layout, zero-filling missing sources; it completes a stage once
+// the copies of the step kStages - 1 steps back have landed (cp.async groups), after a
+// proxy fence, with a second arrival beside the operator tile's bulk copy.
+constexpr int kLStages = 4;
+constexpr uint32_t kLStageBytes = 2 * 16384 + 8192;
+constexpr size_t kLSmem = 1024 + (size_t)kLStages * kLStageBytes + (size_t)128 * 28 * sizeof(int);
+
+__global__ void __launch_bounds__(kTmaThreads, 1) m2l_tc_list_kernel(
+    const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
+    const float* __restrict__ qhi, const float* __restrict__ qlo, const float* __restrict__ uhi,
+    const float* __restrict__ ulo, const float* __restrict__ tiles, const float* __restrict__ mono,
+    const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout,
+    int* __restrict__ status) {
+    constexpr int NP = 32;
+    extern __shared__ __align__(1024) unsigned char tl_smem[];
+    const uint32_t base = smem_u32(tl_smem) + ((1024u - (smem_u32(tl_smem) & 1023u)) & 1023u);
+    // the current tile's source rows per K-step (producer only): [128 rows][28]
+    int* s_src = reinterpret_cast<int*>(tl_smem + (base - smem_u32(tl_smem)) + kLStages * kLStageBytes);
+    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages], acc_full[kTmaAcc], acc_empty[kTmaAcc];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_op[4][28];  // operator tile of K-step st for class c
+    __shared__ long long s_c[5], s_t[5];  // class starts; first tile of each class
+    __shared__ int s_abort;
+    __shared__ int s_issued[2];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool has_l2l = uhi != nullptr;
+    const int n_steps = 27 + (has_l2l ? 1 : 0);
+    volatile int* vabort = &s_abort;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 4; ++c) {
+            const int px = c & 1, py = c >> 1;
+            int nn = 0;
+            for (int d = 0; d < 36; ++d) {
+                const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+                s_op[c][nn++] = offset_index_tc(dx, dy);  // list slot order
+            }
+            s_op[c][27] = kNumOffsets + c;
+        }
+        long long t = 0;
+        for (int c = 0; c <= 4; ++c) {
+            s_c[c] = cls_start[c];
+            s_t[c] = t;
+            if (c < 4) t += (cls_start[c + 1] - cls_start[c] + 127) / 128;
+        }
+        for (int i = 0; i < kLStages; ++i) {
+            mbar_init(&full[i], 2);  // operator tile (with its bytes) + the gathered rows
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < kTmaAcc; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        fence_barrier_init();
+        s_abort = 0;
+        s_issued[0] = s_issued[1] = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, kTmaCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const int n_tiles = (int)s_t[4];
+    const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * n_steps;
+    auto abort_now = [&]() {
+        atomicExch(&s_abort, 1);
+        atomicExch(status, LFMM_ETIMEOUT);
+    };
+    // it-th tile of this CTA: class and first / end box
+    auto tile_of = [&](int it, int& cls, long long& b0, long long& b1) {
+        const long long t = (long long)blockIdx.x + (long long)it * gridDim.x;
+        cls = (t >= s_t[1]) + (t >= s_t[2]) + (t >= s_t[3]);
+        b0 = s_c[cls] + (t - s_t[cls]) * 128;
+        b1 = min(b0 + 128, s_c[cls + 1]);
+    };
+
+    if (warp == 4) {
+        int it = 0, st = 0, slot = 0, use = 0, cls = 0;
+        long long b0 = 0, b1 = 0;
+        int pend_step = 0;  // first step whose gathered rows have not been announced
+        for (int gs = 0; gs < total; ++gs) {
+            if (__any_sync(0xffffffffu, *vabort != 0)) break;  // warp-uniform
+            if (st == 0) {
+                tile_of(it, cls, b0, b1);
+                // source rows of the tile's K-steps
+                for (int i = lane; i < 128 * 28; i += 32) {
+                    const int r = i / 28, k = i % 28;
+                    const long long b = b0 + r;
+                    int v = -1;
+                    if (b < b1) v = k < 27 ? il[b * 27 + k] : (has_l2l ? par[b] : -1);
+                    s_src[i] = v;
+                }
+                __syncwarp();
+            }
+            bool ok = true;
+            if (use > 0) ok = mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) abort_now();
+                break;
+            }
+            const uint32_t sa = base + (uint32_t)slot * kLStageBytes;
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&full[slot], 8192);
+                bulk_g2s_u32(sa + 32768, tiles + (size_t)s_op[cls][st] * 2048, 8192, &full[slot]);
+            }
+            const float* hs = st < 27 ? qhi : uhi;
+            const float* ls = st < 27 ? qlo : ulo;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = lane + 32 * i;
+                const int si = s_src[r * 28 + st];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const size_t off = si < 0 ? 0 : (size_t)si * NP + 4 * c;
+                    const int bytes = si < 0 ? 0 : 16;
+                    const uint32_t dst = (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + dst), "l"(hs + off),
+                                 "r"(bytes)
+                                 : "memory");
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + 16384 + dst),
+                                 "l"(ls + off), "r"(bytes)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            // announce the rows of step gs - (kLStages - 2) - ... : at most kLStages - 2
+            // groups stay in flight
+            if (gs - pend_step >= kLStages - 2) {
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(kLStages - 2) : "memory");
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[pend_step % kLStages]);
+                ++pend_step;
+            }
+            if (lane == 0) s_issued[0] = gs + 1;
+            if (++slot == kLStages) {
+                slot = 0;
+                ++use;
+            }
+            if (++st == n_steps) {
+                st = 0;
+                ++it;
+            }
+        }
+        // announce what is left (also after an abort, so that the teardown's waits end)
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        fence_proxy_async_smem();
+        __syncwarp();
+        const int issued = s_issued[0];
+        if (lane == 0)
+            for (; pend_step < issued; ++pend_step) mbar_arrive(&full[pend_step % kLStages]);
+    } else if (warp == 5) {
+        if (lane == 0) {
+            constexpr uint32_t kIdesc64 = idesc_tf32(128, 64), kIdesc32 = idesc_tf32(128, 32);
+            int slot = 0, use = 0, d = 0, du = 0;
+            for (int gs = 0; gs < total; ++gs) {
+                if (*vabort) break;
+                if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1)) ||
+                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1)))) {
+                    abort_now();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_hi = base + (uint32_t)slot * kLStageBytes, a_lo = a_hi + 16384;
+                const uint32_t b_hi = a_hi + 32768;
+                const uint32_t d_big = tmem + 64 * d, d_small = d_big + 32;
+                const uint64_t dah = smem_desc_sw128(a_hi), dal = smem_desc_sw128(a_lo), dbh = smem_desc_sw128(b_hi);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdesc64, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdesc32, 1u);
+                }
+                mma_commit(&empty[slot]);
+                mma_commit(&acc_full[d]);
+                s_issued[1] = gs + 1;
+                if (++slot == kLStages) {
+                    slot = 0;
+                    ++use;
+                }
+                if (++d == kTmaAcc) {
+                    d = 0;
+                    ++du;
+                }
+            }
+        }
+    } else if (warp == 6) {
+        for (int it = 0; it < my_tiles; ++it) {
+            int cls;
+            long long b0, b1;
+            tile_of(it, cls, b0, b1);
+            for (long long b = b0 + lane; b < b1; b += 32) {
+                const int pb = has_l2l ? par[b] : -1;
+                DFv sacc = pb >= 0 ? Cpar[pb] : DFv{0.f, 0.f};
+                for (int k0 = 0; k0 < 27; k0 += 9) {
+                    int sb[9];
+                    DFv qv[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) sb[k] = il[b * 27 + k0 + k];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) qv[k] = sb[k] >= 0 ? Qin[sb[k]] : DFv{0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const int o = s_op[cls][k0 + k];
+                        if (sb[k] >= 0) sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+                    }
+                }
+                Cout[b] = sacc;
+            }
+        }
+    } else {
+        const int r = threadIdx.x;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        int it = 0, st = 0, d = 0, du = 0, cls = 0;
+        long long b0 = 0, b1 = 0;
+        for (int gs = 0; gs < total; ++gs) {
+            if (st == 0) tile_of(it, cls, b0, b1);
+            bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) abort_now();
+                break;
+            }
+            tc_fence_after();
+            uint32_t big[32], small[32];
+            tmem_ld32(tmem + lane_base + 64 * d, big);
+            tmem_ld32(tmem + lane_base + 64 * d + 32, small);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[d]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+            if (st == n_steps - 1) {
+                if (b0 + r < b1) {
+                    float4* dst = reinterpret_cast<float4*>(out + (size_t)(b0 + r) * NP);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+            }
+            if (++d == kTmaAcc) {
+                d = 0;
+                ++du;
+            }
+            if (++st == n_steps) {
+                st = 0;
+                ++it;
+            }
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) {
+        // the producer announced every stage it issued: wait for them, then for the MMAs
+        const int p = s_issued[0], m = s_issued[1];
+        for (int gs = p > kLStages ? p - kLStages : 0; gs < p; ++gs)
+            mbar_poll_bounded(&full[gs % kLStages], (uint32_t)((gs / kLStages) & 1));
+        if (m > 0) mbar_poll_bounded(&acc_full[(m - 1) % kTmaAcc], (uint32_t)(((m - 1) / kTmaAcc) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmaCols);
+    }
+}
+
 // hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
 // tensor maps describe: planes = 1 -> [hl][plane][y'][x'][32] (targets' level),
 // planes = 0 -> [hl][y][x][32] (parent level, row-major).  One float4 per thread.
@@ -891,6 +1174,32 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     m2l_tma_kernel<<<grid, kTmaThreads, smem, s>>>(mq, mu, g, (const float*)ops.tc[k], (const float*)ops.mono[k],
                                                    (const DFv*)Q_level, (const DFv*)C_parent, u_level,
                                                    (DFv*)C_level, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, int64_t n_tiles,
+                               const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
+                               const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
+                               float* u_level, void* C_level, float* split, int* status, int num_sms,
+                               cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
+    float* qhi = split;
+    float* qlo = qhi + (size_t)nb * 32;
+    float* uhi = qlo + (size_t)nb * 32;
+    float* ulo = uhi + (size_t)nb_parent * 32;
+    {
+        cudaError_t e = launch_split_tf32(q_level, qhi, qlo, nb * 32, s);
+        if (e != cudaSuccess) return e;
+        if (u_parent && (e = launch_split_tf32(u_parent, uhi, ulo, nb_parent * 32, s)) != cudaSuccess) return e;
+    }
+    {
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tc_list_kernel, kLSmem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = (int)std::min<int64_t>(n_tiles, num_sms);
+    m2l_tc_list_kernel<<<grid, kTmaThreads, kLSmem, s>>>(
+        cls_start, il, par, qhi, qlo, u_parent ? uhi : nullptr, u_parent ? ulo : nullptr, (const float*)ops.tc[k],
+        (const float*)ops.mono[k], (const DFv*)Q_level, (const DFv*)C_parent, u_level, (DFv*)C_level, status);
     return cudaGetLastError();
 }
 
