@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 // 128-byte-swizzled layout, zero-filling missing sources; it completes a stage once
 // the copies of the step kStages - 1 steps back have landed (cp.async groups), after a
 // proxy fence, with a second arrival beside the operator tile's bulk copy.
-constexpr int kLStages = 4;
+constexpr int kLStages = 5;
 constexpr uint32_t kLStageBytes = 2 * 16384 + 8192;
 constexpr size_t kLSmem = 1024 + (size_t)kLStages * kLStageBytes + (size_t)128 * 28 * sizeof(int);
 
@@ -902,10 +902,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tc_list_kernel(
                 }
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
-            // announce the rows of step gs - (kLStages - 2) - ... : at most kLStages - 2
-            // groups stay in flight
-            if (gs - pend_step >= kLStages - 2) {
-                asm volatile("cp.async.wait_group %0;\n" ::"n"(kLStages - 2) : "memory");
+            // announce the rows of step gs - (kLStages - 1): at most kLStages - 1 groups
+            // stay in flight (the stage of step gs + 1 waits for the MMA of step
+            // gs + 1 - kLStages, announced here)
+            if (gs - pend_step >= kLStages - 1) {
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(kLStages - 1) : "memory");
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[pend_step % kLStages]);
