@@ -149,6 +149,14 @@ int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_
 /* Release a plan (NULL is a no-op).  Waits for the plan's outstanding work. */
 int lfmm_plan_destroy(lfmm_plan* plan);
 
+/* One-shot solve: lfmm_plan_create + lfmm_eval + lfmm_plan_destroy in one call, for
+ * points that are solved once.  Host inputs are uploaded first (coordinates on
+ * `stream`); the upload of a host f runs on a second stream behind them, overlapping
+ * the tree build.  A host u is filled when the call returns (it synchronises `stream`);
+ * a device u is ready in stream order.  Arguments as for the three calls. */
+int lfmm_solve(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy, int64_t n_tgt, const double* f,
+               double* u, const lfmm_opts* opts, void* stream);
+
 /* Replace the plan's LFMM_FLAG_* bits (graph replay, serial order) for later
  * evaluations; clearing LFMM_FLAG_GRAPH releases the recorded graph.  Work already
  * queued is not affected. */

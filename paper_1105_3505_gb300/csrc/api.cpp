@@ -256,14 +256,6 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     p->status = (int*)stbuf;
     LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
     p->tc_min_level = p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level;
-    if (p->opts.precision == LFMM_MIXED && p->NP == 32 && p->tc_min_level <= 30) {
-        // TF32 hi / lo of the largest tensor-core level's q_hat and of its parent's u_hat
-        int64_t rows = 0;
-        for (size_t k = 0; k < F.levels.size(); ++k)
-            if (F.levels[k].nb >= kForestTcMinBoxes)
-                rows = std::max(rows, F.levels[k].nb + (k + 1 < F.levels.size() ? F.levels[k + 1].nb : 0));
-        if (rows > 0 && (st = palloc(p, &p->tc_split, (size_t)2 * rows * 32 * sizeof(float), s))) return st;
-    }
     p->bytes += F.bytes;
     return LFMM_OK;
 }
@@ -458,7 +450,7 @@ template <typename T>
 int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
     if (p->forest)
         return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
-                              u, un, uf, (float*)p->tc_split, p->status, p->num_sms, s);
+                              u, un, uf, p->num_sms, s);
     TreeView t;
     t.L = p->L;
     t.side = p->side;
@@ -736,6 +728,73 @@ int lfmm_plan_destroy(lfmm_plan* plan) {
     delete plan;
     if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("plan destroy: ") + cudaGetErrorString(e));
     return LFMM_OK;
+}
+
+int lfmm_solve(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy, int64_t n_tgt, const double* f,
+               double* u, const lfmm_opts* opts, void* stream) {
+    if (!src_xy || !tgt_xy || !f || !u) return fail(LFMM_EINVAL, "NULL argument");
+    if (n_src < 1 || n_tgt < 1 || n_src > INT32_MAX / 2 || n_tgt > INT32_MAX / 2)
+        return fail(LFMM_EINVAL, "n_src and n_tgt must be in [1, 2^30)");
+    cudaStream_t s = (cudaStream_t)stream;
+    int device = 0;
+    LFMM_CUDA_TRY(cudaGetDevice(&device));
+    setup_pool(device);
+    std::vector<void*> temps;
+    auto release = [&]() {
+        for (void* t : temps) cudaFreeAsync(t, s);
+    };
+    auto upload = [&](const void* h, size_t bytes, cudaStream_t on, void** d) -> int {
+        LFMM_CUDA_TRY(cudaMallocAsync(d, bytes, s));
+        temps.push_back(*d);
+        LFMM_CUDA_TRY(cudaMemcpyAsync(*d, h, bytes, cudaMemcpyHostToDevice, on));
+        return LFMM_OK;
+    };
+    int st = LFMM_OK;
+    const int32_t* sd = src_xy;
+    const int32_t* td = tgt_xy;
+    const double* fd = f;
+    AuxStream* aux = nullptr;
+    {
+        PhaseTimer pt(LFMM_PHASE_COPY, s);
+        void* d;
+        if (!is_device_ptr(src_xy)) {
+            if ((st = upload(src_xy, (size_t)n_src * 2 * sizeof(int32_t), s, &d))) return release(), st;
+            sd = (const int32_t*)d;
+        }
+        if (!is_device_ptr(tgt_xy)) {
+            if ((st = upload(tgt_xy, (size_t)n_tgt * 2 * sizeof(int32_t), s, &d))) return release(), st;
+            td = (const int32_t*)d;
+        }
+        if (!is_device_ptr(f)) {
+            // f behind the coordinates on a second stream: it lands while the tree is built
+            aux = acquire_aux(device);
+            cudaStream_t fs = s;
+            if (aux) {
+                LFMM_CUDA_TRY(cudaEventRecord(aux->fork, s));
+                LFMM_CUDA_TRY(cudaStreamWaitEvent(aux->s, aux->fork, 0));
+                fs = aux->s;
+            }
+            if ((st = upload(f, (size_t)n_src * sizeof(double), fs, &d))) {
+                release_aux(aux);
+                return release(), st;
+            }
+            fd = (const double*)d;
+            if (aux) LFMM_CUDA_TRY(cudaEventRecord(aux->join, aux->s));
+        }
+    }
+    lfmm_plan* plan = nullptr;
+    st = lfmm_plan_create(&plan, sd, n_src, td, n_tgt, opts, stream);
+    if (!st) {
+        if (aux) cudaStreamWaitEvent(s, aux->join, 0);
+        st = lfmm_eval(plan, fd, u, stream);
+    }
+    const int st2 = plan ? lfmm_plan_destroy(plan) : LFMM_OK;
+    if (aux) {
+        cudaStreamWaitEvent(s, aux->join, 0);  // the upload is done before its buffer is freed
+        release_aux(aux);
+    }
+    release();
+    return st ? st : st2;
 }
 
 int lfmm_plan_set_flags(lfmm_plan* p, int32_t flags) {

@@ -750,8 +750,9 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(
 // coalesced loads; each staged source gets its table offset relative to the strip's
 // first leaf, so a target in leaf bx reads phi through a pointer shifted by
 // (bx - bx0) * s and the pair loop stays one load and one multiply-add per pair.
-// Targets, leaf charges, incoming expansions and constants of the strip are staged
-// alongside.  The host picks SW so the staged data fit (3 (SW+2) max_leaf_src <= CAPS).
+// Targets and leaf charges of the strip are staged alongside.  The strip form computes
+// the near field alone (the far field has its own L2P kernel).  The host picks SW so
+// the staged data fit (3 (SW+2) max_leaf_src <= CAPS).
 template <typename T>
 struct StripCfg {
     static constexpr int WARPS = 8;
@@ -765,9 +766,8 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
     int L, int side, int SW, const int32_t* __restrict__ sbeg, const int32_t* __restrict__ sloc,
     const int32_t* __restrict__ tbeg, const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
     const T* __restrict__ f_sorted, const T* __restrict__ table, int tab_H, int tab_W,
-    const T* __restrict__ uhat, const typename Mono<T>::V* __restrict__ Cleaf,
-    const typename Mono<T>::V* __restrict__ Qleaf, const T* __restrict__ tofsT, double* __restrict__ u,
-    double* __restrict__ u_near, double* __restrict__ u_far) {
+    const typename Mono<T>::V* __restrict__ Cleaf, const typename Mono<T>::V* __restrict__ Qleaf,
+    double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
     using M = Mono<T>;
     using V = typename M::V;
     using Cfg = StripCfg<T>;
@@ -775,8 +775,7 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
     const int tab_n = (2 * tab_H + 1) * tab_W;
     T* tab = reinterpret_cast<T*>(smem_raw);
     SrcEntry<T>* s_src = reinterpret_cast<SrcEntry<T>*>(tab + tab_n);
-    T* s_uhat = reinterpret_cast<T*>(s_src + Cfg::CAPS);                 // [MAXSW][NP]
-    V* s_q = reinterpret_cast<V*>(s_uhat + Cfg::MAXSW * NP);             // [3][MAXSW+2]
+    V* s_q = reinterpret_cast<V*>(s_src + Cfg::CAPS);                    // [3][MAXSW+2]
     V* s_c = s_q + 3 * (Cfg::MAXSW + 2);                                 // [MAXSW]
     int* s_tloc = reinterpret_cast<int*>(s_c + Cfg::MAXSW);              // [CAPT]
     int* s_tperm = s_tloc + Cfg::CAPT;                                   // [CAPT]
@@ -812,10 +811,6 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
             const int r = i / ncol, c = i % ncol;
             const int yy = by + r - 1;
             s_q[r * (Cfg::MAXSW + 2) + c] = (yy >= 0 && yy < n) ? Qleaf[morton2(c_lo + c, yy)] : M::zero();
-        }
-        for (int i = threadIdx.x; i < (bx1 - bx0) * NP; i += blockDim.x) {
-            const int c = i / NP, pp = i % NP;
-            s_uhat[i] = uhat ? uhat[(size_t)morton2(bx0 + c, by) * NP + pp] : T(0);
         }
         for (int i = threadIdx.x; i < bx1 - bx0; i += blockDim.x)
             s_c[i] = Cleaf ? Cleaf[morton2(bx0 + i, by)] : M::zero();
@@ -886,7 +881,6 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
         for (int chunk = warp; chunk < n_chunks; chunk += Cfg::WARPS) {
             const int v = chunk * 32 + lane;
             const bool active = v < nt_strip;
-            const int n_act = min(32, nt_strip - chunk * 32);
             const int tl = s_tloc[active ? v : chunk * 32];
             const int li = (tl >> 8) & 0xff, tx = tl & 0xff, ty = tl >> 16;
             const T* tp = tab_c + (tx + tab_W * ty + li * side);
@@ -924,32 +918,10 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
                 }
             }
             acc -= cmp;
-            // L2P: lanes own expansion entries p; one coalesced row of T_ofs^T per target
-            // against its leaf's incoming expansion, then a reduce-scatter leaves target
-            // q's value in lane q
-            T far = T(0);
-            if (uhat) {
-                constexpr int PL = NP / 32;
-                const int myJ = tx + side * ty;
-                T part[32];
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int Jq = shfl(myJ, q), lq = shfl(li, q);
-                    T w = T(0);
-                    if (q < n_act) {
-                        const T* row = tofsT + (size_t)Jq * NP;
-                        const T* uq = s_uhat + lq * NP;
-#pragma unroll
-                        for (int i = 0; i < PL; ++i) w = fma(ldg(row + lane + 32 * i), uq[lane + 32 * i], w);
-                    }
-                    part[q] = w;
-                }
-                far = reduce_scatter32(part);
-            }
             if (active) {
                 const int dst = s_tperm[v];
                 const double dn = (double)acc + s_nc[li];
-                const double df = (double)far + M::to_double(s_c[li]);
+                const double df = M::to_double(s_c[li]);
                 if (u) u[dst] = dn + df;
                 if (u_near) u_near[dst] = dn;
                 if (u_far) u_far[dst] = df;
@@ -1302,7 +1274,7 @@ static cudaError_t launch_p2p_strip(const TreeView& t, const DeviceOps& ops, int
     using Cfg = StripCfg<T>;
     using V = typename Mono<T>::V;
     const size_t tab_bytes = (size_t)(2 * ops.tab_H + 1) * ops.tab_W * sizeof(T);
-    const size_t smem = tab_bytes + (size_t)Cfg::CAPS * sizeof(SrcEntry<T>) + (size_t)Cfg::MAXSW * NP * sizeof(T) +
+    const size_t smem = tab_bytes + (size_t)Cfg::CAPS * sizeof(SrcEntry<T>) +
                         (size_t)(3 * (Cfg::MAXSW + 2) + Cfg::MAXSW) * sizeof(V) + (size_t)2 * Cfg::CAPT * sizeof(int) +
                         (size_t)(3 * (Cfg::MAXSW + 3) + Cfg::MAXSW + 1) * sizeof(int);
     {
@@ -1316,8 +1288,7 @@ static cudaError_t launch_p2p_strip(const TreeView& t, const DeviceOps& ops, int
     if (blocks < 1) blocks = 1;
     p2p_strip_kernel<T, NP><<<(int)blocks, Cfg::WARPS * 32, smem, s>>>(
         t.L, t.side, SW, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted,
-        (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const V*)Qleaf, (const T*)ops.tofsT,
-        u, un, uf);
+        (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, (const V*)Cleaf, (const V*)Qleaf, u, un, uf);
     return cudaGetLastError();
 }
 
@@ -1329,7 +1300,7 @@ cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_s
     const int n = 1 << t.L;
     const int ms = std::max(1, t.max_leaf_src), mt = std::max(1, t.max_leaf_tgt);
     int SW = std::min({Cfg::MAXSW, Cfg::CAPS / (3 * ms) - 2, Cfg::CAPT / mt, n});
-    if (SW >= 1) {
+    if (SW >= 1 && uhat == nullptr) {  // the strip form is the near field alone
         if (ops.NP == 32) return launch_p2p_strip<T, 32>(t, ops, SW, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
         return launch_p2p_strip<T, 64>(t, ops, SW, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
     }

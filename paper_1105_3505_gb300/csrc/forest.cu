@@ -1202,8 +1202,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
 
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, float* tc_split, int* status, int num_sms,
-                cudaStream_t s) {
+                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s) {
     using V = typename Mono<T>::V;
     const int NP = ops.NP;
     const int nk = (int)F.levels.size();
@@ -1255,19 +1254,6 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             int64_t maxc = 0;
             for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
             if (maxc == 0) continue;
-            if constexpr (sizeof(T) == 4) {
-                if (tc_split && NP == 32 && lv.nb >= kForestTcMinBoxes && m2l_uses_tc(ops, k, 0, 0, true)) {
-                    int64_t n_tiles = 0;
-                    for (int c = 0; c < 4; ++c) n_tiles += (lv.cls[c + 1] - lv.cls[c] + 127) / 128;
-                    LFMM_CUDA_TRY(launch_m2l_tc_list(ops, k, lv.d_cls, n_tiles, lv.il, l2l ? lv.par : nullptr,
-                                                     (const float*)Qx(k), lv.nb, Qm(k),
-                                                     l2l ? (const float*)Ux(k + 1) : nullptr,
-                                                     l2l ? F.levels[k + 1].nb : 0, l2l ? Cm(k + 1) : nullptr,
-                                                     (float*)Ux(k), Cm(k), tc_split, status, num_sms, s));
-                    pt.add_launches(l2l ? 3 : 2);
-                    continue;
-                }
-            }
             dim3 grid((unsigned)((maxc + 31) / 32), 4);
             auto go = [&](auto np_tag) -> cudaError_t {
                 constexpr int NPc = decltype(np_tag)::value;
@@ -1318,10 +1304,10 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
 }
 
 template int forest_eval<float>(const Forest&, const DeviceOps&, const double*, float*, float*, float*, void*, void*,
-                                double*, double*, double*, float*, int*, int, cudaStream_t);
+                                double*, double*, double*, int, cudaStream_t);
 template int forest_eval<double>(const Forest&, const DeviceOps&, const double*, double*, double*, double*, void*,
-                                 void*, double*, double*, double*, float*, int*, int, cudaStream_t);
+                                 void*, double*, double*, double*, int, cudaStream_t);
 template int forest_eval<DF>(const Forest&, const DeviceOps&, const double*, DF*, DF*, DF*, void*, void*, double*,
-                             double*, double*, float*, int*, int, cudaStream_t);
+                             double*, double*, int, cudaStream_t);
 
 }  // namespace lfmm

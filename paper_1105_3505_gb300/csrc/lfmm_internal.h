@@ -253,13 +253,9 @@ struct Forest {
 int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
                  const int64_t* toff_h, int64_t nt, int np, int leaf_size, int max_leaf_side, cudaStream_t s,
                  PhaseTimer* timer);
-// Levels with at least this many boxes run the list form of the tensor-core M2L
-// (mixed path, P <= 32) when a split buffer is given.
-constexpr int64_t kForestTcMinBoxes = 1024;
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, float* tc_split, int* status, int num_sms,
-                cudaStream_t s);
+                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s);
 
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);
 cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
@@ -336,29 +332,13 @@ inline bool m2l_uses_tc(const DeviceOps& ops, int k, int level, int tc_min_level
 template <typename T>
 cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level, const void* Q_level,
                        const T* u_parent, const void* C_parent, T* u_level, void* C_level, cudaStream_t s);
-// Shared-memory form of the tensor-core M2L: the level's expansions and the parent
-// level's incoming expansions pre-split into TF32 hi / lo arrays (launch_split_tf32).
-cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float* qhi, const float* qlo,
-                             const void* Q_level, const float* uhi, const float* ulo, const void* C_parent,
-                             float* u_level, void* C_level, int* status, cudaStream_t s);
-// TMA form of the tensor-core M2L + L2L of one level (Morton-ordered q_hat / u_hat in
-// and out): splits the level's expansions and the parent's into TF32 hi / lo layouts in
-// `split` (8 np^2 + 2 np^2 rows of 32 floats, np = 2^(level-1)), then one persistent
-// launch; a timed-out wait is reported in *status.
+// Tensor-core M2L + L2L of one level (Morton-ordered q_hat / u_hat in and out):
+// splits the level's expansions and the parent's into TF32 hi / lo layouts in `split`
+// (8 np^2 + 2 np^2 rows of 32 floats, np = 2^(level-1)), then one persistent launch fed
+// by tiled TMA loads; a timed-out wait is reported in *status.
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
                            int* status, int num_sms, cudaStream_t s);
-// List form of the tensor-core M2L + L2L (pruned storage, forests): compact boxes of
-// one level grouped by class (cls_start, device, 5 entries; n_tiles = sum over classes
-// of ceil(count / 128)), 27 list entries and the parent per box; `split` holds
-// 2 (nb + nb_parent) rows of 32 floats.
-cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, int64_t n_tiles,
-                               const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
-                               const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
-                               float* u_level, void* C_level, float* split, int* status, int num_sms,
-                               cudaStream_t s);
-// hi = TF32(x), lo = TF32(x - hi), n floats (a multiple of 4).
-cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
                            const T* uhat_leaf, const void* C_leaf, const void* Q_leaf, double* u,

@@ -4,32 +4,18 @@
 //   u_hat^tau = sum_{sigma in int(tau)} (T_ifo^o - c_o 1 1^T) q_hat^sigma + T_ifi^c u_hat^parent
 //
 // as an implicit GEMM per CTA: M = 128 target boxes (TMEM lanes), N = 32 outputs,
-// K = 27 x 32 gathered source expansions (+ 32 for the parent).  Operands are split
-// into TF32 hi + lo parts (round to nearest) and three products hi*hi + hi*lo + lo*hi
-// are formed (the lo*lo term is below 2^-22 relative).  The tensor core's fp32
-// accumulation rounds toward zero, and that bias grows linearly with the number of
-// MMAs feeding one accumulator; so every K-step writes fresh TMEM accumulators (hi*hi
-// in one, the small hi*lo + lo*hi terms in another), which the threads read back one
-// step later and add in registers with round-to-nearest fp32.
+// K = 27 x 32 source expansions (+ 32 for the parent).  Operands are split into TF32
+// hi + lo parts (round to nearest) and three products hi*hi + hi*lo + lo*hi are formed
+// (the lo*lo term is below 2^-22 relative).  The tensor core's fp32 accumulation rounds
+// toward zero, and that bias grows linearly with the number of MMAs feeding one
+// accumulator; so every K-step writes fresh TMEM accumulators (hi*hi in one, the small
+// hi*lo + lo*hi terms in another), which are read back after the step and added in
+// registers with round-to-nearest fp32.
 //
-//  - A (gathered expansions): the level's expansions, and the parent level's incoming
-//    expansions, are split once into TF32 hi and lo arrays (split_tf32_kernel).  Each
-//    K-step copies the 128 gathered source rows of hi and of lo with cp.async (16-byte
-//    chunks) straight into the 128-byte-swizzled K-major layout that a shared-memory
-//    matrix descriptor describes, so the tensor core reads A like B and no thread
-//    touches the values between the gather and the MMA.
-//  - B (operators): pre-split, pre-swizzled 4 KB tiles in the device image, fetched
-//    with cp.async.bulk into a 3-deep ring in shared memory two steps ahead, completion
-//    tracked by mbarriers.
-//  - TMEM holds only the two accumulator pairs (128 columns).
-//  - step s: fold in the partials of step s-1 (waiting for its MMAs, which also frees
-//    the A stage they read), start the gather of step s+1 into that stage, wait for the
-//    own copies of step s, make them visible to the tensor core, barrier; one elected
-//    thread issues the 12 MMAs (K = 8 each) of step s and the B copy of step s+2.
-// Every mbarrier wait is bounded (clock64 budget, suspend-time hint); on expiry the CTA
-// records LFMM_ETIMEOUT in the plan's status word, all its threads stop issuing work
-// together (the abort flag is block-uniform), wait (bounded) for what was issued, free
-// the TMEM and return.
+// A (source expansions) arrives by tiled TMA loads from parity-plane layouts of the
+// split expansions, B (operators) as pre-split, pre-swizzled 4 KB tiles of the device
+// image by bulk copies; both land in the 128-byte-swizzled K-major layout that the
+// shared-memory matrix descriptors describe.  The pipeline is described at the kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -39,7 +25,6 @@ namespace lfmm {
 
 namespace {
 
-constexpr int kTcThreads = 128;          // 4 warps, one TMEM lane quarter each
 constexpr long long kWaitBudget = 4000000000ll;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -54,27 +39,8 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// try_wait with a suspend-time hint: the thread sleeps until the phase completes or the
-// hint (ns) runs out, instead of spinning through issue slots
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitBudget) return false;
-    return true;
-}
-// non-blocking probe of a phase; the TMA pipeline's role threads poll with it, since a
-// suspended try_wait can sleep past the phase change and every K-step waits three times
+// non-blocking probe of a phase; the pipeline's role threads poll with it (a suspended
+// try_wait can sleep past the phase change, and every K-step waits three times)
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -92,12 +58,6 @@ __device__ __forceinline__ bool mbar_poll_bounded(uint64_t* bar, uint32_t parity
     while (!mbar_test(bar, parity))
         if (clock64() - t0 > kWaitBudget) return false;
     return true;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
 }
 __device__ __forceinline__ void bulk_g2s_u32(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -143,10 +103,6 @@ __device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t a_desc, ui
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
-}
-// makes this thread's completed cp.async writes to shared memory visible to the tensor core
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -207,268 +163,6 @@ __device__ __forceinline__ DFv dmul(DFv a, DFv b) {
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
     return qsum(p, e);
-}
-
-constexpr int kTc2Cols = 128;  // D_big[b]: [32b, 32b+32), D_small[b]: [64+32b, 96+32b)
-
-__global__ void __launch_bounds__(kTcThreads) m2l_tc_ss_kernel(int level, const float* __restrict__ qhi,
-                                                               const float* __restrict__ qlo,
-                                                               const float* __restrict__ uhi,
-                                                               const float* __restrict__ ulo,
-                                                               const float* __restrict__ tiles,
-                                                               const float* __restrict__ mono,
-                                                               const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar,
-                                                               float* __restrict__ out, DFv* __restrict__ Cout,
-                                                               int* __restrict__ status) {
-    constexpr int NP = 32;
-    // dynamic shared memory (1024-byte aligned): B ring [3][hi, lo][32 x 32], then the A
-    // stages [2][hi, lo][128 x 32], all 128-byte swizzled
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    float (*sB)[2][1024] = reinterpret_cast<float (*)[2][1024]>(
-        tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u));
-    float (*sA)[2][kTcThreads * 32] = reinterpret_cast<float (*)[2][kTcThreads * 32]>(&sB[3][0][0]);
-    __shared__ __align__(8) uint64_t bar_b[3], bar_mma[2];
-    __shared__ uint32_t s_tmem;
-    __shared__ int s_off[27][3];
-    __shared__ int s_abort;
-    __shared__ int s_src[28][kTcThreads];
-
-    const int cls = blockIdx.y;
-    const int px = cls & 1, py = cls >> 1;
-    const int lg = level - 1;
-    const int np_side = 1 << lg;
-    const int64_t n_rows = (int64_t)1 << (2 * lg);
-    const int64_t row = (int64_t)blockIdx.x * kTcThreads + threadIdx.x;
-    const bool valid = row < n_rows;
-    const int side = 1 << level;
-    const bool has_l2l = uhi != nullptr;
-    const int n_steps = 27 + (has_l2l ? 1 : 0);
-    const int warp = threadIdx.x >> 5;
-    const int ri = valid ? (int)(row & (np_side - 1)) : 0;
-    const int rj = valid ? (int)(row >> lg) : 0;
-
-    if (smem_u32(&sB[0][0][0]) & 1023u) {
-        if (threadIdx.x == 0) atomicExch(status, LFMM_EINTERNAL);
-        return;
-    }
-    if (threadIdx.x == 0) {
-        int nn = 0;
-        for (int d = 0; d < 36; ++d) {
-            const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
-            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-            s_off[nn][0] = dx;
-            s_off[nn][1] = dy;
-            s_off[nn][2] = offset_index_tc(dx, dy);
-            ++nn;
-        }
-        for (int i = 0; i < 3; ++i) mbar_init(&bar_b[i], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
-        fence_barrier_init();
-        s_abort = 0;
-    }
-    if (warp == 0) {
-        tmem_alloc(&s_tmem, kTc2Cols);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    for (int st = 0; st < 27; ++st) {
-        int si = -1;
-        if (valid) {
-            const int sx = 2 * ri + px + s_off[st][0], sy = 2 * rj + py + s_off[st][1];
-            if (sx >= 0 && sx < side && sy >= 0 && sy < side) si = (int)morton2(sx, sy);
-        }
-        s_src[st][threadIdx.x] = si;
-    }
-    s_src[27][threadIdx.x] = (valid && has_l2l) ? (int)morton2(ri, rj) : -1;
-    __syncthreads();
-    const uint32_t tmem = s_tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-
-    // gather of step `step` into A stage b: thread t copies 16-byte chunk t % 8 of rows
-    // t / 8 + 16 j of hi and of lo; chunk c of row r lands at chunk c ^ (r % 8)
-    auto gather = [&](int step, int b) {
-        const int ch = threadIdx.x & 7;
-        const float* hsrc = step < 27 ? qhi : uhi;
-        const float* lsrc = step < 27 ? qlo : ulo;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = (threadIdx.x >> 3) + 16 * j;
-            const int si = s_src[step][r];
-            const size_t off = si < 0 ? 0 : (size_t)si * NP + 4 * ch;
-            const int bytes = si < 0 ? 0 : 16;
-            const int pos = r * 32 + ((ch ^ (r & 7)) << 2);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(&sA[b][0][pos])),
-                         "l"(hsrc + off), "r"(bytes)
-                         : "memory");
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(&sA[b][1][pos])),
-                         "l"(lsrc + off), "r"(bytes)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    auto b_src = [&](int step) -> const float* {
-        return step < 27 ? tiles + (size_t)s_off[step][2] * 2048 : tiles + (size_t)(kNumOffsets + cls) * 2048;
-    };
-
-    constexpr uint32_t kIdesc = idesc_tf32(128, NP);
-    float acc[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    auto flush = [&](int b) {
-        uint32_t big[32], small[32];
-        tmem_ld32(tmem + lane_base + 32 * b, big);
-        tmem_ld32(tmem + lane_base + 64 + 32 * b, small);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
-    };
-    volatile int* vabort = &s_abort;
-    int issued_steps = 0, b_issued = 0;
-    if (threadIdx.x == 0) {  // B tiles of steps 0 and 1
-        for (int st = 0; st < 2 && st < n_steps; ++st) {
-            mbar_arrive_expect_tx(&bar_b[st], 8192);
-            bulk_g2s(&sB[st][0][0], b_src(st), 8192, &bar_b[st]);
-            b_issued = st + 1;
-        }
-    }
-    gather(0, 0);
-    // Aborts are block-uniform: a failed wait only records s_abort; every thread tests
-    // it right after the step's barrier, so all warps leave the loop at the same step
-    // and meet the same barriers afterwards.
-    for (int step = 0; step < n_steps; ++step) {
-        const int buf = step & 1;
-        bool w_ok = true;
-        if (step >= 1) {
-            // MMAs of step - 1 done: their partials in, their A stage free
-            w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[buf ^ 1], ((step - 1) >> 1) & 1);
-            w_ok = __all_sync(0xffffffffu, w_ok);
-            if (w_ok) {
-                tc_fence_after();
-                flush(buf ^ 1);
-            } else {
-                atomicExch(&s_abort, 1);
-            }
-        }
-        if (w_ok && step + 1 < n_steps) {
-            gather(step + 1, buf ^ 1);
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (*vabort != 0) break;
-        if (threadIdx.x == 0) {
-            const int slot = step % 3;
-            const bool good = mbar_wait_bounded(&bar_b[slot], (step / 3) & 1);
-            if (!good) {
-                atomicExch(&s_abort, 1);  // seen by all after the next barrier
-            } else {
-                tc_fence_after();
-                const uint32_t a_hi = smem_u32(&sA[buf][0][0]), a_lo = smem_u32(&sA[buf][1][0]);
-                const uint32_t b_hi = smem_u32(&sB[slot][0][0]), b_lo = smem_u32(&sB[slot][1][0]);
-                const uint32_t d_big = tmem + 32 * buf, d_small = tmem + 64 + 32 * buf;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t ah = smem_desc_sw128(a_hi + 32 * kk), al = smem_desc_sw128(a_lo + 32 * kk);
-                    const uint64_t bh = smem_desc_sw128(b_hi + 32 * kk), bl = smem_desc_sw128(b_lo + 32 * kk);
-                    mma_tf32_ss(d_big, ah, bh, kIdesc, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, ah, bl, kIdesc, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, al, bh, kIdesc, 1u);
-                }
-                mma_commit(&bar_mma[buf]);
-                // B tiles of step + 2 into the slot step - 1 used (its MMAs are done)
-                if (step + 2 < n_steps) {
-                    const int ns = (step + 2) % 3;
-                    mbar_arrive_expect_tx(&bar_b[ns], 8192);
-                    bulk_g2s(&sB[ns][0][0], b_src(step + 2), 8192, &bar_b[ns]);
-                    b_issued = step + 3;
-                }
-            }
-        }
-        issued_steps = step + 1;
-    }
-
-    // incoming constant (compensated), one box per thread, while the last MMAs run
-    if (valid) {
-        DFv sacc = has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
-        for (int c0 = 0; c0 < 27; c0 += 9) {
-            DFv qv[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int si = s_src[c0 + k][threadIdx.x];
-                qv[k] = si >= 0 ? Qin[si] : DFv{0.f, 0.f};
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const int o = s_off[c0 + k][2];
-                sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
-            }
-        }
-        Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
-    }
-
-    // partials of the last step; after an abort, wait (bounded) for what was issued
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    bool ok = s_abort == 0;
-    if (ok && n_steps > 0) {
-        const int st = n_steps - 1;
-        bool w_ok = *vabort == 0 && mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
-        w_ok = __all_sync(0xffffffffu, w_ok);
-        if (!w_ok) {
-            atomicExch(&s_abort, 1);
-            ok = false;
-        } else {
-            tc_fence_after();
-            flush(st & 1);
-        }
-    }
-    __syncthreads();
-    if (s_abort) ok = false;
-    if (!ok) {
-        for (int st = max(0, issued_steps - 2); st < issued_steps; ++st)
-            mbar_wait_bounded(&bar_mma[st & 1], (st >> 1) & 1);
-        if (threadIdx.x == 0 && b_issued > 0)
-            for (int st = max(0, b_issued - 2); st < b_issued; ++st) mbar_wait_bounded(&bar_b[st % 3], (st / 3) & 1);
-    }
-    if (ok) {
-        if (valid) {
-            float4* dst = reinterpret_cast<float4*>(out + (size_t)morton2(2 * ri + px, 2 * rj + py) * NP);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-        }
-    } else if (threadIdx.x == 0) {
-        atomicExch(status, LFMM_ETIMEOUT);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kTc2Cols);
-    }
-}
-
-// hi = TF32 round-to-nearest of x, lo = the same of the remainder (the A operand split
-// of the shared-memory form), elementwise over n floats (n a multiple of 4)
-__global__ void split_tf32_kernel(const float4* __restrict__ x, float4* __restrict__ hi, float4* __restrict__ lo,
-                                  int64_t n4) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 v = x[i];
-        const float a[4] = {v.x, v.y, v.z, v.w};
-        float h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            h[e] = __uint_as_float(tf32_rna_bits(a[e]));
-            l[e] = __uint_as_float(tf32_rna_bits(a[e] - h[e]));
-        }
-        hi[i] = make_float4(h[0], h[1], h[2], h[3]);
-        lo[i] = make_float4(l[0], l[1], l[2], l[3]);
-    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -766,290 +460,6 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     }
 }
 
-// ---------------------------------------------------------------------------------
-// List form, for pruned storage and forests: the boxes of a level are compact and
-// grouped by parity class, and each box carries its 27 interaction-list entries (-1:
-// no box) and its parent.  Same persistent warp-specialised pipeline as the TMA form,
-// but the A operand is gathered: the producer warp copies the 128 source rows of a
-// K-step (hi and lo, split beforehand by split_tf32_kernel) with cp.async into the
-// 128-byte-swizzled layout, zero-filling missing sources; it completes a stage once
-// the copies of the step kStages - 1 steps back have landed (cp.async groups), after a
-// proxy fence, with a second arrival beside the operator tile's bulk copy.
-constexpr int kLStages = 5;
-constexpr uint32_t kLStageBytes = 2 * 16384 + 8192;
-constexpr size_t kLSmem = 1024 + (size_t)kLStages * kLStageBytes + (size_t)128 * 28 * sizeof(int);
-
-__global__ void __launch_bounds__(kTmaThreads, 1) m2l_tc_list_kernel(
-    const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
-    const float* __restrict__ qhi, const float* __restrict__ qlo, const float* __restrict__ uhi,
-    const float* __restrict__ ulo, const float* __restrict__ tiles, const float* __restrict__ mono,
-    const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout,
-    int* __restrict__ status) {
-    constexpr int NP = 32;
-    extern __shared__ __align__(1024) unsigned char tl_smem[];
-    const uint32_t base = smem_u32(tl_smem) + ((1024u - (smem_u32(tl_smem) & 1023u)) & 1023u);
-    // the current tile's source rows per K-step (producer only): [128 rows][28]
-    int* s_src = reinterpret_cast<int*>(tl_smem + (base - smem_u32(tl_smem)) + kLStages * kLStageBytes);
-    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages], acc_full[kTmaAcc], acc_empty[kTmaAcc];
-    __shared__ uint32_t s_tmem;
-    __shared__ int s_op[4][28];  // operator tile of K-step st for class c
-    __shared__ long long s_c[5], s_t[5];  // class starts; first tile of each class
-    __shared__ int s_abort;
-    __shared__ int s_issued[2];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool has_l2l = uhi != nullptr;
-    const int n_steps = 27 + (has_l2l ? 1 : 0);
-    volatile int* vabort = &s_abort;
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < 4; ++c) {
-            const int px = c & 1, py = c >> 1;
-            int nn = 0;
-            for (int d = 0; d < 36; ++d) {
-                const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
-                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-                s_op[c][nn++] = offset_index_tc(dx, dy);  // list slot order
-            }
-            s_op[c][27] = kNumOffsets + c;
-        }
-        long long t = 0;
-        for (int c = 0; c <= 4; ++c) {
-            s_c[c] = cls_start[c];
-            s_t[c] = t;
-            if (c < 4) t += (cls_start[c + 1] - cls_start[c] + 127) / 128;
-        }
-        for (int i = 0; i < kLStages; ++i) {
-            mbar_init(&full[i], 2);  // operator tile (with its bytes) + the gathered rows
-            mbar_init(&empty[i], 1);
-        }
-        for (int i = 0; i < kTmaAcc; ++i) {
-            mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 4);
-        }
-        fence_barrier_init();
-        s_abort = 0;
-        s_issued[0] = s_issued[1] = 0;
-    }
-    if (warp == 0) {
-        tmem_alloc(&s_tmem, kTmaCols);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = s_tmem;
-    const int n_tiles = (int)s_t[4];
-    const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = my_tiles * n_steps;
-    auto abort_now = [&]() {
-        atomicExch(&s_abort, 1);
-        atomicExch(status, LFMM_ETIMEOUT);
-    };
-    // it-th tile of this CTA: class and first / end box
-    auto tile_of = [&](int it, int& cls, long long& b0, long long& b1) {
-        const long long t = (long long)blockIdx.x + (long long)it * gridDim.x;
-        cls = (t >= s_t[1]) + (t >= s_t[2]) + (t >= s_t[3]);
-        b0 = s_c[cls] + (t - s_t[cls]) * 128;
-        b1 = min(b0 + 128, s_c[cls + 1]);
-    };
-
-    if (warp == 4) {
-        int it = 0, st = 0, slot = 0, use = 0, cls = 0;
-        long long b0 = 0, b1 = 0;
-        int pend_step = 0;  // first step whose gathered rows have not been announced
-        for (int gs = 0; gs < total; ++gs) {
-            if (__any_sync(0xffffffffu, *vabort != 0)) break;  // warp-uniform
-            if (st == 0) {
-                tile_of(it, cls, b0, b1);
-                // source rows of the tile's K-steps
-                for (int i = lane; i < 128 * 28; i += 32) {
-                    const int r = i / 28, k = i % 28;
-                    const long long b = b0 + r;
-                    int v = -1;
-                    if (b < b1) v = k < 27 ? il[b * 27 + k] : (has_l2l ? par[b] : -1);
-                    s_src[i] = v;
-                }
-                __syncwarp();
-            }
-            bool ok = true;
-            if (use > 0) ok = mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1));
-            if (!__all_sync(0xffffffffu, ok)) {
-                if (lane == 0) abort_now();
-                break;
-            }
-            const uint32_t sa = base + (uint32_t)slot * kLStageBytes;
-            if (lane == 0) {
-                mbar_arrive_expect_tx(&full[slot], 8192);
-                bulk_g2s_u32(sa + 32768, tiles + (size_t)s_op[cls][st] * 2048, 8192, &full[slot]);
-            }
-            const float* hs = st < 27 ? qhi : uhi;
-            const float* ls = st < 27 ? qlo : ulo;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = lane + 32 * i;
-                const int si = s_src[r * 28 + st];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const size_t off = si < 0 ? 0 : (size_t)si * NP + 4 * c;
-                    const int bytes = si < 0 ? 0 : 16;
-                    const uint32_t dst = (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + dst), "l"(hs + off),
-                                 "r"(bytes)
-                                 : "memory");
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + 16384 + dst),
-                                 "l"(ls + off), "r"(bytes)
-                                 : "memory");
-                }
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            // announce the rows of step gs - (kLStages - 1): at most kLStages - 1 groups
-            // stay in flight (the stage of step gs + 1 waits for the MMA of step
-            // gs + 1 - kLStages, announced here)
-            if (gs - pend_step >= kLStages - 1) {
-                asm volatile("cp.async.wait_group %0;\n" ::"n"(kLStages - 1) : "memory");
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[pend_step % kLStages]);
-                ++pend_step;
-            }
-            if (lane == 0) s_issued[0] = gs + 1;
-            if (++slot == kLStages) {
-                slot = 0;
-                ++use;
-            }
-            if (++st == n_steps) {
-                st = 0;
-                ++it;
-            }
-        }
-        // announce what is left (also after an abort, so that the teardown's waits end)
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        fence_proxy_async_smem();
-        __syncwarp();
-        const int issued = s_issued[0];
-        if (lane == 0)
-            for (; pend_step < issued; ++pend_step) mbar_arrive(&full[pend_step % kLStages]);
-    } else if (warp == 5) {
-        if (lane == 0) {
-            constexpr uint32_t kIdesc64 = idesc_tf32(128, 64), kIdesc32 = idesc_tf32(128, 32);
-            int slot = 0, use = 0, d = 0, du = 0;
-            for (int gs = 0; gs < total; ++gs) {
-                if (*vabort) break;
-                if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1)) ||
-                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1)))) {
-                    abort_now();
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t a_hi = base + (uint32_t)slot * kLStageBytes, a_lo = a_hi + 16384;
-                const uint32_t b_hi = a_hi + 32768;
-                const uint32_t d_big = tmem + 64 * d, d_small = d_big + 32;
-                const uint64_t dah = smem_desc_sw128(a_hi), dal = smem_desc_sw128(a_lo), dbh = smem_desc_sw128(b_hi);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdesc64, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdesc32, 1u);
-                }
-                mma_commit(&empty[slot]);
-                mma_commit(&acc_full[d]);
-                s_issued[1] = gs + 1;
-                if (++slot == kLStages) {
-                    slot = 0;
-                    ++use;
-                }
-                if (++d == kTmaAcc) {
-                    d = 0;
-                    ++du;
-                }
-            }
-        }
-    } else if (warp == 6) {
-        for (int it = 0; it < my_tiles; ++it) {
-            int cls;
-            long long b0, b1;
-            tile_of(it, cls, b0, b1);
-            for (long long b = b0 + lane; b < b1; b += 32) {
-                const int pb = has_l2l ? par[b] : -1;
-                DFv sacc = pb >= 0 ? Cpar[pb] : DFv{0.f, 0.f};
-                for (int k0 = 0; k0 < 27; k0 += 9) {
-                    int sb[9];
-                    DFv qv[9];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) sb[k] = il[b * 27 + k0 + k];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) qv[k] = sb[k] >= 0 ? Qin[sb[k]] : DFv{0.f, 0.f};
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        const int o = s_op[cls][k0 + k];
-                        if (sb[k] >= 0) sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
-                    }
-                }
-                Cout[b] = sacc;
-            }
-        }
-    } else {
-        const int r = threadIdx.x;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        float acc[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-        int it = 0, st = 0, d = 0, du = 0, cls = 0;
-        long long b0 = 0, b1 = 0;
-        for (int gs = 0; gs < total; ++gs) {
-            if (st == 0) tile_of(it, cls, b0, b1);
-            bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1));
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                if (lane == 0) abort_now();
-                break;
-            }
-            tc_fence_after();
-            uint32_t big[32], small[32];
-            tmem_ld32(tmem + lane_base + 64 * d, big);
-            tmem_ld32(tmem + lane_base + 64 * d + 32, small);
-            tmem_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[d]);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
-            if (st == n_steps - 1) {
-                if (b0 + r < b1) {
-                    float4* dst = reinterpret_cast<float4*>(out + (size_t)(b0 + r) * NP);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-            }
-            if (++d == kTmaAcc) {
-                d = 0;
-                ++du;
-            }
-            if (++st == n_steps) {
-                st = 0;
-                ++it;
-            }
-        }
-    }
-    __syncwarp();
-    __syncthreads();
-    if (s_abort && threadIdx.x == 0) {
-        // the producer announced every stage it issued: wait for them, then for the MMAs
-        const int p = s_issued[0], m = s_issued[1];
-        for (int gs = p > kLStages ? p - kLStages : 0; gs < p; ++gs)
-            mbar_poll_bounded(&full[gs % kLStages], (uint32_t)((gs / kLStages) & 1));
-        if (m > 0) mbar_poll_bounded(&acc_full[(m - 1) % kTmaAcc], (uint32_t)(((m - 1) / kTmaAcc) & 1));
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kTmaCols);
-    }
-}
-
 // hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
 // tensor maps describe: planes = 1 -> [hl][plane][y'][x'][32] (targets' level),
 // planes = 0 -> [hl][y][x][32] (parent level, row-major).  One float4 per thread.
@@ -1121,16 +531,6 @@ bool encode_map(CUtensorMap* m, const float* base, int rank, const uint64_t* dim
 
 }  // namespace
 
-cudaError_t launch_split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t s) {
-    const int64_t n4 = n / 4;
-    int64_t blocks = (n4 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    split_tf32_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<const float4*>(x), reinterpret_cast<float4*>(hi),
-                                                   reinterpret_cast<float4*>(lo), n4);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
                            int* status, int num_sms, cudaStream_t s) {
@@ -1175,48 +575,6 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     m2l_tma_kernel<<<grid, kTmaThreads, smem, s>>>(mq, mu, g, (const float*)ops.tc[k], (const float*)ops.mono[k],
                                                    (const DFv*)Q_level, (const DFv*)C_parent, u_level,
                                                    (DFv*)C_level, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, int64_t n_tiles,
-                               const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
-                               const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
-                               float* u_level, void* C_level, float* split, int* status, int num_sms,
-                               cudaStream_t s) {
-    if (n_tiles <= 0) return cudaSuccess;
-    float* qhi = split;
-    float* qlo = qhi + (size_t)nb * 32;
-    float* uhi = qlo + (size_t)nb * 32;
-    float* ulo = uhi + (size_t)nb_parent * 32;
-    {
-        cudaError_t e = launch_split_tf32(q_level, qhi, qlo, nb * 32, s);
-        if (e != cudaSuccess) return e;
-        if (u_parent && (e = launch_split_tf32(u_parent, uhi, ulo, nb_parent * 32, s)) != cudaSuccess) return e;
-    }
-    {
-        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tc_list_kernel, kLSmem);
-        if (e != cudaSuccess) return e;
-    }
-    const int grid = (int)std::min<int64_t>(n_tiles, num_sms);
-    m2l_tc_list_kernel<<<grid, kTmaThreads, kLSmem, s>>>(
-        cls_start, il, par, qhi, qlo, u_parent ? uhi : nullptr, u_parent ? ulo : nullptr, (const float*)ops.tc[k],
-        (const float*)ops.mono[k], (const DFv*)Q_level, (const DFv*)C_parent, u_level, (DFv*)C_level, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_m2l_tc_ss(const DeviceOps& ops, int k, int level, const float* qhi, const float* qlo,
-                             const void* Q_level, const float* uhi, const float* ulo, const void* C_parent,
-                             float* u_level, void* C_level, int* status, cudaStream_t s) {
-    constexpr size_t smem = 1024 + sizeof(float) * (3 * 2 * 1024 + 2 * 2 * kTcThreads * 32);
-    {
-        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tc_ss_kernel, smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int64_t rows = (int64_t)1 << (2 * (level - 1));
-    dim3 grid((unsigned)((rows + kTcThreads - 1) / kTcThreads), 4);
-    m2l_tc_ss_kernel<<<grid, kTcThreads, smem, s>>>(level, qhi, qlo, uhi, ulo, (const float*)ops.tc[k],
-                                                    (const float*)ops.mono[k], (const DFv*)Q_level,
-                                                    (const DFv*)C_parent, u_level, (DFv*)C_level, status);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_eval_parts": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lfmm_plan_destroy": (ctypes.c_int, [vp]),
         "lfmm_plan_set_flags": (ctypes.c_int, [vp, i32]),
+        "lfmm_solve": (ctypes.c_int, [vp, i64, vp, i64, vp, vp, ctypes.POINTER(lfmm_opts), vp]),
         "lfmm_plan_status": (ctypes.c_int, [vp, vp]),
         "lfmm_plan_get_info": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_plan_info)]),
         "lfmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -276,6 +277,13 @@ def lfmm_profile_read(reset: bool = False) -> dict:
 
 def lfmm_launch_count() -> int:
     return int(load().lfmm_launch_count())
+
+
+def lfmm_solve(src, tgt, f, u, opts: lfmm_opts | None = None, stream=None) -> None:
+    """One-shot solve (plan create + eval + destroy); host f uploads beside the tree build."""
+    st = load().lfmm_solve(_ptr(src), int(src.shape[0]), _ptr(tgt), int(tgt.shape[0]), _ptr(f), _ptr(u),
+                           ctypes.byref(opts) if opts is not None else None, _stream_handle(stream))
+    _check(st, "lfmm_solve")
 
 
 def autotune(src, tgt, tol: float, src_offsets=None, tgt_offsets=None, base: lfmm_opts | None = None,

@@ -192,24 +192,3 @@ def test_clustered_4m_sampled(lfmm):
     idx = np.random.default_rng(321).choice(prob.tgt.shape[0], 256, replace=False)
     ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
     assert rel_err(u[idx], ref) <= MIXED_TOL
-
-
-def test_forest_tensor_core_list_m2l(lfmm):
-    """Levels of >= 1024 compact boxes run the list form of the tensor-core M2L on the
-    mixed path; tc_min_level > 30 turns it off (SIMT list kernel).  Both meet the mixed
-    bar against the oracle and differ only by rounding."""
-    probs = forest_case(77, 24, n_min=2000, n_max=6000)
-    src, so, tgt, to, f = concat(probs)
-    with lfmm.Forest(src, so, tgt, to, precision=lfmm.LFMM_MIXED, p=8) as fo:
-        info = fo.info()
-        u_tc = fo.eval(f)
-        fo.status()
-    with lfmm.Forest(src, so, tgt, to, precision=lfmm.LFMM_MIXED, p=8, tc_min_level=99) as fo:
-        u_simt = fo.eval(f)
-    assert info["n_boxes"] > 4 * 1024
-    for i, (s_, t_, fi) in enumerate(probs):
-        ref = oracle.lattice_sum(s_, fi, t_)
-        for u in (u_tc, u_simt):
-            assert rel_err(u[to[i]:to[i + 1]], ref) <= MIXED_TOL, i
-        scale = np.abs(ref).max()
-        assert np.abs(u_tc[to[i]:to[i + 1]] - u_simt[to[i]:to[i + 1]]).max() <= 1e-6 * scale

@@ -125,3 +125,25 @@ def test_serial_equals_overlapped(lfmm, precision):
         u2 = pl.eval(prob.f)
         pl.status()
     assert np.array_equal(u0, u1) and np.array_equal(u0, u2)
+
+
+def test_solve_equals_plan_eval(lfmm):
+    """lfmm_solve (one-shot, host inputs uploaded beside the tree build) gives the plan +
+    eval result to rounding (its own plan may order a leaf's points differently), for
+    host and device arrays, and meets the oracle."""
+    prob = workloads.uniform_box(30000, 20000, 700, seed=14)
+    with lfmm.Plan(prob.src, prob.tgt) as pl:
+        u_ref = pl.eval(prob.f)
+    u_h = np.empty(prob.tgt.shape[0])
+    lfmm.lfmm_solve(prob.src, prob.tgt, prob.f, u_h, lfmm.make_opts())
+    dev = torch.device("cuda:0")
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (prob.src, prob.tgt, prob.f))
+    u_d = torch.empty(prob.tgt.shape[0], dtype=torch.float64, device=dev)
+    lfmm.lfmm_solve(s_d, t_d, f_d, u_d, lfmm.make_opts())
+    torch.cuda.synchronize()
+    scale = np.abs(u_ref).max()
+    assert np.abs(u_h - u_ref).max() <= 1e-6 * scale
+    assert np.abs(u_d.cpu().numpy() - u_ref).max() <= 1e-6 * scale
+    idx = np.random.default_rng(5).choice(prob.tgt.shape[0], 48, replace=False)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+    assert np.abs(u_h[idx] - ref).max() <= 1e-6 * np.abs(ref).max()
