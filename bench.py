@@ -319,9 +319,11 @@ def serve_leg(lfmm, n_requests: int, slots: int, check: int = 24):
 # ---------------------------------------------------------------- batched forest leg
 def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
     """The batched workload: 4,096 independent problems (N_src log-uniform in [512, 8192],
-    box side 4 sqrt(N), targets = sources) in one forest plan, mixed path p = 8; one step
-    = lfmm_forest_create + lfmm_eval with inputs resident in device memory, L2 flushed
-    before each step; 24 problems checked in full against the oracle."""
+    box side 4 sqrt(N), targets = sources) in one forest plan, mixed path with p and the
+    leaf size from the autotuner (rel. error <= 1e-6); one step = lfmm_forest_create +
+    lfmm_eval with inputs resident in device memory, L2 flushed before each step; also
+    the evaluation alone, eager and as a recorded CUDA graph; 24 problems checked in
+    full against the oracle."""
     import torch
     import oracle
     from paper_1105_3505_gb300 import workloads
@@ -337,8 +339,11 @@ def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
     s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (src, tgt, f))
     u_d = torch.empty(tgt.shape[0], dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    opts = lfmm.make_opts(lfmm.LFMM_MIXED, 8, 64, 32, 64)
     stream = torch.cuda.current_stream(dev)
+    # p, leaf size and M2L path picked by the autotuner for rel. error <= 1e-6
+    t_tune = time.perf_counter()
+    opts, tune = lfmm.autotune(s_d, t_d, 1e-6, so, to, stream=stream)
+    t_tune = time.perf_counter() - t_tune
 
     def step():
         h = lfmm.lfmm_forest_create(s_d, so, t_d, to, opts, stream)
@@ -362,8 +367,25 @@ def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
     h = step()
     info = lfmm.lfmm_plan_get_info(h)
     torch.cuda.synchronize()
-    lfmm.lfmm_plan_destroy(h)
     u = u_d.cpu().numpy()
+    # evaluation alone on the built forest: eager launches vs the recorded CUDA graph
+    ev_ms = {}
+    for mode in ("eager", "graph"):
+        lfmm.lfmm_plan_set_flags(h, lfmm.LFMM_FLAG_GRAPH if mode == "graph" else 0)
+        for _ in range(2):
+            lfmm.lfmm_eval(h, f_d, u_d, stream)
+        torch.cuda.synchronize()
+        evs2 = []
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lfmm.lfmm_eval(h, f_d, u_d, stream)
+            b.record(stream)
+            evs2.append((a, b))
+        torch.cuda.synchronize()
+        ev_ms[mode] = float(np.median([a.elapsed_time(b) for a, b in evs2]))
+    lfmm.lfmm_plan_destroy(h)
     err = 0.0
     for i in np.random.default_rng(11).choice(len(probs), 24, replace=False):
         ref = oracle.lattice_sum(probs[i].src, probs[i].f, probs[i].tgt)
@@ -372,7 +394,10 @@ def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
     return {"workload": "forest_4096: 4,096 problems, N log-uniform in [512, 8192], side 4 sqrt(N), targets = sources, seed 3",
             "points": pts, "ms_per_step": ms, "Mpoints_per_s": pts / (ms * 1e-3) / 1e6,
             "leaf_side": info["leaf_side"], "boxes": info["n_boxes"], "max_rel_err_24_problems": err,
-            "step": "lfmm_forest_create + lfmm_eval", "generation_s": t_gen}
+            "step": "lfmm_forest_create + lfmm_eval", "generation_s": t_gen,
+            "autotune": {"p": tune["p"], "leaf_size": tune["leaf_size"], "candidates": tune["candidates"],
+                         "tuned_rel_err": tune["rel_err"], "seconds": t_tune},
+            "eval_only_ms": ev_ms}
 
 
 def eval_leg(lfmm, steps: int = 20, warmup: int = 3):

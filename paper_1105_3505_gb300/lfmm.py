@@ -279,6 +279,10 @@ def lfmm_launch_count() -> int:
     return int(load().lfmm_launch_count())
 
 
+def lfmm_plan_set_flags(handle: int, flags: int) -> None:
+    _check(load().lfmm_plan_set_flags(handle, int(flags)), "lfmm_plan_set_flags")
+
+
 def lfmm_solve(src, tgt, f, u, opts: lfmm_opts | None = None, stream=None) -> None:
     """One-shot solve (plan create + eval + destroy); host f uploads beside the tree build."""
     st = load().lfmm_solve(_ptr(src), int(src.shape[0]), _ptr(tgt), int(tgt.shape[0]), _ptr(f), _ptr(u),
@@ -340,8 +344,7 @@ class Plan:
 
     def set_flags(self, graph: bool = False, serial: bool = False):
         """lfmm_plan_set_flags: graph replay and serial order for later evaluations."""
-        flags = (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0)
-        _check(load().lfmm_plan_set_flags(self.handle, flags), "lfmm_plan_set_flags")
+        lfmm_plan_set_flags(self.handle, (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0))
 
     def info(self) -> dict:
         return lfmm_plan_get_info(self.handle)
