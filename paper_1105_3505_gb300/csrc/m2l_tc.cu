@@ -375,16 +375,19 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
             for (int r = lane; r < rows; r += 32) {
                 const int ri = ri0 + r % g.TX, rj = rj0 + r / g.TX;
                 DFv sacc = g.has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
-                DFv qv[27];
+                for (int k0 = 0; k0 < 27; k0 += 9) {  // nine loads in flight at a time
+                    DFv qv[9];
 #pragma unroll
-                for (int k = 0; k < 27; ++k) {
-                    const int sx = 2 * ri + px + s_off[cls][k][0], sy = 2 * rj + py + s_off[cls][k][1];
-                    qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qin[morton2(sx, sy)] : DFv{0.f, 0.f};
-                }
+                    for (int k = 0; k < 9; ++k) {
+                        const int sx = 2 * ri + px + s_off[cls][k0 + k][0], sy = 2 * rj + py + s_off[cls][k0 + k][1];
+                        qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qin[morton2(sx, sy)]
+                                                                                 : DFv{0.f, 0.f};
+                    }
 #pragma unroll
-                for (int k = 0; k < 27; ++k) {
-                    const int o = s_off[cls][k][2];
-                    sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+                    for (int k = 0; k < 9; ++k) {
+                        const int o = s_off[cls][k0 + k][2];
+                        sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+                    }
                 }
                 Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
             }
