@@ -444,6 +444,68 @@ def eval_leg(lfmm, steps: int = 20, warmup: int = 3):
     return res
 
 
+def multi_leg(lfmm, k: int = 8, steps: int = 10, warmup: int = 2):
+    """k charge vectors on the uniform_1m plan (mixed, p = 8): lfmm_eval_multi against k
+    calls of lfmm_eval (plan built once, L2 flushed before each timed call), and the
+    near-field time per vector of the batched pass against the single-vector kernel."""
+    import torch
+    from paper_1105_3505_gb300 import workloads
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    prob = workloads.uniform_1m()
+    ns, nt = prob.src.shape[0], prob.tgt.shape[0]
+    rng = np.random.default_rng(5)
+    F = np.stack([workloads.zero_sum(rng.standard_normal(ns)) for _ in range(k)])
+    s_d, t_d, F_d = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (prob.src, prob.tgt, F))
+    U_d = torch.empty((k, nt), dtype=torch.float64, device=dev)
+    o = lfmm.make_opts(lfmm.LFMM_MIXED, 8, 64, 32, 64)
+    h = lfmm.lfmm_plan_create(s_d, ns, t_d, nt, o, stream)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        evs = []
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    def multi():
+        lfmm.load().lfmm_eval_multi(h, F_d.data_ptr(), k, U_d.data_ptr(), stream.cuda_stream)
+
+    def singles():
+        for r in range(k):
+            lfmm.lfmm_eval(h, F_d[r], U_d[r], stream)
+
+    ms_multi, ms_single = timed(multi), timed(singles)
+    # near-field device time per vector: batched pass vs single-vector kernel (serial order)
+    lfmm.lfmm_plan_set_flags(h, lfmm.LFMM_FLAG_SERIAL)
+    lfmm.lfmm_profile_enable(True)
+    lfmm.lfmm_profile_read(reset=True)
+    multi()
+    torch.cuda.synchronize()
+    ph_m = lfmm.lfmm_profile_read(reset=True)
+    lfmm.lfmm_eval(h, F_d[0], U_d[0], stream)
+    torch.cuda.synchronize()
+    ph_s = lfmm.lfmm_profile_read(reset=True)
+    lfmm.lfmm_profile_enable(False)
+    lfmm.lfmm_plan_destroy(h)
+    pairs = 150228790  # near-field pairs of uniform_1m (per vector)
+    p2p_m = ph_m["p2p"][0] / k
+    return {"k": k, "ms_eval_multi": ms_multi, "ms_k_evals": ms_single, "speedup": ms_single / ms_multi,
+            "Mpoints_per_s_per_vector_multi": k * (ns + nt) / (ms_multi * 1e-3) / 1e6,
+            "near_field_us_per_vector": {"batched": p2p_m * 1e3, "single": ph_s["p2p"][0] * 1e3},
+            "near_field_Gpair_fma_per_s": pairs * k / (ph_m["p2p"][0] * 1e-3) / 1e9,
+            "note": "evaluation only; four vectors per near-field pass share each phi table lookup"}
+
+
 # ---------------------------------------------------------------- replicas
 def replica_throughput(ms_local, points_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` independent replicas: every rank solved
@@ -648,6 +710,7 @@ def main():
         out["cpu_baseline"] = cpu_baseline(prob)
         out["forest"] = forest_leg(lfmm)
         out["eval_only"] = eval_leg(lfmm)
+        out["multi_rhs"] = multi_leg(lfmm)
         if args.serve_requests > 0:
             out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots)
     print(json.dumps(out), flush=True)

@@ -149,6 +149,15 @@ int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_
 /* Release a plan (NULL is a no-op).  Waits for the plan's outstanding work. */
 int lfmm_plan_destroy(lfmm_plan* plan);
 
+/* Apply the plan to k charge vectors at once: U[r n_tgt + i] = sum_j phi(tgt_i - src_j)
+ * F[r n_src + j] for r < k (vector-major layouts, host or device, k in [1, 4096]).
+ * Each vector's result is bit-identical to lfmm_eval on the same plan; the near field of
+ * four vectors shares every table lookup (a uniform plan with a far field; forests and
+ * trees without a far field evaluate the vectors one after another).  The per-vector
+ * buffers grow with the largest k seen and stay with the plan.  Evaluates eagerly (the
+ * graph flag applies to lfmm_eval). */
+int lfmm_eval_multi(lfmm_plan* plan, const double* F, int32_t k, double* U, void* stream);
+
 /* One-shot solve: lfmm_plan_create + lfmm_eval + lfmm_plan_destroy in one call, for
  * points that are solved once.  Host inputs are uploaded first (coordinates on
  * `stream`); the upload of a host f runs on a second stream behind them, overlapping

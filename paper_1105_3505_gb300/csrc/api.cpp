@@ -64,6 +64,16 @@ struct lfmm_plan {
     cudaGraphExec_t graph = nullptr;
     const double* graph_f = nullptr;
     double* graph_out[3] = {nullptr, nullptr, nullptr};
+    // lfmm_eval_multi: per-vector sorted charges, leaf charges, near and far parts,
+    // and host staging, for up to multi_cap vectors (grown on demand)
+    int multi_cap = 0;
+    void* m_fsorted = nullptr;
+    void* m_Q = nullptr;
+    double* m_un = nullptr;
+    double* m_uf = nullptr;
+    int host_cap = 0;
+    double* m_fstage = nullptr;
+    double* m_ustage = nullptr;
 };
 
 // A second stream with its fork / join events, pooled process-wide (plans are often
@@ -446,11 +456,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     return LFMM_OK;
 }
 
-template <typename T>
-int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
-    if (p->forest)
-        return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
-                              u, un, uf, p->num_sms, s);
+TreeView tree_view(const lfmm_plan* p) {
     TreeView t;
     t.L = p->L;
     t.side = p->side;
@@ -465,29 +471,24 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     t.n_tgt = p->nt;
     t.max_leaf_src = p->max_src;
     t.max_leaf_tgt = p->max_tgt;
+    return t;
+}
+
+// M2M, M2L and L2L of a uniform plan (Sec. 8.2 steps 2-4), from the leaf expansions the
+// P2M left in p->qhat / p->Qbox to the leaf incoming expansions in p->uhat / p->Cbox.
+// `before_fine` runs after the cooperative coarse-level kernels, before the per-level
+// launches (the near field is forked there).
+template <typename T, typename Hook>
+int far_sweeps(lfmm_plan* p, cudaStream_t s, Hook before_fine) {
     const DeviceOps& ops = *p->ops;
     const int NP = p->NP;
+    const int L = p->L;
     T* q = (T*)p->qhat;
     T* uh = (T*)p->uhat;
     auto Qx = [&](int l) { return q + (size_t)p->lvl_off[l] * NP; };
     auto Ux = [&](int l) { return uh + (size_t)p->lvl_off[l] * NP; };
     auto Qm = [&](int l) { return (void*)((char*)p->Qbox + (size_t)p->lvl_off[l] * 8); };
     auto Cm = [&](int l) { return (void*)((char*)p->Cbox + (size_t)p->lvl_off[l] * 8); };
-    const int L = p->L;
-    {
-        PhaseTimer pt(LFMM_PHASE_P2M, s);
-        LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, Qx(L), Qm(L), s));
-        pt.add_launches(1);
-    }
-    // The near field depends only on the sorted charges and the leaf charges (P2M): it
-    // runs on the plan's second stream beside the per-level M2L launches and the L2P
-    // (after the cooperative coarse-level kernels, which need the whole device), and
-    // one elementwise sum joins the two.
-    // With LFMM_FLAG_SERIAL the same kernels run in the same order on `s` alone.
-    const bool split = L >= 2 && p->un_tmp != nullptr;
-    if (split && !(p->opts.flags & LFMM_FLAG_SERIAL) && !p->aux) p->aux = acquire_aux(p->device);
-    const bool concurrent = split && !(p->opts.flags & LFMM_FLAG_SERIAL) && p->aux != nullptr;
-    cudaStream_t near_s = concurrent ? p->aux->s : s;
     LevelBufs lb;
     for (int l = std::min(2, L); l <= L && l < 16; ++l) {
         lb.q[l] = Qx(l);
@@ -516,15 +517,9 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
             l_first = last + 1;
         }
     }
-    if (split) {
-        if (concurrent) {
-            LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
-            LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
-        }
-        PhaseTimer pt(LFMM_PHASE_P2P, near_s);
-        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Qm(L), nullptr, p->un_tmp,
-                                        nullptr, p->num_sms, near_s));
-        pt.add_launches(1);
+    {
+        const int st = before_fine();
+        if (st) return st;
     }
     for (int l = l_first; l <= L; ++l) {
         const bool tc = m2l_uses_tc(ops, L - l, l, p->tc_min_level, sizeof(T) == 4);
@@ -542,10 +537,57 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
                                     l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), s));
         pt.add_launches(1);
     }
+    return LFMM_OK;
+}
+
+template <typename T>
+int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
+    if (p->forest)
+        return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
+                              u, un, uf, p->num_sms, s);
+    const TreeView t = tree_view(p);
+    const DeviceOps& ops = *p->ops;
+    const int NP = p->NP;
+    const int L = p->L;
+    const size_t leaf_off = (size_t)p->lvl_off[L];
+    T* q_leaf = (T*)p->qhat + leaf_off * NP;
+    T* u_leaf = (T*)p->uhat + leaf_off * NP;
+    void* Q_leaf = (char*)p->Qbox + leaf_off * 8;
+    void* C_leaf = (char*)p->Cbox + leaf_off * 8;
+    {
+        PhaseTimer pt(LFMM_PHASE_P2M, s);
+        LFMM_CUDA_TRY(launch_p2m<T>(t, ops, f, (T*)p->f_sorted, q_leaf, Q_leaf, s));
+        pt.add_launches(1);
+    }
+    // The near field depends only on the sorted charges and the leaf charges (P2M): it
+    // runs on the plan's second stream beside the per-level M2L launches and the L2P
+    // (after the cooperative coarse-level kernels, which need the whole device), and
+    // one elementwise sum joins the two.  With LFMM_FLAG_SERIAL the same kernels run in
+    // the same order on `s` alone.
+    const bool split = L >= 2 && p->un_tmp != nullptr;
+    if (split && !(p->opts.flags & LFMM_FLAG_SERIAL) && !p->aux) p->aux = acquire_aux(p->device);
+    const bool concurrent = split && !(p->opts.flags & LFMM_FLAG_SERIAL) && p->aux != nullptr;
+    cudaStream_t near_s = concurrent ? p->aux->s : s;
+    auto near = [&]() -> int {
+        if (!split) return LFMM_OK;
+        if (concurrent) {
+            LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
+            LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
+        }
+        PhaseTimer pt(LFMM_PHASE_P2P, near_s);
+        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Q_leaf, nullptr, p->un_tmp,
+                                        nullptr, p->num_sms, near_s));
+        pt.add_launches(1);
+        return LFMM_OK;
+    };
+    {
+        const int st = far_sweeps<T>(p, s, near);
+        if (st) return st;
+    }
     if (split) {
         {
             PhaseTimer pt(LFMM_PHASE_L2P, s);
-            LFMM_CUDA_TRY(launch_l2p<T>(t, ops, Ux(L), Cm(L), p->uf_tmp, s));
+            LFMM_CUDA_TRY(launch_l2p<T>(t, ops, u_leaf, C_leaf, p->uf_tmp, s));
             pt.add_launches(1);
         }
         if (concurrent) {
@@ -557,10 +599,61 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         pt.add_launches(1);
     } else {
         PhaseTimer pt(LFMM_PHASE_P2P, s);
-        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, L >= 2 ? Ux(L) : nullptr,
-                                        L >= 2 ? Cm(L) : nullptr, Qm(L), u, un, uf, p->num_sms, s));
+        LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Q_leaf, u, un, uf,
+                                        p->num_sms, s));
         pt.add_launches(1);
     }
+    return LFMM_OK;
+}
+
+// k charge vectors on one uniform plan: per vector P2M, the far-field sweeps and L2P
+// (the expansion arrays are reused vector after vector), then the near field of all
+// vectors in passes of four that share each table lookup, then one binary64 sum.
+// Every vector's arithmetic is that of lfmm_eval, so the results are bit-identical.
+template <typename T>
+int eval_multi_impl(lfmm_plan* p, const double* F, int k, double* U, cudaStream_t s) {
+    const int L = p->L;
+    if (p->forest || L < 2 || !p->un_tmp) {  // one vector at a time
+        for (int r = 0; r < k; ++r) {
+            const int st = eval_impl<T>(p, F + (size_t)r * p->ns, U + (size_t)r * p->nt, nullptr, nullptr, s);
+            if (st) return st;
+        }
+        return LFMM_OK;
+    }
+    const TreeView t = tree_view(p);
+    const DeviceOps& ops = *p->ops;
+    const int NP = p->NP;
+    const size_t leaf_off = (size_t)p->lvl_off[L];
+    const int64_t n_leaf = (int64_t)1 << (2 * L);
+    T* q_leaf = (T*)p->qhat + leaf_off * NP;
+    T* u_leaf = (T*)p->uhat + leaf_off * NP;
+    void* Q_leaf = (char*)p->Qbox + leaf_off * 8;
+    void* C_leaf = (char*)p->Cbox + leaf_off * 8;
+    T* fs = (T*)p->m_fsorted;
+    char* Qs = (char*)p->m_Q;
+    for (int r = 0; r < k; ++r) {
+        {
+            PhaseTimer pt(LFMM_PHASE_P2M, s);
+            LFMM_CUDA_TRY(launch_p2m<T>(t, ops, F + (size_t)r * p->ns, fs + (size_t)r * p->ns, q_leaf, Q_leaf, s));
+            pt.add_launches(1);
+        }
+        // the leaf charges of vector r, for the near-field constant
+        LFMM_CUDA_TRY(cudaMemcpyAsync(Qs + (size_t)r * n_leaf * 8, Q_leaf, (size_t)n_leaf * 8,
+                                      cudaMemcpyDeviceToDevice, s));
+        const int st = far_sweeps<T>(p, s, [] { return LFMM_OK; });
+        if (st) return st;
+        PhaseTimer pt(LFMM_PHASE_L2P, s);
+        LFMM_CUDA_TRY(launch_l2p<T>(t, ops, u_leaf, C_leaf, p->m_uf + (size_t)r * p->nt, s));
+        pt.add_launches(1);
+    }
+    {
+        PhaseTimer pt(LFMM_PHASE_P2P, s);
+        LFMM_CUDA_TRY(launch_p2p_multi<T>(t, ops, k, fs, p->ns, Qs, n_leaf, p->m_un, p->nt, p->num_sms, s));
+        pt.add_launches((k + 3) / 4);
+    }
+    PhaseTimer pt(LFMM_PHASE_L2P, s);
+    LFMM_CUDA_TRY(launch_combine((int64_t)k * p->nt, p->m_un, p->m_uf, U, nullptr, nullptr, s));
+    pt.add_launches(1);
     return LFMM_OK;
 }
 
@@ -795,6 +888,57 @@ int lfmm_solve(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy, int6
     }
     release();
     return st ? st : st2;
+}
+
+int lfmm_eval_multi(lfmm_plan* p, const double* F, int32_t k, double* U, void* stream) {
+    if (!p || !F || !U) return fail(LFMM_EINVAL, "NULL plan, F or U");
+    if (k < 1 || k > 4096) return fail(LFMM_EINVAL, "k must be in [1, 4096]");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    int st;
+    const bool uniform = !p->forest && p->L >= 2 && p->un_tmp;
+    if (uniform && p->multi_cap < k) {
+        // grow the per-vector buffers (the old ones are released in stream order)
+        const size_t esz = p->opts.precision == LFMM_MIXED ? sizeof(float) : sizeof(double);
+        const int64_t n_leaf = (int64_t)1 << (2 * p->L);
+        void *a, *b, *c;
+        if ((st = palloc(p, &a, (size_t)k * p->ns * esz, s))) return st;
+        if ((st = palloc(p, &b, (size_t)k * n_leaf * 8, s))) return st;
+        if ((st = palloc(p, &c, (size_t)2 * k * p->nt * sizeof(double), s))) return st;
+        p->m_fsorted = a;
+        p->m_Q = b;
+        p->m_un = (double*)c;
+        p->m_uf = p->m_un + (size_t)k * p->nt;
+        p->multi_cap = k;
+    }
+    const double* Fd = F;
+    double* Ud = U;
+    const bool host_f = !is_device_ptr(F), host_u = !is_device_ptr(U);
+    if ((host_f || host_u) && p->host_cap < k) {
+        void *a, *b;
+        if ((st = palloc(p, &a, (size_t)k * p->ns * sizeof(double), s))) return st;
+        if ((st = palloc(p, &b, (size_t)k * p->nt * sizeof(double), s))) return st;
+        p->m_fstage = (double*)a;
+        p->m_ustage = (double*)b;
+        p->host_cap = k;
+    }
+    if (host_f) {
+        PhaseTimer pt(LFMM_PHASE_COPY, s);
+        LFMM_CUDA_TRY(cudaMemcpyAsync(p->m_fstage, F, (size_t)k * p->ns * sizeof(double), cudaMemcpyHostToDevice, s));
+        Fd = p->m_fstage;
+    }
+    if (host_u) Ud = p->m_ustage;
+    st = p->opts.precision == LFMM_MIXED ? eval_multi_impl<float>(p, Fd, k, Ud, s)
+         : p->opts.precision == LFMM_DF  ? eval_multi_impl<DF>(p, Fd, k, Ud, s)
+                                         : eval_multi_impl<double>(p, Fd, k, Ud, s);
+    if (st) return st;
+    if (host_u) {
+        PhaseTimer pt(LFMM_PHASE_COPY, s);
+        LFMM_CUDA_TRY(cudaMemcpyAsync(U, Ud, (size_t)k * p->nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+        LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (profiling_enabled()) profile_flush();
+    return LFMM_OK;
 }
 
 int lfmm_plan_set_flags(lfmm_plan* p, int32_t flags) {

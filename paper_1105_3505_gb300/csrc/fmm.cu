@@ -930,6 +930,198 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
     }
 }
 
+// Near field for KR charge vectors at once (lfmm_eval_multi): the strip kernel's
+// staging and pair loop, with each staged source carrying its KR charges (one 16-byte
+// vector for KR = 4 in binary32) so that every table word serves KR multiply-adds.
+// Per charge vector the operations and their order are those of p2p_strip_kernel, so
+// each result equals the single-vector one bit for bit.  Vector r of the pass reads
+// f_sorted + r * f_stride and Qleaf + r * q_stride and writes u_near + r * u_stride
+// (binary64, caller order); nr <= KR vectors are active.
+template <typename T, int KR>
+struct StripMultiCfg {
+    static constexpr int WARPS = 8;
+    static constexpr int CAPS = (sizeof(T) == 4 ? 4096 : 2048) / (KR > 1 ? 2 : 1);
+    static constexpr int CAPT = 2048;
+    static constexpr int MAXSW = 32;
+};
+
+template <typename T, int KR>
+__global__ void __launch_bounds__(StripMultiCfg<T, KR>::WARPS * 32) p2p_strip_multi_kernel(
+    int L, int side, int SW, int nr, const int32_t* __restrict__ sbeg, const int32_t* __restrict__ sloc,
+    const int32_t* __restrict__ tbeg, const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
+    const T* __restrict__ f_sorted, int64_t f_stride, const T* __restrict__ table, int tab_H, int tab_W,
+    const typename Mono<T>::V* __restrict__ Qleaf, int64_t q_stride, double* __restrict__ u_near,
+    int64_t u_stride) {
+    using M = Mono<T>;
+    using V = typename M::V;
+    using Cfg = StripMultiCfg<T, KR>;
+    using FV = VecT<T, KR>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tab_n = (2 * tab_H + 1) * tab_W;
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    FV* s_f = reinterpret_cast<FV*>(reinterpret_cast<unsigned char*>(smem_raw) +
+                                    (((size_t)tab_n * sizeof(T) + 15) & ~(size_t)15));   // [CAPS]
+    int* s_off = reinterpret_cast<int*>(s_f + Cfg::CAPS);                              // [CAPS]
+    V* s_q = reinterpret_cast<V*>(s_off + Cfg::CAPS);                                  // [KR][3][MAXSW+2]
+    int* s_tloc = reinterpret_cast<int*>(s_q + KR * 3 * (Cfg::MAXSW + 2));             // [CAPT]
+    int* s_tperm = s_tloc + Cfg::CAPT;                                                 // [CAPT]
+    int* s_sb = s_tperm + Cfg::CAPT;                                                   // [3][MAXSW+3]
+    int* s_tb = s_sb + 3 * (Cfg::MAXSW + 3);                                           // [MAXSW+1]
+    __shared__ int s_rs[4];
+    __shared__ int s_ra[Cfg::MAXSW][3], s_rl[Cfg::MAXSW][3];
+    __shared__ double s_nc[KR][Cfg::MAXSW];
+
+    for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
+    const T* tab_c = tab + (tab_H + tab_H * tab_W);
+    const int n = 1 << L;
+    const int n_seg = (n + SW - 1) / SW;
+    const int64_t n_strips = (int64_t)n * n_seg;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int64_t strip = blockIdx.x; strip < n_strips; strip += gridDim.x) {
+        const int by = (int)(strip / n_seg);
+        const int bx0 = (int)(strip % n_seg) * SW;
+        const int bx1 = min(bx0 + SW, n);
+        const int c_lo = max(bx0 - 1, 0), c_hi = min(bx1, n - 1);
+        const int ncol = c_hi - c_lo + 1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * (ncol + 1); i += blockDim.x) {
+            const int r = i / (ncol + 1), c = i % (ncol + 1);
+            const int yy = by + r - 1;
+            s_sb[r * (Cfg::MAXSW + 3) + c] = (yy >= 0 && yy < n) ? sbeg[(int64_t)yy * n + c_lo + c] : 0;
+        }
+        for (int i = threadIdx.x; i <= bx1 - bx0; i += blockDim.x) s_tb[i] = tbeg[(int64_t)by * n + bx0 + i];
+        for (int i = threadIdx.x; i < KR * 3 * ncol; i += blockDim.x) {
+            const int k = i / (3 * ncol), rc = i % (3 * ncol);
+            const int r = rc / ncol, c = rc % ncol;
+            const int yy = by + r - 1;
+            s_q[(k * 3 + r) * (Cfg::MAXSW + 2) + c] =
+                (k < nr && yy >= 0 && yy < n) ? Qleaf[(size_t)k * q_stride + morton2(c_lo + c, yy)] : M::zero();
+        }
+        __syncthreads();
+        for (int li = threadIdx.x; li < bx1 - bx0; li += blockDim.x) {
+            const int bx = bx0 + li;
+            const int ca = max(bx - 1, 0) - c_lo, cb = min(bx + 1, n - 1) - c_lo + 1;
+            int rs = 0;
+            V qn[KR];
+#pragma unroll
+            for (int k = 0; k < KR; ++k) qn[k] = M::zero();
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int* sb = s_sb + r * (Cfg::MAXSW + 3);
+                s_ra[li][r] = rs + (sb[ca] - sb[0]);
+                s_rl[li][r] = sb[cb] - sb[ca];
+                rs += sb[ncol] - sb[0];
+                for (int c = ca; c < cb; ++c)
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) qn[k] = M::add(qn[k], s_q[(k * 3 + r) * (Cfg::MAXSW + 2) + c]);
+            }
+#pragma unroll
+            for (int k = 0; k < KR; ++k) s_nc[k][li] = M::to_double(M::mul(phi0, qn[k]));
+        }
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int r = 0; r < 3; ++r) {
+                s_rs[r] = acc;
+                acc += s_sb[r * (Cfg::MAXSW + 3) + ncol] - s_sb[r * (Cfg::MAXSW + 3)];
+            }
+            s_rs[3] = acc;
+        }
+        __syncthreads();
+        const int ns_strip = s_rs[3];
+        for (int v = threadIdx.x; v < ns_strip; v += blockDim.x) {
+            const int r = (v >= s_rs[1]) + (v >= s_rs[2]);
+            const int* sb = s_sb + r * (Cfg::MAXSW + 3);
+            const int j = sb[0] + (v - s_rs[r]);
+            int lo = 0, hi = ncol;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (sb[mid] <= j) lo = mid;
+                else hi = mid;
+            }
+            const int l = sloc[j];
+            s_off[v] = (c_lo + lo - bx0) * side + (l & 0xffff) + tab_W * ((r - 1) * side + (l >> 16));
+            FV fv;
+#pragma unroll
+            for (int k = 0; k < KR; ++k) fv.v[k] = k < nr ? f_sorted[(size_t)k * f_stride + j] : T(0);
+            s_f[v] = fv;
+        }
+        const int tb0 = s_tb[0], nt_strip = s_tb[bx1 - bx0] - tb0;
+        for (int v = threadIdx.x; v < nt_strip; v += blockDim.x) {
+            int lo = 0, hi = bx1 - bx0;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_tb[mid] - tb0 <= v) lo = mid;
+                else hi = mid;
+            }
+            s_tloc[v] = tloc[tb0 + v] | (lo << 8);
+            s_tperm[v] = tperm[tb0 + v];
+        }
+        __syncthreads();
+
+        const int n_chunks = (nt_strip + 31) >> 5;
+        for (int chunk = warp; chunk < n_chunks; chunk += Cfg::WARPS) {
+            const int v = chunk * 32 + lane;
+            const bool active = v < nt_strip;
+            const int tl = s_tloc[active ? v : chunk * 32];
+            const int li = (tl >> 8) & 0xff, tx = tl & 0xff, ty = tl >> 16;
+            const T* tp = tab_c + (tx + tab_W * ty + li * side);
+            T acc[KR], cmp[KR];
+#pragma unroll
+            for (int k = 0; k < KR; ++k) acc[k] = cmp[k] = T(0);
+            auto add = [&](int k, T term) {
+                if constexpr (sizeof(T) == 4) {
+                    const T y = term - cmp[k];
+                    const T s2 = acc[k] + y;
+                    cmp[k] = (s2 - acc[k]) - y;
+                    acc[k] = s2;
+                } else {
+                    acc[k] += term;
+                }
+            };
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int* so = s_off + s_ra[li][r];
+                const FV* sf = s_f + s_ra[li][r];
+                const int len = active ? s_rl[li][r] : 0;
+                int j = 0;
+                for (; j + 4 <= len; j += 4) {
+                    const T p0 = tp[-so[j]], p1 = tp[-so[j + 1]], p2 = tp[-so[j + 2]], p3 = tp[-so[j + 3]];
+                    const FV f0 = sf[j], f1 = sf[j + 1], f2 = sf[j + 2], f3 = sf[j + 3];
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) {
+                        T b = p0 * f0.v[k];
+                        b = fma(p1, f1.v[k], b);
+                        b = fma(p2, f2.v[k], b);
+                        b = fma(p3, f3.v[k], b);
+                        add(k, b);
+                    }
+                }
+                if (j < len) {
+                    T b[KR];
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) b[k] = T(0);
+                    for (; j < len; ++j) {
+                        const T pj = tp[-so[j]];
+                        const FV fj = sf[j];
+#pragma unroll
+                        for (int k = 0; k < KR; ++k) b[k] = fma(pj, fj.v[k], b[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) add(k, b[k]);
+                }
+            }
+            if (active) {
+                const int dst = s_tperm[v];
+#pragma unroll
+                for (int k = 0; k < KR; ++k)
+                    if (k < nr) u_near[(size_t)k * u_stride + dst] = (double)(acc[k] - cmp[k]) + s_nc[k][li];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------- fused small levels
 // The coarse levels hold few boxes, so one launch per level is mostly launch and
 // latency.  Two cooperative kernels (all blocks co-resident) cover them instead:
@@ -1308,6 +1500,60 @@ cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_s
     return launch_p2p_np<T, 64>(t, ops, f_sorted, uhat, Cleaf, Qleaf, u, un, uf, num_sms, s);
 }
 
+template <typename T, int KR>
+static cudaError_t launch_p2p_multi_kr(const TreeView& t, const DeviceOps& ops, int SW, int nr, const T* f_sorted,
+                                       int64_t f_stride, const void* Qleaf, int64_t q_stride, double* un,
+                                       int64_t u_stride, int num_sms, cudaStream_t s) {
+    using Cfg = StripMultiCfg<T, KR>;
+    using V = typename Mono<T>::V;
+    const size_t tab_bytes = (((size_t)(2 * ops.tab_H + 1) * ops.tab_W * sizeof(T)) + 15) & ~(size_t)15;
+    const size_t smem = tab_bytes + (size_t)Cfg::CAPS * (sizeof(VecT<T, KR>) + sizeof(int)) +
+                        (size_t)KR * 3 * (Cfg::MAXSW + 2) * sizeof(V) + (size_t)2 * Cfg::CAPT * sizeof(int) +
+                        (size_t)(3 * (Cfg::MAXSW + 3) + Cfg::MAXSW + 1) * sizeof(int);
+    const void* fn = (const void*)p2p_strip_multi_kernel<T, KR>;
+    {
+        cudaError_t e = ensure_dynamic_smem(fn, smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int n = 1 << t.L;
+    const int64_t strips = (int64_t)n * ((n + SW - 1) / SW);
+    int64_t blocks = std::min<int64_t>(strips, (int64_t)num_sms * blocks_per_sm(fn, Cfg::WARPS * 32, smem));
+    if (blocks < 1) blocks = 1;
+    p2p_strip_multi_kernel<T, KR><<<(int)blocks, Cfg::WARPS * 32, smem, s>>>(
+        t.L, t.side, SW, nr, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted, f_stride,
+        (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, (const V*)Qleaf, q_stride, un, u_stride);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_p2p_multi(const TreeView& t, const DeviceOps& ops, int k, const T* f_sorted, int64_t f_stride,
+                             const void* Qleaf, int64_t q_stride, double* un, int64_t u_stride, int num_sms,
+                             cudaStream_t s) {
+    using V = typename Mono<T>::V;
+    constexpr int KR = 4;
+    const int n = 1 << t.L;
+    const int ms = std::max(1, t.max_leaf_src), mt = std::max(1, t.max_leaf_tgt);
+    const int SW = std::min({StripMultiCfg<T, KR>::MAXSW, StripMultiCfg<T, KR>::CAPS / (3 * ms) - 2,
+                             StripMultiCfg<T, KR>::CAPT / mt, n});
+    for (int r0 = 0; r0 < k; r0 += KR) {
+        const int nr = std::min(KR, k - r0);
+        const T* f = f_sorted + (size_t)r0 * f_stride;
+        const V* q = (const V*)Qleaf + (size_t)r0 * q_stride;
+        double* u = un + (size_t)r0 * u_stride;
+        cudaError_t e;
+        if (SW >= 1)
+            e = launch_p2p_multi_kr<T, KR>(t, ops, SW, nr, f, f_stride, q, q_stride, u, u_stride, num_sms, s);
+        else  // leaves too full for the staging: one vector at a time through the leaf kernel
+            for (int r = 0; r < nr; ++r)
+                if ((e = launch_p2p_l2p<T>(t, ops, f + (size_t)r * f_stride, nullptr, nullptr, q + (size_t)r * q_stride,
+                                           nullptr, u + (size_t)r * u_stride, nullptr, num_sms, s)) != cudaSuccess)
+                    break;
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+
 // ---- fused small levels (cooperative launches)
 template <typename T>
 static void fill_levels(LevelPtrs<T>& P, const DeviceOps& ops, int L, const LevelBufs& b) {
@@ -1460,6 +1706,8 @@ cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double
                                        cudaStream_t);                                                         \
     template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const void*, const T*,          \
                                        const void*, T*, void*, cudaStream_t);                                \
+    template cudaError_t launch_p2p_multi<T>(const TreeView&, const DeviceOps&, int, const T*, int64_t, const void*, \
+                                             int64_t, double*, int64_t, int, cudaStream_t);                     \
     template cudaError_t launch_p2p_l2p<T>(const TreeView&, const DeviceOps&, const T*, const T*, const void*, \
                                            const void*, double*, double*, double*, int, cudaStream_t);
 

@@ -339,6 +339,12 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
                            int* status, int num_sms, cudaStream_t s);
+// Near field of k charge vectors (vector r: f_sorted + r f_stride, Qleaf + r q_stride,
+// out u_near + r u_stride), four vectors per pass sharing each table lookup.
+template <typename T>
+cudaError_t launch_p2p_multi(const TreeView& t, const DeviceOps& ops, int k, const T* f_sorted, int64_t f_stride,
+                             const void* Qleaf, int64_t q_stride, double* u_near, int64_t u_stride, int num_sms,
+                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_p2p_l2p(const TreeView& t, const DeviceOps& ops, const T* f_sorted,
                            const T* uhat_leaf, const void* C_leaf, const void* Q_leaf, double* u,

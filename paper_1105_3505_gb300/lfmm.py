@@ -82,6 +82,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_plan_destroy": (ctypes.c_int, [vp]),
         "lfmm_plan_set_flags": (ctypes.c_int, [vp, i32]),
         "lfmm_solve": (ctypes.c_int, [vp, i64, vp, i64, vp, vp, ctypes.POINTER(lfmm_opts), vp]),
+        "lfmm_eval_multi": (ctypes.c_int, [vp, vp, i32, vp, vp]),
         "lfmm_plan_status": (ctypes.c_int, [vp, vp]),
         "lfmm_plan_get_info": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_plan_info)]),
         "lfmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -357,6 +358,19 @@ class Plan:
                 import torch
                 out = torch.empty(self.n_tgt, dtype=torch.float64, device=f.device)
         lfmm_eval(self.handle, f, out, self.stream)
+        return out
+
+    def eval_multi(self, F, out=None):
+        """lfmm_eval_multi: F of shape (k, n_src) -> U of shape (k, n_tgt), same kind of memory."""
+        k = int(F.shape[0])
+        if out is None:
+            if isinstance(F, np.ndarray):
+                out = np.empty((k, self.n_tgt), dtype=np.float64)
+            else:
+                import torch
+                out = torch.empty((k, self.n_tgt), dtype=torch.float64, device=F.device)
+        _check(load().lfmm_eval_multi(self.handle, _ptr(F), k, _ptr(out), _stream_handle(self.stream)),
+               "lfmm_eval_multi")
         return out
 
     def eval_parts(self, f):
