@@ -68,7 +68,11 @@ struct lfmm_plan {
     // and host staging, for up to multi_cap vectors (grown on demand)
     int multi_cap = 0;
     void* m_fsorted = nullptr;
+    void* m_qhat = nullptr;
+    void* m_uhat = nullptr;
     void* m_Q = nullptr;
+    void* m_C = nullptr;
+    void* m_split = nullptr;
     double* m_un = nullptr;
     double* m_uf = nullptr;
     int host_cap = 0;
@@ -469,43 +473,61 @@ TreeView tree_view(const lfmm_plan* p) {
     t.tgt_perm = p->tgt_perm;
     t.tgt_leaf = p->tgt_leaf;
     t.n_tgt = p->nt;
+    t.n_src_all = p->ns;
     t.max_leaf_src = p->max_src;
     t.max_leaf_tgt = p->max_tgt;
     return t;
 }
 
+// Expansion arrays of one or more charge vectors: vector v's q_hat / u_hat start v vq
+// elements, its Q / C v vQ value pairs after vector 0's.
+struct FarBufs {
+    void *q, *u, *Q, *C;
+    float* split;
+    int nvec;
+    int64_t vq, vQ;
+};
+
+FarBufs plan_far_bufs(lfmm_plan* p) {
+    return FarBufs{p->qhat, p->uhat, p->Qbox, p->Cbox, (float*)p->tc_split, 1, 0, 0};
+}
+
 // M2M, M2L and L2L of a uniform plan (Sec. 8.2 steps 2-4), from the leaf expansions the
-// P2M left in p->qhat / p->Qbox to the leaf incoming expansions in p->uhat / p->Cbox.
-// `before_fine` runs after the cooperative coarse-level kernels, before the per-level
-// launches (the near field is forked there).
+// P2M left in b.q / b.Q to the leaf incoming expansions in b.u / b.C, for b.nvec
+// vectors at once (the fused coarse-level kernels and the tensor-core M2L take them in
+// one launch; the per-level fallbacks loop).  `before_fine` runs after the cooperative
+// coarse-level kernels, before the per-level launches (the near field is forked there).
 template <typename T, typename Hook>
-int far_sweeps(lfmm_plan* p, cudaStream_t s, Hook before_fine) {
+int far_sweeps(lfmm_plan* p, const FarBufs& b, cudaStream_t s, Hook before_fine) {
     const DeviceOps& ops = *p->ops;
     const int NP = p->NP;
     const int L = p->L;
-    T* q = (T*)p->qhat;
-    T* uh = (T*)p->uhat;
-    auto Qx = [&](int l) { return q + (size_t)p->lvl_off[l] * NP; };
-    auto Ux = [&](int l) { return uh + (size_t)p->lvl_off[l] * NP; };
-    auto Qm = [&](int l) { return (void*)((char*)p->Qbox + (size_t)p->lvl_off[l] * 8); };
-    auto Cm = [&](int l) { return (void*)((char*)p->Cbox + (size_t)p->lvl_off[l] * 8); };
+    using V8 = char[8];
+    auto Qx = [&](int l, int v) { return (T*)b.q + v * b.vq + (size_t)p->lvl_off[l] * NP; };
+    auto Ux = [&](int l, int v) { return (T*)b.u + v * b.vq + (size_t)p->lvl_off[l] * NP; };
+    auto Qm = [&](int l, int v) { return (void*)((V8*)b.Q + v * b.vQ + (size_t)p->lvl_off[l]); };
+    auto Cm = [&](int l, int v) { return (void*)((V8*)b.C + v * b.vQ + (size_t)p->lvl_off[l]); };
     LevelBufs lb;
     for (int l = std::min(2, L); l <= L && l < 16; ++l) {
-        lb.q[l] = Qx(l);
-        lb.u[l] = Ux(l);
-        lb.Q[l] = Qm(l);
-        lb.C[l] = Cm(l);
+        lb.q[l] = Qx(l, 0);
+        lb.u[l] = Ux(l, 0);
+        lb.Q[l] = Qm(l, 0);
+        lb.C[l] = Cm(l, 0);
     }
+    lb.nvec = b.nvec;
+    lb.vq = b.vq;
+    lb.vQ = b.vQ;
     unsigned* gsync = (unsigned*)(p->status + 1);  // grid-barrier words beside the status word
     {
         PhaseTimer pt(LFMM_PHASE_M2M, s);
         if (L >= 3 && launch_m2m_fused<T>(ops, L, lb, gsync, p->status, p->num_sms, s) == cudaSuccess) {
             pt.add_launches(1);
         } else {
-            for (int l = L - 1; l >= 2; --l) {
-                LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, l, Qx(l + 1), Qm(l + 1), Qx(l), Qm(l), s));
-                pt.add_launches(1);
-            }
+            for (int v = 0; v < b.nvec; ++v)
+                for (int l = L - 1; l >= 2; --l) {
+                    LFMM_CUDA_TRY(launch_m2m<T>(ops, L - l, l, Qx(l + 1, v), Qm(l + 1, v), Qx(l, v), Qm(l, v), s));
+                    pt.add_launches(1);
+                }
         }
     }
     int l_first = 2;  // first level left for the per-level M2L launches
@@ -526,16 +548,19 @@ int far_sweeps(lfmm_plan* p, cudaStream_t s, Hook before_fine) {
         PhaseTimer pt(tc ? LFMM_PHASE_M2L_TC : LFMM_PHASE_M2L, s);
         if constexpr (sizeof(T) == 4) {
             if (tc) {
-                LFMM_CUDA_TRY(launch_m2l_tma(ops, L - l, l, (const float*)Qx(l), Qm(l),
-                                             l >= 3 ? (const float*)Ux(l - 1) : nullptr, l >= 3 ? Cm(l - 1) : nullptr,
-                                             (float*)Ux(l), Cm(l), (float*)p->tc_split, p->status, p->num_sms, s));
+                LFMM_CUDA_TRY(launch_m2l_tma(ops, L - l, l, (const float*)Qx(l, 0), Qm(l, 0),
+                                             l >= 3 ? (const float*)Ux(l - 1, 0) : nullptr,
+                                             l >= 3 ? Cm(l - 1, 0) : nullptr, (float*)Ux(l, 0), Cm(l, 0), b.split,
+                                             p->status, p->num_sms, s, b.nvec, b.vq, b.vQ));
                 pt.add_launches(l >= 3 ? 3 : 2);
                 continue;
             }
         }
-        LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l), Qm(l), l >= 3 ? Ux(l - 1) : nullptr,
-                                    l >= 3 ? Cm(l - 1) : nullptr, Ux(l), Cm(l), s));
-        pt.add_launches(1);
+        for (int v = 0; v < b.nvec; ++v) {
+            LFMM_CUDA_TRY(launch_m2l<T>(ops, L - l, l, Qx(l, v), Qm(l, v), l >= 3 ? Ux(l - 1, v) : nullptr,
+                                        l >= 3 ? Cm(l - 1, v) : nullptr, Ux(l, v), Cm(l, v), s));
+            pt.add_launches(1);
+        }
     }
     return LFMM_OK;
 }
@@ -581,7 +606,7 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         return LFMM_OK;
     };
     {
-        const int st = far_sweeps<T>(p, s, near);
+        const int st = far_sweeps<T>(p, plan_far_bufs(p), s, near);
         if (st) return st;
     }
     if (split) {
@@ -606,10 +631,15 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     return LFMM_OK;
 }
 
-// k charge vectors on one uniform plan: per vector P2M, the far-field sweeps and L2P
-// (the expansion arrays are reused vector after vector), then the near field of all
-// vectors in passes of four that share each table lookup, then one binary64 sum.
-// Every vector's arithmetic is that of lfmm_eval, so the results are bit-identical.
+// Charge vectors evaluated together by lfmm_eval_multi (the per-vector buffers hold
+// this many).
+constexpr int kMultiGroup = 16;
+
+// k charge vectors on one uniform plan, in groups of up to kMultiGroup: P2M, the
+// far-field sweeps and L2P take a group's vectors in one launch each (per-vector
+// expansion arrays), the near field four vectors per pass sharing each table lookup,
+// and one binary64 sum writes the group's results.  Every vector's arithmetic is that
+// of lfmm_eval, so the results are bit-identical.
 template <typename T>
 int eval_multi_impl(lfmm_plan* p, const double* F, int k, double* U, cudaStream_t s) {
     const int L = p->L;
@@ -624,36 +654,39 @@ int eval_multi_impl(lfmm_plan* p, const double* F, int k, double* U, cudaStream_
     const DeviceOps& ops = *p->ops;
     const int NP = p->NP;
     const size_t leaf_off = (size_t)p->lvl_off[L];
-    const int64_t n_leaf = (int64_t)1 << (2 * L);
-    T* q_leaf = (T*)p->qhat + leaf_off * NP;
-    T* u_leaf = (T*)p->uhat + leaf_off * NP;
-    void* Q_leaf = (char*)p->Qbox + leaf_off * 8;
-    void* C_leaf = (char*)p->Cbox + leaf_off * 8;
+    const int64_t vq = p->n_boxes * NP, vQ = p->n_boxes;
     T* fs = (T*)p->m_fsorted;
-    char* Qs = (char*)p->m_Q;
-    for (int r = 0; r < k; ++r) {
+    T* mq = (T*)p->m_qhat;
+    T* mu = (T*)p->m_uhat;
+    char* mQ = (char*)p->m_Q;
+    char* mC = (char*)p->m_C;
+    for (int r0 = 0; r0 < k; r0 += kMultiGroup) {
+        const int g = std::min(kMultiGroup, k - r0);
         {
             PhaseTimer pt(LFMM_PHASE_P2M, s);
-            LFMM_CUDA_TRY(launch_p2m<T>(t, ops, F + (size_t)r * p->ns, fs + (size_t)r * p->ns, q_leaf, Q_leaf, s));
+            LFMM_CUDA_TRY(launch_p2m<T>(t, ops, F + (size_t)r0 * p->ns, fs, mq + leaf_off * NP, mQ + leaf_off * 8, s,
+                                        g, vq, vQ));
             pt.add_launches(1);
         }
-        // the leaf charges of vector r, for the near-field constant
-        LFMM_CUDA_TRY(cudaMemcpyAsync(Qs + (size_t)r * n_leaf * 8, Q_leaf, (size_t)n_leaf * 8,
-                                      cudaMemcpyDeviceToDevice, s));
-        const int st = far_sweeps<T>(p, s, [] { return LFMM_OK; });
+        const FarBufs fb{mq, mu, mQ, mC, (float*)p->m_split, g, vq, vQ};
+        const int st = far_sweeps<T>(p, fb, s, [] { return LFMM_OK; });
         if (st) return st;
+        {
+            PhaseTimer pt(LFMM_PHASE_L2P, s);
+            LFMM_CUDA_TRY(launch_l2p<T>(t, ops, mu + leaf_off * NP, mC + leaf_off * 8, p->m_uf, s, g, vq, vQ));
+            pt.add_launches(1);
+        }
+        {
+            PhaseTimer pt(LFMM_PHASE_P2P, s);
+            LFMM_CUDA_TRY(launch_p2p_multi<T>(t, ops, g, fs, p->ns, mQ + leaf_off * 8, vQ, p->m_un, p->nt,
+                                              p->num_sms, s));
+            pt.add_launches((g + 3) / 4);
+        }
         PhaseTimer pt(LFMM_PHASE_L2P, s);
-        LFMM_CUDA_TRY(launch_l2p<T>(t, ops, u_leaf, C_leaf, p->m_uf + (size_t)r * p->nt, s));
+        LFMM_CUDA_TRY(launch_combine((int64_t)g * p->nt, p->m_un, p->m_uf, U + (size_t)r0 * p->nt, nullptr, nullptr,
+                                     s));
         pt.add_launches(1);
     }
-    {
-        PhaseTimer pt(LFMM_PHASE_P2P, s);
-        LFMM_CUDA_TRY(launch_p2p_multi<T>(t, ops, k, fs, p->ns, Qs, n_leaf, p->m_un, p->nt, p->num_sms, s));
-        pt.add_launches((k + 3) / 4);
-    }
-    PhaseTimer pt(LFMM_PHASE_L2P, s);
-    LFMM_CUDA_TRY(launch_combine((int64_t)k * p->nt, p->m_un, p->m_uf, U, nullptr, nullptr, s));
-    pt.add_launches(1);
     return LFMM_OK;
 }
 
@@ -897,19 +930,30 @@ int lfmm_eval_multi(lfmm_plan* p, const double* F, int32_t k, double* U, void* s
     p->last_stream = s;
     int st;
     const bool uniform = !p->forest && p->L >= 2 && p->un_tmp;
-    if (uniform && p->multi_cap < k) {
-        // grow the per-vector buffers (the old ones are released in stream order)
+    const int group = std::min(k, kMultiGroup);
+    if (uniform && p->multi_cap < group) {
+        // per-vector buffers for one group (allocated once per plan and size)
         const size_t esz = p->opts.precision == LFMM_MIXED ? sizeof(float) : sizeof(double);
-        const int64_t n_leaf = (int64_t)1 << (2 * p->L);
-        void *a, *b, *c;
-        if ((st = palloc(p, &a, (size_t)k * p->ns * esz, s))) return st;
-        if ((st = palloc(p, &b, (size_t)k * n_leaf * 8, s))) return st;
-        if ((st = palloc(p, &c, (size_t)2 * k * p->nt * sizeof(double), s))) return st;
+        const size_t g = (size_t)group;
+        const size_t split = p->tc_split ? ((size_t)p->NP << (2 * p->L)) * 2 + ((size_t)p->NP << (2 * (p->L - 1))) * 2
+                                         : 0;
+        void *a, *bq, *bu, *bQ, *bC, *c, *d = nullptr;
+        if ((st = palloc(p, &a, g * p->ns * esz, s))) return st;
+        if ((st = palloc(p, &bq, g * p->n_boxes * p->NP * esz, s))) return st;
+        if ((st = palloc(p, &bu, g * p->n_boxes * p->NP * esz, s))) return st;
+        if ((st = palloc(p, &bQ, g * p->n_boxes * 8, s))) return st;
+        if ((st = palloc(p, &bC, g * p->n_boxes * 8, s))) return st;
+        if ((st = palloc(p, &c, (size_t)2 * g * p->nt * sizeof(double), s))) return st;
+        if (split && (st = palloc(p, &d, g * split * sizeof(float), s))) return st;
         p->m_fsorted = a;
-        p->m_Q = b;
+        p->m_qhat = bq;
+        p->m_uhat = bu;
+        p->m_Q = bQ;
+        p->m_C = bC;
+        p->m_split = d;
         p->m_un = (double*)c;
-        p->m_uf = p->m_un + (size_t)k * p->nt;
-        p->multi_cap = k;
+        p->m_uf = p->m_un + g * p->nt;
+        p->multi_cap = group;
     }
     const double* Fd = F;
     double* Ud = U;

@@ -49,14 +49,21 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                                                   T* __restrict__ f_sorted,
                                                   const T* __restrict__ tofsT, int side,
                                                   T* __restrict__ qhat,
-                                                  typename Mono<T>::V* __restrict__ Q) {
+                                                  typename Mono<T>::V* __restrict__ Q, int nvec, int64_t ns,
+                                                  int64_t vq, int64_t vQ) {
     using M = Mono<T>;
     constexpr int G = 16, PL = NP / G;
     using Row = VecT<T, PL>;
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & (G - 1);
     const int64_t n_leaves = (int64_t)1 << (2 * L);
+    const int64_t n_pairs = (n_leaves + 1) >> 1;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t pair = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; 2 * pair < n_leaves; pair += nw) {
+    // (charge vector, leaf pair): vector v reads f + v ns, writes f_sorted + v ns,
+    // qhat + v vq and Q + v vQ
+    for (int64_t pv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pv < n_pairs * nvec; pv += nw) {
+        const int64_t v = pv / n_pairs, pair = pv - v * n_pairs;
+        const double* fv = f + v * ns;
+        T* fsv = f_sorted + v * ns;
         const int64_t leaf = 2 * pair + half;
         const bool lv = leaf < n_leaves;
         const int b = lv ? begin[leaf] : 0, cnt = lv ? begin[leaf + 1] - b : 0;
@@ -72,9 +79,9 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                 const int j = b + j0 + hl;
                 const int l = loc[j];
                 J = (l & 0xffff) + side * (l >> 16);
-                const double fd = f[perm[j]];
+                const double fd = fv[perm[j]];
                 fj = (T)fd;
-                f_sorted[j] = fj;
+                fsv[j] = fj;
                 qsum = M::add(qsum, M::from_double(fd));
             }
             const int cc = min(G, cmax - j0);
@@ -92,12 +99,12 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
             Row o;
 #pragma unroll
             for (int i = 0; i < PL; ++i) o.v[i] = acc[i];
-            *reinterpret_cast<Row*>(qhat + (size_t)mort * NP + hl * PL) = o;
+            *reinterpret_cast<Row*>(qhat + v * vq + (size_t)mort * NP + hl * PL) = o;
         }
         // sum of the compensated partial charges over the half
 #pragma unroll
         for (int off = 8; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
-        if (lv && hl == 0) Q[morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L))] = qsum;
+        if (lv && hl == 0) Q[v * vQ + morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L))] = qsum;
     }
 }
 
@@ -502,30 +509,34 @@ template <typename T, int NP>
 __device__ __forceinline__ void m2m_parents(int level, const T* __restrict__ qc, const T* __restrict__ op,
                                             const typename Mono<T>::V* __restrict__ Qin, T* __restrict__ qp,
                                             typename Mono<T>::V* __restrict__ Qout, int64_t warp_id,
-                                            int64_t n_warps) {
+                                            int64_t n_warps, int nvec = 1, int64_t vq = 0, int64_t vQ = 0) {
     using M = Mono<T>;
     constexpr int CL = 4 * NP / 32, PL = NP / 32;
     const int lane = threadIdx.x & 31;
     const int64_t n_parent = (int64_t)1 << (2 * level);
+    const int64_t n_items = n_parent * nvec;  // (charge vector, parent); vector v's arrays at v vq / v vQ
     // software pipeline: the next parent's children and charges are loaded while this
     // parent is computed
     T nx[CL];
     typename M::V nq = M::zero();
-    if (warp_id < n_parent) {
+    if (warp_id < n_items) {
+        const int64_t v = warp_id / n_parent, pr = warp_id - v * n_parent;
 #pragma unroll
-        for (int c = 0; c < CL; ++c) nx[c] = ldcg(qc + (size_t)warp_id * 4 * NP + lane + 32 * c);
-        if (lane < 4) nq = ldcg(Qin + 4 * warp_id + lane);
+        for (int c = 0; c < CL; ++c) nx[c] = ldcg(qc + v * vq + (size_t)pr * 4 * NP + lane + 32 * c);
+        if (lane < 4) nq = ldcg(Qin + v * vQ + 4 * pr + lane);
     }
-    for (int64_t par = warp_id; par < n_parent; par += n_warps) {
+    for (int64_t item = warp_id; item < n_items; item += n_warps) {
+        const int64_t vv = item / n_parent, par = item - vv * n_parent;
         T xv[CL];
 #pragma unroll
         for (int c = 0; c < CL; ++c) xv[c] = nx[c];
         typename M::V qv = nq;
-        const int64_t nxt = par + n_warps;
-        if (nxt < n_parent) {
+        const int64_t nxt = item + n_warps;
+        if (nxt < n_items) {
+            const int64_t v = nxt / n_parent, pr = nxt - v * n_parent;
 #pragma unroll
-            for (int c = 0; c < CL; ++c) nx[c] = ldcg(qc + (size_t)nxt * 4 * NP + lane + 32 * c);
-            if (lane < 4) nq = ldcg(Qin + 4 * nxt + lane);
+            for (int c = 0; c < CL; ++c) nx[c] = ldcg(qc + v * vq + (size_t)pr * 4 * NP + lane + 32 * c);
+            if (lane < 4) nq = ldcg(Qin + v * vQ + 4 * pr + lane);
         }
         // one accumulator chain per 32-wide input chunk, added at the end
         T acc[CL][PL];
@@ -548,12 +559,12 @@ __device__ __forceinline__ void m2m_parents(int level, const T* __restrict__ qc,
             T a = acc[0][i];
 #pragma unroll
             for (int c = 1; c < CL; ++c) a += acc[c][i];
-            qp[(size_t)par * NP + lane + 32 * i] = a;
+            qp[vv * vq + (size_t)par * NP + lane + 32 * i] = a;
         }
         // total charge of the parent: lanes 0..3 hold the children's, all lanes shuffle
         qv = M::add(qv, shfl_xor_v(qv, 1));
         qv = M::add(qv, shfl_xor_v(qv, 2));
-        if (lane == 0) Qout[par] = qv;
+        if (lane == 0) Qout[vv * vQ + par] = qv;
     }
 }
 
@@ -1145,6 +1156,8 @@ struct LevelPtrs {
     const T* l2l[kMaxLevels];    // [4][NP][NP] from level l-1 to level l
     const T* m2m[kMaxLevels];    // [4NP][NP] from level l+1 to level l
     int64_t item_off[kMaxLevels + 1];  // downward: first M2L work item of level l0 + i
+    int nvec;                          // charge vectors; vector v's arrays at v vq (q, u) / v vQ (Q, C)
+    int64_t vq, vQ;
 };
 
 // Grid-wide barrier of a cooperative launch.  count and gen are plan-owned device words
@@ -1193,7 +1206,7 @@ __global__ void __launch_bounds__(256) m2m_up_kernel(LevelPtrs<T> P, int l_top, 
             __syncthreads();
             op = sop;
         }
-        m2m_parents<T, NP>(l, P.q[l + 1], op, P.Q[l + 1], P.q[l], P.Q[l], wid, nw);
+        m2m_parents<T, NP>(l, P.q[l + 1], op, P.Q[l + 1], P.q[l], P.Q[l], wid, nw, P.nvec, P.vq, P.vQ);
         if (l > l_bot) grid_barrier(sync, sync + 1, status);
     }
 }
@@ -1213,16 +1226,17 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
     constexpr int PL = NP / 32;
     const int nl = l1 - l0 + 1;
     const int64_t n_items = P.item_off[nl];
-    // M2L part of every level: work item = (level, class, 32-box tile)
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    // M2L part of every level: work item = (charge vector, level, class, 32-box tile)
+    for (int64_t it = blockIdx.x; it < n_items * P.nvec; it += gridDim.x) {
+        const int64_t v = it / n_items, item = it - v * n_items;
         int i = 0;
         while (item >= P.item_off[i + 1]) ++i;
         const int l = l0 + i;
         const int64_t tiles = (((int64_t)1 << (2 * (l - 1))) + 31) / 32;
         const int64_t local = item - P.item_off[i];
-        m2l_splitk_tile<T, NP, FusedCfg<T, NP>::WARPS>(l, (int)(local / tiles), local % tiles, P.q[l], nullptr,
-                                                       P.tifo[l], nullptr, P.mono[l], P.Q[l], nullptr, P.u[l],
-                                                       P.C[l]);
+        m2l_splitk_tile<T, NP, FusedCfg<T, NP>::WARPS>(l, (int)(local / tiles), local % tiles, P.q[l] + v * P.vq,
+                                                       nullptr, P.tifo[l], nullptr, P.mono[l], P.Q[l] + v * P.vQ,
+                                                       nullptr, P.u[l] + v * P.vq, P.C[l] + v * P.vQ);
     }
     if (nl == 1) return;
     grid_barrier(sync, sync + 1, status);
@@ -1233,31 +1247,36 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int l = l0 + 1; l <= l1; ++l) {
         const int64_t nb = (int64_t)1 << (2 * l);
-        const T* up = P.u[l - 1];
+        const int64_t n_box_items = nb * P.nvec;  // (charge vector, child box)
         // software pipeline over the boxes: the next box's rows load during this one
         T npv[PL], nacc[PL];
-        if (wid < nb) {
+        if (wid < n_box_items) {
+            const int64_t v = wid / nb, bb = wid - v * nb;
 #pragma unroll
             for (int i = 0; i < PL; ++i) {
-                npv[i] = ldcg(up + (size_t)(wid >> 2) * NP + lane + 32 * i);
-                nacc[i] = ldcg(P.u[l] + (size_t)wid * NP + lane + 32 * i);
+                npv[i] = ldcg(P.u[l - 1] + v * P.vq + (size_t)(bb >> 2) * NP + lane + 32 * i);
+                nacc[i] = ldcg(P.u[l] + v * P.vq + (size_t)bb * NP + lane + 32 * i);
             }
         }
-        for (int64_t b = wid; b < nb; b += nw) {
+        for (int64_t item = wid; item < n_box_items; item += nw) {
+            const int64_t vv = item / nb, b = item - vv * nb;
             const int64_t par = b >> 2;
             const int c = (int)(b & 3);  // Morton: child index = parity class (cx + 2 cy)
             const T* op = P.l2l[l] + (size_t)c * NP * NP;
+            T* ul = P.u[l] + vv * P.vq;
+            typename M::V* Cl = P.C[l] + vv * P.vQ;
             T pv[PL], acc[PL];
 #pragma unroll
             for (int i = 0; i < PL; ++i) {
                 pv[i] = npv[i];
                 acc[i] = nacc[i];
             }
-            if (b + nw < nb) {
+            if (item + nw < n_box_items) {
+                const int64_t v = (item + nw) / nb, bb = (item + nw) - v * nb;
 #pragma unroll
                 for (int i = 0; i < PL; ++i) {
-                    npv[i] = ldcg(up + (size_t)((b + nw) >> 2) * NP + lane + 32 * i);
-                    nacc[i] = ldcg(P.u[l] + (size_t)(b + nw) * NP + lane + 32 * i);
+                    npv[i] = ldcg(P.u[l - 1] + v * P.vq + (size_t)(bb >> 2) * NP + lane + 32 * i);
+                    nacc[i] = ldcg(P.u[l] + v * P.vq + (size_t)bb * NP + lane + 32 * i);
                 }
             }
 #pragma unroll
@@ -1270,8 +1289,8 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
                     for (int o = 0; o < PL; ++o) acc[o] = fma(ldg(row + lane + 32 * o), v, acc[o]);
                 }
 #pragma unroll
-            for (int i = 0; i < PL; ++i) P.u[l][(size_t)b * NP + lane + 32 * i] = acc[i];
-            if (lane == 0) P.C[l][b] = M::add(ldcg(P.C[l] + b), ldcg(P.C[l - 1] + par));
+            for (int i = 0; i < PL; ++i) ul[(size_t)b * NP + lane + 32 * i] = acc[i];
+            if (lane == 0) Cl[b] = M::add(ldcg(Cl + b), ldcg(P.C[l - 1] + vv * P.vQ + par));
         }
         if (l < l1) grid_barrier(sync, sync + 1, status);
     }
@@ -1288,7 +1307,8 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
                                                   const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
                                                   const T* __restrict__ uhat,
                                                   const typename Mono<T>::V* __restrict__ Cleaf,
-                                                  const T* __restrict__ tofsT, double* __restrict__ uf) {
+                                                  const T* __restrict__ tofsT, double* __restrict__ uf, int nvec,
+                                                  int64_t vq, int64_t vQ) {
     using M = Mono<T>;
     constexpr int E = (int)(16 / sizeof(T));
     constexpr int RS = NP + 1;
@@ -1299,12 +1319,15 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
         for (int i = threadIdx.x; i < rows * NP; i += blockDim.x) st[(i / NP) * RS + (i % NP)] = tofsT[i];
         __syncthreads();
     }
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+    // (charge vector, target): vector v reads uhat + v vq, Cleaf + v vQ, writes uf + v nt
+    for (int64_t tv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tv < nt * nvec;
+         tv += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = tv / nt, t = tv - v * nt;
         const int leaf = tleaf[t];
         const int l = tloc[t];
         const int J = (l & 0xffff) + side * (l >> 16);
         const T* row = SMEM ? st + J * RS : tofsT + (size_t)J * NP;  // (table too large: L1 / L2)
-        const uint4* uh = reinterpret_cast<const uint4*>(uhat + (size_t)leaf * NP);
+        const uint4* uh = reinterpret_cast<const uint4*>(uhat + v * vq + (size_t)leaf * NP);
         T far = T(0);
 #pragma unroll
         for (int c = 0; c < NP / E; ++c) {
@@ -1313,7 +1336,7 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
 #pragma unroll
             for (int e = 0; e < E; ++e) far = fma(row[c * E + e], v[e], far);
         }
-        uf[tperm[t]] = (double)far + M::to_double(Cleaf[leaf]);
+        uf[v * nt + tperm[t]] = (double)far + M::to_double(Cleaf[v * vQ + leaf]);
     }
 }
 
@@ -1333,18 +1356,20 @@ __global__ void combine_kernel(int64_t n, const double* __restrict__ un, const d
 // ------------------------------------------------------------------------- launchers
 template <typename T>
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
-                       T* qhat_leaf, void* Q, cudaStream_t s) {
+                       T* qhat_leaf, void* Q, cudaStream_t s, int nvec, int64_t vq, int64_t vQ) {
     const int threads = 256;
-    int64_t blocks = (t.n_leaves * 16 + threads - 1) / threads;
+    int64_t blocks = (t.n_leaves * 16 * nvec + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
     using V = typename Mono<T>::V;
     if (ops.NP == 32)
         p2m_kernel<T, 32><<<(int)blocks, threads, 0, s>>>(t.L, t.src_begin, t.src_loc, t.src_perm, f, f_sorted,
-                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q);
+                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q, nvec,
+                                                          t.n_src_all, vq, vQ);
     else
         p2m_kernel<T, 64><<<(int)blocks, threads, 0, s>>>(t.L, t.src_begin, t.src_loc, t.src_perm, f, f_sorted,
-                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q);
+                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q, nvec,
+                                                          t.n_src_all, vq, vQ);
     return cudaGetLastError();
 }
 
@@ -1572,6 +1597,9 @@ static void fill_levels(LevelPtrs<T>& P, const DeviceOps& ops, int L, const Leve
             if (k >= 1) P.m2m[l] = (const T*)ops.m2m[k];
         }
     }
+    P.nvec = b.nvec;
+    P.vq = b.vq;
+    P.vQ = b.vQ;
 }
 
 // Cooperative launch (all blocks co-resident, as the grid barrier needs) through the
@@ -1655,7 +1683,7 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
 
 template <typename T>
 cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_leaf, const void* Cleaf, double* uf,
-                       cudaStream_t s) {
+                       cudaStream_t s, int nvec, int64_t vq, int64_t vQ) {
     using V = typename Mono<T>::V;
     if (!t.tgt_leaf) return cudaErrorInvalidValue;
     const size_t table = (size_t)t.side * t.side * (ops.NP + 1) * sizeof(T);
@@ -1668,12 +1696,13 @@ cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_le
         cudaError_t e = ensure_dynamic_smem(fn, smem);
         if (e != cudaSuccess) return e;
         // persistent: each block stages the table once
-        int64_t blocks = (t.n_tgt + 255) / 256;
+        int64_t blocks = (t.n_tgt * nvec + 255) / 256;
         const int64_t cap = (int64_t)152 * blocks_per_sm(fn, 256, smem);
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
         l2p_kernel<T, NPc, SM><<<(int)blocks, 256, smem, s>>>(t.n_tgt, t.side, t.tgt_leaf, t.tgt_loc, t.tgt_perm,
-                                                              uhat_leaf, (const V*)Cleaf, (const T*)ops.tofsT, uf);
+                                                              uhat_leaf, (const V*)Cleaf, (const T*)ops.tofsT, uf,
+                                                              nvec, vq, vQ);
         return cudaGetLastError();
     };
     using I32 = std::integral_constant<int, 32>;
@@ -1699,9 +1728,9 @@ cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double
     template cudaError_t launch_m2l_fused<T>(const DeviceOps&, int, const LevelBufs&, int, unsigned*, int*, int, \
                                              int*, cudaStream_t);                                            \
     template cudaError_t launch_l2p<T>(const TreeView&, const DeviceOps&, const T*, const void*, double*,          \
-                                       cudaStream_t);                                                        \
+                                       cudaStream_t, int, int64_t, int64_t);                                  \
     template cudaError_t launch_p2m<T>(const TreeView&, const DeviceOps&, const double*, T*, T*, void*,       \
-                                       cudaStream_t);                                                         \
+                                       cudaStream_t, int, int64_t, int64_t);                                  \
     template cudaError_t launch_m2m<T>(const DeviceOps&, int, int, const T*, const void*, T*, void*,         \
                                        cudaStream_t);                                                         \
     template cudaError_t launch_m2l<T>(const DeviceOps&, int, int, const T*, const void*, const T*,          \

@@ -183,6 +183,7 @@ struct TreeView {
     const int32_t* tgt_perm = nullptr;
     const int32_t* tgt_leaf = nullptr;   // Morton index of each sorted target's leaf
     int64_t n_tgt = 0;         // targets
+    int64_t n_src_all = 0;     // sources
     int max_leaf_src = 0;      // largest leaf occupancies (size the P2P staging)
     int max_leaf_tgt = 0;
 };
@@ -288,12 +289,15 @@ cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0,
 // Per-box scalars Q (total charge) and C (incoming constant) are 8 bytes per box:
 // a float (hi, lo) pair on the mixed path, a double on the binary64 path.
 template <typename T>
+// nvec charge vectors: vector v reads f + v n_src, writes f_sorted + v n_src and the
+// leaf expansions / charges v vq / v vQ elements after vector 0's.
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
-                       T* qhat_leaf, void* Q_leaf, cudaStream_t s);
+                       T* qhat_leaf, void* Q_leaf, cudaStream_t s, int nvec = 1, int64_t vq = 0, int64_t vQ = 0);
 // Far field of every target (L2P + incoming constant), binary64, caller order.
 template <typename T>
+// (nvec vectors: uhat / Cleaf of vector v at v vq / v vQ elements, uf at v n_tgt.)
 cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_leaf, const void* Cleaf, double* uf,
-                       cudaStream_t s);
+                       cudaStream_t s, int nvec = 1, int64_t vq = 0, int64_t vQ = 0);
 // u = un + uf elementwise (and the parts, where requested; any output may be null).
 cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double* u, double* u_near, double* u_far,
                            cudaStream_t s);
@@ -306,6 +310,10 @@ struct LevelBufs {
     void* u[16] = {nullptr};
     void* Q[16] = {nullptr};
     void* C[16] = {nullptr};
+    // charge vectors evaluated together: vector v's arrays start v vq elements (q, u)
+    // and v vQ elements (Q, C) after vector 0's
+    int nvec = 1;
+    int64_t vq = 0, vQ = 0;
 };
 // M2M of levels L-1 .. 2 in one cooperative launch (grid barriers between levels).
 // sync: two zero device words (barrier state).  Returns an error (nothing launched)
@@ -336,9 +344,11 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
 // splits the level's expansions and the parent's into TF32 hi / lo layouts in `split`
 // (8 np^2 + 2 np^2 rows of 32 floats, np = 2^(level-1)), then one persistent launch fed
 // by tiled TMA loads; a timed-out wait is reported in *status.
+// nvec charge vectors at once: vector v's arrays start v vq floats (q, u) and v vQ
+// value pairs (Q, C) after vector 0's; `split` then holds nvec times the rows.
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
-                           int* status, int num_sms, cudaStream_t s);
+                           int* status, int num_sms, cudaStream_t s, int nvec = 1, int64_t vq = 0, int64_t vQ = 0);
 // Near field of k charge vectors (vector r: f_sorted + r f_stride, Qleaf + r q_stride,
 // out u_near + r u_stride), four vectors per pass sharing each table lookup.
 template <typename T>

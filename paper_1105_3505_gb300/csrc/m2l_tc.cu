@@ -203,6 +203,8 @@ struct TmaGeo {
     int tiles_per_class;
     int n_tiles;          // 4 classes x tiles_per_class
     int has_l2l;
+    int nvec;             // charge vectors: vector v's expansions at v vq floats, charges /
+    long long vq, vQ;     // constants at v vQ pairs; its split layouts at TMA index 2v + hl
 };
 
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3, int c4,
@@ -241,8 +243,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     const int np = 1 << g.lg, side = 2 << g.lg;
     const int rows = g.TX * g.TY;
     const uint32_t tx_bytes = 2u * (uint32_t)rows * 128u + 8192u;
-    const int my_tiles = blockIdx.x < (unsigned)g.n_tiles ? (g.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = my_tiles * n_steps;  // K-steps of this CTA (< 2^31: n_tiles <= 4^14 / 128)
+    const int all_tiles = g.n_tiles * g.nvec;
+    const int my_tiles = blockIdx.x < (unsigned)all_tiles ? (all_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * n_steps;  // K-steps of this CTA
     volatile int* vabort = &s_abort;
 
     if (threadIdx.x == 0) {
@@ -282,12 +285,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         atomicExch(&s_abort, 1);
         atomicExch(status, LFMM_ETIMEOUT);
     };
-    // it-th tile of this CTA: t = blockIdx.x + it * gridDim.x; class t & 3 (classes
-    // interleave for balance), then row-major tiles of the class
-    auto tile_of = [&](int it, int& cls, int& ri0, int& rj0) {
+    // it-th tile of this CTA: t = blockIdx.x + it * gridDim.x; charge vector t / n_tiles,
+    // then class (t mod n_tiles) & 3 (classes interleave for balance) and row-major tiles
+    // of the class
+    auto tile_of = [&](int it, int& cls, int& ri0, int& rj0, int& v) {
         const int t = (int)blockIdx.x + it * (int)gridDim.x;
-        cls = t & 3;
-        const int k = t >> 2;
+        v = t / g.n_tiles;
+        const int tt = t - v * g.n_tiles;
+        cls = tt & 3;
+        const int k = tt >> 2;
         ri0 = (k % g.tiles_x) * g.TX;
         rj0 = (k / g.tiles_x) * g.TY;
     };
@@ -298,8 +304,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     if (warp == 4) {
         if (lane == 0) {
             int it = 0, st = 0, slot = 0, use = 0;
-            int cls = 0, ri0 = 0, rj0 = 0;
-            tile_of(0, cls, ri0, rj0);
+            int cls = 0, ri0 = 0, rj0 = 0, v = 0;
+            tile_of(0, cls, ri0, rj0, v);
             for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
                 if (use > 0 && !mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1))) {
@@ -311,12 +317,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                 if (st < 27) {
                     const int sx = (cls & 1) + s_off[cls][st][0], sy = (cls >> 1) + s_off[cls][st][1];
                     const int plane = (sx & 1) + 2 * (sy & 1);
-                    tma_load_5d(sa, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 0, &full[slot]);
-                    tma_load_5d(sa + kTmaABytes, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 1, &full[slot]);
+                    tma_load_5d(sa, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 2 * v, &full[slot]);
+                    tma_load_5d(sa + kTmaABytes, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 2 * v + 1,
+                                &full[slot]);
                     bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)s_off[cls][st][2] * 2048, 8192, &full[slot]);
                 } else {
-                    tma_load_4d(sa, &tm_u, ri0, rj0, 0, &full[slot]);
-                    tma_load_4d(sa + kTmaABytes, &tm_u, ri0, rj0, 1, &full[slot]);
+                    tma_load_4d(sa, &tm_u, ri0, rj0, 2 * v, &full[slot]);
+                    tma_load_4d(sa + kTmaABytes, &tm_u, ri0, rj0, 2 * v + 1, &full[slot]);
                     bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)(kNumOffsets + cls) * 2048, 8192, &full[slot]);
                 }
                 s_issued[0] = gs + 1;
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                 }
                 if (++st == n_steps) {
                     st = 0;
-                    if (++it < my_tiles) tile_of(it, cls, ri0, rj0);
+                    if (++it < my_tiles) tile_of(it, cls, ri0, rj0, v);
                 }
             }
         }
@@ -369,18 +376,19 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         }
     } else if (warp == 6) {
         for (int it = 0; it < my_tiles; ++it) {
-            int cls, ri0, rj0;
-            tile_of(it, cls, ri0, rj0);
+            int cls, ri0, rj0, v;
+            tile_of(it, cls, ri0, rj0, v);
             const int px = cls & 1, py = cls >> 1;
+            const DFv* Qv = Qin + v * g.vQ;
             for (int r = lane; r < rows; r += 32) {
                 const int ri = ri0 + r % g.TX, rj = rj0 + r / g.TX;
-                DFv sacc = g.has_l2l ? Cpar[(size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
+                DFv sacc = g.has_l2l ? Cpar[v * g.vQ + (size_t)morton2(ri, rj)] : DFv{0.f, 0.f};
                 for (int k0 = 0; k0 < 27; k0 += 9) {  // nine loads in flight at a time
                     DFv qv[9];
 #pragma unroll
                     for (int k = 0; k < 9; ++k) {
                         const int sx = 2 * ri + px + s_off[cls][k0 + k][0], sy = 2 * rj + py + s_off[cls][k0 + k][1];
-                        qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qin[morton2(sx, sy)]
+                        qv[k] = (sx >= 0 && sx < side && sy >= 0 && sy < side) ? Qv[morton2(sx, sy)]
                                                                                  : DFv{0.f, 0.f};
                     }
 #pragma unroll
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                         sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
                     }
                 }
-                Cout[morton2(2 * ri + px, 2 * rj + py)] = sacc;
+                Cout[v * g.vQ + morton2(2 * ri + px, 2 * rj + py)] = sacc;
             }
         }
     } else {
@@ -401,11 +409,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] = 0.f;
         int it = 0, st = 0, d = 0, du = 0;
-        int cls = 0, ri = 0, rj = 0;
+        int cls = 0, ri = 0, rj = 0, v = 0;
         for (int gs = 0; gs < total; ++gs) {
             if (st == 0) {
                 int ri0, rj0;
-                tile_of(it, cls, ri0, rj0);
+                tile_of(it, cls, ri0, rj0, v);
                 ri = ri0 + xl;
                 rj = rj0 + yl;
             }
@@ -428,7 +436,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
             if (st == n_steps - 1) {
                 if (valid) {
                     float4* dst = reinterpret_cast<float4*>(
-                        out + (size_t)morton2(2 * ri + (cls & 1), 2 * rj + (cls >> 1)) * NP);
+                        out + v * g.vq + (size_t)morton2(2 * ri + (cls & 1), 2 * rj + (cls >> 1)) * NP);
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
                         dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
@@ -466,12 +474,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 // hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
 // tensor maps describe: planes = 1 -> [hl][plane][y'][x'][32] (targets' level),
 // planes = 0 -> [hl][y][x][32] (parent level, row-major).  One float4 per thread.
-__global__ void split_tf32_layout_kernel(const float4* __restrict__ x, float4* __restrict__ dst, int lg,
-                                         int planes) {
+__global__ void split_tf32_layout_kernel(const float4* __restrict__ x0, float4* __restrict__ dst0, int lg,
+                                         int planes, int nvec, int64_t vq4) {
     const int np = 1 << lg;
     const int64_t nb = planes ? (int64_t)4 << (2 * lg) : (int64_t)1 << (2 * lg);  // boxes
     const int64_t n4 = nb * 8;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    // vector vec: input at x0 + vec vq4, output (hi then lo) at dst0 + 2 vec n4
+    for (int64_t iv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; iv < n4 * nvec;
+         iv += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vec = iv / n4, i = iv - vec * n4;
+        const float4* x = x0 + vec * vq4;
+        float4* dst = dst0 + 2 * vec * n4;
         const int64_t b = i >> 3;
         const int c = (int)(i & 7);
         uint32_t bx, by;
@@ -536,21 +549,21 @@ bool encode_map(CUtensorMap* m, const float* base, int rank, const uint64_t* dim
 
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
-                           int* status, int num_sms, cudaStream_t s) {
+                           int* status, int num_sms, cudaStream_t s, int nvec, int64_t vq, int64_t vQ) {
     const int lg = level - 1;
     const int np = 1 << lg;
     const bool l2l = u_parent != nullptr;
-    float* qs = split;                                    // [2][4][np][np][32]
-    float* us = split + ((size_t)2 * 4 * np * np * 32);   // [2][np][np][32]
+    float* qs = split;                                           // [nvec][2][4][np][np][32]
+    float* us = split + ((size_t)nvec * 2 * 4 * np * np * 32);   // [nvec][2][np][np][32]
     auto grid_for = [&](int64_t n4) {
         int64_t b = (n4 + 255) / 256;
         return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
     };
-    split_tf32_layout_kernel<<<grid_for((int64_t)4 * np * np * 8), 256, 0, s>>>(
-        reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs), lg, 1);
+    split_tf32_layout_kernel<<<grid_for((int64_t)4 * np * np * 8 * nvec), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs), lg, 1, nvec, vq / 4);
     if (l2l)
-        split_tf32_layout_kernel<<<grid_for((int64_t)np * np * 8), 256, 0, s>>>(
-            reinterpret_cast<const float4*>(u_parent), reinterpret_cast<float4*>(us), lg, 0);
+        split_tf32_layout_kernel<<<grid_for((int64_t)np * np * 8 * nvec), 256, 0, s>>>(
+            reinterpret_cast<const float4*>(u_parent), reinterpret_cast<float4*>(us), lg, 0, nvec, vq / 4);
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -564,9 +577,12 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     g.tiles_per_class = g.tiles_x * (np / g.TY);
     g.n_tiles = 4 * g.tiles_per_class;
     g.has_l2l = l2l ? 1 : 0;
+    g.nvec = nvec;
+    g.vq = vq;
+    g.vQ = vQ;
     CUtensorMap mq, mu;
-    const uint64_t dq[5] = {32, (uint64_t)np, (uint64_t)np, 4, 2};
-    const uint64_t du[4] = {32, (uint64_t)np, (uint64_t)np, 2};
+    const uint64_t dq[5] = {32, (uint64_t)np, (uint64_t)np, 4, (uint64_t)(2 * nvec)};
+    const uint64_t du[4] = {32, (uint64_t)np, (uint64_t)np, (uint64_t)(2 * nvec)};
     if (!encode_map(&mq, qs, 5, dq, g.TX, g.TY)) return cudaErrorInvalidValue;
     if (!encode_map(&mu, l2l ? us : qs, 4, du, g.TX, g.TY)) return cudaErrorInvalidValue;
     constexpr size_t smem = 1024 + (size_t)kTmaStages * kTmaStageBytes;
@@ -574,7 +590,7 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
         cudaError_t e = ensure_dynamic_smem((const void*)m2l_tma_kernel, smem);
         if (e != cudaSuccess) return e;
     }
-    const int grid = std::min(g.n_tiles, num_sms);
+    const int grid = std::min(g.n_tiles * nvec, num_sms);
     m2l_tma_kernel<<<grid, kTmaThreads, smem, s>>>(mq, mu, g, (const float*)ops.tc[k], (const float*)ops.mono[k],
                                                    (const DFv*)Q_level, (const DFv*)C_parent, u_level,
                                                    (DFv*)C_level, status);

@@ -33,7 +33,7 @@ def charges(n, k, seed):
 def test_multi_equals_single(lfmm, precision, p):
     pr = {"mixed": lfmm.LFMM_MIXED, "fp64": lfmm.LFMM_FP64, "df": lfmm.LFMM_DF}[precision]
     prob = workloads.uniform_box(40000, 30000, 900, seed=17)
-    F = charges(prob.src.shape[0], 6, 3)
+    F = charges(prob.src.shape[0], 19, 3)  # more than one group of 16
     with lfmm.Plan(prob.src, prob.tgt, precision=pr, p=p) as pl:
         assert pl.info()["L"] >= 2
         U = pl.eval_multi(F)
