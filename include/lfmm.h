@@ -347,6 +347,21 @@ int64_t lfmm_launch_count(void);
  * computed by the one-dimensional integral of Remark 3.1 (t1 integrated in closed
  * form, composite Gauss-Legendre in t2).  1 <= R <= 256; out holds (R+1)(R+2)/2 doubles. */
 int lfmm_phi_table(int32_t R, double* out);
+/* phi near the origin for a symmetric lattice operator with constant coefficients,
+ * by the two-dimensional quadrature of Sec. 3.2 on the GPU (boxes of about one
+ * oscillation with 20 x 20 Gauss-Legendre rules, the singular centre box as a sum of
+ * annuli with Richardson extrapolation).  The operator is
+ *   (A u)(m) = sum_k w[k] (2 u(m) - u(m + d_k) - u(m - d_k)),  d_k = (d[2k], d[2k+1]),
+ * with 1 <= n_terms <= 8 distinct offsets (no two opposite), |d| <= 64, w[k] > 0, and two
+ * offsets of determinant +-1 (so that the symbol vanishes only at 0); the 5-point
+ * operator of eq. 1.2 is d = {1,0, 0,1}, w = {1, 1}.  Then A phi = delta_0, phi(0) = 0.
+ * With Q = sum_k w[k] d_k d_k', c = sqrt(det Q) / max(Q_11, Q_22) must be >= 1/8 (the
+ * pieces near the origin are split ceil(1/c) times per side; c = 1 for eq. 1.2).
+ * out: (2R+1)^2 doubles (host or device), out[(y + R)(2R+1) + x + R] = phi(x, y);
+ * R in [1, 64].  Runs on `stream` (this one needs the GPU); a host `out` is filled when
+ * the call returns.  LFMM_EINVAL for arguments outside these ranges (checked before any
+ * launch), LFMM_ECUDA for a failed launch or copy. */
+int lfmm_phi_quadrature(const int32_t* d, const double* w, int32_t n_terms, int32_t R, double* out, void* stream);
 
 /* phi at n integer offsets d = (dx0, dy0, dx1, dy1, ...): the table above for
  * |d|_inf <= 128, the asymptotic expansion eq. 3.1 beyond. */

@@ -96,6 +96,8 @@ __host__ __device__ inline void unmorton2(uint32_t m, uint32_t& bx, uint32_t& by
 }
 
 // ---------------------------------------------------------------- phi (host)
+// Gauss-Legendre nodes and weights on [-1, 1].
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // Library phi on the packed octant |m|_inf <= R by Remark 3.1 quadrature.
 std::vector<double> compute_phi_octant(int R);
 const std::vector<double>& phi_host_table();  // R = kPhiHostRadius, computed once

@@ -24,9 +24,9 @@
 namespace lfmm {
 
 namespace {
-
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kEulerGamma = 0.577215664901532860606512090082402431;
+}  // namespace
 
 // Gauss-Legendre nodes/weights on [-1, 1]: Newton iteration on the three-term
 // recurrence of the Legendre polynomials, started from Tricomi's approximation.
@@ -62,6 +62,8 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
         w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
     }
 }
+
+namespace {
 
 struct Neumaier {
     double s = 0.0, c = 0.0;

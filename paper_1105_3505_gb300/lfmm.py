@@ -83,6 +83,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_plan_set_flags": (ctypes.c_int, [vp, i32]),
         "lfmm_solve": (ctypes.c_int, [vp, i64, vp, i64, vp, vp, ctypes.POINTER(lfmm_opts), vp]),
         "lfmm_eval_multi": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+        "lfmm_phi_quadrature": (ctypes.c_int, [vp, vp, i32, i32, vp, vp]),
         "lfmm_plan_status": (ctypes.c_int, [vp, vp]),
         "lfmm_plan_get_info": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_plan_info)]),
         "lfmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -278,6 +279,17 @@ def lfmm_profile_read(reset: bool = False) -> dict:
 
 def lfmm_launch_count() -> int:
     return int(load().lfmm_launch_count())
+
+
+def lfmm_phi_quadrature(offsets, weights, R: int, stream=None) -> np.ndarray:
+    """phi of the operator sum_k w_k (2u(m) - u(m+d_k) - u(m-d_k)) on |m|_inf <= R by the
+    GPU quadrature; returns a (2R+1, 2R+1) array indexed [y + R, x + R]."""
+    d = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 2))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+    out = np.empty((2 * R + 1, 2 * R + 1), dtype=np.float64)
+    _check(load().lfmm_phi_quadrature(d.ctypes.data, w.ctypes.data, int(d.shape[0]), int(R), out.ctypes.data,
+                                      _stream_handle(stream)), "lfmm_phi_quadrature")
+    return out
 
 
 def lfmm_plan_set_flags(handle: int, flags: int) -> None:

@@ -112,3 +112,13 @@ def test_tune_cache_roundtrip_without_gpu(lib, tmp_path):
     lfmm.tune_cache_clear()
     lfmm.tune_cache_save(str(out))
     assert out.read_text() == ""
+
+
+def test_phi_quadrature_arguments_validated_without_gpu(lib):
+    for offsets, weights, R in [([[2, 0], [0, 2]], [1.0, 1.0], 4),   # does not connect the lattice
+                                ([[1, 0], [0, 1]], [1.0, -1.0], 4),  # negative conductivity
+                                ([[1, 0], [0, 1]], [1.0, 1.0], 65),  # radius out of range
+                                ([[0, 0], [0, 1]], [1.0, 1.0], 4),   # zero offset
+                                ([[1, 0], [0, 1]], [1.0, 1000.0], 4)]:  # too anisotropic
+        with pytest.raises(lfmm.LfmmError):
+            lfmm.lfmm_phi_quadrature(offsets, weights, R)
