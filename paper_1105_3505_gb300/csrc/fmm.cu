@@ -568,6 +568,74 @@ __device__ __forceinline__ void m2m_parents(int level, const T* __restrict__ qc,
     }
 }
 
+// M2M of one level in tiles of 64 parents (binary32, NP = 32, 256 threads): a tile's
+// children expansions (64 x 128 floats, contiguous in Morton order) are staged in
+// shared memory with a row stride of 132 floats, and thread t computes parents
+// 2 (t / 8) + {0, 1} of the tile at outputs 4 (t % 8) + {0..3}, so every step of the
+// 128-long contraction is two broadcast words, one 16-byte operator word and eight
+// multiply-adds.  Per output the products are summed exactly as in m2m_parents (one
+// chain per child in ascending input order, the chains added child by child), and the
+// parent's charge is the same pairwise sum, so both give bit-identical results.
+constexpr int kM2MTile = 64;
+constexpr int kM2MTileStride = 132;
+constexpr int64_t kM2MTileMinItems = 4096;  // fewer parents: the warp-per-parent path
+constexpr size_t kM2MTileSmem = (size_t)kM2MTile * kM2MTileStride * sizeof(float);
+
+__device__ __forceinline__ void m2m_tiles_f32(int level, const float* __restrict__ qc, const float* __restrict__ op,
+                                              const DF* __restrict__ Qin, float* __restrict__ qp,
+                                              DF* __restrict__ Qout, int nvec, int64_t vq, int64_t vQ,
+                                              float* __restrict__ sin) {
+    const int64_t n_parent = (int64_t)1 << (2 * level);  // a multiple of 64 (level >= 3)
+    const int64_t n_tiles = n_parent * nvec / kM2MTile;
+    const int g = threadIdx.x >> 3, cq = threadIdx.x & 7;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t item0 = tile * kM2MTile;
+        const int64_t v = item0 / n_parent, pr0 = item0 - v * n_parent;
+        const float* src = qc + v * vq + pr0 * 128;
+        __syncthreads();  // the previous tile's reads are done
+        for (int i = threadIdx.x; i < kM2MTile * 32; i += blockDim.x) {
+            const int it = i >> 5, k4 = i & 31;
+            const float4 x = __ldcg(reinterpret_cast<const float4*>(src + (size_t)it * 128) + k4);
+            *reinterpret_cast<float4*>(sin + it * kM2MTileStride + 4 * k4) = x;
+        }
+        if (threadIdx.x < kM2MTile) {
+            const DF* qi = Qin + v * vQ + 4 * (pr0 + threadIdx.x);
+            const DF q0 = ldcg(qi), q1 = ldcg(qi + 1), q2 = ldcg(qi + 2), q3 = ldcg(qi + 3);
+            Qout[v * vQ + pr0 + threadIdx.x] = df_add(df_add(q0, q1), df_add(q2, q3));
+        }
+        __syncthreads();
+        const float* x0p = sin + (2 * g) * kM2MTileStride;
+        const float* x1p = x0p + kM2MTileStride;
+        float r0[4], r1[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                const int k = 32 * c + l;
+                const float4 o = *reinterpret_cast<const float4*>(op + k * 32 + 4 * cq);
+                const float x0 = x0p[k], x1 = x1p[k];
+                a0[0] = fmaf(o.x, x0, a0[0]);
+                a0[1] = fmaf(o.y, x0, a0[1]);
+                a0[2] = fmaf(o.z, x0, a0[2]);
+                a0[3] = fmaf(o.w, x0, a0[3]);
+                a1[0] = fmaf(o.x, x1, a1[0]);
+                a1[1] = fmaf(o.y, x1, a1[1]);
+                a1[2] = fmaf(o.z, x1, a1[2]);
+                a1[3] = fmaf(o.w, x1, a1[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                r0[j] = c == 0 ? a0[j] : r0[j] + a0[j];
+                r1[j] = c == 0 ? a1[j] : r1[j] + a1[j];
+            }
+        }
+        float* dst = qp + v * vq + (pr0 + 2 * g) * 32 + 4 * cq;
+        *reinterpret_cast<float4*>(dst) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+        *reinterpret_cast<float4*>(dst + 32) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+    }
+}
+
 template <typename T, int NP, bool SMEM_OP>
 __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __restrict__ qc,
                                                        const T* __restrict__ m2m,
@@ -1206,7 +1274,16 @@ __global__ void __launch_bounds__(256) m2m_up_kernel(LevelPtrs<T> P, int l_top, 
             __syncthreads();
             op = sop;
         }
-        m2m_parents<T, NP>(l, P.q[l + 1], op, P.Q[l + 1], P.q[l], P.Q[l], wid, nw, P.nvec, P.vq, P.vQ);
+        bool tiled = false;
+        if constexpr (std::is_same<T, float>::value && NP == 32 && SMEM_OP) {
+            if (((int64_t)P.nvec << (2 * l)) >= kM2MTileMinItems) {
+                m2m_tiles_f32(l, P.q[l + 1], op, P.Q[l + 1], P.q[l], P.Q[l], P.nvec, P.vq, P.vQ,
+                              sop + 4 * NP * NP);
+                tiled = true;
+            }
+        }
+        if (!tiled)
+            m2m_parents<T, NP>(l, P.q[l + 1], op, P.Q[l + 1], P.q[l], P.Q[l], wid, nw, P.nvec, P.vq, P.vQ);
         if (l > l_bot) grid_barrier(sync, sync + 1, status);
     }
 }
@@ -1639,7 +1716,9 @@ cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, un
     };
     if (ops.NP == 32) {
         constexpr size_t ob = (size_t)4 * 32 * 32 * sizeof(T);
-        if constexpr (ob <= 64 * 1024) return go((const void*)m2m_up_kernel<T, 32, true>, ob);
+        // binary32: the operator and one tile of staged children (m2m_tiles_f32)
+        if constexpr (std::is_same<T, float>::value) return go((const void*)m2m_up_kernel<T, 32, true>, ob + kM2MTileSmem);
+        else if constexpr (ob <= 64 * 1024) return go((const void*)m2m_up_kernel<T, 32, true>, ob);
         else return go((const void*)m2m_up_kernel<T, 32, false>, 0);
     }
     constexpr size_t ob = (size_t)4 * 64 * 64 * sizeof(T);
