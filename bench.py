@@ -506,6 +506,60 @@ def multi_leg(lfmm, k: int = 8, steps: int = 10, warmup: int = 2):
             "note": "evaluation only; four vectors per near-field pass share each phi table lookup"}
 
 
+def solvers_leg(lfmm):
+    """The two solvers built on the lattice FMM, wall clock (host-driven GMRES):
+    a Dirichlet problem on a digital disk of radius 1500 (about 7.07e6 nodes, 8.5e3
+    boundary nodes; data x^2 - y^2 + 3 x y, scaled) and a lattice with 10^4 changed bars in
+    a 2048^2 box; both with the float-float path at p = 16."""
+    import time
+    import torch
+    from paper_1105_3505_gb300.bvp import LatticeDirichlet
+    from paper_1105_3505_gb300.inclusions import LatticeInclusions
+    res = {}
+    r = 1500
+    x, y = np.meshgrid(np.arange(-r, r + 1), np.arange(-r, r + 1), indexing="ij")
+    keep = x * x + y * y <= r * r
+    nodes = np.stack([x[keep], y[keep]], axis=1)
+    t0 = time.perf_counter()
+    bv = LatticeDirichlet(nodes)
+    t1 = time.perf_counter()
+    gx, gy = bv.gamma[:, 0].astype(np.float64), bv.gamma[:, 1].astype(np.float64)
+    bv.solve((gx * gx - gy * gy + 3.0 * gx * gy) / r ** 2, tol=1e-12)
+    t2 = time.perf_counter()
+    u = bv.potential()
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    ox, oy = bv.omega[:, 0].astype(np.float64), bv.omega[:, 1].astype(np.float64)
+    err = float(np.abs(u - (ox * ox - oy * oy + 3.0 * ox * oy) / r ** 2).max())
+    res["dirichlet_disk_r1500"] = {"interior_nodes": int(bv.omega.shape[0]), "boundary_nodes": int(bv.gamma.shape[0]),
+                                   "setup_ms": (t1 - t0) * 1e3, "gmres_iterations": bv.iterations,
+                                   "solve_ms": (t2 - t1) * 1e3, "ms_per_iteration": (t2 - t1) * 1e3 / bv.iterations,
+                                   "interior_eval_ms": (t3 - t2) * 1e3, "residual": bv.residual,
+                                   "max_abs_err_vs_harmonic_data": err}
+    bv.close()
+    rng = np.random.default_rng(11)
+    seen, bars, delta = set(), [], []
+    while len(bars) < 10000:
+        x0, y0 = (int(v) for v in rng.integers(0, 2048, size=2))
+        horiz = bool(rng.integers(0, 2))
+        key = (x0, y0, x0 + horiz, y0 + (not horiz))
+        if key in seen:
+            continue
+        seen.add(key)
+        bars.append(key)
+        delta.append(-1.0 if rng.random() < 0.5 else float(rng.uniform(0.5, 3.0)))
+    t0 = time.perf_counter()
+    li = LatticeInclusions(np.array(bars), np.array(delta))
+    t1 = time.perf_counter()
+    li.solve(1.0, 0.5, tol=1e-12)
+    t2 = time.perf_counter()
+    res["inclusions_10k_bars"] = {"nodes": int(li.nodes.shape[0]), "setup_ms": (t1 - t0) * 1e3,
+                                  "gmres_iterations": li.iterations, "solve_ms": (t2 - t1) * 1e3,
+                                  "ms_per_iteration": (t2 - t1) * 1e3 / li.iterations, "residual": li.residual}
+    li.close()
+    return res
+
+
 # ---------------------------------------------------------------- replicas
 def replica_throughput(ms_local, points_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` independent replicas: every rank solved
@@ -711,6 +765,7 @@ def main():
         out["forest"] = forest_leg(lfmm)
         out["eval_only"] = eval_leg(lfmm)
         out["multi_rhs"] = multi_leg(lfmm)
+        out["solvers"] = solvers_leg(lfmm)
         if args.serve_requests > 0:
             out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots)
     print(json.dumps(out), flush=True)
