@@ -33,10 +33,11 @@ _STEPS = ((1, 0), (-1, 0), (0, 1), (0, -1))
 
 def _grid(nodes: np.ndarray):
     """Occupancy grid of the bounding box padded by one node: (grid[y, x], x0, y0)."""
-    lo = nodes.min(axis=0) - 1
-    hi = nodes.max(axis=0) + 1
+    xs, ys = nodes[:, 0], nodes[:, 1]
+    lo = np.array([xs.min(), ys.min()]) - 1
+    hi = np.array([xs.max(), ys.max()]) + 1
     grid = np.zeros((int(hi[1] - lo[1] + 1), int(hi[0] - lo[0] + 1)), dtype=bool)
-    grid[nodes[:, 1] - lo[1], nodes[:, 0] - lo[0]] = True
+    grid[ys - lo[1], xs - lo[0]] = True
     return grid, int(lo[0]), int(lo[1])
 
 
@@ -64,9 +65,11 @@ def boundary_of(nodes):
     is_gamma = grid & ~interior
 
     def sorted_xy(mask):
-        ys, xs = np.nonzero(mask)
-        order = np.lexsort((ys, xs))
-        return np.stack([xs[order] + x0, ys[order] + y0], axis=1).astype(np.int64)
+        xs, ys = np.nonzero(mask.T)  # row-major over (x, y): sorted by x, then y
+        out = np.empty((xs.shape[0], 2), dtype=np.int64)
+        out[:, 0] = xs + x0
+        out[:, 1] = ys + y0
+        return out
 
     gamma, omega = sorted_xy(is_gamma), sorted_xy(grid & interior)
     gy, gx = gamma[:, 1] - y0, gamma[:, 0] - x0

@@ -287,29 +287,49 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     }
     std::unique_ptr<PhaseTimer> tree_timer(new PhaseTimer(LFMM_PHASE_TREE, s));
 
-    // ---- root box (Sec. 6): lower-left corner of all points, side 2^K
+    // ---- root box (Sec. 6): lower-left corner of all points, side 2^K.  The leaf level
+    // is at least the pigeonhole level L_pig, known without the points; unless the
+    // leaf-side bound raises it, the first level counted below is L_pig + 1.  That count
+    // is launched right behind the bounding box (the kernel reads the root box on the
+    // device), so one host round trip returns both; a wrong guess is counted again.
+    const int nleaf = p->opts.leaf_size;
+    const int64_t nmax = std::max(p->ns, p->nt);
+    int L_pig = 0;
+    while (((int64_t)nleaf << (2 * L_pig)) < nmax) ++L_pig;
+    const int Lf_guess = L_pig + 1;
     Temp t4;
     if ((st = talloc(t4, 10 * sizeof(int), s))) return st;
     int* d4 = (int*)t4.ptr;
     LFMM_CUDA_TRY(launch_set4(d4, INT_MAX, INT_MAX, INT_MIN, INT_MIN, s));
     LFMM_CUDA_TRY(launch_bbox(src, p->ns, tgt, p->nt, d4, s));
     tree_timer->add_launches(2);
-    int h4[4];
-    LFMM_CUDA_TRY(cudaMemcpyAsync(h4, d4, sizeof(h4), cudaMemcpyDeviceToHost, s));
+    Temp ranks;  // each point's arrival rank in its box of level Lf_last
+    if ((st = talloc(ranks, (size_t)(p->ns + p->nt) * sizeof(int32_t), s))) return st;
+    Temp guess;  // counts at level Lf_guess: [fine src][fine tgt][coarse src][coarse tgt]
+    bool have_guess = Lf_guess <= kMaxLevel;
+    if (have_guess) {
+        const int64_t nf = (int64_t)1 << (2 * Lf_guess), nc = nf / 4;
+        if ((st = talloc(guess, (size_t)(2 * nf + 2 * nc) * sizeof(int32_t), s))) return st;
+        int32_t* fs = (int32_t*)guess.ptr;
+        LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
+        LFMM_CUDA_TRY(launch_histogram_bbox(src, p->ns, tgt, p->nt, d4, Lf_guess, fs, fs + nf,
+                                            (int32_t*)ranks.ptr, s));
+        LFMM_CUDA_TRY(cudaMemsetAsync(d4 + 4, 0, 6 * sizeof(int), s));
+        LFMM_CUDA_TRY(launch_coarsen(fs, fs + nf, nc, fs + 2 * nf, fs + 2 * nf + nc, d4 + 4, s));
+        tree_timer->add_launches(2);
+    }
+    int h10[10];
+    LFMM_CUDA_TRY(cudaMemcpyAsync(h10, d4, (have_guess ? 10 : 4) * sizeof(int), cudaMemcpyDeviceToHost, s));
     LFMM_CUDA_TRY(cudaStreamSynchronize(s));
-    p->x0 = h4[0];
-    p->y0 = h4[1];
-    const int64_t ext = std::max((int64_t)h4[2] - h4[0], (int64_t)h4[3] - h4[1]) + 1;
+    p->x0 = h10[0];
+    p->y0 = h10[1];
+    const int64_t ext = std::max((int64_t)h10[2] - h10[0], (int64_t)h10[3] - h10[1]) + 1;
     if (ext > ((int64_t)1 << 30)) return fail(LFMM_EINVAL, "points span more than 2^30 lattice cells");
     p->K = ilog2_ceil(ext);
 
     // ---- leaf level: coarsest level with <= N_leaf sources and targets per box,
     // leaf side <= max_leaf_side.  Levels below the pigeonhole bound cannot qualify.
-    const int nleaf = p->opts.leaf_size;
     const int L_side = std::max(0, p->K - ilog2_ceil(p->opts.max_leaf_side));
-    const int64_t nmax = std::max(p->ns, p->nt);
-    int L_pig = 0;
-    while (((int64_t)nleaf << (2 * L_pig)) < nmax) ++L_pig;
     int L_try = std::max(L_side, L_pig);
     if (L_try > p->K) L_try = p->K;
     int Lf = std::min(p->K, L_try + 1);
@@ -317,8 +337,6 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     int32_t *cs = nullptr, *ct = nullptr;  // counts at the chosen level
     int32_t *fs_last = nullptr, *ft_last = nullptr;  // counts at the histogram level Lf_last
     int Lf_last = 0;
-    Temp ranks;  // each point's arrival rank in its box of level Lf_last
-    if ((st = talloc(ranks, (size_t)(p->ns + p->nt) * sizeof(int32_t), s))) return st;
     int chosen = -1;
     int64_t nonempty = 1;  // leaves holding a source or a target at the chosen level
     for (;;) {
@@ -327,24 +345,33 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         const int64_t nf = (int64_t)1 << (2 * Lf);
         const int64_t nc = Lf >= 1 ? nf / 4 : 0;
         Temp c2;
-        if ((st = talloc(c2, (size_t)(2 * nf + 2 * nc) * sizeof(int32_t), s))) return st;
+        // [max fine src, max fine tgt, max coarse src, max coarse tgt, non-empty fine, non-empty coarse]
+        int m4[6] = {(int)std::min<int64_t>(p->ns, INT_MAX), (int)std::min<int64_t>(p->nt, INT_MAX), 0, 0, 1, 1};
+        if (have_guess && Lf == Lf_guess) {  // counted with the bounding box
+            c2.ptr = guess.ptr;
+            c2.s = s;
+            guess.ptr = nullptr;
+            for (int k = 0; k < 6; ++k) m4[k] = h10[4 + k];
+        } else {
+            if ((st = talloc(c2, (size_t)(2 * nf + 2 * nc) * sizeof(int32_t), s))) return st;
+            int32_t* f0 = (int32_t*)c2.ptr;
+            LFMM_CUDA_TRY(cudaMemsetAsync(f0, 0, (size_t)2 * nf * sizeof(int32_t), s));
+            LFMM_CUDA_TRY(launch_histogram(src, p->ns, tgt, p->nt, p->x0, p->y0, p->K - Lf, f0, f0 + nf, s,
+                                           (int32_t*)ranks.ptr));
+            tree_timer->add_launches(1);
+            if (Lf >= 1) {
+                LFMM_CUDA_TRY(cudaMemsetAsync(d4 + 4, 0, 6 * sizeof(int), s));
+                LFMM_CUDA_TRY(launch_coarsen(f0, f0 + nf, nc, f0 + 2 * nf, f0 + 2 * nf + nc, d4 + 4, s));
+                tree_timer->add_launches(1);
+                LFMM_CUDA_TRY(cudaMemcpyAsync(m4, d4 + 4, sizeof(m4), cudaMemcpyDeviceToHost, s));
+                LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+            }
+        }
+        have_guess = false;  // a later pass counts again (and overwrites the ranks)
         int32_t* fs = (int32_t*)c2.ptr;
         int32_t* ft = fs + nf;
         int32_t* ccs = ft + nf;
         int32_t* cct = ccs + nc;
-        LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
-        LFMM_CUDA_TRY(launch_histogram(src, p->ns, tgt, p->nt, p->x0, p->y0, p->K - Lf, fs, ft, s,
-                                       (int32_t*)ranks.ptr));
-        tree_timer->add_launches(1);
-        // [max fine src, max fine tgt, max coarse src, max coarse tgt, non-empty fine, non-empty coarse]
-        int m4[6] = {(int)std::min<int64_t>(p->ns, INT_MAX), (int)std::min<int64_t>(p->nt, INT_MAX), 0, 0, 1, 1};
-        if (Lf >= 1) {
-            LFMM_CUDA_TRY(cudaMemsetAsync(d4 + 4, 0, 6 * sizeof(int), s));
-            LFMM_CUDA_TRY(launch_coarsen(fs, ft, nc, ccs, cct, d4 + 4, s));
-            tree_timer->add_launches(1);
-            LFMM_CUDA_TRY(cudaMemcpyAsync(m4, d4 + 4, sizeof(m4), cudaMemcpyDeviceToHost, s));
-            LFMM_CUDA_TRY(cudaStreamSynchronize(s));
-        }
         if (Lf - 1 >= L_try && std::max(m4[2], m4[3]) <= nleaf) {
             chosen = Lf - 1;
             p->max_src = m4[2];

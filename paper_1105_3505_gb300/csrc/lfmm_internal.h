@@ -276,6 +276,10 @@ cudaError_t launch_scatter_ranked(const int32_t* xy, int64_t n, int64_t x0, int6
 // Sums 2x2 blocks of two Morton count arrays; max4[0..3] receive (atomic max) the
 // largest fine source / target count and the largest coarse ones, max4[4..5] (atomic
 // add) the number of non-empty fine and coarse boxes.  max4 must be zeroed first.
+// Counts at level Lf with the root box taken from the device bbox words {min x, min y,
+// max x, max y} (no host round trip); ranks always recorded; nothing counted if K < Lf.
+cudaError_t launch_histogram_bbox(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt, const int* bbox4,
+                                  int Lf, int32_t* cs, int32_t* ct, int32_t* rank, cudaStream_t s);
 cudaError_t launch_coarsen(const int32_t* fs, const int32_t* ft, int64_t n_coarse, int32_t* cs,
                            int32_t* ct, int* max4, cudaStream_t s);
 // Exclusive scan over the 4^L leaves in row-major order of two Morton-indexed count

@@ -88,6 +88,28 @@ __global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
     }
 }
 
+// The same counts at level Lf before the host has read the bounding box: the root box
+// (corner and side 2^K, K the smallest with 2^K >= the larger extent) comes from the
+// bbox words the previous kernel wrote.  Nothing is counted when K < Lf (the host then
+// finds that level Lf was the wrong guess and counts again).
+__global__ void histogram_bbox_kernel(const int2* __restrict__ src, int64_t ns, const int2* __restrict__ tgt,
+                                      int64_t nt, const int* __restrict__ bbox4, int Lf, int32_t* __restrict__ cs,
+                                      int32_t* __restrict__ ct, int32_t* __restrict__ rank) {
+    const int64_t x0 = bbox4[0], y0 = bbox4[1];
+    const int64_t ext = max((int64_t)bbox4[2] - x0, (int64_t)bbox4[3] - y0) + 1;
+    if (ext < 1) return;
+    const int K = ext <= 1 ? 0 : 64 - __clzll((unsigned long long)(ext - 1));
+    if (K < Lf) return;
+    const int shift = K - Lf;
+    const int64_t n = ns + nt;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = i < ns ? atomicAdd(cs + box_of(src[i], x0, y0, shift), 1)
+                             : atomicAdd(ct + box_of(tgt[i - ns], x0, y0, shift), 1);
+        rank[i] = r;
+    }
+}
+
 // Buckets points by leaf (row-major leaf order at level L) from the ranks the histogram
 // recorded at level Lf (= L or L + 1, Morton counts `fine` of that level): a point's
 // slot is its leaf's start, plus the counts of its box's earlier siblings when Lf = L + 1,
@@ -289,6 +311,13 @@ cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt,
                              cudaStream_t s, int32_t* rank) {
     histogram_kernel<<<grid_for(ns + nt, kThreads), kThreads, 0, s>>>(
         (const int2*)src, ns, (const int2*)tgt, nt, x0, y0, shift, cs, ct, rank);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_histogram_bbox(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt, const int* bbox4,
+                                  int Lf, int32_t* cs, int32_t* ct, int32_t* rank, cudaStream_t s) {
+    histogram_bbox_kernel<<<grid_for(ns + nt, kThreads), kThreads, 0, s>>>((const int2*)src, ns, (const int2*)tgt,
+                                                                           nt, bbox4, Lf, cs, ct, rank);
     return cudaGetLastError();
 }
 
