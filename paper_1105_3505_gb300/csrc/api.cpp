@@ -579,7 +579,7 @@ int far_sweeps(lfmm_plan* p, const FarBufs& b, cudaStream_t s, Hook before_fine)
                                              l >= 3 ? (const float*)Ux(l - 1, 0) : nullptr,
                                              l >= 3 ? Cm(l - 1, 0) : nullptr, (float*)Ux(l, 0), Cm(l, 0), b.split,
                                              p->status, p->num_sms, s, b.nvec, b.vq, b.vQ));
-                pt.add_launches(l >= 3 ? 3 : 2);
+                pt.add_launches(2);
                 continue;
             }
         }

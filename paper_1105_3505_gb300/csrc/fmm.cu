@@ -1288,6 +1288,38 @@ __global__ void __launch_bounds__(256) m2m_up_kernel(LevelPtrs<T> P, int l_top, 
     }
 }
 
+// L2L of one child box b of level l (charge vector vv) by one warp: lanes own outputs,
+// the parent's expansion broadcast by shuffles; adds to the box's M2L result and carries
+// the incoming constant down.
+template <typename T, int NP>
+__device__ __forceinline__ void l2l_box(const LevelPtrs<T>& P, int l, int64_t vv, int64_t b, int lane) {
+    using M = Mono<T>;
+    constexpr int PL = NP / 32;
+    const int64_t par = b >> 2;
+    const int c = (int)(b & 3);  // Morton: child index = parity class (cx + 2 cy)
+    const T* op = P.l2l[l] + (size_t)c * NP * NP;
+    T* ul = P.u[l] + vv * P.vq;
+    typename M::V* Cl = P.C[l] + vv * P.vQ;
+    T pv[PL], acc[PL];
+#pragma unroll
+    for (int i = 0; i < PL; ++i) {
+        pv[i] = ldcg(P.u[l - 1] + vv * P.vq + (size_t)par * NP + lane + 32 * i);
+        acc[i] = ldcg(ul + (size_t)b * NP + lane + 32 * i);
+    }
+#pragma unroll
+    for (int i = 0; i < PL; ++i)
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            const T v = shfl(pv[i], kk);
+            const T* row = op + (size_t)(32 * i + kk) * NP;
+#pragma unroll
+            for (int o = 0; o < PL; ++o) acc[o] = fma(ldg(row + lane + 32 * o), v, acc[o]);
+        }
+#pragma unroll
+    for (int i = 0; i < PL; ++i) ul[(size_t)b * NP + lane + 32 * i] = acc[i];
+    if (lane == 0) Cl[b] = M::add(ldcg(Cl + b), ldcg(P.C[l - 1] + vv * P.vQ + par));
+}
+
 // The fused kernel's tiles have 27 K-steps (no parent term): 9 warps take 3 each (3 warps
 // x 9 for binary64-width elements with 64 coefficients, to fit shared memory).
 template <typename T, int NP>
@@ -1318,11 +1350,14 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
     if (nl == 1) return;
     grid_barrier(sync, sync + 1, status);
     // L2L chain: one warp per child box, lanes own outputs, the parent's expansion
-    // broadcast by shuffles
+    // broadcast by shuffles.  Levels below l_sub level by level with a grid barrier
+    // between them; the last three levels by subtrees (one block per box of level l_sub
+    // and its children and grandchildren, block barriers only).
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int l = l0 + 1; l <= l1; ++l) {
+    const int l_sub = l1 - l0 >= 3 ? l1 - 2 : l1 + 1;
+    for (int l = l0 + 1; l < l_sub; ++l) {
         const int64_t nb = (int64_t)1 << (2 * l);
         const int64_t n_box_items = nb * P.nvec;  // (charge vector, child box)
         // software pipeline over the boxes: the next box's rows load during this one
@@ -1370,6 +1405,18 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
             if (lane == 0) Cl[b] = M::add(ldcg(Cl + b), ldcg(P.C[l - 1] + vv * P.vQ + par));
         }
         if (l < l1) grid_barrier(sync, sync + 1, status);
+    }
+    if (l_sub > l1) return;
+    const int warp = threadIdx.x >> 5;
+    const int64_t n_roots = ((int64_t)1 << (2 * l_sub)) * P.nvec;  // (charge vector, root box)
+    for (int64_t item = blockIdx.x; item < n_roots; item += gridDim.x) {
+        const int64_t vv = item >> (2 * l_sub), r = item & (((int64_t)1 << (2 * l_sub)) - 1);
+        for (int g = 0; g <= l1 - l_sub; ++g) {
+            const int64_t nb = (int64_t)1 << (2 * g);  // the root's descendants on level l_sub + g
+            for (int64_t k = warp; k < nb; k += FusedCfg<T, NP>::WARPS)
+                l2l_box<T, NP>(P, l_sub + g, vv, (r << (2 * g)) + k, lane);
+            __syncthreads();  // the next generation reads this one
+        }
     }
 }
 

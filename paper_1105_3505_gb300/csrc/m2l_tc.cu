@@ -473,40 +473,48 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 
 // hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
 // tensor maps describe: planes = 1 -> [hl][plane][y'][x'][32] (targets' level),
-// planes = 0 -> [hl][y][x][32] (parent level, row-major).  One float4 per thread.
-__global__ void split_tf32_layout_kernel(const float4* __restrict__ x0, float4* __restrict__ dst0, int lg,
-                                         int planes, int nvec, int64_t vq4) {
+// planes = 0 -> [hl][y][x][32] (parent level, row-major).  Item iv is one float4 of
+// vector iv / n4.
+__device__ __forceinline__ void split_tf32_item(const float4* __restrict__ x0, float4* __restrict__ dst0, int lg,
+                                                int planes, int64_t vq4, int64_t n4, int64_t iv) {
     const int np = 1 << lg;
-    const int64_t nb = planes ? (int64_t)4 << (2 * lg) : (int64_t)1 << (2 * lg);  // boxes
-    const int64_t n4 = nb * 8;
-    // vector vec: input at x0 + vec vq4, output (hi then lo) at dst0 + 2 vec n4
-    for (int64_t iv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; iv < n4 * nvec;
-         iv += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vec = iv / n4, i = iv - vec * n4;
-        const float4* x = x0 + vec * vq4;
-        float4* dst = dst0 + 2 * vec * n4;
-        const int64_t b = i >> 3;
-        const int c = (int)(i & 7);
-        uint32_t bx, by;
-        if (planes) {
-            const int plane = (int)(b >> (2 * lg));
-            const int64_t rem = b & (((int64_t)1 << (2 * lg)) - 1);
-            bx = 2 * (uint32_t)(rem & (np - 1)) + (plane & 1);
-            by = 2 * (uint32_t)(rem >> lg) + (plane >> 1);
-        } else {
-            bx = (uint32_t)(b & (np - 1));
-            by = (uint32_t)(b >> lg);
-        }
-        const float4 v = x[(size_t)morton2(bx, by) * 8 + c];
-        const float a[4] = {v.x, v.y, v.z, v.w};
-        float h[4], l[4];
+    const int64_t vec = iv / n4, i = iv - vec * n4;
+    const float4* x = x0 + vec * vq4;
+    float4* dst = dst0 + 2 * vec * n4;  // vector vec: hi then lo
+    const int64_t b = i >> 3;
+    const int c = (int)(i & 7);
+    uint32_t bx, by;
+    if (planes) {
+        const int plane = (int)(b >> (2 * lg));
+        const int64_t rem = b & (((int64_t)1 << (2 * lg)) - 1);
+        bx = 2 * (uint32_t)(rem & (np - 1)) + (plane & 1);
+        by = 2 * (uint32_t)(rem >> lg) + (plane >> 1);
+    } else {
+        bx = (uint32_t)(b & (np - 1));
+        by = (uint32_t)(b >> lg);
+    }
+    const float4 v = x[(size_t)morton2(bx, by) * 8 + c];
+    const float a[4] = {v.x, v.y, v.z, v.w};
+    float h[4], l[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            h[e] = __uint_as_float(tf32_rna_bits(a[e]));
-            l[e] = __uint_as_float(tf32_rna_bits(a[e] - h[e]));
-        }
-        dst[i] = make_float4(h[0], h[1], h[2], h[3]);
-        dst[i + n4] = make_float4(l[0], l[1], l[2], l[3]);
+    for (int e = 0; e < 4; ++e) {
+        h[e] = __uint_as_float(tf32_rna_bits(a[e]));
+        l[e] = __uint_as_float(tf32_rna_bits(a[e] - h[e]));
+    }
+    dst[i] = make_float4(h[0], h[1], h[2], h[3]);
+    dst[i + n4] = make_float4(l[0], l[1], l[2], l[3]);
+}
+
+// The target level's expansions (parity planes) and, when xu is set, the parent level's
+// (row-major) in one launch: items [0, nvec nq4) are the former, the rest the latter.
+__global__ void split_tf32_layout_kernel(const float4* __restrict__ xq, float4* __restrict__ dq,
+                                         const float4* __restrict__ xu, float4* __restrict__ du, int lg, int nvec,
+                                         int64_t vq4) {
+    const int64_t nq4 = ((int64_t)4 << (2 * lg)) * 8, nu4 = ((int64_t)1 << (2 * lg)) * 8;
+    const int64_t nq = nq4 * nvec, n = nq + (xu ? nu4 * nvec : 0);
+    for (int64_t iv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; iv < n; iv += (int64_t)gridDim.x * blockDim.x) {
+        if (iv < nq) split_tf32_item(xq, dq, lg, 1, vq4, nq4, iv);
+        else split_tf32_item(xu, du, lg, 0, vq4, nu4, iv - nq);
     }
 }
 
@@ -559,11 +567,9 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
         int64_t b = (n4 + 255) / 256;
         return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
     };
-    split_tf32_layout_kernel<<<grid_for((int64_t)4 * np * np * 8 * nvec), 256, 0, s>>>(
-        reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs), lg, 1, nvec, vq / 4);
-    if (l2l)
-        split_tf32_layout_kernel<<<grid_for((int64_t)np * np * 8 * nvec), 256, 0, s>>>(
-            reinterpret_cast<const float4*>(u_parent), reinterpret_cast<float4*>(us), lg, 0, nvec, vq / 4);
+    split_tf32_layout_kernel<<<grid_for((int64_t)(4 + (l2l ? 1 : 0)) * np * np * 8 * nvec), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs),
+        l2l ? reinterpret_cast<const float4*>(u_parent) : nullptr, reinterpret_cast<float4*>(us), lg, nvec, vq / 4);
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
