@@ -188,7 +188,7 @@ __device__ __forceinline__ DFv dmul(DFv a, DFv b) {
 //     loads and float-pair arithmetic, independent of the pipeline).
 // Every wait is bounded; on expiry the CTA records LFMM_ETIMEOUT, every role stops at
 // its next iteration, and the teardown waits (bounded) for the copies and MMAs issued.
-constexpr int kTmaStages = 5;
+constexpr int kTmaStages = 3;
 constexpr int kTmaAcc = 4;
 constexpr int kTmaThreads = 224;
 constexpr int kTmaCols = 256;  // buffer b: D_big at columns [64b, 64b+32), D_small at [64b+32, 64b+64)
