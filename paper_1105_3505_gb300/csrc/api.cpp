@@ -935,18 +935,51 @@ int lfmm_solve(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy, int6
             if (aux) LFMM_CUDA_TRY(cudaEventRecord(aux->join, aux->s));
         }
     }
+    // a host u is written by one copy from a device temporary, so that everything up to
+    // the plan's release is queued before the host waits (once, in lfmm_plan_destroy)
+    double* ud = u;
+    if (!is_device_ptr(u)) {
+        void* d;
+        const cudaError_t e = cudaMallocAsync(&d, (size_t)n_tgt * sizeof(double), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (aux) {
+                cudaStreamWaitEvent(s, aux->join, 0);
+                cudaStreamSynchronize(s);
+                release_aux(aux);
+            }
+            release();
+            return fail(LFMM_ENOMEM, std::string("temporary allocation failed: ") + cudaGetErrorString(e));
+        }
+        temps.push_back(d);
+        ud = (double*)d;
+    }
     lfmm_plan* plan = nullptr;
     st = lfmm_plan_create(&plan, sd, n_src, td, n_tgt, opts, stream);
     if (!st) {
         if (aux) cudaStreamWaitEvent(s, aux->join, 0);
-        st = lfmm_eval(plan, fd, u, stream);
+        st = lfmm_eval(plan, fd, ud, stream);
     }
-    const int st2 = plan ? lfmm_plan_destroy(plan) : LFMM_OK;
-    if (aux) {
-        cudaStreamWaitEvent(s, aux->join, 0);  // the upload is done before its buffer is freed
-        release_aux(aux);
+    if (!st && ud != u) {
+        const cudaError_t e = cudaMemcpyAsync(u, ud, (size_t)n_tgt * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(LFMM_ECUDA, std::string("result copy: ") + cudaGetErrorString(e));
+        }
     }
-    release();
+    if (aux) cudaStreamWaitEvent(s, aux->join, 0);  // the upload is done before its buffer is freed
+    release();                                       // in stream order, behind the result copy
+    int st2 = LFMM_OK;
+    if (plan) {
+        st2 = lfmm_plan_destroy(plan);  // frees in stream order, then waits for the stream
+    } else {
+        const cudaError_t e = cudaStreamSynchronize(s);  // host inputs were read, host output written
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st2 = fail(LFMM_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+        }
+    }
+    release_aux(aux);
     return st ? st : st2;
 }
 
