@@ -300,22 +300,21 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     Temp t4;
     if ((st = talloc(t4, 10 * sizeof(int), s))) return st;
     int* d4 = (int*)t4.ptr;
-    LFMM_CUDA_TRY(launch_set4(d4, INT_MAX, INT_MAX, INT_MIN, INT_MIN, s));
-    LFMM_CUDA_TRY(launch_bbox(src, p->ns, tgt, p->nt, d4, s));
-    tree_timer->add_launches(2);
     Temp ranks;  // each point's arrival rank in its box of level Lf_last
     if ((st = talloc(ranks, (size_t)(p->ns + p->nt) * sizeof(int32_t), s))) return st;
     Temp guess;  // counts at level Lf_guess: [fine src][fine tgt][coarse src][coarse tgt]
     bool have_guess = Lf_guess <= kMaxLevel;
+    const int64_t nf_g = have_guess ? (int64_t)1 << (2 * Lf_guess) : 0, nc_g = nf_g / 4;
+    if (have_guess && (st = talloc(guess, (size_t)(2 * nf_g + 2 * nc_g) * sizeof(int32_t), s))) return st;
+    // one launch sets the bounding-box words, zeroes the maxima words and the fine counts
+    LFMM_CUDA_TRY(launch_init_tree(d4, (int32_t*)guess.ptr, 2 * nf_g, s));
+    LFMM_CUDA_TRY(launch_bbox(src, p->ns, tgt, p->nt, d4, s));
+    tree_timer->add_launches(2);
     if (have_guess) {
-        const int64_t nf = (int64_t)1 << (2 * Lf_guess), nc = nf / 4;
-        if ((st = talloc(guess, (size_t)(2 * nf + 2 * nc) * sizeof(int32_t), s))) return st;
         int32_t* fs = (int32_t*)guess.ptr;
-        LFMM_CUDA_TRY(cudaMemsetAsync(fs, 0, (size_t)2 * nf * sizeof(int32_t), s));
-        LFMM_CUDA_TRY(launch_histogram_bbox(src, p->ns, tgt, p->nt, d4, Lf_guess, fs, fs + nf,
+        LFMM_CUDA_TRY(launch_histogram_bbox(src, p->ns, tgt, p->nt, d4, Lf_guess, fs, fs + nf_g,
                                             (int32_t*)ranks.ptr, s));
-        LFMM_CUDA_TRY(cudaMemsetAsync(d4 + 4, 0, 6 * sizeof(int), s));
-        LFMM_CUDA_TRY(launch_coarsen(fs, fs + nf, nc, fs + 2 * nf, fs + 2 * nf + nc, d4 + 4, s));
+        LFMM_CUDA_TRY(launch_coarsen(fs, fs + nf_g, nc_g, fs + 2 * nf_g, fs + 2 * nf_g + nc_g, d4 + 4, s));
         tree_timer->add_launches(2);
     }
     int h10[10];

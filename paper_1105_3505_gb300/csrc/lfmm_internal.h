@@ -260,6 +260,9 @@ template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
                 void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s);
 
+// words[0..3] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN}, words[4..9] = 0, zero[0..n_zero) = 0
+// (zero 16-byte aligned), in one launch.
+cudaError_t launch_init_tree(int* words, int32_t* zero, int64_t n_zero, cudaStream_t s);
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s);
 cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
                         cudaStream_t s);

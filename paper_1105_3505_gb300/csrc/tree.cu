@@ -7,6 +7,8 @@
 // one coarsening pass; an exclusive scan turns leaf counts into bucket offsets, and a
 // scatter places every point in its leaf bucket (order inside a bucket is the
 // arrival order of the atomics; nothing downstream depends on it beyond rounding).
+#include <algorithm>
+
 #include "lfmm_internal.h"
 
 namespace lfmm {
@@ -31,14 +33,24 @@ __global__ void bbox_kernel(const int2* __restrict__ a, int64_t na, const int2* 
     __shared__ int sh[4][kThreads / 32];
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
     const int64_t n = na + nb;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int2 p = i < na ? a[i] : b[i - na];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto at = [&](int64_t i) { return i < na ? a[i] : b[i - na]; };
+    auto take = [&](int2 p) {
         mnx = min(mnx, p.x);
         mny = min(mny, p.y);
         mxx = max(mxx, p.x);
         mxy = max(mxy, p.y);
+    };
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four independent loads in flight per thread (the input is read cold from DRAM)
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const int2 p0 = at(i), p1 = at(i + stride), p2 = at(i + 2 * stride), p3 = at(i + 3 * stride);
+        take(p0);
+        take(p1);
+        take(p2);
+        take(p3);
     }
+    for (; i < n; i += stride) take(at(i));
     mnx = warp_min(mnx);
     mny = warp_min(mny);
     mxx = warp_max(mxx);
@@ -285,6 +297,16 @@ __global__ void set4_kernel(int* p, int a, int b, int c, int d) {
     p[3] = d;
 }
 
+// words[0..3] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN} (bounding box to be reduced),
+// words[4..9] = 0 (maxima and counts of coarsen_kernel), zero[0..n_zero) = 0
+__global__ void init_tree_kernel(int* __restrict__ words, int32_t* __restrict__ zero, int64_t n_zero) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 10) words[t] = t < 2 ? INT_MAX : (t < 4 ? INT_MIN : 0);
+    for (int64_t i = t; i < n_zero / 4; i += (int64_t)gridDim.x * blockDim.x)
+        reinterpret_cast<int4*>(zero)[i] = make_int4(0, 0, 0, 0);
+    for (int64_t i = n_zero / 4 * 4 + t; i < n_zero; i += (int64_t)gridDim.x * blockDim.x) zero[i] = 0;
+}
+
 int grid_for(int64_t n, int threads, int cap = 152 * 16) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -296,6 +318,11 @@ int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 
 cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s) {
     set4_kernel<<<1, 1, 0, s>>>(p, a, b, c, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_tree(int* words, int32_t* zero, int64_t n_zero, cudaStream_t s) {
+    init_tree_kernel<<<grid_for(std::max<int64_t>(n_zero / 4, 10), kThreads), kThreads, 0, s>>>(words, zero, n_zero);
     return cudaGetLastError();
 }
 
