@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                                                   T* __restrict__ qhat,
                                                   typename Mono<T>::V* __restrict__ Q, int nvec, int64_t ns,
                                                   int64_t vq, int64_t vQ) {
+    griddep_wait();
     using M = Mono<T>;
     constexpr int G = 16, PL = NP / G;
     using Row = VecT<T, PL>;
@@ -1433,6 +1434,7 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
                                                   const typename Mono<T>::V* __restrict__ Cleaf,
                                                   const T* __restrict__ tofsT, double* __restrict__ uf, int nvec,
                                                   int64_t vq, int64_t vQ) {
+    griddep_wait();
     using M = Mono<T>;
     constexpr int E = (int)(16 / sizeof(T));
     constexpr int RS = NP + 1;
@@ -1467,6 +1469,7 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
 // u = u_near + u_far (caller order), and the parts where requested
 __global__ void combine_kernel(int64_t n, const double* __restrict__ un, const double* __restrict__ uf,
                                double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
+    griddep_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double a = un[i], b = uf[i];
         if (u) u[i] = a + b;
@@ -1487,14 +1490,12 @@ cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f,
     if (blocks < 1) blocks = 1;
     using V = typename Mono<T>::V;
     if (ops.NP == 32)
-        p2m_kernel<T, 32><<<(int)blocks, threads, 0, s>>>(t.L, t.src_begin, t.src_loc, t.src_perm, f, f_sorted,
-                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q, nvec,
-                                                          t.n_src_all, vq, vQ);
-    else
-        p2m_kernel<T, 64><<<(int)blocks, threads, 0, s>>>(t.L, t.src_begin, t.src_loc, t.src_perm, f, f_sorted,
-                                                          (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q, nvec,
-                                                          t.n_src_all, vq, vQ);
-    return cudaGetLastError();
+        return launch_dependent(p2m_kernel<T, 32>, dim3((unsigned)blocks), dim3(threads), 0, s, t.L, t.src_begin,
+                                t.src_loc, t.src_perm, f, f_sorted, (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q,
+                                nvec, t.n_src_all, vq, vQ);
+    return launch_dependent(p2m_kernel<T, 64>, dim3((unsigned)blocks), dim3(threads), 0, s, t.L, t.src_begin,
+                            t.src_loc, t.src_perm, f, f_sorted, (const T*)ops.tofsT, t.side, qhat_leaf, (V*)Q, nvec,
+                            t.n_src_all, vq, vQ);
 }
 
 template <typename T, int NP, int MODE>
@@ -1826,10 +1827,9 @@ cudaError_t launch_l2p(const TreeView& t, const DeviceOps& ops, const T* uhat_le
         const int64_t cap = (int64_t)152 * blocks_per_sm(fn, 256, smem);
         if (blocks > cap) blocks = cap;
         if (blocks < 1) blocks = 1;
-        l2p_kernel<T, NPc, SM><<<(int)blocks, 256, smem, s>>>(t.n_tgt, t.side, t.tgt_leaf, t.tgt_loc, t.tgt_perm,
-                                                              uhat_leaf, (const V*)Cleaf, (const T*)ops.tofsT, uf,
-                                                              nvec, vq, vQ);
-        return cudaGetLastError();
+        return launch_dependent(l2p_kernel<T, NPc, SM>, dim3((unsigned)blocks), dim3(256), smem, s, t.n_tgt, t.side,
+                                t.tgt_leaf, t.tgt_loc, t.tgt_perm, uhat_leaf, (const V*)Cleaf, (const T*)ops.tofsT,
+                                uf, nvec, vq, vQ);
     };
     using I32 = std::integral_constant<int, 32>;
     using I64 = std::integral_constant<int, 64>;
@@ -1844,8 +1844,7 @@ cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    combine_kernel<<<(int)blocks, 256, 0, s>>>(n, un, uf, u, u_near, u_far);
-    return cudaGetLastError();
+    return launch_dependent(combine_kernel, dim3((unsigned)blocks), dim3(256), 0, s, n, un, uf, u, u_near, u_far);
 }
 
 #define LFMM_INSTANTIATE(T)                                                                                   \

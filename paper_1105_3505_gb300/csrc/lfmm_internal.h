@@ -15,6 +15,32 @@
 
 namespace lfmm {
 
+#ifdef __CUDACC__
+// ---------------------------------------------------------------- dependent launches
+// Kernels of one dependency chain on a stream are launched with programmatic stream
+// serialisation: a kernel's blocks may be scheduled while its predecessor's last blocks
+// drain, and griddep_wait() - the first statement of every kernel launched this way -
+// holds them until the predecessor has completed and its writes are visible.  Launched
+// without the attribute (or behind a copy, a memset or an event), the wait returns at once.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#endif
+
 // ---------------------------------------------------------------- float-float numbers
 // hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits in two binary32 values.
 // Element type of the LFMM_DF path (and of the compensated total-charge / incoming-

@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_u, const TmaGeo g,
     const float* __restrict__ tiles, const float* __restrict__ mono, const DFv* __restrict__ Qin,
     const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout, int* __restrict__ status) {
+    griddep_wait();
     constexpr int NP = 32;
     extern __shared__ __align__(1024) unsigned char tma_smem[];
     // stage i: A hi, A lo (128 rows x 128 B each, 128-byte swizzled), B hi + lo (8 KB)
@@ -510,6 +511,7 @@ __device__ __forceinline__ void split_tf32_item(const float4* __restrict__ x0, f
 __global__ void split_tf32_layout_kernel(const float4* __restrict__ xq, float4* __restrict__ dq,
                                          const float4* __restrict__ xu, float4* __restrict__ du, int lg, int nvec,
                                          int64_t vq4) {
+    griddep_wait();
     const int64_t nq4 = ((int64_t)4 << (2 * lg)) * 8, nu4 = ((int64_t)1 << (2 * lg)) * 8;
     const int64_t nq = nq4 * nvec, n = nq + (xu ? nu4 * nvec : 0);
     for (int64_t iv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; iv < n; iv += (int64_t)gridDim.x * blockDim.x) {
@@ -567,9 +569,13 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
         int64_t b = (n4 + 255) / 256;
         return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
     };
-    split_tf32_layout_kernel<<<grid_for((int64_t)(4 + (l2l ? 1 : 0)) * np * np * 8 * nvec), 256, 0, s>>>(
-        reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs),
-        l2l ? reinterpret_cast<const float4*>(u_parent) : nullptr, reinterpret_cast<float4*>(us), lg, nvec, vq / 4);
+    {
+        const cudaError_t e = launch_dependent(
+            split_tf32_layout_kernel, dim3(grid_for((int64_t)(4 + (l2l ? 1 : 0)) * np * np * 8 * nvec)), dim3(256), 0, s,
+            reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs),
+            l2l ? reinterpret_cast<const float4*>(u_parent) : nullptr, reinterpret_cast<float4*>(us), lg, nvec, vq / 4);
+        if (e != cudaSuccess) return e;
+    }
     {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -597,10 +603,9 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
         if (e != cudaSuccess) return e;
     }
     const int grid = std::min(g.n_tiles * nvec, num_sms);
-    m2l_tma_kernel<<<grid, kTmaThreads, smem, s>>>(mq, mu, g, (const float*)ops.tc[k], (const float*)ops.mono[k],
-                                                   (const DFv*)Q_level, (const DFv*)C_parent, u_level,
-                                                   (DFv*)C_level, status);
-    return cudaGetLastError();
+    return launch_dependent(m2l_tma_kernel, dim3(grid), dim3(kTmaThreads), smem, s, mq, mu, g,
+                            (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
+                            (const DFv*)C_parent, u_level, (DFv*)C_level, status);
 }
 
 }  // namespace lfmm

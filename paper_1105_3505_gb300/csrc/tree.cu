@@ -30,6 +30,7 @@ __device__ __forceinline__ int warp_max(int v) {
 // Warp and block reductions first: one set of atomics per block.
 __global__ void bbox_kernel(const int2* __restrict__ a, int64_t na, const int2* __restrict__ b,
                             int64_t nb, int* __restrict__ out4) {
+    griddep_wait();
     __shared__ int sh[4][kThreads / 32];
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
     const int64_t n = na + nb;
@@ -107,6 +108,7 @@ __global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
 __global__ void histogram_bbox_kernel(const int2* __restrict__ src, int64_t ns, const int2* __restrict__ tgt,
                                       int64_t nt, const int* __restrict__ bbox4, int Lf, int32_t* __restrict__ cs,
                                       int32_t* __restrict__ ct, int32_t* __restrict__ rank) {
+    griddep_wait();
     const int64_t x0 = bbox4[0], y0 = bbox4[1];
     const int64_t ext = max((int64_t)bbox4[2] - x0, (int64_t)bbox4[3] - y0) + 1;
     if (ext < 1) return;
@@ -130,6 +132,7 @@ __global__ void scatter_ranked_kernel(const int2* __restrict__ xy, int64_t n, in
                                       int Lf, const int32_t* __restrict__ begin, const int32_t* __restrict__ fine,
                                       const int32_t* __restrict__ rank, int32_t* __restrict__ loc,
                                       int32_t* __restrict__ perm, int32_t* __restrict__ leaf_of_slot) {
+    griddep_wait();
     const int shift = K - L, lside = 1 << shift;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = xy[i];
@@ -152,6 +155,7 @@ __global__ void scatter_ranked_kernel(const int2* __restrict__ xy, int64_t n, in
 __global__ void coarsen_kernel(const int4* __restrict__ fs, const int4* __restrict__ ft,
                                int64_t n_coarse, int32_t* __restrict__ cs,
                                int32_t* __restrict__ ct, int* __restrict__ max4) {
+    griddep_wait();
     int m0 = 0, m1 = 0, m2 = 0, m3 = 0, nf = 0, nc = 0;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_coarse;
          b += (int64_t)gridDim.x * blockDim.x) {
@@ -222,6 +226,7 @@ __device__ __forceinline__ int32_t count_rm(const int32_t* in, int64_t i, int L)
 
 __global__ void scan_tile_sums(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
                                int64_t n, int L, int32_t* __restrict__ partials) {
+    griddep_wait();
     __shared__ int sh[kThreads / 32];
     const int32_t* in = blockIdx.y ? b : a;
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -236,6 +241,7 @@ __global__ void scan_tile_sums(const int32_t* __restrict__ a, const int32_t* __r
 }
 
 __global__ void scan_partials(int32_t* __restrict__ partials, int n_tiles) {
+    griddep_wait();
     __shared__ int sh[kThreads / 32];
     int32_t* p = partials + (int64_t)blockIdx.x * n_tiles;
     int carry = 0;
@@ -252,6 +258,7 @@ __global__ void scan_partials(int32_t* __restrict__ partials, int n_tiles) {
 __global__ void scan_tiles(const int32_t* __restrict__ a, int32_t* __restrict__ oa,
                            const int32_t* __restrict__ b, int32_t* __restrict__ ob, int64_t n, int L,
                            const int32_t* __restrict__ partials) {
+    griddep_wait();
     __shared__ int sh[kThreads / 32];
     const int32_t* in = blockIdx.y ? b : a;
     int32_t* out = blockIdx.y ? ob : oa;
@@ -328,9 +335,8 @@ cudaError_t launch_init_tree(int* words, int32_t* zero, int64_t n_zero, cudaStre
 
 cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int* out4,
                         cudaStream_t s) {
-    bbox_kernel<<<grid_for((na + nb + 7) / 8, kThreads, 152 * 8), kThreads, 0, s>>>((const int2*)a, na,
-                                                                (const int2*)b, nb, out4);
-    return cudaGetLastError();
+    return launch_dependent(bbox_kernel, dim3(grid_for((na + nb + 7) / 8, kThreads, 152 * 8)), dim3(kThreads), 0, s,
+                            (const int2*)a, na, (const int2*)b, nb, out4);
 }
 
 cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
@@ -343,24 +349,21 @@ cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt,
 
 cudaError_t launch_histogram_bbox(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt, const int* bbox4,
                                   int Lf, int32_t* cs, int32_t* ct, int32_t* rank, cudaStream_t s) {
-    histogram_bbox_kernel<<<grid_for(ns + nt, kThreads), kThreads, 0, s>>>((const int2*)src, ns, (const int2*)tgt,
-                                                                           nt, bbox4, Lf, cs, ct, rank);
-    return cudaGetLastError();
+    return launch_dependent(histogram_bbox_kernel, dim3(grid_for(ns + nt, kThreads)), dim3(kThreads), 0, s,
+                            (const int2*)src, ns, (const int2*)tgt, nt, bbox4, Lf, cs, ct, rank);
 }
 
 cudaError_t launch_scatter_ranked(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int K, int L, int Lf,
                                   const int32_t* begin, const int32_t* fine, const int32_t* rank, int32_t* loc,
                                   int32_t* perm, cudaStream_t s, int32_t* leaf_of_slot) {
-    scatter_ranked_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>((const int2*)xy, n, x0, y0, K, L, Lf, begin,
-                                                                     fine, rank, loc, perm, leaf_of_slot);
-    return cudaGetLastError();
+    return launch_dependent(scatter_ranked_kernel, dim3(grid_for(n, kThreads)), dim3(kThreads), 0, s,
+                            (const int2*)xy, n, x0, y0, K, L, Lf, begin, fine, rank, loc, perm, leaf_of_slot);
 }
 
 cudaError_t launch_coarsen(const int32_t* fs, const int32_t* ft, int64_t n_coarse, int32_t* cs,
                            int32_t* ct, int* max4, cudaStream_t s) {
-    coarsen_kernel<<<grid_for(n_coarse, kThreads), kThreads, 0, s>>>(
-        (const int4*)fs, (const int4*)ft, n_coarse, cs, ct, max4);
-    return cudaGetLastError();
+    return launch_dependent(coarsen_kernel, dim3(grid_for(n_coarse, kThreads)), dim3(kThreads), 0, s,
+                            (const int4*)fs, (const int4*)ft, n_coarse, cs, ct, max4);
 }
 
 size_t scan_partials_size(int64_t n) {
@@ -374,10 +377,10 @@ cudaError_t launch_scan2(const int32_t* a, int32_t* oa, const int32_t* b, int32_
     int tiles = (int)((n + kScanTile - 1) / kScanTile);
     if (tiles < 1) tiles = 1;
     dim3 g(tiles, 2);
-    scan_tile_sums<<<g, kThreads, 0, s>>>(a, b, n, L, partials);
-    scan_partials<<<2, kThreads, 0, s>>>(partials, tiles);
-    scan_tiles<<<g, kThreads, 0, s>>>(a, oa, b, ob, n, L, partials);
-    return cudaGetLastError();
+    cudaError_t e = launch_dependent(scan_tile_sums, g, dim3(kThreads), 0, s, a, b, n, L, partials);
+    if (e == cudaSuccess) e = launch_dependent(scan_partials, dim3(2), dim3(kThreads), 0, s, partials, tiles);
+    if (e == cudaSuccess) e = launch_dependent(scan_tiles, g, dim3(kThreads), 0, s, a, oa, b, ob, n, L, partials);
+    return e;
 }
 
 cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int shift,
