@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(128) translate_kernel(int level, const T* __re
                                                         T* __restrict__ out,
                                                         typename Mono<T>::V* __restrict__ Qout,
                                                         typename Mono<T>::V* __restrict__ Cout) {
+    griddep_wait();
     using C = TrCfg<T, NP>;
     using M = Mono<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -497,6 +498,7 @@ __global__ void __launch_bounds__(SkCfg<T, NP>::WARPS * 32) m2l_splitk_kernel(in
                                                                    const typename Mono<T>::V* __restrict__ Cpar,
                                                                    T* __restrict__ out,
                                                                    typename Mono<T>::V* __restrict__ Cout) {
+    griddep_wait();
     m2l_splitk_tile<T, NP, SkCfg<T, NP>::WARPS>(level, blockIdx.y, blockIdx.x, q, u_par, ops, l2l, mono, Qin, Cpar,
                                                  out, Cout);
 }
@@ -643,6 +645,7 @@ __global__ void __launch_bounds__(256) m2m_warp_kernel(int level, const T* __res
                                                        const typename Mono<T>::V* __restrict__ Qin,
                                                        T* __restrict__ qp,
                                                        typename Mono<T>::V* __restrict__ Qout) {
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sop = reinterpret_cast<T*>(smem_raw);
     if (SMEM_OP) {
@@ -677,6 +680,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(
     int tab_H, int tab_W, const T* __restrict__ uhat, const typename Mono<T>::V* __restrict__ Cleaf,
     const typename Mono<T>::V* __restrict__ Qleaf, const T* __restrict__ tofsT,
     double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
+    griddep_wait();
     using M = Mono<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tab_n = (2 * tab_H + 1) * tab_W;
@@ -1032,6 +1036,7 @@ __global__ void __launch_bounds__(StripMultiCfg<T, KR>::WARPS * 32) p2p_strip_mu
     const T* __restrict__ f_sorted, int64_t f_stride, const T* __restrict__ table, int tab_H, int tab_W,
     const typename Mono<T>::V* __restrict__ Qleaf, int64_t q_stride, double* __restrict__ u_near,
     int64_t u_stride) {
+    griddep_wait();
     using M = Mono<T>;
     using V = typename M::V;
     using Cfg = StripMultiCfg<T, KR>;
@@ -1511,7 +1516,7 @@ static cudaError_t launch_translate(int level, const T* q, const T* u_par, const
     const int lg = MODE == kModeM2L ? level - 1 : level;
     const int64_t rows = (int64_t)1 << (2 * lg);
     dim3 grid((unsigned)((rows + C::BB - 1) / C::BB), MODE == kModeM2L ? 4 : 1);
-    translate_kernel<T, NP, MODE><<<grid, C::THREADS, C::SMEM, s>>>(
+    (void)launch_dependent(translate_kernel<T, NP, MODE>, dim3(grid), dim3(C::THREADS), C::SMEM, s,
         level, q, u_par, op, l2l, mono, (const V*)Qin, (const V*)Cpar, out, (V*)Qout, (V*)Cout);
     return cudaGetLastError();
 }
@@ -1529,10 +1534,10 @@ static cudaError_t launch_m2m_warp(const DeviceOps& ops, int k, int level, const
             cudaError_t e = ensure_dynamic_smem((const void*)m2m_warp_kernel<T, NP, true>, op_bytes);
             if (e != cudaSuccess) return e;
         }
-        m2m_warp_kernel<T, NP, true><<<(int)blocks, 256, op_bytes, s>>>(level, q_child, (const T*)ops.m2m[k],
+        (void)launch_dependent(m2m_warp_kernel<T, NP, true>, dim3((int)blocks), dim3(256), op_bytes, s, level, q_child, (const T*)ops.m2m[k],
                                                                          (const V*)Q_child, q_parent, (V*)Q_parent);
     } else {
-        m2m_warp_kernel<T, NP, false><<<(int)blocks, 256, 0, s>>>(level, q_child, (const T*)ops.m2m[k],
+        (void)launch_dependent(m2m_warp_kernel<T, NP, false>, dim3((int)blocks), dim3(256), 0, s, level, q_child, (const T*)ops.m2m[k],
                                                                    (const V*)Q_child, q_parent, (V*)Q_parent);
     }
     return cudaGetLastError();
@@ -1558,7 +1563,7 @@ static cudaError_t launch_m2l_splitk(const DeviceOps& ops, int k, int level, con
     }
     const int64_t rows = (int64_t)1 << (2 * (level - 1));
     dim3 grid((unsigned)((rows + 31) / 32), 4);
-    m2l_splitk_kernel<T, NP><<<grid, SkCfg<T, NP>::WARPS * 32, smem, s>>>(level, q, u_par, (const T*)ops.tifo[k], l2l,
+    (void)launch_dependent(m2l_splitk_kernel<T, NP>, dim3(grid), dim3(SkCfg<T, NP>::WARPS * 32), smem, s, level, q, u_par, (const T*)ops.tifo[k], l2l,
                                                               (const T*)ops.mono[k], (const V*)Qin, (const V*)Cpar,
                                                               out, (V*)Cout);
     return cudaGetLastError();
@@ -1603,7 +1608,7 @@ static cudaError_t launch_p2p_np(const TreeView& t, const DeviceOps& ops, const 
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     using V = typename Mono<T>::V;
-    p2p_leaf_kernel<T, NP><<<(int)blocks, kP2PWarps * 32, smem, s>>>(
+    (void)launch_dependent(p2p_leaf_kernel<T, NP>, dim3((int)blocks), dim3(kP2PWarps * 32), smem, s,
         t.L, t.side, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted, (const T*)ops.p2p_table,
         ops.tab_H, ops.tab_W, uhat, (const V*)Cleaf, (const V*)Qleaf, (const T*)ops.tofsT, u, un, uf);
     return cudaGetLastError();
@@ -1669,7 +1674,7 @@ static cudaError_t launch_p2p_multi_kr(const TreeView& t, const DeviceOps& ops, 
     const int64_t strips = (int64_t)n * ((n + SW - 1) / SW);
     int64_t blocks = std::min<int64_t>(strips, (int64_t)num_sms * blocks_per_sm(fn, Cfg::WARPS * 32, smem));
     if (blocks < 1) blocks = 1;
-    p2p_strip_multi_kernel<T, KR><<<(int)blocks, Cfg::WARPS * 32, smem, s>>>(
+    (void)launch_dependent(p2p_strip_multi_kernel<T, KR>, dim3((int)blocks), dim3(Cfg::WARPS * 32), smem, s,
         t.L, t.side, SW, nr, t.src_begin, t.src_loc, t.tgt_begin, t.tgt_loc, t.tgt_perm, f_sorted, f_stride,
         (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, (const V*)Qleaf, q_stride, un, u_stride);
     return cudaGetLastError();

@@ -62,6 +62,7 @@ __device__ __forceinline__ int64_t plane_entry(int64_t S, int64_t off_p, int l, 
 
 // ------------------------------------------------------------------------- tree build
 __global__ void pid_kernel(const int64_t* __restrict__ off, int np, int32_t* __restrict__ pid) {
+    griddep_wait();
     for (int p = blockIdx.x; p < np; p += gridDim.x)
         for (int64_t i = off[p] + threadIdx.x; i < off[p + 1]; i += blockDim.x) pid[i] = p;
 }
@@ -70,6 +71,7 @@ __global__ void pid_kernel(const int64_t* __restrict__ off, int np, int32_t* __r
 __global__ void bbox_forest_kernel(const int2* __restrict__ src, const int64_t* __restrict__ soff,
                                    const int2* __restrict__ tgt, const int64_t* __restrict__ toff, int np,
                                    int4* __restrict__ bb) {
+    griddep_wait();
     __shared__ int red[4][kThreads / 32];
     for (int p = blockIdx.x; p < np; p += gridDim.x) {
         int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
@@ -121,6 +123,7 @@ __device__ __forceinline__ int64_t leaf_of(const ProblemGeo& g, int p, int2 v, i
 // leaf counts; rank[i] = the point's arrival rank in its leaf (its slot offset later)
 __global__ void count_forest_kernel(const int2* __restrict__ xy, int64_t n, ProblemGeo g, int ls,
                                     int32_t* __restrict__ cnt, int32_t* __restrict__ rank) {
+    griddep_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lx, ly;
         rank[i] = atomicAdd(cnt + leaf_of(g, g.pid[i], xy[i], ls, lx, ly), 1);
@@ -129,6 +132,7 @@ __global__ void count_forest_kernel(const int2* __restrict__ xy, int64_t n, Prob
 
 __global__ void max2_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int64_t n,
                             int* __restrict__ out2) {
+    griddep_wait();
     int ma = 0, mb = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         ma = max(ma, a[i]);
@@ -147,6 +151,7 @@ __global__ void max2_kernel(const int32_t* __restrict__ a, const int32_t* __rest
 __global__ void scatter_forest_kernel(const int2* __restrict__ xy, int64_t n, ProblemGeo g, int ls,
                                       const int32_t* __restrict__ begin, const int32_t* __restrict__ rank,
                                       int32_t* __restrict__ loc, int32_t* __restrict__ perm) {
+    griddep_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lx, ly;
         const int64_t leaf = leaf_of(g, g.pid[i], xy[i], ls, lx, ly);
@@ -160,6 +165,7 @@ __global__ void scatter_forest_kernel(const int2* __restrict__ xy, int64_t n, Pr
 constexpr int kScanBlock = 1024;
 
 __global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
+    griddep_wait();
     __shared__ int32_t w[kThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     int32_t v = 0;
@@ -177,6 +183,7 @@ __global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, in
 
 // exclusive scan of the block totals in place (one block); total to sums[nb]
 __global__ void scan_sums_kernel(int32_t* __restrict__ sums, int nb) {
+    griddep_wait();
     __shared__ int32_t carry_s, w[1024 / 32];
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
@@ -212,6 +219,7 @@ __global__ void scan_sums_kernel(int32_t* __restrict__ sums, int nb) {
 
 __global__ void scan_apply_kernel(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ sums,
                                   int32_t* __restrict__ out) {
+    griddep_wait();
     __shared__ int32_t w[kThreads / 32];
     constexpr int PER = kScanBlock / kThreads;  // 4 consecutive items per thread
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * PER;
@@ -260,6 +268,7 @@ struct LevelGeo {
 // flags of the leaves (k = 0): box non-empty if it holds a source or a target
 __global__ void flag_leaves_kernel(const int32_t* __restrict__ cs, const int32_t* __restrict__ ct, int64_t NL,
                                    ProblemGeo g, int np, LevelGeo lv, int32_t* __restrict__ flags) {
+    griddep_wait();
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < NL; a += (int64_t)gridDim.x * blockDim.x) {
         if (cs[a] + ct[a] == 0) continue;
         const int p = upper_index(g.leaf_off, np, a);
@@ -273,6 +282,7 @@ __global__ void flag_leaves_kernel(const int32_t* __restrict__ cs, const int32_t
 // flags of level k >= 1 from the compact map of level k-1 (any child present)
 __global__ void flag_parents_kernel(ProblemGeo g, LevelGeo lv, LevelGeo lc, const int32_t* __restrict__ map_child,
                                     int32_t* __restrict__ flags) {
+    griddep_wait();
     const int64_t n = 4 * lv.S;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / lv.S);
@@ -297,6 +307,7 @@ __global__ void flag_parents_kernel(ProblemGeo g, LevelGeo lv, LevelGeo lc, cons
 // map[e] = compact id or -1; box records of the compact ids
 __global__ void compact_kernel(ProblemGeo g, LevelGeo lv, const int32_t* __restrict__ scan, int32_t* __restrict__ map,
                                int32_t* __restrict__ bp, int32_t* __restrict__ bxy) {
+    griddep_wait();
     const int64_t n = 4 * lv.S;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const bool on = scan[e + 1] != scan[e];
@@ -326,6 +337,7 @@ __global__ void links_kernel(ProblemGeo g, LevelGeo lv, int64_t nb, const int32_
                              LevelGeo lpar, const int32_t* __restrict__ map_par, LevelGeo lch,
                              const int32_t* __restrict__ map_ch, int32_t* __restrict__ par, int32_t* __restrict__ ch,
                              int32_t* __restrict__ il) {
+    griddep_wait();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
         const int p = bp[b];
         const int x = bxy[b] & 0xffff, y = bxy[b] >> 16;
@@ -358,6 +370,7 @@ __global__ void links_kernel(ProblemGeo g, LevelGeo lv, int64_t nb, const int32_
 // strips of SW leaves of one leaf row holding at least one target
 __global__ void strip_flag_kernel(ProblemGeo g, int np, const int64_t* __restrict__ strip_off, int SW,
                                   const int32_t* __restrict__ tbeg, int32_t* __restrict__ flags) {
+    griddep_wait();
     const int64_t n = strip_off[np];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const int p = upper_index(strip_off, np, q);
@@ -372,6 +385,7 @@ __global__ void strip_flag_kernel(ProblemGeo g, int np, const int64_t* __restric
 
 __global__ void strip_compact_kernel(ProblemGeo g, int np, const int64_t* __restrict__ strip_off, int SW,
                                      const int32_t* __restrict__ scan, int4* __restrict__ strips) {
+    griddep_wait();
     const int64_t n = strip_off[np];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         if (scan[q + 1] == scan[q]) continue;
@@ -384,6 +398,7 @@ __global__ void strip_compact_kernel(ProblemGeo g, int np, const int64_t* __rest
 
 __global__ void gather_kernel(const int32_t* __restrict__ a, const int64_t* __restrict__ idx, int n,
                               int32_t* __restrict__ out) {
+    griddep_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[idx[i]];
 }
@@ -399,6 +414,7 @@ __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t
                                                        const double* __restrict__ f, T* __restrict__ f_sorted,
                                                        const T* __restrict__ tofsT, int side, T* __restrict__ qhat,
                                                        typename Mono<T>::V* __restrict__ Q) {
+    griddep_wait();
     using M = Mono<T>;
     constexpr int PL = NP / 32;
     const int lane = threadIdx.x & 31;
@@ -446,6 +462,7 @@ __global__ void __launch_bounds__(256) m2m_list_kernel(int64_t nb, const int32_t
                                                        const T* __restrict__ qc, const T* __restrict__ m2m,
                                                        const typename Mono<T>::V* __restrict__ Qin,
                                                        T* __restrict__ qp, typename Mono<T>::V* __restrict__ Qout) {
+    griddep_wait();
     using M = Mono<T>;
     constexpr int CL = 4 * NP / 32, PL = NP / 32;
     const int lane = threadIdx.x & 31;
@@ -511,6 +528,7 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
     const T* __restrict__ q, const T* __restrict__ u_par, const T* __restrict__ ops, const T* __restrict__ l2l,
     const T* __restrict__ mono, const typename Mono<T>::V* __restrict__ Qin,
     const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out, typename Mono<T>::V* __restrict__ Cout) {
+    griddep_wait();
     using M = Mono<T>;
     using V = typename M::V;
     constexpr int W = LCfg<T, NP>::WARPS;
@@ -662,6 +680,7 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
     const T* __restrict__ table, int tab_H, int tab_W, const T* __restrict__ uhat,
     const typename Mono<T>::V* __restrict__ Cleaf, const typename Mono<T>::V* __restrict__ Qleaf,
     const T* __restrict__ tofsT, double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
+    griddep_wait();
     using M = Mono<T>;
     using V = typename M::V;
     using Cfg = LStripCfg<T>;
@@ -873,9 +892,9 @@ int alloc(std::vector<void*>& owned, int64_t& bytes, void** out, size_t n, cudaS
 cudaError_t exscan(const int32_t* in, int32_t* out, int64_t n, int32_t* sums, cudaStream_t s) {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
-    scan_reduce_kernel<<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(sums, (int)nb);
-    scan_apply_kernel<<<(unsigned)nb, kThreads, 0, s>>>(in, n, sums, out);
+    (void)launch_dependent(scan_reduce_kernel, dim3((unsigned)nb), dim3(kThreads), 0, s, in, n, sums);
+    (void)launch_dependent(scan_sums_kernel, dim3(1), dim3(1024), 0, s, sums, (int)nb);
+    (void)launch_dependent(scan_apply_kernel, dim3((unsigned)nb), dim3(kThreads), 0, s, in, n, sums, out);
     return cudaGetLastError();
 }
 
@@ -917,8 +936,8 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     if (np == 1) {
         LFMM_CUDA_TRY(cudaMemsetAsync(F.spid, 0, (size_t)(ns + nt) * sizeof(int32_t), s));
     } else {
-        pid_kernel<<<std::min(np, 152 * 8), kThreads, 0, s>>>(soff, np, F.spid);
-        pid_kernel<<<std::min(np, 152 * 8), kThreads, 0, s>>>(toff, np, F.tpid);
+        (void)launch_dependent(pid_kernel, dim3(std::min(np, 152 * 8)), dim3(kThreads), 0, s, soff, np, F.spid);
+        (void)launch_dependent(pid_kernel, dim3(std::min(np, 152 * 8)), dim3(kThreads), 0, s, toff, np, F.tpid);
     }
     // bounding boxes
     if ((st = A(&v, (size_t)np * sizeof(int4)))) return st;
@@ -927,7 +946,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
         LFMM_CUDA_TRY(launch_set4((int*)bb, INT_MAX, INT_MAX, INT_MIN, INT_MIN, s));
         LFMM_CUDA_TRY(launch_bbox(src, ns, tgt, nt, (int*)bb, s));
     } else {
-        bbox_forest_kernel<<<std::min(np, 152 * 8), kThreads, 0, s>>>((const int2*)src, soff, (const int2*)tgt,
+        (void)launch_dependent(bbox_forest_kernel, dim3(std::min(np, 152 * 8)), dim3(kThreads), 0, s, (const int2*)src, soff, (const int2*)tgt,
                                                                        toff, np, bb);
     }
     LFMM_CUDA_TRY(cudaGetLastError());
@@ -992,10 +1011,10 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
         LFMM_CUDA_TRY(cudaMemcpyAsync(dL, F.L.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         LFMM_CUDA_TRY(cudaMemcpyAsync(dlo, leaf_off.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         ProblemGeo g{F.spid, dx0, dy0, dL, dlo};
-        count_forest_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>((const int2*)src, ns, g, ls, cs, rank_s);
+        (void)launch_dependent(count_forest_kernel, dim3(grid_for(ns, kThreads)), dim3(kThreads), 0, s, (const int2*)src, ns, g, ls, cs, rank_s);
         g.pid = F.tpid;
-        count_forest_kernel<<<grid_for(nt, kThreads), kThreads, 0, s>>>((const int2*)tgt, nt, g, ls, ct, rank_t);
-        max2_kernel<<<grid_for(NL, kThreads), kThreads, 0, s>>>(cs, ct, NL, mx);
+        (void)launch_dependent(count_forest_kernel, dim3(grid_for(nt, kThreads)), dim3(kThreads), 0, s, (const int2*)tgt, nt, g, ls, ct, rank_t);
+        (void)launch_dependent(max2_kernel, dim3(grid_for(NL, kThreads)), dim3(kThreads), 0, s, cs, ct, NL, mx);
         LFMM_CUDA_TRY(cudaGetLastError());
         timer->add_launches(3);
         int hm[2];
@@ -1039,10 +1058,10 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     F.tloc = F.sperm + ns;
     F.tperm = F.tloc + nt;
     g.pid = F.spid;
-    scatter_forest_kernel<<<grid_for(ns, kThreads), kThreads, 0, s>>>((const int2*)src, ns, g, ls, F.sbeg, rank_s,
+    (void)launch_dependent(scatter_forest_kernel, dim3(grid_for(ns, kThreads)), dim3(kThreads), 0, s, (const int2*)src, ns, g, ls, F.sbeg, rank_s,
                                                                        F.sloc, F.sperm);
     g.pid = F.tpid;
-    scatter_forest_kernel<<<grid_for(nt, kThreads), kThreads, 0, s>>>((const int2*)tgt, nt, g, ls, F.tbeg, rank_t,
+    (void)launch_dependent(scatter_forest_kernel, dim3(grid_for(nt, kThreads)), dim3(kThreads), 0, s, (const int2*)tgt, nt, g, ls, F.tbeg, rank_t,
                                                                        F.tloc, F.tperm);
     LFMM_CUDA_TRY(cudaGetLastError());
     timer->add_launches(8);
@@ -1102,14 +1121,14 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
         if (k == 0) {
             LFMM_CUDA_TRY(cudaMemsetAsync(lv.map, 0, (size_t)4 * lv.S * sizeof(int32_t), s));
             g.pid = F.spid;
-            flag_leaves_kernel<<<grid_for(NL, kThreads), kThreads, 0, s>>>(cs, ct, NL, g, np, lg, lv.map);
+            (void)launch_dependent(flag_leaves_kernel, dim3(grid_for(NL, kThreads)), dim3(kThreads), 0, s, cs, ct, NL, g, np, lg, lv.map);
         } else {
             const ForestLevel& lc = F.levels[k - 1];
             LevelGeo lcg{k - 1, np, lc.S, lc.off, lc.size};
-            flag_parents_kernel<<<grid_for(4 * lv.S, kThreads), kThreads, 0, s>>>(g, lg, lcg, lc.map, lv.map);
+            (void)launch_dependent(flag_parents_kernel, dim3(grid_for(4 * lv.S, kThreads)), dim3(kThreads), 0, s, g, lg, lcg, lc.map, lv.map);
         }
         LFMM_CUDA_TRY(exscan(lv.map, scan[k], 4 * lv.S, (int32_t*)ssum.ptr, s));
-        compact_kernel<<<grid_for(4 * lv.S, kThreads), kThreads, 0, s>>>(g, lg, scan[k], lv.map, nullptr, nullptr);
+        (void)launch_dependent(compact_kernel, dim3(grid_for(4 * lv.S, kThreads)), dim3(kThreads), 0, s, g, lg, scan[k], lv.map, nullptr, nullptr);
         LFMM_CUDA_TRY(cudaGetLastError());
         timer->add_launches(5);
     }
@@ -1123,7 +1142,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     int64_t* didx = (int64_t*)gi.ptr;
     int32_t* dval = (int32_t*)(didx + idx.size());
     LFMM_CUDA_TRY(cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    gather_kernel<<<(unsigned)((idx.size() + 127) / 128), 128, 0, s>>>(scan[0], didx, (int)idx.size(), dval);
+    (void)launch_dependent(gather_kernel, dim3((unsigned)((idx.size() + 127) / 128)), dim3(128), 0, s, scan[0], didx, (int)idx.size(), dval);
     LFMM_CUDA_TRY(cudaGetLastError());
     std::vector<int32_t> hval(idx.size());
     LFMM_CUDA_TRY(cudaMemcpyAsync(hval.data(), dval, hval.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1147,7 +1166,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
         lv.il = lv.par + lv.nb;
         lv.ch = k >= 1 ? lv.il + lv.nb * 27 : nullptr;
         LevelGeo lg{k, np, lv.S, lv.off, lv.size};
-        compact_kernel<<<grid_for(4 * lv.S, kThreads), kThreads, 0, s>>>(g, lg, scan[k], lv.map, lv.bp, lv.bxy);
+        (void)launch_dependent(compact_kernel, dim3(grid_for(4 * lv.S, kThreads)), dim3(kThreads), 0, s, g, lg, scan[k], lv.map, lv.bp, lv.bxy);
         LFMM_CUDA_TRY(cudaGetLastError());
         timer->add_launches(1);
     }
@@ -1160,7 +1179,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
                                 : lg;
         LevelGeo lch = k >= 1 ? LevelGeo{k - 1, np, F.levels[k - 1].S, F.levels[k - 1].off, F.levels[k - 1].size}
                               : lg;
-        links_kernel<<<grid_for(lv.nb, kThreads), kThreads, 0, s>>>(
+        (void)launch_dependent(links_kernel, dim3(grid_for(lv.nb, kThreads)), dim3(kThreads), 0, s,
             g, lg, lv.nb, lv.bp, lv.bxy, lv.map, lpar, has_par ? F.levels[k + 1].map : nullptr, lch,
             k >= 1 ? F.levels[k - 1].map : nullptr, lv.par, lv.ch, lv.il);
         LFMM_CUDA_TRY(cudaGetLastError());
@@ -1188,12 +1207,12 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     int32_t* sscan = sflag + ncand + 1;
     int32_t* ssums = sscan + ncand + 1;
     LFMM_CUDA_TRY(cudaMemcpyAsync(dsoff, soffs.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    strip_flag_kernel<<<grid_for(ncand, kThreads), kThreads, 0, s>>>(g, np, dsoff, SW, F.tbeg, sflag);
+    (void)launch_dependent(strip_flag_kernel, dim3(grid_for(ncand, kThreads)), dim3(kThreads), 0, s, g, np, dsoff, SW, F.tbeg, sflag);
     LFMM_CUDA_TRY(exscan(sflag, sscan, ncand, ssums, s));
     if ((st = A(&v, (size_t)std::max<int64_t>(ncand, 1) * sizeof(int4) + 16))) return st;
     F.strips = (int4*)v;
     F.n_strips_d = (int32_t*)(F.strips + std::max<int64_t>(ncand, 1));
-    strip_compact_kernel<<<grid_for(ncand, kThreads), kThreads, 0, s>>>(g, np, dsoff, SW, sscan, F.strips);
+    (void)launch_dependent(strip_compact_kernel, dim3(grid_for(ncand, kThreads)), dim3(kThreads), 0, s, g, np, dsoff, SW, sscan, F.strips);
     LFMM_CUDA_TRY(cudaMemcpyAsync(F.n_strips_d, sscan + ncand, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     LFMM_CUDA_TRY(cudaGetLastError());
     timer->add_launches(5);
@@ -1218,11 +1237,11 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         if (l0.nb > 0) {
             int64_t blocks = std::min<int64_t>((l0.nb * 32 + 255) / 256, 152 * 64);
             if (NP == 32)
-                p2m_list_kernel<T, 32><<<(int)blocks, 256, 0, s>>>(l0.nb, l0.bp, l0.bxy, g, F.sbeg, F.sloc, F.sperm,
+                (void)launch_dependent(p2m_list_kernel<T, 32>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.bp, l0.bxy, g, F.sbeg, F.sloc, F.sperm,
                                                                     f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0),
                                                                     Qm(0));
             else
-                p2m_list_kernel<T, 64><<<(int)blocks, 256, 0, s>>>(l0.nb, l0.bp, l0.bxy, g, F.sbeg, F.sloc, F.sperm,
+                (void)launch_dependent(p2m_list_kernel<T, 64>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.bp, l0.bxy, g, F.sbeg, F.sloc, F.sperm,
                                                                     f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0),
                                                                     Qm(0));
             LFMM_CUDA_TRY(cudaGetLastError());
@@ -1236,10 +1255,10 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             if (lv.nb == 0) continue;
             int64_t blocks = std::min<int64_t>((lv.nb * 32 + 255) / 256, 152 * 8);
             if (NP == 32)
-                m2m_list_kernel<T, 32><<<(int)blocks, 256, 0, s>>>(lv.nb, lv.ch, Qx(k - 1), (const T*)ops.m2m[k],
+                (void)launch_dependent(m2m_list_kernel<T, 32>, dim3((int)blocks), dim3(256), 0, s, lv.nb, lv.ch, Qx(k - 1), (const T*)ops.m2m[k],
                                                                     Qm(k - 1), Qx(k), Qm(k));
             else
-                m2m_list_kernel<T, 64><<<(int)blocks, 256, 0, s>>>(lv.nb, lv.ch, Qx(k - 1), (const T*)ops.m2m[k],
+                (void)launch_dependent(m2m_list_kernel<T, 64>, dim3((int)blocks), dim3(256), 0, s, lv.nb, lv.ch, Qx(k - 1), (const T*)ops.m2m[k],
                                                                     Qm(k - 1), Qx(k), Qm(k));
             LFMM_CUDA_TRY(cudaGetLastError());
             pt.add_launches(1);
@@ -1262,7 +1281,7 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                     cudaError_t e = ensure_dynamic_smem((const void*)m2l_list_kernel<T, NPc>, smem);
                     if (e != cudaSuccess) return e;
                 }
-                m2l_list_kernel<T, NPc><<<grid, LCfg<T, NPc>::WARPS * 32, smem, s>>>(
+                (void)launch_dependent(m2l_list_kernel<T, NPc>, dim3(grid), dim3(LCfg<T, NPc>::WARPS * 32), smem, s,
                     lv.d_cls, lv.il, l2l ? lv.par : nullptr, Qx(k), l2l ? Ux(k + 1) : nullptr,
                     (const T*)ops.tifo[k], l2l ? (const T*)ops.l2l[k + 1] : nullptr, (const T*)ops.mono[k], Qm(k),
                     l2l ? Cm(k + 1) : nullptr, Ux(k), Cm(k));
@@ -1290,7 +1309,7 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                 if (e != cudaSuccess) return e;
             }
             const int per_sm = blocks_per_sm((const void*)p2p_list_kernel<T, NPc>, Cfg::WARPS * 32, smem);
-            p2p_list_kernel<T, NPc><<<num_sms * per_sm, Cfg::WARPS * 32, smem, s>>>(
+            (void)launch_dependent(p2p_list_kernel<T, NPc>, dim3(num_sms * per_sm), dim3(Cfg::WARPS * 32), smem, s,
                 F.strips, F.n_strips_d, g, lm, F.side, F.SW, F.sbeg, F.sloc, F.tbeg, F.tloc, F.tperm, f_sorted,
                 (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, far ? Ux(0) : nullptr, far ? Cm(0) : nullptr, Qm(0),
                 (const T*)ops.tofsT, u, un, uf);

@@ -92,6 +92,7 @@ __global__ void histogram_kernel(const int2* __restrict__ src, int64_t ns,
                                  const int2* __restrict__ tgt, int64_t nt, int64_t x0,
                                  int64_t y0, int shift, int32_t* __restrict__ cs,
                                  int32_t* __restrict__ ct, int32_t* __restrict__ rank) {
+    griddep_wait();
     const int64_t n = ns + nt;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -284,6 +285,7 @@ __global__ void scatter_kernel(const int2* __restrict__ xy, int64_t n, int64_t x
                                int shift, int leaf_side, int n_side, const int32_t* __restrict__ begin,
                                int32_t* __restrict__ cursor, int32_t* __restrict__ loc,
                                int32_t* __restrict__ perm) {
+    griddep_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = xy[i];
@@ -307,6 +309,7 @@ __global__ void set4_kernel(int* p, int a, int b, int c, int d) {
 // words[0..3] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN} (bounding box to be reduced),
 // words[4..9] = 0 (maxima and counts of coarsen_kernel), zero[0..n_zero) = 0
 __global__ void init_tree_kernel(int* __restrict__ words, int32_t* __restrict__ zero, int64_t n_zero) {
+    griddep_wait();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < 10) words[t] = t < 2 ? INT_MAX : (t < 4 ? INT_MIN : 0);
     for (int64_t i = t; i < n_zero / 4; i += (int64_t)gridDim.x * blockDim.x)
@@ -329,7 +332,7 @@ cudaError_t launch_set4(int* p, int a, int b, int c, int d, cudaStream_t s) {
 }
 
 cudaError_t launch_init_tree(int* words, int32_t* zero, int64_t n_zero, cudaStream_t s) {
-    init_tree_kernel<<<grid_for(std::max<int64_t>(n_zero / 4, 10), kThreads), kThreads, 0, s>>>(words, zero, n_zero);
+    (void)launch_dependent(init_tree_kernel, dim3(grid_for(std::max<int64_t>(n_zero / 4, 10), kThreads)), dim3(kThreads), 0, s, words, zero, n_zero);
     return cudaGetLastError();
 }
 
@@ -342,7 +345,7 @@ cudaError_t launch_bbox(const int32_t* a, int64_t na, const int32_t* b, int64_t 
 cudaError_t launch_histogram(const int32_t* src, int64_t ns, const int32_t* tgt, int64_t nt,
                              int64_t x0, int64_t y0, int shift, int32_t* cs, int32_t* ct,
                              cudaStream_t s, int32_t* rank) {
-    histogram_kernel<<<grid_for(ns + nt, kThreads), kThreads, 0, s>>>(
+    (void)launch_dependent(histogram_kernel, dim3(grid_for(ns + nt, kThreads)), dim3(kThreads), 0, s,
         (const int2*)src, ns, (const int2*)tgt, nt, x0, y0, shift, cs, ct, rank);
     return cudaGetLastError();
 }
@@ -386,7 +389,7 @@ cudaError_t launch_scan2(const int32_t* a, int32_t* oa, const int32_t* b, int32_
 cudaError_t launch_scatter(const int32_t* xy, int64_t n, int64_t x0, int64_t y0, int shift,
                            int leaf_side, int L, const int32_t* begin, int32_t* cursor, int32_t* loc,
                            int32_t* perm, cudaStream_t s) {
-    scatter_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>((const int2*)xy, n, x0, y0, shift,
+    (void)launch_dependent(scatter_kernel, dim3(grid_for(n, kThreads)), dim3(kThreads), 0, s, (const int2*)xy, n, x0, y0, shift,
                                                              leaf_side, 1 << L, begin, cursor, loc, perm);
     return cudaGetLastError();
 }
