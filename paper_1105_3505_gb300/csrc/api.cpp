@@ -210,6 +210,20 @@ int validate_opts(const lfmm_opts& o) {
     return LFMM_OK;
 }
 
+// Page-locked host words for the tree build's readbacks (one set per host thread): a
+// copy into pageable memory would be staged by the driver and complete later.
+int* readback_words() {
+    static thread_local int* words = [] {
+        void* h = nullptr;
+        if (cudaMallocHost(&h, 16 * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            h = nullptr;
+        }
+        return (int*)h;
+    }();
+    return words;
+}
+
 int ilog2_ceil(int64_t v) {
     int k = 0;
     while (((int64_t)1 << k) < v) ++k;
@@ -318,8 +332,14 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         tree_timer->add_launches(2);
     }
     int h10[10];
-    LFMM_CUDA_TRY(cudaMemcpyAsync(h10, d4, (have_guess ? 10 : 4) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+    {
+        int* hw = readback_words();
+        int* dst = hw ? hw : h10;
+        const int nw = have_guess ? 10 : 4;
+        LFMM_CUDA_TRY(cudaMemcpyAsync(dst, d4, nw * sizeof(int), cudaMemcpyDeviceToHost, s));
+        LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hw) std::copy(hw, hw + nw, h10);
+    }
     p->x0 = h10[0];
     p->y0 = h10[1];
     const int64_t ext = std::max((int64_t)h10[2] - h10[0], (int64_t)h10[3] - h10[1]) + 1;
