@@ -510,7 +510,8 @@ def solvers_leg(lfmm):
     """The two solvers built on the lattice FMM, wall clock (host-driven GMRES):
     a Dirichlet problem on a digital disk of radius 1500 (about 7.07e6 nodes, 8.5e3
     boundary nodes; data x^2 - y^2 + 3 x y, scaled) and a lattice with 10^4 changed bars in
-    a 2048^2 box; both with the float-float path at p = 16."""
+    a 2048^2 box; both with the float-float path at p = 16.  Also the GPU quadrature of
+    phi near the origin (binary64) for radii 8, 16 and 32."""
     import time
     import torch
     from paper_1105_3505_gb300.bvp import LatticeDirichlet
@@ -557,6 +558,17 @@ def solvers_leg(lfmm):
                                   "gmres_iterations": li.iterations, "solve_ms": (t2 - t1) * 1e3,
                                   "ms_per_iteration": (t2 - t1) * 1e3 / li.iterations, "residual": li.residual}
     li.close()
+    # phi near the origin by the 2-D quadrature (binary64), 5-point and anisotropic operators
+    for name, offs, w in (("phi_quadrature_5point", [[1, 0], [0, 1]], [1.0, 1.0]),
+                          ("phi_quadrature_anisotropic_1_20", [[1, 0], [0, 1]], [1.0, 20.0])):
+        row = {}
+        for R in (8, 16, 32):
+            lfmm.lfmm_phi_quadrature(offs, w, 2)  # warm-up
+            t0 = time.perf_counter()
+            lfmm.lfmm_phi_quadrature(offs, w, R)
+            dt = time.perf_counter() - t0
+            row[f"R{R}"] = {"entries": (2 * R + 1) ** 2, "ms": dt * 1e3}
+        res[name] = row
     return res
 
 
