@@ -349,8 +349,8 @@ int64_t lfmm_launch_count(void);
 int lfmm_phi_table(int32_t R, double* out);
 /* phi near the origin for a symmetric lattice operator with constant coefficients,
  * by the two-dimensional quadrature of Sec. 3.2 on the GPU (boxes of about one
- * oscillation with 20 x 20 Gauss-Legendre rules, the singular centre box as a sum of
- * annuli with Richardson extrapolation).  The operator is
+ * oscillation with 20 x 20 Gauss-Legendre rules next to the centre and 14 x 14 further
+ * out, the singular centre box as a sum of annuli with Richardson extrapolation).  The operator is
  *   (A u)(m) = sum_k w[k] (2 u(m) - u(m + d_k) - u(m - d_k)),  d_k = (d[2k], d[2k+1]),
  * with 1 <= n_terms <= 8 distinct offsets (no two opposite), |d| <= 64, w[k] > 0, and two
  * offsets of determinant +-1 (so that the symbol vanishes only at 0); the 5-point

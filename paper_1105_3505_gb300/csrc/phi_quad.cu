@@ -9,8 +9,9 @@
 // d = (1,0), (0,1), w = 1, 1).  Such operators have no closed recurrence in general; the
 // quadrature needs only the symbol.  For a table entry m:
 //   - the square is cut into n x n boxes, n the odd number >= |m|_inf (about one
-//     oscillation of the integrand per box); every box but the centre one gets a 20 x 20
-//     Gauss-Legendre rule;
+//     oscillation of the integrand per box); the rings of boxes around the centre one
+//     get a 20 x 20 Gauss-Legendre rule, the boxes from about three box sizes out (see
+//     below) 14 x 14;
 //   - the centre box [-a, a]^2, a = pi / n, is the sum of the annuli
 //     Omega_j = [-a 2^-j, a 2^-j]^2 minus [-a 2^-j-1, a 2^-j-1]^2, j >= 0, each cut
 //     into eight rectangles with a 20 x 20 rule; the integrand is bounded at 0 and its
@@ -39,6 +40,7 @@ namespace {
 
 constexpr int kQuadMaxTerms = 8;
 constexpr int kQuadNodes = 20;
+constexpr int kQuadNodesFar = 14;  // boxes two or more rings away from the centre
 constexpr int kQuadAnnuli = 16;
 constexpr int kQuadThreads = 256;
 constexpr int kQuadMaxSplit = 8;
@@ -50,6 +52,7 @@ struct QuadStencil {
     int dx[kQuadMaxTerms], dy[kQuadMaxTerms];
     double w[kQuadMaxTerms];
     double gx[kQuadNodes], gw[kQuadNodes];  // Gauss-Legendre on [-1, 1]
+    double fx[kQuadNodesFar], fw[kQuadNodesFar];
     double c;                                // sqrt(det Q) / max(Q_11, Q_22)
 };
 
@@ -68,17 +71,19 @@ __device__ __forceinline__ double integrand(const QuadStencil& q, int m1, int m2
     return -2.0 * h * h / sig;
 }
 
-// node `idx` of the s x s split of the rectangle [x0, x1] x [y0, y1], a Gauss-Legendre
-// rule on each sub-rectangle: idx = (sub-rectangle) * NN + (node)
-__device__ __forceinline__ double rect_node(const QuadStencil& q, int m1, int m2, double x0, double x1, double y0,
-                                            double y1, int s, int idx) {
-    constexpr int NN = kQuadNodes * kQuadNodes;
+// node `idx` of the s x s split of the rectangle [x0, x1] x [y0, y1], a Q-point
+// Gauss-Legendre rule (nodes x, weights w) on each sub-rectangle: idx = (sub-rectangle)
+// * Q^2 + (node)
+template <int Q>
+__device__ __forceinline__ double rect_node(const QuadStencil& q, const double* x, const double* w, int m1, int m2,
+                                            double x0, double x1, double y0, double y1, int s, int idx) {
+    constexpr int NN = Q * Q;
     const int sub = idx / NN, node = idx % NN;
-    const int si = sub % s, sj = sub / s, i = node % kQuadNodes, j = node / kQuadNodes;
+    const int si = sub % s, sj = sub / s, i = node % Q, j = node / Q;
     const double hx = 0.5 * (x1 - x0) / s, hy = 0.5 * (y1 - y0) / s;
     const double xa = x0 + 2.0 * hx * si, ya = y0 + 2.0 * hy * sj;
-    const double t1 = xa + hx * (1.0 + q.gx[i]), t2 = ya + hy * (1.0 + q.gx[j]);
-    return q.gw[i] * q.gw[j] * hx * hy * integrand(q, m1, m2, t1, t2);
+    const double t1 = xa + hx * (1.0 + x[i]), t2 = ya + hy * (1.0 + x[j]);
+    return w[i] * w[j] * hx * hy * integrand(q, m1, m2, t1, t2);
 }
 
 __device__ double block_sum(double v, double* red) {
@@ -108,28 +113,32 @@ __global__ void __launch_bounds__(kQuadThreads) phi_quad_kernel(const QuadStenci
     const double h = kTwoPi / n;
     const int cb = (n - 1) / 2;  // the centre box, and the number of rings around it
     constexpr int NN = kQuadNodes * kQuadNodes;
-    // boxes away from the centre: the rings that need splitting box by box, then the
-    // rest in one flat loop
+    // boxes away from the centre: the rings closer than three box sizes (times c) to the
+    // origin's complex zeros box by box with the 20-point rule (split as needed), the
+    // rest in one flat loop with 14 points per side, which there reach the same accuracy
+    // (the integrand is about one oscillation of the numerator wide and far from the
+    // zeros).
     double outer = 0.0;
-    int k_flat = 1;
-    while (k_flat <= cb && quad_split(q.c, 2 * k_flat - 1) > 1) ++k_flat;
-    for (int k = 1; k < k_flat; ++k) {
+    int k_flat = 2;
+    while (k_flat <= cb && q.c * (2 * k_flat - 1) < 3.0 - 1e-12) ++k_flat;
+    for (int k = 1; k < k_flat && k <= cb; ++k) {
         const int s = quad_split(q.c, 2 * k - 1);
         for (int bj = cb - k; bj <= cb + k; ++bj)
             for (int bi = cb - k; bi <= cb + k; ++bi) {
                 if (max(abs(bi - cb), abs(bj - cb)) != k) continue;
                 const double x0 = -kPiQ + bi * h, y0 = -kPiQ + bj * h;
                 for (int idx = threadIdx.x; idx < s * s * NN; idx += blockDim.x)
-                    outer += rect_node(q, m1, m2, x0, x0 + h, y0, y0 + h, s, idx);
+                    outer += rect_node<kQuadNodes>(q, q.gx, q.gw, m1, m2, x0, x0 + h, y0, y0 + h, s, idx);
             }
     }
-    const int64_t n_outer = (int64_t)n * n * NN;
-    for (int64_t idx = threadIdx.x; idx < n_outer; idx += blockDim.x) {
-        const int box = (int)(idx / NN), node = (int)(idx % NN);
+    constexpr int NF = kQuadNodesFar * kQuadNodesFar;
+    const int n_outer = n * n * NF;  // below 2^31: n <= 129
+    for (int idx = threadIdx.x; idx < n_outer; idx += blockDim.x) {
+        const int box = idx / NF, node = idx - box * NF;
         const int bi = box % n, bj = box / n;
         if (max(abs(bi - cb), abs(bj - cb)) < k_flat) continue;
         const double x0 = -kPiQ + bi * h, y0 = -kPiQ + bj * h;
-        outer += rect_node(q, m1, m2, x0, x0 + h, y0, y0 + h, 1, node);
+        outer += rect_node<kQuadNodesFar>(q, q.fx, q.fw, m1, m2, x0, x0 + h, y0, y0 + h, 1, node);
     }
     const double outer_sum = block_sum(outer, red);
     // annuli of the centre box, one partial sum per annulus
@@ -145,7 +154,8 @@ __global__ void __launch_bounds__(kQuadThreads) phi_quad_kernel(const QuadStenci
             const int rr = r < 4 ? r : r + 1;
             const double xs[4] = {-aj, -bj, bj, aj};
             const int ci = rr % 3, cj = rr / 3;
-            part += rect_node(q, m1, m2, xs[ci], xs[ci + 1], xs[cj], xs[cj + 1], s0, idx % per_piece);
+            part += rect_node<kQuadNodes>(q, q.gx, q.gw, m1, m2, xs[ci], xs[ci + 1], xs[cj], xs[cj + 1], s0,
+                                          idx % per_piece);
         }
         const double ps = block_sum(part, red);
         if (threadIdx.x == 0) s_ann[j] = ps;
@@ -210,6 +220,11 @@ extern "C" int lfmm_phi_quadrature(const int32_t* d, const double* w, int32_t n_
     for (int i = 0; i < kQuadNodes; ++i) {
         q.gx[i] = x[i];
         q.gw[i] = wt[i];
+    }
+    gauss_legendre(kQuadNodesFar, x, wt);
+    for (int i = 0; i < kQuadNodesFar; ++i) {
+        q.fx[i] = x[i];
+        q.fw[i] = wt[i];
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int side = 2 * R + 1;
