@@ -21,11 +21,13 @@
 // The rule on a piece converges at a rate set by how far the complex zeros of the
 // symbol lie from it, relative to its size.  Near the origin those zeros are the zeros of
 // the quadratic form t'Qt, Q = sum_k w_k d_k d_k', whose imaginary parts are c |t| with
-// c = sqrt(det Q) / max(Q_11, Q_22) (c = 1 for the 5-point operator).  Every annulus
-// piece is therefore split into s x s sub-rectangles, s = ceil(1 / c), and an outer box
-// in ring k around the centre (Chebyshev distance k boxes) into ceil(1 / (c (2k - 1)))
-// per side, which keeps the relative distance at least that of the 5-point operator
-// with no splitting.  Operators with s > 8 (strongly anisotropic) are rejected.
+// c = sqrt(det Q) / max(Q_11, Q_22) (c = 1 for the 5-point operator); along t1 alone the
+// distance is set by c_x = sqrt(det Q) / Q_11, along t2 by c_y = sqrt(det Q) / Q_22.
+// Every annulus piece is therefore split into ceil(1 / c_x) x ceil(1 / c_y)
+// sub-rectangles, and an outer box in ring k around the centre (Chebyshev distance k
+// boxes) into ceil(1 / (c_x (2k - 1))) x ceil(1 / (c_y (2k - 1))), which keeps the
+// relative distance at least that of the 5-point operator with no splitting.  Operators
+// with c < 1/8 (a split above 8, strongly anisotropic) are rejected.
 // The numerator is written -2 sin^2(m.t / 2) and the symbol as a sum of squares, so
 // neither loses digits near t = 0.  One block per table entry; binary64 throughout.
 #include <algorithm>
@@ -54,6 +56,7 @@ struct QuadStencil {
     double gx[kQuadNodes], gw[kQuadNodes];  // Gauss-Legendre on [-1, 1]
     double fx[kQuadNodesFar], fw[kQuadNodesFar];
     double c;                                // sqrt(det Q) / max(Q_11, Q_22)
+    double cx, cy;                           // sqrt(det Q) / Q_11, sqrt(det Q) / Q_22
 };
 
 // splits per side of a piece whose distance from the origin is `dist` piece sizes
@@ -76,11 +79,11 @@ __device__ __forceinline__ double integrand(const QuadStencil& q, int m1, int m2
 // * Q^2 + (node)
 template <int Q>
 __device__ __forceinline__ double rect_node(const QuadStencil& q, const double* x, const double* w, int m1, int m2,
-                                            double x0, double x1, double y0, double y1, int s, int idx) {
+                                            double x0, double x1, double y0, double y1, int sx, int sy, int idx) {
     constexpr int NN = Q * Q;
     const int sub = idx / NN, node = idx % NN;
-    const int si = sub % s, sj = sub / s, i = node % Q, j = node / Q;
-    const double hx = 0.5 * (x1 - x0) / s, hy = 0.5 * (y1 - y0) / s;
+    const int si = sub % sx, sj = sub / sx, i = node % Q, j = node / Q;
+    const double hx = 0.5 * (x1 - x0) / sx, hy = 0.5 * (y1 - y0) / sy;
     const double xa = x0 + 2.0 * hx * si, ya = y0 + 2.0 * hy * sj;
     const double t1 = xa + hx * (1.0 + x[i]), t2 = ya + hy * (1.0 + x[j]);
     return w[i] * w[j] * hx * hy * integrand(q, m1, m2, t1, t2);
@@ -122,13 +125,13 @@ __global__ void __launch_bounds__(kQuadThreads) phi_quad_kernel(const QuadStenci
     int k_flat = 2;
     while (k_flat <= cb && q.c * (2 * k_flat - 1) < 3.0 - 1e-12) ++k_flat;
     for (int k = 1; k < k_flat && k <= cb; ++k) {
-        const int s = quad_split(q.c, 2 * k - 1);
+        const int sx = quad_split(q.cx, 2 * k - 1), sy = quad_split(q.cy, 2 * k - 1);
         for (int bj = cb - k; bj <= cb + k; ++bj)
             for (int bi = cb - k; bi <= cb + k; ++bi) {
                 if (max(abs(bi - cb), abs(bj - cb)) != k) continue;
                 const double x0 = -kPiQ + bi * h, y0 = -kPiQ + bj * h;
-                for (int idx = threadIdx.x; idx < s * s * NN; idx += blockDim.x)
-                    outer += rect_node<kQuadNodes>(q, q.gx, q.gw, m1, m2, x0, x0 + h, y0, y0 + h, s, idx);
+                for (int idx = threadIdx.x; idx < sx * sy * NN; idx += blockDim.x)
+                    outer += rect_node<kQuadNodes>(q, q.gx, q.gw, m1, m2, x0, x0 + h, y0, y0 + h, sx, sy, idx);
             }
     }
     constexpr int NF = kQuadNodesFar * kQuadNodesFar;
@@ -138,13 +141,13 @@ __global__ void __launch_bounds__(kQuadThreads) phi_quad_kernel(const QuadStenci
         const int bi = box % n, bj = box / n;
         if (max(abs(bi - cb), abs(bj - cb)) < k_flat) continue;
         const double x0 = -kPiQ + bi * h, y0 = -kPiQ + bj * h;
-        outer += rect_node<kQuadNodesFar>(q, q.fx, q.fw, m1, m2, x0, x0 + h, y0, y0 + h, 1, node);
+        outer += rect_node<kQuadNodesFar>(q, q.fx, q.fw, m1, m2, x0, x0 + h, y0, y0 + h, 1, 1, node);
     }
     const double outer_sum = block_sum(outer, red);
     // annuli of the centre box, one partial sum per annulus
     const double a = 0.5 * h;
-    const int s0 = quad_split(q.c, 1);
-    const int per_piece = s0 * s0 * NN;
+    const int sx0 = quad_split(q.cx, 1), sy0 = quad_split(q.cy, 1);
+    const int per_piece = sx0 * sy0 * NN;
     for (int j = 0; j < kQuadAnnuli; ++j) {
         const double aj = ldexp(a, -j), bj = 0.5 * aj;
         double part = 0.0;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kQuadThreads) phi_quad_kernel(const QuadStenci
             const int rr = r < 4 ? r : r + 1;
             const double xs[4] = {-aj, -bj, bj, aj};
             const int ci = rr % 3, cj = rr / 3;
-            part += rect_node<kQuadNodes>(q, q.gx, q.gw, m1, m2, xs[ci], xs[ci + 1], xs[cj], xs[cj + 1], s0,
+            part += rect_node<kQuadNodes>(q, q.gx, q.gw, m1, m2, xs[ci], xs[ci + 1], xs[cj], xs[cj + 1], sx0, sy0,
                                           idx % per_piece);
         }
         const double ps = block_sum(part, red);
@@ -213,6 +216,8 @@ extern "C" int lfmm_phi_quadrature(const int32_t* d, const double* w, int32_t n_
         q22 += q.w[k] * q.dy[k] * q.dy[k];
     }
     q.c = std::sqrt(q11 * q22 - q12 * q12) / std::max(q11, q22);
+    q.cx = std::sqrt(q11 * q22 - q12 * q12) / q11;
+    q.cy = std::sqrt(q11 * q22 - q12 * q12) / q22;
     if (!(q.c * kQuadMaxSplit >= 1.0))
         return fail(LFMM_EINVAL, "operator too anisotropic for the quadrature (sqrt(det Q) / max(Q_11, Q_22) < 1/8)");
     std::vector<double> x, wt;
