@@ -277,6 +277,10 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     p->n_boxes = F.total_boxes;
     if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
+    {  // partial sums of the list M2L levels split along K (few boxes)
+        const int64_t sb = forest_m2l_split_bytes(F, p->NP, esz, p->num_sms);
+        if (sb > 0 && (st = palloc(p, &F.m2l_part, (size_t)sb, s))) return st;
+    }
     if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
     if ((st = palloc(p, &p->Cbox, (size_t)boxes * 8, s))) return st;
     void* stbuf;

@@ -527,11 +527,16 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
     const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
     const T* __restrict__ q, const T* __restrict__ u_par, const T* __restrict__ ops, const T* __restrict__ l2l,
     const T* __restrict__ mono, const typename Mono<T>::V* __restrict__ Qin,
-    const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out, typename Mono<T>::V* __restrict__ Cout) {
+    const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out, typename Mono<T>::V* __restrict__ Cout,
+    int64_t nb, T* __restrict__ part, typename Mono<T>::V* __restrict__ cpart) {
     griddep_wait();
     using M = Mono<T>;
     using V = typename M::V;
     constexpr int W = LCfg<T, NP>::WARPS;
+    // K split over gridDim.z chunks (levels with few boxes): chunk z takes the steps
+    // [z per, (z + 1) per) and writes its partial sums to part / cpart (chunk-major);
+    // m2l_list_reduce_kernel adds the chunks in order.
+    const int n_chunks = gridDim.z;
     constexpr int kRows = LCfg<T, NP>::ROWS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sop = reinterpret_cast<T*>(smem_raw);
@@ -557,11 +562,13 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
     T* my_op = sop + warp * NP * 32;
     T* my_rows = red + (size_t)warp * kRows;
     V cacc = M::zero();
+    const int per = (n_steps + n_chunks - 1) / n_chunks;
+    const int st0 = (int)blockIdx.z * per, st1 = min(n_steps, st0 + per);
     for (int half = 0; half < NP / 32; ++half) {
         T acc[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] = T(0);
-        for (int st = warp; st < n_steps; st += W) {
+        for (int st = st0 + warp; st < st1; st += W) {
             const T* op;
             const T* src = nullptr;
             if (st < 27) {
@@ -641,15 +648,48 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
 #pragma unroll
             for (int w = 0; w < W; ++w) v += red[(size_t)w * kRows + b * 33 + j];
             const int64_t bb = c0 + (int64_t)blockIdx.x * 32 + b;
-            if (bb < c1) out[(size_t)bb * NP + 32 * half + j] = v;
+            if (bb < c1) {
+                if (n_chunks == 1) out[(size_t)bb * NP + 32 * half + j] = v;
+                else part[((size_t)blockIdx.z * nb + bb) * NP + 32 * half + j] = v;
+            }
         }
         __syncthreads();
     }
     if (warp == 0 && valid) {
-        V sacc = pbox >= 0 ? Cpar[pbox] : M::zero();
+        if (n_chunks == 1) {
+            V sacc = pbox >= 0 ? Cpar[pbox] : M::zero();
 #pragma unroll
-        for (int w = 0; w < W; ++w) sacc = M::add(sacc, s_cpart[w][lane]);
-        Cout[box] = sacc;
+            for (int w = 0; w < W; ++w) sacc = M::add(sacc, s_cpart[w][lane]);
+            Cout[box] = sacc;
+        } else {
+            V sacc = M::zero();
+#pragma unroll
+            for (int w = 0; w < W; ++w) sacc = M::add(sacc, s_cpart[w][lane]);
+            cpart[(size_t)blockIdx.z * nb + box] = sacc;
+        }
+    }
+}
+
+// The chunks of a K-split list M2L added in chunk order: out = sum_z part[z], and
+// Cout = Cpar[parent] + sum_z cpart[z].
+template <typename T, int NP>
+__global__ void m2l_list_reduce_kernel(int64_t nb, int n_chunks, const T* __restrict__ part,
+                                       const typename Mono<T>::V* __restrict__ cpart, const int32_t* __restrict__ par,
+                                       const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out,
+                                       typename Mono<T>::V* __restrict__ Cout) {
+    griddep_wait();
+    using M = Mono<T>;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb * NP; i += stride) {
+        T v = part[i];
+        for (int z = 1; z < n_chunks; ++z) v += part[(size_t)z * nb * NP + i];
+        out[i] = v;
+    }
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+        const int pb = (par && Cpar) ? par[b] : -1;
+        typename M::V sacc = pb >= 0 ? Cpar[pb] : M::zero();
+        for (int z = 0; z < n_chunks; ++z) sacc = M::add(sacc, cpart[(size_t)z * nb + b]);
+        Cout[b] = sacc;
     }
 }
 
@@ -912,6 +952,23 @@ void Forest::release(cudaStream_t s) {
     for (void* a : owned) cudaFreeAsync(a, s);
     owned.clear();
     levels.clear();
+}
+
+int m2l_list_chunks(int64_t maxc, int num_sms) {
+    const int64_t blocks = 4 * ((maxc + 31) / 32);
+    if (blocks == 0 || 2 * blocks >= num_sms) return 1;
+    return (int)std::max<int64_t>(2, std::min<int64_t>(7, num_sms / blocks));
+}
+
+int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms) {
+    int64_t need = 0;
+    for (const ForestLevel& lv : F.levels) {
+        int64_t maxc = 0;
+        for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
+        const int nc = m2l_list_chunks(maxc, num_sms);
+        if (nc > 1) need = std::max<int64_t>(need, (int64_t)nc * lv.nb * ((int64_t)NP * (int64_t)esz + 8));
+    }
+    return need;
 }
 
 int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
@@ -1273,7 +1330,10 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             int64_t maxc = 0;
             for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
             if (maxc == 0) continue;
-            dim3 grid((unsigned)((maxc + 31) / 32), 4);
+            const int nc = F.m2l_part ? m2l_list_chunks(maxc, num_sms) : 1;
+            dim3 grid((unsigned)((maxc + 31) / 32), 4, (unsigned)nc);
+            T* part = nc > 1 ? (T*)F.m2l_part : nullptr;
+            V* cpart = nc > 1 ? (V*)(part + (size_t)nc * lv.nb * NP) : nullptr;
             auto go = [&](auto np_tag) -> cudaError_t {
                 constexpr int NPc = decltype(np_tag)::value;
                 constexpr size_t smem = LCfg<T, NPc>::SMEM;
@@ -1284,12 +1344,19 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                 (void)launch_dependent(m2l_list_kernel<T, NPc>, dim3(grid), dim3(LCfg<T, NPc>::WARPS * 32), smem, s,
                     lv.d_cls, lv.il, l2l ? lv.par : nullptr, Qx(k), l2l ? Ux(k + 1) : nullptr,
                     (const T*)ops.tifo[k], l2l ? (const T*)ops.l2l[k + 1] : nullptr, (const T*)ops.mono[k], Qm(k),
-                    l2l ? Cm(k + 1) : nullptr, Ux(k), Cm(k));
+                    l2l ? Cm(k + 1) : nullptr, Ux(k), Cm(k), lv.nb, part, cpart);
+                if (nc > 1) {
+                    const int64_t rb = std::min<int64_t>((lv.nb * NPc + 255) / 256, (int64_t)num_sms * 8);
+                    (void)launch_dependent(m2l_list_reduce_kernel<T, NPc>, dim3((unsigned)std::max<int64_t>(rb, 1)),
+                                           dim3(256), 0, s, lv.nb, nc, (const T*)part, (const V*)cpart,
+                                           l2l ? (const int32_t*)lv.par : nullptr, l2l ? (const V*)Cm(k + 1) : nullptr,
+                                           Ux(k), (V*)Cm(k));
+                }
                 return cudaGetLastError();
             };
             cudaError_t e = NP == 32 ? go(std::integral_constant<int, 32>()) : go(std::integral_constant<int, 64>());
             if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("m2l_list_kernel: ") + cudaGetErrorString(e));
-            pt.add_launches(1);
+            pt.add_launches(nc > 1 ? 2 : 1);
         }
     }
     {

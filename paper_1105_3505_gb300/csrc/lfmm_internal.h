@@ -273,8 +273,15 @@ struct Forest {
     int32_t* n_strips_d = nullptr;
     std::vector<void*> owned;
     int64_t bytes = 0;
+    void* m2l_part = nullptr;               // partial sums of K-split list M2L levels (plan-owned)
     void release(cudaStream_t s);
 };
+
+// K chunks of the list M2L of a level whose largest parity class has maxc boxes: more
+// than one when its 32-box tiles leave most SMs idle.
+int m2l_list_chunks(int64_t maxc, int num_sms);
+// Bytes of partial sums the K-split list M2L levels of F need (0: none split).
+int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms);
 
 // Builds the tree of every problem (offsets: n_problems + 1 entries, host memory).
 // Leaf side: the largest power of two <= max_leaf_side at which no leaf holds more than
