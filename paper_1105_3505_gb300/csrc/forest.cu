@@ -457,6 +457,57 @@ __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t
 }
 
 // M2M: one warp per compact parent; children by compact id (-1: empty).
+// The same M2M for levels with few parents: one block per parent, warp c computing the
+// 32 products of input chunk c; the chunks are added in order, as in m2m_list_kernel,
+// so both give bit-identical results.
+template <typename T, int NP>
+__global__ void __launch_bounds__(4 * NP) m2m_list_block_kernel(int64_t nb, const int32_t* __restrict__ ch,
+                                                               const T* __restrict__ qc, const T* __restrict__ m2m,
+                                                               const typename Mono<T>::V* __restrict__ Qin,
+                                                               T* __restrict__ qp,
+                                                               typename Mono<T>::V* __restrict__ Qout) {
+    griddep_wait();
+    using M = Mono<T>;
+    constexpr int CL = 4 * NP / 32, PL = NP / 32;
+    __shared__ T red[CL][PL][32];
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int child = ch[b * 4 + (32 * c) / NP];
+        const T xv = child >= 0 ? qc[(size_t)child * NP + (32 * c) % NP + lane] : T(0);
+        T acc[PL];
+#pragma unroll
+        for (int i = 0; i < PL; ++i) acc[i] = T(0);
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+            const T v = shfl(xv, l);
+            const T* row = m2m + (size_t)(32 * c + l) * NP;
+#pragma unroll
+            for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), v, acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < PL; ++i) red[c][i][lane] = acc[i];
+        __syncthreads();
+        if (c == 0) {
+#pragma unroll
+            for (int i = 0; i < PL; ++i) {
+                T a = red[0][i][lane];
+#pragma unroll
+                for (int cc = 1; cc < CL; ++cc) a += red[cc][i][lane];
+                qp[(size_t)b * NP + lane + 32 * i] = a;
+            }
+            typename M::V qv = M::zero();
+            if (lane < 4) {
+                const int cb = ch[b * 4 + lane];
+                if (cb >= 0) qv = Qin[cb];
+            }
+            qv = M::add(qv, shfl_xor_v(qv, 1));
+            qv = M::add(qv, shfl_xor_v(qv, 2));
+            if (lane == 0) Qout[b] = qv;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) m2m_list_kernel(int64_t nb, const int32_t* __restrict__ ch,
                                                        const T* __restrict__ qc, const T* __restrict__ m2m,
@@ -1310,6 +1361,18 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         for (int k = 1; k < nk; ++k) {
             const ForestLevel& lv = F.levels[k];
             if (lv.nb == 0) continue;
+            if (lv.nb < (int64_t)num_sms * 16) {  // few parents: one block each
+                const int64_t nbk = std::min<int64_t>(lv.nb, (int64_t)num_sms * 16);
+                if (NP == 32)
+                    (void)launch_dependent(m2m_list_block_kernel<T, 32>, dim3((unsigned)nbk), dim3(128), 0, s, lv.nb,
+                                           lv.ch, Qx(k - 1), (const T*)ops.m2m[k], Qm(k - 1), Qx(k), Qm(k));
+                else
+                    (void)launch_dependent(m2m_list_block_kernel<T, 64>, dim3((unsigned)nbk), dim3(256), 0, s, lv.nb,
+                                           lv.ch, Qx(k - 1), (const T*)ops.m2m[k], Qm(k - 1), Qx(k), Qm(k));
+                LFMM_CUDA_TRY(cudaGetLastError());
+                pt.add_launches(1);
+                continue;
+            }
             int64_t blocks = std::min<int64_t>((lv.nb * 32 + 255) / 256, 152 * 8);
             if (NP == 32)
                 (void)launch_dependent(m2m_list_kernel<T, 32>, dim3((int)blocks), dim3(256), 0, s, lv.nb, lv.ch, Qx(k - 1), (const T*)ops.m2m[k],
