@@ -1007,8 +1007,8 @@ void Forest::release(cudaStream_t s) {
 
 int m2l_list_chunks(int64_t maxc, int num_sms) {
     const int64_t blocks = 4 * ((maxc + 31) / 32);
-    if (blocks == 0 || 2 * blocks >= num_sms) return 1;
-    return (int)std::max<int64_t>(2, std::min<int64_t>(7, num_sms / blocks));
+    if (blocks == 0 || blocks >= 3 * (int64_t)num_sms) return 1;
+    return (int)std::min<int64_t>(7, (3 * (int64_t)num_sms + blocks - 1) / blocks);
 }
 
 int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms) {

@@ -278,7 +278,7 @@ struct Forest {
 };
 
 // K chunks of the list M2L of a level whose largest parity class has maxc boxes: more
-// than one when its 32-box tiles leave most SMs idle.
+// than one (up to 7) while its 32-box tiles are fewer than three per SM.
 int m2l_list_chunks(int64_t maxc, int num_sms);
 // Bytes of partial sums the K-split list M2L levels of F need (0: none split).
 int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms);
