@@ -53,6 +53,8 @@ struct lfmm_plan {
     int tc_min_level = kDefaultTcMinLevel;
     double* f_stage = nullptr;     // device copy of a host f
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
+    void* m2l_part = nullptr;      // partial sums of the K-split fused small-level M2L
+    int64_t m2l_part_bytes = 0;
     std::unique_ptr<Forest> forest;  // pruned tree or forest (null: uniform tree)
     void* tc_split = nullptr;        // TF32 hi/lo copies of q_hat and the parent u_hat for the tensor cores
     double* un_tmp = nullptr;        // near field per target (caller order) from the concurrent near-field pass
@@ -567,6 +569,8 @@ int far_sweeps(lfmm_plan* p, const FarBufs& b, cudaStream_t s, Hook before_fine)
     lb.nvec = b.nvec;
     lb.vq = b.vq;
     lb.vQ = b.vQ;
+    lb.part = p->m2l_part;
+    lb.part_bytes = p->m2l_part_bytes;
     unsigned* gsync = (unsigned*)(p->status + 1);  // grid-barrier words beside the status word
     {
         PhaseTimer pt(LFMM_PHASE_M2M, s);
@@ -790,11 +794,32 @@ int eval_graph(lfmm_plan* p, const double* f, double* const out[3], cudaStream_t
     return LFMM_OK;
 }
 
+// Room for the partial sums of the K-split fused small-level M2L for nvec vectors
+// (plan-owned, allocated before any evaluation or graph capture needs it).
+int ensure_m2l_part(lfmm_plan* p, int nvec, cudaStream_t s) {
+    if (p->forest || p->L < 2 || !p->ops) return LFMM_OK;
+    const int64_t need =
+        p->opts.precision == LFMM_MIXED ? m2l_fused_split_bytes<float>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec)
+        : p->opts.precision == LFMM_DF  ? m2l_fused_split_bytes<DF>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec)
+                                         : m2l_fused_split_bytes<double>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec);
+    if (need <= p->m2l_part_bytes) return LFMM_OK;
+    void* b;
+    const int st = palloc(p, &b, (size_t)need, s);
+    if (st) return st;
+    p->m2l_part = b;
+    p->m2l_part_bytes = need;
+    return LFMM_OK;
+}
+
 int eval_common(lfmm_plan* p, const double* f, double* u, double* un, double* uf, void* stream) {
     if (!p || !f) return fail(LFMM_EINVAL, "NULL plan or f");
     if (!u && !un && !uf) return fail(LFMM_EINVAL, "no output");
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
+    {
+        const int st = ensure_m2l_part(p, 1, s);
+        if (st) return st;
+    }
     const double* fd = f;
     if (!is_device_ptr(f)) {
         if (!p->f_stage) {
@@ -1014,6 +1039,7 @@ int lfmm_eval_multi(lfmm_plan* p, const double* F, int32_t k, double* U, void* s
     int st;
     const bool uniform = !p->forest && p->L >= 2 && p->un_tmp;
     const int group = std::min(k, kMultiGroup);
+    if (uniform && (st = ensure_m2l_part(p, group, s))) return st;
     if (uniform && p->multi_cap < group) {
         // per-vector buffers for one group (allocated once per plan and size)
         const size_t esz = p->opts.precision == LFMM_MIXED ? sizeof(float) : sizeof(double);

@@ -333,13 +333,15 @@ struct SkCfg {
 
 // One 32-box tile of parity class cls at `level` (shared by the per-level kernel and
 // the fused small-level kernel).  u_par == nullptr: no L2L step and C starts at 0.
+// Only the K-steps [st_begin, st_end) are taken (all by default).
 template <typename T, int NP, int W>
 __device__ __forceinline__ void m2l_splitk_tile(int level, int cls, int64_t tile, const T* __restrict__ q,
                                                 const T* __restrict__ u_par, const T* __restrict__ ops,
                                                 const T* __restrict__ l2l, const T* __restrict__ mono,
                                                 const typename Mono<T>::V* __restrict__ Qin,
                                                 const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out,
-                                                typename Mono<T>::V* __restrict__ Cout) {
+                                                typename Mono<T>::V* __restrict__ Cout, int st_begin = 0,
+                                                int st_end = 1 << 30) {
     using M = Mono<T>;
     using V = typename M::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -384,7 +386,7 @@ __device__ __forceinline__ void m2l_splitk_tile(int level, int cls, int64_t tile
         T acc[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) acc[j] = T(0);
-        for (int st = warp; st < n_steps; st += kSkWarps) {
+        for (int st = st_begin + warp; st < min(n_steps, st_end); st += kSkWarps) {
             const T* op;
             const T* src = nullptr;
             if (st < 27) {
@@ -1232,6 +1234,11 @@ struct LevelPtrs {
     int64_t item_off[kMaxLevels + 1];  // downward: first M2L work item of level l0 + i
     int nvec;                          // charge vectors; vector v's arrays at v vq (q, u) / v vQ (Q, C)
     int64_t vq, vQ;
+    // fused small-level M2L split along K: chunk c of vector v writes its partial sums
+    // to part + ((v nch + c) part_stride + box over the levels) NP (then the constants)
+    T* part;
+    int nch;
+    int64_t part_stride;
 };
 
 // Grid-wide barrier of a cooperative launch.  count and gen are plan-owned device words
@@ -1341,17 +1348,59 @@ __global__ void __launch_bounds__(FusedCfg<T, NP>::WARPS * 32) m2l_small_kernel(
     constexpr int PL = NP / 32;
     const int nl = l1 - l0 + 1;
     const int64_t n_items = P.item_off[nl];
-    // M2L part of every level: work item = (charge vector, level, class, 32-box tile)
-    for (int64_t it = blockIdx.x; it < n_items * P.nvec; it += gridDim.x) {
-        const int64_t v = it / n_items, item = it - v * n_items;
+    const int nch = P.nch;
+    using V = typename M::V;
+    V* cpart = nch > 1 ? reinterpret_cast<V*>(P.part + (int64_t)P.nvec * nch * P.part_stride * NP) : nullptr;
+    // M2L part of every level: work item = (K chunk, charge vector, level, class, 32-box
+    // tile); with several chunks each writes partial sums, added below in chunk order
+    for (int64_t it = blockIdx.x; it < n_items * P.nvec * nch; it += gridDim.x) {
+        const int ch = (int)(it / (n_items * P.nvec));
+        const int64_t rest = it - (int64_t)ch * n_items * P.nvec;
+        const int64_t v = rest / n_items, item = rest - v * n_items;
         int i = 0;
         while (item >= P.item_off[i + 1]) ++i;
         const int l = l0 + i;
         const int64_t tiles = (((int64_t)1 << (2 * (l - 1))) + 31) / 32;
         const int64_t local = item - P.item_off[i];
-        m2l_splitk_tile<T, NP, FusedCfg<T, NP>::WARPS>(l, (int)(local / tiles), local % tiles, P.q[l] + v * P.vq,
-                                                       nullptr, P.tifo[l], nullptr, P.mono[l], P.Q[l] + v * P.vQ,
-                                                       nullptr, P.u[l] + v * P.vq, P.C[l] + v * P.vQ);
+        if (nch == 1) {
+            m2l_splitk_tile<T, NP, FusedCfg<T, NP>::WARPS>(l, (int)(local / tiles), local % tiles, P.q[l] + v * P.vq,
+                                                           nullptr, P.tifo[l], nullptr, P.mono[l], P.Q[l] + v * P.vQ,
+                                                           nullptr, P.u[l] + v * P.vq, P.C[l] + v * P.vQ);
+        } else {
+            const int per = (27 + nch - 1) / nch;
+            int64_t loff = 0;  // boxes of the levels before l
+            for (int ll = l0; ll < l; ++ll) loff += (int64_t)1 << (2 * ll);
+            const int64_t base = (v * nch + ch) * P.part_stride + loff;
+            m2l_splitk_tile<T, NP, FusedCfg<T, NP>::WARPS>(l, (int)(local / tiles), local % tiles, P.q[l] + v * P.vq,
+                                                           nullptr, P.tifo[l], nullptr, P.mono[l], P.Q[l] + v * P.vQ,
+                                                           nullptr, P.part + base * NP, cpart + base, ch * per,
+                                                           ch * per + per);
+        }
+    }
+    if (nch > 1) {  // expansions and constants = the chunks' partial sums, in chunk order
+        grid_barrier(sync, sync + 1, status);
+        const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+        const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t per_v = P.part_stride * NP;
+        for (int64_t e = t0; e < P.nvec * per_v; e += nt) {
+            const int64_t v = e / per_v, r = e - v * per_v, gb = r / NP;
+            const int j = (int)(r - gb * NP);
+            int l = l0;
+            int64_t b = gb;
+            while (b >= ((int64_t)1 << (2 * l))) b -= (int64_t)1 << (2 * l++);
+            T acc = P.part[((v * nch) * P.part_stride + gb) * NP + j];
+            for (int c = 1; c < nch; ++c) acc += P.part[((v * nch + c) * P.part_stride + gb) * NP + j];
+            P.u[l][v * P.vq + b * NP + j] = acc;
+        }
+        for (int64_t e = t0; e < P.nvec * P.part_stride; e += nt) {
+            const int64_t v = e / P.part_stride, gb = e - v * P.part_stride;
+            int l = l0;
+            int64_t b = gb;
+            while (b >= ((int64_t)1 << (2 * l))) b -= (int64_t)1 << (2 * l++);
+            V acc = M::zero();
+            for (int c = 0; c < nch; ++c) acc = M::add(acc, cpart[(v * nch + c) * P.part_stride + gb]);
+            P.C[l][v * P.vQ + b] = acc;
+        }
     }
     if (nl == 1) return;
     grid_barrier(sync, sync + 1, status);
@@ -1779,6 +1828,38 @@ cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, un
     else return go((const void*)m2m_up_kernel<T, 64, false>, 0);
 }
 
+// K chunks of the fused small-level M2L: more than one (up to 9, at least 3 K-steps each)
+// when its 32-box tiles are fewer than half the grid's blocks.
+static int fused_split_chunks(int64_t items, int grid) {
+    if (items <= 0 || 2 * items >= grid) return 1;
+    return (int)std::min<int64_t>(9, std::max<int64_t>(2, grid / items));
+}
+
+template <typename T>
+int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec) {
+    int Ls = 1;
+    for (int l = 2; l <= std::min(L, kM2LSplitKMaxLevel); ++l) {
+        if (m2l_uses_tc(ops, L - l, l, tc_min_level, sizeof(T) == 4)) break;
+        Ls = l;
+    }
+    if (Ls < 2 || L >= kMaxLevels) return 0;
+    int64_t items = 0, stride = 0;
+    for (int l = 2; l <= Ls; ++l) {
+        items += 4 * ((((int64_t)1 << (2 * (l - 1))) + 31) / 32);
+        stride += (int64_t)1 << (2 * l);
+    }
+    auto bytes = [&](auto np_tag) -> int64_t {
+        constexpr int NPc = decltype(np_tag)::value;
+        const void* fn = (const void*)m2l_small_kernel<T, NPc>;
+        constexpr size_t smem = FusedCfg<T, NPc>::SMEM;
+        if (ensure_dynamic_smem(fn, smem) != cudaSuccess) return 0;
+        const int grid = num_sms * blocks_per_sm(fn, FusedCfg<T, NPc>::WARPS * 32, smem);
+        const int nch = fused_split_chunks(items, grid);
+        return nch > 1 ? (int64_t)nvec * nch * stride * (NPc * (int64_t)sizeof(T) + 8) : 0;
+    };
+    return ops.NP == 32 ? bytes(std::integral_constant<int, 32>()) : bytes(std::integral_constant<int, 64>());
+}
+
 template <typename T>
 cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, int tc_min_level, unsigned* sync,
                              int* status, int num_sms, int* last_level, cudaStream_t s) {
@@ -1804,6 +1885,18 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
         cudaError_t e = ensure_dynamic_smem(fn, smem);
         if (e != cudaSuccess) return e;
         const int grid = num_sms * blocks_per_sm(fn, threads, smem);
+        // few tiles for the grid: split the 27 K-steps into chunks (partial sums)
+        const int nch = fused_split_chunks(P.item_off[l1 - l0 + 1], grid);
+        P.nch = 1;
+        if (nch > 1) {
+            int64_t stride = 0;
+            for (int l = l0; l <= l1; ++l) stride += (int64_t)1 << (2 * l);
+            const int64_t need = (int64_t)P.nvec * nch * stride * (NPc * (int64_t)sizeof(T) + 8);
+            if (!b.part || b.part_bytes < need) return cudaErrorInvalidValue;  // the caller sizes it
+            P.part = (T*)b.part;
+            P.nch = nch;
+            P.part_stride = stride;
+        }
         void* args[] = {&P, &l0, &l1, &sync, &status};
         e = launch_cooperative(fn, grid, threads, smem, args, s);
         return e == cudaSuccess ? cudaSuccess : clear_and_return(e);
@@ -1855,6 +1948,7 @@ cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double
 #define LFMM_INSTANTIATE(T)                                                                                   \
     template cudaError_t launch_m2m_fused<T>(const DeviceOps&, int, const LevelBufs&, unsigned*, int*, int,      \
                                              cudaStream_t);                                                  \
+    template int64_t m2l_fused_split_bytes<T>(const DeviceOps&, int, int, int, int);                          \
     template cudaError_t launch_m2l_fused<T>(const DeviceOps&, int, const LevelBufs&, int, unsigned*, int*, int, \
                                              int*, cudaStream_t);                                            \
     template cudaError_t launch_l2p<T>(const TreeView&, const DeviceOps&, const T*, const void*, double*,          \

@@ -356,7 +356,14 @@ struct LevelBufs {
     // and v vQ elements (Q, C) after vector 0's
     int nvec = 1;
     int64_t vq = 0, vQ = 0;
+    // partial sums of the fused small-level M2L split along K (m2l_fused_split_bytes)
+    void* part = nullptr;
+    int64_t part_bytes = 0;
 };
+// Bytes of partial sums launch_m2l_fused needs for nvec charge vectors (0: no K split;
+// the split depends on the plan, not on nvec, so one and several vectors sum alike).
+template <typename T>
+int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec);
 // M2M of levels L-1 .. 2 in one cooperative launch (grid barriers between levels).
 // sync: two zero device words (barrier state).  Returns an error (nothing launched)
 // when a cooperative launch is not possible; the caller then runs the per-level path.
