@@ -55,6 +55,7 @@ struct lfmm_plan {
     double* u_stage = nullptr;     // device result before a host copy (3 x n_tgt)
     void* m2l_part = nullptr;      // partial sums of the K-split fused small-level M2L
     int64_t m2l_part_bytes = 0;
+    int m2l_part_nvec = 0;         // vectors the buffer has been sized for
     std::unique_ptr<Forest> forest;  // pruned tree or forest (null: uniform tree)
     void* tc_split = nullptr;        // TF32 hi/lo copies of q_hat and the parent u_hat for the tensor cores
     double* un_tmp = nullptr;        // near field per target (caller order) from the concurrent near-field pass
@@ -797,17 +798,19 @@ int eval_graph(lfmm_plan* p, const double* f, double* const out[3], cudaStream_t
 // Room for the partial sums of the K-split fused small-level M2L for nvec vectors
 // (plan-owned, allocated before any evaluation or graph capture needs it).
 int ensure_m2l_part(lfmm_plan* p, int nvec, cudaStream_t s) {
-    if (p->forest || p->L < 2 || !p->ops) return LFMM_OK;
+    if (p->forest || p->L < 2 || !p->ops || nvec <= p->m2l_part_nvec) return LFMM_OK;
     const int64_t need =
         p->opts.precision == LFMM_MIXED ? m2l_fused_split_bytes<float>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec)
         : p->opts.precision == LFMM_DF  ? m2l_fused_split_bytes<DF>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec)
                                          : m2l_fused_split_bytes<double>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec);
-    if (need <= p->m2l_part_bytes) return LFMM_OK;
-    void* b;
-    const int st = palloc(p, &b, (size_t)need, s);
-    if (st) return st;
-    p->m2l_part = b;
-    p->m2l_part_bytes = need;
+    if (need > p->m2l_part_bytes) {
+        void* b;
+        const int st = palloc(p, &b, (size_t)need, s);
+        if (st) return st;
+        p->m2l_part = b;
+        p->m2l_part_bytes = need;
+    }
+    p->m2l_part_nvec = nvec;
     return LFMM_OK;
 }
 
