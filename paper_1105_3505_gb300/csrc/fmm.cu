@@ -1828,11 +1828,25 @@ cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, un
     else return go((const void*)m2m_up_kernel<T, 64, false>, 0);
 }
 
-// K chunks of the fused small-level M2L: more than one (up to 9, at least 3 K-steps each)
-// when its 32-box tiles are fewer than half the grid's blocks.
-static int fused_split_chunks(int64_t items, int grid) {
-    if (items <= 0 || 2 * items >= grid) return 1;
-    return (int)std::min<int64_t>(9, std::max<int64_t>(2, grid / items));
+// K chunks of the fused small-level M2L (up to 9, at least 3 K-steps each).  Binary32
+// tiles are short, and only split when they are fewer than half the grid's blocks;
+// binary64-width tiles are long enough that balancing the last round pays: the count
+// that minimises the rounds of work units over the grid, each chunk doing 1/n of a
+// tile's work, with a 10 % allowance for the partial sums and their reduction (one
+// chunk unless that saves more than 10 %).
+static int fused_split_chunks(int64_t items, int grid, bool wide) {
+    if (items <= 0 || grid <= 0) return 1;
+    if (!wide) return 2 * items >= grid ? 1 : (int)std::min<int64_t>(9, std::max<int64_t>(2, grid / items));
+    int best = 1;
+    double best_cost = (double)((items + grid - 1) / grid);
+    for (int n = 2; n <= 9; ++n) {
+        const double cost = (double)((items * n + grid - 1) / grid) / n * 1.1;
+        if (cost < best_cost * 0.9 && cost < best_cost) {
+            best_cost = cost;
+            best = n;
+        }
+    }
+    return best;
 }
 
 template <typename T>
@@ -1854,7 +1868,7 @@ int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int
         constexpr size_t smem = FusedCfg<T, NPc>::SMEM;
         if (ensure_dynamic_smem(fn, smem) != cudaSuccess) return 0;
         const int grid = num_sms * blocks_per_sm(fn, FusedCfg<T, NPc>::WARPS * 32, smem);
-        const int nch = fused_split_chunks(items, grid);
+        const int nch = fused_split_chunks(items, grid, sizeof(T) == 8);
         return nch > 1 ? (int64_t)nvec * nch * stride * (NPc * (int64_t)sizeof(T) + 8) : 0;
     };
     return ops.NP == 32 ? bytes(std::integral_constant<int, 32>()) : bytes(std::integral_constant<int, 64>());
@@ -1886,7 +1900,7 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
         if (e != cudaSuccess) return e;
         const int grid = num_sms * blocks_per_sm(fn, threads, smem);
         // few tiles for the grid: split the 27 K-steps into chunks (partial sums)
-        const int nch = fused_split_chunks(P.item_off[l1 - l0 + 1], grid);
+        const int nch = fused_split_chunks(P.item_off[l1 - l0 + 1], grid, sizeof(T) == 8);
         P.nch = 1;
         if (nch > 1) {
             int64_t stride = 0;
