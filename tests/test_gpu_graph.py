@@ -31,7 +31,8 @@ def lfmm():
 
 
 def prec(lfmm, name):
-    return {"fp64": (lfmm.LFMM_FP64, 16), "mixed": (lfmm.LFMM_MIXED, 8), "df": (lfmm.LFMM_DF, 16)}[name]
+    return {"fp64": (lfmm.LFMM_FP64, 16), "mixed": (lfmm.LFMM_MIXED, 8), "mixed16": (lfmm.LFMM_MIXED, 16),
+            "df": (lfmm.LFMM_DF, 16)}[name]
 
 
 def eager(lfmm, plan, f, parts=False):
@@ -43,7 +44,7 @@ def eager(lfmm, plan, f, parts=False):
         plan.set_flags(graph=True)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64", "df"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed16", "fp64", "df"])
 def test_graph_equals_eager(lfmm, precision):
     prob = workloads.uniform_box(60000, 50000, 1024, seed=12)
     pr, p = prec(lfmm, precision)
@@ -71,11 +72,11 @@ def test_graph_equals_eager(lfmm, precision):
         # another plan of the same points: equal to rounding
         uo = other.eval(f2)
         scale = float(ue2.abs().max())
-        assert float((uo - ue2).abs().max()) <= (1e-6 if precision == "mixed" else 1e-12) * scale
+        assert float((uo - ue2).abs().max()) <= (1e-6 if precision.startswith("mixed") else 1e-12) * scale
     idx = np.random.default_rng(1).choice(prob.tgt.shape[0], 48, replace=False)
     ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
     err = np.abs(uh[idx] - ref).max() / np.abs(ref).max()
-    assert err <= (1e-6 if precision == "mixed" else 1e-10), err
+    assert err <= (1e-6 if precision.startswith("mixed") else 1e-10), err
 
 
 def test_graph_forest_equals_eager(lfmm):

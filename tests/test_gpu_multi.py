@@ -29,7 +29,7 @@ def charges(n, k, seed):
     return np.ascontiguousarray(np.stack([workloads.zero_sum(rng.standard_normal(n)) for _ in range(k)]))
 
 
-@pytest.mark.parametrize("precision,p", [("mixed", 8), ("fp64", 16), ("df", 16)])
+@pytest.mark.parametrize("precision,p", [("mixed", 8), ("mixed", 16), ("fp64", 16), ("df", 16)])
 def test_multi_equals_single(lfmm, precision, p):
     pr = {"mixed": lfmm.LFMM_MIXED, "fp64": lfmm.LFMM_FP64, "df": lfmm.LFMM_DF}[precision]
     prob = workloads.uniform_box(40000, 30000, 900, seed=17)
