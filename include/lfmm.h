@@ -47,6 +47,8 @@ extern "C" {
 #define LFMM_ETIMEOUT 4      /* a bounded device-side wait gave up                      */
 #define LFMM_EUNSUPPORTED 5  /* valid request this build does not handle                */
 #define LFMM_EINTERNAL 6     /* internal consistency check failed                       */
+#define LFMM_EBUSY 7         /* a server refused or shed a request (overload policy)    */
+#define LFMM_ECANCELED 8     /* a queued server request was cancelled                   */
 
 /* ---- precision paths ------------------------------------------------------------- */
 /* LFMM_FP64: every step in binary64 (the plain path, relative error <= 1e-10 at p >= 16).
@@ -177,6 +179,24 @@ int lfmm_plan_set_flags(lfmm_plan* plan, int32_t flags);
  * results are not valid), else LFMM_OK.  Clears the status. */
 int lfmm_plan_status(lfmm_plan* plan, void* stream);
 
+/* Bound of the plan's device-side waits (the grid barriers of the cooperative coarse-level
+ * kernels and the mbarrier polls of the tensor-core M2L), in polls; 0 restores the
+ * defaults (about 2^24 polls, a second or more).  An expired wait records LFMM_ETIMEOUT
+ * for lfmm_plan_status and lets the kernel finish with invalid results instead of
+ * hanging; the tensor-core kernel still waits, with the default bound, for the copies and
+ * products it has issued before it frees its tensor memory and exits.  A small bound
+ * turns slow progress into timeouts: it is meant for tests of the timeout path and for
+ * callers that prefer a fast failure.  Enqueued on the plan's last stream. */
+int lfmm_plan_set_wait_budget(lfmm_plan* plan, int32_t polls);
+
+/* Test hook for the timeout path: sets the arrival count of the plan's grid barrier far
+ * beyond any grid size, so that no arrival completes the next barrier, as if blocks of
+ * the next cooperative kernel never arrived.  Every block then waits its poll budget out
+ * at each barrier of the evaluation, which records LFMM_ETIMEOUT.
+ * lfmm_plan_status reports it and puts the barrier words back to zero, after which the
+ * plan evaluates normally again.  Enqueued on the plan's last stream. */
+int lfmm_plan_inject_barrier_stall(lfmm_plan* plan);
+
 typedef struct lfmm_plan_info {
     int64_t n_src, n_tgt;
     int64_t x0, y0;           /* lower-left corner of the root box                       */
@@ -245,6 +265,17 @@ int lfmm_server_submit(lfmm_server* server, const lfmm_request* req, int64_t* ti
 int lfmm_server_wait(lfmm_server* server, int64_t ticket, lfmm_request_stats* stats);
 /* Finish the queued requests, stop the workers and free the server (NULL: no-op). */
 int lfmm_server_destroy(lfmm_server* server);
+/* Overload policy.  max_pending > 0 bounds the requests waiting for admission:
+ * lfmm_server_submit refuses a request beyond it with LFMM_EBUSY (no ticket is issued).
+ * max_queue_ms > 0 is a latency budget for the wait before admission: a request that has
+ * waited longer is shed when the server next considers its queue (at every submit and
+ * whenever a slot frees) and completes with LFMM_EBUSY; its ticket must still be waited
+ * for.  0 disables either limit (the default: every request is eventually served). */
+int lfmm_server_set_limits(lfmm_server* server, int32_t max_pending, double max_queue_ms);
+/* Cancel a request that is still waiting for admission: it leaves the queue and
+ * completes with LFMM_ECANCELED (its ticket must still be waited for).  A request that
+ * has been admitted runs to the end: LFMM_EINVAL, and the request is not affected. */
+int lfmm_server_cancel(lfmm_server* server, int64_t ticket);
 
 /* ---- autotuner ---------------------------------------------------------------------- */
 /* Picks the expansion order p, the leaf size N_leaf and the tensor-core levels for a
@@ -316,6 +347,18 @@ int lfmm_tune_cache_load(const char* path);
 int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy,
                             int64_t n_tgt, const lfmm_opts* opts, lfmm_plan_info* info,
                             void* stream);
+
+/* ---- device memory accounting and allocation-failure injection --------------------- */
+/* Bytes in use in the current device's default stream-ordered memory pool, from which
+ * the library takes plan memory and temporaries (the shared operator cache is separate).
+ * With no plan alive and no call in flight it returns to its earlier value: a failed
+ * call leaks nothing. */
+int lfmm_pool_used_bytes(int64_t* bytes);
+/* Test hook: the nth device allocation the library makes from now on (n >= 1; plans,
+ * temporaries and staging buffers, any thread) fails as if the device were out of
+ * memory, so that the caller sees LFMM_ENOMEM; the hook disarms itself after that
+ * allocation.  n = 0 disarms it.  Process-wide. */
+int lfmm_fault_inject_alloc(int64_t nth);
 
 /* ---- tracing ---------------------------------------------------------------------- */
 /* Phases timed by the profiler with CUDA events recorded on the stream each phase is

@@ -1,5 +1,6 @@
 // C ABI of liblfmm.so: plans, evaluation, diagnostics (declared in include/lfmm.h).
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
 #include <mutex>
@@ -21,6 +22,23 @@ int fail(int status, const std::string& msg) {
 }
 
 const char* last_error_cstr() { return t_last_error.c_str(); }
+
+// lfmm_fault_inject_alloc: allocations left until the failing one (0: disarmed)
+std::atomic<int64_t> g_alloc_fail_in{0};
+
+cudaError_t dev_malloc(void** ptr, size_t bytes, cudaStream_t s) {
+    int64_t n = g_alloc_fail_in.load(std::memory_order_relaxed);
+    while (n > 0) {
+        if (g_alloc_fail_in.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) {
+                *ptr = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMallocAsync(ptr, bytes, s);
+}
 
 }  // namespace lfmm
 
@@ -155,7 +173,7 @@ void setup_pool(int dev) {
 int palloc(lfmm_plan* p, void** out, size_t bytes, cudaStream_t s) {
     *out = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(out, bytes, s);
+    cudaError_t e = dev_malloc(out, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *out = nullptr;
@@ -181,7 +199,7 @@ struct Temp {  // stream-ordered temporary freed on scope exit
 
 int talloc(Temp& t, size_t bytes, cudaStream_t s) {
     t.s = s;
-    cudaError_t e = cudaMallocAsync(&t.ptr, bytes ? bytes : 16, s);
+    cudaError_t e = dev_malloc(&t.ptr, bytes ? bytes : 16, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         t.ptr = nullptr;
@@ -294,6 +312,8 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     p->bytes += F.bytes;
     return LFMM_OK;
 }
+
+int ensure_m2l_part(lfmm_plan* p, int nvec, cudaStream_t s);
 
 int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaStream_t s) {
     int st;
@@ -508,6 +528,9 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     p->status = (int*)stbuf;
     LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, s));  // status word + grid-barrier words
     p->tc_min_level = p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level;
+    // the one-vector partial sums of the K-split coarse-level M2L belong to the plan from
+    // the start, so that device_bytes counts them before the first evaluation
+    if ((st = ensure_m2l_part(p, 1, s))) return st;
     // no final synchronisation: temporaries are freed in stream order, and the host
     // buffers of copied coordinates were read before the root-box readback
     return LFMM_OK;
@@ -948,7 +971,7 @@ int lfmm_solve(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy, int6
         for (void* t : temps) cudaFreeAsync(t, s);
     };
     auto upload = [&](const void* h, size_t bytes, cudaStream_t on, void** d) -> int {
-        LFMM_CUDA_TRY(cudaMallocAsync(d, bytes, s));
+        LFMM_CUDA_TRY(dev_malloc(d, bytes, s));
         temps.push_back(*d);
         LFMM_CUDA_TRY(cudaMemcpyAsync(*d, h, bytes, cudaMemcpyHostToDevice, on));
         return LFMM_OK;
@@ -991,7 +1014,7 @@ int lfmm_solve(const int32_t* src_xy, int64_t n_src, const int32_t* tgt_xy, int6
     double* ud = u;
     if (!is_device_ptr(u)) {
         void* d;
-        const cudaError_t e = cudaMallocAsync(&d, (size_t)n_tgt * sizeof(double), s);
+        const cudaError_t e = dev_malloc(&d, (size_t)n_tgt * sizeof(double), s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             if (aux) {
@@ -1115,11 +1138,48 @@ int lfmm_plan_status(lfmm_plan* p, void* stream) {
     LFMM_CUDA_TRY(cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     LFMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     if (h != LFMM_OK) {
-        // status word and the grid-barrier words (a barrier that gave up may leave them set)
-        LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 16, (cudaStream_t)stream));
+        // status word and the grid-barrier words (a barrier that gave up may leave them
+        // set); the fourth word, the wait budget, stays
+        LFMM_CUDA_TRY(cudaMemsetAsync(p->status, 0, 12, (cudaStream_t)stream));
         LFMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
         return fail(h, "a bounded device-side wait gave up; results of the affected evaluation are invalid");
     }
+    return LFMM_OK;
+}
+
+int lfmm_plan_set_wait_budget(lfmm_plan* p, int32_t polls) {
+    if (!p) return fail(LFMM_EINVAL, "NULL plan");
+    if (polls < 0) return fail(LFMM_EINVAL, "polls must be >= 0");
+    // the fourth word of the status buffer (status, barrier count, barrier generation, budget)
+    LFMM_CUDA_TRY(cudaMemcpyAsync(p->status + 3, &polls, sizeof(int32_t), cudaMemcpyHostToDevice, p->last_stream));
+    LFMM_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+    return LFMM_OK;
+}
+
+int lfmm_plan_inject_barrier_stall(lfmm_plan* p) {
+    if (!p) return fail(LFMM_EINVAL, "NULL plan");
+    // an arrival count far beyond any grid: no arrival ever completes the barrier
+    const uint32_t far = 0x80000000u;
+    LFMM_CUDA_TRY(cudaMemcpyAsync(p->status + 1, &far, sizeof(uint32_t), cudaMemcpyHostToDevice, p->last_stream));
+    LFMM_CUDA_TRY(cudaStreamSynchronize(p->last_stream));
+    return LFMM_OK;
+}
+
+int lfmm_pool_used_bytes(int64_t* bytes) {
+    if (!bytes) return fail(LFMM_EINVAL, "NULL argument");
+    int dev = 0;
+    LFMM_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    LFMM_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t used = 0;
+    LFMM_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *bytes = (int64_t)used;
+    return LFMM_OK;
+}
+
+int lfmm_fault_inject_alloc(int64_t nth) {
+    if (nth < 0) return fail(LFMM_EINVAL, "nth must be >= 0");
+    g_alloc_fail_in.store(nth);
     return LFMM_OK;
 }
 
@@ -1211,6 +1271,8 @@ const char* lfmm_status_string(int status) {
         case LFMM_ETIMEOUT: return "device wait timed out";
         case LFMM_EUNSUPPORTED: return "unsupported";
         case LFMM_EINTERNAL: return "internal error";
+        case LFMM_EBUSY: return "refused or shed by the server's overload policy";
+        case LFMM_ECANCELED: return "cancelled";
         default: return "unknown status";
     }
 }

@@ -968,7 +968,7 @@ namespace {
 
 int alloc(std::vector<void*>& owned, int64_t& bytes, void** out, size_t n, cudaStream_t s) {
     *out = nullptr;
-    cudaError_t e = cudaMallocAsync(out, n ? n : 16, s);
+    cudaError_t e = dev_malloc(out, n ? n : 16, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *out = nullptr;
@@ -1092,7 +1092,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     ls = std::min(ls, Kmax);
     DevTemp counts;  // dense leaf counts of the accepted side
     DevTemp ranks;   // each point's arrival rank in its leaf (sources, then targets)
-    LFMM_CUDA_TRY(cudaMallocAsync(&ranks.ptr, (size_t)(ns + nt) * sizeof(int32_t), s));
+    LFMM_CUDA_TRY(dev_malloc(&ranks.ptr, (size_t)(ns + nt) * sizeof(int32_t), s));
     ranks.s = s;
     int32_t* rank_s = (int32_t*)ranks.ptr;
     int32_t* rank_t = rank_s + ns;
@@ -1109,7 +1109,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
         const int64_t NL = leaf_off[np];
         if (NL > ((int64_t)1 << 28)) return fail(LFMM_EUNSUPPORTED, "forest has more than 2^28 leaves");
         counts.reset(s);
-        LFMM_CUDA_TRY(cudaMallocAsync(&counts.ptr, (size_t)(2 * NL + 2) * sizeof(int32_t) + (np + 1) * sizeof(int64_t), s));
+        LFMM_CUDA_TRY(dev_malloc(&counts.ptr, (size_t)(2 * NL + 2) * sizeof(int32_t) + (np + 1) * sizeof(int64_t), s));
         counts.s = s;
         int32_t* cs = (int32_t*)counts.ptr;
         int32_t* ct = cs + NL;
@@ -1155,7 +1155,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     F.tbeg = F.sbeg + (NL + 1);
     DevTemp tmp;
     const int64_t big = std::max<int64_t>(NL, 1);
-    LFMM_CUDA_TRY(cudaMallocAsync(&tmp.ptr, (size_t)exscan_tmp_ints(big) * sizeof(int32_t), s));
+    LFMM_CUDA_TRY(dev_malloc(&tmp.ptr, (size_t)exscan_tmp_ints(big) * sizeof(int32_t), s));
     tmp.s = s;
     int32_t* sums = (int32_t*)tmp.ptr;
     LFMM_CUDA_TRY(exscan(cs, F.sbeg, NL, sums, s));
@@ -1203,7 +1203,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     {
         int64_t ints = 0;
         for (int k = 0; k < nk; ++k) ints += 4 * F.levels[k].S + 1;
-        LFMM_CUDA_TRY(cudaMallocAsync(&lt.ptr, (size_t)(ints + 1) * sizeof(int32_t), s));
+        LFMM_CUDA_TRY(dev_malloc(&lt.ptr, (size_t)(ints + 1) * sizeof(int32_t), s));
         lt.s = s;
         int32_t* q = (int32_t*)lt.ptr;
         for (int k = 0; k < nk; ++k) {
@@ -1214,7 +1214,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     int64_t maxflags = 1;
     for (int k = 0; k < nk; ++k) maxflags = std::max(maxflags, 4 * F.levels[k].S);
     DevTemp ssum;
-    LFMM_CUDA_TRY(cudaMallocAsync(&ssum.ptr, (size_t)exscan_tmp_ints(maxflags) * sizeof(int32_t), s));
+    LFMM_CUDA_TRY(dev_malloc(&ssum.ptr, (size_t)exscan_tmp_ints(maxflags) * sizeof(int32_t), s));
     ssum.s = s;
     for (int k = 0; k < nk; ++k) {
         ForestLevel& lv = F.levels[k];
@@ -1245,7 +1245,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     for (int k = 0; k < nk; ++k)
         for (int c = 0; c <= 4; ++c) idx.push_back((int64_t)(scan[k] - scan[0]) + c * F.levels[k].S);
     DevTemp gi;
-    LFMM_CUDA_TRY(cudaMallocAsync(&gi.ptr, idx.size() * (sizeof(int64_t) + sizeof(int32_t)), s));
+    LFMM_CUDA_TRY(dev_malloc(&gi.ptr, idx.size() * (sizeof(int64_t) + sizeof(int32_t)), s));
     gi.s = s;
     int64_t* didx = (int64_t*)gi.ptr;
     int32_t* dval = (int32_t*)(didx + idx.size());
@@ -1307,7 +1307,7 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     }
     const int64_t ncand = soffs[np];
     DevTemp sf;
-    LFMM_CUDA_TRY(cudaMallocAsync(&sf.ptr, (size_t)(np + 1) * sizeof(int64_t) +
+    LFMM_CUDA_TRY(dev_malloc(&sf.ptr, (size_t)(np + 1) * sizeof(int64_t) +
                                                (size_t)(2 * ncand + 2 + exscan_tmp_ints(ncand)) * sizeof(int32_t), s));
     sf.s = s;
     int64_t* dsoff = (int64_t*)sf.ptr;

@@ -62,9 +62,14 @@ int fail(int status, const std::string& msg);
     do {                                                                               \
         cudaError_t _e = (expr);                                                       \
         if (_e != cudaSuccess)                                                         \
-            return ::lfmm::fail(LFMM_ECUDA, std::string(#expr) + ": " +                 \
-                                                cudaGetErrorString(_e));               \
+            return ::lfmm::fail(_e == cudaErrorMemoryAllocation ? LFMM_ENOMEM : LFMM_ECUDA, \
+                                std::string(#expr) + ": " + cudaGetErrorString(_e));   \
     } while (0)
+
+// Every device allocation of plans, temporaries and staging buffers goes through here
+// (the stream-ordered pool); lfmm_fault_inject_alloc can make the n-th call fail with
+// cudaErrorMemoryAllocation, as a full device would.
+cudaError_t dev_malloc(void** ptr, size_t bytes, cudaStream_t s);
 
 // A failed runtime call that is not a launch (an attribute set, say) also leaves its
 // code as the thread's last error, which the next launch check would report again:
@@ -364,6 +369,10 @@ struct LevelBufs {
 // the split depends on the plan, not on nvec, so one and several vectors sum alike).
 template <typename T>
 int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec);
+// The same from the plan's shape alone (has_tc: the mixed path's tensor-core tiles exist,
+// i.e. binary32 with NP = 32), for footprints computed before any operator is uploaded.
+template <typename T>
+int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level, int num_sms, int nvec);
 // M2M of levels L-1 .. 2 in one cooperative launch (grid barriers between levels).
 // sync: two zero device words (barrier state).  Returns an error (nothing launched)
 // when a cooperative launch is not possible; the caller then runs the per-level path.

@@ -52,11 +52,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_poll_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded by kWaitBudget clock cycles and, for the pipeline's waits, by the plan's poll
+// budget (max_polls); the teardown's waits for work already issued keep the clock bound
+// only, so that no copy or product is in flight when the CTA frees its memory.
+__device__ __forceinline__ bool mbar_poll_bounded(uint64_t* bar, uint32_t parity, uint32_t max_polls = 0xffffffffu) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
+    uint32_t n = 0;
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > kWaitBudget) return false;
+        if (clock64() - t0 > kWaitBudget || ++n > max_polls) return false;
     return true;
 }
 __device__ __forceinline__ void bulk_g2s_u32(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -248,6 +252,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     const int my_tiles = blockIdx.x < (unsigned)all_tiles ? (all_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int total = my_tiles * n_steps;  // K-steps of this CTA
     volatile int* vabort = &s_abort;
+    // the plan's wait budget in polls (status[3], 0: the clock bound alone)
+    const uint32_t wb = ((volatile int*)status)[3] > 0 ? (uint32_t)((volatile int*)status)[3] : 0xffffffffu;
 
     if (threadIdx.x == 0) {
         for (int c = 0; c < 4; ++c) {
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
             tile_of(0, cls, ri0, rj0, v);
             for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
-                if (use > 0 && !mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1))) {
+                if (use > 0 && !mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1), wb)) {
                     abort_now();
                     break;
                 }
@@ -346,8 +352,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
             int slot = 0, use = 0, d = 0, du = 0;
             for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
-                if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1)) ||
-                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1)))) {
+                if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1), wb) ||
+                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1), wb))) {
                     abort_now();
                     break;
                 }
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                 ri = ri0 + xl;
                 rj = rj0 + yl;
             }
-            bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1));
+            bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1), wb);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 if (lane == 0) abort_now();

@@ -243,7 +243,7 @@ extern "C" int lfmm_phi_quadrature(const int32_t* d, const double* w, int32_t n_
         return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
     }();
     double* d_out = out;
-    if (!dev) LFMM_CUDA_TRY(cudaMallocAsync((void**)&d_out, bytes, s));
+    if (!dev) LFMM_CUDA_TRY(dev_malloc((void**)&d_out, bytes, s));
     phi_quad_kernel<<<side * side, kQuadThreads, 0, s>>>(q, R, d_out);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !dev) {

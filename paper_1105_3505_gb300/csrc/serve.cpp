@@ -68,6 +68,8 @@ struct lfmm_server {
     int running = 0;
     int running_cls[2] = {0, 0};
     int max_cls[2] = {0, 0};  // binary64 requests leave slots to the mixed ones
+    int max_pending = 0;      // overload policy (lfmm_server_set_limits); 0: no limit
+    double max_queue_ms = 0.0;
     bool stopping = false;
     std::vector<std::thread> workers;
 
@@ -99,6 +101,37 @@ struct lfmm_server {
         if (in_flight + j.est > budget) return false;
         if (2 * (in_flight + j.est) <= budget) return true;
         return j.est + ((int64_t)256 << 20) <= available();
+    }
+
+    // Completes a waiting request without running it (status EBUSY or ECANCELED).
+    // Caller holds mu and removes the ticket from `pending`.
+    void finish_unrun(Job& j, int status, Clock::time_point now) {
+        j.t_admit = j.t_done = now;
+        j.stats.status = status;
+        j.stats.precision = j.opts.precision;
+        j.stats.queue_ms = ms_between(j.t_submit, now);
+        j.stats.run_ms = 0.0;
+        j.stats.total_ms = j.stats.queue_ms;
+        j.done = true;
+    }
+
+    // Overload policy: sheds every waiting request whose wait exceeds the latency budget.
+    // Caller holds mu; returns whether any was shed (waiters must then be woken).
+    bool shed_expired() {
+        if (max_queue_ms <= 0.0 || pending.empty()) return false;
+        const Clock::time_point now = Clock::now();
+        bool any = false;
+        for (size_t i = 0; i < pending.size();) {
+            Job& j = jobs[pending[i]];
+            if (ms_between(j.t_submit, now) > max_queue_ms) {
+                finish_unrun(j, LFMM_EBUSY, now);
+                pending.erase(pending.begin() + (std::ptrdiff_t)i);
+                any = true;
+            } else {
+                ++i;
+            }
+        }
+        return any;
     }
 
     // Position in `pending` of the request to start next, or -1.  Requests start in
@@ -133,7 +166,10 @@ struct lfmm_server {
             {
                 std::unique_lock<std::mutex> lk(mu);
                 int64_t at = -1;
-                cv_work.wait(lk, [&] { return (stopping && pending.empty()) || (at = pick()) >= 0; });
+                cv_work.wait(lk, [&] {
+                    if (shed_expired()) cv_done.notify_all();
+                    return (stopping && pending.empty()) || (at = pick()) >= 0;
+                });
                 if (pending.empty()) break;  // stopping and drained
                 ticket = pending[at];
                 pending.erase(pending.begin() + at);
@@ -233,13 +269,49 @@ int lfmm_server_submit(lfmm_server* sv, const lfmm_request* req, int64_t* ticket
     }
     j.est = estimate_bytes(*req, j.opts);
     j.t_submit = Clock::now();
+    bool shed = false;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stopping) return lfmm::fail(LFMM_EINVAL, "server is shutting down");
+        shed = sv->shed_expired();
+        if (sv->max_pending > 0 && (int64_t)sv->pending.size() >= sv->max_pending) {
+            if (shed) sv->cv_done.notify_all();
+            return lfmm::fail(LFMM_EBUSY, "server queue full (" + std::to_string(sv->pending.size()) +
+                                              " requests waiting for admission)");
+        }
         *ticket = sv->next_ticket++;
         sv->jobs.emplace(*ticket, j);
         sv->pending.push_back(*ticket);
     }
+    if (shed) sv->cv_done.notify_all();
+    sv->cv_work.notify_all();
+    return LFMM_OK;
+}
+
+int lfmm_server_set_limits(lfmm_server* sv, int32_t max_pending, double max_queue_ms) {
+    if (!sv) return lfmm::fail(LFMM_EINVAL, "NULL server");
+    if (max_pending < 0 || !(max_queue_ms >= 0.0)) return lfmm::fail(LFMM_EINVAL, "limits must be >= 0");
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->max_pending = max_pending;
+        sv->max_queue_ms = max_queue_ms;
+    }
+    sv->cv_work.notify_all();
+    return LFMM_OK;
+}
+
+int lfmm_server_cancel(lfmm_server* sv, int64_t ticket) {
+    if (!sv) return lfmm::fail(LFMM_EINVAL, "NULL server");
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = std::find(sv->pending.begin(), sv->pending.end(), ticket);
+        if (it == sv->pending.end())
+            return lfmm::fail(LFMM_EINVAL, sv->jobs.count(ticket) ? "request already admitted or finished"
+                                                                   : "unknown ticket");
+        sv->finish_unrun(sv->jobs[ticket], LFMM_ECANCELED, Clock::now());
+        sv->pending.erase(it);
+    }
+    sv->cv_done.notify_all();
     sv->cv_work.notify_all();
     return LFMM_OK;
 }

@@ -161,8 +161,8 @@ int lfmm_autotune(const int32_t* src_xy, int64_t n_src, const int64_t* src_offse
     b.s = (cudaStream_t)stream;
     LFMM_CUDA_TRY(cudaEventCreate(&b.a));
     LFMM_CUDA_TRY(cudaEventCreate(&b.b));
-    LFMM_CUDA_TRY(cudaMallocAsync((void**)&b.f, (size_t)n_src * sizeof(double), b.s));
-    LFMM_CUDA_TRY(cudaMallocAsync((void**)&b.u, (size_t)n_tgt * sizeof(double), b.s));
+    LFMM_CUDA_TRY(lfmm::dev_malloc((void**)&b.f, (size_t)n_src * sizeof(double), b.s));
+    LFMM_CUDA_TRY(lfmm::dev_malloc((void**)&b.u, (size_t)n_tgt * sizeof(double), b.s));
     {
         // uniform in (-1, 1), each problem shifted to zero sum
         std::vector<double> f((size_t)n_src);

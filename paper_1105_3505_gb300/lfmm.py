@@ -15,7 +15,8 @@ import numpy as np
 
 from .build import LIB
 
-LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL = range(7)
+(LFMM_OK, LFMM_EINVAL, LFMM_ENOMEM, LFMM_ECUDA, LFMM_ETIMEOUT, LFMM_EUNSUPPORTED, LFMM_EINTERNAL, LFMM_EBUSY,
+ LFMM_ECANCELED) = range(9)
 LFMM_FP64, LFMM_MIXED, LFMM_DF = 0, 1, 2
 LFMM_TREE_AUTO, LFMM_TREE_UNIFORM, LFMM_TREE_PRUNED = 0, 1, 2
 LFMM_FLAG_GRAPH, LFMM_FLAG_SERIAL = 1, 2
@@ -102,6 +103,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lfmm_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(lfmm_request), ctypes.POINTER(i64)]),
         "lfmm_server_wait": (ctypes.c_int, [vp, i64, ctypes.POINTER(lfmm_request_stats)]),
         "lfmm_server_destroy": (ctypes.c_int, [vp]),
+        "lfmm_server_set_limits": (ctypes.c_int, [vp, i32, ctypes.c_double]),
+        "lfmm_server_cancel": (ctypes.c_int, [vp, i64]),
+        "lfmm_plan_set_wait_budget": (ctypes.c_int, [vp, i32]),
+        "lfmm_plan_inject_barrier_stall": (ctypes.c_int, [vp]),
+        "lfmm_pool_used_bytes": (ctypes.c_int, [ctypes.POINTER(i64)]),
+        "lfmm_fault_inject_alloc": (ctypes.c_int, [i64]),
         "lfmm_autotune": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, i64, ctypes.c_double, ctypes.POINTER(lfmm_opts),
                                          ctypes.POINTER(lfmm_tune_result), vp]),
         "lfmm_tune_cache_clear": (ctypes.c_int, []),
@@ -275,6 +282,24 @@ def lfmm_profile_read(reset: bool = False) -> dict:
     n = np.zeros(len(PHASES), dtype=np.int64)
     _check(load().lfmm_profile_read(ms.ctypes.data, n.ctypes.data, 1 if reset else 0), "lfmm_profile_read")
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PHASES)}
+
+
+def lfmm_plan_set_wait_budget(plan: int, polls: int) -> None:
+    _check(load().lfmm_plan_set_wait_budget(plan, int(polls)), "lfmm_plan_set_wait_budget")
+
+
+def lfmm_plan_inject_barrier_stall(plan: int) -> None:
+    _check(load().lfmm_plan_inject_barrier_stall(plan), "lfmm_plan_inject_barrier_stall")
+
+
+def lfmm_pool_used_bytes() -> int:
+    v = ctypes.c_int64()
+    _check(load().lfmm_pool_used_bytes(ctypes.byref(v)), "lfmm_pool_used_bytes")
+    return v.value
+
+
+def lfmm_fault_inject_alloc(nth: int) -> None:
+    _check(load().lfmm_fault_inject_alloc(int(nth)), "lfmm_fault_inject_alloc")
 
 
 def lfmm_launch_count() -> int:
@@ -460,11 +485,27 @@ class Server:
         return t.value
 
     def wait(self, ticket: int):
+        out, stats = self.wait_stats(ticket)
+        _check(stats["status"], "lfmm_server_wait")
+        return out, stats
+
+    def wait_stats(self, ticket: int):
+        """(u or None, stats) without raising for the request's own failure (a refused,
+        shed or cancelled request has stats["status"] != LFMM_OK)."""
         st = lfmm_request_stats()
         status = load().lfmm_server_wait(self.handle, int(ticket), ctypes.byref(st))
         _, _, _, out = self._live.pop(ticket)
-        _check(status, "lfmm_server_wait")
-        return out, {name: getattr(st, name) for name, _ in lfmm_request_stats._fields_}
+        stats = {name: getattr(st, name) for name, _ in lfmm_request_stats._fields_}
+        if status != LFMM_OK and stats["status"] == LFMM_OK:
+            stats["status"] = status
+        return (out if status == LFMM_OK else None), stats
+
+    def set_limits(self, max_pending: int = 0, max_queue_ms: float = 0.0):
+        _check(load().lfmm_server_set_limits(self.handle, int(max_pending), float(max_queue_ms)),
+               "lfmm_server_set_limits")
+
+    def cancel(self, ticket: int):
+        _check(load().lfmm_server_cancel(self.handle, int(ticket)), "lfmm_server_cancel")
 
     def close(self):
         if getattr(self, "handle", None):
