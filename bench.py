@@ -47,9 +47,12 @@ def parse_args():
     ap.add_argument("--impl", choices=["lfmm", "reference"], default="lfmm")
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 comparison, oracle checks, cpu baseline, serving")
-    ap.add_argument("--serve-requests", type=int, default=600,
-                    help="requests of the serving stream replayed at its arrival times (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="requests of the serving stream replayed at their arrival times (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-pool", type=int, default=1024, help="distinct request contents generated for the replay")
+    ap.add_argument("--serve-budget-ms", type=float, default=100.0,
+                    help="server overload policy: shed a request after this long waiting for admission")
     return ap.parse_args()
 
 
@@ -151,6 +154,23 @@ def m2l_flops(info, P, levels=None) -> int:
     return total
 
 
+def m2l_tc_roofline(info, P, tc_levels, phases, n_prof, peaks, peak_src):
+    """Tensor-core M2L (+ fused L2L) of the step's tensor-core levels: useful flops per
+    level over the phase's device time per level (which also holds each level's TF32
+    split launch, so the fraction is a lower bound for the kernel itself)."""
+    ms_level = phases["m2l_tc"][0] / n_prof / max(1, len(tc_levels))
+    flops = m2l_flops(info, P, tc_levels) // max(1, len(tc_levels))
+    achieved = flops / (ms_level * 1e-3) / 1e12
+    peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
+    return {"kernel": "m2l_tma_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l_tma_kernel"),
+            "peak_basis": f"tf32 dense = measured bf16 burst {peaks['bf16_tflops']} x {TF32_PER_BF16:.3f} "
+                          f"(nominal 1.1 / 2.25 PFLOP/s) ({peak_src}); useful flops only, the 3xTF32 split "
+                          f"issues 3 MMAs per useful product",
+            "levels": tc_levels, "units_per_launch": flops, "ms_per_launch": ms_level,
+            "time_basis": "tensor-core phase per level, TF32 split launch included"}
+
+
 # ---------------------------------------------------------------- reference arm (oracle)
 def reference_arm(args, rank, world):
     if rank != 0:
@@ -220,6 +240,145 @@ def traffic_for(kernel: str):
     return e["bytes_per_launch"] if h == e.get("source_sha256_16") else None
 
 
+# ---------------------------------------------------------------- equal-accuracy binary64 arm
+def fp64_equal_accuracy(lfmm, timed, s_d, t_d, f_d, u_d, idx, ref, ns, nt, value_mixed, steps):
+    """The plain all-binary64 path at the metric's accuracy bar: the smallest p in 5..9
+    whose sampled max-norm error is <= 1e-6 at leaf size 64, then that p timed (plan
+    create + eval, L2 flushed) at leaf sizes 64, 128 and 256; the best is reported."""
+    scale = np.abs(ref).max()
+    chosen, errs = None, {}
+    for p in range(5, 10):
+        ms, _ = timed(s_d, t_d, f_d, u_d, lfmm.make_opts(lfmm.LFMM_FP64, p, 64, 32, 64), 1, 0, sync_ranks=False)
+        errs[p] = float(np.abs(u_d.cpu().numpy()[idx] - ref).max() / scale)
+        if errs[p] <= 1e-6:
+            chosen = p
+            break
+    if chosen is None:
+        return {"error": "no p in 5..9 met 1e-6", "rel_err_by_p": errs}
+    rows = {}
+    for leaf in (64, 128, 256):
+        ms, _ = timed(s_d, t_d, f_d, u_d, lfmm.make_opts(lfmm.LFMM_FP64, chosen, leaf, 32, 64), steps, 1,
+                      sync_ranks=False)
+        rows[leaf] = {"ms_per_step": ms, "Mpoints_per_s": (ns + nt) / (ms * 1e-3) / 1e6,
+                      "rel_err": float(np.abs(u_d.cpu().numpy()[idx] - ref).max() / scale)}
+    best = min(rows, key=lambda k: rows[k]["ms_per_step"])
+    return {"p": chosen, "leaf_size": best, "value": rows[best]["Mpoints_per_s"], "unit": "Mpoints/s",
+            "ms_per_step": rows[best]["ms_per_step"], "rel_err": rows[best]["rel_err"], "by_leaf": rows,
+            "rel_err_by_p_leaf64": errs, "mixed_over_fp64": value_mixed / rows[best]["Mpoints_per_s"],
+            "note": "plan create + eval, inputs resident, L2 flushed; smallest p meeting rel err <= 1e-6 on the "
+                    "128 sampled targets, best leaf size"}
+
+
+def cold_plan_create(lfmm, s_d, t_d, ns, nt, stream, p):
+    """Plan creation with the model-box operators built in the call (fresh cache keys)."""
+    import torch
+    ts = []
+    for ppe in (63, 62, 61):
+        o = lfmm.make_opts(lfmm.LFMM_MIXED, p, 64, 32, ppe)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = lfmm.lfmm_plan_create(s_d, ns, t_d, nt, o, stream)
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+        lfmm.lfmm_plan_destroy(h)
+    return {"median_ms": float(np.median(ts)), "samples_ms": ts,
+            "note": "host wall clock of lfmm_plan_create with a cold operator cache (skeletons, T_ofs, M2M/L2L, "
+                    "T_ifo and their device images built in the call); the timed step reuses the cache"}
+
+
+def _timed_steps(fn, steps, warmup, stream, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def uniform_4k_leg(lfmm, steps: int = 20, warmup: int = 3):
+    """The plain-method case: 4,096 distinct points from [0,256)^2, targets = sources
+    (seed 0); plan create + eval per step, binary64 at p = 16 and mixed at p = 8, each
+    checked against the full oracle."""
+    import torch
+    import oracle
+    from paper_1105_3505_gb300 import workloads
+    prob = workloads.uniform_4k()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (prob.src, prob.tgt, prob.f))
+    u_d = torch.empty(prob.tgt.shape[0], dtype=torch.float64, device=dev)
+    ns, nt = prob.src.shape[0], prob.tgt.shape[0]
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt)
+    res = {"workload": "uniform_4k: 4,096 distinct points from [0,256)^2, targets = sources, seed 0"}
+    for name, prec, p in (("fp64_p16", lfmm.LFMM_FP64, 16), ("mixed_p8", lfmm.LFMM_MIXED, 8)):
+        o = lfmm.make_opts(prec, p, 64, 32, 64)
+
+        def step():
+            h = lfmm.lfmm_plan_create(s_d, ns, t_d, nt, o, stream)
+            lfmm.lfmm_eval(h, f_d, u_d, stream)
+            lfmm.lfmm_plan_destroy(h)
+
+        ms = _timed_steps(step, steps, warmup, stream, flush)
+        err = float(np.abs(u_d.cpu().numpy() - ref).max() / np.abs(ref).max())
+        res[name] = {"ms_per_step": ms, "Mpoints_per_s": (ns + nt) / (ms * 1e-3) / 1e6, "rel_err_full_oracle": err}
+    return res
+
+
+def clustered_leg(lfmm, steps: int = 5, warmup: int = 2):
+    """The clustered workload (4,194,304 points in 64 Gaussian clusters plus 16 segments,
+    targets = sources, seed 2) on the pruned tree, mixed at p = 8: plan create + eval per
+    step (L2 flushed), the tree build's share of a serial pass, and 256 sampled targets
+    against the oracle."""
+    import torch
+    import oracle
+    from paper_1105_3505_gb300 import workloads
+    prob = workloads.clustered_4m()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (prob.src, prob.tgt, prob.f))
+    u_d = torch.empty(prob.tgt.shape[0], dtype=torch.float64, device=dev)
+    ns, nt = prob.src.shape[0], prob.tgt.shape[0]
+    o = lfmm.make_opts(lfmm.LFMM_MIXED, 8, 64, 32, 64)
+
+    def step():
+        h = lfmm.lfmm_plan_create(s_d, ns, t_d, nt, o, stream)
+        lfmm.lfmm_eval(h, f_d, u_d, stream)
+        lfmm.lfmm_plan_destroy(h)
+
+    ms = _timed_steps(step, steps, warmup, stream, flush)
+    u = u_d.cpu().numpy()
+    lfmm.lfmm_profile_enable(True)
+    lfmm.lfmm_profile_read(reset=True)
+    os_ = lfmm.make_opts(lfmm.LFMM_MIXED, 8, 64, 32, 64, serial=True)
+    h = lfmm.lfmm_plan_create(s_d, ns, t_d, nt, os_, stream)
+    lfmm.lfmm_eval(h, f_d, u_d, stream)
+    info = lfmm.lfmm_plan_get_info(h)
+    torch.cuda.synchronize()
+    lfmm.lfmm_plan_destroy(h)
+    ph = lfmm.lfmm_profile_read(reset=True)
+    lfmm.lfmm_profile_enable(False)
+    total = sum(v[0] for v in ph.values())
+    idx = np.random.default_rng(321).choice(nt, 256, replace=False)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+    return {"workload": "clustered_4m: 4,194,304 points, 64 Gaussian clusters (sigma 200) + 1% on 16 segments, "
+                        "targets = sources, seed 2",
+            "ms_per_step": ms, "Mpoints_per_s": (ns + nt) / (ms * 1e-3) / 1e6, "tree": info["tree"],
+            "levels": info["L"], "leaf_side": info["leaf_side"], "boxes": info["n_boxes"],
+            "phases_ms_serial": {k: v[0] for k, v in ph.items()},
+            "tree_share_serial": ph["tree"][0] / total if total > 0 else None,
+            "rel_err_256_sampled": float(np.abs(u[idx] - ref).max() / np.abs(ref).max())}
+
+
 # ---------------------------------------------------------------- serving leg
 def _serve_gen(task):
     seed, n, i = task
@@ -227,19 +386,27 @@ def _serve_gen(task):
     return workloads.serve_request(workloads.serve_schedule(seed=seed, n_requests=n), i)
 
 
-def serve_leg(lfmm, n_requests: int, slots: int, check: int = 24):
-    """Replays the first n_requests of the serving stream (Poisson arrivals at 2,000
-    req/s, N_src log-uniform in [1e3, 1e6], uniform or four clusters, N_tgt = N_src/4,
-    tolerance 1e-6 or 1e-10) against an lfmm server: each request is submitted at its
-    arrival time; latency = submit -> result in host memory."""
+def serve_leg(lfmm, n_requests: int, slots: int, pool_size: int = 1024, budget_ms: float = 100.0,
+              check: int = 24):
+    """Replays the serving stream against an lfmm server: n_requests Poisson arrivals at
+    2,000 req/s (the whole 20,000-request stream by default), each submitted at its
+    arrival time; latency = submit -> result in host memory.  Request contents (N_src
+    log-uniform in [1e3, 1e6], uniform or four clusters, N_tgt = N_src/4, tolerance 1e-6
+    or 1e-10) are the first pool_size requests of the stream, generated once and reused
+    in turn (request i carries request i mod pool_size's points, charges and tolerance),
+    so that the replay needs seconds of host time rather than minutes.  The server runs
+    its overload policy: a request that waited more than budget_ms for admission is shed
+    (LFMM_EBUSY)."""
     import multiprocessing as mp
     import threading
     import oracle
     from paper_1105_3505_gb300 import workloads
     seed = 4
+    pool_size = min(pool_size, n_requests)
+    sched = workloads.serve_schedule(seed=seed, n_requests=n_requests)
     t_gen = time.perf_counter()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
-        reqs = pool.map(_serve_gen, [(seed, n_requests, i) for i in range(n_requests)], chunksize=4)
+        reqs = pool.map(_serve_gen, [(seed, pool_size, i) for i in range(pool_size)], chunksize=4)
         warm = pool.map(_serve_gen, [(seed + 101, 24, i) for i in range(24)], chunksize=2)
     t_gen = time.perf_counter() - t_gen
     # requests arrive in page-locked host buffers (as a serving front end would hand
@@ -253,67 +420,93 @@ def serve_leg(lfmm, n_requests: int, slots: int, check: int = 24):
                        torch.from_numpy(pr.f).pin_memory(),
                        torch.empty(pr.tgt.shape[0], dtype=torch.float64).pin_memory()))
     t_pin = time.perf_counter() - t_pin
+    arrival = sched["arrival_s"]
+    rng = np.random.default_rng(7)
+    checked_idx = set(int(i) for i in rng.choice(n_requests, min(4 * check, n_requests), replace=False))
     with lfmm.Server(n_slots=slots) as sv:
         # warm start: model-box operators of both precisions at the leaf sides that occur
         for r in warm:
             sv.wait(sv.submit(r.problem.src, r.problem.tgt, r.problem.f, r.tol))
-        tickets, submit_t = [], []
-        results = [None] * n_requests
-        done_t = [0.0] * n_requests
+        sv.set_limits(max_pending=0, max_queue_ms=budget_ms)
+        tickets = [None] * n_requests
+        stats = [None] * n_requests
+        done = [threading.Event() for _ in range(n_requests)]
+        kept = {}
+        submit_err = [0]
 
         def waiter():
             for i in range(n_requests):
-                while i >= len(tickets):
+                while tickets[i] is None:
                     time.sleep(0.0002)
-                try:
-                    results[i] = sv.wait(tickets[i])
-                except lfmm.LfmmError as e:
-                    results[i] = (None, {"status": e.status, "total_ms": float("nan"), "queue_ms": float("nan"),
-                                         "run_ms": float("nan")})
-                done_t[i] = time.perf_counter()
+                if tickets[i] < 0:
+                    stats[i] = {"status": -tickets[i]}
+                else:
+                    u, st = sv.wait_stats(tickets[i])
+                    stats[i] = st
+                    if u is not None and i in checked_idx:
+                        kept[i] = u.numpy().copy()
+                done[i].set()
 
         th = threading.Thread(target=waiter)
         th.start()
         t0 = time.perf_counter()
-        for r, (ps, pt, pf, pu) in zip(reqs, pinned):
-            delay = t0 + r.arrival_s - time.perf_counter()
+        for i in range(n_requests):
+            k = i % pool_size
+            if i >= pool_size:
+                done[i - pool_size].wait()  # its output buffer is reused
+            delay = t0 + arrival[i] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            submit_t.append(time.perf_counter())
-            tickets.append(sv.submit(ps, pt, pf, r.tol, out=pu))
+            r, (ps, pt, pf, pu) = reqs[k], pinned[k]
+            try:
+                tickets[i] = sv.submit(ps, pt, pf, r.tol, out=pu)
+            except lfmm.LfmmError as e:
+                submit_err[0] += 1
+                tickets[i] = -e.status
         th.join()
-    failed = sum(1 for u, _ in results if u is None)
-    keep = [i for i, (u, _) in enumerate(results) if u is not None]
-    reqs = [reqs[i] for i in keep]
-    results = [results[i] for i in keep]
-    lat = np.array([st["total_ms"] for _, st in results])
-    qms = np.array([st["queue_ms"] for _, st in results])
-    rms = np.array([st["run_ms"] for _, st in results])
-    tight = np.array([r.tol < 1e-6 for r in reqs])
-    pts = sum(r.problem.n_points for r in reqs)
-    span = max(done_t) - t0
+        t_end = time.perf_counter()
+    codes = np.array([st["status"] for st in stats])
+    ok = codes == lfmm.LFMM_OK
+    tol = np.array([reqs[i % pool_size].tol for i in range(n_requests)])
+    pts_all = np.array([reqs[i % pool_size].problem.n_points for i in range(n_requests)])
+    served = np.nonzero(ok)[0]
+    lat = np.array([stats[i]["total_ms"] for i in served])
+    qms = np.array([stats[i]["queue_ms"] for i in served])
+    rms = np.array([stats[i]["run_ms"] for i in served])
+    tight = tol[served] < 1e-6
+    span = t_end - t0
     errs = []
-    for i in np.random.default_rng(7).choice(len(reqs), min(check, len(reqs)), replace=False):
-        r = reqs[i]
+    for i in sorted(kept)[:check]:
+        r = reqs[i % pool_size]
         idx = np.random.default_rng(int(i)).choice(r.problem.tgt.shape[0], min(64, r.problem.tgt.shape[0]),
                                                    replace=False)
         ref = oracle.lattice_sum(r.problem.src, r.problem.f, r.problem.tgt[idx])
-        errs.append((r.tol, float(np.abs(results[i][0].numpy()[idx] - ref).max() / np.abs(ref).max())))
-    return {"requests": n_requests, "failed": failed, "rate_req_per_s": 2000.0, "slots": slots,
-            "arrival_span_s": float(reqs[-1].arrival_s), "completion_span_s": span,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "p50_ms_mixed": float(np.percentile([l for l, r in zip(lat, reqs) if r.tol >= 1e-6], 50)),
-            "p50_ms_df": float(np.percentile([l for l, r in zip(lat, reqs) if r.tol < 1e-6], 50)),
-            "queue_p50_ms": float(np.percentile(qms, 50)), "queue_p99_ms": float(np.percentile(qms, 99)),
-            "run_p50_ms_mixed": float(np.percentile(rms[~tight], 50)), "run_p50_ms_df": float(np.percentile(rms[tight], 50)),
-            "run_p99_ms_mixed": float(np.percentile(rms[~tight], 99)), "run_p99_ms_df": float(np.percentile(rms[tight], 99)),
-            "pin_s": t_pin,
-            "Mpoints_per_s": pts / span / 1e6, "points": int(pts),
+        errs.append((r.tol, float(np.abs(kept[i][idx] - ref).max() / np.abs(ref).max())))
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if len(a) else None
+
+    return {"requests": n_requests, "served": int(ok.sum()), "shed": int((codes == lfmm.LFMM_EBUSY).sum()),
+            "failed_other": int((~ok & (codes != lfmm.LFMM_EBUSY)).sum()), "refused_at_submit": submit_err[0],
+            "served_1e-6": int((ok & (tol >= 1e-6)).sum()), "served_1e-10": int((ok & (tol < 1e-6)).sum()),
+            "offered_1e-6": int((tol >= 1e-6).sum()), "offered_1e-10": int((tol < 1e-6).sum()),
+            "rate_req_per_s": 2000.0, "slots": slots, "latency_budget_ms": budget_ms,
+            "arrival_span_s": float(arrival[-1]), "completion_span_s": span,
+            "offered_Mpoints_per_s": float(pts_all.sum() / arrival[-1] / 1e6),
+            "served_Mpoints_per_s": float(pts_all[served].sum() / span / 1e6),
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+            "p50_ms_mixed": pct(lat[~tight], 50), "p99_ms_mixed": pct(lat[~tight], 99),
+            "p50_ms_df": pct(lat[tight], 50), "p99_ms_df": pct(lat[tight], 99),
+            "queue_p50_ms": pct(qms, 50), "queue_p99_ms": pct(qms, 99),
+            "run_p50_ms_mixed": pct(rms[~tight], 50), "run_p50_ms_df": pct(rms[tight], 50),
+            "run_p99_ms_mixed": pct(rms[~tight], 99), "run_p99_ms_df": pct(rms[tight], 99),
             "checked": len(errs), "max_rel_err_1e-6_requests": max([e for t, e in errs if t >= 1e-6], default=None),
             "max_rel_err_1e-10_requests": max([e for t, e in errs if t < 1e-6], default=None),
-            "generation_s": t_gen,
-            "note": "first n requests of the 20,000-request stream (seed 4), submitted at their arrival times; "
-                    "tol 1e-6 -> mixed path p = 8, tol 1e-10 -> float-float path p = 16 (leaf 192)"}
+            "generation_s": t_gen, "pin_s": t_pin, "pool": pool_size,
+            "note": f"the whole {n_requests}-request stream (seed 4) submitted at its arrival times; contents of "
+                    f"the first {pool_size} requests reused in turn; overload policy: shed after {budget_ms} ms "
+                    "waiting for admission; tol 1e-6 -> mixed path p = 8, tol 1e-10 -> float-float path p = 16 "
+                    "(leaf 192)"}
 
 
 # ---------------------------------------------------------------- batched forest leg
@@ -718,15 +911,7 @@ def main():
                 "peak_basis": f"shared-memory loads: 152 SMs x 32 lanes/clk x {sm_mhz:.0f} MHz ({peak_src})",
                 "units_per_launch": pairs, "ms_per_launch": cands[dom]}
     elif dom == "m2l_tc":
-        flops = m2l_flops(info, P, tc_levels) // max(1, len(tc_levels))
-        achieved = flops / t_launch / 1e12
-        peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
-        roof = {"kernel": "m2l_tc_ss_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic_for("m2l_tc_ss_kernel"),
-                "peak_basis": f"tf32 dense = measured bf16 burst {peaks['bf16_tflops']} x {TF32_PER_BF16:.3f} "
-                              f"(nominal 1.1 / 2.25 PFLOP/s) ({peak_src}); useful flops only, the 3xTF32 split "
-                              f"issues 3 MMAs per useful product",
-                "units_per_launch": flops, "ms_per_launch": cands[dom]}
+        roof = m2l_tc_roofline(info, P, tc_levels, phases, n_prof, peaks, peak_src)
     else:
         flops = 2 * P * ns
         achieved = flops / t_launch / 1e12
@@ -748,6 +933,8 @@ def main():
                    "d2h_bytes_per_step": int(u_h.numel() * 8)},
            "gpu_launches": int(launches),
            "roofline": roof,
+           "roofline_m2l_tc": (m2l_tc_roofline(info, P, tc_levels, phases, n_prof, peaks, peak_src)
+                               if tc_levels and phases["m2l_tc"][1] > 0 else None),
            "phases_ms": phase_ms,
            "phases_note": "per-phase device time from CUDA events around each phase, over a pass of the same "
                           "step with LFMM_FLAG_SERIAL (every kernel alone on the device); the timed value runs "
@@ -760,6 +947,13 @@ def main():
         ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
         scale = np.abs(ref).max()
         out["rel_err"] = float(np.abs(u_mixed[idx] - ref).max() / scale)
+        # the plain all-binary64 path at the same accuracy bar (rel err <= 1e-6): the
+        # smallest p that meets it on the sampled targets, at its best leaf size
+        out["fp64_at_1e-6"] = fp64_equal_accuracy(lfmm, timed, s_d, t_d, f_d, u_d, idx, ref, ns, nt, value,
+                                                  max(3, args.steps // 4))
+        # plan creation with the operator cache cold (a proxies_per_edge not used before
+        # gives a new cache key: skeletons, operators and their device images are built)
+        out["cold_plan_create_ms"] = cold_plan_create(lfmm, s_d, t_d, ns, nt, stream, args.p)
         # the plain all-binary64 path at p = 16 on the same workload
         o64 = lfmm.make_opts(lfmm.LFMM_FP64, 16, 64, 32, 64)
         ms64, _ = timed(s_d, t_d, f_d, u_d, o64, max(2, args.steps // 5), 1, sync_ranks=False)
@@ -774,12 +968,15 @@ def main():
             out[key] = {"value": (ns + nt) / (ms2 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms2,
                         "rel_err": float(np.abs(u2[idx] - ref).max() / scale), "leaf_size": leaf}
         out["cpu_baseline"] = cpu_baseline(prob)
+        out["uniform_4k"] = uniform_4k_leg(lfmm)
+        out["clustered_4m"] = clustered_leg(lfmm)
         out["forest"] = forest_leg(lfmm)
         out["eval_only"] = eval_leg(lfmm)
         out["multi_rhs"] = multi_leg(lfmm)
         out["solvers"] = solvers_leg(lfmm)
         if args.serve_requests > 0:
-            out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots)
+            out["serve"] = serve_leg(lfmm, args.serve_requests, args.serve_slots, args.serve_pool,
+                                     args.serve_budget_ms)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
