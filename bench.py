@@ -51,7 +51,7 @@ def parse_args():
                     help="requests of the serving stream replayed at their arrival times (0: skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=1024, help="distinct request contents generated for the replay")
-    ap.add_argument("--serve-budget-ms", type=float, default=100.0,
+    ap.add_argument("--serve-budget-ms", type=float, default=50.0,
                     help="server overload policy: shed a request after this long waiting for admission")
     return ap.parse_args()
 
@@ -386,7 +386,7 @@ def _serve_gen(task):
     return workloads.serve_request(workloads.serve_schedule(seed=seed, n_requests=n), i)
 
 
-def serve_leg(lfmm, n_requests: int, slots: int, pool_size: int = 1024, budget_ms: float = 100.0,
+def serve_leg(lfmm, n_requests: int, slots: int, pool_size: int = 1024, budget_ms: float = 50.0,
               check: int = 24):
     """Replays the serving stream against an lfmm server: n_requests Poisson arrivals at
     2,000 req/s (the whole 20,000-request stream by default), each submitted at its
@@ -395,8 +395,9 @@ def serve_leg(lfmm, n_requests: int, slots: int, pool_size: int = 1024, budget_m
     or 1e-10) are the first pool_size requests of the stream, generated once and reused
     in turn (request i carries request i mod pool_size's points, charges and tolerance),
     so that the replay needs seconds of host time rather than minutes.  The server runs
-    its overload policy: a request that waited more than budget_ms for admission is shed
-    (LFMM_EBUSY)."""
+    its overload policy with a latency budget of budget_ms: a request whose predicted wait
+    exceeds it is refused at submit, and one that waits longer anyway is shed (both
+    LFMM_EBUSY)."""
     import multiprocessing as mp
     import threading
     import oracle
@@ -504,9 +505,9 @@ def serve_leg(lfmm, n_requests: int, slots: int, pool_size: int = 1024, budget_m
             "max_rel_err_1e-10_requests": max([e for t, e in errs if t < 1e-6], default=None),
             "generation_s": t_gen, "pin_s": t_pin, "pool": pool_size,
             "note": f"the whole {n_requests}-request stream (seed 4) submitted at its arrival times; contents of "
-                    f"the first {pool_size} requests reused in turn; overload policy: shed after {budget_ms} ms "
-                    "waiting for admission; tol 1e-6 -> mixed path p = 8, tol 1e-10 -> float-float path p = 16 "
-                    "(leaf 192)"}
+                    f"the first {pool_size} requests reused in turn; overload policy with a {budget_ms} ms latency "
+                    "budget (refused at submit when the predicted wait exceeds it, shed when the wait does); tol "
+                    "1e-6 -> mixed path p = 8, tol 1e-10 -> float-float path p = 16 (leaf 192)"}
 
 
 # ---------------------------------------------------------------- batched forest leg

@@ -76,6 +76,16 @@ typedef struct lfmm_opts {
                               /* tensor cores (0 = default 7; a value > 30 disables them)     */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
     int32_t flags;            /* bitwise OR of LFMM_FLAG_* (0: none)                           */
+    /* M2L tiling (0 everywhere: the library's rules; lfmm_autotune picks these).  They    */
+    /* change how the interaction-list GEMM of Sec. 8.2 step 3 is cut into tiles, not    */
+    /* what it computes: results differ at most by rounding (summation order).            */
+    int32_t m2l_tile;         /* tensor-core M2L: target tile width in boxes, 16, 32, 64 or    */
+                              /* 128 (a tile is 128 boxes of one parity class, as wide as    */
+                              /* this and the class row allow); 0: as wide as possible       */
+    int32_t m2l_stages;       /* tensor-core M2L: depth of the TMA ring, 2, 3 or 4 (0: 3)      */
+    int32_t m2l_split;        /* coarse-level and list M2L kernels: chunks the 27 interaction  */
+                              /* offsets are split into, 1 .. 9 (0: by the number of tiles)   */
+    int32_t reserved;         /* must be 0                                                     */
 } lfmm_opts;
 
 /* Evaluate through a CUDA graph: the first lfmm_eval / lfmm_eval_parts of a plan records
@@ -104,7 +114,8 @@ typedef struct lfmm_opts {
 #define LFMM_TREE_PRUNED 2
 
 /* Fill opts with the defaults: LFMM_MIXED, p = 8, leaf_size = 64, max_leaf_side = 32,
- * proxies_per_edge = 64, tc_min_level = 0, tree = LFMM_TREE_AUTO, flags = 0. */
+ * proxies_per_edge = 64, tc_min_level = 0, tree = LFMM_TREE_AUTO, flags = 0, M2L tiling
+ * by the library's rules (m2l_tile = m2l_stages = m2l_split = 0). */
 void lfmm_opts_default(lfmm_opts* opts);
 
 /* Build a plan for fixed source and target locations (Sec. 8.1 precomputation):
@@ -267,10 +278,14 @@ int lfmm_server_wait(lfmm_server* server, int64_t ticket, lfmm_request_stats* st
 int lfmm_server_destroy(lfmm_server* server);
 /* Overload policy.  max_pending > 0 bounds the requests waiting for admission:
  * lfmm_server_submit refuses a request beyond it with LFMM_EBUSY (no ticket is issued).
- * max_queue_ms > 0 is a latency budget for the wait before admission: a request that has
- * waited longer is shed when the server next considers its queue (at every submit and
- * whenever a slot frees) and completes with LFMM_EBUSY; its ticket must still be waited
- * for.  0 disables either limit (the default: every request is eventually served). */
+ * max_queue_ms > 0 is a latency budget for the wait before admission.  At submit, the
+ * server predicts the wait (the run times it has measured for requests of the same path
+ * and size, summed over the queued requests and divided by the slots) and refuses the
+ * request with LFMM_EBUSY when that exceeds the budget; a queued request that has waited
+ * longer than the budget anyway is shed when the server next considers its queue (at
+ * every submit and whenever a slot frees) and completes with LFMM_EBUSY (its ticket must
+ * still be waited for).  0 disables either limit (the default: every request is
+ * eventually served). */
 int lfmm_server_set_limits(lfmm_server* server, int32_t max_pending, double max_queue_ms);
 /* Cancel a request that is still waiting for admission: it leaves the queue and
  * completes with LFMM_ECANCELED (its ticket must still be waited for).  A request that

@@ -228,6 +228,12 @@ int validate_opts(const lfmm_opts& o) {
     if (o.tree != LFMM_TREE_AUTO && o.tree != LFMM_TREE_UNIFORM && o.tree != LFMM_TREE_PRUNED)
         return fail(LFMM_EINVAL, "opts.tree must be LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED");
     if (o.flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL)) return fail(LFMM_EINVAL, "opts.flags has unknown bits");
+    if (o.m2l_tile != 0 && o.m2l_tile != 16 && o.m2l_tile != 32 && o.m2l_tile != 64 && o.m2l_tile != 128)
+        return fail(LFMM_EINVAL, "opts.m2l_tile must be 0, 16, 32, 64 or 128");
+    if (o.m2l_stages != 0 && (o.m2l_stages < 2 || o.m2l_stages > 4))
+        return fail(LFMM_EINVAL, "opts.m2l_stages must be 0, 2, 3 or 4");
+    if (o.m2l_split < 0 || o.m2l_split > 9) return fail(LFMM_EINVAL, "opts.m2l_split must be in [0, 9]");
+    if (o.reserved != 0) return fail(LFMM_EINVAL, "opts.reserved must be 0");
     return LFMM_OK;
 }
 
@@ -299,7 +305,8 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
     {  // partial sums of the list M2L levels split along K (few boxes)
-        const int64_t sb = forest_m2l_split_bytes(F, p->NP, esz, p->num_sms);
+        F.m2l_split = p->opts.m2l_split;
+        const int64_t sb = forest_m2l_split_bytes(F, p->NP, esz, p->num_sms, F.m2l_split);
         if (sb > 0 && (st = palloc(p, &F.m2l_part, (size_t)sb, s))) return st;
     }
     if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
@@ -612,7 +619,8 @@ int far_sweeps(lfmm_plan* p, const FarBufs& b, cudaStream_t s, Hook before_fine)
     if (L >= 2) {
         PhaseTimer pt(LFMM_PHASE_M2L, s);
         int last = 1;
-        if (launch_m2l_fused<T>(ops, L, lb, p->tc_min_level, gsync, p->status, p->num_sms, &last, s) == cudaSuccess) {
+        if (launch_m2l_fused<T>(ops, L, lb, p->tc_min_level, gsync, p->status, p->num_sms, &last, s,
+                                p->opts.m2l_split) == cudaSuccess) {
             pt.add_launches(1);
             l_first = last + 1;
         }
@@ -629,7 +637,8 @@ int far_sweeps(lfmm_plan* p, const FarBufs& b, cudaStream_t s, Hook before_fine)
                 LFMM_CUDA_TRY(launch_m2l_tma(ops, L - l, l, (const float*)Qx(l, 0), Qm(l, 0),
                                              l >= 3 ? (const float*)Ux(l - 1, 0) : nullptr,
                                              l >= 3 ? Cm(l - 1, 0) : nullptr, (float*)Ux(l, 0), Cm(l, 0), b.split,
-                                             p->status, p->num_sms, s, b.nvec, b.vq, b.vQ));
+                                             p->status, p->num_sms, s, b.nvec, b.vq, b.vQ, p->opts.m2l_tile,
+                                             p->opts.m2l_stages));
                 pt.add_launches(2);
                 continue;
             }
@@ -823,9 +832,11 @@ int eval_graph(lfmm_plan* p, const double* f, double* const out[3], cudaStream_t
 int ensure_m2l_part(lfmm_plan* p, int nvec, cudaStream_t s) {
     if (p->forest || p->L < 2 || !p->ops || nvec <= p->m2l_part_nvec) return LFMM_OK;
     const int64_t need =
-        p->opts.precision == LFMM_MIXED ? m2l_fused_split_bytes<float>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec)
-        : p->opts.precision == LFMM_DF  ? m2l_fused_split_bytes<DF>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec)
-                                         : m2l_fused_split_bytes<double>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec);
+        p->opts.precision == LFMM_MIXED
+            ? m2l_fused_split_bytes<float>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec, p->opts.m2l_split)
+        : p->opts.precision == LFMM_DF
+            ? m2l_fused_split_bytes<DF>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec, p->opts.m2l_split)
+            : m2l_fused_split_bytes<double>(*p->ops, p->L, p->tc_min_level, p->num_sms, nvec, p->opts.m2l_split);
     if (need > p->m2l_part_bytes) {
         void* b;
         const int st = palloc(p, &b, (size_t)need, s);

@@ -1839,7 +1839,8 @@ cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, un
 // count so far only when it costs less than 0.9 times that count's cost: a split has to
 // cut the rounds by about 18 % over one chunk.  The rule is kept as measured (float-float
 // uniform_1m evaluation 4.45 -> 4.05 ms with it).
-static int fused_split_chunks(int64_t items, int grid, bool wide) {
+static int fused_split_chunks(int64_t items, int grid, bool wide, int split) {
+    if (split > 0) return std::min(split, 9);  // chosen by the caller (opts.m2l_split)
     if (items <= 0 || grid <= 0) return 1;
     if (!wide) return 2 * items >= grid ? 1 : (int)std::min<int64_t>(9, std::max<int64_t>(2, grid / items));
     int best = 1;
@@ -1855,7 +1856,7 @@ static int fused_split_chunks(int64_t items, int grid, bool wide) {
 }
 
 template <typename T>
-int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level, int num_sms, int nvec) {
+int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level, int num_sms, int nvec, int split) {
     int Ls = 1;
     for (int l = 2; l <= std::min(L, kM2LSplitKMaxLevel); ++l) {
         if (sizeof(T) == 4 && NP == 32 && has_tc && l >= tc_min_level) break;  // m2l_uses_tc
@@ -1873,21 +1874,21 @@ int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level
         constexpr size_t smem = FusedCfg<T, NPc>::SMEM;
         if (ensure_dynamic_smem(fn, smem) != cudaSuccess) return 0;
         const int grid = num_sms * blocks_per_sm(fn, FusedCfg<T, NPc>::WARPS * 32, smem);
-        const int nch = fused_split_chunks(items, grid, sizeof(T) == 8);
+        const int nch = fused_split_chunks(items, grid, sizeof(T) == 8, split);
         return nch > 1 ? (int64_t)nvec * nch * stride * (NPc * (int64_t)sizeof(T) + 8) : 0;
     };
     return NP == 32 ? bytes(std::integral_constant<int, 32>()) : bytes(std::integral_constant<int, 64>());
 }
 
 template <typename T>
-int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec) {
+int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec, int split) {
     const bool has_tc = ops.NP == 32 && !ops.tc.empty() && ops.tc[0] != nullptr;  // all levels or none
-    return m2l_fused_split_bytes_shape<T>(ops.NP, has_tc, L, tc_min_level, num_sms, nvec);
+    return m2l_fused_split_bytes_shape<T>(ops.NP, has_tc, L, tc_min_level, num_sms, nvec, split);
 }
 
 template <typename T>
 cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, int tc_min_level, unsigned* sync,
-                             int* status, int num_sms, int* last_level, cudaStream_t s) {
+                             int* status, int num_sms, int* last_level, cudaStream_t s, int split) {
     *last_level = 1;
     // small levels: 2 .. Ls, the levels the per-level path sends to the split-K kernel
     int Ls = 1;
@@ -1911,7 +1912,7 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
         if (e != cudaSuccess) return e;
         const int grid = num_sms * blocks_per_sm(fn, threads, smem);
         // few tiles for the grid: split the 27 K-steps into chunks (partial sums)
-        const int nch = fused_split_chunks(P.item_off[l1 - l0 + 1], grid, sizeof(T) == 8);
+        const int nch = fused_split_chunks(P.item_off[l1 - l0 + 1], grid, sizeof(T) == 8, split);
         P.nch = 1;
         if (nch > 1) {
             int64_t stride = 0;
@@ -1973,10 +1974,10 @@ cudaError_t launch_combine(int64_t n, const double* un, const double* uf, double
 #define LFMM_INSTANTIATE(T)                                                                                   \
     template cudaError_t launch_m2m_fused<T>(const DeviceOps&, int, const LevelBufs&, unsigned*, int*, int,      \
                                              cudaStream_t);                                                  \
-    template int64_t m2l_fused_split_bytes<T>(const DeviceOps&, int, int, int, int);                          \
-    template int64_t m2l_fused_split_bytes_shape<T>(int, bool, int, int, int, int);                          \
+    template int64_t m2l_fused_split_bytes<T>(const DeviceOps&, int, int, int, int, int);                     \
+    template int64_t m2l_fused_split_bytes_shape<T>(int, bool, int, int, int, int, int);                     \
     template cudaError_t launch_m2l_fused<T>(const DeviceOps&, int, const LevelBufs&, int, unsigned*, int*, int, \
-                                             int*, cudaStream_t);                                            \
+                                             int*, cudaStream_t, int);                                       \
     template cudaError_t launch_l2p<T>(const TreeView&, const DeviceOps&, const T*, const void*, double*,          \
                                        cudaStream_t, int, int64_t, int64_t);                                  \
     template cudaError_t launch_p2m<T>(const TreeView&, const DeviceOps&, const double*, T*, T*, void*,       \

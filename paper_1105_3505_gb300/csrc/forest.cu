@@ -1005,18 +1005,19 @@ void Forest::release(cudaStream_t s) {
     levels.clear();
 }
 
-int m2l_list_chunks(int64_t maxc, int num_sms) {
+int m2l_list_chunks(int64_t maxc, int num_sms, int split) {
+    if (split > 0) return std::min(split, 7);  // chosen by the caller (opts.m2l_split)
     const int64_t blocks = 4 * ((maxc + 31) / 32);
     if (blocks == 0 || blocks >= 3 * (int64_t)num_sms) return 1;
     return (int)std::min<int64_t>(7, (3 * (int64_t)num_sms + blocks - 1) / blocks);
 }
 
-int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms) {
+int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms, int split) {
     int64_t need = 0;
     for (const ForestLevel& lv : F.levels) {
         int64_t maxc = 0;
         for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
-        const int nc = m2l_list_chunks(maxc, num_sms);
+        const int nc = m2l_list_chunks(maxc, num_sms, split);
         if (nc > 1) need = std::max<int64_t>(need, (int64_t)nc * lv.nb * ((int64_t)NP * (int64_t)esz + 8));
     }
     return need;
@@ -1393,7 +1394,7 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             int64_t maxc = 0;
             for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
             if (maxc == 0) continue;
-            const int nc = F.m2l_part ? m2l_list_chunks(maxc, num_sms) : 1;
+            const int nc = F.m2l_part ? m2l_list_chunks(maxc, num_sms, F.m2l_split) : 1;
             dim3 grid((unsigned)((maxc + 31) / 32), 4, (unsigned)nc);
             T* part = nc > 1 ? (T*)F.m2l_part : nullptr;
             V* cpart = nc > 1 ? (V*)(part + (size_t)nc * lv.nb * NP) : nullptr;

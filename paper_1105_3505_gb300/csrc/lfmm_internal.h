@@ -279,14 +279,15 @@ struct Forest {
     std::vector<void*> owned;
     int64_t bytes = 0;
     void* m2l_part = nullptr;               // partial sums of K-split list M2L levels (plan-owned)
+    int m2l_split = 0;                      // opts.m2l_split (0: chunks by the number of tiles)
     void release(cudaStream_t s);
 };
 
 // K chunks of the list M2L of a level whose largest parity class has maxc boxes: more
 // than one (up to 7) while its 32-box tiles are fewer than three per SM.
-int m2l_list_chunks(int64_t maxc, int num_sms);
+int m2l_list_chunks(int64_t maxc, int num_sms, int split = 0);
 // Bytes of partial sums the K-split list M2L levels of F need (0: none split).
-int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms);
+int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms, int split = 0);
 
 // Builds the tree of every problem (offsets: n_problems + 1 entries, host memory).
 // Leaf side: the largest power of two <= max_leaf_side at which no leaf holds more than
@@ -368,11 +369,12 @@ struct LevelBufs {
 // Bytes of partial sums launch_m2l_fused needs for nvec charge vectors (0: no K split;
 // the split depends on the plan, not on nvec, so one and several vectors sum alike).
 template <typename T>
-int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec);
+int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec, int split = 0);
 // The same from the plan's shape alone (has_tc: the mixed path's tensor-core tiles exist,
 // i.e. binary32 with NP = 32), for footprints computed before any operator is uploaded.
 template <typename T>
-int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level, int num_sms, int nvec);
+int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level, int num_sms, int nvec,
+                                    int split = 0);
 // M2M of levels L-1 .. 2 in one cooperative launch (grid barriers between levels).
 // sync: two zero device words (barrier state).  Returns an error (nothing launched)
 // when a cooperative launch is not possible; the caller then runs the per-level path.
@@ -383,7 +385,7 @@ cudaError_t launch_m2m_fused(const DeviceOps& ops, int L, const LevelBufs& b, un
 // split-K kernel) in one cooperative launch; the caller continues at *last_level + 1.
 template <typename T>
 cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, int tc_min_level, unsigned* sync,
-                             int* status, int num_sms, int* last_level, cudaStream_t s);
+                             int* status, int num_sms, int* last_level, cudaStream_t s, int split = 0);
 
 // First tree level whose M2L runs on the tensor cores when opts.tc_min_level is 0
 // (levels of 4^7 boxes and more; below that the fused SIMT kernel wins).
@@ -406,7 +408,8 @@ cudaError_t launch_m2l(const DeviceOps& ops, int k, int level, const T* q_level,
 // value pairs (Q, C) after vector 0's; `split` then holds nvec times the rows.
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
-                           int* status, int num_sms, cudaStream_t s, int nvec = 1, int64_t vq = 0, int64_t vQ = 0);
+                           int* status, int num_sms, cudaStream_t s, int nvec = 1, int64_t vq = 0, int64_t vQ = 0,
+                           int tile = 0, int stages = 0);
 // Near field of k charge vectors (vector r: f_sorted + r f_stride, Qleaf + r q_stride,
 // out u_near + r u_stride), four vectors per pass sharing each table lookup.
 template <typename T>

@@ -192,7 +192,7 @@ __device__ __forceinline__ DFv dmul(DFv a, DFv b) {
 //     loads and float-pair arithmetic, independent of the pipeline).
 // Every wait is bounded; on expiry the CTA records LFMM_ETIMEOUT, every role stops at
 // its next iteration, and the teardown waits (bounded) for the copies and MMAs issued.
-constexpr int kTmaStages = 3;
+constexpr int kTmaStagesDefault = 3;  // ring depth unless opts.m2l_stages says otherwise
 constexpr int kTmaAcc = 4;
 constexpr int kTmaThreads = 224;
 constexpr int kTmaCols = 256;  // buffer b: D_big at columns [64b, 64b+32), D_small at [64b+32, 64b+64)
@@ -228,6 +228,7 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+template <int kTmaStages>
 __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_u, const TmaGeo g,
     const float* __restrict__ tiles, const float* __restrict__ mono, const DFv* __restrict__ Qin,
@@ -565,7 +566,8 @@ bool encode_map(CUtensorMap* m, const float* base, int rank, const uint64_t* dim
 
 cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* q_level, const void* Q_level,
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
-                           int* status, int num_sms, cudaStream_t s, int nvec, int64_t vq, int64_t vQ) {
+                           int* status, int num_sms, cudaStream_t s, int nvec, int64_t vq, int64_t vQ, int tile,
+                           int stages) {
     const int lg = level - 1;
     const int np = 1 << lg;
     const bool l2l = u_parent != nullptr;
@@ -589,7 +591,8 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     TmaGeo g;
     g.level = level;
     g.lg = lg;
-    g.TX = std::min(np, 128);
+    // tiles of 128 boxes of one parity class, tile boxes wide (opts.m2l_tile; 0: 128)
+    g.TX = std::min(np, tile > 0 ? tile : 128);
     g.TY = std::min(128 / g.TX, np);
     g.tiles_x = np / g.TX;
     g.tiles_per_class = g.tiles_x * (np / g.TY);
@@ -603,15 +606,21 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     const uint64_t du[4] = {32, (uint64_t)np, (uint64_t)np, (uint64_t)(2 * nvec)};
     if (!encode_map(&mq, qs, 5, dq, g.TX, g.TY)) return cudaErrorInvalidValue;
     if (!encode_map(&mu, l2l ? us : qs, 4, du, g.TX, g.TY)) return cudaErrorInvalidValue;
-    constexpr size_t smem = 1024 + (size_t)kTmaStages * kTmaStageBytes;
-    {
-        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tma_kernel, smem);
-        if (e != cudaSuccess) return e;
-    }
     const int grid = std::min(g.n_tiles * nvec, num_sms);
-    return launch_dependent(m2l_tma_kernel, dim3(grid), dim3(kTmaThreads), smem, s, mq, mu, g,
-                            (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
-                            (const DFv*)C_parent, u_level, (DFv*)C_level, status);
+    auto go = [&](auto stages_tag) -> cudaError_t {
+        constexpr int S = decltype(stages_tag)::value;
+        constexpr size_t smem = 1024 + (size_t)S * kTmaStageBytes;
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tma_kernel<S>, smem);
+        if (e != cudaSuccess) return e;
+        return launch_dependent(m2l_tma_kernel<S>, dim3(grid), dim3(kTmaThreads), smem, s, mq, mu, g,
+                                (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
+                                (const DFv*)C_parent, u_level, (DFv*)C_level, status);
+    };
+    switch (stages > 0 ? stages : kTmaStagesDefault) {
+        case 2: return go(std::integral_constant<int, 2>());
+        case 4: return go(std::integral_constant<int, 4>());
+        default: return go(std::integral_constant<int, 3>());
+    }
 }
 
 }  // namespace lfmm

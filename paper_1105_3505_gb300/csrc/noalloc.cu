@@ -166,9 +166,9 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     LFMM_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
     const bool has_tc = o.precision == LFMM_MIXED && NP == 32;
     const int64_t part = L < 2 ? 0
-                         : o.precision == LFMM_MIXED ? m2l_fused_split_bytes_shape<float>(NP, has_tc, L, tc_min, num_sms, 1)
-                         : o.precision == LFMM_DF    ? m2l_fused_split_bytes_shape<DF>(NP, has_tc, L, tc_min, num_sms, 1)
-                                                     : m2l_fused_split_bytes_shape<double>(NP, has_tc, L, tc_min, num_sms, 1);
+                         : o.precision == LFMM_MIXED ? m2l_fused_split_bytes_shape<float>(NP, has_tc, L, tc_min, num_sms, 1, o.m2l_split)
+                         : o.precision == LFMM_DF    ? m2l_fused_split_bytes_shape<DF>(NP, has_tc, L, tc_min, num_sms, 1, o.m2l_split)
+                                                     : m2l_fused_split_bytes_shape<double>(NP, has_tc, L, tc_min, num_sms, 1, o.m2l_split);
     const int64_t bytes = a(2 * (n_leaves + 1) * 4) + a((2 * (n_src + n_tgt) + n_tgt) * 4) + a(n_src * esz) + split +
                           un_tmp + part +
                           2 * a(boxes * NP * esz) + 2 * a(boxes * 8) + 16 /* status word */;

@@ -10,7 +10,13 @@
 // stay resident; plan workspaces come from the stream-ordered pool, which keeps freed
 // memory for reuse.  A request's result does not depend on what runs beside it: each
 // request owns its plan, stream and buffers.
+//
+// Overload policy (lfmm_server_set_limits): a bounded queue, a refusal at submit when the
+// predicted wait (the smoothed run times of the requests queued ahead, by class and size,
+// over the slots) exceeds the latency budget, and shedding of requests that waited past
+// it anyway; cancellation removes a queued request.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <algorithm>
@@ -38,6 +44,7 @@ struct Job {
     lfmm_opts opts{};
     int cls = 0;  // 0: mixed path, 1: binary64 path
     int64_t est = 0;
+    double est_ms = 0.0;  // predicted run time (overload policy)
     Clock::time_point t_submit, t_admit, t_done;
     lfmm_request_stats stats{};
     bool done = false;
@@ -70,7 +77,31 @@ struct lfmm_server {
     int max_cls[2] = {0, 0};  // binary64 requests leave slots to the mixed ones
     int max_pending = 0;      // overload policy (lfmm_server_set_limits); 0: no limit
     double max_queue_ms = 0.0;
+    // measured run times per class and size bucket (log2 of the point count), smoothed;
+    // the predicted work queued ahead of a new request is their sum over `pending`
+    double run_ms_fit[2][40] = {};
+    double pending_ms = 0.0;
     bool stopping = false;
+
+    static int size_bucket(const Job& j) {
+        int b = 0;
+        while (b < 39 && ((int64_t)2 << b) <= j.req.n_src + j.req.n_tgt) ++b;
+        return b;
+    }
+    // predicted run time of a request from the nearest measured bucket of its class,
+    // scaled by the point count; 0 while nothing is measured
+    double predict_ms(const Job& j) const {
+        const int b = size_bucket(j);
+        for (int d = 0; d < 40; ++d)
+            for (int bb : {b - d, b + d})
+                if (bb >= 0 && bb < 40 && run_ms_fit[j.cls][bb] > 0.0)
+                    return run_ms_fit[j.cls][bb] * std::max(0.25, std::min(4.0, std::ldexp(1.0, b - bb)));
+        return 0.0;
+    }
+    void learn(const Job& j, double run_ms) {
+        double& m = run_ms_fit[j.cls][size_bucket(j)];
+        m = m > 0.0 ? 0.8 * m + 0.2 * run_ms : run_ms;
+    }
     std::vector<std::thread> workers;
 
     // free device memory plus what the default pool holds but does not use
@@ -125,6 +156,7 @@ struct lfmm_server {
             Job& j = jobs[pending[i]];
             if (ms_between(j.t_submit, now) > max_queue_ms) {
                 finish_unrun(j, LFMM_EBUSY, now);
+                pending_ms -= j.est_ms;
                 pending.erase(pending.begin() + (std::ptrdiff_t)i);
                 any = true;
             } else {
@@ -174,6 +206,7 @@ struct lfmm_server {
                 ticket = pending[at];
                 pending.erase(pending.begin() + at);
                 job = &jobs[ticket];
+                pending_ms -= job->est_ms;
                 job->t_admit = Clock::now();
                 in_flight += job->est;
                 ++running;
@@ -186,6 +219,7 @@ struct lfmm_server {
                 in_flight -= job->est;
                 --running;
                 --running_cls[job->cls];
+                if (st == LFMM_OK) learn(*job, ms_between(job->t_admit, job->t_done));
                 job->stats.status = st;
                 job->stats.precision = job->opts.precision;
                 job->stats.queue_ms = ms_between(job->t_submit, job->t_admit);
@@ -279,9 +313,17 @@ int lfmm_server_submit(lfmm_server* sv, const lfmm_request* req, int64_t* ticket
             return lfmm::fail(LFMM_EBUSY, "server queue full (" + std::to_string(sv->pending.size()) +
                                               " requests waiting for admission)");
         }
+        j.est_ms = sv->predict_ms(j);
+        const double wait_ms = sv->pending_ms / sv->n_slots;
+        if (sv->max_queue_ms > 0.0 && wait_ms > sv->max_queue_ms) {
+            if (shed) sv->cv_done.notify_all();
+            return lfmm::fail(LFMM_EBUSY, "predicted wait " + std::to_string(wait_ms) +
+                                              " ms exceeds the server's latency budget");
+        }
         *ticket = sv->next_ticket++;
         sv->jobs.emplace(*ticket, j);
         sv->pending.push_back(*ticket);
+        sv->pending_ms += j.est_ms;
     }
     if (shed) sv->cv_done.notify_all();
     sv->cv_work.notify_all();
@@ -309,6 +351,7 @@ int lfmm_server_cancel(lfmm_server* sv, int64_t ticket) {
             return lfmm::fail(LFMM_EINVAL, sv->jobs.count(ticket) ? "request already admitted or finished"
                                                                    : "unknown ticket");
         sv->finish_unrun(sv->jobs[ticket], LFMM_ECANCELED, Clock::now());
+        sv->pending_ms -= sv->jobs[ticket].est_ms;
         sv->pending.erase(it);
     }
     sv->cv_done.notify_all();

@@ -29,6 +29,7 @@ struct Key {
 struct Entry {
     int p, leaf_size, tc_min_level;
     double rel_err, ms;
+    int m2l_tile = 0, m2l_stages = 0, m2l_split = 0;
 };
 
 std::mutex g_mu;
@@ -150,6 +151,9 @@ int lfmm_autotune(const int32_t* src_xy, int64_t n_src, const int64_t* src_offse
             result->opts.p = it->second.p;
             result->opts.leaf_size = it->second.leaf_size;
             result->opts.tc_min_level = it->second.tc_min_level;
+            result->opts.m2l_tile = it->second.m2l_tile;
+            result->opts.m2l_stages = it->second.m2l_stages;
+            result->opts.m2l_split = it->second.m2l_split;
             result->rel_err = it->second.rel_err;
             result->ms = it->second.ms;
             result->from_cache = 1;
@@ -255,6 +259,41 @@ int lfmm_autotune(const int32_t* src_xy, int64_t n_src, const int64_t* src_offse
             }
         }
     }
+    // 5. M2L tiling: the tensor-core tile width and TMA ring depth (mixed, single problem,
+    // when tensor-core levels are in use), then the K-split of the coarse-level / list
+    // M2L kernels; each candidate must still meet the tolerance
+    auto try_opts = [&](const lfmm_opts& c) {
+        double ms = 0.0;
+        if (measure(pr, c, b, 3, u, &ms) != LFMM_OK) return;
+        ++candidates;
+        const double e = rel_err(u, ref);
+        if (e > goal) return;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_err = e;
+            pick = c;
+        }
+    };
+    if (mixed && !src_offsets && pick.tc_min_level != 99) {
+        for (int tile : {64, 32, 16}) {
+            lfmm_opts c = pick;
+            c.m2l_tile = tile;
+            try_opts(c);
+        }
+        for (int stages : {2, 4}) {
+            lfmm_opts c = pick;
+            c.m2l_stages = stages;
+            try_opts(c);
+        }
+    }
+    {
+        const lfmm_opts base_pick = pick;
+        for (int split : {1, 2, 4, 8}) {
+            lfmm_opts c = base_pick;
+            c.m2l_split = split;
+            try_opts(c);
+        }
+    }
     if (base) pick.flags = base->flags;
     result->opts = pick;
     result->rel_err = best_err;
@@ -262,7 +301,8 @@ int lfmm_autotune(const int32_t* src_xy, int64_t n_src, const int64_t* src_offse
     result->candidates = candidates;
     result->from_cache = 0;
     std::lock_guard<std::mutex> g(g_mu);
-    g_cache[key] = Entry{pick.p, pick.leaf_size, pick.tc_min_level, best_err, best_ms};
+    g_cache[key] = Entry{pick.p, pick.leaf_size, pick.tc_min_level, best_err, best_ms, pick.m2l_tile, pick.m2l_stages,
+                         pick.m2l_split};
     return LFMM_OK;
 }
 
@@ -280,8 +320,9 @@ int lfmm_tune_cache_save(const char* path) {
     for (const auto& kv : g_cache) {
         const Key& k = kv.first;
         const Entry& e = kv.second;
-        std::fprintf(fp, "lfmm-tune-1 %d %d %d %d %d %d %d %d %d %.6e %.6e\n", k.precision, k.tol_dec, k.ls, k.lt,
-                     k.lp, k.tree, e.p, e.leaf_size, e.tc_min_level, e.rel_err, e.ms);
+        std::fprintf(fp, "lfmm-tune-2 %d %d %d %d %d %d %d %d %d %.6e %.6e %d %d %d\n", k.precision, k.tol_dec, k.ls,
+                     k.lt, k.lp, k.tree, e.p, e.leaf_size, e.tc_min_level, e.rel_err, e.ms, e.m2l_tile, e.m2l_stages,
+                     e.m2l_split);
     }
     const bool ok = std::fclose(fp) == 0;
     return ok ? LFMM_OK : fail(LFMM_EINVAL, std::string("write failed: ") + path);
@@ -299,11 +340,17 @@ int lfmm_tune_cache_load(const char* path) {
         Key k;
         Entry e;
         char tag[32];
-        if (std::sscanf(line, "%31s %d %d %d %d %d %d %d %d %d %lf %lf", tag, &k.precision, &k.tol_dec, &k.ls, &k.lt,
-                        &k.lp, &k.tree, &e.p, &e.leaf_size, &e.tc_min_level, &e.rel_err, &e.ms) != 12 ||
-            std::strcmp(tag, "lfmm-tune-1") != 0 ||
-            (k.precision != LFMM_MIXED && k.precision != LFMM_DF && k.precision != LFMM_FP64) || e.p < 2 ||
-            e.p > 17 || e.leaf_size < 1 || e.tc_min_level < 0) {
+        // version 1 lines carry no M2L tiling (the library's rules)
+        const int got = std::sscanf(line, "%31s %d %d %d %d %d %d %d %d %d %lf %lf %d %d %d", tag, &k.precision,
+                                    &k.tol_dec, &k.ls, &k.lt, &k.lp, &k.tree, &e.p, &e.leaf_size, &e.tc_min_level,
+                                    &e.rel_err, &e.ms, &e.m2l_tile, &e.m2l_stages, &e.m2l_split);
+        const bool v1 = got == 12 && std::strcmp(tag, "lfmm-tune-1") == 0;
+        const bool v2 = got == 15 && std::strcmp(tag, "lfmm-tune-2") == 0;
+        if (v1) e.m2l_tile = e.m2l_stages = e.m2l_split = 0;
+        if ((!v1 && !v2) || (k.precision != LFMM_MIXED && k.precision != LFMM_DF && k.precision != LFMM_FP64) ||
+            e.p < 2 || e.p > 17 || e.leaf_size < 1 || e.tc_min_level < 0 ||
+            (e.m2l_tile != 0 && e.m2l_tile != 16 && e.m2l_tile != 32 && e.m2l_tile != 64 && e.m2l_tile != 128) ||
+            (e.m2l_stages != 0 && (e.m2l_stages < 2 || e.m2l_stages > 4)) || e.m2l_split < 0 || e.m2l_split > 9) {
             st = fail(LFMM_EINVAL, std::string("malformed tuning line ") + std::to_string(n) + " in " + path);
             break;
         }

@@ -33,7 +33,9 @@ class LfmmError(RuntimeError):
 class lfmm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("p", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
                 ("max_leaf_side", ctypes.c_int32), ("proxies_per_edge", ctypes.c_int32),
-                ("tc_min_level", ctypes.c_int32), ("tree", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("tc_min_level", ctypes.c_int32), ("tree", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("m2l_tile", ctypes.c_int32), ("m2l_stages", ctypes.c_int32), ("m2l_split", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class lfmm_plan_info(ctypes.Structure):
@@ -158,12 +160,14 @@ def lfmm_opts_default() -> lfmm_opts:
 
 def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
               proxies_per_edge: int = 64, tc_min_level: int = 0, tree: int = LFMM_TREE_AUTO,
-              graph: bool = False, serial: bool = False) -> lfmm_opts:
+              graph: bool = False, serial: bool = False, m2l_tile: int = 0, m2l_stages: int = 0,
+              m2l_split: int = 0) -> lfmm_opts:
     o = lfmm_opts_default()
     o.precision, o.p, o.leaf_size = precision, p, leaf_size
     o.max_leaf_side, o.proxies_per_edge, o.tc_min_level = max_leaf_side, proxies_per_edge, tc_min_level
     o.tree = tree
     o.flags = (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0)
+    o.m2l_tile, o.m2l_stages, o.m2l_split = m2l_tile, m2l_stages, m2l_split
     return o
 
 
@@ -346,7 +350,9 @@ def autotune(src, tgt, tol: float, src_offsets=None, tgt_offsets=None, base: lfm
     _check(st, "lfmm_autotune")
     return r.opts, {"rel_err": r.rel_err, "ms": r.ms, "candidates": int(r.candidates),
                     "from_cache": bool(r.from_cache), "p": int(r.opts.p), "leaf_size": int(r.opts.leaf_size),
-                    "tc_min_level": int(r.opts.tc_min_level), "precision": int(r.opts.precision)}
+                    "tc_min_level": int(r.opts.tc_min_level), "precision": int(r.opts.precision),
+                    "m2l_tile": int(r.opts.m2l_tile), "m2l_stages": int(r.opts.m2l_stages),
+                    "m2l_split": int(r.opts.m2l_split)}
 
 
 def tune_cache_clear() -> None:

@@ -41,7 +41,8 @@ def test_status_strings_and_defaults(lib):
     o = lfmm.lfmm_opts_default()
     assert (o.precision, o.p, o.leaf_size, o.max_leaf_side, o.proxies_per_edge, o.tc_min_level) == \
         (lfmm.LFMM_MIXED, 8, 64, 32, 64, 0)
-    assert ctypes.sizeof(lfmm.lfmm_opts) == 32
+    assert (o.m2l_tile, o.m2l_stages, o.m2l_split, o.reserved) == (0, 0, 0, 0)
+    assert ctypes.sizeof(lfmm.lfmm_opts) == 48
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):
@@ -98,17 +99,27 @@ def test_autotune_arguments_validated_without_gpu(lib):
 def test_tune_cache_roundtrip_without_gpu(lib, tmp_path):
     lfmm.tune_cache_clear()
     good = tmp_path / "tune.txt"
-    good.write_text("lfmm-tune-1 1 -6 20 20 0 0 7 64 7 2.500000e-07 4.100000e-01\n"
-                    "lfmm-tune-1 2 -10 17 15 0 0 14 128 0 3.000000e-12 2.000000e+00\n")
+    good.write_text("lfmm-tune-2 1 -6 20 20 0 0 7 64 7 2.500000e-07 4.100000e-01 32 4 0\n"
+                    "lfmm-tune-2 2 -10 17 15 0 0 14 128 0 3.000000e-12 2.000000e+00 0 0 3\n")
     lfmm.tune_cache_load(str(good))
     out = tmp_path / "out.txt"
     lfmm.tune_cache_save(str(out))
     lines = sorted(out.read_text().splitlines())
     assert lines == sorted(good.read_text().splitlines())
-    bad = tmp_path / "bad.txt"
-    bad.write_text("lfmm-tune-1 1 -6 20 20 0 0 99 64 7 1e-7 1.0\n")  # p out of range
-    with pytest.raises(lfmm.LfmmError, match="line 1"):
-        lfmm.tune_cache_load(str(bad))
+    # a version-1 line (no M2L tiling) loads with the library's tiling rules
+    old = tmp_path / "old.txt"
+    old.write_text("lfmm-tune-1 1 -6 22 22 0 0 8 64 7 2.500000e-07 4.100000e-01\n")
+    lfmm.tune_cache_clear()
+    lfmm.tune_cache_load(str(old))
+    lfmm.tune_cache_save(str(out))
+    assert out.read_text().split() == "lfmm-tune-2 1 -6 22 22 0 0 8 64 7 2.500000e-07 4.100000e-01 0 0 0".split()
+    for line in ["lfmm-tune-1 1 -6 20 20 0 0 99 64 7 1e-7 1.0\n",  # p out of range
+                 "lfmm-tune-2 1 -6 20 20 0 0 7 64 7 1e-7 1.0 48 0 0\n",  # tile width not allowed
+                 "lfmm-tune-2 1 -6 20 20 0 0 7 64 7 1e-7 1.0 0 5 0\n"]:  # ring depth out of range
+        bad = tmp_path / "bad.txt"
+        bad.write_text(line)
+        with pytest.raises(lfmm.LfmmError, match="line 1"):
+            lfmm.tune_cache_load(str(bad))
     lfmm.tune_cache_clear()
     lfmm.tune_cache_save(str(out))
     assert out.read_text() == ""
