@@ -952,6 +952,13 @@ def main():
         # smallest p that meets it on the sampled targets, at its best leaf size
         out["fp64_at_1e-6"] = fp64_equal_accuracy(lfmm, timed, s_d, t_d, f_d, u_d, idx, ref, ns, nt, value,
                                                   max(3, args.steps // 4))
+        # the mixed path at the configuration's second order, p = 16 (P_pad = 64)
+        o16 = lfmm.make_opts(lfmm.LFMM_MIXED, 16, 64, 32, 64)
+        ms16, _ = timed(s_d, t_d, f_d, u_d, o16, max(3, args.steps // 4), 1, sync_ranks=False)
+        u16 = u_d.cpu().numpy()
+        out["mixed_p16"] = {"value": (ns + nt) / (ms16 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms16,
+                            "rel_err": float(np.abs(u16[idx] - ref).max() / scale), "leaf_size": 64,
+                            "note": "plan create + eval, inputs resident, L2 flushed"}
         # plan creation with the operator cache cold (a proxies_per_edge not used before
         # gives a new cache key: skeletons, operators and their device images are built)
         out["cold_plan_create_ms"] = cold_plan_create(lfmm, s_d, t_d, ns, nt, stream, args.p)

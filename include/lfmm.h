@@ -72,8 +72,8 @@ typedef struct lfmm_opts {
     int32_t max_leaf_side;    /* largest leaf side in lattice cells, a power of 2 in [1, 32]   */
     int32_t proxies_per_edge; /* proxy points per edge of the proxy ring of Sec. 5 (>= 8);     */
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
-    int32_t tc_min_level;     /* mixed path, P <= 32: tree levels >= this run M2L on the      */
-                              /* tensor cores (0 = default 7; a value > 30 disables them)     */
+    int32_t tc_min_level;     /* mixed path: tree levels >= this run M2L on the tensor cores  */
+                              /* (0 = default 7; a value > 30 disables them)                  */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
     int32_t flags;            /* bitwise OR of LFMM_FLAG_* (0: none)                           */
     /* M2L tiling (0 everywhere: the library's rules; lfmm_autotune picks these).  They    */

@@ -515,7 +515,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         boxes += (int64_t)1 << (2 * l);
     }
     p->n_boxes = boxes;
-    if (p->opts.precision == LFMM_MIXED && p->NP == 32 && p->L >= (p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level)) {
+    if (p->opts.precision == LFMM_MIXED && p->L >= (p->opts.tc_min_level == 0 ? kDefaultTcMinLevel : p->opts.tc_min_level)) {
         // largest tensor-core level: TF32 hi/lo of its q_hat and of its parent's u_hat
         const size_t n = ((size_t)p->NP << (2 * p->L)) * 2 + ((size_t)p->NP << (2 * std::max(0, p->L - 1))) * 2;
         if ((st = palloc(p, &p->tc_split, n * sizeof(float), s))) return st;

@@ -1859,7 +1859,7 @@ template <typename T>
 int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level, int num_sms, int nvec, int split) {
     int Ls = 1;
     for (int l = 2; l <= std::min(L, kM2LSplitKMaxLevel); ++l) {
-        if (sizeof(T) == 4 && NP == 32 && has_tc && l >= tc_min_level) break;  // m2l_uses_tc
+        if (sizeof(T) == 4 && has_tc && l >= tc_min_level) break;  // m2l_uses_tc
         Ls = l;
     }
     if (Ls < 2 || L >= kMaxLevels) return 0;
@@ -1882,7 +1882,7 @@ int64_t m2l_fused_split_bytes_shape(int NP, bool has_tc, int L, int tc_min_level
 
 template <typename T>
 int64_t m2l_fused_split_bytes(const DeviceOps& ops, int L, int tc_min_level, int num_sms, int nvec, int split) {
-    const bool has_tc = ops.NP == 32 && !ops.tc.empty() && ops.tc[0] != nullptr;  // all levels or none
+    const bool has_tc = !ops.tc.empty() && ops.tc[0] != nullptr;  // all levels or none
     return m2l_fused_split_bytes_shape<T>(ops.NP, has_tc, L, tc_min_level, num_sms, nvec, split);
 }
 

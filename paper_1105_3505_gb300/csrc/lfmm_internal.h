@@ -393,7 +393,8 @@ constexpr int kDefaultTcMinLevel = 7;
 // Whether level `level` (k levels above the leaves) runs M2L + L2L on the tensor cores:
 // fp32 arithmetic, P <= 32, tiles present, level >= tc_min_level.
 inline bool m2l_uses_tc(const DeviceOps& ops, int k, int level, int tc_min_level, bool fp32) {
-    return fp32 && ops.NP == 32 && ops.tc.size() > (size_t)k && ops.tc[k] != nullptr && level >= tc_min_level;
+    return fp32 && (ops.NP == 32 || ops.NP == 64) && ops.tc.size() > (size_t)k && ops.tc[k] != nullptr &&
+           level >= tc_min_level;
 }
 // M2L + L2L of one level; mixed-path levels >= tc_min_level (P <= 32) run on the
 // tensor cores, which report a timed-out wait in *status.

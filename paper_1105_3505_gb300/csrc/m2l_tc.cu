@@ -171,23 +171,28 @@ __device__ __forceinline__ DFv dmul(DFv a, DFv b) {
 
 // ---------------------------------------------------------------------------------
 // TMA form.  The level's expansions are split into TF32 hi / lo once and stored by
-// parity plane, Q5[hl][py'][px'][y'][x'][32] with box (x, y) = (2x' + px', 2y' + py'):
+// parity plane, Q5[hl][py'][px'][y'][x'][NP] with box (x, y) = (2x' + px', 2y' + py'):
 // for a target tile of one parity class, the sources at one interaction offset are then
 // a rectangle of one plane, so a single tiled TMA load (5-D tensor map, 128-byte
-// swizzle, zero fill outside the level) writes the A operand of a K-step directly in
+// swizzle, zero fill outside the level) writes the A operand of a K-block directly in
 // the layout the tensor core reads.  The parent level's incoming expansions are stored
 // row-major (4-D map) and their window is the tile itself.
 //
+// A K-block is 32 expansion coefficients (one 128-byte swizzled row per box): NP = 32
+// takes one K-block per interaction offset, NP = 64 two, accumulated into the same
+// fresh accumulator of that offset.
+//
 // Persistent CTAs (one per SM) walk the tiles with a continuous pipeline:
-//   warp 4 (one thread): producer - for every K-step of every tile, wait until the
-//     stage is free, then two TMA loads (A hi, A lo) and one bulk copy (B hi + lo)
-//     completing on the stage's "full" mbarrier;
-//   warp 5 (one thread): MMA issuer - wait "full", wait until the accumulator buffer
-//     is folded, issue the 12 MMAs of the step, commit to the stage's "empty" barrier
-//     (frees the shared memory) and to the buffer's "acc_full" barrier;
-//   warps 0-3: one target box per thread (TMEM lane) - fold every step's fresh
+//   warp 4 (one thread): producer - for every K-block of every offset of every tile,
+//     wait until the stage is free, then two TMA loads (A hi, A lo) and one bulk copy
+//     (B hi + lo) completing on the stage's "full" mbarrier;
+//   warp 5 (one thread): MMA issuer - wait "full" (and, at an offset's first K-block,
+//     until the accumulator buffer is folded), issue the block's 8 MMAs, commit to the
+//     stage's "empty" barrier (frees the shared memory) and, at the offset's last
+//     K-block, to the buffer's "acc_full" barrier;
+//   warps 0-3: one target box per thread (TMEM lane) - fold every offset's fresh
 //     accumulators into round-to-nearest fp32 registers, arrive on "acc_empty"; at a
-//     tile's last step write the row of u_hat;
+//     tile's last offset write the row of u_hat;
 //   warp 6: the compensated incoming constant of every box of the CTA's tiles (plain
 //     loads and float-pair arithmetic, independent of the pipeline).
 // Every wait is bounded; on expiry the CTA records LFMM_ETIMEOUT, every role stops at
@@ -195,9 +200,16 @@ __device__ __forceinline__ DFv dmul(DFv a, DFv b) {
 constexpr int kTmaStagesDefault = 3;  // ring depth unless opts.m2l_stages says otherwise
 constexpr int kTmaAcc = 4;
 constexpr int kTmaThreads = 224;
-constexpr int kTmaCols = 256;  // buffer b: D_big at columns [64b, 64b+32), D_small at [64b+32, 64b+64)
-constexpr uint32_t kTmaABytes = 128 * 32 * 4;
-constexpr uint32_t kTmaStageBytes = 2 * kTmaABytes + 8192;
+constexpr uint32_t kTmaABytes = 128 * 32 * 4;  // one A K-block (hi or lo): 128 rows x 128 B
+
+template <int NP>
+struct TmaCfg {
+    static constexpr int KB = NP / 32;                          // K-blocks per interaction offset
+    static constexpr uint32_t BBytes = 2u * NP * 128u;          // B K-block: [B_hi | B_lo], 2 NP rows x 128 B
+    static constexpr uint32_t StageBytes = 2 * kTmaABytes + BBytes;
+    static constexpr int AccCols = 2 * NP;                      // buffer: D_big [0, 2NP), D_small [NP, 2NP)
+    static constexpr int Cols = kTmaAcc * AccCols;              // TMEM columns (256 or 512)
+};
 
 struct TmaGeo {
     int level;            // tree level of the targets
@@ -211,47 +223,49 @@ struct TmaGeo {
     long long vq, vQ;     // constants at v vQ pairs; its split layouts at TMA index 2v + hl
 };
 
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3, int c4,
-                                            uint64_t* bar) {
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
         "%5, %6}], [%7];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3,
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
         "%5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
 
-template <int kTmaStages>
+template <int NP, int kTmaStages>
 __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_u, const TmaGeo g,
     const float* __restrict__ tiles, const float* __restrict__ mono, const DFv* __restrict__ Qin,
     const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout, int* __restrict__ status) {
     griddep_wait();
-    constexpr int NP = 32;
+    using Cfg = TmaCfg<NP>;
+    constexpr int KB = Cfg::KB;
+    constexpr uint32_t kStageBytes = Cfg::StageBytes;
     extern __shared__ __align__(1024) unsigned char tma_smem[];
-    // stage i: A hi, A lo (128 rows x 128 B each, 128-byte swizzled), B hi + lo (8 KB)
+    // stage i: A hi, A lo (128 rows x 128 B each, 128-byte swizzled), B hi + lo (2 NP rows x 128 B)
     const uint32_t base = smem_u32(tma_smem) + ((1024u - (smem_u32(tma_smem) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[kTmaStages], empty[kTmaStages], acc_full[kTmaAcc], acc_empty[kTmaAcc];
     __shared__ uint32_t s_tmem;
     __shared__ int s_off[4][27][3];
     __shared__ int s_abort;
-    __shared__ int s_issued[2];  // K-steps issued by the producer and by the MMA thread
+    __shared__ int s_issued[2];  // K-blocks issued by the producer and by the MMA thread
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_steps = 27 + g.has_l2l;
+    const int n_steps = 27 + g.has_l2l;  // interaction offsets (+ the parent) per tile
     const int np = 1 << g.lg, side = 2 << g.lg;
     const int rows = g.TX * g.TY;
-    const uint32_t tx_bytes = 2u * (uint32_t)rows * 128u + 8192u;
+    const uint32_t tx_bytes = 2u * (uint32_t)rows * 128u + Cfg::BBytes;
     const int all_tiles = g.n_tiles * g.nvec;
     const int my_tiles = blockIdx.x < (unsigned)all_tiles ? (all_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = my_tiles * n_steps;  // K-steps of this CTA
+    const int total = my_tiles * n_steps * KB;  // K-blocks of this CTA
     volatile int* vabort = &s_abort;
     // the plan's wait budget in polls (status[3], 0: the clock bound alone)
     const uint32_t wb = ((volatile int*)status)[3] > 0 ? (uint32_t)((volatile int*)status)[3] : 0xffffffffu;
@@ -282,7 +296,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         s_issued[0] = s_issued[1] = 0;
     }
     if (warp == 0) {
-        tmem_alloc(&s_tmem, kTmaCols);
+        tmem_alloc(&s_tmem, Cfg::Cols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -305,13 +319,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         ri0 = (k % g.tiles_x) * g.TX;
         rj0 = (k / g.tiles_x) * g.TY;
     };
-    // The roles walk the same sequence of K-steps gs = it * n_steps + st with running
-    // counters: stage slot gs % kTmaStages and its use count, accumulator buffer
-    // gs % kTmaAcc and its use count.
+    // The roles walk the same sequence of K-blocks gs = (it * n_steps + st) * KB + h with
+    // running counters: stage slot gs % kTmaStages and its use count; the accumulator
+    // buffer advances once per offset (every KB blocks).
 
     if (warp == 4) {
         if (lane == 0) {
-            int it = 0, st = 0, slot = 0, use = 0;
+            int it = 0, st = 0, h = 0, slot = 0, use = 0;
             int cls = 0, ri0 = 0, rj0 = 0, v = 0;
             tile_of(0, cls, ri0, rj0, v);
             for (int gs = 0; gs < total; ++gs) {
@@ -320,65 +334,75 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                     abort_now();
                     break;
                 }
-                const uint32_t sa = base + (uint32_t)slot * kTmaStageBytes;
+                const uint32_t sa = base + (uint32_t)slot * kStageBytes;
                 mbar_arrive_expect_tx(&full[slot], tx_bytes);
+                const int c0 = 32 * h;
                 if (st < 27) {
                     const int sx = (cls & 1) + s_off[cls][st][0], sy = (cls >> 1) + s_off[cls][st][1];
                     const int plane = (sx & 1) + 2 * (sy & 1);
-                    tma_load_5d(sa, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 2 * v, &full[slot]);
-                    tma_load_5d(sa + kTmaABytes, &tm_q, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 2 * v + 1,
+                    tma_load_5d(sa, &tm_q, c0, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 2 * v, &full[slot]);
+                    tma_load_5d(sa + kTmaABytes, &tm_q, c0, ri0 + (sx >> 1), rj0 + (sy >> 1), plane, 2 * v + 1,
                                 &full[slot]);
-                    bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)s_off[cls][st][2] * 2048, 8192, &full[slot]);
+                    bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + ((size_t)s_off[cls][st][2] * KB + h) * (Cfg::BBytes / 4),
+                                 Cfg::BBytes, &full[slot]);
                 } else {
-                    tma_load_4d(sa, &tm_u, ri0, rj0, 2 * v, &full[slot]);
-                    tma_load_4d(sa + kTmaABytes, &tm_u, ri0, rj0, 2 * v + 1, &full[slot]);
-                    bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)(kNumOffsets + cls) * 2048, 8192, &full[slot]);
+                    tma_load_4d(sa, &tm_u, c0, ri0, rj0, 2 * v, &full[slot]);
+                    tma_load_4d(sa + kTmaABytes, &tm_u, c0, ri0, rj0, 2 * v + 1, &full[slot]);
+                    bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + ((size_t)(kNumOffsets + cls) * KB + h) * (Cfg::BBytes / 4),
+                                 Cfg::BBytes, &full[slot]);
                 }
                 s_issued[0] = gs + 1;
                 if (++slot == kTmaStages) {
                     slot = 0;
                     ++use;
                 }
-                if (++st == n_steps) {
-                    st = 0;
-                    if (++it < my_tiles) tile_of(it, cls, ri0, rj0, v);
+                if (++h == KB) {
+                    h = 0;
+                    if (++st == n_steps) {
+                        st = 0;
+                        if (++it < my_tiles) tile_of(it, cls, ri0, rj0, v);
+                    }
                 }
             }
         }
     } else if (warp == 5) {
         if (lane == 0) {
-            // per kk: D[0, 64) = A_hi x [B_hi | B_lo] (N = 64: the hi*hi and hi*lo terms
-            // side by side), then D[32, 64) += A_lo x B_hi (N = 32)
-            constexpr uint32_t kIdesc64 = idesc_tf32(128, 64), kIdesc32 = idesc_tf32(128, 32);
-            int slot = 0, use = 0, d = 0, du = 0;
+            // per K slice kk of the block: D_big[0, 2NP) (+)= A_hi x [B_hi | B_lo] (N = 2 NP:
+            // the hi*hi and hi*lo terms side by side), then D_small = D_big + NP += A_lo x B_hi
+            // (N = NP)
+            constexpr uint32_t kIdescBig = idesc_tf32(128, 2 * NP), kIdescSmall = idesc_tf32(128, NP);
+            int slot = 0, use = 0, h = 0, d = 0, du = 0;
             for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
                 if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1), wb) ||
-                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1), wb))) {
+                    (h == 0 && du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1), wb))) {
                     abort_now();
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_hi = base + (uint32_t)slot * kTmaStageBytes, a_lo = a_hi + kTmaABytes;
+                const uint32_t a_hi = base + (uint32_t)slot * kStageBytes, a_lo = a_hi + kTmaABytes;
                 const uint32_t b_hi = a_hi + 2 * kTmaABytes;
-                const uint32_t d_big = tmem + 64 * d, d_small = d_big + 32;
+                const uint32_t d_big = tmem + Cfg::AccCols * d, d_small = d_big + NP;
                 const uint64_t dah = smem_desc_sw128(a_hi), dal = smem_desc_sw128(a_lo), dbh = smem_desc_sw128(b_hi);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     // +32 bytes along K inside the swizzled rows = +2 in the descriptor's address field
-                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdesc64, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdesc32, 1u);
+                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdescBig, (h > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdescSmall, 1u);
                 }
                 mma_commit(&empty[slot]);
-                mma_commit(&acc_full[d]);
                 s_issued[1] = gs + 1;
                 if (++slot == kTmaStages) {
                     slot = 0;
                     ++use;
                 }
-                if (++d == kTmaAcc) {
-                    d = 0;
-                    ++du;
+                if (++h == KB) {
+                    h = 0;
+                    mma_commit(&acc_full[d]);
+                    if (++d == kTmaAcc) {
+                        d = 0;
+                        ++du;
+                    }
                 }
             }
         }
@@ -413,12 +437,13 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
         const bool valid = r < rows;
         const int xl = r % g.TX, yl = r / g.TX;
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        float acc[32];
+        float acc[NP];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+        for (int j = 0; j < NP; ++j) acc[j] = 0.f;
         int it = 0, st = 0, d = 0, du = 0;
         int cls = 0, ri = 0, rj = 0, v = 0;
-        for (int gs = 0; gs < total; ++gs) {
+        const int offsets_total = my_tiles * n_steps;
+        for (int gs = 0; gs < offsets_total; ++gs) {
             if (st == 0) {
                 int ri0, rj0;
                 tile_of(it, cls, ri0, rj0, v);
@@ -432,25 +457,28 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
                 break;
             }
             tc_fence_after();
-            uint32_t big[32], small[32];
-            tmem_ld32(tmem + lane_base + 64 * d, big);
-            tmem_ld32(tmem + lane_base + 64 * d + 32, small);
-            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < NP / 32; ++c) {
+                uint32_t big[32], small[32];
+                tmem_ld32(tmem + lane_base + Cfg::AccCols * d + 32 * c, big);
+                tmem_ld32(tmem + lane_base + Cfg::AccCols * d + NP + 32 * c, small);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[32 * c + j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[d]);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
             if (st == n_steps - 1) {
                 if (valid) {
                     float4* dst = reinterpret_cast<float4*>(
                         out + v * g.vq + (size_t)morton2(2 * ri + (cls & 1), 2 * rj + (cls >> 1)) * NP);
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
+                    for (int c = 0; c < NP / 4; ++c)
                         dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
                 }
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+                for (int j = 0; j < NP; ++j) acc[j] = 0.f;
             }
             if (++d == kTmaAcc) {
                 d = 0;
@@ -465,32 +493,36 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     __syncwarp();
     __syncthreads();
     if (s_abort && threadIdx.x == 0) {
-        // copies and MMAs issued before the abort land before the memory is released
+        // copies and MMAs issued before the abort land before the memory is released: the
+        // last kTmaStages loads, and the commit of the last issued K-block (a commit
+        // tracks every MMA issued before it)
         const int p = s_issued[0], m = s_issued[1];
         for (int gs = p > kTmaStages ? p - kTmaStages : 0; gs < p; ++gs)
             mbar_poll_bounded(&full[gs % kTmaStages], (uint32_t)((gs / kTmaStages) & 1));
-        if (m > 0) mbar_poll_bounded(&acc_full[(m - 1) % kTmaAcc], (uint32_t)(((m - 1) / kTmaAcc) & 1));
+        if (m > 0) mbar_poll_bounded(&empty[(m - 1) % kTmaStages], (uint32_t)(((m - 1) / kTmaStages) & 1));
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, kTmaCols);
+        tmem_dealloc(tmem, Cfg::Cols);
     }
 }
 
 // hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
-// tensor maps describe: planes = 1 -> [hl][plane][y'][x'][32] (targets' level),
-// planes = 0 -> [hl][y][x][32] (parent level, row-major).  Item iv is one float4 of
+// tensor maps describe: planes = 1 -> [hl][plane][y'][x'][NP] (targets' level),
+// planes = 0 -> [hl][y][x][NP] (parent level, row-major).  Item iv is one float4 of
 // vector iv / n4.
+template <int NP>
 __device__ __forceinline__ void split_tf32_item(const float4* __restrict__ x0, float4* __restrict__ dst0, int lg,
                                                 int planes, int64_t vq4, int64_t n4, int64_t iv) {
+    constexpr int Q = NP / 4;  // float4 per box
     const int np = 1 << lg;
     const int64_t vec = iv / n4, i = iv - vec * n4;
     const float4* x = x0 + vec * vq4;
     float4* dst = dst0 + 2 * vec * n4;  // vector vec: hi then lo
-    const int64_t b = i >> 3;
-    const int c = (int)(i & 7);
+    const int64_t b = i / Q;
+    const int c = (int)(i - b * Q);
     uint32_t bx, by;
     if (planes) {
         const int plane = (int)(b >> (2 * lg));
@@ -501,7 +533,7 @@ __device__ __forceinline__ void split_tf32_item(const float4* __restrict__ x0, f
         bx = (uint32_t)(b & (np - 1));
         by = (uint32_t)(b >> lg);
     }
-    const float4 v = x[(size_t)morton2(bx, by) * 8 + c];
+    const float4 v = x[(size_t)morton2(bx, by) * Q + c];
     const float a[4] = {v.x, v.y, v.z, v.w};
     float h[4], l[4];
 #pragma unroll
@@ -515,15 +547,16 @@ __device__ __forceinline__ void split_tf32_item(const float4* __restrict__ x0, f
 
 // The target level's expansions (parity planes) and, when xu is set, the parent level's
 // (row-major) in one launch: items [0, nvec nq4) are the former, the rest the latter.
+template <int NP>
 __global__ void split_tf32_layout_kernel(const float4* __restrict__ xq, float4* __restrict__ dq,
                                          const float4* __restrict__ xu, float4* __restrict__ du, int lg, int nvec,
                                          int64_t vq4) {
     griddep_wait();
-    const int64_t nq4 = ((int64_t)4 << (2 * lg)) * 8, nu4 = ((int64_t)1 << (2 * lg)) * 8;
+    const int64_t nq4 = ((int64_t)4 << (2 * lg)) * (NP / 4), nu4 = ((int64_t)1 << (2 * lg)) * (NP / 4);
     const int64_t nq = nq4 * nvec, n = nq + (xu ? nu4 * nvec : 0);
     for (int64_t iv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; iv < n; iv += (int64_t)gridDim.x * blockDim.x) {
-        if (iv < nq) split_tf32_item(xq, dq, lg, 1, vq4, nq4, iv);
-        else split_tf32_item(xu, du, lg, 0, vq4, nu4, iv - nq);
+        if (iv < nq) split_tf32_item<NP>(xq, dq, lg, 1, vq4, nq4, iv);
+        else split_tf32_item<NP>(xu, du, lg, 0, vq4, nu4, iv - nq);
     }
 }
 
@@ -542,8 +575,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// fp32 tiled map over `rank` dims (dims[0] = 32 coefficients, innermost), box
-// {32, TX, TY, 1, ...}, 128-byte swizzle, zero fill outside
+// fp32 tiled map over `rank` dims (dims[0] = NP coefficients, innermost), box
+// {32, TX, TY, 1, ...} (one 128-byte K-block), 128-byte swizzle, zero fill outside
 bool encode_map(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, int TX, int TY) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
@@ -568,20 +601,28 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
                            const float* u_parent, const void* C_parent, float* u_level, void* C_level, float* split,
                            int* status, int num_sms, cudaStream_t s, int nvec, int64_t vq, int64_t vQ, int tile,
                            int stages) {
+    const int NP = ops.NP;
+    if (NP != 32 && NP != 64) return cudaErrorInvalidValue;
     const int lg = level - 1;
     const int np = 1 << lg;
     const bool l2l = u_parent != nullptr;
-    float* qs = split;                                           // [nvec][2][4][np][np][32]
-    float* us = split + ((size_t)nvec * 2 * 4 * np * np * 32);   // [nvec][2][np][np][32]
+    float* qs = split;                                           // [nvec][2][4][np][np][NP]
+    float* us = split + ((size_t)nvec * 2 * 4 * np * np * NP);   // [nvec][2][np][np][NP]
     auto grid_for = [&](int64_t n4) {
         int64_t b = (n4 + 255) / 256;
         return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
     };
     {
-        const cudaError_t e = launch_dependent(
-            split_tf32_layout_kernel, dim3(grid_for((int64_t)(4 + (l2l ? 1 : 0)) * np * np * 8 * nvec)), dim3(256), 0, s,
-            reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs),
-            l2l ? reinterpret_cast<const float4*>(u_parent) : nullptr, reinterpret_cast<float4*>(us), lg, nvec, vq / 4);
+        const dim3 sg(grid_for((int64_t)(4 + (l2l ? 1 : 0)) * np * np * (NP / 4) * nvec));
+        const cudaError_t e = NP == 32
+            ? launch_dependent(split_tf32_layout_kernel<32>, sg, dim3(256), 0, s,
+                               reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs),
+                               l2l ? reinterpret_cast<const float4*>(u_parent) : nullptr, reinterpret_cast<float4*>(us),
+                               lg, nvec, vq / 4)
+            : launch_dependent(split_tf32_layout_kernel<64>, sg, dim3(256), 0, s,
+                               reinterpret_cast<const float4*>(q_level), reinterpret_cast<float4*>(qs),
+                               l2l ? reinterpret_cast<const float4*>(u_parent) : nullptr, reinterpret_cast<float4*>(us),
+                               lg, nvec, vq / 4);
         if (e != cudaSuccess) return e;
     }
     {
@@ -602,25 +643,30 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     g.vq = vq;
     g.vQ = vQ;
     CUtensorMap mq, mu;
-    const uint64_t dq[5] = {32, (uint64_t)np, (uint64_t)np, 4, (uint64_t)(2 * nvec)};
-    const uint64_t du[4] = {32, (uint64_t)np, (uint64_t)np, (uint64_t)(2 * nvec)};
+    const uint64_t dq[5] = {(uint64_t)NP, (uint64_t)np, (uint64_t)np, 4, (uint64_t)(2 * nvec)};
+    const uint64_t du[4] = {(uint64_t)NP, (uint64_t)np, (uint64_t)np, (uint64_t)(2 * nvec)};
     if (!encode_map(&mq, qs, 5, dq, g.TX, g.TY)) return cudaErrorInvalidValue;
     if (!encode_map(&mu, l2l ? us : qs, 4, du, g.TX, g.TY)) return cudaErrorInvalidValue;
     const int grid = std::min(g.n_tiles * nvec, num_sms);
-    auto go = [&](auto stages_tag) -> cudaError_t {
+    auto go = [&](auto np_tag, auto stages_tag) -> cudaError_t {
+        constexpr int NPc = decltype(np_tag)::value;
         constexpr int S = decltype(stages_tag)::value;
-        constexpr size_t smem = 1024 + (size_t)S * kTmaStageBytes;
-        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tma_kernel<S>, smem);
+        constexpr size_t smem = 1024 + (size_t)S * TmaCfg<NPc>::StageBytes;
+        static_assert(smem <= 227 * 1024, "TMA ring exceeds shared memory");
+        cudaError_t e = ensure_dynamic_smem((const void*)m2l_tma_kernel<NPc, S>, smem);
         if (e != cudaSuccess) return e;
-        return launch_dependent(m2l_tma_kernel<S>, dim3(grid), dim3(kTmaThreads), smem, s, mq, mu, g,
+        return launch_dependent(m2l_tma_kernel<NPc, S>, dim3(grid), dim3(kTmaThreads), smem, s, mq, mu, g,
                                 (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
                                 (const DFv*)C_parent, u_level, (DFv*)C_level, status);
     };
-    switch (stages > 0 ? stages : kTmaStagesDefault) {
-        case 2: return go(std::integral_constant<int, 2>());
-        case 4: return go(std::integral_constant<int, 4>());
-        default: return go(std::integral_constant<int, 3>());
-    }
+    auto by_stages = [&](auto np_tag) -> cudaError_t {
+        switch (stages > 0 ? stages : kTmaStagesDefault) {
+            case 2: return go(np_tag, std::integral_constant<int, 2>());
+            case 4: return go(np_tag, std::integral_constant<int, 4>());
+            default: return go(np_tag, std::integral_constant<int, 3>());
+        }
+    };
+    return NP == 32 ? by_stages(std::integral_constant<int, 32>()) : by_stages(std::integral_constant<int, 64>());
 }
 
 }  // namespace lfmm

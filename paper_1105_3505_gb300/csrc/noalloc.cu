@@ -157,14 +157,14 @@ extern "C" int lfmm_plan_shape_noalloc(const int32_t* src_xy, int64_t n_src, con
     for (int l = std::min(2, L); l <= L; ++l) boxes += (int64_t)1 << (2 * l);
     auto a = [](int64_t b) { return b == 0 ? (int64_t)16 : b; };
     const int tc_min = o.tc_min_level == 0 ? kDefaultTcMinLevel : o.tc_min_level;
-    const int64_t split = (o.precision == LFMM_MIXED && NP == 32 && L >= tc_min)
+    const int64_t split = (o.precision == LFMM_MIXED && L >= tc_min)
                               ? a(((int64_t)NP << (2 * L)) * 2 * 4 + ((int64_t)NP << (2 * std::max(0, L - 1))) * 2 * 4)
                               : 0;  // TF32 hi/lo copies for the tensor-core M2L
     const int64_t un_tmp = L >= 2 ? a(2 * n_tgt * 8) : 0;  // near and far parts before the final sum
     // one vector's partial sums of the coarse-level M2L split along K (sized from the shape)
     int num_sms = 0;
     LFMM_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-    const bool has_tc = o.precision == LFMM_MIXED && NP == 32;
+    const bool has_tc = o.precision == LFMM_MIXED;
     const int64_t part = L < 2 ? 0
                          : o.precision == LFMM_MIXED ? m2l_fused_split_bytes_shape<float>(NP, has_tc, L, tc_min, num_sms, 1, o.m2l_split)
                          : o.precision == LFMM_DF    ? m2l_fused_split_bytes_shape<DF>(NP, has_tc, L, tc_min, num_sms, 1, o.m2l_split)

@@ -284,20 +284,27 @@ float tf32_rna(float x) {
     return r;
 }
 
-// One tensor-core B tile: 32 rows (n = output p) x 32 K (q) fp32, K-major, laid out as the
-// 128-byte-swizzled shared-memory image (row n at 128 n bytes, 16-byte chunk c of the row
-// at chunk c ^ (n mod 8)); value(n, k) split into TF32 hi and lo tiles.
+// Tensor-core B operand of one operator for K-block h (k in [32h, 32h + 32)): the
+// operator's value(n, k) (n = output p < NP) split into TF32 hi and lo and stacked as one
+// K-major matrix of 2 NP rows (hi rows, then lo rows) x 32 K in fp32, laid out as the
+// 128-byte-swizzled shared-memory image (row r at 128 r bytes, 16-byte chunk c of the
+// row at chunk c ^ (r mod 8)).  NP / 32 such blocks per operator, block h at
+// dst + h * 64 NP floats.
 template <typename F>
-void write_tc_tile(float* hi, float* lo, int rows, int cols, F value) {
-    for (int n = 0; n < 32; ++n)
-        for (int k = 0; k < 32; ++k) {
-            const float v = (n < rows && k < cols) ? (float)value(n, k) : 0.0f;
-            const float h = tf32_rna(v);
-            const float l = tf32_rna(v - h);
-            const size_t idx = (size_t)n * 32 + ((size_t)(((k >> 2) ^ (n & 7)) << 2)) + (k & 3);
-            hi[idx] = h;
-            lo[idx] = l;
-        }
+void write_tc_tile(float* dst, int NP, int rows, int cols, F value) {
+    for (int h = 0; h < NP / 32; ++h) {
+        float* blk = dst + (size_t)h * 64 * NP;
+        for (int n = 0; n < NP; ++n)
+            for (int k = 0; k < 32; ++k) {
+                const int kg = 32 * h + k;
+                const float v = (n < rows && kg < cols) ? (float)value(n, kg) : 0.0f;
+                const float hv = tf32_rna(v);
+                const float lv = tf32_rna(v - hv);
+                const size_t sw = ((size_t)(((k >> 2) ^ (n & 7)) << 2)) + (k & 3);  // (NP + n) & 7 == n & 7
+                blk[(size_t)n * 32 + sw] = hv;
+                blk[(size_t)(NP + n) * 32 + sw] = lv;
+            }
+    }
 }
 
 template <typename T>
@@ -318,12 +325,12 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
     off_tifo.assign(n_levels, 0);
     off_mono.assign(n_levels, 0);
     off_tc.assign(n_levels, 0);
-    const bool tc = sizeof(T) == 4 && NP == 32;
+    const bool tc = sizeof(T) == 4 && (NP == 32 || NP == 64);
     for (int k = 0; k < n_levels; ++k) {
         if (tc) {
             n = (n + 255) & ~(size_t)255;  // 1 KB aligned tiles
             off_tc[k] = n;
-            n += (size_t)(kNumOffsets + 4) * 2 * 1024;
+            n += (size_t)(kNumOffsets + 4) * 2 * NP * NP;  // per operator NP / 32 blocks of 64 NP floats
         }
         off_mono[k] = n;
         n = align(n + (size_t)2 * kNumOffsets);
@@ -385,17 +392,16 @@ void fill_device_image(const ModelOps& mo, int NP, int n_levels, int H, int W,
                 for (int q = 0; q < lv.P; ++q)
                     img[off_tifo[k] + ((size_t)o * NP + q) * NP + p] = (T)(t[(size_t)p * lv.P + q] - c);
             if (tc) {
-                float* base = reinterpret_cast<float*>(img.data() + off_tc[k]) + (size_t)o * 2048;
-                write_tc_tile(base, base + 1024, lv.P, lv.P,
-                              [&](int n_, int k_) { return t[(size_t)n_ * lv.P + k_] - c; });
+                float* base = reinterpret_cast<float*>(img.data() + off_tc[k]) + (size_t)o * 2 * NP * NP;
+                write_tc_tile(base, NP, lv.P, lv.P, [&](int n_, int k_) { return t[(size_t)n_ * lv.P + k_] - c; });
             }
         }
         // tensor-core L2L tiles for class c: B[n = child p][k = parent q] = S_{k+1}[q][c P_k + p]
         if (tc && k + 1 < (int)mo.levels.size() && k + 1 < n_levels) {
             const LevelOps& par = mo.levels[k + 1];
             for (int c = 0; c < 4; ++c) {
-                float* base = reinterpret_cast<float*>(img.data() + off_tc[k]) + (size_t)(kNumOffsets + c) * 2048;
-                write_tc_tile(base, base + 1024, lv.P, par.P, [&](int n_, int k_) {
+                float* base = reinterpret_cast<float*>(img.data() + off_tc[k]) + (size_t)(kNumOffsets + c) * 2 * NP * NP;
+                write_tc_tile(base, NP, lv.P, par.P, [&](int n_, int k_) {
                     return par.S[(size_t)k_ * (4 * lv.P) + c * lv.P + n_];
                 });
             }
@@ -464,7 +470,7 @@ const DeviceOps* get_device_ops(ModelOps* mo, int precision, int NP, int n_level
     d->mono.resize(nl);
     d->tc.assign(nl, nullptr);
     for (int k = 0; k < nl; ++k) {
-        if (precision == LFMM_MIXED && NP == 32) d->tc[k] = b + otc[k] * elem;
+        if (precision == LFMM_MIXED && (NP == 32 || NP == 64)) d->tc[k] = b + otc[k] * elem;
         d->m2m[k] = k >= 1 ? b + om[k] * elem : nullptr;
         d->l2l[k] = k >= 1 ? b + ol[k] * elem : nullptr;
         d->tifo[k] = b + ot[k] * elem;
