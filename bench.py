@@ -562,10 +562,12 @@ def forest_leg(lfmm, steps: int = 5, warmup: int = 2):
     info = lfmm.lfmm_plan_get_info(h)
     torch.cuda.synchronize()
     u = u_d.cpu().numpy()
-    # evaluation alone on the built forest: eager launches vs the recorded CUDA graph
+    # evaluation alone on the built forest: eager launches (one per level and sweep step),
+    # the recorded CUDA graph, and one persistent launch per sweep for comparison
     ev_ms = {}
-    for mode in ("eager", "graph"):
-        lfmm.lfmm_plan_set_flags(h, lfmm.LFMM_FLAG_GRAPH if mode == "graph" else 0)
+    for mode in ("eager", "graph", "persistent"):
+        lfmm.lfmm_plan_set_flags(h, {"eager": 0, "graph": lfmm.LFMM_FLAG_GRAPH,
+                                     "persistent": lfmm.LFMM_FLAG_PERSISTENT}[mode])
         for _ in range(2):
             lfmm.lfmm_eval(h, f_d, u_d, stream)
         torch.cuda.synchronize()

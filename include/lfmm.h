@@ -103,6 +103,13 @@ typedef struct lfmm_opts {
  * device, so per-phase timings (lfmm_profile_*) measure each kernel alone.  Results
  * are bit-identical either way. */
 #define LFMM_FLAG_SERIAL 2
+/* Pruned trees and forests: run the upward sweep (P2M of every leaf, then M2M level by
+ * level) and the downward sweep (M2L + L2L level by level) of all problems each as one
+ * persistent cooperative launch (blocks take work from per-level queues, bounded grid
+ * barriers between levels) instead of one launch per level.  The results are
+ * bit-identical either way; on the 4,096-problem forest the per-level launches measured
+ * faster, so they are the default. */
+#define LFMM_FLAG_PERSISTENT 4
 
 /* Tree storage.  UNIFORM: every box of every level is stored (Sec. 6), the layout for
  * points that fill their root box.  PRUNED: the same levels and boxes, but only boxes

@@ -227,7 +227,8 @@ int validate_opts(const lfmm_opts& o) {
     if (o.tc_min_level < 0) return fail(LFMM_EINVAL, "opts.tc_min_level must be >= 0");
     if (o.tree != LFMM_TREE_AUTO && o.tree != LFMM_TREE_UNIFORM && o.tree != LFMM_TREE_PRUNED)
         return fail(LFMM_EINVAL, "opts.tree must be LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED");
-    if (o.flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL)) return fail(LFMM_EINVAL, "opts.flags has unknown bits");
+    if (o.flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL | LFMM_FLAG_PERSISTENT))
+        return fail(LFMM_EINVAL, "opts.flags has unknown bits");
     if (o.m2l_tile != 0 && o.m2l_tile != 16 && o.m2l_tile != 32 && o.m2l_tile != 64 && o.m2l_tile != 128)
         return fail(LFMM_EINVAL, "opts.m2l_tile must be 0, 16, 32, 64 or 128");
     if (o.m2l_stages != 0 && (o.m2l_stages < 2 || o.m2l_stages > 4))
@@ -304,6 +305,11 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
     p->n_boxes = F.total_boxes;
     if ((st = palloc(p, &p->qhat, (size_t)boxes * p->NP * esz, s))) return st;
     if ((st = palloc(p, &p->uhat, (size_t)boxes * p->NP * esz, s))) return st;
+    {  // work-queue counters of the persistent sweeps
+        void* c;
+        if ((st = palloc(p, &c, 32 * sizeof(unsigned long long), s))) return st;
+        F.sweep_ctr = (unsigned long long*)c;
+    }
     {  // partial sums of the list M2L levels split along K (few boxes)
         F.m2l_split = p->opts.m2l_split;
         const int64_t sb = forest_m2l_split_bytes(F, p->NP, esz, p->num_sms, F.m2l_split);
@@ -656,7 +662,7 @@ template <typename T>
 int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
     if (p->forest)
         return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
-                              u, un, uf, p->num_sms, s);
+                              u, un, uf, p->num_sms, s, (p->opts.flags & LFMM_FLAG_PERSISTENT) ? p->status : nullptr);
     const TreeView t = tree_view(p);
     const DeviceOps& ops = *p->ops;
     const int NP = p->NP;
@@ -1133,7 +1139,8 @@ int lfmm_eval_multi(lfmm_plan* p, const double* F, int32_t k, double* U, void* s
 
 int lfmm_plan_set_flags(lfmm_plan* p, int32_t flags) {
     if (!p) return fail(LFMM_EINVAL, "NULL plan");
-    if (flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL)) return fail(LFMM_EINVAL, "flags has unknown bits");
+    if (flags & ~(LFMM_FLAG_GRAPH | LFMM_FLAG_SERIAL | LFMM_FLAG_PERSISTENT))
+        return fail(LFMM_EINVAL, "flags has unknown bits");
     if (flags != p->opts.flags && p->graph) {
         // the recorded launch sequence depends on the flags
         cudaGraphExecDestroy(p->graph);

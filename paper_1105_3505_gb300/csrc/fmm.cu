@@ -1241,38 +1241,6 @@ struct LevelPtrs {
     int64_t part_stride;
 };
 
-// Grid-wide barrier of a cooperative launch.  count and gen are plan-owned device words
-// (zero before the first use, and back to that state after every barrier); status[3]
-// holds the plan's wait budget in polls (0: 2^24 polls, about a second).  The wait is
-// bounded; on expiry the block records LFMM_ETIMEOUT and goes on (results invalid, no
-// hang).
-__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* status) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vgen = gen;
-        const unsigned g = *vgen;
-        const unsigned b = (unsigned)((volatile int*)status)[3];
-        const unsigned budget = b ? b : (1u << 24);
-        __threadfence();
-        if (atomicAdd(count, 1u) + 1 == gridDim.x) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            unsigned it = 0;
-            while (*vgen == g) {
-                if (++it > budget) {
-                    atomicExch(status, LFMM_ETIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
 template <typename T, int NP, bool SMEM_OP>
 __global__ void __launch_bounds__(256) m2m_up_kernel(LevelPtrs<T> P, int l_top, int l_bot, unsigned* sync,
                                                      int* status) {

@@ -406,6 +406,50 @@ __global__ void gather_kernel(const int32_t* __restrict__ a, const int64_t* __re
 // ------------------------------------------------------------------------- sweeps
 // P2M: one warp per compact leaf.
 template <typename T, int NP>
+__device__ __forceinline__ void p2m_list_warp(int64_t b, int lane, const int32_t* __restrict__ bp,
+                                              const int32_t* __restrict__ bxy, const ProblemGeo& g,
+                                              const int32_t* __restrict__ begin, const int32_t* __restrict__ loc,
+                                              const int32_t* __restrict__ perm, const double* __restrict__ f,
+                                              T* __restrict__ f_sorted, const T* __restrict__ tofsT, int side,
+                                              T* __restrict__ qhat, typename Mono<T>::V* __restrict__ Q) {
+    using M = Mono<T>;
+    constexpr int PL = NP / 32;
+    const int p = bp[b];
+    const int x = bxy[b] & 0xffff, y = bxy[b] >> 16;
+    const int64_t leaf = g.leaf_off[p] + ((int64_t)y << g.L[p]) + x;
+    const int s0 = begin[leaf], s1 = begin[leaf + 1];
+    T acc[PL];
+#pragma unroll
+    for (int i = 0; i < PL; ++i) acc[i] = T(0);
+    typename M::V qsum = M::zero();
+    for (int j0 = s0; j0 < s1; j0 += 32) {
+        const int j = j0 + lane;
+        T fj = T(0);
+        int J = 0;
+        if (j < s1) {
+            const int l = loc[j];
+            J = (l & 0xffff) + side * (l >> 16);
+            const double fd = f[perm[j]];
+            fj = (T)fd;
+            f_sorted[j] = fj;
+            qsum = M::add(qsum, M::from_double(fd));
+        }
+        const int cnt = min(32, s1 - j0);
+        for (int kk = 0; kk < cnt; ++kk) {
+            const T fk = shfl(fj, kk);
+            const T* row = tofsT + (size_t)shfl(J, kk) * NP;
+#pragma unroll
+            for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), fk, acc[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PL; ++i) qhat[(size_t)b * NP + lane + 32 * i] = acc[i];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
+    if (lane == 0) Q[b] = qsum;
+}
+
+template <typename T, int NP>
 __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t* __restrict__ bp,
                                                        const int32_t* __restrict__ bxy, ProblemGeo g,
                                                        const int32_t* __restrict__ begin,
@@ -415,45 +459,10 @@ __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t
                                                        const T* __restrict__ tofsT, int side, T* __restrict__ qhat,
                                                        typename Mono<T>::V* __restrict__ Q) {
     griddep_wait();
-    using M = Mono<T>;
-    constexpr int PL = NP / 32;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw) {
-        const int p = bp[b];
-        const int x = bxy[b] & 0xffff, y = bxy[b] >> 16;
-        const int64_t leaf = g.leaf_off[p] + ((int64_t)y << g.L[p]) + x;
-        const int s0 = begin[leaf], s1 = begin[leaf + 1];
-        T acc[PL];
-#pragma unroll
-        for (int i = 0; i < PL; ++i) acc[i] = T(0);
-        typename M::V qsum = M::zero();
-        for (int j0 = s0; j0 < s1; j0 += 32) {
-            const int j = j0 + lane;
-            T fj = T(0);
-            int J = 0;
-            if (j < s1) {
-                const int l = loc[j];
-                J = (l & 0xffff) + side * (l >> 16);
-                const double fd = f[perm[j]];
-                fj = (T)fd;
-                f_sorted[j] = fj;
-                qsum = M::add(qsum, M::from_double(fd));
-            }
-            const int cnt = min(32, s1 - j0);
-            for (int kk = 0; kk < cnt; ++kk) {
-                const T fk = shfl(fj, kk);
-                const T* row = tofsT + (size_t)shfl(J, kk) * NP;
-#pragma unroll
-                for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), fk, acc[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PL; ++i) qhat[(size_t)b * NP + lane + 32 * i] = acc[i];
-#pragma unroll
-        for (int off = 16; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
-        if (lane == 0) Q[b] = qsum;
-    }
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw)
+        p2m_list_warp<T, NP>(b, lane, bp, bxy, g, begin, loc, perm, f, f_sorted, tofsT, side, qhat, Q);
 }
 
 // M2M: one warp per compact parent; children by compact id (-1: empty).
@@ -508,54 +517,64 @@ __global__ void __launch_bounds__(4 * NP) m2m_list_block_kernel(int64_t nb, cons
     }
 }
 
+// One parent per warp (lanes own outputs).  CG: children read through L2 only (they
+// were written by other blocks of the same cooperative launch).
+template <typename T, int NP, bool CG>
+__device__ __forceinline__ void m2m_list_warp(int64_t b, int lane, const int32_t* __restrict__ ch,
+                                              const T* __restrict__ qc, const T* __restrict__ m2m,
+                                              const typename Mono<T>::V* __restrict__ Qin, T* __restrict__ qp,
+                                              typename Mono<T>::V* __restrict__ Qout) {
+    using M = Mono<T>;
+    constexpr int CL = 4 * NP / 32, PL = NP / 32;
+    T xv[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) {
+        const int child = ch[b * 4 + (32 * c) / NP];
+        const T* src = qc + (size_t)child * NP + (32 * c) % NP + lane;
+        xv[c] = child >= 0 ? (CG ? ldcg(src) : *src) : T(0);
+    }
+    T acc[CL][PL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c)
+#pragma unroll
+        for (int i = 0; i < PL; ++i) acc[c][i] = T(0);
+#pragma unroll 4
+    for (int l = 0; l < 32; ++l) {
+#pragma unroll
+        for (int c = 0; c < CL; ++c) {
+            const T v = shfl(xv[c], l);
+            const T* row = m2m + (size_t)(32 * c + l) * NP;
+#pragma unroll
+            for (int i = 0; i < PL; ++i) acc[c][i] = fma(ldg(row + lane + 32 * i), v, acc[c][i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PL; ++i) {
+        T a = acc[0][i];
+#pragma unroll
+        for (int c = 1; c < CL; ++c) a += acc[c][i];
+        qp[(size_t)b * NP + lane + 32 * i] = a;
+    }
+    typename M::V qv = M::zero();
+    if (lane < 4) {
+        const int child = ch[b * 4 + lane];
+        if (child >= 0) qv = CG ? ldcg(Qin + child) : Qin[child];
+    }
+    qv = M::add(qv, shfl_xor_v(qv, 1));
+    qv = M::add(qv, shfl_xor_v(qv, 2));
+    if (lane == 0) Qout[b] = qv;
+}
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) m2m_list_kernel(int64_t nb, const int32_t* __restrict__ ch,
                                                        const T* __restrict__ qc, const T* __restrict__ m2m,
                                                        const typename Mono<T>::V* __restrict__ Qin,
                                                        T* __restrict__ qp, typename Mono<T>::V* __restrict__ Qout) {
     griddep_wait();
-    using M = Mono<T>;
-    constexpr int CL = 4 * NP / 32, PL = NP / 32;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw) {
-        T xv[CL];
-#pragma unroll
-        for (int c = 0; c < CL; ++c) {
-            const int child = ch[b * 4 + (32 * c) / NP];
-            xv[c] = child >= 0 ? qc[(size_t)child * NP + (32 * c) % NP + lane] : T(0);
-        }
-        T acc[CL][PL];
-#pragma unroll
-        for (int c = 0; c < CL; ++c)
-#pragma unroll
-            for (int i = 0; i < PL; ++i) acc[c][i] = T(0);
-#pragma unroll 4
-        for (int l = 0; l < 32; ++l) {
-#pragma unroll
-            for (int c = 0; c < CL; ++c) {
-                const T v = shfl(xv[c], l);
-                const T* row = m2m + (size_t)(32 * c + l) * NP;
-#pragma unroll
-                for (int i = 0; i < PL; ++i) acc[c][i] = fma(ldg(row + lane + 32 * i), v, acc[c][i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < PL; ++i) {
-            T a = acc[0][i];
-#pragma unroll
-            for (int c = 1; c < CL; ++c) a += acc[c][i];
-            qp[(size_t)b * NP + lane + 32 * i] = a;
-        }
-        typename M::V qv = M::zero();
-        if (lane < 4) {
-            const int child = ch[b * 4 + lane];
-            if (child >= 0) qv = Qin[child];
-        }
-        qv = M::add(qv, shfl_xor_v(qv, 1));
-        qv = M::add(qv, shfl_xor_v(qv, 2));
-        if (lane == 0) Qout[b] = qv;
-    }
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw)
+        m2m_list_warp<T, NP, false>(b, lane, ch, qc, m2m, Qin, qp, Qout);
 }
 
 // M2L + L2L over compact boxes of one level.  A block takes 32 boxes of one parity
@@ -573,30 +592,30 @@ struct LCfg {
     static constexpr size_t SMEM = (size_t)WARPS * (NP * 32 + ROWS) * sizeof(T);
 };
 
-template <typename T, int NP>
-__global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
-    const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
-    const T* __restrict__ q, const T* __restrict__ u_par, const T* __restrict__ ops, const T* __restrict__ l2l,
-    const T* __restrict__ mono, const typename Mono<T>::V* __restrict__ Qin,
+// The work of one block: 32 boxes (tile bx) of class cls, K chunk z of n_chunks.  CG: the
+// parent level's expansions and constants read through L2 only (written by other blocks
+// of the same cooperative launch).
+template <typename T, int NP, bool CG>
+__device__ __forceinline__ void m2l_list_block(
+    int64_t bx, int cls, int z, int n_chunks, const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il,
+    const int32_t* __restrict__ par, const T* __restrict__ q, const T* __restrict__ u_par, const T* __restrict__ ops,
+    const T* __restrict__ l2l, const T* __restrict__ mono, const typename Mono<T>::V* __restrict__ Qin,
     const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out, typename Mono<T>::V* __restrict__ Cout,
     int64_t nb, T* __restrict__ part, typename Mono<T>::V* __restrict__ cpart) {
-    griddep_wait();
     using M = Mono<T>;
     using V = typename M::V;
     constexpr int W = LCfg<T, NP>::WARPS;
-    // K split over gridDim.z chunks (levels with few boxes): chunk z takes the steps
+    // K split over n_chunks chunks (levels with few boxes): chunk z takes the steps
     // [z per, (z + 1) per) and writes its partial sums to part / cpart (chunk-major);
-    // m2l_list_reduce_kernel adds the chunks in order.
-    const int n_chunks = gridDim.z;
+    // the reduction adds the chunks in order.
     constexpr int kRows = LCfg<T, NP>::ROWS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sop = reinterpret_cast<T*>(smem_raw);
     T* red = sop + W * NP * 32;
     __shared__ int s_op[27];
     __shared__ V s_cpart[W][32];
-    const int cls = blockIdx.y;
     const int64_t c0 = cls_start[cls], c1 = cls_start[cls + 1];
-    if ((int64_t)blockIdx.x * 32 >= c1 - c0) return;  // block-uniform
+    if (bx * 32 >= c1 - c0) return;  // block-uniform
     const int px = cls & 1, py = cls >> 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < 27) {
@@ -605,7 +624,7 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
         s_op[threadIdx.x] = offset_index(dx, dy);
     }
     __syncthreads();
-    const int64_t box = c0 + (int64_t)blockIdx.x * 32 + lane;
+    const int64_t box = c0 + bx * 32 + lane;
     const bool valid = box < c1;
     const int pbox = (valid && par) ? par[box] : -1;
     const bool has_l2l = u_par != nullptr;
@@ -614,7 +633,7 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
     T* my_rows = red + (size_t)warp * kRows;
     V cacc = M::zero();
     const int per = (n_steps + n_chunks - 1) / n_chunks;
-    const int st0 = (int)blockIdx.z * per, st1 = min(n_steps, st0 + per);
+    const int st0 = z * per, st1 = min(n_steps, st0 + per);
     for (int half = 0; half < NP / 32; ++half) {
         T acc[32];
 #pragma unroll
@@ -653,18 +672,39 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
                 constexpr int CPR = NP / V4;
                 constexpr int RPI = 32 / CPR;
                 const int ch = lane % CPR;
+                // the parent's incoming expansion (step 27) may come from an earlier level of
+                // the same cooperative launch: through L2 only; source expansions (from the
+                // upward sweep) through the read-only cache, where the neighbouring target
+                // boxes of an SM share them.  Loads go out four at a time before their stores.
+                const bool cg = CG && st >= 27;
+                constexpr int NI = 32 / RPI, G = NI < 4 ? NI : 4;
 #pragma unroll
-                for (int i = 0; i < 32 / RPI; ++i) {
-                    const int r = lane / CPR + RPI * i;
-                    const T* rs = reinterpret_cast<const T*>(
-                        __shfl_sync(kFull, reinterpret_cast<unsigned long long>(src), r));
-                    uint4 v = make_uint4(0, 0, 0, 0);
-                    if (rs) v = __ldg(reinterpret_cast<const uint4*>(rs) + ch);
-                    const T* ve = reinterpret_cast<const T*>(&v);
+                for (int i0 = 0; i0 < NI; i0 += G) {
+                    uint4 vals[G];
+                    if (cg) {
 #pragma unroll
-                    for (int e = 0; e < V4; ++e) {
-                        const int k = ch * V4 + e;
-                        my_rows[r * NP + ((k + r) & (NP - 1))] = ve[e];
+                        for (int i = 0; i < G; ++i) {
+                            const T* rs = reinterpret_cast<const T*>(__shfl_sync(
+                                kFull, reinterpret_cast<unsigned long long>(src), lane / CPR + RPI * (i0 + i)));
+                            vals[i] = rs ? __ldcg(reinterpret_cast<const uint4*>(rs) + ch) : make_uint4(0, 0, 0, 0);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < G; ++i) {
+                            const T* rs = reinterpret_cast<const T*>(__shfl_sync(
+                                kFull, reinterpret_cast<unsigned long long>(src), lane / CPR + RPI * (i0 + i)));
+                            vals[i] = rs ? __ldg(reinterpret_cast<const uint4*>(rs) + ch) : make_uint4(0, 0, 0, 0);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        const int r = lane / CPR + RPI * (i0 + i);
+                        const T* ve = reinterpret_cast<const T*>(&vals[i]);
+#pragma unroll
+                        for (int e = 0; e < V4; ++e) {
+                            const int k = ch * V4 + e;
+                            my_rows[r * NP + ((k + r) & (NP - 1))] = ve[e];
+                        }
                     }
                 }
             }
@@ -698,17 +738,17 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
             T v = T(0);
 #pragma unroll
             for (int w = 0; w < W; ++w) v += red[(size_t)w * kRows + b * 33 + j];
-            const int64_t bb = c0 + (int64_t)blockIdx.x * 32 + b;
+            const int64_t bb = c0 + bx * 32 + b;
             if (bb < c1) {
                 if (n_chunks == 1) out[(size_t)bb * NP + 32 * half + j] = v;
-                else part[((size_t)blockIdx.z * nb + bb) * NP + 32 * half + j] = v;
+                else part[((size_t)z * nb + bb) * NP + 32 * half + j] = v;
             }
         }
         __syncthreads();
     }
     if (warp == 0 && valid) {
         if (n_chunks == 1) {
-            V sacc = pbox >= 0 ? Cpar[pbox] : M::zero();
+            V sacc = pbox >= 0 ? (CG ? ldcg(Cpar + pbox) : Cpar[pbox]) : M::zero();
 #pragma unroll
             for (int w = 0; w < W; ++w) sacc = M::add(sacc, s_cpart[w][lane]);
             Cout[box] = sacc;
@@ -716,31 +756,165 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
             V sacc = M::zero();
 #pragma unroll
             for (int w = 0; w < W; ++w) sacc = M::add(sacc, s_cpart[w][lane]);
-            cpart[(size_t)blockIdx.z * nb + box] = sacc;
+            cpart[(size_t)z * nb + box] = sacc;
         }
     }
 }
 
+template <typename T, int NP>
+__global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32) m2l_list_kernel(
+    const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
+    const T* __restrict__ q, const T* __restrict__ u_par, const T* __restrict__ ops, const T* __restrict__ l2l,
+    const T* __restrict__ mono, const typename Mono<T>::V* __restrict__ Qin,
+    const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out, typename Mono<T>::V* __restrict__ Cout,
+    int64_t nb, T* __restrict__ part, typename Mono<T>::V* __restrict__ cpart) {
+    griddep_wait();
+    m2l_list_block<T, NP, false>(blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, cls_start, il, par, q, u_par, ops,
+                                 l2l, mono, Qin, Cpar, out, Cout, nb, part, cpart);
+}
+
 // The chunks of a K-split list M2L added in chunk order: out = sum_z part[z], and
-// Cout = Cpar[parent] + sum_z cpart[z].
+// Cout = Cpar[parent] + sum_z cpart[z].  Grid-stride over (tid, stride); CG: inputs
+// written by other blocks of the same cooperative launch are read through L2 only.
+template <typename T, int NP, bool CG>
+__device__ __forceinline__ void m2l_list_reduce(int64_t tid, int64_t stride, int64_t nb, int n_chunks,
+                                                const T* __restrict__ part,
+                                                const typename Mono<T>::V* __restrict__ cpart,
+                                                const int32_t* __restrict__ par,
+                                                const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out,
+                                                typename Mono<T>::V* __restrict__ Cout) {
+    using M = Mono<T>;
+    for (int64_t i = tid; i < nb * NP; i += stride) {
+        T v = CG ? ldcg(part + i) : part[i];
+        for (int z = 1; z < n_chunks; ++z) v += CG ? ldcg(part + (size_t)z * nb * NP + i) : part[(size_t)z * nb * NP + i];
+        out[i] = v;
+    }
+    for (int64_t b = tid; b < nb; b += stride) {
+        const int pb = (par && Cpar) ? par[b] : -1;
+        typename M::V sacc = pb >= 0 ? (CG ? ldcg(Cpar + pb) : Cpar[pb]) : M::zero();
+        for (int z = 0; z < n_chunks; ++z) sacc = M::add(sacc, CG ? ldcg(cpart + (size_t)z * nb + b) : cpart[(size_t)z * nb + b]);
+        Cout[b] = sacc;
+    }
+}
+
 template <typename T, int NP>
 __global__ void m2l_list_reduce_kernel(int64_t nb, int n_chunks, const T* __restrict__ part,
                                        const typename Mono<T>::V* __restrict__ cpart, const int32_t* __restrict__ par,
                                        const typename Mono<T>::V* __restrict__ Cpar, T* __restrict__ out,
                                        typename Mono<T>::V* __restrict__ Cout) {
     griddep_wait();
-    using M = Mono<T>;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb * NP; i += stride) {
-        T v = part[i];
-        for (int z = 1; z < n_chunks; ++z) v += part[(size_t)z * nb * NP + i];
-        out[i] = v;
+    m2l_list_reduce<T, NP, false>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, nb,
+                                  n_chunks, part, cpart, par, Cpar, out, Cout);
+}
+
+// ------------------------------------------------------------------------- fused sweeps
+// The upward sweep (P2M of every leaf of every problem, then M2M level by level) and the
+// downward sweep (M2L + L2L level by level, coarse to fine) of the whole forest, each in
+// one persistent cooperative launch: the blocks walk the work of a level (leaves, parents,
+// 32-box tiles x K chunks) with a grid stride, and a bounded grid barrier separates the
+// levels.  Every box's arithmetic is that of the per-level kernels, so the results are
+// bit-identical to them.
+constexpr int kMaxForestLevels = 16;
+
+template <typename T>
+struct UpSweep {
+    using V = typename Mono<T>::V;
+    int64_t nb0;  // P2M: compact leaves (k = 0)
+    const int32_t *bp, *bxy, *begin, *loc, *perm;
+    ProblemGeo g;
+    const double* f;
+    T* f_sorted;
+    const T* tofsT;
+    int side;
+    int nk;  // levels k = 0 .. nk - 1
+    int64_t nb[kMaxForestLevels];
+    const int32_t* ch[kMaxForestLevels];
+    const T* m2m[kMaxForestLevels];
+    T* q[kMaxForestLevels];
+    V* Q[kMaxForestLevels];
+};
+
+// Work queue: a warp takes kUpChunk consecutive boxes of a level at a time from the
+// level's counter (ctr[k], zero before the launch), so that uneven boxes balance out.
+constexpr int kUpChunk = 4;
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) forest_up_kernel(const UpSweep<T> U, unsigned* sync, int* status,
+                                                        unsigned long long* ctr) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < U.nk; ++k) {
+        if (k > 0) grid_barrier(sync, sync + 1, status);
+        const int64_t nb = k == 0 ? U.nb0 : U.nb[k];
+        for (;;) {
+            unsigned long long c0 = 0;
+            if (lane == 0) c0 = atomicAdd(ctr + k, (unsigned long long)kUpChunk);
+            c0 = __shfl_sync(kFull, c0, 0);
+            if ((int64_t)c0 >= nb) break;
+            const int64_t c1 = min((int64_t)c0 + kUpChunk, nb);
+            for (int64_t b = (int64_t)c0; b < c1; ++b) {
+                if (k == 0)
+                    p2m_list_warp<T, NP>(b, lane, U.bp, U.bxy, U.g, U.begin, U.loc, U.perm, U.f, U.f_sorted, U.tofsT,
+                                         U.side, U.q[0], U.Q[0]);
+                else
+                    m2m_list_warp<T, NP, true>(b, lane, U.ch[k], U.q[k - 1], U.m2m[k], U.Q[k - 1], U.q[k], U.Q[k]);
+            }
+        }
     }
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
-        const int pb = (par && Cpar) ? par[b] : -1;
-        typename M::V sacc = pb >= 0 ? Cpar[pb] : M::zero();
-        for (int z = 0; z < n_chunks; ++z) sacc = M::add(sacc, cpart[(size_t)z * nb + b]);
-        Cout[b] = sacc;
+}
+
+template <typename T>
+struct DownLevel {
+    using V = typename Mono<T>::V;
+    const int64_t* cls;
+    const int32_t *il, *par;
+    const T *q, *u_par, *tifo, *l2l, *mono;
+    const V *Qin, *Cpar;
+    T* out;
+    V* Cout;
+    int64_t nb;
+    int tiles;  // 32-box tiles of the largest class
+    int nc;     // K chunks (partial sums in the sweep's part / cpart when > 1)
+};
+
+template <typename T>
+struct DownSweep {
+    int n;  // levels in processing order (coarse to fine)
+    DownLevel<T> lv[kMaxForestLevels];
+    T* part;
+    typename Mono<T>::V* cpart;
+};
+
+// Work queue: a block takes one item (tile, class, K chunk) of a level at a time from the
+// level's counter (ctr[i], zero before the launch).
+template <typename T, int NP>
+__global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32, sizeof(T) == 4 ? 2 : 1)
+    forest_m2l_kernel(const DownSweep<T> D, unsigned* sync, int* status, unsigned long long* ctr) {
+    using V = typename Mono<T>::V;
+    __shared__ long long s_item;
+    for (int i = 0; i < D.n; ++i) {
+        const DownLevel<T>& L = D.lv[i];
+        const int tiles = L.tiles, nc = L.nc;
+        const int64_t items = (int64_t)4 * tiles * nc;
+        T* part = nc > 1 ? D.part : nullptr;
+        V* cpart = nc > 1 ? (V*)(D.part + (size_t)nc * L.nb * NP) : nullptr;
+        for (;;) {
+            if (threadIdx.x == 0) s_item = (long long)atomicAdd(ctr + i, 1ull);
+            __syncthreads();
+            const int64_t it = s_item;
+            __syncthreads();
+            if (it >= items) break;
+            const int64_t bx = it % tiles;
+            const int64_t r = it / tiles;
+            m2l_list_block<T, NP, true>(bx, (int)(r & 3), (int)(r >> 2), nc, L.cls, L.il, L.par, L.q, L.u_par, L.tifo,
+                                        L.l2l, L.mono, L.Qin, L.Cpar, L.out, L.Cout, L.nb, part, cpart);
+        }
+        if (nc > 1) {
+            grid_barrier(sync, sync + 1, status);
+            m2l_list_reduce<T, NP, true>((int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                         (int64_t)gridDim.x * blockDim.x, L.nb, nc, part, cpart, L.par, L.Cpar, L.out,
+                                         L.Cout);
+        }
+        if (i + 1 < D.n) grid_barrier(sync, sync + 1, status);
     }
 }
 
@@ -1328,9 +1502,26 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     return LFMM_OK;  // temporaries are freed in stream order
 }
 
+// Cooperative launch through the capturable launch API (the fused sweeps).
+static cudaError_t launch_coop(const void* fn, int grid, int threads, size_t smem, void** args, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+}
+
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s) {
+                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status) {
     using V = typename Mono<T>::V;
     const int NP = ops.NP;
     const int nk = (int)F.levels.size();
@@ -1340,7 +1531,43 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
     auto Qm = [&](int k) { return (V*)Qbox + F.levels[k].box_off; };
     auto Cm = [&](int k) { return (V*)Cbox + F.levels[k].box_off; };
     const bool far = F.kmax >= 0;
-    {
+    unsigned* sync = status ? (unsigned*)(status + 1) : nullptr;  // grid-barrier words beside the status word
+    // ---- upward sweep in one persistent launch (P2M, then M2M level by level)
+    bool up_done = false;
+    if (sync && F.sweep_ctr && nk <= kMaxForestLevels && F.levels[0].nb > 0) {
+        PhaseTimer pt(LFMM_PHASE_M2M, s);
+        UpSweep<T> U;
+        U.nb0 = F.levels[0].nb;
+        U.bp = F.levels[0].bp;
+        U.bxy = F.levels[0].bxy;
+        U.begin = F.sbeg;
+        U.loc = F.sloc;
+        U.perm = F.sperm;
+        U.g = g;
+        U.f = f;
+        U.f_sorted = f_sorted;
+        U.tofsT = (const T*)ops.tofsT;
+        U.side = F.side;
+        U.nk = far ? nk : 1;
+        for (int k = 0; k < kMaxForestLevels; ++k) {
+            const bool on = k < U.nk;
+            U.nb[k] = on ? F.levels[k].nb : 0;
+            U.ch[k] = on ? F.levels[k].ch : nullptr;
+            U.m2m[k] = on && k >= 1 ? (const T*)ops.m2m[k] : nullptr;
+            U.q[k] = on ? Qx(k) : nullptr;
+            U.Q[k] = on ? Qm(k) : nullptr;
+        }
+        const void* fn = NP == 32 ? (const void*)forest_up_kernel<T, 32> : (const void*)forest_up_kernel<T, 64>;
+        const int grid = num_sms * std::max(1, blocks_per_sm(fn, 256, 0));
+        unsigned long long* ctr = F.sweep_ctr;
+        void* args[] = {&U, &sync, &status, &ctr};
+        if (cudaMemsetAsync(ctr, 0, 2 * kMaxForestLevels * sizeof(unsigned long long), s) == cudaSuccess &&
+            launch_coop(fn, grid, 256, 0, args, s) == cudaSuccess) {
+            pt.add_launches(1);
+            up_done = true;
+        }
+    }
+    if (!up_done) {
         PhaseTimer pt(LFMM_PHASE_P2M, s);
         const ForestLevel& l0 = F.levels[0];
         if (l0.nb > 0) {
@@ -1357,7 +1584,7 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             pt.add_launches(1);
         }
     }
-    if (far) {
+    if (far && !up_done) {
         PhaseTimer pt(LFMM_PHASE_M2M, s);
         for (int k = 1; k < nk; ++k) {
             const ForestLevel& lv = F.levels[k];
@@ -1385,7 +1612,61 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             pt.add_launches(1);
         }
     }
-    if (far) {
+    // ---- downward sweep in one persistent launch (M2L + L2L, coarse to fine)
+    bool down_done = false;
+    if (far && up_done && nk <= kMaxForestLevels) {  // its counters were zeroed with the upward sweep's
+        PhaseTimer pt(LFMM_PHASE_M2L, s);
+        DownSweep<T> D;
+        D.n = 0;
+        D.part = (T*)F.m2l_part;
+        D.cpart = nullptr;
+        bool ok = true;
+        for (int k = nk - 1; k >= 0; --k) {
+            const ForestLevel& lv = F.levels[k];
+            if (lv.nb == 0) continue;
+            int64_t maxc = 0;
+            for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
+            if (maxc == 0) continue;
+            const bool l2l = k + 1 < nk;
+            DownLevel<T>& L = D.lv[D.n++];
+            L.cls = lv.d_cls;
+            L.il = lv.il;
+            L.par = l2l ? lv.par : nullptr;
+            L.q = Qx(k);
+            L.u_par = l2l ? Ux(k + 1) : nullptr;
+            L.tifo = (const T*)ops.tifo[k];
+            L.l2l = l2l ? (const T*)ops.l2l[k + 1] : nullptr;
+            L.mono = (const T*)ops.mono[k];
+            L.Qin = Qm(k);
+            L.Cpar = l2l ? Cm(k + 1) : nullptr;
+            L.out = Ux(k);
+            L.Cout = Cm(k);
+            L.nb = lv.nb;
+            L.tiles = (int)((maxc + 31) / 32);
+            L.nc = F.m2l_part ? m2l_list_chunks(maxc, num_sms, F.m2l_split) : 1;
+            if (L.nc > 1 && !F.m2l_part) ok = false;
+        }
+        if (ok && D.n > 0) {
+            auto go = [&](auto np_tag) -> cudaError_t {
+                constexpr int NPc = decltype(np_tag)::value;
+                const void* fn = (const void*)forest_m2l_kernel<T, NPc>;
+                constexpr size_t smem = LCfg<T, NPc>::SMEM;
+                constexpr int threads = LCfg<T, NPc>::WARPS * 32;
+                cudaError_t e = ensure_dynamic_smem(fn, smem);
+                if (e != cudaSuccess) return e;
+                const int grid = num_sms * std::max(1, blocks_per_sm(fn, threads, smem));
+                unsigned long long* ctr = F.sweep_ctr + kMaxForestLevels;  // zeroed with the upward sweep's
+                void* args[] = {&D, &sync, &status, &ctr};
+                return launch_coop(fn, grid, threads, smem, args, s);
+            };
+            if ((NP == 32 ? go(std::integral_constant<int, 32>()) : go(std::integral_constant<int, 64>())) ==
+                cudaSuccess) {
+                pt.add_launches(1);
+                down_done = true;
+            }
+        }
+    }
+    if (far && !down_done) {
         PhaseTimer pt(LFMM_PHASE_M2L, s);
         for (int k = nk - 1; k >= 0; --k) {
             const ForestLevel& lv = F.levels[k];
@@ -1454,10 +1735,10 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
 }
 
 template int forest_eval<float>(const Forest&, const DeviceOps&, const double*, float*, float*, float*, void*, void*,
-                                double*, double*, double*, int, cudaStream_t);
+                                double*, double*, double*, int, cudaStream_t, int*);
 template int forest_eval<double>(const Forest&, const DeviceOps&, const double*, double*, double*, double*, void*,
-                                 void*, double*, double*, double*, int, cudaStream_t);
+                                 void*, double*, double*, double*, int, cudaStream_t, int*);
 template int forest_eval<DF>(const Forest&, const DeviceOps&, const double*, DF*, DF*, DF*, void*, void*, double*,
-                             double*, double*, int, cudaStream_t);
+                             double*, double*, int, cudaStream_t, int*);
 
 }  // namespace lfmm

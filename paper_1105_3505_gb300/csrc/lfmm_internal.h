@@ -280,6 +280,7 @@ struct Forest {
     int64_t bytes = 0;
     void* m2l_part = nullptr;               // partial sums of K-split list M2L levels (plan-owned)
     int m2l_split = 0;                      // opts.m2l_split (0: chunks by the number of tiles)
+    unsigned long long* sweep_ctr = nullptr;  // work-queue counters of the fused sweeps (2 x 16, plan-owned)
     void release(cudaStream_t s);
 };
 
@@ -295,9 +296,11 @@ int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms,
 int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
                  const int64_t* toff_h, int64_t nt, int np, int leaf_size, int max_leaf_side, cudaStream_t s,
                  PhaseTimer* timer);
+// status: the plan's status word (grid-barrier words beside it) to run each sweep as one
+// persistent cooperative launch (LFMM_FLAG_PERSISTENT); NULL: one launch per level.
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s);
+                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status = nullptr);
 
 // words[0..3] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN}, words[4..9] = 0, zero[0..n_zero) = 0
 // (zero 16-byte aligned), in one launch.

@@ -19,7 +19,7 @@ from .build import LIB
  LFMM_ECANCELED) = range(9)
 LFMM_FP64, LFMM_MIXED, LFMM_DF = 0, 1, 2
 LFMM_TREE_AUTO, LFMM_TREE_UNIFORM, LFMM_TREE_PRUNED = 0, 1, 2
-LFMM_FLAG_GRAPH, LFMM_FLAG_SERIAL = 1, 2
+LFMM_FLAG_GRAPH, LFMM_FLAG_SERIAL, LFMM_FLAG_PERSISTENT = 1, 2, 4
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lfmm.h")
 
@@ -161,12 +161,13 @@ def lfmm_opts_default() -> lfmm_opts:
 def make_opts(precision: int = LFMM_MIXED, p: int = 8, leaf_size: int = 64, max_leaf_side: int = 32,
               proxies_per_edge: int = 64, tc_min_level: int = 0, tree: int = LFMM_TREE_AUTO,
               graph: bool = False, serial: bool = False, m2l_tile: int = 0, m2l_stages: int = 0,
-              m2l_split: int = 0) -> lfmm_opts:
+              m2l_split: int = 0, persistent: bool = False) -> lfmm_opts:
     o = lfmm_opts_default()
     o.precision, o.p, o.leaf_size = precision, p, leaf_size
     o.max_leaf_side, o.proxies_per_edge, o.tc_min_level = max_leaf_side, proxies_per_edge, tc_min_level
     o.tree = tree
-    o.flags = (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0)
+    o.flags = (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0) | \
+        (LFMM_FLAG_PERSISTENT if persistent else 0)
     o.m2l_tile, o.m2l_stages, o.m2l_split = m2l_tile, m2l_stages, m2l_split
     return o
 
@@ -386,9 +387,11 @@ class Plan:
     def status(self):
         lfmm_plan_status(self.handle, self.stream)
 
-    def set_flags(self, graph: bool = False, serial: bool = False):
-        """lfmm_plan_set_flags: graph replay and serial order for later evaluations."""
-        lfmm_plan_set_flags(self.handle, (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0))
+    def set_flags(self, graph: bool = False, serial: bool = False, persistent: bool = False):
+        """lfmm_plan_set_flags: graph replay, serial order and (pruned trees, forests) one
+        persistent launch per sweep for later evaluations."""
+        lfmm_plan_set_flags(self.handle, (LFMM_FLAG_GRAPH if graph else 0) | (LFMM_FLAG_SERIAL if serial else 0) |
+                            (LFMM_FLAG_PERSISTENT if persistent else 0))
 
     def info(self) -> dict:
         return lfmm_plan_get_info(self.handle)

@@ -78,10 +78,16 @@ def test_opts_flags_validated_without_gpu(lib):
     h = ctypes.c_void_p(123)
     pts = np.zeros((4, 2), dtype=np.int32)
     o = lfmm.make_opts()
-    o.flags = 6  # unknown bits
+    o.flags = 8  # unknown bit
     st = lib.lfmm_plan_create(ctypes.byref(h), pts.ctypes.data, 4, pts.ctypes.data, 4, ctypes.byref(o), None)
     assert st == lfmm.LFMM_EINVAL and "flags" in lfmm.lfmm_last_error()
     assert lfmm.make_opts(graph=True).flags == lfmm.LFMM_FLAG_GRAPH
+    # the M2L tiling fields are validated too
+    for field, bad in (("m2l_tile", 48), ("m2l_stages", 5), ("m2l_split", 10), ("reserved", 1)):
+        o = lfmm.make_opts()
+        setattr(o, field, bad)
+        st = lib.lfmm_plan_create(ctypes.byref(h), pts.ctypes.data, 4, pts.ctypes.data, 4, ctypes.byref(o), None)
+        assert st == lfmm.LFMM_EINVAL and field in lfmm.lfmm_last_error()
 
 
 def test_autotune_arguments_validated_without_gpu(lib):

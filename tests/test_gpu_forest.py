@@ -217,3 +217,48 @@ def test_clustered_4m_sampled(lfmm, clustered_4m, precision, p):
         info = pl.info()
     assert info["tree"] == lfmm.LFMM_TREE_PRUNED and np.isfinite(u).all()
     assert rel_err(u[idx], ref) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed16", "df"])
+def test_forest_persistent_sweeps_equal_per_level(lfmm, precision):
+    """With LFMM_FLAG_PERSISTENT the upward and downward sweeps of a forest run as one
+    persistent cooperative launch each (work queues per level, grid barriers between
+    levels); by default the same plan runs one launch per level.  Same arithmetic per box:
+    the results are bit-identical, and the persistent form launches one kernel per sweep."""
+    probs = forest_case(zlib.crc32(b"fused"), 60, n_min=200, n_max=9000)
+    src, so, tgt, to, f = concat(probs)
+    prec, p, tol = prec_of(lfmm, precision)
+    with lfmm.Forest(src, so, tgt, to, precision=prec, p=p) as fo:
+        lfmm.lfmm_profile_enable(True)
+        lfmm.lfmm_profile_read(reset=True)
+        try:
+            u_level = fo.eval(f)
+            prof_level = lfmm.lfmm_profile_read(reset=True)
+            fo.set_flags(persistent=True)
+            u_fused = fo.eval(f)
+            prof = lfmm.lfmm_profile_read(reset=True)
+        finally:
+            lfmm.lfmm_profile_enable(False)
+        fo.status()
+    assert np.array_equal(u_fused, u_level)
+    assert prof["m2m"][1] == 1 and prof["m2l"][1] == 1 and prof["p2m"][1] == 0
+    assert prof_level["m2l"][1] > 1
+    for i in (0, 31, 59):
+        ref = oracle.lattice_sum(probs[i][0], probs[i][2], probs[i][1])
+        assert rel_err(u_fused[to[i]:to[i + 1]], ref) <= tol
+
+
+def test_clustered_persistent_sweeps(lfmm):
+    """A pruned tree of many levels (the persistent sweeps cross 9 grid barriers) against
+    the per-level launches and the oracle."""
+    prob = small_clustered()
+    for prec, p, tol in ((lfmm.LFMM_MIXED, 8, MIXED_TOL), (lfmm.LFMM_DF, 16, FP64_TOL)):
+        with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p) as pl:
+            u0 = pl.eval(prob.f)
+            pl.set_flags(persistent=True)
+            u1 = pl.eval(prob.f)
+            pl.status()
+        assert np.array_equal(u0, u1)
+    idx = np.arange(0, prob.tgt.shape[0], 37)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
+    assert rel_err(u1[idx], ref) <= tol
