@@ -7,19 +7,18 @@
 // whose empty boxes are dropped.  Boxes are grouped by k = levels above the leaves
 // (k = 0: leaves), because the model-box operators of Sec. 8.1 depend on k only.
 //
-// Level k over all problems is described by a dense map in parity-plane order: for
-// each parity class c = (x & 1) + 2 (y & 1), the problems in turn, and inside a
-// problem the (x >> 1, y >> 1) grid of that class row by row.  Non-empty boxes
-// (any source or target below them) get compact ids by an exclusive scan of that
-// map, so compact ids come grouped by parity class - what the M2L kernels need, since
-// a class fixes the 27 operators of a box's interaction list (Def. 6.1).  Per compact
-// box the builder stores its problem, coordinates, parent, children and interaction
-// list (27 compact ids in slot order, -1 where the box is empty or outside).
+// The builder (forest_tree.cu) numbers the non-empty boxes of each level (a source or
+// target below them) in parity-class order - class c = (x & 1) + 2 (y & 1), then
+// problem, then the (x >> 1, y >> 1) grid row by row - so compact ids come grouped by
+// class, which is what the M2L kernels need: a class fixes the 27 operators of a box's
+// interaction list (Def. 6.1).  Per compact box it stores its problem, coordinates,
+// parent, children and interaction list (27 compact ids in slot order, -1 where the box
+// is empty or outside).
 //
-// Points are bucketed per problem into row-major leaves, as on the uniform tree, so
-// the sources of a leaf's 3 x 3 neighbourhood are three contiguous ranges and the
+// Points are sorted per problem into row-major leaves, as on the uniform tree, so the
+// sources of a leaf's 3 x 3 neighbourhood are three contiguous ranges and the
 // near-field strip kernel carries over; it walks a list of the strips that hold
-// targets.
+// targets, each with the occupied leaves of its three neighbour-row segments.
 #include <algorithm>
 #include <climits>
 #include <type_traits>
@@ -40,384 +39,19 @@ int grid_for(int64_t n, int threads, int cap = 152 * 16) {
     return (int)g;
 }
 
-// last index p in [0, n) with a[p] <= v (a non-decreasing, a[0] <= v)
-template <typename I>
-__device__ __forceinline__ int upper_index(const I* a, int n, int64_t v) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if ((int64_t)a[mid] <= v) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// position of box (x, y) of level l of a problem starting at off_p in each class
-// segment of length S (parity-plane order)
-__device__ __forceinline__ int64_t plane_entry(int64_t S, int64_t off_p, int l, int x, int y) {
-    const int c = (x & 1) | ((y & 1) << 1);
-    const int64_t h = l >= 1 ? ((int64_t)1 << (l - 1)) : 1;
-    return (int64_t)c * S + off_p + (int64_t)(y >> 1) * h + (x >> 1);
-}
-
-// ------------------------------------------------------------------------- tree build
-__global__ void pid_kernel(const int64_t* __restrict__ off, int np, int32_t* __restrict__ pid) {
-    griddep_wait();
-    for (int p = blockIdx.x; p < np; p += gridDim.x)
-        for (int64_t i = off[p] + threadIdx.x; i < off[p + 1]; i += blockDim.x) pid[i] = p;
-}
-
-// bounding box of each problem's sources and targets, one block per problem
-__global__ void bbox_forest_kernel(const int2* __restrict__ src, const int64_t* __restrict__ soff,
-                                   const int2* __restrict__ tgt, const int64_t* __restrict__ toff, int np,
-                                   int4* __restrict__ bb) {
-    griddep_wait();
-    __shared__ int red[4][kThreads / 32];
-    for (int p = blockIdx.x; p < np; p += gridDim.x) {
-        int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
-        for (int64_t i = soff[p] + threadIdx.x; i < soff[p + 1]; i += blockDim.x) {
-            const int2 v = src[i];
-            x0 = min(x0, v.x), y0 = min(y0, v.y), x1 = max(x1, v.x), y1 = max(y1, v.y);
-        }
-        for (int64_t i = toff[p] + threadIdx.x; i < toff[p + 1]; i += blockDim.x) {
-            const int2 v = tgt[i];
-            x0 = min(x0, v.x), y0 = min(y0, v.y), x1 = max(x1, v.x), y1 = max(y1, v.y);
-        }
-        for (int o = 16; o; o >>= 1) {
-            x0 = min(x0, __shfl_xor_sync(kFull, x0, o));
-            y0 = min(y0, __shfl_xor_sync(kFull, y0, o));
-            x1 = max(x1, __shfl_xor_sync(kFull, x1, o));
-            y1 = max(y1, __shfl_xor_sync(kFull, y1, o));
-        }
-        const int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) red[0][w] = x0, red[1][w] = y0, red[2][w] = x1, red[3][w] = y1;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-                x0 = min(x0, red[0][i]), y0 = min(y0, red[1][i]);
-                x1 = max(x1, red[2][i]), y1 = max(y1, red[3][i]);
-            }
-            bb[p] = make_int4(x0, y0, x1, y1);
-        }
-        __syncthreads();
-    }
-}
-
-struct ProblemGeo {
-    const int32_t* pid;       // problem of each point
-    const int32_t* x0;        // [np] root corner
-    const int32_t* y0;
-    const int32_t* L;         // [np] leaf level
-    const int64_t* leaf_off;  // [np + 1] first absolute leaf of each problem
-};
-
-__device__ __forceinline__ int64_t leaf_of(const ProblemGeo& g, int p, int2 v, int ls, int& lx, int& ly) {
-    const int64_t rx = (int64_t)v.x - g.x0[p], ry = (int64_t)v.y - g.y0[p];
-    const int n = 1 << g.L[p];
-    const int bx = (int)(rx >> ls), by = (int)(ry >> ls);
-    lx = (int)(rx & ((1 << ls) - 1));
-    ly = (int)(ry & ((1 << ls) - 1));
-    return g.leaf_off[p] + (int64_t)by * n + bx;
-}
-
-// leaf counts; rank[i] = the point's arrival rank in its leaf (its slot offset later)
-__global__ void count_forest_kernel(const int2* __restrict__ xy, int64_t n, ProblemGeo g, int ls,
-                                    int32_t* __restrict__ cnt, int32_t* __restrict__ rank) {
-    griddep_wait();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int lx, ly;
-        rank[i] = atomicAdd(cnt + leaf_of(g, g.pid[i], xy[i], ls, lx, ly), 1);
-    }
-}
-
-__global__ void max2_kernel(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int64_t n,
-                            int* __restrict__ out2) {
-    griddep_wait();
-    int ma = 0, mb = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        ma = max(ma, a[i]);
-        mb = max(mb, b[i]);
-    }
-    for (int o = 16; o; o >>= 1) {
-        ma = max(ma, __shfl_xor_sync(kFull, ma, o));
-        mb = max(mb, __shfl_xor_sync(kFull, mb, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(out2, ma);
-        atomicMax(out2 + 1, mb);
-    }
-}
-
-__global__ void scatter_forest_kernel(const int2* __restrict__ xy, int64_t n, ProblemGeo g, int ls,
-                                      const int32_t* __restrict__ begin, const int32_t* __restrict__ rank,
-                                      int32_t* __restrict__ loc, int32_t* __restrict__ perm) {
-    griddep_wait();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int lx, ly;
-        const int64_t leaf = leaf_of(g, g.pid[i], xy[i], ls, lx, ly);
-        const int slot = begin[leaf] + rank[i];
-        loc[slot] = lx | (ly << 16);
-        perm[slot] = (int32_t)i;
-    }
-}
-
-// ---- exclusive scan of int32 (blocks of 1024, one block for the block totals)
-constexpr int kScanBlock = 1024;
-
-__global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
-    griddep_wait();
-    __shared__ int32_t w[kThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
-    int32_t v = 0;
-    for (int i = threadIdx.x; i < kScanBlock; i += blockDim.x)
-        if (base + i < n) v += in[base + i];
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t t = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += w[i];
-        sums[blockIdx.x] = t;
-    }
-}
-
-// exclusive scan of the block totals in place (one block); total to sums[nb]
-__global__ void scan_sums_kernel(int32_t* __restrict__ sums, int nb) {
-    griddep_wait();
-    __shared__ int32_t carry_s, w[1024 / 32];
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    for (int base = 0; base < nb; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int32_t v = i < nb ? sums[i] : 0;
-        int32_t x = v;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) w[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            int32_t s = lane < (int)(blockDim.x >> 5) ? w[lane] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(kFull, s, o);
-                if (lane >= o) s += y;
-            }
-            w[lane] = s;
-        }
-        __syncthreads();
-        const int32_t incl = x + (wid > 0 ? w[wid - 1] : 0);
-        const int32_t carry = carry_s;
-        if (i < nb) sums[i] = carry + incl - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry_s = carry + incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) sums[nb] = carry_s;
-}
-
-__global__ void scan_apply_kernel(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ sums,
-                                  int32_t* __restrict__ out) {
-    griddep_wait();
-    __shared__ int32_t w[kThreads / 32];
-    constexpr int PER = kScanBlock / kThreads;  // 4 consecutive items per thread
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * PER;
-    int32_t v[PER], t = 0;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        v[j] = base + j < n ? in[base + j] : 0;
-        t += v[j];
-    }
-    int32_t x = t;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) w[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int32_t s = lane < (int)(blockDim.x >> 5) ? w[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(kFull, s, o);
-            if (lane >= o) s += y;
-        }
-        w[lane] = s;
-    }
-    __syncthreads();
-    int32_t run = sums[blockIdx.x] + x - t + (wid > 0 ? w[wid - 1] : 0);
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        if (base + j < n) out[base + j] = run;
-        run += v[j];
-    }
-    const int64_t nblk = (n + kScanBlock - 1) / kScanBlock;
-    if (blockIdx.x == nblk - 1 && threadIdx.x == blockDim.x - 1) out[n] = sums[nblk];
-}
-
-// ---- levels
-struct LevelGeo {
-    int k;
-    int np;
-    int64_t S;                // entries per class segment
-    const int64_t* off;       // [np] start of each problem in a class segment
-    const int64_t* size;      // [np] entries per class of each problem (0: absent)
-};
-
-// flags of the leaves (k = 0): box non-empty if it holds a source or a target
-__global__ void flag_leaves_kernel(const int32_t* __restrict__ cs, const int32_t* __restrict__ ct, int64_t NL,
-                                   ProblemGeo g, int np, LevelGeo lv, int32_t* __restrict__ flags) {
-    griddep_wait();
-    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < NL; a += (int64_t)gridDim.x * blockDim.x) {
-        if (cs[a] + ct[a] == 0) continue;
-        const int p = upper_index(g.leaf_off, np, a);
-        const int L = g.L[p];
-        const int64_t r = a - g.leaf_off[p];
-        const int x = (int)(r & ((1 << L) - 1)), y = (int)(r >> L);
-        flags[plane_entry(lv.S, lv.off[p], L, x, y)] = 1;
-    }
-}
-
-// flags of level k >= 1 from the compact map of level k-1 (any child present)
-__global__ void flag_parents_kernel(ProblemGeo g, LevelGeo lv, LevelGeo lc, const int32_t* __restrict__ map_child,
-                                    int32_t* __restrict__ flags) {
-    griddep_wait();
-    const int64_t n = 4 * lv.S;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e / lv.S);
-        const int64_t r = e - (int64_t)c * lv.S;
-        const int p = upper_index(lv.off, lv.np, r);
-        const int64_t rr = r - lv.off[p];
-        if (rr >= lv.size[p]) {
-            flags[e] = 0;
-            continue;
-        }
-        const int l = g.L[p] - lv.k;
-        const int h = 1 << (l - 1);
-        const int x = 2 * (int)(rr % h) + (c & 1), y = 2 * (int)(rr / h) + (c >> 1);
-        int any = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            any |= map_child[plane_entry(lc.S, lc.off[p], l + 1, 2 * x + (b & 1), 2 * y + (b >> 1))] >= 0;
-        flags[e] = any;
-    }
-}
-
-// map[e] = compact id or -1; box records of the compact ids
-__global__ void compact_kernel(ProblemGeo g, LevelGeo lv, const int32_t* __restrict__ scan, int32_t* __restrict__ map,
-                               int32_t* __restrict__ bp, int32_t* __restrict__ bxy) {
-    griddep_wait();
-    const int64_t n = 4 * lv.S;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const bool on = scan[e + 1] != scan[e];
-        if (!on) {
-            map[e] = -1;
-            continue;
-        }
-        const int cid = scan[e];
-        map[e] = cid;
-        if (bp) {
-            const int c = (int)(e / lv.S);
-            const int64_t r = e - (int64_t)c * lv.S;
-            const int p = upper_index(lv.off, lv.np, r);
-            const int64_t rr = r - lv.off[p];
-            const int l = g.L[p] - lv.k;
-            const int h = l >= 1 ? 1 << (l - 1) : 1;
-            const int x = 2 * (int)(rr % h) + (c & 1), y = 2 * (int)(rr / h) + (c >> 1);
-            bp[cid] = p;
-            bxy[cid] = x | (y << 16);
-        }
-    }
-}
-
-// parent, children and interaction list of every compact box of level k
-__global__ void links_kernel(ProblemGeo g, LevelGeo lv, int64_t nb, const int32_t* __restrict__ bp,
-                             const int32_t* __restrict__ bxy, const int32_t* __restrict__ map,
-                             LevelGeo lpar, const int32_t* __restrict__ map_par, LevelGeo lch,
-                             const int32_t* __restrict__ map_ch, int32_t* __restrict__ par, int32_t* __restrict__ ch,
-                             int32_t* __restrict__ il) {
-    griddep_wait();
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
-        const int p = bp[b];
-        const int x = bxy[b] & 0xffff, y = bxy[b] >> 16;
-        const int l = g.L[p] - lv.k;
-        const int n = 1 << l;
-        if (par) {
-            int v = -1;
-            if (map_par && l - 1 >= 2 && lpar.size[p] > 0)
-                v = map_par[plane_entry(lpar.S, lpar.off[p], l - 1, x >> 1, y >> 1)];
-            par[b] = v;
-        }
-        if (ch) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                ch[b * 4 + c] = map_ch[plane_entry(lch.S, lch.off[p], l + 1, 2 * x + (c & 1), 2 * y + (c >> 1))];
-        }
-        if (il) {
-            for (int st = 0; st < 27; ++st) {
-                int dx, dy;
-                interaction_slot(x & 1, y & 1, st, dx, dy);
-                const int sx = x + dx, sy = y + dy;
-                int v = -1;
-                if (sx >= 0 && sx < n && sy >= 0 && sy < n) v = map[plane_entry(lv.S, lv.off[p], l, sx, sy)];
-                il[b * 27 + st] = v;
-            }
-        }
-    }
-}
-
-// strips of SW leaves of one leaf row holding at least one target
-__global__ void strip_flag_kernel(ProblemGeo g, int np, const int64_t* __restrict__ strip_off, int SW,
-                                  const int32_t* __restrict__ tbeg, int32_t* __restrict__ flags) {
-    griddep_wait();
-    const int64_t n = strip_off[np];
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int p = upper_index(strip_off, np, q);
-        const int L = g.L[p];
-        const int nn = 1 << L, nseg = (nn + SW - 1) / SW;
-        const int64_t r = q - strip_off[p];
-        const int by = (int)(r / nseg), bx0 = (int)(r % nseg) * SW, bx1 = min(bx0 + SW, nn);
-        const int64_t row = g.leaf_off[p] + (int64_t)by * nn;
-        flags[q] = tbeg[row + bx1] != tbeg[row + bx0];
-    }
-}
-
-__global__ void strip_compact_kernel(ProblemGeo g, int np, const int64_t* __restrict__ strip_off, int SW,
-                                     const int32_t* __restrict__ scan, int4* __restrict__ strips) {
-    griddep_wait();
-    const int64_t n = strip_off[np];
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        if (scan[q + 1] == scan[q]) continue;
-        const int p = upper_index(strip_off, np, q);
-        const int nn = 1 << g.L[p], nseg = (nn + SW - 1) / SW;
-        const int64_t r = q - strip_off[p];
-        strips[scan[q]] = make_int4(p, (int)(r / nseg), (int)(r % nseg) * SW, 0);
-    }
-}
-
-__global__ void gather_kernel(const int32_t* __restrict__ a, const int64_t* __restrict__ idx, int n,
-                              int32_t* __restrict__ out) {
-    griddep_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = a[idx[i]];
-}
-
 // ------------------------------------------------------------------------- sweeps
-// P2M: one warp per compact leaf.
+// P2M: one warp per compact leaf; its sources are [rl_s[j], rl_s[j + 1]), j = the leaf's
+// row-major index.
 template <typename T, int NP>
-__device__ __forceinline__ void p2m_list_warp(int64_t b, int lane, const int32_t* __restrict__ bp,
-                                              const int32_t* __restrict__ bxy, const ProblemGeo& g,
-                                              const int32_t* __restrict__ begin, const int32_t* __restrict__ loc,
+__device__ __forceinline__ void p2m_list_warp(int64_t b, int lane, const int32_t* __restrict__ leaf_rl,
+                                              const int32_t* __restrict__ rl_s, const int32_t* __restrict__ loc,
                                               const int32_t* __restrict__ perm, const double* __restrict__ f,
                                               T* __restrict__ f_sorted, const T* __restrict__ tofsT, int side,
                                               T* __restrict__ qhat, typename Mono<T>::V* __restrict__ Q) {
     using M = Mono<T>;
     constexpr int PL = NP / 32;
-    const int p = bp[b];
-    const int x = bxy[b] & 0xffff, y = bxy[b] >> 16;
-    const int64_t leaf = g.leaf_off[p] + ((int64_t)y << g.L[p]) + x;
-    const int s0 = begin[leaf], s1 = begin[leaf + 1];
+    const int j = leaf_rl[b];
+    const int s0 = rl_s[j], s1 = rl_s[j + 1];
     T acc[PL];
 #pragma unroll
     for (int i = 0; i < PL; ++i) acc[i] = T(0);
@@ -450,9 +84,8 @@ __device__ __forceinline__ void p2m_list_warp(int64_t b, int lane, const int32_t
 }
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t* __restrict__ bp,
-                                                       const int32_t* __restrict__ bxy, ProblemGeo g,
-                                                       const int32_t* __restrict__ begin,
+__global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t* __restrict__ leaf_rl,
+                                                       const int32_t* __restrict__ rl_s,
                                                        const int32_t* __restrict__ loc,
                                                        const int32_t* __restrict__ perm,
                                                        const double* __restrict__ f, T* __restrict__ f_sorted,
@@ -462,7 +95,7 @@ __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw)
-        p2m_list_warp<T, NP>(b, lane, bp, bxy, g, begin, loc, perm, f, f_sorted, tofsT, side, qhat, Q);
+        p2m_list_warp<T, NP>(b, lane, leaf_rl, rl_s, loc, perm, f, f_sorted, tofsT, side, qhat, Q);
 }
 
 // M2M: one warp per compact parent; children by compact id (-1: empty).
@@ -820,8 +453,7 @@ template <typename T>
 struct UpSweep {
     using V = typename Mono<T>::V;
     int64_t nb0;  // P2M: compact leaves (k = 0)
-    const int32_t *bp, *bxy, *begin, *loc, *perm;
-    ProblemGeo g;
+    const int32_t *leaf_rl, *rl_s, *loc, *perm;
     const double* f;
     T* f_sorted;
     const T* tofsT;
@@ -853,7 +485,7 @@ __global__ void __launch_bounds__(256) forest_up_kernel(const UpSweep<T> U, unsi
             const int64_t c1 = min((int64_t)c0 + kUpChunk, nb);
             for (int64_t b = (int64_t)c0; b < c1; ++b) {
                 if (k == 0)
-                    p2m_list_warp<T, NP>(b, lane, U.bp, U.bxy, U.g, U.begin, U.loc, U.perm, U.f, U.f_sorted, U.tofsT,
+                    p2m_list_warp<T, NP>(b, lane, U.leaf_rl, U.rl_s, U.loc, U.perm, U.f, U.f_sorted, U.tofsT,
                                          U.side, U.q[0], U.Q[0]);
                 else
                     m2m_list_warp<T, NP, true>(b, lane, U.ch[k], U.q[k - 1], U.m2m[k], U.Q[k - 1], U.q[k], U.Q[k]);
@@ -926,22 +558,17 @@ struct LStripCfg {
     static constexpr int CAPS = sizeof(T) == 4 ? 4096 : 2048;
     static constexpr int CAPT = 2048;
     static constexpr int MAXSW = 32;
-};
-
-struct LeafMap {  // compact leaf ids through the k = 0 map
-    const int32_t* map;
-    const int64_t* off;
-    int64_t S;
-    __device__ __forceinline__ int operator()(int p, int L, int x, int y) const {
-        return map[plane_entry(S, off[p], L, x, y)];
-    }
+    // the builder sizes strips with the smallest of these (kStripCapSrc: the binary64 case)
+    static_assert(MAXSW == kStripMaxSW && CAPT == kStripCapTgt && CAPS >= kStripCapSrc, "strip staging caps");
 };
 
 template <typename T, int NP>
 __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
-    const int4* __restrict__ strips, const int32_t* __restrict__ n_strips_d, ProblemGeo g, LeafMap lm, int side,
-    int SW, const int32_t* __restrict__ sbeg, const int32_t* __restrict__ sloc, const int32_t* __restrict__ tbeg,
-    const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm, const T* __restrict__ f_sorted,
+    const int4* __restrict__ strips, const int4* __restrict__ strip_rows, const int32_t* __restrict__ n_strips_d,
+    const int32_t* __restrict__ Lp, const uint64_t* __restrict__ rl_key, const int32_t* __restrict__ rl_s,
+    const int32_t* __restrict__ rl_t, const int32_t* __restrict__ rl_id, int kb, int side, int SW,
+    const int32_t* __restrict__ sloc, const int32_t* __restrict__ tloc, const int32_t* __restrict__ tperm,
+    const T* __restrict__ f_sorted,
     const T* __restrict__ table, int tab_H, int tab_W, const T* __restrict__ uhat,
     const typename Mono<T>::V* __restrict__ Cleaf, const typename Mono<T>::V* __restrict__ Qleaf,
     const T* __restrict__ tofsT, double* __restrict__ u, double* __restrict__ u_near, double* __restrict__ u_far) {
@@ -964,6 +591,8 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
     __shared__ int s_ra[Cfg::MAXSW][3], s_rl[Cfg::MAXSW][3];
     __shared__ double s_nc[Cfg::MAXSW];
     __shared__ int s_has[Cfg::MAXSW];
+    __shared__ int s_rj[3][2];                 // leaf-list range [j0, j1) of each row (-1: outside)
+    __shared__ int s_lc[3][Cfg::MAXSW + 2];    // column - c_lo of each listed leaf (ascending)
 
     for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
     const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
@@ -974,31 +603,57 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
     for (int strip = blockIdx.x; strip < n_strips; strip += gridDim.x) {
         const int4 sd = strips[strip];
         const int p = sd.x, by = sd.y, bx0 = sd.z;
-        const int L = g.L[p];
-        const int n = 1 << L;
-        const int64_t lo_leaf = g.leaf_off[p];
+        const int n = 1 << Lp[p];
         const int bx1 = min(bx0 + SW, n);
         const int c_lo = max(bx0 - 1, 0), c_hi = min(bx1, n - 1);
         const int ncol = c_hi - c_lo + 1;
         __syncthreads();
+        // the occupied leaves of the three row segments: short ascending lists, so each
+        // column below is a search in shared memory
+        if (threadIdx.x < 6) {
+            const int4 q = strip_rows[2 * (int64_t)strip + (threadIdx.x >> 2)];
+            const int e = threadIdx.x & 3;
+            s_rj[threadIdx.x >> 1][threadIdx.x & 1] = e == 0 ? q.x : e == 1 ? q.y : e == 2 ? q.z : q.w;
+        }
+        __syncthreads();
+        const uint64_t kmask = ((uint64_t)1 << kb) - 1;
+        for (int i = threadIdx.x; i < 3 * (Cfg::MAXSW + 2); i += blockDim.x) {
+            const int r = i / (Cfg::MAXSW + 2), q = i % (Cfg::MAXSW + 2);
+            const int j0 = s_rj[r][0];
+            if (j0 >= 0 && j0 + q < s_rj[r][1]) s_lc[r][q] = (int)(rl_key[j0 + q] & kmask) - c_lo;
+        }
+        __syncthreads();
+        // first listed leaf of row r at column >= c (the row's count if none)
+        auto first_at = [&](int r, int c) {
+            int lo = 0, hi = s_rj[r][1] - s_rj[r][0];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_lc[r][mid] < c) lo = mid + 1;
+                else hi = mid;
+            }
+            return lo;
+        };
         for (int i = threadIdx.x; i < 3 * (ncol + 1); i += blockDim.x) {
             const int r = i / (ncol + 1), c = i % (ncol + 1);
-            const int yy = by + r - 1;
-            s_sb[r * (Cfg::MAXSW + 3) + c] = (yy >= 0 && yy < n) ? sbeg[lo_leaf + (int64_t)yy * n + c_lo + c] : 0;
+            // first source at or after column c of the row (past its last column: the first
+            // source of the next occupied leaf, as in a dense bucket array)
+            const int j0 = s_rj[r][0];
+            s_sb[r * (Cfg::MAXSW + 3) + c] = j0 >= 0 ? rl_s[j0 + first_at(r, c)] : 0;
         }
-        for (int i = threadIdx.x; i <= bx1 - bx0; i += blockDim.x) s_tb[i] = tbeg[lo_leaf + (int64_t)by * n + bx0 + i];
+        for (int i = threadIdx.x; i <= bx1 - bx0; i += blockDim.x) s_tb[i] = rl_t[s_rj[1][0] + first_at(1, bx0 + i - c_lo)];
         for (int i = threadIdx.x; i < 3 * ncol; i += blockDim.x) {
             const int r = i / ncol, c = i % ncol;
-            const int yy = by + r - 1;
             V qv = M::zero();
-            if (yy >= 0 && yy < n) {
-                const int cid = lm(p, L, c_lo + c, yy);
-                if (cid >= 0) qv = Qleaf[cid];
+            const int j0 = s_rj[r][0];
+            if (j0 >= 0) {
+                const int q = first_at(r, c);
+                if (j0 + q < s_rj[r][1] && s_lc[r][q] == c) qv = Qleaf[rl_id[j0 + q]];
             }
             s_q[r * (Cfg::MAXSW + 2) + c] = qv;
         }
         for (int i = threadIdx.x; i < bx1 - bx0; i += blockDim.x) {
-            const int cid = lm(p, L, bx0 + i, by);
+            const int q = first_at(1, bx0 + i - c_lo);
+            const int cid = (s_rj[1][0] + q < s_rj[1][1] && s_lc[1][q] == bx0 + i - c_lo) ? rl_id[s_rj[1][0] + q] : -1;
             s_has[i] = cid;
             s_c[i] = (Cleaf && cid >= 0) ? Cleaf[cid] : M::zero();
         }
@@ -1138,41 +793,6 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
 }  // namespace
 
 // ------------------------------------------------------------------------- host side
-namespace {
-
-int alloc(std::vector<void*>& owned, int64_t& bytes, void** out, size_t n, cudaStream_t s) {
-    *out = nullptr;
-    cudaError_t e = dev_malloc(out, n ? n : 16, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *out = nullptr;
-        return fail(LFMM_ENOMEM, std::string("device allocation of ") + std::to_string(n) + " bytes failed: " +
-                                     cudaGetErrorString(e));
-    }
-    owned.push_back(*out);
-    bytes += (int64_t)(n ? n : 16);
-    return LFMM_OK;
-}
-
-cudaError_t exscan(const int32_t* in, int32_t* out, int64_t n, int32_t* sums, cudaStream_t s) {
-    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    if (nb == 0) return cudaMemsetAsync(out, 0, sizeof(int32_t), s);
-    (void)launch_dependent(scan_reduce_kernel, dim3((unsigned)nb), dim3(kThreads), 0, s, in, n, sums);
-    (void)launch_dependent(scan_sums_kernel, dim3(1), dim3(1024), 0, s, sums, (int)nb);
-    (void)launch_dependent(scan_apply_kernel, dim3((unsigned)nb), dim3(kThreads), 0, s, in, n, sums, out);
-    return cudaGetLastError();
-}
-
-int64_t exscan_tmp_ints(int64_t n) { return (n + kScanBlock - 1) / kScanBlock + 1; }
-
-int ceil_log2(int64_t v) {
-    int k = 0;
-    while (((int64_t)1 << k) < v) ++k;
-    return k;
-}
-
-}  // namespace
-
 void Forest::release(cudaStream_t s) {
     for (void* a : owned) cudaFreeAsync(a, s);
     owned.clear();
@@ -1195,311 +815,6 @@ int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms,
         if (nc > 1) need = std::max<int64_t>(need, (int64_t)nc * lv.nb * ((int64_t)NP * (int64_t)esz + 8));
     }
     return need;
-}
-
-int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
-                 const int64_t* toff_h, int64_t nt, int np, int leaf_size, int max_leaf_side, cudaStream_t s,
-                 PhaseTimer* timer) {
-    int st;
-    F.np = np;
-    F.ns = ns;
-    F.nt = nt;
-    if (ns > INT32_MAX / 2 || nt > INT32_MAX / 2) return fail(LFMM_EINVAL, "forest too large");
-    auto A = [&](void** p, size_t n) { return alloc(F.owned, F.bytes, p, n, s); };
-    void* v;
-    // problem offsets and per-point problem ids
-    if ((st = A(&v, (size_t)2 * (np + 1) * sizeof(int64_t)))) return st;
-    int64_t* soff = (int64_t*)v;
-    int64_t* toff = soff + (np + 1);
-    LFMM_CUDA_TRY(cudaMemcpyAsync(soff, soff_h, (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    LFMM_CUDA_TRY(cudaMemcpyAsync(toff, toff_h, (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    if ((st = A(&v, (size_t)(ns + nt) * sizeof(int32_t)))) return st;
-    F.spid = (int32_t*)v;
-    F.tpid = F.spid + ns;
-    if (np == 1) {
-        LFMM_CUDA_TRY(cudaMemsetAsync(F.spid, 0, (size_t)(ns + nt) * sizeof(int32_t), s));
-    } else {
-        (void)launch_dependent(pid_kernel, dim3(std::min(np, 152 * 8)), dim3(kThreads), 0, s, soff, np, F.spid);
-        (void)launch_dependent(pid_kernel, dim3(std::min(np, 152 * 8)), dim3(kThreads), 0, s, toff, np, F.tpid);
-    }
-    // bounding boxes
-    if ((st = A(&v, (size_t)np * sizeof(int4)))) return st;
-    int4* bb = (int4*)v;
-    if (np == 1) {
-        LFMM_CUDA_TRY(launch_set4((int*)bb, INT_MAX, INT_MAX, INT_MIN, INT_MIN, s));
-        LFMM_CUDA_TRY(launch_bbox(src, ns, tgt, nt, (int*)bb, s));
-    } else {
-        (void)launch_dependent(bbox_forest_kernel, dim3(std::min(np, 152 * 8)), dim3(kThreads), 0, s, (const int2*)src, soff, (const int2*)tgt,
-                                                                       toff, np, bb);
-    }
-    LFMM_CUDA_TRY(cudaGetLastError());
-    timer->add_launches(4);
-    std::vector<int4> hbb(np);
-    LFMM_CUDA_TRY(cudaMemcpyAsync(hbb.data(), bb, np * sizeof(int4), cudaMemcpyDeviceToHost, s));
-    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
-    F.x0.resize(np);
-    F.y0.resize(np);
-    F.K.resize(np);
-    int Kmax = 0;
-    for (int p = 0; p < np; ++p) {
-        const int4 b = hbb[p];
-        if (b.x > b.z) return fail(LFMM_EINVAL, "forest problem " + std::to_string(p) + " has no points");
-        F.x0[p] = b.x;
-        F.y0[p] = b.y;
-        const int64_t ext = std::max((int64_t)b.z - b.x, (int64_t)b.w - b.y) + 1;
-        if (ext > ((int64_t)1 << 30)) return fail(LFMM_EINVAL, "points span more than 2^30 lattice cells");
-        F.K[p] = ceil_log2(ext);
-        Kmax = std::max(Kmax, F.K[p]);
-    }
-    if ((st = A(&v, (size_t)3 * np * sizeof(int32_t)))) return st;
-    int32_t* dx0 = (int32_t*)v;
-    int32_t* dy0 = dx0 + np;
-    int32_t* dL = dy0 + np;
-    F.d_L = dL;
-    LFMM_CUDA_TRY(cudaMemcpyAsync(dx0, F.x0.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    LFMM_CUDA_TRY(cudaMemcpyAsync(dy0, F.y0.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-
-    // common leaf side: the largest power of two <= max_leaf_side (and <= every root
-    // that needs splitting) at which no leaf of any problem holds more than leaf_size
-    // sources or targets
-    int ls = ceil_log2(max_leaf_side);
-    if ((1 << ls) > max_leaf_side) --ls;
-    ls = std::min(ls, Kmax);
-    DevTemp counts;  // dense leaf counts of the accepted side
-    DevTemp ranks;   // each point's arrival rank in its leaf (sources, then targets)
-    LFMM_CUDA_TRY(dev_malloc(&ranks.ptr, (size_t)(ns + nt) * sizeof(int32_t), s));
-    ranks.s = s;
-    int32_t* rank_s = (int32_t*)ranks.ptr;
-    int32_t* rank_t = rank_s + ns;
-    std::vector<int64_t> leaf_off(np + 1);
-    int maxs = 0, maxt = 0;
-    for (;;) {
-        F.L.assign(np, 0);
-        leaf_off[0] = 0;
-        for (int p = 0; p < np; ++p) {
-            F.L[p] = std::max(0, F.K[p] - ls);
-            if (F.L[p] > 14) return fail(LFMM_EUNSUPPORTED, "forest problem needs more than 4^14 leaves");
-            leaf_off[p + 1] = leaf_off[p] + ((int64_t)1 << (2 * F.L[p]));
-        }
-        const int64_t NL = leaf_off[np];
-        if (NL > ((int64_t)1 << 28)) return fail(LFMM_EUNSUPPORTED, "forest has more than 2^28 leaves");
-        counts.reset(s);
-        LFMM_CUDA_TRY(dev_malloc(&counts.ptr, (size_t)(2 * NL + 2) * sizeof(int32_t) + (np + 1) * sizeof(int64_t), s));
-        counts.s = s;
-        int32_t* cs = (int32_t*)counts.ptr;
-        int32_t* ct = cs + NL;
-        int32_t* mx = ct + NL;
-        int64_t* dlo = (int64_t*)(mx + 2);
-        LFMM_CUDA_TRY(cudaMemsetAsync(cs, 0, (size_t)(2 * NL + 2) * sizeof(int32_t), s));
-        LFMM_CUDA_TRY(cudaMemcpyAsync(dL, F.L.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        LFMM_CUDA_TRY(cudaMemcpyAsync(dlo, leaf_off.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        ProblemGeo g{F.spid, dx0, dy0, dL, dlo};
-        (void)launch_dependent(count_forest_kernel, dim3(grid_for(ns, kThreads)), dim3(kThreads), 0, s, (const int2*)src, ns, g, ls, cs, rank_s);
-        g.pid = F.tpid;
-        (void)launch_dependent(count_forest_kernel, dim3(grid_for(nt, kThreads)), dim3(kThreads), 0, s, (const int2*)tgt, nt, g, ls, ct, rank_t);
-        (void)launch_dependent(max2_kernel, dim3(grid_for(NL, kThreads)), dim3(kThreads), 0, s, cs, ct, NL, mx);
-        LFMM_CUDA_TRY(cudaGetLastError());
-        timer->add_launches(3);
-        int hm[2];
-        LFMM_CUDA_TRY(cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, s));
-        LFMM_CUDA_TRY(cudaStreamSynchronize(s));
-        maxs = hm[0];
-        maxt = hm[1];
-        if (std::max(maxs, maxt) <= leaf_size || ls == 0) break;
-        --ls;
-    }
-    F.ls = ls;
-    F.side = 1 << ls;
-    F.max_src = maxs;
-    F.max_tgt = maxt;
-    F.leaf_off = leaf_off;
-    const int64_t NL = leaf_off[np];
-    F.NL = NL;
-    if ((st = A(&v, (size_t)(np + 1) * sizeof(int64_t)))) return st;
-    F.d_leaf_off = (int64_t*)v;
-    LFMM_CUDA_TRY(cudaMemcpyAsync(F.d_leaf_off, leaf_off.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    ProblemGeo g{F.spid, dx0, dy0, dL, F.d_leaf_off};
-    F.geo_x0 = dx0;
-    F.geo_y0 = dy0;
-    int32_t* cs = (int32_t*)counts.ptr;
-    int32_t* ct = cs + NL;
-
-    // buckets
-    if ((st = A(&v, (size_t)2 * (NL + 1) * sizeof(int32_t)))) return st;
-    F.sbeg = (int32_t*)v;
-    F.tbeg = F.sbeg + (NL + 1);
-    DevTemp tmp;
-    const int64_t big = std::max<int64_t>(NL, 1);
-    LFMM_CUDA_TRY(dev_malloc(&tmp.ptr, (size_t)exscan_tmp_ints(big) * sizeof(int32_t), s));
-    tmp.s = s;
-    int32_t* sums = (int32_t*)tmp.ptr;
-    LFMM_CUDA_TRY(exscan(cs, F.sbeg, NL, sums, s));
-    LFMM_CUDA_TRY(exscan(ct, F.tbeg, NL, sums, s));
-    if ((st = A(&v, (size_t)2 * (ns + nt) * sizeof(int32_t)))) return st;
-    F.sloc = (int32_t*)v;
-    F.sperm = F.sloc + ns;
-    F.tloc = F.sperm + ns;
-    F.tperm = F.tloc + nt;
-    g.pid = F.spid;
-    (void)launch_dependent(scatter_forest_kernel, dim3(grid_for(ns, kThreads)), dim3(kThreads), 0, s, (const int2*)src, ns, g, ls, F.sbeg, rank_s,
-                                                                       F.sloc, F.sperm);
-    g.pid = F.tpid;
-    (void)launch_dependent(scatter_forest_kernel, dim3(grid_for(nt, kThreads)), dim3(kThreads), 0, s, (const int2*)tgt, nt, g, ls, F.tbeg, rank_t,
-                                                                       F.tloc, F.tperm);
-    LFMM_CUDA_TRY(cudaGetLastError());
-    timer->add_launches(8);
-
-    // levels k = 0 .. kmax
-    int Lmax = 0;
-    for (int p = 0; p < np; ++p) Lmax = std::max(Lmax, F.L[p]);
-    F.kmax = Lmax - 2;  // may be negative: no far field anywhere
-    const int nk = std::max(F.kmax, 0) + 1;
-    F.levels.assign(nk, ForestLevel());
-    std::vector<std::vector<int64_t>> hoff(nk), hsize(nk);
-    int64_t flag_total = 0;
-    for (int k = 0; k < nk; ++k) {
-        ForestLevel& lv = F.levels[k];
-        hoff[k].assign(np, 0);
-        hsize[k].assign(np, 0);
-        int64_t S = 0;
-        for (int p = 0; p < np; ++p) {
-            const int l = F.L[p] - k;
-            const bool present = (k == 0) || (l >= 2);
-            hoff[k][p] = S;
-            if (present) hsize[k][p] = l >= 1 ? ((int64_t)1 << (2 * (l - 1))) : 1;
-            S += hsize[k][p];
-        }
-        lv.S = S;
-        flag_total += 4 * S + 1;
-    }
-    // device: per level off/size, map, scan
-    std::vector<int32_t*> scan(nk);
-    DevTemp lt;
-    {
-        int64_t ints = 0;
-        for (int k = 0; k < nk; ++k) ints += 4 * F.levels[k].S + 1;
-        LFMM_CUDA_TRY(dev_malloc(&lt.ptr, (size_t)(ints + 1) * sizeof(int32_t), s));
-        lt.s = s;
-        int32_t* q = (int32_t*)lt.ptr;
-        for (int k = 0; k < nk; ++k) {
-            scan[k] = q;
-            q += 4 * F.levels[k].S + 1;
-        }
-    }
-    int64_t maxflags = 1;
-    for (int k = 0; k < nk; ++k) maxflags = std::max(maxflags, 4 * F.levels[k].S);
-    DevTemp ssum;
-    LFMM_CUDA_TRY(dev_malloc(&ssum.ptr, (size_t)exscan_tmp_ints(maxflags) * sizeof(int32_t), s));
-    ssum.s = s;
-    for (int k = 0; k < nk; ++k) {
-        ForestLevel& lv = F.levels[k];
-        if ((st = A(&v, (size_t)2 * np * sizeof(int64_t)))) return st;
-        lv.off = (int64_t*)v;
-        lv.size = lv.off + np;
-        LFMM_CUDA_TRY(cudaMemcpyAsync(lv.off, hoff[k].data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        LFMM_CUDA_TRY(cudaMemcpyAsync(lv.size, hsize[k].data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        if ((st = A(&v, (size_t)4 * lv.S * sizeof(int32_t)))) return st;
-        lv.map = (int32_t*)v;
-        LevelGeo lg{k, np, lv.S, lv.off, lv.size};
-        if (k == 0) {
-            LFMM_CUDA_TRY(cudaMemsetAsync(lv.map, 0, (size_t)4 * lv.S * sizeof(int32_t), s));
-            g.pid = F.spid;
-            (void)launch_dependent(flag_leaves_kernel, dim3(grid_for(NL, kThreads)), dim3(kThreads), 0, s, cs, ct, NL, g, np, lg, lv.map);
-        } else {
-            const ForestLevel& lc = F.levels[k - 1];
-            LevelGeo lcg{k - 1, np, lc.S, lc.off, lc.size};
-            (void)launch_dependent(flag_parents_kernel, dim3(grid_for(4 * lv.S, kThreads)), dim3(kThreads), 0, s, g, lg, lcg, lc.map, lv.map);
-        }
-        LFMM_CUDA_TRY(exscan(lv.map, scan[k], 4 * lv.S, (int32_t*)ssum.ptr, s));
-        (void)launch_dependent(compact_kernel, dim3(grid_for(4 * lv.S, kThreads)), dim3(kThreads), 0, s, g, lg, scan[k], lv.map, nullptr, nullptr);
-        LFMM_CUDA_TRY(cudaGetLastError());
-        timer->add_launches(5);
-    }
-    // compact counts and class starts
-    std::vector<int64_t> idx;
-    for (int k = 0; k < nk; ++k)
-        for (int c = 0; c <= 4; ++c) idx.push_back((int64_t)(scan[k] - scan[0]) + c * F.levels[k].S);
-    DevTemp gi;
-    LFMM_CUDA_TRY(dev_malloc(&gi.ptr, idx.size() * (sizeof(int64_t) + sizeof(int32_t)), s));
-    gi.s = s;
-    int64_t* didx = (int64_t*)gi.ptr;
-    int32_t* dval = (int32_t*)(didx + idx.size());
-    LFMM_CUDA_TRY(cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    (void)launch_dependent(gather_kernel, dim3((unsigned)((idx.size() + 127) / 128)), dim3(128), 0, s, scan[0], didx, (int)idx.size(), dval);
-    LFMM_CUDA_TRY(cudaGetLastError());
-    std::vector<int32_t> hval(idx.size());
-    LFMM_CUDA_TRY(cudaMemcpyAsync(hval.data(), dval, hval.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    LFMM_CUDA_TRY(cudaStreamSynchronize(s));
-    F.total_boxes = 0;
-    for (int k = 0; k < nk; ++k) {
-        ForestLevel& lv = F.levels[k];
-        for (int c = 0; c <= 4; ++c) lv.cls[c] = hval[k * 5 + c];
-        lv.nb = lv.cls[4];
-        lv.box_off = F.total_boxes;
-        F.total_boxes += lv.nb;
-        if ((st = A(&v, (size_t)5 * sizeof(int64_t)))) return st;
-        lv.d_cls = (int64_t*)v;
-        LFMM_CUDA_TRY(cudaMemcpyAsync(lv.d_cls, lv.cls, 5 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        // box records, links
-        const size_t per = 2 + 1 + (k >= 1 ? 4 : 0) + 27;
-        if ((st = A(&v, (size_t)std::max<int64_t>(lv.nb, 1) * per * sizeof(int32_t)))) return st;
-        lv.bp = (int32_t*)v;
-        lv.bxy = lv.bp + lv.nb;
-        lv.par = lv.bxy + lv.nb;
-        lv.il = lv.par + lv.nb;
-        lv.ch = k >= 1 ? lv.il + lv.nb * 27 : nullptr;
-        LevelGeo lg{k, np, lv.S, lv.off, lv.size};
-        (void)launch_dependent(compact_kernel, dim3(grid_for(4 * lv.S, kThreads)), dim3(kThreads), 0, s, g, lg, scan[k], lv.map, lv.bp, lv.bxy);
-        LFMM_CUDA_TRY(cudaGetLastError());
-        timer->add_launches(1);
-    }
-    for (int k = 0; k < nk; ++k) {
-        ForestLevel& lv = F.levels[k];
-        if (lv.nb == 0) continue;
-        LevelGeo lg{k, np, lv.S, lv.off, lv.size};
-        const bool has_par = k + 1 < nk;
-        LevelGeo lpar = has_par ? LevelGeo{k + 1, np, F.levels[k + 1].S, F.levels[k + 1].off, F.levels[k + 1].size}
-                                : lg;
-        LevelGeo lch = k >= 1 ? LevelGeo{k - 1, np, F.levels[k - 1].S, F.levels[k - 1].off, F.levels[k - 1].size}
-                              : lg;
-        (void)launch_dependent(links_kernel, dim3(grid_for(lv.nb, kThreads)), dim3(kThreads), 0, s,
-            g, lg, lv.nb, lv.bp, lv.bxy, lv.map, lpar, has_par ? F.levels[k + 1].map : nullptr, lch,
-            k >= 1 ? F.levels[k - 1].map : nullptr, lv.par, lv.ch, lv.il);
-        LFMM_CUDA_TRY(cudaGetLastError());
-        timer->add_launches(1);
-    }
-
-    // strips of the near-field sweep
-    const int ms = std::max(1, maxs), mt = std::max(1, maxt);
-    int SW = std::min({LStripCfg<float>::MAXSW, LStripCfg<double>::CAPS / (3 * ms) - 2, LStripCfg<float>::CAPT / mt});
-    if (SW < 1) return fail(LFMM_EUNSUPPORTED, "leaves too full for the near-field staging (" + std::to_string(ms) +
-                                                   " sources / " + std::to_string(mt) + " targets)");
-    F.SW = SW;
-    std::vector<int64_t> soffs(np + 1, 0);
-    for (int p = 0; p < np; ++p) {
-        const int64_t nn = (int64_t)1 << F.L[p];
-        soffs[p + 1] = soffs[p] + nn * ((nn + SW - 1) / SW);
-    }
-    const int64_t ncand = soffs[np];
-    DevTemp sf;
-    LFMM_CUDA_TRY(dev_malloc(&sf.ptr, (size_t)(np + 1) * sizeof(int64_t) +
-                                               (size_t)(2 * ncand + 2 + exscan_tmp_ints(ncand)) * sizeof(int32_t), s));
-    sf.s = s;
-    int64_t* dsoff = (int64_t*)sf.ptr;
-    int32_t* sflag = (int32_t*)(dsoff + np + 1);
-    int32_t* sscan = sflag + ncand + 1;
-    int32_t* ssums = sscan + ncand + 1;
-    LFMM_CUDA_TRY(cudaMemcpyAsync(dsoff, soffs.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    (void)launch_dependent(strip_flag_kernel, dim3(grid_for(ncand, kThreads)), dim3(kThreads), 0, s, g, np, dsoff, SW, F.tbeg, sflag);
-    LFMM_CUDA_TRY(exscan(sflag, sscan, ncand, ssums, s));
-    if ((st = A(&v, (size_t)std::max<int64_t>(ncand, 1) * sizeof(int4) + 16))) return st;
-    F.strips = (int4*)v;
-    F.n_strips_d = (int32_t*)(F.strips + std::max<int64_t>(ncand, 1));
-    (void)launch_dependent(strip_compact_kernel, dim3(grid_for(ncand, kThreads)), dim3(kThreads), 0, s, g, np, dsoff, SW, sscan, F.strips);
-    LFMM_CUDA_TRY(cudaMemcpyAsync(F.n_strips_d, sscan + ncand, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    LFMM_CUDA_TRY(cudaGetLastError());
-    timer->add_launches(5);
-    return LFMM_OK;  // temporaries are freed in stream order
 }
 
 // Cooperative launch through the capturable launch API (the fused sweeps).
@@ -1525,7 +840,6 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
     using V = typename Mono<T>::V;
     const int NP = ops.NP;
     const int nk = (int)F.levels.size();
-    ProblemGeo g{F.spid, F.geo_x0, F.geo_y0, F.d_L, F.d_leaf_off};
     auto Qx = [&](int k) { return qhat + (size_t)F.levels[k].box_off * NP; };
     auto Ux = [&](int k) { return uhat + (size_t)F.levels[k].box_off * NP; };
     auto Qm = [&](int k) { return (V*)Qbox + F.levels[k].box_off; };
@@ -1538,12 +852,10 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         PhaseTimer pt(LFMM_PHASE_M2M, s);
         UpSweep<T> U;
         U.nb0 = F.levels[0].nb;
-        U.bp = F.levels[0].bp;
-        U.bxy = F.levels[0].bxy;
-        U.begin = F.sbeg;
+        U.leaf_rl = F.levels[0].rl;
+        U.rl_s = F.rl_s;
         U.loc = F.sloc;
         U.perm = F.sperm;
-        U.g = g;
         U.f = f;
         U.f_sorted = f_sorted;
         U.tofsT = (const T*)ops.tofsT;
@@ -1573,13 +885,11 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         if (l0.nb > 0) {
             int64_t blocks = std::min<int64_t>((l0.nb * 32 + 255) / 256, 152 * 64);
             if (NP == 32)
-                (void)launch_dependent(p2m_list_kernel<T, 32>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.bp, l0.bxy, g, F.sbeg, F.sloc, F.sperm,
-                                                                    f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0),
-                                                                    Qm(0));
+                (void)launch_dependent(p2m_list_kernel<T, 32>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.rl, F.rl_s,
+                                       F.sloc, F.sperm, f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0), Qm(0));
             else
-                (void)launch_dependent(p2m_list_kernel<T, 64>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.bp, l0.bxy, g, F.sbeg, F.sloc, F.sperm,
-                                                                    f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0),
-                                                                    Qm(0));
+                (void)launch_dependent(p2m_list_kernel<T, 64>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.rl, F.rl_s,
+                                       F.sloc, F.sperm, f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0), Qm(0));
             LFMM_CUDA_TRY(cudaGetLastError());
             pt.add_launches(1);
         }
@@ -1712,8 +1022,6 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                             (size_t)Cfg::MAXSW * NP * sizeof(T) +
                             (size_t)(3 * (Cfg::MAXSW + 2) + Cfg::MAXSW) * sizeof(V) + (size_t)2 * Cfg::CAPT * sizeof(int) +
                             (size_t)(3 * (Cfg::MAXSW + 3) + Cfg::MAXSW + 1) * sizeof(int);
-        const ForestLevel& l0 = F.levels[0];
-        LeafMap lm{l0.map, l0.off, l0.S};
         auto go = [&](auto np_tag) -> cudaError_t {
             constexpr int NPc = decltype(np_tag)::value;
             {
@@ -1722,7 +1030,8 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             }
             const int per_sm = blocks_per_sm((const void*)p2p_list_kernel<T, NPc>, Cfg::WARPS * 32, smem);
             (void)launch_dependent(p2p_list_kernel<T, NPc>, dim3(num_sms * per_sm), dim3(Cfg::WARPS * 32), smem, s,
-                F.strips, F.n_strips_d, g, lm, F.side, F.SW, F.sbeg, F.sloc, F.tbeg, F.tloc, F.tperm, f_sorted,
+                F.strips, F.strip_rows, F.n_strips_d, F.d_L, F.rl_key, F.rl_s, F.rl_t, F.rl_id, F.kb, F.side, F.SW,
+                F.sloc, F.tloc, F.tperm, f_sorted,
                 (const T*)ops.p2p_table, ops.tab_H, ops.tab_W, far ? Ux(0) : nullptr, far ? Cm(0) : nullptr, Qm(0),
                 (const T*)ops.tofsT, u, un, uf);
             return cudaGetLastError();

@@ -236,15 +236,11 @@ struct DevTemp {
     }
 };
 
-// Boxes k levels above the leaves over all problems of a forest.  The dense map lists
-// every cell of the level in parity-plane order (class c = (x & 1) + 2 (y & 1), then
-// problem, then the (x >> 1, y >> 1) grid row by row); compact ids number the
-// non-empty boxes in that order, so each parity class is one contiguous range.
+// Boxes of level k (k = levels above the leaves) over all problems of a pruned tree or
+// forest.  Compact ids number the non-empty boxes (a source or target below them) in
+// parity-class order (class c = (x & 1) + 2 (y & 1), then problem, then the (x >> 1,
+// y >> 1) grid row by row), so each parity class is one contiguous range.
 struct ForestLevel {
-    int64_t S = 0;             // map entries per class segment
-    int64_t* off = nullptr;    // [np] start of each problem inside a class segment (device)
-    int64_t* size = nullptr;   // [np] entries of each problem per class (0: not at this level)
-    int32_t* map = nullptr;    // [4 S] compact id or -1 (device)
     int64_t nb = 0;            // compact boxes
     int64_t cls[5] = {0};      // class ranges of the compact ids (host)
     int64_t* d_cls = nullptr;  // same on the device
@@ -254,33 +250,45 @@ struct ForestLevel {
     int32_t* par = nullptr;    // [nb] parent's compact id at k + 1, or -1
     int32_t* il = nullptr;     // [nb][27] interaction list (slot order of the box's class)
     int32_t* ch = nullptr;     // [nb][4] children's compact ids at k - 1 (k >= 1), -1 if empty
+    int32_t* rl = nullptr;     // k = 0: [nb] the leaf's index in the row-major leaf list
 };
+
+// Near-field staging of the pruned / forest strip kernel: leaves per strip and staged
+// sources and targets per block.
+constexpr int kStripMaxSW = 32;
+constexpr int kStripCapSrc = 2048;
+constexpr int kStripCapTgt = 2048;
 
 struct Forest {
     int np = 0;
     int64_t ns = 0, nt = 0;
     int ls = 0, side = 1;                   // common leaf side 2^ls
     std::vector<int32_t> x0, y0, K, L;      // per problem: root corner, root 2^K, leaf level
-    std::vector<int64_t> leaf_off;          // [np + 1] first absolute leaf of each problem
-    int64_t NL = 0;                         // leaves over all problems (dense per problem)
+    int kb = 1;                             // bits per coordinate in packed box keys
     int kmax = -1;                          // deepest k with expansions (levels >= 2)
     int max_src = 0, max_tgt = 0;           // largest leaf occupancies
     int SW = 1;                             // leaves per near-field strip
     int64_t total_boxes = 0;                // expansion rows over all levels
     std::vector<ForestLevel> levels;        // k = 0 .. max(kmax, 0)
     // device
-    int32_t *spid = nullptr, *tpid = nullptr;
-    int32_t *geo_x0 = nullptr, *geo_y0 = nullptr, *d_L = nullptr;
-    int64_t* d_leaf_off = nullptr;
-    int32_t *sbeg = nullptr, *tbeg = nullptr;   // [NL + 1] absolute bucket starts
+    int32_t* d_L = nullptr;                 // [np] leaf level of each problem
+    // occupied leaves in row-major order per problem, keys (p << 2 kb) | (y << kb) | x:
+    // first sorted source and target of each ([n_leaves] = totals) and compact id
+    int64_t n_leaves = 0;
+    uint64_t* rl_key = nullptr;
+    int32_t *rl_s = nullptr, *rl_t = nullptr, *rl_id = nullptr;
     int32_t *sloc = nullptr, *sperm = nullptr, *tloc = nullptr, *tperm = nullptr;
     int4* strips = nullptr;                     // (problem, leaf row, first column, 0)
+    // per strip, the leaves of its three neighbour-row segments (columns first - 1 ..
+    // first + SW): [j0, j1) in the occupied-leaf list for each row, -1 outside the tree;
+    // 2 int4 per strip {j0 r0, j1 r0, j0 r1, j1 r1}, {j0 r2, j1 r2, 0, 0}
+    int4* strip_rows = nullptr;
     int32_t* n_strips_d = nullptr;
     std::vector<void*> owned;
     int64_t bytes = 0;
     void* m2l_part = nullptr;               // partial sums of K-split list M2L levels (plan-owned)
     int m2l_split = 0;                      // opts.m2l_split (0: chunks by the number of tiles)
-    unsigned long long* sweep_ctr = nullptr;  // work-queue counters of the fused sweeps (2 x 16, plan-owned)
+    unsigned long long* sweep_ctr = nullptr;  // work-queue counters of the persistent sweeps (2 x 16)
     void release(cudaStream_t s);
 };
 
