@@ -1,23 +1,29 @@
 // Construction of pruned quadtrees and forests (Sec. 6, Def. 6.1) in O(N log N) work:
-// every structure comes from sorting packed box keys, none from dense per-level maps.
+// every structure comes from sorted packed box keys or, for forests of small problems,
+// from counts on each problem's dense leaf grid - never from dense maps of a deep level.
 //
 // A box of problem p at coordinates (x, y) of its level packs into the 64-bit key
 // (p << 2 kb) | (y << kb) | x, kb = bits of the deepest leaf level, so a sorted key array
 // lists the boxes of each problem row by row.  The builder
 //   1. picks the common leaf side (the largest power of two <= max_leaf_side at which no
-//      leaf holds more than leaf_size sources or targets) from sorted leaf keys of the
-//      points: a run of equal keys is one leaf;
-//   2. keeps the points in that order (row-major leaves per problem, so the sources of a
-//      leaf row segment are one contiguous range) and lists the occupied leaves (a source
-//      or a target) with their first source and target;
-//   3. derives each coarser level's boxes by halving the coordinates and sorting again,
-//      numbers every level's boxes in parity-class order (class, problem, (y >> 1,
-//      x >> 1) row by row: each class one contiguous range of compact ids), and finds
-//      parents, children and interaction lists by binary search in the level's sorted
-//      keys;
-//   4. lists the near-field strips (SW consecutive leaves of a row holding a target).
+//      leaf holds more than leaf_size sources or targets): on the problems' dense leaf
+//      grids when their cells are few (occupancy counts), else from sorted leaf keys of
+//      the points (a run of equal keys is one leaf);
+//   2. puts the points in row-major leaf order per problem (a counting sort on the dense
+//      grids, else the sorted keys), so the sources of a leaf row segment are one
+//      contiguous range, and lists the occupied leaves with their first source and
+//      target;
+//   3. builds the boxes of every level at once: each leaf emits its level-k key where it
+//      heads its level-k row segment, one sort and one unique pass give every level's
+//      boxes; a second sort numbers each level's boxes in parity-class order (class,
+//      problem, (y >> 1, x >> 1) row by row: each class one contiguous range of compact
+//      ids), and one kernel finds parents, children and interaction lists by binary
+//      search;
+//   4. lists the near-field strips (SW consecutive leaves of a row holding a target) and
+//      the occupied leaves of each strip's three neighbour-row segments.
 // The sorts are a stable least-significant-digit radix sort (8-bit digits, per-block
-// digit counts, one exclusive scan, ranked scatter).
+// digit counts, one exclusive scan, ranked scatter).  When targets equal sources (same
+// offsets and coordinates) one order serves both.
 #include <algorithm>
 #include <climits>
 
@@ -555,6 +561,55 @@ __global__ void dense_count_kernel(const int2* __restrict__ xy, int64_t n, const
     }
 }
 
+// Counting sort on the dense leaf grids: each point takes the next slot of its leaf
+// (cursor = the leaf's first slot, advanced atomically), so points come out row-major by
+// leaf per problem, in arrival order inside a leaf; loc = lx | ly << 16, perm = the
+// caller's index.
+__global__ void dense_scatter_kernel(const int2* __restrict__ xy, int64_t n, const int32_t* __restrict__ pid,
+                                     const int32_t* __restrict__ x0, const int32_t* __restrict__ y0,
+                                     const int32_t* __restrict__ L, const int64_t* __restrict__ cell_off, int ls,
+                                     int32_t* __restrict__ cursor, int32_t* __restrict__ loc,
+                                     int32_t* __restrict__ perm) {
+    const int mask = (1 << ls) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = pid[i];
+        const int2 v = xy[i];
+        const int64_t dx = (int64_t)v.x - x0[p], dy = (int64_t)v.y - y0[p];
+        const int pos = atomicAdd(cursor + cell_off[p] + ((dy >> ls) << L[p]) + (dx >> ls), 1);
+        loc[pos] = (int)(dx & mask) | ((int)(dy & mask) << 16);
+        perm[pos] = (int32_t)i;
+    }
+}
+
+// 1 where a dense leaf holds a source or a target
+__global__ void occupied_flag_kernel(const int32_t* __restrict__ cs, const int32_t* __restrict__ ct, int64_t cells,
+                                     int32_t* __restrict__ flag) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x)
+        flag[c] = (cs[c] + (ct ? ct[c] : 0)) > 0 ? 1 : 0;
+}
+
+// occupied leaf j (dense cell c, pos[c] = j): key, first source and first target
+__global__ void occupied_compact_kernel(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                        int64_t cells, const int64_t* __restrict__ cell_off, int np,
+                                        const int32_t* __restrict__ L, int kb, const int32_t* __restrict__ ss,
+                                        const int32_t* __restrict__ ts, uint64_t* __restrict__ key,
+                                        int32_t* __restrict__ rs, int32_t* __restrict__ rt) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[c]) continue;
+        int lo = 0, hi = np;  // problem p: cell_off[p] <= c < cell_off[p + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (cell_off[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        const int64_t r = c - cell_off[lo];
+        const int j = pos[c];
+        key[j] = pack_key(lo, (int)(r >> L[lo]), (int)(r & (((int64_t)1 << L[lo]) - 1)), kb);
+        rs[j] = ss[c];
+        rt[j] = ts[c];
+    }
+}
+
 // *mx = max(*mx, largest count)
 __global__ void max_count_kernel(const int32_t* __restrict__ cnt, int64_t n, int* __restrict__ mx) {
     int best = 0;
@@ -791,7 +846,9 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     if ((1 << ls) > max_leaf_side) --ls;
     ls = std::min(ls, Kmax);
     int maxs = 0, maxt = 0, kb = 1;
-    bool sorted = false;
+    bool dense = false;             // the final side was checked on dense grids (kept in cbk)
+    DevBuf cbk;
+    int64_t cells_k = 0;
     auto sort_side = [&](bool is_src, int bits, int* maxrun) -> int {
         const int64_t n = is_src ? ns : nt;
         uint64_t* k = is_src ? sk : tk;
@@ -829,8 +886,9 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
             return fail(LFMM_EUNSUPPORTED, "forest problem needs more than 2^20 leaves per side");
         LFMM_CUDA_TRY(cudaMemcpyAsync(dL, F.L.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         const int bits = pbits + 2 * kb;
-        if (cells <= std::max<int64_t>(2 * (ns + nt), (int64_t)1 << 22)) {
-            DevBuf cb;
+        dense = cells <= std::max<int64_t>(2 * (ns + nt), (int64_t)1 << 22);
+        DevBuf cb;
+        if (dense) {
             if ((st = cb.get((size_t)(np + 1) * sizeof(int64_t) + (size_t)2 * cells * sizeof(int32_t) + 16, s))) return st;
             int64_t* doff = (int64_t*)cb.ptr;
             int32_t* cnt = (int32_t*)(doff + np + 1);
@@ -851,14 +909,19 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
             timer->add_launches(4);
             maxs = h[0];
             maxt = same ? h[0] : h[1];
-            sorted = false;
         } else {
             if ((st = sort_side(true, bits, &maxs))) return st;
             if (same) maxt = maxs;
             else if ((st = sort_side(false, bits, &maxt))) return st;
-            sorted = true;
         }
-        if (std::max(maxs, maxt) <= leaf_size || ls == 0) break;
+        if (std::max(maxs, maxt) <= leaf_size || ls == 0) {
+            if (dense) {  // keep the grids' offsets and counts for the counting sort
+                std::swap(cbk.ptr, cb.ptr);
+                cbk.s = s;
+                cells_k = cells;
+            }
+            break;
+        }
         --ls;
     }
     F.ls = ls;
@@ -869,50 +932,87 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     const int kbits = pbits + 2 * kb;          // bits of a packed key
     int Lmax = 0;
     for (int p = 0; p < np; ++p) Lmax = std::max(Lmax, F.L[p]);
-    if (!sorted) {
-        if ((st = sort_side(true, kbits, nullptr))) return st;
-        if (!same && (st = sort_side(false, kbits, nullptr))) return st;
-    }
-
     // ---- 2. points in leaf order, occupied leaves with their first source and target
     void* vp;
     if ((st = alloc(F, &vp, (size_t)2 * (ns + (same ? 0 : nt)) * sizeof(int32_t), s))) return st;
     F.sloc = (int32_t*)vp;
     F.sperm = F.sloc + ns;
-    point_order_kernel<<<grid_of(ns), kT, 0, s>>>((const int2*)src, ns, sv, spid, dx0, dy0, ls, F.sloc, F.sperm);
-    if (same) {
-        F.tloc = F.sloc;
-        F.tperm = F.sperm;
-    } else {
-        F.tloc = F.sperm + ns;
-        F.tperm = F.tloc + nt;
-        point_order_kernel<<<grid_of(nt), kT, 0, s>>>((const int2*)tgt, nt, tv, tpid, dx0, dy0, ls, F.tloc, F.tperm);
-    }
-    LFMM_CUDA_TRY(cudaGetLastError());
+    F.tloc = same ? F.sloc : F.sperm + ns;
+    F.tperm = same ? F.sperm : F.tloc + nt;
     int M = 0;
-    if (same) {
-        if ((st = alloc(F, &vp, (size_t)(ns + 1) * sizeof(uint64_t), s))) return st;
+    if (dense) {
+        // counting sort on the grids: first slot of every leaf by one exclusive scan of the
+        // counts, points placed by atomic cursors; occupied leaves by one compaction
+        const int64_t cells = cells_k;
+        if (cells > INT32_MAX / 2) return fail(LFMM_EUNSUPPORTED, "forest leaf grids too large");
+        int64_t* doff = (int64_t*)cbk.ptr;
+        int32_t* cs = (int32_t*)(doff + np + 1);
+        int32_t* ct = same ? nullptr : cs + cells;
+        DevBuf gb;
+        const int64_t sc = scan_tmp_ints(cells);
+        if ((st = gb.get((size_t)(4 * (cells + 1) + 2 * sc) * sizeof(int32_t), s))) return st;
+        int32_t* ss = (int32_t*)gb.ptr;      // [cells + 1] first source of each leaf
+        int32_t* ts = ss + (cells + 1);      // [cells + 1] first target (targets != sources)
+        int32_t* gflag = ts + (cells + 1);
+        int32_t* gpos = gflag + (cells + 1);
+        int32_t* gsum = gpos + (cells + 1);
+        // occupied leaves before the counts turn into cursors
+        occupied_flag_kernel<<<grid_of(cells), kT, 0, s>>>(cs, ct, cells, gflag);
+        LFMM_CUDA_TRY(exscan(gflag, gpos, cells, gsum, s));
+        LFMM_CUDA_TRY(exscan(cs, ss, cells, gsum + sc, s));
+        if (!same) LFMM_CUDA_TRY(exscan(ct, ts, cells, gsum + sc, s));
+        LFMM_CUDA_TRY(cudaMemcpyAsync(&M, gpos + cells, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LFMM_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((st = alloc(F, &vp, (size_t)(M + 1) * sizeof(uint64_t), s))) return st;
         F.rl_key = (uint64_t*)vp;
-        if ((st = unique_runs(sk, ns, ~0ull, F.rl_key, nullptr, flag, pos, ssum, &M, s))) return st;
+        if ((st = alloc(F, &vp, (size_t)(same ? 2 : 3) * (M + 1) * sizeof(int32_t), s))) return st;
+        F.rl_s = (int32_t*)vp;
+        F.rl_id = F.rl_s + (M + 1);
+        F.rl_t = same ? F.rl_s : F.rl_id + (M + 1);
+        occupied_compact_kernel<<<grid_of(cells), kT, 0, s>>>(gflag, gpos, cells, doff, np, dL, kb, ss, same ? ss : ts,
+                                                              F.rl_key, F.rl_s, F.rl_t);
+        LFMM_CUDA_TRY(cudaMemcpyAsync(F.rl_s + M, ss + cells, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        if (!same) LFMM_CUDA_TRY(cudaMemcpyAsync(F.rl_t + M, ts + cells, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        // the counts become cursors (each leaf's first slot), then the points are placed
+        LFMM_CUDA_TRY(cudaMemcpyAsync(cs, ss, (size_t)cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        dense_scatter_kernel<<<grid_of(ns), kT, 0, s>>>((const int2*)src, ns, spid, dx0, dy0, dL, doff, ls, cs, F.sloc,
+                                                        F.sperm);
+        if (!same) {
+            LFMM_CUDA_TRY(cudaMemcpyAsync(ct, ts, (size_t)cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            dense_scatter_kernel<<<grid_of(nt), kT, 0, s>>>((const int2*)tgt, nt, tpid, dx0, dy0, dL, doff, ls, ct,
+                                                            F.tloc, F.tperm);
+        }
+        LFMM_CUDA_TRY(cudaGetLastError());
+        timer->add_launches(16);
     } else {
-        // unique source leaves and unique target leaves, merged by one more sort
-        int mm = 0, mt = 0;
-        if ((st = unique_runs(sk, ns, ~0ull, kspare, nullptr, flag, pos, ssum, &mm, s))) return st;
-        if ((st = unique_runs(tk, nt, ~0ull, kspare + mm, nullptr, flag, pos, ssum, &mt, s))) return st;
-        LFMM_CUDA_TRY(radix_sort(kspare, nullptr, (int64_t)mm + mt, kbits, sbuf, s));
-        if ((st = alloc(F, &vp, (size_t)(mm + mt + 1) * sizeof(uint64_t), s))) return st;
-        F.rl_key = (uint64_t*)vp;
-        if ((st = unique_runs(kspare, (int64_t)mm + mt, ~0ull, F.rl_key, nullptr, flag, pos, ssum, &M, s))) return st;
+        point_order_kernel<<<grid_of(ns), kT, 0, s>>>((const int2*)src, ns, sv, spid, dx0, dy0, ls, F.sloc, F.sperm);
+        if (!same)
+            point_order_kernel<<<grid_of(nt), kT, 0, s>>>((const int2*)tgt, nt, tv, tpid, dx0, dy0, ls, F.tloc, F.tperm);
+        LFMM_CUDA_TRY(cudaGetLastError());
+        if (same) {
+            if ((st = alloc(F, &vp, (size_t)(ns + 1) * sizeof(uint64_t), s))) return st;
+            F.rl_key = (uint64_t*)vp;
+            if ((st = unique_runs(sk, ns, ~0ull, F.rl_key, nullptr, flag, pos, ssum, &M, s))) return st;
+        } else {
+            // unique source leaves and unique target leaves, merged by one more sort
+            int mm = 0, mt = 0;
+            if ((st = unique_runs(sk, ns, ~0ull, kspare, nullptr, flag, pos, ssum, &mm, s))) return st;
+            if ((st = unique_runs(tk, nt, ~0ull, kspare + mm, nullptr, flag, pos, ssum, &mt, s))) return st;
+            LFMM_CUDA_TRY(radix_sort(kspare, nullptr, (int64_t)mm + mt, kbits, sbuf, s));
+            if ((st = alloc(F, &vp, (size_t)(mm + mt + 1) * sizeof(uint64_t), s))) return st;
+            F.rl_key = (uint64_t*)vp;
+            if ((st = unique_runs(kspare, (int64_t)mm + mt, ~0ull, F.rl_key, nullptr, flag, pos, ssum, &M, s))) return st;
+        }
+        if ((st = alloc(F, &vp, (size_t)(same ? 2 : 3) * (M + 1) * sizeof(int32_t), s))) return st;
+        F.rl_s = (int32_t*)vp;
+        F.rl_id = F.rl_s + (M + 1);
+        F.rl_t = same ? F.rl_s : F.rl_id + (M + 1);
+        leaf_ranges_kernel<<<grid_of(M + 1), kT, 0, s>>>(F.rl_key, M, sk, ns, same ? sk : tk, same ? ns : nt, F.rl_s,
+                                                         F.rl_t);
+        LFMM_CUDA_TRY(cudaGetLastError());
+        timer->add_launches(12);
     }
     F.n_leaves = M;
-    if ((st = alloc(F, &vp, (size_t)(same ? 2 : 3) * (M + 1) * sizeof(int32_t), s))) return st;
-    F.rl_s = (int32_t*)vp;
-    F.rl_id = F.rl_s + (M + 1);
-    F.rl_t = same ? F.rl_s : F.rl_id + (M + 1);
-    leaf_ranges_kernel<<<grid_of(M + 1), kT, 0, s>>>(F.rl_key, M, sk, ns, same ? sk : tk, same ? ns : nt, F.rl_s,
-                                                     F.rl_t);
-    LFMM_CUDA_TRY(cudaGetLastError());
-    timer->add_launches(12);
 
     // ---- 3. boxes of every level: A = the leaves (k = 0), then the boxes of levels
     // k = 1 .. kmax, sorted by (k, problem, row, column); compact ids number each level's
