@@ -73,7 +73,9 @@ typedef struct lfmm_opts {
     int32_t proxies_per_edge; /* proxy points per edge of the proxy ring of Sec. 5 (>= 8);     */
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
     int32_t tc_min_level;     /* mixed path: tree levels >= this run M2L on the tensor cores  */
-                              /* (0 = default 7; a value > 30 disables them)                  */
+                              /* (0 = default 7; a value > 30 disables them); pruned storage  */
+                              /* and forests (P_pad 32): every list level of >= 1024 boxes    */
+                              /* runs there unless this is > 30                               */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
     int32_t flags;            /* bitwise OR of LFMM_FLAG_* (0: none)                           */
     /* M2L tiling (0 everywhere: the library's rules; lfmm_autotune picks these).  They    */
@@ -84,7 +86,9 @@ typedef struct lfmm_opts {
                               /* this and the class row allow); 0: as wide as possible       */
     int32_t m2l_stages;       /* tensor-core M2L: depth of the TMA ring, 2, 3 or 4 (0: 3)      */
     int32_t m2l_split;        /* coarse-level and list M2L kernels: chunks the 27 interaction  */
-                              /* offsets are split into, 1 .. 9 (0: by the number of tiles)   */
+                              /* offsets are split into, 1 .. 9 (0: by the number of tiles); */
+                              /* list levels whose 32-box tiles fill the GPU three times over */
+                              /* are never split                                              */
     int32_t reserved;         /* must be 0                                                     */
 } lfmm_opts;
 

@@ -148,6 +148,7 @@ void release_aux(AuxStream* a) {
 }
 
 constexpr int kMaxLevel = 14;  // deepest leaf level searched (pruned storage beyond 4^13 leaves)
+constexpr int kMaxTreeLevelForTc = 30;  // opts.tc_min_level above this: no level on the tensor cores
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
@@ -314,6 +315,19 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
         F.m2l_split = p->opts.m2l_split;
         const int64_t sb = forest_m2l_split_bytes(F, p->NP, esz, p->num_sms, F.m2l_split);
         if (sb > 0 && (st = palloc(p, &F.m2l_part, (size_t)sb, s))) return st;
+    }
+    // tensor-core list M2L of the large levels (mixed path, P_pad 32; opts.tc_min_level
+    // beyond every tree level keeps them on the CUDA cores): TF32 hi / lo rows
+    F.tc_list = p->opts.precision == LFMM_MIXED && p->NP == 32 && p->opts.tc_min_level <= kMaxTreeLevelForTc;
+    if (F.tc_list) {
+        int64_t need = 0;
+        const int nk = (int)F.levels.size();
+        for (int k = 0; k < nk && F.kmax >= 0; ++k)
+            if (F.levels[k].nb >= kTcListMinBoxes)
+                need = std::max(need, m2l_tc_list_split_floats(F.levels[k].nb, k + 1 < nk ? F.levels[k + 1].nb : 0));
+        void* b = nullptr;
+        if (need > 0 && (st = palloc(p, &b, (size_t)need * sizeof(float), s))) return st;
+        F.tc_split = (float*)b;
     }
     if ((st = palloc(p, &p->Qbox, (size_t)boxes * 8, s))) return st;
     if ((st = palloc(p, &p->Cbox, (size_t)boxes * 8, s))) return st;
@@ -662,7 +676,7 @@ template <typename T>
 int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, cudaStream_t s) {
     if (p->forest)
         return forest_eval<T>(*p->forest, *p->ops, f, (T*)p->f_sorted, (T*)p->qhat, (T*)p->uhat, p->Qbox, p->Cbox,
-                              u, un, uf, p->num_sms, s, (p->opts.flags & LFMM_FLAG_PERSISTENT) ? p->status : nullptr);
+                              u, un, uf, p->num_sms, s, p->status, (p->opts.flags & LFMM_FLAG_PERSISTENT) != 0);
     const TreeView t = tree_view(p);
     const DeviceOps& ops = *p->ops;
     const int NP = p->NP;

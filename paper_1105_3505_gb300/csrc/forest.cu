@@ -799,10 +799,13 @@ void Forest::release(cudaStream_t s) {
     levels.clear();
 }
 
+// K chunks of a list M2L level: 1 for levels whose 32-box tiles fill the grid three
+// times over; for the others the caller's choice (opts.m2l_split), else enough chunks to
+// fill it (at most 7).
 int m2l_list_chunks(int64_t maxc, int num_sms, int split) {
-    if (split > 0) return std::min(split, 7);  // chosen by the caller (opts.m2l_split)
     const int64_t blocks = 4 * ((maxc + 31) / 32);
     if (blocks == 0 || blocks >= 3 * (int64_t)num_sms) return 1;
+    if (split > 0) return std::min(split, 7);
     return (int)std::min<int64_t>(7, (3 * (int64_t)num_sms + blocks - 1) / blocks);
 }
 
@@ -836,7 +839,9 @@ static cudaError_t launch_coop(const void* fn, int grid, int threads, size_t sme
 
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status) {
+                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status_word,
+                bool persistent) {
+    int* status = persistent ? status_word : nullptr;
     using V = typename Mono<T>::V;
     const int NP = ops.NP;
     const int nk = (int)F.levels.size();
@@ -977,7 +982,6 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         }
     }
     if (far && !down_done) {
-        PhaseTimer pt(LFMM_PHASE_M2L, s);
         for (int k = nk - 1; k >= 0; --k) {
             const ForestLevel& lv = F.levels[k];
             if (lv.nb == 0) continue;
@@ -985,6 +989,19 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             int64_t maxc = 0;
             for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
             if (maxc == 0) continue;
+            if constexpr (std::is_same<T, float>::value) {
+                if (F.tc_list && F.tc_split && NP == 32 && lv.nb >= kTcListMinBoxes && status_word) {
+                    PhaseTimer pt(LFMM_PHASE_M2L_TC, s);
+                    const cudaError_t e = launch_m2l_tc_list(
+                        ops, k, lv.d_cls, lv.cls, lv.il, l2l ? lv.par : nullptr, Qx(k), lv.nb, Qm(k),
+                        l2l ? Ux(k + 1) : nullptr, l2l ? F.levels[k + 1].nb : 0, l2l ? Cm(k + 1) : nullptr, Ux(k), Cm(k),
+                        F.tc_split, status_word, num_sms, s);
+                    if (e != cudaSuccess) return fail(LFMM_ECUDA, std::string("m2l_tc_list_kernel: ") + cudaGetErrorString(e));
+                    pt.add_launches(l2l ? 3 : 2);
+                    continue;
+                }
+            }
+            PhaseTimer pt(LFMM_PHASE_M2L, s);
             const int nc = F.m2l_part ? m2l_list_chunks(maxc, num_sms, F.m2l_split) : 1;
             dim3 grid((unsigned)((maxc + 31) / 32), 4, (unsigned)nc);
             T* part = nc > 1 ? (T*)F.m2l_part : nullptr;
@@ -1044,10 +1061,10 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
 }
 
 template int forest_eval<float>(const Forest&, const DeviceOps&, const double*, float*, float*, float*, void*, void*,
-                                double*, double*, double*, int, cudaStream_t, int*);
+                                double*, double*, double*, int, cudaStream_t, int*, bool);
 template int forest_eval<double>(const Forest&, const DeviceOps&, const double*, double*, double*, double*, void*,
-                                 void*, double*, double*, double*, int, cudaStream_t, int*);
+                                 void*, double*, double*, double*, int, cudaStream_t, int*, bool);
 template int forest_eval<DF>(const Forest&, const DeviceOps&, const double*, DF*, DF*, DF*, void*, void*, double*,
-                             double*, double*, int, cudaStream_t, int*);
+                             double*, double*, int, cudaStream_t, int*, bool);
 
 }  // namespace lfmm

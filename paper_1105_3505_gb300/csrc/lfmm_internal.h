@@ -289,6 +289,8 @@ struct Forest {
     void* m2l_part = nullptr;               // partial sums of K-split list M2L levels (plan-owned)
     int m2l_split = 0;                      // opts.m2l_split (0: chunks by the number of tiles)
     unsigned long long* sweep_ctr = nullptr;  // work-queue counters of the persistent sweeps (2 x 16)
+    bool tc_list = false;                   // list M2L of large levels on the tensor cores (mixed, P_pad 32)
+    float* tc_split = nullptr;              // TF32 hi / lo rows of those levels (plan-owned)
     void release(cudaStream_t s);
 };
 
@@ -304,11 +306,27 @@ int64_t forest_m2l_split_bytes(const Forest& F, int NP, size_t esz, int num_sms,
 int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t ns, const int32_t* tgt,
                  const int64_t* toff_h, int64_t nt, int np, int leaf_size, int max_leaf_side, cudaStream_t s,
                  PhaseTimer* timer);
-// status: the plan's status word (grid-barrier words beside it) to run each sweep as one
-// persistent cooperative launch (LFMM_FLAG_PERSISTENT); NULL: one launch per level.
+// status: the plan's status word (grid-barrier words beside it; timed-out waits are
+// recorded there); persistent: run each sweep as one persistent cooperative launch
+// (LFMM_FLAG_PERSISTENT), else one launch per level, the list M2L of levels with at
+// least kTcListMinBoxes boxes on the tensor cores when F.tc_list is set.
 template <typename T>
 int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sorted, T* qhat, T* uhat, void* Qbox,
-                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status = nullptr);
+                void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status,
+                bool persistent);
+// Tensor-core M2L + L2L over the compact box lists of one pruned / forest level (mixed
+// path, P_pad 32): splits the level's expansions (nb rows) and the parent level's
+// incoming expansions (nb_parent rows, none without L2L) into TF32 hi / lo rows in
+// `split` (m2l_tc_list_split_floats(nb, nb_parent) floats), then one persistent launch
+// over tiles of 128 boxes of one parity class whose A operand is gathered by list;
+// cls_start on the device, cls_host its host copy; a timed-out wait is reported in *status.
+constexpr int64_t kTcListMinBoxes = 1024;
+int64_t m2l_tc_list_split_floats(int64_t nb, int64_t nb_parent);
+cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, const int64_t* cls_host,
+                               const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
+                               const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
+                               float* u_level, void* C_level, float* split, int* status, int num_sms,
+                               cudaStream_t s);
 
 // words[0..3] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN}, words[4..9] = 0, zero[0..n_zero) = 0
 // (zero 16-byte aligned), in one launch.

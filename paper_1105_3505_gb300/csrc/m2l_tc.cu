@@ -509,6 +509,338 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------------
+// List form, for pruned storage and forests (P_pad 32): a level's boxes are compact ids
+// grouped by parity class, each with its 27 interaction-list entries (-1: none) and its
+// parent.  A tile is 128 consecutive boxes of one class; the A operand of a K-step is
+// the gather of the tile's 128 source rows (hi and lo, split beforehand into row-major
+// [box][32] arrays), so no tensor map applies.  Same pipeline as the TMA form, with the
+// copies done by four producer warps, 32 rows each: eight lanes per row and four rows
+// per instruction (16-byte cp.async, coalesced 128-byte rows), written straight into the
+// 128-byte swizzled layout, missing sources zero-filled.  Each producer warp announces
+// its rows on the stage's "full" barrier once they have landed (cp.async groups, kept
+// kLStages - 2 deep, then a proxy fence); producer warp 0 adds the operator tile's bulk
+// copy.  (Measured: the K-steps taken in turn by whole warps, each announced as soon as
+// it lands, and a deeper ring announced later were both slower.)
+//   warps 0-3: fold (one box per TMEM lane), warps 4-7: gather, warp 8: MMA issuer,
+//   warp 9: compensated incoming constants.
+constexpr int kLStages = 4;
+constexpr int kLThreads = 320;
+constexpr uint32_t kLStageBytes = 2 * kTmaABytes + 8192;  // A hi, A lo, [B_hi | B_lo]
+constexpr int kLSrcInts = 4 * 32 * 28;                    // per producer warp: 32 rows x 28 K-steps
+constexpr size_t kLSmem = 1024 + (size_t)kLStages * kLStageBytes + (size_t)kLSrcInts * sizeof(int);
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
+    const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
+    const float* __restrict__ qhi, const float* __restrict__ qlo, const float* __restrict__ uhi,
+    const float* __restrict__ ulo, const float* __restrict__ tiles, const float* __restrict__ mono,
+    const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout,
+    int* __restrict__ status) {
+    griddep_wait();
+    constexpr int NP = 32;
+    extern __shared__ __align__(1024) unsigned char tl_smem[];
+    const uint32_t base = smem_u32(tl_smem) + ((1024u - (smem_u32(tl_smem) & 1023u)) & 1023u);
+    int* s_src = reinterpret_cast<int*>(tl_smem + (base - smem_u32(tl_smem)) + (size_t)kLStages * kLStageBytes);
+    __shared__ __align__(8) uint64_t full[kLStages], empty[kLStages], acc_full[kTmaAcc], acc_empty[kTmaAcc];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_op[4][28];           // operator tile of K-step st for class c
+    __shared__ long long s_c[5], s_t[5];  // class starts; first tile of each class
+    __shared__ int s_abort;
+    __shared__ int s_issued[2];           // K-steps issued by the producers (all four) and by the MMA thread
+    __shared__ int s_pissued[4];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool has_l2l = uhi != nullptr;
+    const int n_steps = 27 + (has_l2l ? 1 : 0);
+    volatile int* vabort = &s_abort;
+    const uint32_t wb = ((volatile int*)status)[3] > 0 ? (uint32_t)((volatile int*)status)[3] : 0xffffffffu;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 4; ++c) {
+            const int px = c & 1, py = c >> 1;
+            int nn = 0;
+            for (int d = 0; d < 36; ++d) {
+                const int dx = (d % 6) - 2 - px, dy = (d / 6) - 2 - py;
+                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+                s_op[c][nn++] = offset_index_tc(dx, dy);  // interaction-list slot order
+            }
+            s_op[c][27] = kNumOffsets + c;
+        }
+        long long t = 0;
+        for (int c = 0; c <= 4; ++c) {
+            s_c[c] = cls_start[c];
+            s_t[c] = t;
+            if (c < 4) t += (cls_start[c + 1] - cls_start[c] + 127) / 128;
+        }
+        for (int i = 0; i < kLStages; ++i) {
+            mbar_init(&full[i], 5);  // four producer warps + the operator tile (with its bytes)
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < kTmaAcc; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+        fence_barrier_init();
+        s_abort = 0;
+        s_issued[0] = s_issued[1] = 0;
+        for (int i = 0; i < 4; ++i) s_pissued[i] = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_tmem, TmaCfg<32>::Cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const int n_tiles = (int)s_t[4];
+    const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * n_steps;
+    auto abort_now = [&]() {
+        atomicExch(&s_abort, 1);
+        atomicExch(status, LFMM_ETIMEOUT);
+    };
+    // it-th tile of this CTA: class and first / end box
+    auto tile_of = [&](int it, int& cls, long long& b0, long long& b1) {
+        const long long t = (long long)blockIdx.x + (long long)it * gridDim.x;
+        cls = (t >= s_t[1]) + (t >= s_t[2]) + (t >= s_t[3]);
+        b0 = s_c[cls] + (t - s_t[cls]) * 128;
+        b1 = min(b0 + 128, s_c[cls + 1]);
+    };
+
+    if (warp >= 4 && warp < 8) {
+        const int pw = warp - 4;                 // rows 32 pw .. 32 pw + 31 of every tile
+        int* my_src = s_src + pw * 32 * 28;      // [row][K-step] source row, -1: none
+        const int sub = lane >> 3, ch = lane & 7;  // row within a group of four, 16-byte chunk
+        int it = 0, st = 0, slot = 0, use = 0, cls = 0;
+        long long b0 = 0, b1 = 0;
+        int pend = 0;  // first K-step whose rows this warp has not announced
+        int gs = 0;
+        for (; gs < total; ++gs) {
+            if (__any_sync(0xffffffffu, *vabort != 0)) break;  // warp-uniform
+            if (st == 0) {
+                tile_of(it, cls, b0, b1);
+                for (int i = lane; i < 32 * 28; i += 32) {
+                    const int r = i / 28, k = i % 28;
+                    const long long b = b0 + 32 * pw + r;
+                    int v = -1;
+                    if (b < b1) v = k < 27 ? il[b * 27 + k] : (has_l2l ? par[b] : -1);
+                    my_src[i] = v;
+                }
+                __syncwarp();
+            }
+            bool ok = true;
+            if (use > 0 && lane == 0) ok = mbar_poll_bounded(&empty[slot], (uint32_t)((use - 1) & 1), wb);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
+                if (lane == 0) abort_now();
+                break;
+            }
+            const uint32_t sa = base + (uint32_t)slot * kLStageBytes;
+            if (pw == 0 && lane == 0) {
+                mbar_arrive_expect_tx(&full[slot], 8192);
+                bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)s_op[cls][st] * 2048, 8192, &full[slot]);
+            }
+            const float* hs = st < 27 ? qhi : uhi;
+            const float* ls = st < 27 ? qlo : ulo;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int rl = 4 * g + sub;          // row within this warp's 32
+                const int r = 32 * pw + rl;          // row of the tile (TMEM lane)
+                const int si = my_src[rl * 28 + st];
+                const size_t off = si < 0 ? 0 : (size_t)si * NP + 4 * ch;
+                const int bytes = si < 0 ? 0 : 16;
+                const uint32_t dst = (uint32_t)(r * 128 + ((ch ^ (r & 7)) << 4));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + dst), "l"(hs + off),
+                             "r"(bytes)
+                             : "memory");
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + kTmaABytes + dst),
+                             "l"(ls + off), "r"(bytes)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            // announce the rows of the K-step kLStages - 2 groups back
+            if (gs - pend >= kLStages - 2) {
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(kLStages - 2) : "memory");
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[pend % kLStages]);
+                ++pend;
+            }
+            if (lane == 0) s_pissued[pw] = gs + 1;
+            if (++slot == kLStages) {
+                slot = 0;
+                ++use;
+            }
+            if (++st == n_steps) {
+                st = 0;
+                ++it;
+            }
+        }
+        // announce what is left (also after an abort, so that the teardown's waits end);
+        // the operator tile of a step this warp did not issue is never awaited
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0)
+            for (; pend < gs; ++pend) mbar_arrive(&full[pend % kLStages]);
+    } else if (warp == 8) {
+        if (lane == 0) {
+            constexpr uint32_t kIdesc64 = idesc_tf32(128, 64), kIdesc32 = idesc_tf32(128, 32);
+            int slot = 0, use = 0, d = 0, du = 0;
+            for (int gs = 0; gs < total; ++gs) {
+                if (*vabort) break;
+                if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1), wb) ||
+                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1), wb))) {
+                    abort_now();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_hi = base + (uint32_t)slot * kLStageBytes, a_lo = a_hi + kTmaABytes;
+                const uint32_t b_hi = a_hi + 2 * kTmaABytes;
+                const uint32_t d_big = tmem + 64 * d, d_small = d_big + 32;
+                const uint64_t dah = smem_desc_sw128(a_hi), dal = smem_desc_sw128(a_lo), dbh = smem_desc_sw128(b_hi);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdesc64, kk > 0 ? 1u : 0u);
+                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdesc32, 1u);
+                }
+                mma_commit(&empty[slot]);
+                mma_commit(&acc_full[d]);
+                s_issued[1] = gs + 1;
+                if (++slot == kLStages) {
+                    slot = 0;
+                    ++use;
+                }
+                if (++d == kTmaAcc) {
+                    d = 0;
+                    ++du;
+                }
+            }
+        }
+    } else if (warp == 9) {
+        for (int it = 0; it < my_tiles; ++it) {
+            int cls;
+            long long b0, b1;
+            tile_of(it, cls, b0, b1);
+            for (long long b = b0 + lane; b < b1; b += 32) {
+                const int pb = has_l2l ? par[b] : -1;
+                DFv sacc = pb >= 0 ? Cpar[pb] : DFv{0.f, 0.f};
+                for (int k0 = 0; k0 < 27; k0 += 9) {
+                    int sb[9];
+                    DFv qv[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) sb[k] = il[b * 27 + k0 + k];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) qv[k] = sb[k] >= 0 ? Qin[sb[k]] : DFv{0.f, 0.f};
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const int o = s_op[cls][k0 + k];
+                        if (sb[k] >= 0) sacc = dadd(sacc, dmul(DFv{mono[o], mono[kNumOffsets + o]}, qv[k]));
+                    }
+                }
+                Cout[b] = sacc;
+            }
+        }
+    } else if (warp < 4) {
+        const int r = threadIdx.x;  // TMEM lane = tile row
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float acc[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc[j] = 0.f;
+        int it = 0, st = 0, d = 0, du = 0, cls = 0;
+        long long b0 = 0, b1 = 0;
+        for (int gs = 0; gs < total; ++gs) {
+            if (st == 0) tile_of(it, cls, b0, b1);
+            bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1), wb);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) abort_now();
+                break;
+            }
+            tc_fence_after();
+            uint32_t big[32], small[32];
+            tmem_ld32(tmem + lane_base + 64 * d, big);
+            tmem_ld32(tmem + lane_base + 64 * d + 32, small);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[d]);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+            if (st == n_steps - 1) {
+                if (b0 + r < b1) {
+                    float4* dst = reinterpret_cast<float4*>(out + (size_t)(b0 + r) * NP);
+#pragma unroll
+                    for (int c = 0; c < NP / 4; ++c)
+                        dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                }
+#pragma unroll
+                for (int j = 0; j < NP; ++j) acc[j] = 0.f;
+            }
+            if (++d == kTmaAcc) {
+                d = 0;
+                ++du;
+            }
+            if (++st == n_steps) {
+                st = 0;
+                ++it;
+            }
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) {
+        // Every producer warp announced the steps it issued, but the warps stopped at
+        // different steps.  A warp issues step g + kLStages only after step g's stage was
+        // consumed, so the steps issued by some warps and not by others are fewer than
+        // kLStages, each in its own slot and phase: arrive for the warps that skipped them
+        // (and for warp 0's operator-tile arrival), then wait until the copies of the last
+        // kLStages issued steps have landed and the MMAs issued have completed (a commit
+        // tracks every MMA before it).
+        int pmin = s_pissued[0], pmax = s_pissued[0];
+        for (int i = 1; i < 4; ++i) {
+            pmin = min(pmin, s_pissued[i]);
+            pmax = max(pmax, s_pissued[i]);
+        }
+        for (int g = pmin; g < pmax; ++g) {
+            int missing = s_pissued[0] <= g ? 1 : 0;
+            for (int i = 0; i < 4; ++i) missing += s_pissued[i] <= g ? 1 : 0;
+            for (int j = 0; j < missing; ++j) mbar_arrive(&full[g % kLStages]);
+        }
+        for (int g = pmax > kLStages ? pmax - kLStages : 0; g < pmax; ++g)
+            mbar_poll_bounded(&full[g % kLStages], (uint32_t)((g / kLStages) & 1));
+        const int m = s_issued[1];
+        if (m > 0) mbar_poll_bounded(&empty[(m - 1) % kLStages], (uint32_t)(((m - 1) / kLStages) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TmaCfg<32>::Cols);
+    }
+}
+
+// hi / lo TF32 split of row-major expansions ([box][32]), float4 items: hi and lo arrays
+__global__ void split_tf32_rows_kernel(const float4* __restrict__ x, int64_t n4, float4* __restrict__ hi,
+                                       float4* __restrict__ lo) {
+    griddep_wait();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x[i];
+        const float a[4] = {v.x, v.y, v.z, v.w};
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = __uint_as_float(tf32_rna_bits(a[e]));
+            l[e] = __uint_as_float(tf32_rna_bits(a[e] - h[e]));
+        }
+        hi[i] = make_float4(h[0], h[1], h[2], h[3]);
+        lo[i] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 // hi / lo TF32 split of a level's expansions (Morton order in) into the layouts the
 // tensor maps describe: planes = 1 -> [hl][plane][y'][x'][NP] (targets' level),
 // planes = 0 -> [hl][y][x][NP] (parent level, row-major).  Item iv is one float4 of
@@ -667,6 +999,44 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
         }
     };
     return NP == 32 ? by_stages(std::integral_constant<int, 32>()) : by_stages(std::integral_constant<int, 64>());
+}
+
+int64_t m2l_tc_list_split_floats(int64_t nb, int64_t nb_parent) { return 2 * (nb + nb_parent) * 32; }
+
+cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, const int64_t* cls_host,
+                               const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
+                               const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
+                               float* u_level, void* C_level, float* split, int* status, int num_sms,
+                               cudaStream_t s) {
+    if (ops.NP != 32 || !ops.tc[k]) return cudaErrorInvalidValue;
+    int64_t n_tiles = 0;
+    for (int c = 0; c < 4; ++c) n_tiles += (cls_host[c + 1] - cls_host[c] + 127) / 128;
+    if (n_tiles <= 0) return cudaSuccess;
+    float* qhi = split;
+    float* qlo = qhi + (size_t)nb * 32;
+    float* uhi = qlo + (size_t)nb * 32;
+    float* ulo = uhi + (size_t)nb_parent * 32;
+    auto grid_for = [&](int64_t n4) {
+        int64_t b = (n4 + 255) / 256;
+        return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
+    };
+    cudaError_t e = launch_dependent(split_tf32_rows_kernel, dim3(grid_for(nb * 8)), dim3(256), 0, s,
+                                     reinterpret_cast<const float4*>(q_level), nb * 8, reinterpret_cast<float4*>(qhi),
+                                     reinterpret_cast<float4*>(qlo));
+    if (e != cudaSuccess) return e;
+    if (u_parent) {
+        e = launch_dependent(split_tf32_rows_kernel, dim3(grid_for(nb_parent * 8)), dim3(256), 0, s,
+                             reinterpret_cast<const float4*>(u_parent), nb_parent * 8, reinterpret_cast<float4*>(uhi),
+                             reinterpret_cast<float4*>(ulo));
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = ensure_dynamic_smem((const void*)m2l_tc_list_kernel, kLSmem)) != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(n_tiles, num_sms);
+    return launch_dependent(m2l_tc_list_kernel, dim3(grid), dim3(kLThreads), kLSmem, s, cls_start, il,
+                            u_parent ? par : nullptr, (const float*)qhi, (const float*)qlo,
+                            u_parent ? (const float*)uhi : nullptr, u_parent ? (const float*)ulo : nullptr,
+                            (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
+                            (const DFv*)C_parent, u_level, (DFv*)C_level, status);
 }
 
 }  // namespace lfmm

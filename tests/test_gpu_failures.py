@@ -192,6 +192,48 @@ def test_tensor_core_wait_budget_times_out_and_recovers(lfmm):
         lfmm.lfmm_plan_destroy(h)
 
 
+def test_tensor_core_list_wait_budget_times_out_and_recovers(lfmm):
+    """The same for the tensor-core list M2L of a forest (four gathering producer warps):
+    with one poll per wait it gives up, the producers announce what they issued, the
+    teardown completes the stages some producers skipped and waits for every copy and
+    product in flight before freeing tensor memory; the plan reports LFMM_ETIMEOUT and
+    evaluates as before.  Forest evaluation runs one launch per level, so no grid
+    barrier can time out."""
+    rng = np.random.default_rng(65)
+    srcs, fs = [], []
+    for i in range(48):
+        n = int(rng.integers(300, 3000))
+        r = np.random.default_rng([65, i])
+        srcs.append(workloads.distinct_in_box(r, n, int(np.ceil(4 * np.sqrt(n))), int(r.integers(-9000, 9000)), 0))
+        fs.append(workloads.zero_sum(r.standard_normal(n)))
+    src = np.ascontiguousarray(np.concatenate(srcs).astype(np.int32))
+    off = np.concatenate([[0], np.cumsum([a.shape[0] for a in srcs])]).astype(np.int64)
+    f = np.concatenate(fs)
+    with lfmm.Forest(src, off, src, off, precision=lfmm.LFMM_MIXED, p=8) as fo:
+        u0 = fo.eval(f)
+        fo.status()
+        lfmm.lfmm_plan_set_wait_budget(fo.handle, 1)
+        lfmm.lfmm_profile_enable(True)
+        lfmm.lfmm_profile_read(reset=True)
+        try:
+            fo.eval(f)
+            prof = lfmm.lfmm_profile_read(reset=True)
+        finally:
+            lfmm.lfmm_profile_enable(False)
+        assert prof["m2l_tc"][1] > 0  # the tensor-core list levels ran
+        with pytest.raises(lfmm.LfmmError) as ei:
+            fo.status()
+        assert ei.value.status == lfmm.LFMM_ETIMEOUT
+        lfmm.lfmm_plan_set_wait_budget(fo.handle, 0)
+        for _ in range(2):
+            u1 = fo.eval(f)
+            fo.status()
+            assert np.array_equal(u0, u1)
+    ref = oracle.lattice_sum(srcs[5], fs[5], srcs[5])
+    u5 = u0[off[5]:off[6]]
+    assert np.abs(u5 - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
 def test_server_overload_policy_and_cancel(lfmm):
     """One slot, so requests queue behind the one running: a bounded queue refuses the
     excess at submit, a latency budget of 0.01 ms sheds whatever waits, cancel removes a

@@ -223,12 +223,13 @@ def test_clustered_4m_sampled(lfmm, clustered_4m, precision, p):
 def test_forest_persistent_sweeps_equal_per_level(lfmm, precision):
     """With LFMM_FLAG_PERSISTENT the upward and downward sweeps of a forest run as one
     persistent cooperative launch each (work queues per level, grid barriers between
-    levels); by default the same plan runs one launch per level.  Same arithmetic per box:
-    the results are bit-identical, and the persistent form launches one kernel per sweep."""
+    levels); by default the same plan runs one launch per level.  Same arithmetic per box
+    (the list M2L on the CUDA cores in both forms: tc_min_level 99): the results are
+    bit-identical, and the persistent form launches one kernel per sweep."""
     probs = forest_case(zlib.crc32(b"fused"), 60, n_min=200, n_max=9000)
     src, so, tgt, to, f = concat(probs)
     prec, p, tol = prec_of(lfmm, precision)
-    with lfmm.Forest(src, so, tgt, to, precision=prec, p=p) as fo:
+    with lfmm.Forest(src, so, tgt, to, precision=prec, p=p, tc_min_level=99) as fo:
         lfmm.lfmm_profile_enable(True)
         lfmm.lfmm_profile_read(reset=True)
         try:
@@ -253,7 +254,7 @@ def test_clustered_persistent_sweeps(lfmm):
     the per-level launches and the oracle."""
     prob = small_clustered()
     for prec, p, tol in ((lfmm.LFMM_MIXED, 8, MIXED_TOL), (lfmm.LFMM_DF, 16, FP64_TOL)):
-        with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p) as pl:
+        with lfmm.Plan(prob.src, prob.tgt, precision=prec, p=p, tc_min_level=99) as pl:
             u0 = pl.eval(prob.f)
             pl.set_flags(persistent=True)
             u1 = pl.eval(prob.f)
@@ -262,3 +263,40 @@ def test_clustered_persistent_sweeps(lfmm):
     idx = np.arange(0, prob.tgt.shape[0], 37)
     ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[idx])
     assert rel_err(u1[idx], ref) <= tol
+
+
+@pytest.mark.parametrize("case", ["forest", "forest_separate_targets", "clustered"])
+def test_tensor_core_list_m2l(lfmm, case):
+    """Mixed path, P_pad 32: the list M2L of every pruned / forest level with at least
+    1,024 boxes runs on the tensor cores (gathered A operand, 3xTF32 split, fresh
+    accumulators per offset); against the CUDA-core list kernel (tc_min_level 99) to
+    the mixed path's rounding, and against the oracle.  Class ranges are not multiples of
+    the 128-box tile, so partial tiles are covered."""
+    if case == "clustered":
+        prob = small_clustered()
+        make = lambda **kw: lfmm.Plan(prob.src, prob.tgt, precision=lfmm.LFMM_MIXED, p=8, **kw)
+        f, tgt_ranges = prob.f, [(0, prob.tgt.shape[0], prob.src, prob.f, prob.tgt)]
+    else:
+        probs = forest_case(zlib.crc32(case.encode()), 48, targets_equal=(case == "forest"))
+        src, so, tgt, to, f = concat(probs)
+        make = lambda **kw: lfmm.Forest(src, so, tgt, to, precision=lfmm.LFMM_MIXED, p=8, **kw)
+        tgt_ranges = [(to[i], to[i + 1], probs[i][0], probs[i][2], probs[i][1]) for i in (0, 23, 47)]
+    out, prof = {}, {}
+    for name, kw in (("tc", {}), ("simt", dict(tc_min_level=99))):
+        with make(**kw) as pl:
+            assert pl.info()["tree"] == lfmm.LFMM_TREE_PRUNED
+            lfmm.lfmm_profile_enable(True)
+            lfmm.lfmm_profile_read(reset=True)
+            try:
+                out[name] = pl.eval(f)
+                prof[name] = lfmm.lfmm_profile_read(reset=True)
+            finally:
+                lfmm.lfmm_profile_enable(False)
+            pl.status()
+    assert prof["tc"]["m2l_tc"][1] > 0 and prof["simt"]["m2l_tc"][1] == 0
+    scale = np.abs(out["simt"]).max()
+    assert np.abs(out["tc"] - out["simt"]).max() <= MIXED_TOL * scale
+    for a, b, s, fi, t in tgt_ranges:
+        idx = np.arange(a, b, max(1, (b - a) // 200))
+        ref = oracle.lattice_sum(s, fi, t[idx - a])
+        assert rel_err(out["tc"][idx], ref) <= MIXED_TOL
