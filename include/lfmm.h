@@ -74,8 +74,8 @@ typedef struct lfmm_opts {
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
     int32_t tc_min_level;     /* mixed path: tree levels >= this run M2L on the tensor cores  */
                               /* (0 = default 7; a value > 30 disables them); pruned storage  */
-                              /* and forests (P_pad 32): every list level of >= 1024 boxes    */
-                              /* runs there unless this is > 30                               */
+                              /* and forests: every list level of >= 1024 boxes runs there    */
+                              /* unless this is > 30                                          */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */
     int32_t flags;            /* bitwise OR of LFMM_FLAG_* (0: none)                           */
     /* M2L tiling (0 everywhere: the library's rules; lfmm_autotune picks these).  They    */

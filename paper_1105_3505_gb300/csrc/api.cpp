@@ -316,15 +316,16 @@ int forest_workspaces(lfmm_plan* p, cudaStream_t s) {
         const int64_t sb = forest_m2l_split_bytes(F, p->NP, esz, p->num_sms, F.m2l_split);
         if (sb > 0 && (st = palloc(p, &F.m2l_part, (size_t)sb, s))) return st;
     }
-    // tensor-core list M2L of the large levels (mixed path, P_pad 32; opts.tc_min_level
+    // tensor-core list M2L of the large levels (mixed path; opts.tc_min_level
     // beyond every tree level keeps them on the CUDA cores): TF32 hi / lo rows
-    F.tc_list = p->opts.precision == LFMM_MIXED && p->NP == 32 && p->opts.tc_min_level <= kMaxTreeLevelForTc;
+    F.tc_list = p->opts.precision == LFMM_MIXED && p->opts.tc_min_level <= kMaxTreeLevelForTc;
     if (F.tc_list) {
         int64_t need = 0;
         const int nk = (int)F.levels.size();
         for (int k = 0; k < nk && F.kmax >= 0; ++k)
             if (F.levels[k].nb >= kTcListMinBoxes)
-                need = std::max(need, m2l_tc_list_split_floats(F.levels[k].nb, k + 1 < nk ? F.levels[k + 1].nb : 0));
+                need = std::max(need, m2l_tc_list_split_floats(F.levels[k].nb, k + 1 < nk ? F.levels[k + 1].nb : 0,
+                                                               p->NP));
         void* b = nullptr;
         if (need > 0 && (st = palloc(p, &b, (size_t)need * sizeof(float), s))) return st;
         F.tc_split = (float*)b;

@@ -990,7 +990,7 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             for (int c = 0; c < 4; ++c) maxc = std::max(maxc, lv.cls[c + 1] - lv.cls[c]);
             if (maxc == 0) continue;
             if constexpr (std::is_same<T, float>::value) {
-                if (F.tc_list && F.tc_split && NP == 32 && lv.nb >= kTcListMinBoxes && status_word) {
+                if (F.tc_list && F.tc_split && lv.nb >= kTcListMinBoxes && status_word) {
                     PhaseTimer pt(LFMM_PHASE_M2L_TC, s);
                     const cudaError_t e = launch_m2l_tc_list(
                         ops, k, lv.d_cls, lv.cls, lv.il, l2l ? lv.par : nullptr, Qx(k), lv.nb, Qm(k),

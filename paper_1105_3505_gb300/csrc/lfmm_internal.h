@@ -289,7 +289,7 @@ struct Forest {
     void* m2l_part = nullptr;               // partial sums of K-split list M2L levels (plan-owned)
     int m2l_split = 0;                      // opts.m2l_split (0: chunks by the number of tiles)
     unsigned long long* sweep_ctr = nullptr;  // work-queue counters of the persistent sweeps (2 x 16)
-    bool tc_list = false;                   // list M2L of large levels on the tensor cores (mixed, P_pad 32)
+    bool tc_list = false;                   // list M2L of large levels on the tensor cores (mixed path)
     float* tc_split = nullptr;              // TF32 hi / lo rows of those levels (plan-owned)
     void release(cudaStream_t s);
 };
@@ -315,13 +315,13 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                 void* Cbox, double* u, double* un, double* uf, int num_sms, cudaStream_t s, int* status,
                 bool persistent);
 // Tensor-core M2L + L2L over the compact box lists of one pruned / forest level (mixed
-// path, P_pad 32): splits the level's expansions (nb rows) and the parent level's
+// path, P_pad 32 or 64): splits the level's expansions (nb rows) and the parent level's
 // incoming expansions (nb_parent rows, none without L2L) into TF32 hi / lo rows in
-// `split` (m2l_tc_list_split_floats(nb, nb_parent) floats), then one persistent launch
+// `split` (m2l_tc_list_split_floats(nb, nb_parent, NP) floats), then one persistent launch
 // over tiles of 128 boxes of one parity class whose A operand is gathered by list;
 // cls_start on the device, cls_host its host copy; a timed-out wait is reported in *status.
 constexpr int64_t kTcListMinBoxes = 1024;
-int64_t m2l_tc_list_split_floats(int64_t nb, int64_t nb_parent);
+int64_t m2l_tc_list_split_floats(int64_t nb, int64_t nb_parent, int NP);
 cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, const int64_t* cls_host,
                                const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
                                const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,

@@ -510,11 +510,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 }
 
 // ---------------------------------------------------------------------------------
-// List form, for pruned storage and forests (P_pad 32): a level's boxes are compact ids
+// List form, for pruned storage and forests (P_pad 32 and 64): a level's boxes are compact ids
 // grouped by parity class, each with its 27 interaction-list entries (-1: none) and its
 // parent.  A tile is 128 consecutive boxes of one class; the A operand of a K-step is
 // the gather of the tile's 128 source rows (hi and lo, split beforehand into row-major
-// [box][32] arrays), so no tensor map applies.  Same pipeline as the TMA form, with the
+// [box][NP] arrays; one 128-byte K-block of each row per ring step), so no tensor map
+// applies.  Same pipeline as the TMA form, with the
 // copies done by four producer warps, 32 rows each: eight lanes per row and four rows
 // per instruction (16-byte cp.async, coalesced 128-byte rows), written straight into the
 // 128-byte swizzled layout, missing sources zero-filled.  Each producer warp announces
@@ -526,14 +527,23 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 //   warp 9: compensated incoming constants.
 constexpr int kLStages = 4;
 constexpr int kLThreads = 320;
-constexpr uint32_t kLStageBytes = 2 * kTmaABytes + 8192;  // A hi, A lo, [B_hi | B_lo]
-constexpr int kLSrcInts = 4 * 32 * 28;                    // per producer warp: 32 rows x 28 K-steps
-constexpr size_t kLSmem = 1024 + (size_t)kLStages * kLStageBytes + (size_t)kLSrcInts * sizeof(int);
+constexpr int kLSrcInts = 4 * 32 * 28;  // per producer warp: 32 rows x 28 offsets
+// P_pad 32: one K-block per offset; P_pad 64: two (each a ring step), accumulated in the
+// offset's fresh accumulator, as in the TMA form
+template <int NP>
+struct ListTcCfg {
+    static constexpr int KB = NP / 32;
+    static constexpr uint32_t BBytes = 2u * NP * 128u;                 // [B_hi | B_lo] of one K-block
+    static constexpr uint32_t StageBytes = 2 * kTmaABytes + BBytes;    // A hi, A lo, B
+    static constexpr size_t Smem = 1024 + (size_t)kLStages * StageBytes + (size_t)kLSrcInts * sizeof(int);
+    static_assert(Smem <= 227 * 1024, "list ring exceeds shared memory");
+};
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+template <int NP>
 __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
     const int64_t* __restrict__ cls_start, const int32_t* __restrict__ il, const int32_t* __restrict__ par,
     const float* __restrict__ qhi, const float* __restrict__ qlo, const float* __restrict__ uhi,
@@ -541,7 +551,10 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
     const DFv* __restrict__ Qin, const DFv* __restrict__ Cpar, float* __restrict__ out, DFv* __restrict__ Cout,
     int* __restrict__ status) {
     griddep_wait();
-    constexpr int NP = 32;
+    using Cfg = ListTcCfg<NP>;
+    constexpr int KB = Cfg::KB;
+    constexpr uint32_t kLStageBytes = Cfg::StageBytes;
+    constexpr uint32_t kAccCols = TmaCfg<NP>::AccCols;
     extern __shared__ __align__(1024) unsigned char tl_smem[];
     const uint32_t base = smem_u32(tl_smem) + ((1024u - (smem_u32(tl_smem) & 1023u)) & 1023u);
     int* s_src = reinterpret_cast<int*>(tl_smem + (base - smem_u32(tl_smem)) + (size_t)kLStages * kLStageBytes);
@@ -589,7 +602,7 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
         for (int i = 0; i < 4; ++i) s_pissued[i] = 0;
     }
     if (warp == 0) {
-        tmem_alloc(&s_tmem, TmaCfg<32>::Cols);
+        tmem_alloc(&s_tmem, TmaCfg<NP>::Cols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -598,7 +611,7 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
     const uint32_t tmem = s_tmem;
     const int n_tiles = (int)s_t[4];
     const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int total = my_tiles * n_steps;
+    const int total = my_tiles * n_steps * KB;  // ring steps: K-blocks of every offset of every tile
     auto abort_now = [&]() {
         atomicExch(&s_abort, 1);
         atomicExch(status, LFMM_ETIMEOUT);
@@ -615,13 +628,13 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
         const int pw = warp - 4;                 // rows 32 pw .. 32 pw + 31 of every tile
         int* my_src = s_src + pw * 32 * 28;      // [row][K-step] source row, -1: none
         const int sub = lane >> 3, ch = lane & 7;  // row within a group of four, 16-byte chunk
-        int it = 0, st = 0, slot = 0, use = 0, cls = 0;
+        int it = 0, st = 0, h = 0, slot = 0, use = 0, cls = 0;
         long long b0 = 0, b1 = 0;
-        int pend = 0;  // first K-step whose rows this warp has not announced
+        int pend = 0;  // first ring step whose rows this warp has not announced
         int gs = 0;
         for (; gs < total; ++gs) {
             if (__any_sync(0xffffffffu, *vabort != 0)) break;  // warp-uniform
-            if (st == 0) {
+            if (st == 0 && h == 0) {
                 tile_of(it, cls, b0, b1);
                 for (int i = lane; i < 32 * 28; i += 32) {
                     const int r = i / 28, k = i % 28;
@@ -640,8 +653,9 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
             }
             const uint32_t sa = base + (uint32_t)slot * kLStageBytes;
             if (pw == 0 && lane == 0) {
-                mbar_arrive_expect_tx(&full[slot], 8192);
-                bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + (size_t)s_op[cls][st] * 2048, 8192, &full[slot]);
+                mbar_arrive_expect_tx(&full[slot], Cfg::BBytes);
+                bulk_g2s_u32(sa + 2 * kTmaABytes, tiles + ((size_t)s_op[cls][st] * KB + h) * (Cfg::BBytes / 4),
+                             Cfg::BBytes, &full[slot]);
             }
             const float* hs = st < 27 ? qhi : uhi;
             const float* ls = st < 27 ? qlo : ulo;
@@ -650,7 +664,7 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
                 const int rl = 4 * g + sub;          // row within this warp's 32
                 const int r = 32 * pw + rl;          // row of the tile (TMEM lane)
                 const int si = my_src[rl * 28 + st];
-                const size_t off = si < 0 ? 0 : (size_t)si * NP + 4 * ch;
+                const size_t off = si < 0 ? 0 : (size_t)si * NP + 32 * h + 4 * ch;
                 const int bytes = si < 0 ? 0 : 16;
                 const uint32_t dst = (uint32_t)(r * 128 + ((ch ^ (r & 7)) << 4));
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + dst), "l"(hs + off),
@@ -674,9 +688,12 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
                 slot = 0;
                 ++use;
             }
-            if (++st == n_steps) {
-                st = 0;
-                ++it;
+            if (++h == KB) {
+                h = 0;
+                if (++st == n_steps) {
+                    st = 0;
+                    ++it;
+                }
             }
         }
         // announce what is left (also after an abort, so that the teardown's waits end);
@@ -688,35 +705,40 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
             for (; pend < gs; ++pend) mbar_arrive(&full[pend % kLStages]);
     } else if (warp == 8) {
         if (lane == 0) {
-            constexpr uint32_t kIdesc64 = idesc_tf32(128, 64), kIdesc32 = idesc_tf32(128, 32);
-            int slot = 0, use = 0, d = 0, du = 0;
+            // per K slice: D_big[0, 2 NP) (+)= A_hi x [B_hi | B_lo], D_small = D_big + NP +=
+            // A_lo x B_hi
+            constexpr uint32_t kIdescBig = idesc_tf32(128, 2 * NP), kIdescSmall = idesc_tf32(128, NP);
+            int slot = 0, use = 0, h = 0, d = 0, du = 0;
             for (int gs = 0; gs < total; ++gs) {
                 if (*vabort) break;
                 if (!mbar_poll_bounded(&full[slot], (uint32_t)(use & 1), wb) ||
-                    (du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1), wb))) {
+                    (h == 0 && du > 0 && !mbar_poll_bounded(&acc_empty[d], (uint32_t)((du - 1) & 1), wb))) {
                     abort_now();
                     break;
                 }
                 tc_fence_after();
                 const uint32_t a_hi = base + (uint32_t)slot * kLStageBytes, a_lo = a_hi + kTmaABytes;
                 const uint32_t b_hi = a_hi + 2 * kTmaABytes;
-                const uint32_t d_big = tmem + 64 * d, d_small = d_big + 32;
+                const uint32_t d_big = tmem + kAccCols * d, d_small = d_big + NP;
                 const uint64_t dah = smem_desc_sw128(a_hi), dal = smem_desc_sw128(a_lo), dbh = smem_desc_sw128(b_hi);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdesc64, kk > 0 ? 1u : 0u);
-                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdesc32, 1u);
+                    mma_tf32_ss(d_big, dah + 2 * kk, dbh + 2 * kk, kIdescBig, (h > 0 || kk > 0) ? 1u : 0u);
+                    mma_tf32_ss(d_small, dal + 2 * kk, dbh + 2 * kk, kIdescSmall, 1u);
                 }
                 mma_commit(&empty[slot]);
-                mma_commit(&acc_full[d]);
                 s_issued[1] = gs + 1;
                 if (++slot == kLStages) {
                     slot = 0;
                     ++use;
                 }
-                if (++d == kTmaAcc) {
-                    d = 0;
-                    ++du;
+                if (++h == KB) {
+                    h = 0;
+                    mma_commit(&acc_full[d]);
+                    if (++d == kTmaAcc) {
+                        d = 0;
+                        ++du;
+                    }
                 }
             }
         }
@@ -752,7 +774,8 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
         for (int j = 0; j < NP; ++j) acc[j] = 0.f;
         int it = 0, st = 0, d = 0, du = 0, cls = 0;
         long long b0 = 0, b1 = 0;
-        for (int gs = 0; gs < total; ++gs) {
+        const int offsets_total = total / KB;
+        for (int gs = 0; gs < offsets_total; ++gs) {
             if (st == 0) tile_of(it, cls, b0, b1);
             bool ok = *vabort == 0 && mbar_poll_bounded(&acc_full[d], (uint32_t)(du & 1), wb);
             ok = __all_sync(0xffffffffu, ok);
@@ -761,15 +784,18 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
                 break;
             }
             tc_fence_after();
-            uint32_t big[32], small[32];
-            tmem_ld32(tmem + lane_base + 64 * d, big);
-            tmem_ld32(tmem + lane_base + 64 * d + 32, small);
-            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < NP / 32; ++c) {
+                uint32_t big[32], small[32];
+                tmem_ld32(tmem + lane_base + kAccCols * d + 32 * c, big);
+                tmem_ld32(tmem + lane_base + kAccCols * d + NP + 32 * c, small);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[32 * c + j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[d]);
-#pragma unroll
-            for (int j = 0; j < NP; ++j) acc[j] += __uint_as_float(small[j]) + __uint_as_float(big[j]);
             if (st == n_steps - 1) {
                 if (b0 + r < b1) {
                     float4* dst = reinterpret_cast<float4*>(out + (size_t)(b0 + r) * NP);
@@ -819,7 +845,7 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, TmaCfg<32>::Cols);
+        tmem_dealloc(tmem, TmaCfg<NP>::Cols);
     }
 }
 
@@ -1001,42 +1027,49 @@ cudaError_t launch_m2l_tma(const DeviceOps& ops, int k, int level, const float* 
     return NP == 32 ? by_stages(std::integral_constant<int, 32>()) : by_stages(std::integral_constant<int, 64>());
 }
 
-int64_t m2l_tc_list_split_floats(int64_t nb, int64_t nb_parent) { return 2 * (nb + nb_parent) * 32; }
+int64_t m2l_tc_list_split_floats(int64_t nb, int64_t nb_parent, int NP) { return 2 * (nb + nb_parent) * NP; }
 
 cudaError_t launch_m2l_tc_list(const DeviceOps& ops, int k, const int64_t* cls_start, const int64_t* cls_host,
                                const int32_t* il, const int32_t* par, const float* q_level, int64_t nb,
                                const void* Q_level, const float* u_parent, int64_t nb_parent, const void* C_parent,
                                float* u_level, void* C_level, float* split, int* status, int num_sms,
                                cudaStream_t s) {
-    if (ops.NP != 32 || !ops.tc[k]) return cudaErrorInvalidValue;
+    const int NP = ops.NP;
+    if ((NP != 32 && NP != 64) || !ops.tc[k]) return cudaErrorInvalidValue;
     int64_t n_tiles = 0;
     for (int c = 0; c < 4; ++c) n_tiles += (cls_host[c + 1] - cls_host[c] + 127) / 128;
     if (n_tiles <= 0) return cudaSuccess;
     float* qhi = split;
-    float* qlo = qhi + (size_t)nb * 32;
-    float* uhi = qlo + (size_t)nb * 32;
-    float* ulo = uhi + (size_t)nb_parent * 32;
+    float* qlo = qhi + (size_t)nb * NP;
+    float* uhi = qlo + (size_t)nb * NP;
+    float* ulo = uhi + (size_t)nb_parent * NP;
     auto grid_for = [&](int64_t n4) {
         int64_t b = (n4 + 255) / 256;
         return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms * 16));
     };
-    cudaError_t e = launch_dependent(split_tf32_rows_kernel, dim3(grid_for(nb * 8)), dim3(256), 0, s,
-                                     reinterpret_cast<const float4*>(q_level), nb * 8, reinterpret_cast<float4*>(qhi),
+    const int64_t q4 = nb * (NP / 4), u4 = nb_parent * (NP / 4);
+    cudaError_t e = launch_dependent(split_tf32_rows_kernel, dim3(grid_for(q4)), dim3(256), 0, s,
+                                     reinterpret_cast<const float4*>(q_level), q4, reinterpret_cast<float4*>(qhi),
                                      reinterpret_cast<float4*>(qlo));
     if (e != cudaSuccess) return e;
     if (u_parent) {
-        e = launch_dependent(split_tf32_rows_kernel, dim3(grid_for(nb_parent * 8)), dim3(256), 0, s,
-                             reinterpret_cast<const float4*>(u_parent), nb_parent * 8, reinterpret_cast<float4*>(uhi),
+        e = launch_dependent(split_tf32_rows_kernel, dim3(grid_for(u4)), dim3(256), 0, s,
+                             reinterpret_cast<const float4*>(u_parent), u4, reinterpret_cast<float4*>(uhi),
                              reinterpret_cast<float4*>(ulo));
         if (e != cudaSuccess) return e;
     }
-    if ((e = ensure_dynamic_smem((const void*)m2l_tc_list_kernel, kLSmem)) != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(n_tiles, num_sms);
-    return launch_dependent(m2l_tc_list_kernel, dim3(grid), dim3(kLThreads), kLSmem, s, cls_start, il,
-                            u_parent ? par : nullptr, (const float*)qhi, (const float*)qlo,
-                            u_parent ? (const float*)uhi : nullptr, u_parent ? (const float*)ulo : nullptr,
-                            (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
-                            (const DFv*)C_parent, u_level, (DFv*)C_level, status);
+    auto go = [&](auto np_tag) -> cudaError_t {
+        constexpr int NPc = decltype(np_tag)::value;
+        cudaError_t r = ensure_dynamic_smem((const void*)m2l_tc_list_kernel<NPc>, ListTcCfg<NPc>::Smem);
+        if (r != cudaSuccess) return r;
+        return launch_dependent(m2l_tc_list_kernel<NPc>, dim3(grid), dim3(kLThreads), ListTcCfg<NPc>::Smem, s,
+                                cls_start, il, u_parent ? par : nullptr, (const float*)qhi, (const float*)qlo,
+                                u_parent ? (const float*)uhi : nullptr, u_parent ? (const float*)ulo : nullptr,
+                                (const float*)ops.tc[k], (const float*)ops.mono[k], (const DFv*)Q_level,
+                                (const DFv*)C_parent, u_level, (DFv*)C_level, status);
+    };
+    return NP == 32 ? go(std::integral_constant<int, 32>()) : go(std::integral_constant<int, 64>());
 }
 
 }  // namespace lfmm

@@ -265,21 +265,23 @@ def test_clustered_persistent_sweeps(lfmm):
     assert rel_err(u1[idx], ref) <= tol
 
 
+@pytest.mark.parametrize("p", [8, 16])
 @pytest.mark.parametrize("case", ["forest", "forest_separate_targets", "clustered"])
-def test_tensor_core_list_m2l(lfmm, case):
-    """Mixed path, P_pad 32: the list M2L of every pruned / forest level with at least
-    1,024 boxes runs on the tensor cores (gathered A operand, 3xTF32 split, fresh
-    accumulators per offset); against the CUDA-core list kernel (tc_min_level 99) to
-    the mixed path's rounding, and against the oracle.  Class ranges are not multiples of
-    the 128-box tile, so partial tiles are covered."""
+def test_tensor_core_list_m2l(lfmm, case, p):
+    """Mixed path: the list M2L of every pruned / forest level with at least 1,024 boxes
+    runs on the tensor cores (gathered A operand, 3xTF32 split, fresh accumulators per
+    offset; p = 8: P_pad 32, one K-block per offset; p = 16: P_pad 64, two); against the
+    CUDA-core list kernel (tc_min_level 99) to the mixed path's rounding, and against the
+    oracle.  Class ranges are not multiples of the 128-box tile, so partial tiles are
+    covered."""
     if case == "clustered":
         prob = small_clustered()
-        make = lambda **kw: lfmm.Plan(prob.src, prob.tgt, precision=lfmm.LFMM_MIXED, p=8, **kw)
+        make = lambda **kw: lfmm.Plan(prob.src, prob.tgt, precision=lfmm.LFMM_MIXED, p=p, **kw)
         f, tgt_ranges = prob.f, [(0, prob.tgt.shape[0], prob.src, prob.f, prob.tgt)]
     else:
         probs = forest_case(zlib.crc32(case.encode()), 48, targets_equal=(case == "forest"))
         src, so, tgt, to, f = concat(probs)
-        make = lambda **kw: lfmm.Forest(src, so, tgt, to, precision=lfmm.LFMM_MIXED, p=8, **kw)
+        make = lambda **kw: lfmm.Forest(src, so, tgt, to, precision=lfmm.LFMM_MIXED, p=p, **kw)
         tgt_ranges = [(to[i], to[i + 1], probs[i][0], probs[i][2], probs[i][1]) for i in (0, 23, 47)]
     out, prof = {}, {}
     for name, kw in (("tc", {}), ("simt", dict(tc_min_level=99))):
