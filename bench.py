@@ -35,7 +35,7 @@ METRIC = "Mpoints/s at rel err≤1e-6 (mixed vs plain FP64 on GPU); serve p50/p9
 WORKLOAD = "uniform_1m: 2^20 distinct sources + 2^20 distinct targets uniform in [0,4096)^2, seed 1"
 L2_FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
-TC_MIN_LEVEL = 7            # library default: levels >= 7 of the fp32 path on the tensor cores
+TC_MIN_LEVEL = 6            # library default: levels >= 6 of the fp32 path on the tensor cores
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 : bf16 tensor throughput
 
 

@@ -73,7 +73,7 @@ typedef struct lfmm_opts {
     int32_t proxies_per_edge; /* proxy points per edge of the proxy ring of Sec. 5 (>= 8);     */
                               /* the remark of Sec. 5 finds 40 enough for 1e-10               */
     int32_t tc_min_level;     /* mixed path: tree levels >= this run M2L on the tensor cores  */
-                              /* (0 = default 7; a value > 30 disables them); pruned storage  */
+                              /* (0 = default 6; a value > 30 disables them); pruned storage  */
                               /* and forests: every list level of >= 1024 boxes runs there    */
                               /* unless this is > 30                                          */
     int32_t tree;             /* LFMM_TREE_AUTO, LFMM_TREE_UNIFORM or LFMM_TREE_PRUNED         */

@@ -417,8 +417,9 @@ cudaError_t launch_m2l_fused(const DeviceOps& ops, int L, const LevelBufs& b, in
                              int* status, int num_sms, int* last_level, cudaStream_t s, int split = 0);
 
 // First tree level whose M2L runs on the tensor cores when opts.tc_min_level is 0
-// (levels of 4^7 boxes and more; below that the fused SIMT kernel wins).
-constexpr int kDefaultTcMinLevel = 7;
+// (levels of 4^6 boxes and more: on uniform_1m level 6 there took the step from 0.478 to
+// 0.468 ms at p = 8 and from 0.778 to 0.686 ms at p = 16; level 5 was slower again).
+constexpr int kDefaultTcMinLevel = 6;
 // Whether level `level` (k levels above the leaves) runs M2L + L2L on the tensor cores:
 // fp32 arithmetic, P <= 32, tiles present, level >= tc_min_level.
 inline bool m2l_uses_tc(const DeviceOps& ops, int k, int level, int tc_min_level, bool fp32) {

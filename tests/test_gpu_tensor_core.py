@@ -1,7 +1,7 @@
 """The tensor-core M2L (tcgen05, 3xTF32 split, mixed path, P_pad 32 and 64) against the oracle.
 
 tc_min_level = 2 puts every M2L level on the tensor-core kernel, so small problems
-exercise it; the default (level >= 7) is exercised by the full-size test in
+exercise it; the default (level >= 6) is exercised by the full-size test in
 test_gpu_parity.py.  Levels whose parity class spans >= 128 boxes per row (level >= 8)
 use row tiles (one class row per tile); a sparse point set in a 4096^2 box with leaves
 capped at side 16 reaches level 8 with few points, so the oracle checks that shape in
