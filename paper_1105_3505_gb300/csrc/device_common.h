@@ -166,6 +166,33 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Block-wide copy of n16 16-byte words from global to shared memory (both 16-byte
+// aligned): each thread issues U loads before their stores, so a block staging a table
+// pays about n16 / (U blockDim) load latencies instead of n16 / blockDim.
+template <int U = 8>
+__device__ __forceinline__ void block_stage16(uint4* __restrict__ dst, const uint4* __restrict__ src, int n16) {
+    for (int i0 = threadIdx.x; i0 < n16; i0 += U * blockDim.x) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i < n16) v[u] = __ldg(src + i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i < n16) dst[i] = v[u];
+        }
+    }
+}
+// n elements of T (dst and src 16-byte aligned): the 16-byte words as above, then the tail
+template <typename T>
+__device__ __forceinline__ void block_stage(T* __restrict__ dst, const T* __restrict__ src, int n) {
+    const int n16 = (int)((size_t)n * sizeof(T) / 16);
+    block_stage16(reinterpret_cast<uint4*>(dst), reinterpret_cast<const uint4*>(src), n16);
+    for (int i = (int)((size_t)n16 * 16 / sizeof(T)) + threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 // Position of offset (ox, oy) in the list of 40: row-major over [-3,3]^2 minus the core.
 __device__ __forceinline__ int offset_index(int ox, int oy) {
     const int raw = (oy + 3) * 7 + (ox + 3);
@@ -193,6 +220,88 @@ struct alignas(16) SrcEntry<DF> {
     int off, pad;
     DF f;
 };
+
+// Staging of a near-field strip (a run of leaves of one leaf row): its sources are the
+// contiguous source ranges of three leaf rows (row r from sorted index sb_r[0], leaf
+// column boundaries sb_r[0..ncol], rows concatenated at rs[r]).  Each staged source gets
+// its table offset relative to the strip's first leaf bx0.  A thread takes U sources at a
+// time and issues their loads before the searches and stores.
+template <typename T, int U = 4>
+__device__ __forceinline__ void stage_strip_sources(SrcEntry<T>* __restrict__ s_src, int ns_strip,
+                                                    const int* __restrict__ rs, const int* __restrict__ s_sb,
+                                                    int sb_stride, int ncol, int c_lo, int bx0, int side, int tab_W,
+                                                    const int32_t* __restrict__ sloc,
+                                                    const T* __restrict__ f_sorted) {
+    for (int v0 = threadIdx.x; v0 < ns_strip; v0 += U * blockDim.x) {
+        int lv[U];
+        T fv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * (int)blockDim.x;
+            if (v < ns_strip) {
+                const int r = (v >= rs[1]) + (v >= rs[2]);
+                const int j = s_sb[r * sb_stride] + (v - rs[r]);
+                lv[u] = sloc[j];
+                fv[u] = f_sorted[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * (int)blockDim.x;
+            if (v < ns_strip) {
+                const int r = (v >= rs[1]) + (v >= rs[2]);
+                const int* sb = s_sb + r * sb_stride;
+                const int j = sb[0] + (v - rs[r]);
+                int lo = 0, hi = ncol;  // leaf column c with sb[c] <= j < sb[c+1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sb[mid] <= j) lo = mid;
+                    else hi = mid;
+                }
+                const int l = lv[u];
+                SrcEntry<T> e;
+                e.off = (c_lo + lo - bx0) * side + (l & 0xffff) + tab_W * ((r - 1) * side + (l >> 16));
+                e.f = fv[u];
+                s_src[v] = e;
+            }
+        }
+    }
+}
+
+// The strip's targets (sorted indices tb0 .. tb0 + nt_strip - 1; leaf i of the strip starts
+// at s_tb[i]), with the leaf's index in the strip packed into bits 8..15 of the local
+// position (x < 256; leaf sides are at most 32).
+template <int U = 4>
+__device__ __forceinline__ void stage_strip_targets(int* __restrict__ s_tloc, int* __restrict__ s_tperm,
+                                                    int nt_strip, const int* __restrict__ s_tb, int nleaf, int tb0,
+                                                    const int32_t* __restrict__ tloc,
+                                                    const int32_t* __restrict__ tperm) {
+    for (int v0 = threadIdx.x; v0 < nt_strip; v0 += U * blockDim.x) {
+        int lv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * (int)blockDim.x;
+            if (v < nt_strip) {
+                lv[u] = tloc[tb0 + v];
+                pv[u] = tperm[tb0 + v];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * (int)blockDim.x;
+            if (v < nt_strip) {
+                int lo = 0, hi = nleaf;  // leaf li with s_tb[li] <= tb0 + v < s_tb[li + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_tb[mid] - tb0 <= v) lo = mid;
+                    else hi = mid;
+                }
+                s_tloc[v] = lv[u] | (lo << 8);
+                s_tperm[v] = pv[u];
+            }
+        }
+    }
+}
 
 // The 27 interaction-list slots of a box of parity class (px, py): offsets (dx, dy) of
 // the parent's neighbours' children that are not adjacent, in row-major order over the

@@ -31,11 +31,11 @@ namespace lfmm {
 namespace {
 
 // ------------------------------------------------------------------------- P2M
-// Half a warp per leaf (row-major leaf index; a leaf holds ~16 sources at the usual
-// leaf sizes, so a whole warp would idle half its lanes and pay the per-leaf work
-// twice).  Lane h of a half owns expansion entries [h PL, h PL + PL); each source's
-// row of T_ofs^T is one vector load per lane.  Writes the sorted charges in T, the
-// outgoing expansion and the leaf's total charge (Morton index).
+// A quarter warp per leaf (row-major leaf index; a leaf holds ~16 sources at the usual
+// leaf sizes).  Lane h of a quarter owns expansion entries [h PL, h PL + PL), PL = NP/8;
+// each source's row of T_ofs^T is one or two 16-byte loads per lane, so a source step
+// of the warp serves four leaves.  Writes the sorted charges in T, the outgoing
+// expansion and the leaf's total charge (Morton index).
 template <typename T, int N>
 struct alignas(sizeof(T) * N > 16 ? 16 : sizeof(T) * N) VecT {
     T v[N];
@@ -53,22 +53,23 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
                                                   int64_t vq, int64_t vQ) {
     griddep_wait();
     using M = Mono<T>;
-    constexpr int G = 16, PL = NP / G;
+    constexpr int G = 8, PL = NP / G;
     using Row = VecT<T, PL>;
-    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & (G - 1);
+    const int lane = threadIdx.x & 31, grp = lane >> 3, hl = lane & (G - 1);
     const int64_t n_leaves = (int64_t)1 << (2 * L);
-    const int64_t n_pairs = (n_leaves + 1) >> 1;
+    const int64_t n_quads = (n_leaves + 3) >> 2;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // (charge vector, leaf pair): vector v reads f + v ns, writes f_sorted + v ns,
+    // (charge vector, four leaves): vector v reads f + v ns, writes f_sorted + v ns,
     // qhat + v vq and Q + v vQ
-    for (int64_t pv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pv < n_pairs * nvec; pv += nw) {
-        const int64_t v = pv / n_pairs, pair = pv - v * n_pairs;
+    for (int64_t pv = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pv < n_quads * nvec; pv += nw) {
+        const int64_t v = pv / n_quads, quad = pv - v * n_quads;
         const double* fv = f + v * ns;
         T* fsv = f_sorted + v * ns;
-        const int64_t leaf = 2 * pair + half;
+        const int64_t leaf = 4 * quad + grp;
         const bool lv = leaf < n_leaves;
         const int b = lv ? begin[leaf] : 0, cnt = lv ? begin[leaf + 1] - b : 0;
-        const int cmax = max(cnt, __shfl_xor_sync(kFull, cnt, 16));
+        int cmax = max(cnt, __shfl_xor_sync(kFull, cnt, 8));
+        cmax = max(cmax, __shfl_xor_sync(kFull, cmax, 16));
         T acc[PL];
 #pragma unroll
         for (int i = 0; i < PL; ++i) acc[i] = T(0);
@@ -87,9 +88,9 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
             }
             const int cc = min(G, cmax - j0);
             for (int k = 0; k < cc; ++k) {
-                // lanes of a half with fewer sources multiply row 0 by zero
-                const T fk = shfl(fj, (half << 4) + k);
-                const int Jk = __shfl_sync(kFull, J, (half << 4) + k);
+                // lanes of a quarter with fewer sources multiply row 0 by zero
+                const T fk = shfl(fj, (grp << 3) + k);
+                const int Jk = __shfl_sync(kFull, J, (grp << 3) + k);
                 const Row r = *reinterpret_cast<const Row*>(tofsT + (size_t)Jk * NP + hl * PL);
 #pragma unroll
                 for (int i = 0; i < PL; ++i) acc[i] = fma(r.v[i], fk, acc[i]);
@@ -102,9 +103,9 @@ __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restri
             for (int i = 0; i < PL; ++i) o.v[i] = acc[i];
             *reinterpret_cast<Row*>(qhat + v * vq + (size_t)mort * NP + hl * PL) = o;
         }
-        // sum of the compensated partial charges over the half
+        // sum of the compensated partial charges over the quarter
 #pragma unroll
-        for (int off = 8; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
+        for (int off = 4; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
         if (lv && hl == 0) Q[v * vQ + morton2((uint32_t)(leaf & ((1 << L) - 1)), (uint32_t)(leaf >> L))] = qsum;
     }
 }
@@ -691,7 +692,7 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(
     SrcEntry<T>* s_src = reinterpret_cast<SrcEntry<T>*>(tab + tab_n) + warp * kP2PCap;
     T* s_uhat = reinterpret_cast<T*>(reinterpret_cast<SrcEntry<T>*>(tab + tab_n) + kP2PWarps * kP2PCap) +
                 warp * NP;
-    for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    block_stage(tab, table, tab_n);
     const typename M::V phi0 = M::make(table[tab_n], table[tab_n + 1]);
     __syncthreads();
     const T* tab_c = tab + (tab_H + tab_H * tab_W);  // centre: phi(0, 0) - phi0
@@ -871,7 +872,7 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
     __shared__ int s_ra[Cfg::MAXSW][3], s_rl[Cfg::MAXSW][3];  // per-leaf source ranges
     __shared__ double s_nc[Cfg::MAXSW];                       // per-leaf phi0 * Q_near
 
-    for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    block_stage(tab, table, tab_n);
     const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
     const T* tab_c = tab + (tab_H + tab_H * tab_W);
     const int n = 1 << L;
@@ -927,36 +928,12 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
         }
         __syncthreads();
         const int ns_strip = s_rs[3];
-        // sources: coalesced copy + strip-relative table offset
-        for (int v = threadIdx.x; v < ns_strip; v += blockDim.x) {
-            const int r = (v >= s_rs[1]) + (v >= s_rs[2]);
-            const int* sb = s_sb + r * (Cfg::MAXSW + 3);
-            const int j = sb[0] + (v - s_rs[r]);
-            int lo = 0, hi = ncol;  // find leaf column c with sb[c] <= j < sb[c+1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (sb[mid] <= j) lo = mid;
-                else hi = mid;
-            }
-            const int l = sloc[j];
-            SrcEntry<T> e;
-            e.off = (c_lo + lo - bx0) * side + (l & 0xffff) + tab_W * ((r - 1) * side + (l >> 16));
-            e.f = f_sorted[j];
-            s_src[v] = e;
-        }
-        // targets, with their leaf's index in the strip packed into bits 8..15 of the
-        // local position (x and y are below 32)
+        // sources: coalesced copy + strip-relative table offset; targets with their leaf
+        // in the strip
+        stage_strip_sources<T>(s_src, ns_strip, s_rs, s_sb, Cfg::MAXSW + 3, ncol, c_lo, bx0, side, tab_W, sloc,
+                               f_sorted);
         const int tb0 = s_tb[0], nt_strip = s_tb[bx1 - bx0] - tb0;
-        for (int v = threadIdx.x; v < nt_strip; v += blockDim.x) {
-            int lo = 0, hi = bx1 - bx0;  // leaf li with s_tb[li] <= tb0 + v < s_tb[li + 1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_tb[mid] - tb0 <= v) lo = mid;
-                else hi = mid;
-            }
-            s_tloc[v] = tloc[tb0 + v] | (lo << 8);
-            s_tperm[v] = tperm[tb0 + v];
-        }
+        stage_strip_targets(s_tloc, s_tperm, nt_strip, s_tb, bx1 - bx0, tb0, tloc, tperm);
         __syncthreads();
 
         // pairs: a warp takes 32 consecutive targets of the strip (one per lane, from up
@@ -986,6 +963,7 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
                 const SrcEntry<T>* src = s_src + s_ra[li][r];
                 const int len = active ? s_rl[li][r] : 0;
                 int j = 0;
+#pragma unroll 2
                 for (; j + 4 <= len; j += 4) {
                     const SrcEntry<T> e0 = src[j], e1 = src[j + 1], e2 = src[j + 2], e3 = src[j + 3];
                     T b = tp[-e0.off] * e0.f;
@@ -1058,7 +1036,7 @@ __global__ void __launch_bounds__(StripMultiCfg<T, KR>::WARPS * 32) p2p_strip_mu
     __shared__ int s_ra[Cfg::MAXSW][3], s_rl[Cfg::MAXSW][3];
     __shared__ double s_nc[KR][Cfg::MAXSW];
 
-    for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    block_stage(tab, table, tab_n);
     const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
     const T* tab_c = tab + (tab_H + tab_H * tab_W);
     const int n = 1 << L;
@@ -1135,16 +1113,7 @@ __global__ void __launch_bounds__(StripMultiCfg<T, KR>::WARPS * 32) p2p_strip_mu
             s_f[v] = fv;
         }
         const int tb0 = s_tb[0], nt_strip = s_tb[bx1 - bx0] - tb0;
-        for (int v = threadIdx.x; v < nt_strip; v += blockDim.x) {
-            int lo = 0, hi = bx1 - bx0;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_tb[mid] - tb0 <= v) lo = mid;
-                else hi = mid;
-            }
-            s_tloc[v] = tloc[tb0 + v] | (lo << 8);
-            s_tperm[v] = tperm[tb0 + v];
-        }
+        stage_strip_targets(s_tloc, s_tperm, nt_strip, s_tb, bx1 - bx0, tb0, tloc, tperm);
         __syncthreads();
 
         const int n_chunks = (nt_strip + 31) >> 5;
@@ -1173,6 +1142,7 @@ __global__ void __launch_bounds__(StripMultiCfg<T, KR>::WARPS * 32) p2p_strip_mu
                 const FV* sf = s_f + s_ra[li][r];
                 const int len = active ? s_rl[li][r] : 0;
                 int j = 0;
+#pragma unroll 2
                 for (; j + 4 <= len; j += 4) {
                     const T p0 = tp[-so[j]], p1 = tp[-so[j + 1]], p2 = tp[-so[j + 2]], p3 = tp[-so[j + 3]];
                     const FV f0 = sf[j], f1 = sf[j + 1], f2 = sf[j + 2], f3 = sf[j + 3];
@@ -1466,16 +1436,53 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* st = reinterpret_cast<T*>(smem_raw);
     if (SMEM) {
-        const int rows = side * side;
-        for (int i = threadIdx.x; i < rows * NP; i += blockDim.x) st[(i / NP) * RS + (i % NP)] = tofsT[i];
+        // 16-byte loads, four in flight per thread, scattered into the padded rows
+        constexpr int U = 4;
+        const int n16 = side * side * NP / E;
+        const uint4* src = reinterpret_cast<const uint4*>(tofsT);
+        for (int i0 = threadIdx.x; i0 < n16; i0 += U * blockDim.x) {
+            uint4 w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                if (i < n16) w[u] = __ldg(src + i);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                if (i < n16) {
+                    const T* e = reinterpret_cast<const T*>(&w[u]);
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        const int x = i * E + k;
+                        st[(x / NP) * RS + (x % NP)] = e[k];
+                    }
+                }
+            }
+        }
         __syncthreads();
     }
-    // (charge vector, target): vector v reads uhat + v vq, Cleaf + v vQ, writes uf + v nt
-    for (int64_t tv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tv < nt * nvec;
-         tv += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = tv / nt, t = tv - v * nt;
-        const int leaf = tleaf[t];
-        const int l = tloc[t];
+    // (charge vector, target): vector v reads uhat + v vq, Cleaf + v vQ, writes uf + v nt.
+    // The next item's leaf, position and caller index are loaded before this item's
+    // expansion row, so their latency overlaps the arithmetic.
+    const int64_t n_items = nt * nvec, stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t tv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int nx_leaf = 0, nx_loc = 0, nx_perm = 0;
+    if (tv < n_items) {
+        const int64_t t = tv % nt;
+        nx_leaf = tleaf[t];
+        nx_loc = tloc[t];
+        nx_perm = tperm[t];
+    }
+    for (; tv < n_items; tv += stride) {
+        const int64_t v = tv / nt;
+        const int leaf = nx_leaf, l = nx_loc, pm = nx_perm;
+        if (tv + stride < n_items) {
+            const int64_t t2 = (tv + stride) % nt;
+            nx_leaf = tleaf[t2];
+            nx_loc = tloc[t2];
+            nx_perm = tperm[t2];
+        }
         const int J = (l & 0xffff) + side * (l >> 16);
         const T* row = SMEM ? st + J * RS : tofsT + (size_t)J * NP;  // (table too large: L1 / L2)
         const uint4* uh = reinterpret_cast<const uint4*>(uhat + v * vq + (size_t)leaf * NP);
@@ -1487,7 +1494,7 @@ __global__ void __launch_bounds__(256) l2p_kernel(int64_t nt, int side, const in
 #pragma unroll
             for (int e = 0; e < E; ++e) far = fma(row[c * E + e], v[e], far);
         }
-        uf[v * nt + tperm[t]] = (double)far + M::to_double(Cleaf[v * vQ + leaf]);
+        uf[v * nt + pm] = (double)far + M::to_double(Cleaf[v * vQ + leaf]);
     }
 }
 
@@ -1510,7 +1517,7 @@ template <typename T>
 cudaError_t launch_p2m(const TreeView& t, const DeviceOps& ops, const double* f, T* f_sorted,
                        T* qhat_leaf, void* Q, cudaStream_t s, int nvec, int64_t vq, int64_t vQ) {
     const int threads = 256;
-    int64_t blocks = (t.n_leaves * 16 * nvec + threads - 1) / threads;
+    int64_t blocks = (t.n_leaves * 8 * nvec + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
     using V = typename Mono<T>::V;

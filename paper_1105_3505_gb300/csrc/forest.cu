@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
     __shared__ int s_rj[3][2];                 // leaf-list range [j0, j1) of each row (-1: outside)
     __shared__ int s_lc[3][Cfg::MAXSW + 2];    // column - c_lo of each listed leaf (ascending)
 
-    for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = table[i];
+    block_stage(tab, table, tab_n);
     const V phi0 = M::make(table[tab_n], table[tab_n + 1]);
     const T* tab_c = tab + (tab_H + tab_H * tab_W);
     const int n_strips = *n_strips_d;
@@ -658,10 +658,20 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
             s_c[i] = (Cleaf && cid >= 0) ? Cleaf[cid] : M::zero();
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < (bx1 - bx0) * NP; i += blockDim.x) {
-            const int c = i / NP, pp = i % NP;
-            const int cid = s_has[c];
-            s_uhat[i] = (uhat && cid >= 0) ? uhat[(size_t)cid * NP + pp] : T(0);
+        // the strip's leaf expansions (four loads in flight per thread)
+        for (int i0 = threadIdx.x; i0 < (bx1 - bx0) * NP; i0 += 4 * blockDim.x) {
+            T vals[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                const int cid = i < (bx1 - bx0) * NP ? s_has[i / NP] : -1;
+                vals[k] = (uhat && cid >= 0) ? uhat[(size_t)cid * NP + i % NP] : T(0);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = i0 + k * (int)blockDim.x;
+                if (i < (bx1 - bx0) * NP) s_uhat[i] = vals[k];
+            }
         }
         for (int li = threadIdx.x; li < bx1 - bx0; li += blockDim.x) {
             const int bx = bx0 + li;
@@ -688,33 +698,10 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
         }
         __syncthreads();
         const int ns_strip = s_rs[3];
-        for (int v = threadIdx.x; v < ns_strip; v += blockDim.x) {
-            const int r = (v >= s_rs[1]) + (v >= s_rs[2]);
-            const int* sb = s_sb + r * (Cfg::MAXSW + 3);
-            const int j = sb[0] + (v - s_rs[r]);
-            int lo = 0, hi = ncol;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (sb[mid] <= j) lo = mid;
-                else hi = mid;
-            }
-            const int l = sloc[j];
-            SrcEntry<T> e;
-            e.off = (c_lo + lo - bx0) * side + (l & 0xffff) + tab_W * ((r - 1) * side + (l >> 16));
-            e.f = f_sorted[j];
-            s_src[v] = e;
-        }
+        stage_strip_sources<T>(s_src, ns_strip, s_rs, s_sb, Cfg::MAXSW + 3, ncol, c_lo, bx0, side, tab_W, sloc,
+                               f_sorted);
         const int tb0 = s_tb[0], nt_strip = s_tb[bx1 - bx0] - tb0;
-        for (int v = threadIdx.x; v < nt_strip; v += blockDim.x) {
-            int lo = 0, hi = bx1 - bx0;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_tb[mid] - tb0 <= v) lo = mid;
-                else hi = mid;
-            }
-            s_tloc[v] = tloc[tb0 + v] | (lo << 8);
-            s_tperm[v] = tperm[tb0 + v];
-        }
+        stage_strip_targets(s_tloc, s_tperm, nt_strip, s_tb, bx1 - bx0, tb0, tloc, tperm);
         __syncthreads();
 
         const int n_chunks = (nt_strip + 31) >> 5;
@@ -741,6 +728,7 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
                 const SrcEntry<T>* src = s_src + s_ra[li][r];
                 const int len = active ? s_rl[li][r] : 0;
                 int j = 0;
+#pragma unroll 2
                 for (; j + 4 <= len; j += 4) {
                     const SrcEntry<T> e0 = src[j], e1 = src[j + 1], e2 = src[j + 2], e3 = src[j + 3];
                     T b = tp[-e0.off] * e0.f;
