@@ -552,11 +552,17 @@ __global__ void __launch_bounds__(LCfg<T, NP>::WARPS * 32, sizeof(T) == 4 ? 2 : 
 
 // P2P + L2P over a list of strips (problem, leaf row, first leaf column): the
 // uniform-tree strip kernel with per-problem leaf grids and compact-id lookups.
+// Six warps per block and staging for 2,048 sources and 1,536 targets: four blocks per SM
+// at binary32 (forest_4096, mixed p = 7: 2.25 ms with eight warps and room for 4,096
+// sources and 2,048 targets, three blocks per SM; 2.22 ms with eight warps and these
+// caps; 2.73 / 2.23 / 2.00 / 1.95 ms with two / three / four / six warps).  Forest strips
+// are short (rows of 8 to 32 leaves of ~16 targets), so fewer warps per strip idle less
+// at the strip's barriers.
 template <typename T>
 struct LStripCfg {
-    static constexpr int WARPS = 8;
-    static constexpr int CAPS = sizeof(T) == 4 ? 4096 : 2048;
-    static constexpr int CAPT = 2048;
+    static constexpr int WARPS = 6;
+    static constexpr int CAPS = 2048;
+    static constexpr int CAPT = 1536;
     static constexpr int MAXSW = 32;
     // the builder sizes strips with the smallest of these (kStripCapSrc: the binary64 case)
     static_assert(MAXSW == kStripMaxSW && CAPT == kStripCapTgt && CAPS >= kStripCapSrc, "strip staging caps");
@@ -915,16 +921,26 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
             pt.add_launches(1);
         }
     }
-    // ---- downward sweep in one persistent launch (M2L + L2L, coarse to fine)
+    // ---- downward sweep (M2L + L2L, coarse to fine): one persistent launch for the levels
+    // k >= k_pers, then one tensor-core launch per finer level (binary32 levels of at
+    // least kTcListMinBoxes boxes; the boxes per level do not grow with k, so these are
+    // the finest ones)
+    auto tc_level = [&](int k) -> bool {
+        if constexpr (std::is_same<T, float>::value)
+            return F.tc_list && F.tc_split && F.levels[k].nb >= kTcListMinBoxes && status_word != nullptr;
+        return false;
+    };
     bool down_done = false;
+    int k_pers = 0;
     if (far && up_done && nk <= kMaxForestLevels) {  // its counters were zeroed with the upward sweep's
+        while (k_pers < nk && tc_level(k_pers)) ++k_pers;
         PhaseTimer pt(LFMM_PHASE_M2L, s);
         DownSweep<T> D;
         D.n = 0;
         D.part = (T*)F.m2l_part;
         D.cpart = nullptr;
         bool ok = true;
-        for (int k = nk - 1; k >= 0; --k) {
+        for (int k = nk - 1; k >= k_pers; --k) {
             const ForestLevel& lv = F.levels[k];
             if (lv.nb == 0) continue;
             int64_t maxc = 0;
@@ -967,10 +983,12 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                 pt.add_launches(1);
                 down_done = true;
             }
+        } else if (ok) {
+            down_done = true;  // every level with boxes runs on the tensor cores
         }
     }
-    if (far && !down_done) {
-        for (int k = nk - 1; k >= 0; --k) {
+    if (far) {
+        for (int k = (down_done ? k_pers : nk) - 1; k >= 0; --k) {
             const ForestLevel& lv = F.levels[k];
             if (lv.nb == 0) continue;
             const bool l2l = k + 1 < nk;

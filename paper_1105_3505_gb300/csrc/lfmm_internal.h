@@ -257,7 +257,7 @@ struct ForestLevel {
 // sources and targets per block.
 constexpr int kStripMaxSW = 32;
 constexpr int kStripCapSrc = 2048;
-constexpr int kStripCapTgt = 2048;
+constexpr int kStripCapTgt = 1536;
 
 struct Forest {
     int np = 0;

@@ -249,6 +249,33 @@ def test_forest_persistent_sweeps_equal_per_level(lfmm, precision):
         assert rel_err(u_fused[to[i]:to[i + 1]], ref) <= tol
 
 
+@pytest.mark.parametrize("p", [8, 16])
+def test_forest_persistent_sweeps_with_tensor_core_levels(lfmm, p):
+    """Mixed path, default tensor-core levels: the persistent downward sweep takes the
+    coarse levels and the levels of at least 1,024 boxes follow as tensor-core launches,
+    the same kernels as in the per-level form, so the two forms stay bit-identical."""
+    probs = forest_case(zlib.crc32(b"fused-tc"), 48, n_min=500, n_max=6000)
+    src, so, tgt, to, f = concat(probs)
+    with lfmm.Forest(src, so, tgt, to, precision=lfmm.LFMM_MIXED, p=p) as fo:
+        lfmm.lfmm_profile_enable(True)
+        lfmm.lfmm_profile_read(reset=True)
+        try:
+            u_level = fo.eval(f)
+            prof_level = lfmm.lfmm_profile_read(reset=True)
+            fo.set_flags(persistent=True)
+            u_fused = fo.eval(f)
+            prof = lfmm.lfmm_profile_read(reset=True)
+        finally:
+            lfmm.lfmm_profile_enable(False)
+        fo.status()
+    assert np.array_equal(u_fused, u_level)
+    assert prof["m2l_tc"][1] > 0 and prof["m2l_tc"][1] == prof_level["m2l_tc"][1]
+    assert prof["m2m"][1] == 1 and prof["m2l"][1] == 1 and prof_level["m2l"][1] > 1
+    for i in (0, 47):
+        ref = oracle.lattice_sum(probs[i][0], probs[i][2], probs[i][1])
+        assert rel_err(u_fused[to[i]:to[i + 1]], ref) <= MIXED_TOL
+
+
 def test_clustered_persistent_sweeps(lfmm):
     """A pruned tree of many levels (the persistent sweeps cross 9 grid barriers) against
     the per-level launches and the oracle."""
