@@ -108,11 +108,14 @@ typedef struct lfmm_opts {
  * are bit-identical either way. */
 #define LFMM_FLAG_SERIAL 2
 /* Pruned trees and forests: run the upward sweep (P2M of every leaf, then M2M level by
- * level) and the downward sweep (M2L + L2L level by level) of all problems each as one
- * persistent cooperative launch (blocks take work from per-level queues, bounded grid
- * barriers between levels) instead of one launch per level.  The results are
- * bit-identical either way; on the 4,096-problem forest the per-level launches measured
- * faster, so they are the default. */
+ * level) of all problems as one persistent cooperative launch, and the downward sweep
+ * (M2L + L2L, coarse to fine) as one persistent cooperative launch over the levels that
+ * run on the CUDA cores (blocks take work from per-level queues, bounded grid barriers
+ * between levels), followed by one tensor-core launch per finer level (mixed path,
+ * levels of at least 1,024 boxes, as in the default form).  The results are
+ * bit-identical either way; on the 4,096-problem forest the two forms measured within
+ * 1 % of each other (per-level launches slightly ahead), and per-level launches are the
+ * default. */
 #define LFMM_FLAG_PERSISTENT 4
 
 /* Tree storage.  UNIFORM: every box of every level is stored (Sec. 6), the layout for

@@ -198,6 +198,97 @@ __device__ __forceinline__ void m2m_list_warp(int64_t b, int lane, const int32_t
     if (lane == 0) Qout[b] = qv;
 }
 
+// M2M of a level with many parents (binary32, NP = 32, 256 threads): tiles of 64
+// consecutive compact parents, their children's expansions gathered through the child
+// lists into shared memory (row stride 132 floats; an empty child's row is zero), the
+// operator staged once per block; thread t computes parents 2 (t / 8) + {0, 1} of the
+// tile at outputs 4 (t % 8) + {0..3}, so every step of the 128-long contraction is two
+// broadcast words, one 16-byte operator word and eight multiply-adds.  Per output the
+// products are summed as in m2m_list_warp (one chain per child in ascending input
+// order, the chains added child by child) and the parent's charge is the same pairwise
+// sum, so both give bit-identical results.
+constexpr int kListM2MTile = 64;
+constexpr int kListM2MStride = 132;
+constexpr int64_t kListM2MTileMin = 4096;  // fewer parents: a warp or a block per parent
+constexpr size_t kListM2MSmem = (size_t)(128 * 32 + kListM2MTile * kListM2MStride) * sizeof(float);
+
+__global__ void __launch_bounds__(256) m2m_list_tiles_kernel(int64_t nb, const int32_t* __restrict__ ch,
+                                                             const float* __restrict__ qc,
+                                                             const float* __restrict__ m2m, const DF* __restrict__ Qin,
+                                                             float* __restrict__ qp, DF* __restrict__ Qout) {
+    griddep_wait();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sop = reinterpret_cast<float*>(smem_raw);  // [128 inputs][32 outputs]
+    float* sin = sop + 128 * 32;                      // [64 parents][132]
+    __shared__ int s_ch[kListM2MTile * 4];
+    block_stage16<4>(reinterpret_cast<uint4*>(sop), reinterpret_cast<const uint4*>(m2m), 128 * 32 / 4);
+    const int g = threadIdx.x >> 3, cq = threadIdx.x & 7;
+    const int64_t n_tiles = (nb + kListM2MTile - 1) / kListM2MTile;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t b0 = tile * kListM2MTile;
+        __syncthreads();  // the operator is staged; the previous tile's reads are done
+        s_ch[threadIdx.x] = b0 + (threadIdx.x >> 2) < nb ? ch[b0 * 4 + threadIdx.x] : -1;
+        __syncthreads();
+        {
+            // 64 parents x 4 children x 8 float4, eight per thread, the loads first
+            float4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = threadIdx.x + 256 * u, it = i >> 5, k4 = i & 31;
+                const int child = s_ch[it * 4 + (k4 >> 3)];
+                x[u] = child >= 0 ? __ldg(reinterpret_cast<const float4*>(qc + (size_t)child * 32) + (k4 & 7))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = threadIdx.x + 256 * u, it = i >> 5, k4 = i & 31;
+                *reinterpret_cast<float4*>(sin + it * kListM2MStride + 4 * k4) = x[u];
+            }
+        }
+        if (threadIdx.x < kListM2MTile && b0 + threadIdx.x < nb) {
+            DF q[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int child = s_ch[threadIdx.x * 4 + c];
+                q[c] = child >= 0 ? Qin[child] : DF{0.f, 0.f};
+            }
+            Qout[b0 + threadIdx.x] = df_add(df_add(q[0], q[1]), df_add(q[2], q[3]));
+        }
+        __syncthreads();
+        const float* x0p = sin + (2 * g) * kListM2MStride;
+        const float* x1p = x0p + kListM2MStride;
+        float r0[4], r1[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                const int k = 32 * c + l;
+                const float4 o = *reinterpret_cast<const float4*>(sop + k * 32 + 4 * cq);
+                const float x0 = x0p[k], x1 = x1p[k];
+                a0[0] = fmaf(o.x, x0, a0[0]);
+                a0[1] = fmaf(o.y, x0, a0[1]);
+                a0[2] = fmaf(o.z, x0, a0[2]);
+                a0[3] = fmaf(o.w, x0, a0[3]);
+                a1[0] = fmaf(o.x, x1, a1[0]);
+                a1[1] = fmaf(o.y, x1, a1[1]);
+                a1[2] = fmaf(o.z, x1, a1[2]);
+                a1[3] = fmaf(o.w, x1, a1[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                r0[j] = c == 0 ? a0[j] : r0[j] + a0[j];
+                r1[j] = c == 0 ? a1[j] : r1[j] + a1[j];
+            }
+        }
+        const int64_t p0 = b0 + 2 * g;
+        if (p0 < nb)
+            *reinterpret_cast<float4*>(qp + (size_t)p0 * 32 + 4 * cq) = make_float4(r0[0], r0[1], r0[2], r0[3]);
+        if (p0 + 1 < nb)
+            *reinterpret_cast<float4*>(qp + (size_t)(p0 + 1) * 32 + 4 * cq) = make_float4(r1[0], r1[1], r1[2], r1[3]);
+    }
+}
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) m2m_list_kernel(int64_t nb, const int32_t* __restrict__ ch,
                                                        const T* __restrict__ qc, const T* __restrict__ m2m,
@@ -909,6 +1000,21 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
                 LFMM_CUDA_TRY(cudaGetLastError());
                 pt.add_launches(1);
                 continue;
+            }
+            if constexpr (std::is_same<T, float>::value) {
+                if (NP == 32 && lv.nb >= kListM2MTileMin) {  // many parents: 64-parent tiles
+                    const void* fn = (const void*)m2m_list_tiles_kernel;
+                    LFMM_CUDA_TRY(ensure_dynamic_smem(fn, kListM2MSmem));
+                    const int64_t tiles = (lv.nb + kListM2MTile - 1) / kListM2MTile;
+                    const int64_t grid =
+                        std::min<int64_t>(tiles, (int64_t)num_sms * std::max(1, blocks_per_sm(fn, 256, kListM2MSmem)));
+                    (void)launch_dependent(m2m_list_tiles_kernel, dim3((unsigned)grid), dim3(256), kListM2MSmem, s,
+                                           lv.nb, lv.ch, Qx(k - 1), (const float*)ops.m2m[k], Qm(k - 1), Qx(k),
+                                           Qm(k));
+                    LFMM_CUDA_TRY(cudaGetLastError());
+                    pt.add_launches(1);
+                    continue;
+                }
             }
             int64_t blocks = std::min<int64_t>((lv.nb * 32 + 255) / 256, 152 * 8);
             if (NP == 32)
