@@ -65,6 +65,12 @@ __device__ __forceinline__ DF fma(DF a, DF b, DF c) {
     return DF{hi, t - (hi - s)};
 }
 
+// N elements of T loaded and stored as one unit (16-byte aligned from 16 bytes up)
+template <typename T, int N>
+struct alignas(sizeof(T) * N > 16 ? 16 : sizeof(T) * N) VecT {
+    T v[N];
+};
+
 // read-only loads of any element type
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) {

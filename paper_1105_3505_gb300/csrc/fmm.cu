@@ -36,10 +36,6 @@ namespace {
 // each source's row of T_ofs^T is one or two 16-byte loads per lane, so a source step
 // of the warp serves four leaves.  Writes the sorted charges in T, the outgoing
 // expansion and the leaf's total charge (Morton index).
-template <typename T, int N>
-struct alignas(sizeof(T) * N > 16 ? 16 : sizeof(T) * N) VecT {
-    T v[N];
-};
 
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) p2m_kernel(int L, const int32_t* __restrict__ begin,

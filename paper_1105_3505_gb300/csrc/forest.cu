@@ -40,27 +40,39 @@ int grid_for(int64_t n, int threads, int cap = 152 * 16) {
 }
 
 // ------------------------------------------------------------------------- sweeps
-// P2M: one warp per compact leaf; its sources are [rl_s[j], rl_s[j + 1]), j = the leaf's
-// row-major index.
+// P2M of compact leaves b0 .. b0 + 3 (those below nb): a quarter warp per leaf, lane h
+// of a quarter owning expansion entries [h PL, h PL + PL), PL = NP / 8; leaf b's sources
+// are [rl_s[j], rl_s[j + 1]), j = the leaf's row-major index.
 template <typename T, int NP>
-__device__ __forceinline__ void p2m_list_warp(int64_t b, int lane, const int32_t* __restrict__ leaf_rl,
+__device__ __forceinline__ void p2m_list_quad(int64_t b0, int64_t nb, int lane, const int32_t* __restrict__ leaf_rl,
                                               const int32_t* __restrict__ rl_s, const int32_t* __restrict__ loc,
                                               const int32_t* __restrict__ perm, const double* __restrict__ f,
                                               T* __restrict__ f_sorted, const T* __restrict__ tofsT, int side,
                                               T* __restrict__ qhat, typename Mono<T>::V* __restrict__ Q) {
     using M = Mono<T>;
-    constexpr int PL = NP / 32;
-    const int j = leaf_rl[b];
-    const int s0 = rl_s[j], s1 = rl_s[j + 1];
+    constexpr int G = 8, PL = NP / G;
+    using Row = VecT<T, PL>;
+    const int grp = lane >> 3, hl = lane & (G - 1);
+    const int64_t b = b0 + grp;
+    const bool lv = b < nb;
+    int s0 = 0, s1 = 0;
+    if (lv) {
+        const int j = leaf_rl[b];
+        s0 = rl_s[j];
+        s1 = rl_s[j + 1];
+    }
+    const int cnt = s1 - s0;
+    int cmax = max(cnt, __shfl_xor_sync(kFull, cnt, 8));
+    cmax = max(cmax, __shfl_xor_sync(kFull, cmax, 16));
     T acc[PL];
 #pragma unroll
     for (int i = 0; i < PL; ++i) acc[i] = T(0);
     typename M::V qsum = M::zero();
-    for (int j0 = s0; j0 < s1; j0 += 32) {
-        const int j = j0 + lane;
+    for (int j0 = 0; j0 < cmax; j0 += G) {
         T fj = T(0);
         int J = 0;
-        if (j < s1) {
+        if (j0 + hl < cnt) {
+            const int j = s0 + j0 + hl;
             const int l = loc[j];
             J = (l & 0xffff) + side * (l >> 16);
             const double fd = f[perm[j]];
@@ -68,19 +80,25 @@ __device__ __forceinline__ void p2m_list_warp(int64_t b, int lane, const int32_t
             f_sorted[j] = fj;
             qsum = M::add(qsum, M::from_double(fd));
         }
-        const int cnt = min(32, s1 - j0);
-        for (int kk = 0; kk < cnt; ++kk) {
-            const T fk = shfl(fj, kk);
-            const T* row = tofsT + (size_t)shfl(J, kk) * NP;
+        const int cc = min(G, cmax - j0);
+        for (int k = 0; k < cc; ++k) {
+            // lanes of a quarter with fewer sources multiply row 0 by zero
+            const T fk = shfl(fj, (grp << 3) + k);
+            const int Jk = __shfl_sync(kFull, J, (grp << 3) + k);
+            const Row r = *reinterpret_cast<const Row*>(tofsT + (size_t)Jk * NP + hl * PL);
 #pragma unroll
-            for (int i = 0; i < PL; ++i) acc[i] = fma(ldg(row + lane + 32 * i), fk, acc[i]);
+            for (int i = 0; i < PL; ++i) acc[i] = fma(r.v[i], fk, acc[i]);
         }
     }
+    if (lv) {
+        Row o;
 #pragma unroll
-    for (int i = 0; i < PL; ++i) qhat[(size_t)b * NP + lane + 32 * i] = acc[i];
+        for (int i = 0; i < PL; ++i) o.v[i] = acc[i];
+        *reinterpret_cast<Row*>(qhat + (size_t)b * NP + hl * PL) = o;
+    }
 #pragma unroll
-    for (int off = 16; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
-    if (lane == 0) Q[b] = qsum;
+    for (int off = 4; off; off >>= 1) qsum = M::add(qsum, shfl_xor_v(qsum, off));
+    if (lv && hl == 0) Q[b] = qsum;
 }
 
 template <typename T, int NP>
@@ -94,8 +112,8 @@ __global__ void __launch_bounds__(256) p2m_list_kernel(int64_t nb, const int32_t
     griddep_wait();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nw)
-        p2m_list_warp<T, NP>(b, lane, leaf_rl, rl_s, loc, perm, f, f_sorted, tofsT, side, qhat, Q);
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; 4 * w < nb; w += nw)
+        p2m_list_quad<T, NP>(4 * w, nb, lane, leaf_rl, rl_s, loc, perm, f, f_sorted, tofsT, side, qhat, Q);
 }
 
 // M2M: one warp per compact parent; children by compact id (-1: empty).
@@ -558,7 +576,8 @@ struct UpSweep {
 };
 
 // Work queue: a warp takes kUpChunk consecutive boxes of a level at a time from the
-// level's counter (ctr[k], zero before the launch), so that uneven boxes balance out.
+// level's counter (ctr[k], zero before the launch), so that uneven boxes balance out;
+// P2M takes the chunk's four leaves at once (p2m_list_quad, as the per-level kernel).
 constexpr int kUpChunk = 4;
 
 template <typename T, int NP>
@@ -573,14 +592,14 @@ __global__ void __launch_bounds__(256) forest_up_kernel(const UpSweep<T> U, unsi
             if (lane == 0) c0 = atomicAdd(ctr + k, (unsigned long long)kUpChunk);
             c0 = __shfl_sync(kFull, c0, 0);
             if ((int64_t)c0 >= nb) break;
-            const int64_t c1 = min((int64_t)c0 + kUpChunk, nb);
-            for (int64_t b = (int64_t)c0; b < c1; ++b) {
-                if (k == 0)
-                    p2m_list_warp<T, NP>(b, lane, U.leaf_rl, U.rl_s, U.loc, U.perm, U.f, U.f_sorted, U.tofsT,
-                                         U.side, U.q[0], U.Q[0]);
-                else
-                    m2m_list_warp<T, NP, true>(b, lane, U.ch[k], U.q[k - 1], U.m2m[k], U.Q[k - 1], U.q[k], U.Q[k]);
+            if (k == 0) {  // the chunk's four leaves, a quarter warp each
+                p2m_list_quad<T, NP>((int64_t)c0, nb, lane, U.leaf_rl, U.rl_s, U.loc, U.perm, U.f, U.f_sorted,
+                                     U.tofsT, U.side, U.q[0], U.Q[0]);
+                continue;
             }
+            const int64_t c1 = min((int64_t)c0 + kUpChunk, nb);
+            for (int64_t b = (int64_t)c0; b < c1; ++b)
+                m2m_list_warp<T, NP, true>(b, lane, U.ch[k], U.q[k - 1], U.m2m[k], U.Q[k - 1], U.q[k], U.Q[k]);
         }
     }
 }
@@ -973,7 +992,7 @@ int forest_eval(const Forest& F, const DeviceOps& ops, const double* f, T* f_sor
         PhaseTimer pt(LFMM_PHASE_P2M, s);
         const ForestLevel& l0 = F.levels[0];
         if (l0.nb > 0) {
-            int64_t blocks = std::min<int64_t>((l0.nb * 32 + 255) / 256, 152 * 64);
+            int64_t blocks = std::min<int64_t>((l0.nb * 8 + 255) / 256, 152 * 64);  // four leaves per warp
             if (NP == 32)
                 (void)launch_dependent(p2m_list_kernel<T, 32>, dim3((int)blocks), dim3(256), 0, s, l0.nb, l0.rl, F.rl_s,
                                        F.sloc, F.sperm, f, f_sorted, (const T*)ops.tofsT, F.side, Qx(0), Qm(0));
