@@ -235,9 +235,12 @@ def traffic_for(kernel: str):
     e = d.get(kernel)
     if not e:
         return None
-    src = os.path.join(ROOT, "paper_1105_3505_gb300", "csrc", e["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return e["bytes_per_launch"] if h == e.get("source_sha256_16") else None
+    names = e["source"] if isinstance(e["source"], list) else [e["source"]]
+    h = hashlib.sha256()
+    for name in names:  # the kernel's file and the headers it includes
+        with open(os.path.join(ROOT, "paper_1105_3505_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return e["bytes_per_launch"] if h.hexdigest()[:16] == e.get("source_sha256_16") else None
 
 
 # ---------------------------------------------------------------- equal-accuracy binary64 arm

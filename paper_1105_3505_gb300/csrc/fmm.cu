@@ -835,10 +835,12 @@ __global__ void __launch_bounds__(kP2PWarps * 32) p2p_leaf_kernel(
 // (bx - bx0) * s and the pair loop stays one load and one multiply-add per pair.
 // Targets and leaf charges of the strip are staged alongside.  The strip form computes
 // the near field alone (the far field has its own L2P kernel).  The host picks SW so
-// the staged data fit (3 (SW+2) max_leaf_src <= CAPS).
+// the staged data fit (3 (SW+2) max_leaf_src <= CAPS).  Twelve warps per block, three
+// blocks per SM at binary32 (uniform_1m, mixed p = 8: 117 us against 127 us with eight
+// warps and 145 us with sixteen, two blocks per SM).
 template <typename T>
 struct StripCfg {
-    static constexpr int WARPS = 8;
+    static constexpr int WARPS = 12;
     static constexpr int CAPS = sizeof(T) == 4 ? 4096 : 2048;  // staged sources
     static constexpr int CAPT = 2048;                          // staged targets
     static constexpr int MAXSW = 32;
