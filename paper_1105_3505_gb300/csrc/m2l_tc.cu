@@ -39,6 +39,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive_n(uint64_t* bar, uint32_t n) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(n) : "memory");
+}
+// one arrival on `bar` once every cp.async this thread issued before has landed (the
+// arrival counts against the barrier's expected count)
+__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // non-blocking probe of a phase; the pipeline's role threads poll with it (a suspended
 // try_wait can sleep past the phase change, and every K-step waits three times)
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
@@ -518,11 +526,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1) m2l_tma_kernel(
 // applies.  Same pipeline as the TMA form, with the
 // copies done by four producer warps, 32 rows each: eight lanes per row and four rows
 // per instruction (16-byte cp.async, coalesced 128-byte rows), written straight into the
-// 128-byte swizzled layout, missing sources zero-filled.  Each producer warp announces
-// its rows on the stage's "full" barrier once they have landed (cp.async groups, kept
-// kLStages - 2 deep, then a proxy fence); producer warp 0 adds the operator tile's bulk
-// copy.  (Measured: the K-steps taken in turn by whole warps, each announced as soon as
-// it lands, and a deeper ring announced later were both slower.)
+// 128-byte swizzled layout, missing sources zero-filled.  Every producer lane arrives on
+// the stage's "full" barrier through cp.async.mbarrier.arrive.noinc, which fires when
+// that lane's copies have landed, so a stage is released to the MMA thread as soon as
+// its rows are in, however far ahead the producers have run; the MMA thread makes the
+// rows visible to the tensor core with a proxy fence after its wait.  Producer warp 0
+// adds the operator tile's bulk copy.  (Measured before: announcing each warp's rows
+// two cp.async groups late, the K-steps taken in turn by whole warps, and a deeper ring
+// announced later.)
 //   warps 0-3: fold (one box per TMEM lane), warps 4-7: gather, warp 8: MMA issuer,
 //   warp 9: compensated incoming constants.
 constexpr int kLStages = 4;
@@ -589,7 +600,7 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
             if (c < 4) t += (cls_start[c + 1] - cls_start[c] + 127) / 128;
         }
         for (int i = 0; i < kLStages; ++i) {
-            mbar_init(&full[i], 5);  // four producer warps + the operator tile (with its bytes)
+            mbar_init(&full[i], 4 * 32 + 1);  // every producer lane's copies + the operator tile (with its bytes)
             mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < kTmaAcc; ++i) {
@@ -630,7 +641,6 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
         const int sub = lane >> 3, ch = lane & 7;  // row within a group of four, 16-byte chunk
         int it = 0, st = 0, h = 0, slot = 0, use = 0, cls = 0;
         long long b0 = 0, b1 = 0;
-        int pend = 0;  // first ring step whose rows this warp has not announced
         int gs = 0;
         for (; gs < total; ++gs) {
             if (__any_sync(0xffffffffu, *vabort != 0)) break;  // warp-uniform
@@ -674,15 +684,8 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
                              "l"(ls + off), "r"(bytes)
                              : "memory");
             }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            // announce the rows of the K-step kLStages - 2 groups back
-            if (gs - pend >= kLStages - 2) {
-                asm volatile("cp.async.wait_group %0;\n" ::"n"(kLStages - 2) : "memory");
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[pend % kLStages]);
-                ++pend;
-            }
+            // the stage's barrier counts this lane once its copies have landed
+            cp_async_mbar_arrive_noinc(&full[slot]);
             if (lane == 0) s_pissued[pw] = gs + 1;
             if (++slot == kLStages) {
                 slot = 0;
@@ -696,13 +699,8 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
                 }
             }
         }
-        // announce what is left (also after an abort, so that the teardown's waits end);
-        // the operator tile of a step this warp did not issue is never awaited
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0)
-            for (; pend < gs; ++pend) mbar_arrive(&full[pend % kLStages]);
+        // nothing of this lane's in flight when the CTA ends
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else if (warp == 8) {
         if (lane == 0) {
             // per K slice: D_big[0, 2 NP) (+)= A_hi x [B_hi | B_lo], D_small = D_big + NP +=
@@ -716,6 +714,7 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
                     abort_now();
                     break;
                 }
+                fence_proxy_async_smem();  // the producers' cp.async rows, seen by the tensor core
                 tc_fence_after();
                 const uint32_t a_hi = base + (uint32_t)slot * kLStageBytes, a_lo = a_hi + kTmaABytes;
                 const uint32_t b_hi = a_hi + 2 * kTmaABytes;
@@ -819,13 +818,14 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
     __syncwarp();
     __syncthreads();
     if (s_abort && threadIdx.x == 0) {
-        // Every producer warp announced the steps it issued, but the warps stopped at
-        // different steps.  A warp issues step g + kLStages only after step g's stage was
-        // consumed, so the steps issued by some warps and not by others are fewer than
-        // kLStages, each in its own slot and phase: arrive for the warps that skipped them
-        // (and for warp 0's operator-tile arrival), then wait until the copies of the last
-        // kLStages issued steps have landed and the MMAs issued have completed (a commit
-        // tracks every MMA before it).
+        // Every producer lane arrived for the steps its warp issued, but the warps stopped
+        // at different steps.  A warp issues step g + kLStages only after step g's stage
+        // was consumed, so the steps issued by some warps and not by others are fewer than
+        // kLStages, each in its own slot and phase: arrive for the 32 lanes of each warp
+        // that skipped them (and for warp 0's operator-tile arrival), then wait until the
+        // operator copies of the last kLStages issued steps have landed (the lanes waited
+        // for their own cp.async) and the MMAs issued have completed (a commit tracks every
+        // MMA before it).
         int pmin = s_pissued[0], pmax = s_pissued[0];
         for (int i = 1; i < 4; ++i) {
             pmin = min(pmin, s_pissued[i]);
@@ -833,8 +833,8 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
         }
         for (int g = pmin; g < pmax; ++g) {
             int missing = s_pissued[0] <= g ? 1 : 0;
-            for (int i = 0; i < 4; ++i) missing += s_pissued[i] <= g ? 1 : 0;
-            for (int j = 0; j < missing; ++j) mbar_arrive(&full[g % kLStages]);
+            for (int i = 0; i < 4; ++i) missing += s_pissued[i] <= g ? 32 : 0;
+            if (missing > 0) mbar_arrive_n(&full[g % kLStages], (uint32_t)missing);
         }
         for (int g = pmax > kLStages ? pmax - kLStages : 0; g < pmax; ++g)
             mbar_poll_bounded(&full[g % kLStages], (uint32_t)((g / kLStages) & 1));
