@@ -645,13 +645,20 @@ __global__ void __launch_bounds__(kLThreads, 1) m2l_tc_list_kernel(
         for (; gs < total; ++gs) {
             if (__any_sync(0xffffffffu, *vabort != 0)) break;  // warp-uniform
             if (st == 0 && h == 0) {
+                // lane r: the 27 list entries and the parent of row r, seven loads in flight
                 tile_of(it, cls, b0, b1);
-                for (int i = lane; i < 32 * 28; i += 32) {
-                    const int r = i / 28, k = i % 28;
-                    const long long b = b0 + 32 * pw + r;
-                    int v = -1;
-                    if (b < b1) v = k < 27 ? il[b * 27 + k] : (has_l2l ? par[b] : -1);
-                    my_src[i] = v;
+                const long long b = b0 + 32 * pw + lane;
+                const bool bv = b < b1;
+#pragma unroll
+                for (int k0 = 0; k0 < 28; k0 += 7) {
+                    int v[7];
+#pragma unroll
+                    for (int u = 0; u < 7; ++u) {
+                        const int k = k0 + u;
+                        v[u] = !bv ? -1 : k < 27 ? il[b * 27 + k] : (has_l2l ? par[b] : -1);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 7; ++u) my_src[lane * 28 + k0 + u] = v[u];
                 }
                 __syncwarp();
             }
