@@ -885,20 +885,34 @@ __global__ void __launch_bounds__(StripCfg<T>::WARPS * 32) p2p_strip_kernel(
         const int c_lo = max(bx0 - 1, 0), c_hi = min(bx1, n - 1);
         const int ncol = c_hi - c_lo + 1;
         __syncthreads();  // previous strip done with the staging buffers
-        // leaf boundaries of the three source rows and the target row, leaf data
-        for (int i = threadIdx.x; i < 3 * (ncol + 1); i += blockDim.x) {
-            const int r = i / (ncol + 1), c = i % (ncol + 1);
-            const int yy = by + r - 1;
-            s_sb[r * (Cfg::MAXSW + 3) + c] = (yy >= 0 && yy < n) ? sbeg[(int64_t)yy * n + c_lo + c] : 0;
+        // leaf boundaries of the three source rows and the target row (int items), leaf
+        // charges and incoming constants (V items): a thread loads one of each, then stores
+        {
+            const int nA = 3 * (ncol + 1), nI = nA + (bx1 - bx0 + 1);
+            const int nC = 3 * ncol, nV = nC + (bx1 - bx0);
+            for (int i = threadIdx.x; i < max(nI, nV); i += blockDim.x) {
+                int iv = 0;
+                V vv = M::zero();
+                if (i < nA) {
+                    const int r = i / (ncol + 1), c = i % (ncol + 1);
+                    const int yy = by + r - 1;
+                    if (yy >= 0 && yy < n) iv = sbeg[(int64_t)yy * n + c_lo + c];
+                } else if (i < nI) {
+                    iv = tbeg[(int64_t)by * n + bx0 + (i - nA)];
+                }
+                if (i < nC) {
+                    const int r = i / ncol, c = i % ncol;
+                    const int yy = by + r - 1;
+                    if (yy >= 0 && yy < n) vv = Qleaf[morton2(c_lo + c, yy)];
+                } else if (i < nV && Cleaf) {
+                    vv = Cleaf[morton2(bx0 + (i - nC), by)];
+                }
+                if (i < nA) s_sb[(i / (ncol + 1)) * (Cfg::MAXSW + 3) + i % (ncol + 1)] = iv;
+                else if (i < nI) s_tb[i - nA] = iv;
+                if (i < nC) s_q[(i / ncol) * (Cfg::MAXSW + 2) + i % ncol] = vv;
+                else if (i < nV) s_c[i - nC] = vv;
+            }
         }
-        for (int i = threadIdx.x; i <= bx1 - bx0; i += blockDim.x) s_tb[i] = tbeg[(int64_t)by * n + bx0 + i];
-        for (int i = threadIdx.x; i < 3 * ncol; i += blockDim.x) {
-            const int r = i / ncol, c = i % ncol;
-            const int yy = by + r - 1;
-            s_q[r * (Cfg::MAXSW + 2) + c] = (yy >= 0 && yy < n) ? Qleaf[morton2(c_lo + c, yy)] : M::zero();
-        }
-        for (int i = threadIdx.x; i < bx1 - bx0; i += blockDim.x)
-            s_c[i] = Cleaf ? Cleaf[morton2(bx0 + i, by)] : M::zero();
         __syncthreads();
         // per-leaf source ranges (three staged rows) and near-field constant phi0 * Q_near
         for (int li = threadIdx.x; li < bx1 - bx0; li += blockDim.x) {

@@ -749,29 +749,51 @@ __global__ void __launch_bounds__(LStripCfg<T>::WARPS * 32) p2p_list_kernel(
             }
             return lo;
         };
-        for (int i = threadIdx.x; i < 3 * (ncol + 1); i += blockDim.x) {
-            const int r = i / (ncol + 1), c = i % (ncol + 1);
-            // first source at or after column c of the row (past its last column: the first
-            // source of the next occupied leaf, as in a dense bucket array)
-            const int j0 = s_rj[r][0];
-            s_sb[r * (Cfg::MAXSW + 3) + c] = j0 >= 0 ? rl_s[j0 + first_at(r, c)] : 0;
-        }
-        for (int i = threadIdx.x; i <= bx1 - bx0; i += blockDim.x) s_tb[i] = rl_t[s_rj[1][0] + first_at(1, bx0 + i - c_lo)];
-        for (int i = threadIdx.x; i < 3 * ncol; i += blockDim.x) {
-            const int r = i / ncol, c = i % ncol;
-            V qv = M::zero();
-            const int j0 = s_rj[r][0];
-            if (j0 >= 0) {
-                const int q = first_at(r, c);
-                if (j0 + q < s_rj[r][1] && s_lc[r][q] == c) qv = Qleaf[rl_id[j0 + q]];
+        // int items: the first source at or after column c of each row (past its last
+        // column: the first source of the next occupied leaf, as in a dense bucket array)
+        // and the target boundaries of the strip's leaves; V items: the leaf charges of the
+        // three rows and the strip leaves' incoming constants, through each leaf's compact
+        // id.  A thread takes one item of each kind and issues its loads before the stores.
+        {
+            const int nA = 3 * (ncol + 1), nI = nA + (bx1 - bx0 + 1);
+            const int nC = 3 * ncol, nV = nC + (bx1 - bx0);
+            for (int i = threadIdx.x; i < max(nI, nV); i += blockDim.x) {
+                int iv = 0;
+                if (i < nA) {
+                    const int r = i / (ncol + 1), c = i % (ncol + 1);
+                    const int j0 = s_rj[r][0];
+                    if (j0 >= 0) iv = rl_s[j0 + first_at(r, c)];
+                } else if (i < nI) {
+                    iv = rl_t[s_rj[1][0] + first_at(1, bx0 + (i - nA) - c_lo)];
+                }
+                int cid = -1;
+                if (i < nC) {
+                    const int r = i / ncol, c = i % ncol;
+                    const int j0 = s_rj[r][0];
+                    if (j0 >= 0) {
+                        const int q = first_at(r, c);
+                        if (j0 + q < s_rj[r][1] && s_lc[r][q] == c) cid = rl_id[j0 + q];
+                    }
+                } else if (i < nV) {
+                    const int cc = bx0 + (i - nC) - c_lo;
+                    const int q = first_at(1, cc);
+                    if (s_rj[1][0] + q < s_rj[1][1] && s_lc[1][q] == cc) cid = rl_id[s_rj[1][0] + q];
+                }
+                V vv = M::zero();
+                if (i < nC) {
+                    if (cid >= 0) vv = Qleaf[cid];
+                } else if (i < nV) {
+                    if (Cleaf && cid >= 0) vv = Cleaf[cid];
+                }
+                if (i < nA) s_sb[(i / (ncol + 1)) * (Cfg::MAXSW + 3) + i % (ncol + 1)] = iv;
+                else if (i < nI) s_tb[i - nA] = iv;
+                if (i < nC) {
+                    s_q[(i / ncol) * (Cfg::MAXSW + 2) + i % ncol] = vv;
+                } else if (i < nV) {
+                    s_has[i - nC] = cid;
+                    s_c[i - nC] = vv;
+                }
             }
-            s_q[r * (Cfg::MAXSW + 2) + c] = qv;
-        }
-        for (int i = threadIdx.x; i < bx1 - bx0; i += blockDim.x) {
-            const int q = first_at(1, bx0 + i - c_lo);
-            const int cid = (s_rj[1][0] + q < s_rj[1][1] && s_lc[1][q] == bx0 + i - c_lo) ? rl_id[s_rj[1][0] + q] : -1;
-            s_has[i] = cid;
-            s_c[i] = (Cleaf && cid >= 0) ? Cleaf[cid] : M::zero();
         }
         __syncthreads();
         // the strip's leaf expansions (four loads in flight per thread)
