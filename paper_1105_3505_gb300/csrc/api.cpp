@@ -412,6 +412,7 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     int32_t *fs_last = nullptr, *ft_last = nullptr;  // counts at the histogram level Lf_last
     int Lf_last = 0;
     int chosen = -1;
+    int early_side = 0;    // > 0: pruned storage decided on the way, the builder's first leaf side
     int64_t nonempty = 1;  // leaves holding a source or a target at the chosen level
     for (;;) {
         if (Lf > kMaxLevel)
@@ -446,6 +447,17 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         int32_t* ft = fs + nf;
         int32_t* ccs = ft + nf;
         int32_t* cct = ccs + nc;
+        // Clustered input: more than half of the boxes of the coarse level counted here are
+        // empty, hence of every finer level too (a non-empty box has a non-empty parent), so
+        // automatic storage is pruned whatever the leaf level turns out to be.  The forest
+        // builder finds the leaf side itself, starting at the largest side these counts
+        // leave possible; no finer (and larger) dense count is made.
+        if (p->opts.tree == LFMM_TREE_AUTO && Lf >= 1 && 2 * (int64_t)m4[5] < nc) {
+            if (Lf - 1 >= L_try && std::max(m4[2], m4[3]) <= nleaf) early_side = 1 << (p->K - Lf + 1);
+            else if (std::max(m4[0], m4[1]) <= nleaf || Lf == p->K) early_side = 1 << (p->K - Lf);
+            else early_side = 1 << std::max(0, p->K - Lf - 1);
+            break;
+        }
         if (Lf - 1 >= L_try && std::max(m4[2], m4[3]) <= nleaf) {
             chosen = Lf - 1;
             p->max_src = m4[2];
@@ -473,12 +485,12 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
         const int next = std::min({p->K, Lf + 2, kMaxLevel});
         Lf = next > Lf ? next : kMaxLevel + 1;
     }
-    p->L = chosen;
-    p->side = 1 << (p->K - p->L);
+    p->L = early_side > 0 ? 0 : chosen;
+    p->side = early_side > 0 ? early_side : 1 << (p->K - p->L);
     const int64_t n_leaves = (int64_t)1 << (2 * p->L);
 
     // ---- pruned storage: most leaves empty (or asked for)
-    const bool pruned = p->opts.tree == LFMM_TREE_PRUNED ||
+    const bool pruned = early_side > 0 || p->opts.tree == LFMM_TREE_PRUNED ||
                         (p->opts.tree == LFMM_TREE_AUTO && 2 * nonempty < n_leaves);
     if (pruned) {
         cnt.reset_now();
