@@ -79,6 +79,9 @@ struct lfmm_plan {
     double* un_tmp = nullptr;        // near field per target (caller order) from the concurrent near-field pass
     double* uf_tmp = nullptr;        // far field per target (caller order), before the final sum
     struct AuxStream* aux = nullptr;  // near-field pass runs here, beside the far-field sweeps
+    // uniform storage: the targets are bucketed on `aux` while the plan's creation and the
+    // evaluation's upward sweep go on; whatever reads them waits for this event
+    cudaEvent_t tgt_ready = nullptr;
     int64_t n_boxes = 0;
     // LFMM_FLAG_GRAPH: the recorded evaluation and the device pointers it was recorded for
     cudaStream_t cap_stream = nullptr;
@@ -145,6 +148,17 @@ void release_aux(AuxStream* a) {
     cudaStreamSynchronize(a->s);
     std::lock_guard<std::mutex> g(g_aux_mu);
     g_aux_free.push_back(a);
+}
+
+// Work on `s` that reads the bucketed targets waits for their bucketing (a no-op once it
+// has completed; skipped while `s` is being captured, whose graph is launched behind the
+// same wait).
+int wait_targets(const lfmm_plan* p, cudaStream_t s) {
+    if (!p->tgt_ready) return LFMM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LFMM_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) LFMM_CUDA_TRY(cudaStreamWaitEvent(s, p->tgt_ready, 0));
+    return LFMM_OK;
 }
 
 constexpr int kMaxLevel = 14;  // deepest leaf level searched (pruned storage beyond 4^13 leaves)
@@ -519,11 +533,30 @@ int plan_build(lfmm_plan* p, const int32_t* src_xy, const int32_t* tgt_xy, cudaS
     p->tgt_loc = p->src_perm + p->ns;
     p->tgt_perm = p->tgt_loc + p->nt;
     p->tgt_leaf = p->tgt_perm + p->nt;
-    // bucket by the histogram ranks (no second atomic pass)
+    // bucket by the histogram ranks (no second atomic pass): the sources on `s`, the targets
+    // (read first by the near field and L2P) on the plan's second stream, which then frees
+    // the ranks and counts both scatters read
     LFMM_CUDA_TRY(launch_scatter_ranked(src, p->ns, p->x0, p->y0, p->K, p->L, Lf_last, p->src_begin, fs_last,
                                         (const int32_t*)ranks.ptr, p->src_loc, p->src_perm, s));
+    cudaStream_t ts = s;
+    if (!(p->opts.flags & LFMM_FLAG_SERIAL) && p->L >= 2) {
+        if (!p->aux) p->aux = acquire_aux(p->device);
+        if (p->aux && cudaEventCreateWithFlags(&p->tgt_ready, cudaEventDisableTiming) == cudaSuccess) {
+            LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
+            LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
+            ts = p->aux->s;
+        } else {
+            cudaGetLastError();
+            p->tgt_ready = nullptr;
+        }
+    }
     LFMM_CUDA_TRY(launch_scatter_ranked(tgt, p->nt, p->x0, p->y0, p->K, p->L, Lf_last, p->tgt_begin, ft_last,
-                                        (const int32_t*)ranks.ptr + p->ns, p->tgt_loc, p->tgt_perm, s, p->tgt_leaf));
+                                        (const int32_t*)ranks.ptr + p->ns, p->tgt_loc, p->tgt_perm, ts, p->tgt_leaf));
+    if (ts != s) {
+        LFMM_CUDA_TRY(cudaEventRecord(p->tgt_ready, ts));
+        ranks.s = ts;  // freed behind the target scatter
+        cnt.s = ts;
+    }
     tree_timer->add_launches(2);
     tree_timer.reset();
     PhaseTimer op_timer(LFMM_PHASE_OPERATORS, s);
@@ -719,6 +752,10 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
             LFMM_CUDA_TRY(cudaEventRecord(p->aux->fork, s));
             LFMM_CUDA_TRY(cudaStreamWaitEvent(p->aux->s, p->aux->fork, 0));
         }
+        {
+            const int st = wait_targets(p, near_s);
+            if (st) return st;
+        }
         PhaseTimer pt(LFMM_PHASE_P2P, near_s);
         LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Q_leaf, nullptr, p->un_tmp,
                                         nullptr, p->num_sms, near_s));
@@ -731,6 +768,8 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
     }
     if (split) {
         {
+            const int st = wait_targets(p, s);
+            if (st) return st;
             PhaseTimer pt(LFMM_PHASE_L2P, s);
             LFMM_CUDA_TRY(launch_l2p<T>(t, ops, u_leaf, C_leaf, p->uf_tmp, s));
             pt.add_launches(1);
@@ -743,6 +782,8 @@ int eval_impl(lfmm_plan* p, const double* f, double* u, double* un, double* uf, 
         LFMM_CUDA_TRY(launch_combine(p->nt, p->un_tmp, p->uf_tmp, u, un, uf, s));
         pt.add_launches(1);
     } else {
+        const int st = wait_targets(p, s);
+        if (st) return st;
         PhaseTimer pt(LFMM_PHASE_P2P, s);
         LFMM_CUDA_TRY(launch_p2p_l2p<T>(t, ops, (const T*)p->f_sorted, nullptr, nullptr, Q_leaf, u, un, uf,
                                         p->num_sms, s));
@@ -763,6 +804,10 @@ constexpr int kMultiGroup = 16;
 template <typename T>
 int eval_multi_impl(lfmm_plan* p, const double* F, int k, double* U, cudaStream_t s) {
     const int L = p->L;
+    {
+        const int st = wait_targets(p, s);
+        if (st) return st;
+    }
     if (p->forest || L < 2 || !p->un_tmp) {  // one vector at a time
         for (int r = 0; r < k; ++r) {
             const int st = eval_impl<T>(p, F + (size_t)r * p->ns, U + (size_t)r * p->nt, nullptr, nullptr, s);
@@ -855,6 +900,10 @@ int eval_graph(lfmm_plan* p, const double* f, double* const out[3], cudaStream_t
         cudaGraphDestroy(g);
         p->graph_f = f;
         for (int i = 0; i < 3; ++i) p->graph_out[i] = out[i];
+    }
+    {
+        const int st = wait_targets(p, s);
+        if (st) return st;
     }
     LFMM_CUDA_TRY(cudaGraphLaunch(p->graph, s));
     return LFMM_OK;
@@ -991,8 +1040,10 @@ int lfmm_eval_parts(lfmm_plan* plan, const double* f, double* u_near, double* u_
 
 int lfmm_plan_destroy(lfmm_plan* plan) {
     if (!plan) return LFMM_OK;
+    if (plan->tgt_ready) cudaStreamWaitEvent(plan->last_stream, plan->tgt_ready, 0);
     free_plan_buffers(plan);
     cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    if (plan->tgt_ready) cudaEventDestroy(plan->tgt_ready);
     if (plan->graph) cudaGraphExecDestroy(plan->graph);
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     release_aux(plan->aux);
