@@ -277,6 +277,43 @@ __device__ __forceinline__ int64_t lower_bound_key(const uint64_t* __restrict__ 
     return lo;
 }
 
+// [first, end) of every box row of A (level k, problem p, row y; its entry is
+// row_off[k np + p] + y); rows without boxes keep {0, 0}
+__global__ void row_range_kernel(const uint64_t* __restrict__ A, int64_t na, int kb, int kbits, int np,
+                                 const int64_t* __restrict__ row_off, int2* __restrict__ rows) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < na; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = A[j], rk = key >> kb;
+        const bool head = j == 0 || (A[j - 1] >> kb) != rk;
+        const bool tail = j == na - 1 || (A[j + 1] >> kb) != rk;
+        if (!head && !tail) continue;
+        int p, y, x;
+        unpack_key(key & (((uint64_t)1 << kbits) - 1), kb, p, y, x);
+        const int64_t r = row_off[(key >> kbits) * np + p] + y;
+        if (head) rows[r].x = (int)j;
+        if (tail) rows[r].y = (int)(j + 1);
+    }
+}
+
+// First entry of A at or after key v = (k, p, y, x) within its row (the row's end if none;
+// `end` is set to the row's end), or, without a row table, within all of A.
+__device__ __forceinline__ int64_t find_in_row(const uint64_t* __restrict__ A, int64_t na,
+                                               const int2* __restrict__ rows, const int64_t* __restrict__ row_off,
+                                               int np, int k, int p, int y, uint64_t v, int64_t& end) {
+    int64_t lo = 0, hi = na;
+    if (rows) {
+        const int2 rr = rows[row_off[(int64_t)k * np + p] + y];
+        lo = rr.x;
+        hi = rr.y;
+    }
+    end = hi;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (A[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void pid_kernel(const int64_t* __restrict__ off, int np, int32_t* __restrict__ pid) {
     for (int p = blockIdx.x; p < np; p += gridDim.x)
         for (int64_t i = off[p] + threadIdx.x; i < off[p + 1]; i += blockDim.x) pid[i] = p;
@@ -486,6 +523,7 @@ __global__ void box_records_kernel(const uint64_t* __restrict__ A, const uint64_
 __global__ void links_kernel(int64_t n, const uint64_t* __restrict__ ck, const uint64_t* __restrict__ A, int64_t na,
                              const int32_t* __restrict__ local_of, const int32_t* __restrict__ bp,
                              const int32_t* __restrict__ bxy, const int32_t* __restrict__ L, int kb, int kbits, int kmax,
+                             const int2* __restrict__ rows, const int64_t* __restrict__ row_off, int np,
                              int32_t* __restrict__ par, int32_t* __restrict__ ch, int32_t* __restrict__ il) {
     __shared__ signed char s_slot[4][36];
     for (int t = threadIdx.x; t < 4 * 36; t += blockDim.x) (&s_slot[0][0])[t] = -1;
@@ -509,8 +547,9 @@ __global__ void links_kernel(int64_t n, const uint64_t* __restrict__ ck, const u
         int pr = -1;
         if (k + 1 <= kmax && l - 1 >= 2) {
             const uint64_t v = ((uint64_t)(k + 1) << kbits) | pack_key(p, y >> 1, x >> 1, kb);
-            const int64_t j = lower_bound_key(A, na, v);
-            if (j < na && A[j] == v) pr = local_of[j];
+            int64_t e;
+            const int64_t j = find_in_row(A, na, rows, row_off, np, k + 1, p, y >> 1, v, e);
+            if (j < e && A[j] == v) pr = local_of[j];
         }
         par[b] = pr;
         // children at level k - 1, two per row
@@ -518,13 +557,14 @@ __global__ void links_kernel(int64_t n, const uint64_t* __restrict__ ck, const u
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const uint64_t v = ((uint64_t)(k - 1) << kbits) | pack_key(p, 2 * y + r, 2 * x, kb);
-                int64_t j = lower_bound_key(A, na, v);
+                int64_t e;
+                int64_t j = find_in_row(A, na, rows, row_off, np, k - 1, p, 2 * y + r, v, e);
                 int c0 = -1, c1 = -1;
-                if (j < na && A[j] == v) {
+                if (j < e && A[j] == v) {
                     c0 = local_of[j];
                     ++j;
                 }
-                if (j < na && A[j] == v + 1) c1 = local_of[j];
+                if (j < e && A[j] == v + 1) c1 = local_of[j];
                 ch[b * 4 + 2 * r] = c0;
                 ch[b * 4 + 2 * r + 1] = c1;
             }
@@ -538,7 +578,9 @@ __global__ void links_kernel(int64_t n, const uint64_t* __restrict__ ck, const u
             const int yy = y + dy;
             if (yy < 0 || yy >= nn) continue;
             const uint64_t vhi = lev | pack_key(p, yy, xhi, kb);
-            for (int64_t j = lower_bound_key(A, na, lev | pack_key(p, yy, xlo, kb)); j < na && A[j] <= vhi; ++j) {
+            int64_t e;
+            for (int64_t j = find_in_row(A, na, rows, row_off, np, k, p, yy, lev | pack_key(p, yy, xlo, kb), e);
+                 j < e && A[j] <= vhi; ++j) {
                 const int dx = (int)(A[j] & cmask) - x;
                 const int sl = s_slot[c][(dy + 2 + py) * 6 + dx + 2 + px];
                 if (sl >= 0) out[sl] = local_of[j];
@@ -1092,8 +1134,35 @@ int forest_build(Forest& F, const int32_t* src, const int64_t* soff_h, int64_t n
     int32_t* leaf_rl = ch_all + 4 * NB;
     class_starts_kernel<<<(4 * nk + 1 + kT - 1) / kT, kT, 0, s>>>(ck, NB, nk, kbits, cstart);
     box_records_kernel<<<grid_of(NB), kT, 0, s>>>(A, ck, cidx, NB, cstart, kb, kbits, bp_all, bxy_all, local_of, leaf_rl);
-    links_kernel<<<grid_of(NB), kT, 0, s>>>(NB, ck, A, NB, local_of, bp_all, bxy_all, dL, kb, kbits, F.kmax, par_all,
-                                            ch_all, il_all);
+    // the [first, end) of every box row of A, so that the links' searches (parent, two child
+    // rows, six neighbour rows per box) cover one row instead of all of A; without it (a
+    // table far larger than the boxes) they search all of A
+    DevBuf rowbuf;
+    const int2* rows = nullptr;
+    const int64_t* row_off = nullptr;
+    {
+        std::vector<int64_t> ro((size_t)nk * np + 1, 0);
+        int64_t R = 0;
+        for (int k = 0; k < nk; ++k)
+            for (int p = 0; p < np; ++p) {
+                ro[(size_t)k * np + p] = R;
+                if (F.L[p] >= k) R += (int64_t)1 << (F.L[p] - k);
+            }
+        ro[(size_t)nk * np] = R;
+        if (R <= 8 * NB + ((int64_t)1 << 20)) {
+            if ((st = rowbuf.get((size_t)R * sizeof(int2) + ro.size() * sizeof(int64_t) + 16, s))) return st;
+            int2* rt = (int2*)rowbuf.ptr;
+            int64_t* ro_d = (int64_t*)(rt + R);
+            LFMM_CUDA_TRY(cudaMemsetAsync(rt, 0, (size_t)R * sizeof(int2), s));
+            LFMM_CUDA_TRY(cudaMemcpyAsync(ro_d, ro.data(), ro.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            row_range_kernel<<<grid_of(NB), kT, 0, s>>>(A, NB, kb, kbits, np, ro_d, rt);
+            rows = rt;
+            row_off = ro_d;
+            timer->add_launches(1);
+        }
+    }
+    links_kernel<<<grid_of(NB), kT, 0, s>>>(NB, ck, A, NB, local_of, bp_all, bxy_all, dL, kb, kbits, F.kmax, rows,
+                                            row_off, np, par_all, ch_all, il_all);
     LFMM_CUDA_TRY(cudaGetLastError());
     LFMM_CUDA_TRY(cudaMemcpyAsync(F.rl_id, local_of, (size_t)M * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     timer->add_launches(4 + 5 * ((kbits + 2 + lbits + 7) / 8));
