@@ -1017,9 +1017,13 @@ int lfmm_plan_create(lfmm_plan** plan, const int32_t* src_xy, int64_t n_src, con
     p->last_stream = (cudaStream_t)stream;
     st = plan_build(p, src_xy, tgt_xy, (cudaStream_t)stream);
     if (st) {
+        // the target scatter may still run on the second stream: it ends before the buffers go
+        if (p->tgt_ready) cudaEventSynchronize(p->tgt_ready);
         cudaStreamSynchronize((cudaStream_t)stream);
         cudaGetLastError();
         free_plan_buffers(p);
+        if (p->tgt_ready) cudaEventDestroy(p->tgt_ready);
+        release_aux(p->aux);
         delete p;
         return st;
     }
