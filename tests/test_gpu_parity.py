@@ -259,6 +259,33 @@ def test_device_and_host_pointers_agree(lfmm):
         assert np.abs(u_d.cpu().numpy() - u_h).max() <= (1e-12 if prec == lfmm.LFMM_FP64 else 1e-6) * scale
 
 
+def test_plan_created_on_one_stream_evaluated_on_another(lfmm):
+    """A uniform plan buckets its targets on a second stream; an evaluation queued at once
+    on another stream (eager or graph replay) waits for that, and gives the bits of a later
+    evaluation of the same plan (separately created plans may order a leaf's points
+    differently, so the comparison stays within one plan)."""
+    prob = workloads.uniform_box(200_000, 150_000, 2000, seed=12)
+    dev = torch.device("cuda:0")
+    s_d, t_d, f_d = (torch.from_numpy(a).to(dev) for a in (prob.src, prob.tgt, prob.f))
+    n_s, n_t = prob.src.shape[0], prob.tgt.shape[0]
+    a, b = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    o = lfmm.make_opts(lfmm.LFMM_MIXED, 8)
+    ref = oracle.lattice_sum(prob.src, prob.f, prob.tgt[:2000])
+    for flags in (0, lfmm.LFMM_FLAG_GRAPH):
+        first = torch.empty(n_t, dtype=torch.float64, device=dev)
+        again = torch.empty(n_t, dtype=torch.float64, device=dev)
+        h = lfmm.lfmm_plan_create(s_d, n_s, t_d, n_t, o, a)
+        lfmm.lfmm_plan_set_flags(h, flags)
+        lfmm.lfmm_eval(h, f_d, first, b)  # no host wait between the two streams
+        b.synchronize()
+        a.synchronize()
+        lfmm.lfmm_eval(h, f_d, again, a)
+        a.synchronize()
+        lfmm.lfmm_plan_destroy(h)
+        assert torch.equal(first, again)
+        assert rel_err(first[:2000].cpu().numpy(), ref) <= MIXED_TOL
+
+
 @pytest.fixture(scope="module")
 def uniform_1m():
     return workloads.uniform_1m()
