@@ -144,7 +144,10 @@ void lfmm_opts_default(lfmm_opts* opts);
  *   stream   cudaStream_t for all device work
  * The points must span at most 2^30 lattice cells per axis (LFMM_EINVAL).
  * Duplicate points are allowed (the sum is linear).  Synchronises `stream` twice
- * (the root box and the leaf level are read back to size the workspaces). */
+ * (the root box and the leaf level are read back to size the workspaces).  Uniform
+ * storage without LFMM_FLAG_SERIAL buckets the targets on a plan-owned second stream
+ * behind the work queued on `stream`; every later call that reads them (evaluation on
+ * any stream, graph replay, lfmm_plan_destroy) waits for it. */
 int lfmm_plan_create(lfmm_plan** plan, const int32_t* src_xy, int64_t n_src,
                      const int32_t* tgt_xy, int64_t n_tgt, const lfmm_opts* opts, void* stream);
 
