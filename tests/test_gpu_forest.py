@@ -47,6 +47,21 @@ def small_clustered(seed=7):
                                   seg_len=600.0, frac_lines=0.02, domain=4096)
 
 
+@pytest.mark.parametrize("seed", [7, 8, 9])
+def test_automatic_pruned_tree_equals_forced(lfmm, seed):
+    """Automatic storage turns to the pruned builder as soon as a count shows a mostly
+    empty level; the tree it gets (root, leaf level and side, boxes, fullest leaves) is the
+    one the full leaf-level search and forced pruned storage give."""
+    prob = small_clustered(seed=seed)
+    infos = []
+    for tree in (lfmm.LFMM_TREE_AUTO, lfmm.LFMM_TREE_PRUNED):
+        with lfmm.Plan(prob.src, prob.tgt, precision=lfmm.LFMM_MIXED, p=8, tree=tree) as pl:
+            infos.append(pl.info())
+    keys = ("tree", "x0", "y0", "K", "L", "leaf_side", "n_boxes", "max_leaf_src", "max_leaf_tgt")
+    assert [infos[0][k] for k in keys] == [infos[1][k] for k in keys]
+    assert infos[0]["tree"] == lfmm.LFMM_TREE_PRUNED
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed16", "df"])
 def test_pruned_clustered_full_oracle(lfmm, precision):
     prob = small_clustered()
